@@ -1,0 +1,505 @@
+/*
+ * Plain FP64 CPU oracle for the EAM hot path of the MOLDY paper
+ * (Ackland et al., "The MOLDY short-range molecular dynamics package").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the package smoke check and the
+ * benchmark's CPU-baseline leg may load or call this library.  It shares no code,
+ * header, table or constant with the CUDA library: every formula here is written
+ * out from the paper.
+ *
+ * Build: gcc -O2 -ffp-contract=off -fopenmp (no FMA contraction, so that the
+ * minimum-image distances are the same IEEE operations on every machine).
+ *
+ * What it computes (paper references by section / equation):
+ *   - neighbour sets by brute force over all pairs with the minimum image (§2.2)
+ *     and by the hybrid link-cell / neighbour-list method with padding (§3.2.1);
+ *   - the cohesive energy of Eq. (1), U = sum_{i<j} V(r_ij) + sum_i F_i(rho_i),
+ *     rho_i = sum_j phi_{s_i s_j}(r_ij) (asymmetric phi as in §2 and §3.1),
+ *     and the forces F = -grad U, from a full (symmetric) neighbour list (§3.2.2,
+ *     "calculate F_ij twice") and, as a cross-check, from the asymmetric half list
+ *     with F_ij applied to both atoms (§3.2.2);
+ *   - velocity-Verlet time integration (§2.3) in the units of §2.7;
+ *   - microstate thermodynamics: KE, T with 3N-3 degrees of freedom (§2.1.2, §2.6),
+ *     virial and pressure;
+ *   - the strain-rate boundary condition: the box matrix is multiplied by a strain
+ *     matrix each step with fractional coordinates fixed (§2.2).
+ * Parity: pinned by closed-form lattice energies, finite differences, brute force,
+ * Newton's third law and NVE energy conservation (tests/test_oracle_pins.py).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ---- units (§2.7): Å, amu, eV; user time in fs.  CODATA 2018. ---- */
+#define ORC_AMU_KG 1.66053906660e-27
+#define ORC_EV_J 1.602176634e-19
+#define ORC_KB 8.617333262e-5 /* eV / K */
+/* amu * (Å/fs)^2 in eV */
+#define ORC_MVV2E (ORC_AMU_KG * 1.0e10 / ORC_EV_J)
+#define ORC_EVA3_TO_GPA (ORC_EV_J * 1.0e30 / 1.0e9)
+
+typedef struct {
+    int32_t kind; /* 1: analytic Finnis-Sinclair (one species), 2: knot tables */
+    int32_t n_species;
+    int32_t n_knots;
+    int32_t pad;
+    double fs[7]; /* d, c, A, beta, c0, c1, c2 */
+    double r_min, r_cut, rho_min, rho_max;
+    const double *tables; /* V[a][b], phi[a][b], F[a]; each n values then n slopes */
+} orc_potential;
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+/* ------------------------------------------------------------------------- */
+/* Minimum image (§2.2): r_ij is the shortest vector from i to j or any of its
+ * periodic images.  Orthorhombic box of lengths L: d - L*rint(d/L), with d/L
+ * taken as d*(1/L).  Every operation separately rounded.                    */
+static double orc_min_image(double d, double L, double invL) {
+    return d - L * rint(d * invL);
+}
+
+static double orc_dist2(const double *pos, int64_t i, int64_t j, const double *L,
+                        const double *invL, double *dv) {
+    double dx = orc_min_image(pos[3 * j + 0] - pos[3 * i + 0], L[0], invL[0]);
+    double dy = orc_min_image(pos[3 * j + 1] - pos[3 * i + 1], L[1], invL[1]);
+    double dz = orc_min_image(pos[3 * j + 2] - pos[3 * i + 2], L[2], invL[2]);
+    if (dv) { dv[0] = dx; dv[1] = dy; dv[2] = dz; }
+    return (dx * dx + dy * dy) + dz * dz;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Neighbour sets.  j is a neighbour of i iff j != i and |r_ij|^2 < r_list^2,
+ * r_list = potential range + padding (§3.2.1, Table 1 `rpad`).  The list is the
+ * symmetric (full) one; each row is in ascending j.  Returns the largest count
+ * (rows longer than k_max are truncated; the caller compares with k_max).     */
+int32_t orc_neighbours_brute(int64_t n, const double *pos, const double *box, double r_list,
+                             int32_t k_max, int32_t *count, int32_t *list) {
+    double L[3] = {box[0], box[1], box[2]};
+    double invL[3] = {1.0 / box[0], 1.0 / box[1], 1.0 / box[2]};
+    double rl2 = r_list * r_list;
+    int32_t maxc = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(max : maxc)
+    for (int64_t i = 0; i < n; i++) {
+        int32_t c = 0;
+        for (int64_t j = 0; j < n; j++) {
+            if (j == i) continue;
+            if (orc_dist2(pos, i, j, L, invL, NULL) < rl2) {
+                if (c < k_max) list[i * k_max + c] = (int32_t)j;
+                c++;
+            }
+        }
+        count[i] = c;
+        if (c > maxc) maxc = c;
+    }
+    return maxc;
+}
+
+static int orc_cmp_i32(const void *a, const void *b) {
+    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return (x > y) - (x < y);
+}
+
+/* Hybrid link-cell / neighbour list (§3.2.1): link cells are fixed in fractional
+ * coordinates, at least r_list wide; an atom's candidates are the atoms of its own
+ * and the 26 adjacent cells.  Returns -1 if a box edge holds fewer than 3 cells.  */
+int32_t orc_neighbours_cells(int64_t n, const double *pos, const double *box, double r_list,
+                             int32_t k_max, int32_t *count, int32_t *list) {
+    double L[3] = {box[0], box[1], box[2]};
+    double invL[3] = {1.0 / box[0], 1.0 / box[1], 1.0 / box[2]};
+    int nc[3];
+    for (int k = 0; k < 3; k++) {
+        nc[k] = (int)floor(L[k] / r_list);
+        if (nc[k] < 3) return -1;
+    }
+    int64_t ncell = (int64_t)nc[0] * nc[1] * nc[2];
+    int64_t *head = (int64_t *)malloc(sizeof(int64_t) * (ncell + 1));
+    int64_t *cell_of = (int64_t *)malloc(sizeof(int64_t) * (n > 0 ? n : 1));
+    int64_t *members = (int64_t *)malloc(sizeof(int64_t) * (n > 0 ? n : 1));
+    memset(head, 0, sizeof(int64_t) * (ncell + 1));
+    for (int64_t i = 0; i < n; i++) {
+        int c[3];
+        for (int k = 0; k < 3; k++) {
+            double s = pos[3 * i + k] * invL[k];
+            s = s - floor(s); /* wrapped fractional coordinate */
+            c[k] = (int)(s * nc[k]);
+            if (c[k] >= nc[k]) c[k] = nc[k] - 1;
+            if (c[k] < 0) c[k] = 0;
+        }
+        cell_of[i] = ((int64_t)c[2] * nc[1] + c[1]) * nc[0] + c[0];
+        head[cell_of[i] + 1]++;
+    }
+    for (int64_t c = 0; c < ncell; c++) head[c + 1] += head[c];
+    {
+        int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (ncell > 0 ? ncell : 1));
+        memcpy(fill, head, sizeof(int64_t) * ncell);
+        for (int64_t i = 0; i < n; i++) members[fill[cell_of[i]]++] = i; /* ascending i per cell */
+        free(fill);
+    }
+    double rl2 = r_list * r_list;
+    int32_t maxc = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(max : maxc)
+    for (int64_t i = 0; i < n; i++) {
+        int64_t ci = cell_of[i];
+        int cx = (int)(ci % nc[0]), cy = (int)((ci / nc[0]) % nc[1]), cz = (int)(ci / ((int64_t)nc[0] * nc[1]));
+        int32_t c = 0;
+        for (int dz = -1; dz <= 1; dz++)
+            for (int dy = -1; dy <= 1; dy++)
+                for (int dx = -1; dx <= 1; dx++) {
+                    int x = (cx + dx + nc[0]) % nc[0], y = (cy + dy + nc[1]) % nc[1], z = (cz + dz + nc[2]) % nc[2];
+                    int64_t cc = ((int64_t)z * nc[1] + y) * nc[0] + x;
+                    for (int64_t m = head[cc]; m < head[cc + 1]; m++) {
+                        int64_t j = members[m];
+                        if (j == i) continue;
+                        if (orc_dist2(pos, i, j, L, invL, NULL) < rl2) {
+                            if (c < k_max) list[i * k_max + c] = (int32_t)j;
+                            c++;
+                        }
+                    }
+                }
+        count[i] = c;
+        if (c > maxc) maxc = c;
+        qsort(list + i * k_max, (size_t)(c < k_max ? c : k_max), sizeof(int32_t), orc_cmp_i32);
+    }
+    free(head);
+    free(cell_of);
+    free(members);
+    return maxc;
+}
+
+/* ------------------------------------------------------------------------- */
+/* The potential interface (§3.1): V, phi and their derivatives per species pair,
+ * F and F' per species.                                                     */
+
+/* Knot table: values y_k and slopes y'_k at uniform knots x_k = x0 + k h on
+ * [x0, x1]; cubic Hermite interpolation on each interval, written with the four
+ * Hermite basis polynomials; the derivative is that of the same cubic.  Outside
+ * [x0, x1]: linear extrapolation from the end knot, and a range count.       */
+static double orc_table(const double *tab, int n, double x0, double x1, double x, double *dydx,
+                        int64_t *viol) {
+    const double *y = tab, *yp = tab + n;
+    double h = (x1 - x0) / (double)(n - 1);
+    if (x < x0) {
+        (*viol)++;
+        *dydx = yp[0];
+        return y[0] + (x - x0) * yp[0];
+    }
+    if (x > x1) {
+        (*viol)++;
+        *dydx = yp[n - 1];
+        return y[n - 1] + (x - x1) * yp[n - 1];
+    }
+    double u = (x - x0) / h;
+    int k = (int)floor(u);
+    if (k > n - 2) k = n - 2;
+    if (k < 0) k = 0;
+    double t = u - (double)k;
+    double t2 = t * t, t3 = t2 * t;
+    double h00 = 2.0 * t3 - 3.0 * t2 + 1.0, h10 = t3 - 2.0 * t2 + t;
+    double h01 = -2.0 * t3 + 3.0 * t2, h11 = t3 - t2;
+    double g00 = 6.0 * t2 - 6.0 * t, g10 = 3.0 * t2 - 4.0 * t + 1.0;
+    double g01 = -6.0 * t2 + 6.0 * t, g11 = 3.0 * t2 - 2.0 * t;
+    *dydx = (g00 * y[k] + g10 * h * yp[k] + g01 * y[k + 1] + g11 * h * yp[k + 1]) / h;
+    return h00 * y[k] + h10 * h * yp[k] + h01 * y[k + 1] + h11 * h * yp[k + 1];
+}
+
+/* which = 0: V_ab (pair), 1: phi_ab (density at an atom of species a from one of species b). */
+static double orc_pair(const orc_potential *p, int which, int a, int b, double r, double *d,
+                       int64_t *viol) {
+    if (p->kind == 1) {
+        const double dd = p->fs[0], c = p->fs[1], beta = p->fs[3];
+        const double c0 = p->fs[4], c1 = p->fs[5], c2 = p->fs[6];
+        if (which == 0) {
+            if (!(r < c)) { *d = 0.0; return 0.0; }
+            double q = c0 + c1 * r + c2 * r * r;
+            *d = 2.0 * (r - c) * q + (r - c) * (r - c) * (c1 + 2.0 * c2 * r);
+            return (r - c) * (r - c) * q;
+        }
+        if (!(r < dd)) { *d = 0.0; return 0.0; }
+        *d = 2.0 * (r - dd) + 3.0 * beta * (r - dd) * (r - dd) / dd;
+        return (r - dd) * (r - dd) + beta * (r - dd) * (r - dd) * (r - dd) / dd;
+    }
+    int ns = p->n_species, n = p->n_knots;
+    int t = which * ns * ns + a * ns + b;
+    return orc_table(p->tables + (size_t)t * 2 * n, n, p->r_min, p->r_cut, r, d, viol);
+}
+
+static double orc_embed(const orc_potential *p, int a, double rho, double *dF, int64_t *viol) {
+    if (p->kind == 1) {
+        if (!(rho > 0.0)) { *dF = 0.0; return 0.0; } /* F(0) = 0 with F' = 0 (finite at rho = 0) */
+        double s = sqrt(rho);
+        *dF = -0.5 * p->fs[2] / s;
+        return -p->fs[2] * s;
+    }
+    int ns = p->n_species, n = p->n_knots;
+    int t = 2 * ns * ns + a;
+    return orc_table(p->tables + (size_t)t * 2 * n, n, p->rho_min, p->rho_max, rho, dF, viol);
+}
+
+/* Expose the potential functions for the tests. */
+double orc_pair_value(const orc_potential *p, int which, int a, int b, double r, double *d) {
+    int64_t v = 0;
+    return orc_pair(p, which, a, b, r, d, &v);
+}
+double orc_embed_value(const orc_potential *p, int a, double rho, double *dF) {
+    int64_t v = 0;
+    return orc_embed(p, a, rho, dF, &v);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Eq. (1) and its gradient from the full neighbour list.
+ * Pass 1: rho_i = sum_j phi_{s_i s_j}(r_ij); F_i = F_{s_i}(rho_i), F'_i.
+ * Pass 2: with d = r_j - r_i and r = |d|,
+ *   force_i = sum_j [ V'_{s_i s_j}(r) + F'_i phi'_{s_i s_j}(r) + F'_j phi'_{s_j s_i}(r) ] d / r,
+ *   E_i = F_i + 1/2 sum_j V(r)   (each pair's V counted once in U),
+ *   W   = -1/2 sum_i sum_j g d (x) d / r   (virial; g is the bracket above).
+ * Only pairs with r < r_cut contribute.  Per-atom sums run in list order; the
+ * totals are summed over atoms in index order.  Returns the range count.       */
+int64_t orc_eam_forces(int64_t n, const double *pos, const int32_t *species, const double *box,
+                       const orc_potential *pot, const int32_t *count, const int32_t *list,
+                       int32_t k_max, double *rho, double *dF, double *force, double *e_atom,
+                       double *virial, double *pe) {
+    double L[3] = {box[0], box[1], box[2]};
+    double invL[3] = {1.0 / box[0], 1.0 / box[1], 1.0 / box[2]};
+    double rc2 = pot->r_cut * pot->r_cut;
+    int64_t viol = 0;
+    double *w_atom = (double *)calloc((size_t)(n > 0 ? n : 1) * 6, sizeof(double));
+#pragma omp parallel for schedule(static) reduction(+ : viol)
+    for (int64_t i = 0; i < n; i++) {
+        double s = 0.0;
+        for (int32_t k = 0; k < count[i]; k++) {
+            int64_t j = list[i * k_max + k];
+            double r2 = orc_dist2(pos, i, j, L, invL, NULL);
+            if (!(r2 < rc2)) continue;
+            double dphi;
+            s += orc_pair(pot, 1, species[i], species[j], sqrt(r2), &dphi, &viol);
+        }
+        rho[i] = s;
+        e_atom[i] = orc_embed(pot, species[i], s, &dF[i], &viol);
+    }
+#pragma omp parallel for schedule(static) reduction(+ : viol)
+    for (int64_t i = 0; i < n; i++) {
+        double f[3] = {0.0, 0.0, 0.0}, ep = 0.0, w[6] = {0, 0, 0, 0, 0, 0};
+        int a = species[i];
+        for (int32_t k = 0; k < count[i]; k++) {
+            int64_t j = list[i * k_max + k];
+            double dv[3];
+            double r2 = orc_dist2(pos, i, j, L, invL, dv);
+            if (!(r2 < rc2)) continue;
+            double r = sqrt(r2);
+            int b = species[j];
+            double dV, dphi_ab, dphi_ba;
+            double v = orc_pair(pot, 0, a, b, r, &dV, &viol);
+            orc_pair(pot, 1, a, b, r, &dphi_ab, &viol);
+            orc_pair(pot, 1, b, a, r, &dphi_ba, &viol);
+            double g = dV + dF[i] * dphi_ab + dF[j] * dphi_ba;
+            double gr = g / r;
+            for (int c = 0; c < 3; c++) f[c] += gr * dv[c];
+            ep += 0.5 * v;
+            w[0] -= 0.5 * gr * dv[0] * dv[0];
+            w[1] -= 0.5 * gr * dv[1] * dv[1];
+            w[2] -= 0.5 * gr * dv[2] * dv[2];
+            w[3] -= 0.5 * gr * dv[1] * dv[2];
+            w[4] -= 0.5 * gr * dv[0] * dv[2];
+            w[5] -= 0.5 * gr * dv[0] * dv[1];
+        }
+        for (int c = 0; c < 3; c++) force[3 * i + c] = f[c];
+        e_atom[i] += ep;
+        for (int c = 0; c < 6; c++) w_atom[6 * i + c] = w[c];
+    }
+    double tot = 0.0, wt[6] = {0, 0, 0, 0, 0, 0};
+    for (int64_t i = 0; i < n; i++) {
+        tot += e_atom[i];
+        for (int c = 0; c < 6; c++) wt[c] += w_atom[6 * i + c];
+    }
+    free(w_atom);
+    if (pe) *pe = tot;
+    if (virial) { /* xx yy zz, then full 3x3 row-major */
+        double m[9] = {wt[0], wt[5], wt[4], wt[5], wt[1], wt[3], wt[4], wt[3], wt[2]};
+        memcpy(virial, m, sizeof(m));
+    }
+    return viol;
+}
+
+/* The paper's asymmetric (half) list with F_ij applied to i and j (§3.2.2), run
+ * serially: a different order of operations for the same Eq. (1) gradient.
+ * Uses the entries j > i of a full list.                                      */
+int64_t orc_eam_forces_half(int64_t n, const double *pos, const int32_t *species, const double *box,
+                            const orc_potential *pot, const int32_t *count, const int32_t *list,
+                            int32_t k_max, double *force, double *pe) {
+    double L[3] = {box[0], box[1], box[2]};
+    double invL[3] = {1.0 / box[0], 1.0 / box[1], 1.0 / box[2]};
+    double rc2 = pot->r_cut * pot->r_cut;
+    int64_t viol = 0;
+    double *rho = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    double *dF = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    double u = 0.0;
+    for (int64_t i = 0; i < n; i++)
+        for (int32_t k = 0; k < count[i]; k++) {
+            int64_t j = list[i * k_max + k];
+            if (j <= i) continue;
+            double r2 = orc_dist2(pos, i, j, L, invL, NULL);
+            if (!(r2 < rc2)) continue;
+            double r = sqrt(r2), dd;
+            rho[i] += orc_pair(pot, 1, species[i], species[j], r, &dd, &viol);
+            rho[j] += orc_pair(pot, 1, species[j], species[i], r, &dd, &viol);
+        }
+    for (int64_t i = 0; i < n; i++) {
+        u += orc_embed(pot, species[i], rho[i], &dF[i], &viol);
+        force[3 * i] = force[3 * i + 1] = force[3 * i + 2] = 0.0;
+    }
+    for (int64_t i = 0; i < n; i++)
+        for (int32_t k = 0; k < count[i]; k++) {
+            int64_t j = list[i * k_max + k];
+            if (j <= i) continue;
+            double dv[3];
+            double r2 = orc_dist2(pos, i, j, L, invL, dv);
+            if (!(r2 < rc2)) continue;
+            double r = sqrt(r2);
+            int a = species[i], b = species[j];
+            double dV, dab, dba;
+            u += orc_pair(pot, 0, a, b, r, &dV, &viol);
+            orc_pair(pot, 1, a, b, r, &dab, &viol);
+            orc_pair(pot, 1, b, a, r, &dba, &viol);
+            double gr = (dV + dF[i] * dab + dF[j] * dba) / r;
+            for (int c = 0; c < 3; c++) {
+                force[3 * i + c] += gr * dv[c]; /* force on i: along +d (towards j) */
+                force[3 * j + c] -= gr * dv[c]; /* Newton's third law on j           */
+            }
+        }
+    free(rho);
+    free(dF);
+    if (pe) *pe = u;
+    return viol;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Thermodynamics of a microstate (§2.1.2, §2.6): KE = sum m v^2 / 2,
+ * T = 2 KE / ((3N-3) k_B), total momentum.                                    */
+void orc_kinetic(int64_t n, const double *vel, const int32_t *species, const double *masses,
+                 double *ke, double *temperature, double *momentum, double *kin_tensor) {
+    double k = 0.0, p[3] = {0, 0, 0}, kt[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int64_t i = 0; i < n; i++) {
+        double m = masses[species[i]];
+        const double *v = vel + 3 * i;
+        k += 0.5 * m * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        for (int a = 0; a < 3; a++) {
+            p[a] += m * v[a];
+            for (int b = 0; b < 3; b++) kt[3 * a + b] += m * v[a] * v[b];
+        }
+    }
+    k *= ORC_MVV2E;
+    if (ke) *ke = k;
+    if (temperature) *temperature = (n > 1) ? 2.0 * k / ((double)(3 * n - 3) * ORC_KB) : 0.0;
+    if (momentum) memcpy(momentum, p, sizeof(p));
+    if (kin_tensor) for (int a = 0; a < 9; a++) kin_tensor[a] = kt[a] * ORC_MVV2E;
+}
+
+/* Pressure (GPa) from the kinetic and virial tensors: P = (tr(K) + tr(W)) / (3 V). */
+double orc_pressure_gpa(const double *kin_tensor, const double *virial, const double *box) {
+    double vol = box[0] * box[1] * box[2];
+    double tr = kin_tensor[0] + kin_tensor[4] + kin_tensor[8] + virial[0] + virial[4] + virial[8];
+    return tr / (3.0 * vol) * ORC_EVA3_TO_GPA;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Velocity Verlet (§2.3) with the neighbour list rebuilt every `rebuild_every`
+ * steps (Table 1 `nbrupdate`; 0 = never on a schedule) and whenever an atom has
+ * moved more than skin/2 since the last build, so that the padded list stays
+ * complete (§3.2.1).  Time step dt in fs; accelerations F/m converted from
+ * eV/(Å amu) to Å/fs^2 (§2.7).  The strain-rate condition (§2.2): after each
+ * drift, the box z edge and every z coordinate are multiplied by
+ * (1 + strain_rate_zz * dt), fractional coordinates fixed.
+ * `force` holds F(r) at the initial positions on entry (forces_valid = 1) or is
+ * computed first; on exit it holds the forces at the final positions.
+ * energies (if given) receives per step: PE, KE.                              */
+int64_t orc_run_vv(int64_t n, double *pos, double *vel, const int32_t *species, const double *masses,
+                   double *box, const orc_potential *pot, double dt_fs, int32_t n_steps, double skin,
+                   int32_t k_max, int32_t rebuild_every, double strain_rate_zz, double *force,
+                   int32_t forces_valid, double *energies, int32_t *n_rebuilds, int32_t *max_count) {
+    double r_list = pot->r_cut + skin;
+    int32_t *count = (int32_t *)malloc(sizeof(int32_t) * (n > 0 ? n : 1));
+    int32_t *list = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1) * k_max);
+    double *ref = (double *)malloc(sizeof(double) * 3 * (n > 0 ? n : 1));
+    double *rho = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
+    double *dF = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
+    double *ea = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
+    double acc = 1.0 / ORC_MVV2E; /* (eV/Å)/amu -> Å/fs^2 */
+    int64_t viol = 0;
+    int32_t rebuilds = 0, mc = 0;
+
+#define ORC_BUILD()                                                                         \
+    do {                                                                                    \
+        int32_t m_ = orc_neighbours_cells(n, pos, box, r_list, k_max, count, list);         \
+        if (m_ < 0) m_ = orc_neighbours_brute(n, pos, box, r_list, k_max, count, list);     \
+        if (m_ > mc) mc = m_;                                                                \
+        memcpy(ref, pos, sizeof(double) * 3 * n);                                           \
+        rebuilds++;                                                                          \
+    } while (0)
+
+    ORC_BUILD();
+    if (!forces_valid)
+        viol += orc_eam_forces(n, pos, species, box, pot, count, list, k_max, rho, dF, force, ea, NULL, NULL);
+    double half = 0.5 * dt_fs;
+    double lim2 = 0.25 * skin * skin;
+    for (int32_t step = 0; step < n_steps; step++) {
+        for (int64_t i = 0; i < n; i++) {
+            double im = acc / masses[species[i]];
+            for (int c = 0; c < 3; c++) {
+                vel[3 * i + c] += half * force[3 * i + c] * im;
+                pos[3 * i + c] += dt_fs * vel[3 * i + c];
+            }
+        }
+        if (strain_rate_zz != 0.0) {
+            double s = 1.0 + strain_rate_zz * dt_fs * 1.0e-15;
+            box[2] *= s;
+            for (int64_t i = 0; i < n; i++) pos[3 * i + 2] *= s;
+        }
+        int rebuild = (rebuild_every > 0 && (step + 1) % rebuild_every == 0);
+        for (int64_t i = 0; i < n && !rebuild; i++) {
+            double dx = pos[3 * i] - ref[3 * i], dy = pos[3 * i + 1] - ref[3 * i + 1];
+            double dz = pos[3 * i + 2] - ref[3 * i + 2];
+            if ((dx * dx + dy * dy) + dz * dz > lim2) rebuild = 1;
+        }
+        if (rebuild) ORC_BUILD();
+        double pe = 0.0;
+        viol += orc_eam_forces(n, pos, species, box, pot, count, list, k_max, rho, dF, force, ea, NULL, &pe);
+        for (int64_t i = 0; i < n; i++) {
+            double im = acc / masses[species[i]];
+            for (int c = 0; c < 3; c++) vel[3 * i + c] += half * force[3 * i + c] * im;
+        }
+        if (energies) {
+            double ke;
+            orc_kinetic(n, vel, species, masses, &ke, NULL, NULL, NULL);
+            energies[2 * step] = pe;
+            energies[2 * step + 1] = ke;
+        }
+    }
+#undef ORC_BUILD
+    if (n_rebuilds) *n_rebuilds = rebuilds;
+    if (max_count) *max_count = mc;
+    free(count);
+    free(list);
+    free(ref);
+    free(rho);
+    free(dF);
+    free(ea);
+    return viol;
+}
