@@ -1,0 +1,218 @@
+/*
+ * md.h - C ABI of the GB300 EAM hot-path library (libmd.so).
+ *
+ * The operation is the force calculation and time step of the MOLDY method
+ * (Ackland et al., "The MOLDY short-range molecular dynamics package"):
+ *   - link-cell binning and a Verlet neighbour list with padding (§3.2.1);
+ *   - the two sums of Eq. (1): the host density rho_i = sum_j phi(r_ij) with
+ *     F(rho_i), F'(rho_i), then the pair + embedding forces (§2, §3.1);
+ *   - velocity-Verlet integration (§2.3) in the units of §2.7.
+ * The force sums use the symmetric (full) neighbour list of §3.2.2, each atom
+ * gathering its own sum, so no two threads write the same atom.
+ *
+ * Conventions shared by every entry point
+ *   - Units (§2.7): lengths Å, masses amu, energies eV, time fs, velocities Å/fs,
+ *     forces eV/Å, temperature K, pressure GPa.
+ *   - Per-atom arrays are in the caller's atom order (index = atom id given at
+ *     md_create), row-major [N][3] doubles for vectors.
+ *   - `on_device` = 0: the pointer is host memory (pageable or pinned);
+ *     1: it is CUDA device memory of the current device (e.g. a torch tensor).
+ *   - Ownership: the caller owns every array it passes; the library copies what it
+ *     needs before returning (inputs) or writes into the caller's array (outputs).
+ *     The library owns its own device buffers (cells, lists, sorted state).
+ *   - Work is issued on md_config.stream (a cudaStream_t; NULL = legacy default
+ *     stream).  Every entry point that returns data synchronises that stream.
+ *   - Errors: every call returns an md_status; no exception crosses the ABI.  The
+ *     text of the last error of a context is kept until the next failing call and
+ *     is read with md_last_error.  Conditions found on the device (list overflow,
+ *     non-finite forces, table range) are reported by the next call that
+ *     synchronises (md_step, md_eam_forces, md_build_neighbours, md_energy).
+ *   - One context is used by one host thread at a time.
+ */
+#ifndef MD_H
+#define MD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MD_ABI_VERSION 1
+
+typedef struct md_ctx md_ctx; /* opaque, owned by the library */
+
+typedef enum {
+    MD_OK = 0,
+    MD_ERR_ARG = 1,          /* bad argument (NULL pointer, size, unsupported option) */
+    MD_ERR_SPECIES = 2,      /* species index out of range: the paper halts before the run
+                                when the potential cannot handle a species (§3.1) */
+    MD_ERR_BOX = 3,          /* box not orthorhombic, or an edge holds < 3 link cells */
+    MD_ERR_NBR_OVERFLOW = 4, /* an atom has more than k_max neighbours (Table 1 `nnbrs`) */
+    MD_ERR_SKIN = 5,         /* strict mode: an atom moved more than skin/2 since the build */
+    MD_ERR_NONFINITE = 6,    /* NaN or Inf in positions or forces */
+    MD_ERR_TABLE_RANGE = 7,  /* (reserved) strict table range mode */
+    MD_ERR_TIMEOUT = 8,      /* a bounded device-side wait gave up */
+    MD_ERR_CUDA = 9,         /* CUDA runtime error (text in md_last_error) */
+    MD_ERR_OOM = 10,         /* device allocation failed */
+    MD_ERR_STATE = 11        /* call not valid in the context's state */
+} md_status;
+
+enum { MD_POT_FS_ANALYTIC = 1, MD_POT_TABLES = 2 };
+enum { MD_PREC_FP64 = 0, MD_PREC_MIXED = 1 };
+
+/*
+ * The potential as data (the paper's potential interface, §3.1: V, phi, F and their
+ * derivatives per species; the range from get_supported_potential_range).
+ *   kind MD_POT_FS_ANALYTIC: one species, Finnis-Sinclair form with
+ *     fs = {d, c, A, beta, c0, c1, c2}:
+ *       phi(r) = (r-d)^2 + beta (r-d)^3 / d  (r < d),
+ *       V(r)   = (r-c)^2 (c0 + c1 r + c2 r^2)  (r < c),   F(rho) = -A sqrt(rho);
+ *     r_cut must be >= max(c, d).
+ *   kind MD_POT_TABLES: n_species species, knot tables.  `tables` holds
+ *     (2 ns^2 + ns) tables of 2*n_knots doubles each (n_knots values, then n_knots
+ *     slopes at uniform knots): V[a][b] (a, b < ns; V[a][b] must equal V[b][a]),
+ *     phi[a][b] = density at an atom of species a due to a neighbour of species b
+ *     (EAM/FS asymmetric form, §2 and §3.1), F[a].  r-tables span [r_min, r_cut],
+ *     F-tables span [rho_min, rho_max].  Each interval is the cubic Hermite
+ *     polynomial through the end values and slopes; outside the span the table
+ *     continues linearly from the end knot and the event is counted
+ *     (md_energies.range_violations).
+ * The library copies the tables at md_create.
+ */
+typedef struct {
+    int32_t kind;
+    int32_t n_species;
+    const int32_t *atomic_numbers; /* [n_species], informational */
+    const double *masses_amu;      /* [n_species] */
+    double fs[7];
+    int32_t n_knots;
+    double r_min, r_cut; /* potential range (§3.1 get_supported_potential_range) */
+    double rho_min, rho_max;
+    const double *tables;
+} md_potential;
+
+/*
+ * Run configuration (the fields of the paper's parameter file that the hot path
+ * uses, Table 1).
+ */
+typedef struct {
+    int64_t n_atoms;
+    double h[9];           /* box matrix [a; b; c] rows in Å; must be diagonal (orthorhombic) */
+    double skin;           /* `rpad`: list radius = r_cut + skin (§3.2.1) */
+    int32_t k_max;         /* `nnbrs`: list capacity per atom */
+    int32_t rebuild_every; /* `nbrupdate`: rebuild every n steps; 0 = only when needed */
+    double dt_fs;          /* `deltat` */
+    int32_t precision;     /* MD_PREC_FP64, or MD_PREC_MIXED (FP32 pair/density terms,
+                              FP64 positions, velocities, density sum and reductions) */
+    int32_t strict_skin;   /* 1: moving > skin/2 between scheduled rebuilds is MD_ERR_SKIN;
+                              0: it triggers a rebuild */
+    double strain_rate_zz; /* 1/s; each step the box z edge and all z coordinates are
+                              multiplied by (1 + rate*dt) (§2.2 strain-rate loading) */
+    void *stream;          /* cudaStream_t, or NULL */
+} md_config;
+
+typedef struct {
+    double pe, ke, te;    /* potential (Eq. 1), kinetic, total energy, eV */
+    double temperature;   /* 2 KE / ((3N-3) k_B), K (§2.1.2) */
+    double virial[9];     /* W = sum over pairs of r_ij (x) f_ij, eV, row-major */
+    double pressure_gpa;  /* (2 KE + tr W) / (3 V) */
+    double momentum[3];   /* total momentum, amu Å/fs */
+    double volume;        /* Å^3 */
+    double box[3];        /* current box edges, Å */
+    int64_t step;         /* steps taken since md_create */
+    int64_t n_rebuilds;   /* neighbour-list builds so far */
+    int32_t max_neighbours;    /* longest list at the last build */
+    int32_t pad;
+    int64_t range_violations;  /* table lookups outside their span so far */
+} md_energies;
+
+/* md_get selectors */
+enum {
+    MD_GET_POS = 0,       /* double [N][3], unwrapped (§2.2) */
+    MD_GET_VEL = 1,       /* double [N][3] */
+    MD_GET_FORCE = 2,     /* double [N][3] at the current positions */
+    MD_GET_RHO = 3,       /* double [N]: rho_i */
+    MD_GET_EATOM = 4,     /* double [N]: F(rho_i) + 1/2 sum_j V(r_ij), the energy of an atom (§2) */
+    MD_GET_DF = 5,        /* double [N]: F'(rho_i) */
+    MD_GET_NBR_COUNT = 6, /* int32 [N]: neighbours of each atom (may exceed k_max on overflow) */
+    MD_GET_NBR_LIST = 7,  /* int32 [N][k_max]: neighbour atom ids, unused slots -1, order unspecified */
+    MD_GET_SPECIES = 8    /* int32 [N] */
+};
+
+/* Library ABI version (MD_ABI_VERSION). */
+int32_t md_abi_version(void);
+
+/* Short text for a status code (static storage). */
+const char *md_status_string(md_status s);
+
+/*
+ * Create a context: copy the potential, the atoms' positions `pos` [N][3] (Å,
+ * unwrapped), velocities `vel` [N][3] (Å/fs; NULL = zero) and species indices
+ * `species` [N] (NULL = all 0), allocate the device buffers, and check the box
+ * (orthorhombic, >= 3 link cells of width >= r_cut + skin per edge) and the
+ * species (§3.1: halt before the run on an unsupported species).
+ * On failure *out is NULL and the status says why.
+ */
+md_status md_create(const md_config *cfg, const md_potential *pot, const double *pos,
+                    const double *vel, const int32_t *species, int32_t on_device, md_ctx **out);
+
+/* Bin the atoms into link cells (counting sort by cell, atoms renumbered in
+ * cell order with a stable tie-break on atom id) and build the full Verlet list:
+ * j is listed for i iff j != i and |r_ij|^2 < (r_cut + skin)^2 with the minimum
+ * image (§2.2, §3.2.1).  Returns MD_ERR_NBR_OVERFLOW if an atom has > k_max. */
+md_status md_build_neighbours(md_ctx *ctx);
+
+/* Forces, per-atom density and energies at the current positions (pass 1 and
+ * pass 2 of Eq. (1)); rebuilds the list first if it is missing or stale.  If
+ * pe_out is not NULL it receives the total potential energy (FP64 sum). */
+md_status md_eam_forces(md_ctx *ctx, double *pe_out);
+
+/* Advance n_steps velocity-Verlet steps (§2.3): half kick, drift, [strain],
+ * [list rebuild when scheduled or when an atom moved > skin/2], density pass,
+ * force pass, half kick.  Energies of the final state are then available from
+ * md_energy.  Synchronises the stream once, at the end. */
+md_status md_step(md_ctx *ctx, int32_t n_steps);
+
+/* Microstate thermodynamics of the current state (§2.1.2, §2.6), reduced in FP64
+ * in a fixed order (bitwise reproducible). */
+md_status md_energy(md_ctx *ctx, md_energies *out);
+
+/* Copy one per-atom array (see MD_GET_*) into `dst` (caller's atom order). */
+md_status md_get(md_ctx *ctx, int32_t what, void *dst, int32_t on_device);
+
+/* Replace positions and velocities (caller's atom order); `force` may be NULL
+ * (forces are then recomputed before the next step) or the forces at `pos`
+ * (e.g. from a checkpoint, §4.1.3).  Any NULL of pos/vel keeps that array. */
+md_status md_set_state(md_ctx *ctx, const double *pos, const double *vel, const double *force,
+                       int32_t on_device);
+
+/* Kernel timing of a context (tracing).  `launches` counts every kernel the context has
+ * enqueued since md_create.  While profiling is on, md_step brackets each kernel class with
+ * CUDA events on the context's stream and adds their elapsed times here (ms) when the call
+ * synchronises; the counts are the number of timed launches.  "rebuild" covers the skin
+ * check's consequences: the binning, sort and list-build kernels of a step, which exit at
+ * once when no rebuild is due. */
+typedef struct {
+    int64_t launches;
+    int64_t n_kick, n_rebuild, n_density, n_force;
+    double ms_kick, ms_rebuild, ms_density, ms_force;
+} md_profile;
+
+/* Turn per-kernel event timing on (1) or off (0); turning it on clears the sums. */
+md_status md_set_profiling(md_ctx *ctx, int32_t on);
+
+/* Read the launch count and the timing sums. */
+md_status md_get_profile(const md_ctx *ctx, md_profile *out);
+
+/* Text of the last error of this context ("" if none).  Valid until the next call. */
+const char *md_last_error(const md_ctx *ctx);
+
+/* Free the context and its device buffers (NULL is ignored). */
+void md_destroy(md_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MD_H */

@@ -1,0 +1,107 @@
+// Internal declarations shared by the kernels and the C ABI layer of libmd.so.
+// Per-atom state on the device is kept in link-cell order (atoms renumbered at
+// every neighbour-list build, §3.2.1-3.2.2: "ordering the particles array by
+// increasing link-cell index"); id[] maps a slot to the caller's atom id.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "md.h"
+
+namespace mdk {
+
+// Units of §2.7 (CODATA 2018): amu (Å/fs)^2 in eV, Boltzmann constant, eV/Å^3 in GPa.
+constexpr double kAmuKg = 1.66053906660e-27;
+constexpr double kEvJ = 1.602176634e-19;
+constexpr double kKb = 8.617333262e-5;
+constexpr double kMvv2e = kAmuKg * 1.0e10 / kEvJ;
+constexpr double kEva3ToGpa = kEvJ * 1.0e30 / 1.0e9;
+
+enum : int32_t { FLAG_OVERFLOW = 1, FLAG_NONFINITE = 2 };
+
+constexpr int kThreads = 128;     // threads per block of the per-atom kernels
+constexpr int kPartials = 11;     // per-block FP64 partial sums: pe, sum m v^2, W(6), p(3)
+
+// Current orthorhombic box (changes under the strain ramp; kept in device memory so that
+// a captured step reads the live value).
+struct Box {
+    double L[3];
+    double invL[3];
+    float Lf[3];
+    float invLf[3];
+};
+
+// Device-side status, read by the host after each synchronising call.
+struct Flags {
+    int32_t need_rebuild;   // set by the displacement check or the schedule; cleared by pass 1
+    int32_t error;          // FLAG_* bits
+    int32_t max_count;      // longest list at the last build
+    int32_t skin_exceeded;  // an atom moved more than skin/2 since the last build
+    unsigned long long n_rebuilds;
+    unsigned long long range_violations;
+};
+
+// Device view of the potential.  Tables hold, per interval k of a uniform knot grid, the
+// monomial coefficients (c0, c1, c2, c3) of the cubic in t = (x - x_k)/h; row n_knots-1 holds
+// (y_end, h*y'_end, 0, 0) for the linear continuation past the last knot.
+struct Pot {
+    int kind, ns, nk;
+    double rc2;
+    float rc2f;
+    double fs[7];   // d, c, A, beta, c0, c1, c2
+    float fsf[7];
+    double bd;      // beta / d
+    float bdf;
+    double r_min, inv_dr, rho_min, inv_drho;
+    float r_minf, inv_drf;
+    const double4_32a *V64, *P64, *F64;   // [(a*ns+b)*nk + k], F: [a*nk + k]
+    const float4 *V32, *P32;
+};
+
+// Device view of the per-atom state (cell order).
+struct Atoms {
+    int n, k_max;
+    double4_32a *pos, *vel, *force, *ref;        // pos.w = species; vel.w = (1/mvv2e)/m
+    double4_32a *pos_tmp, *vel_tmp, *force_tmp;  // renumbering scratch
+    float4 *posf;                            // FP32 wrapped position, w = species bits
+    float4 *p2f;                             // mixed pass 2: wrapped position + F'(rho)
+    double *rho, *dF, *e_atom;
+    int32_t *id, *id_tmp, *rank, *spec, *spec_tmp;
+    int32_t *cell_of, *slot, *order;
+    int32_t *nbr, *count;                    // nbr[k*n + i], k < k_max
+    double *partials;                        // [n_blocks][kPartials]
+    Box *box;
+    Flags *flags;
+};
+
+struct Cells {
+    int nc[3];
+    int ncell;
+    int ntiles;
+    int32_t *cell_count, *cell_start, *tile_sums;
+};
+
+// Launchers (stream-ordered, no synchronisation).
+cudaError_t launch_set_rebuild(Flags *f, cudaStream_t s);
+cudaError_t launch_clear_rebuild(Flags *f, cudaStream_t s);
+cudaError_t launch_rebuild(const Atoms &A, const Cells &C, double rl2, float band_lo, float band_hi,
+                           cudaStream_t s);
+cudaError_t launch_box_update(Box *box, double scale_z, cudaStream_t s);
+cudaError_t launch_kick_drift(const Atoms &A, double half_dt, double dt, double strain_scale,
+                              double lim2, cudaStream_t s);
+cudaError_t launch_check_displacement(const Atoms &A, double lim2, cudaStream_t s);
+cudaError_t launch_wrap(const Atoms &A, cudaStream_t s);
+cudaError_t launch_density(const Atoms &A, const Pot &P, int precision, cudaStream_t s);
+cudaError_t launch_force(const Atoms &A, const Pot &P, int precision, bool kick, bool energy,
+                         double half_dt, cudaStream_t s);
+cudaError_t launch_reduce(const Atoms &A, double *out, cudaStream_t s);
+cudaError_t launch_unsort_vec(const Atoms &A, const double4_32a *src, double *dst, cudaStream_t s);
+cudaError_t launch_unsort_scalar(const Atoms &A, const double *src, double *dst, cudaStream_t s);
+cudaError_t launch_unsort_int(const Atoms &A, const int32_t *src, int32_t *dst, cudaStream_t s);
+cudaError_t launch_unsort_list(const Atoms &A, int32_t *dst, cudaStream_t s);
+cudaError_t launch_sort_in_vec(const Atoms &A, const double *src, double4_32a *dst, cudaStream_t s);
+
+inline int blocks_for(long long n, int threads) { return (int)((n + threads - 1) / threads); }
+
+}  // namespace mdk

@@ -1,0 +1,318 @@
+"""Thin ctypes binding of libmd.so (include/md.h): argument marshalling only.
+
+Functions carry the C names (md_create, md_build_neighbours, md_eam_forces, md_step,
+md_energy, md_get, md_set_state, md_last_error, md_destroy).  Arrays are numpy
+arrays (host) or CUDA torch tensors (device, passed by data_ptr with on_device=1).
+Every computation runs in the library's CUDA kernels; there is no fallback: if the
+library has not been built, the first call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import inputs as _inputs
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libmd.so")
+
+MD_OK, MD_ERR_ARG, MD_ERR_SPECIES, MD_ERR_BOX, MD_ERR_NBR_OVERFLOW = 0, 1, 2, 3, 4
+MD_ERR_SKIN, MD_ERR_NONFINITE, MD_ERR_TABLE_RANGE, MD_ERR_TIMEOUT = 5, 6, 7, 8
+MD_ERR_CUDA, MD_ERR_OOM, MD_ERR_STATE = 9, 10, 11
+MD_POT_FS_ANALYTIC, MD_POT_TABLES = 1, 2
+MD_PREC_FP64, MD_PREC_MIXED = 0, 1
+(MD_GET_POS, MD_GET_VEL, MD_GET_FORCE, MD_GET_RHO, MD_GET_EATOM, MD_GET_DF, MD_GET_NBR_COUNT,
+ MD_GET_NBR_LIST, MD_GET_SPECIES) = range(9)
+
+# functions declared in include/md.h (checked by the CPU test-suite)
+EXPORTS = ["md_abi_version", "md_status_string", "md_create", "md_build_neighbours", "md_eam_forces",
+           "md_step", "md_energy", "md_get", "md_set_state", "md_set_profiling", "md_get_profile",
+           "md_last_error", "md_destroy"]
+
+
+class md_potential(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("n_species", C.c_int32),
+                ("atomic_numbers", C.POINTER(C.c_int32)), ("masses_amu", C.POINTER(C.c_double)),
+                ("fs", C.c_double * 7), ("n_knots", C.c_int32), ("r_min", C.c_double),
+                ("r_cut", C.c_double), ("rho_min", C.c_double), ("rho_max", C.c_double),
+                ("tables", C.POINTER(C.c_double))]
+
+
+class md_config(C.Structure):
+    _fields_ = [("n_atoms", C.c_int64), ("h", C.c_double * 9), ("skin", C.c_double),
+                ("k_max", C.c_int32), ("rebuild_every", C.c_int32), ("dt_fs", C.c_double),
+                ("precision", C.c_int32), ("strict_skin", C.c_int32), ("strain_rate_zz", C.c_double),
+                ("stream", C.c_void_p)]
+
+
+class md_energies(C.Structure):
+    _fields_ = [("pe", C.c_double), ("ke", C.c_double), ("te", C.c_double), ("temperature", C.c_double),
+                ("virial", C.c_double * 9), ("pressure_gpa", C.c_double), ("momentum", C.c_double * 3),
+                ("volume", C.c_double), ("box", C.c_double * 3), ("step", C.c_int64),
+                ("n_rebuilds", C.c_int64), ("max_neighbours", C.c_int32), ("pad", C.c_int32),
+                ("range_violations", C.c_int64)]
+
+
+class md_profile(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("n_kick", C.c_int64), ("n_rebuild", C.c_int64),
+                ("n_density", C.c_int64), ("n_force", C.c_int64), ("ms_kick", C.c_double),
+                ("ms_rebuild", C.c_double), ("ms_density", C.c_double), ("ms_force", C.c_double)]
+
+
+class MDError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{status_string(status)} ({status}): {message}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """Load libmd.so; raises if it has not been built (no CPU fallback exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = C.CDLL(LIB_PATH)
+        P, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+        L.md_abi_version.restype = i32
+        L.md_status_string.restype = C.c_char_p
+        L.md_status_string.argtypes = [C.c_int]
+        L.md_create.restype = C.c_int
+        L.md_create.argtypes = [C.POINTER(md_config), C.POINTER(md_potential), P, P, P, i32, C.POINTER(P)]
+        L.md_build_neighbours.restype = C.c_int
+        L.md_build_neighbours.argtypes = [P]
+        L.md_eam_forces.restype = C.c_int
+        L.md_eam_forces.argtypes = [P, C.POINTER(C.c_double)]
+        L.md_step.restype = C.c_int
+        L.md_step.argtypes = [P, i32]
+        L.md_energy.restype = C.c_int
+        L.md_energy.argtypes = [P, C.POINTER(md_energies)]
+        L.md_get.restype = C.c_int
+        L.md_get.argtypes = [P, i32, P, i32]
+        L.md_set_state.restype = C.c_int
+        L.md_set_state.argtypes = [P, P, P, P, i32]
+        L.md_set_profiling.restype = C.c_int
+        L.md_set_profiling.argtypes = [P, i32]
+        L.md_get_profile.restype = C.c_int
+        L.md_get_profile.argtypes = [P, C.POINTER(md_profile)]
+        L.md_last_error.restype = C.c_char_p
+        L.md_last_error.argtypes = [P]
+        L.md_destroy.restype = None
+        L.md_destroy.argtypes = [P]
+        _lib = L
+    return _lib
+
+
+def status_string(s: int) -> str:
+    return lib().md_status_string(int(s)).decode()
+
+
+def _ptr(a):
+    """(pointer, on_device, keepalive) for a numpy array, a torch tensor or None."""
+    if a is None:
+        return None, 0, None
+    if hasattr(a, "data_ptr") and hasattr(a, "is_cuda"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return C.c_void_p(a.data_ptr()), (1 if a.is_cuda else 0), a
+    return C.c_void_p(a.ctypes.data), 0, a
+
+
+def _check(ctx, status):
+    if status != MD_OK:
+        msg = lib().md_last_error(ctx).decode() if ctx else ""
+        raise MDError(status, msg)
+
+
+def md_create(config: md_config, potential: md_potential, pos, vel=None, species=None):
+    p, dev, _k1 = _ptr(pos)
+    v, dev_v, _k2 = _ptr(vel)
+    s, dev_s, _k3 = _ptr(species)
+    if vel is not None and dev_v != dev or species is not None and dev_s != dev:
+        raise ValueError("pos, vel and species must all be host or all device arrays")
+    out = C.c_void_p()
+    st = lib().md_create(C.byref(config), C.byref(potential), p, v, s, dev, C.byref(out))
+    if st != MD_OK:
+        raise MDError(st, "md_create failed")
+    return out
+
+
+def md_build_neighbours(ctx):
+    _check(ctx, lib().md_build_neighbours(ctx))
+
+
+def md_eam_forces(ctx) -> float:
+    pe = C.c_double()
+    _check(ctx, lib().md_eam_forces(ctx, C.byref(pe)))
+    return pe.value
+
+
+def md_step(ctx, n_steps: int):
+    _check(ctx, lib().md_step(ctx, int(n_steps)))
+
+
+def md_energy(ctx) -> dict:
+    e = md_energies()
+    _check(ctx, lib().md_energy(ctx, C.byref(e)))
+    return dict(pe=e.pe, ke=e.ke, te=e.te, temperature=e.temperature,
+                virial=np.array(e.virial[:]).reshape(3, 3), pressure_gpa=e.pressure_gpa,
+                momentum=np.array(e.momentum[:]), volume=e.volume, box=np.array(e.box[:]),
+                step=e.step, n_rebuilds=e.n_rebuilds, max_neighbours=e.max_neighbours,
+                range_violations=e.range_violations)
+
+
+def md_get(ctx, what: int, dst):
+    p, dev, _k = _ptr(dst)
+    _check(ctx, lib().md_get(ctx, int(what), p, dev))
+    return dst
+
+
+def md_set_state(ctx, pos=None, vel=None, force=None):
+    devs = [_ptr(a) for a in (pos, vel, force)]
+    flags = {d[1] for d, a in zip(devs, (pos, vel, force)) if a is not None}
+    if len(flags) > 1:
+        raise ValueError("state arrays must all be host or all device arrays")
+    _check(ctx, lib().md_set_state(ctx, devs[0][0], devs[1][0], devs[2][0], flags.pop() if flags else 0))
+
+
+def md_set_profiling(ctx, on: bool):
+    _check(ctx, lib().md_set_profiling(ctx, 1 if on else 0))
+
+
+def md_get_profile(ctx) -> dict:
+    p = md_profile()
+    _check(ctx, lib().md_get_profile(ctx, C.byref(p)))
+    return {k: getattr(p, k) for k, _ in md_profile._fields_}
+
+
+def md_last_error(ctx) -> str:
+    return lib().md_last_error(ctx).decode()
+
+
+def md_destroy(ctx):
+    if ctx:
+        lib().md_destroy(ctx)
+
+
+# ---------------------------------------------------------------------------
+def make_potential(pot: _inputs.Potential):
+    """md_potential view of an inputs.Potential (returns the struct and the arrays it points to)."""
+    an = np.ascontiguousarray(pot.atomic_numbers, dtype=np.int32)
+    ms = np.ascontiguousarray(pot.masses, dtype=np.float64)
+    tb = np.ascontiguousarray(pot.tables if pot.tables.size else np.zeros(1), dtype=np.float64)
+    s = md_potential()
+    s.kind, s.n_species = int(pot.kind), int(pot.n_species)
+    s.atomic_numbers = an.ctypes.data_as(C.POINTER(C.c_int32))
+    s.masses_amu = ms.ctypes.data_as(C.POINTER(C.c_double))
+    for k in range(7):
+        s.fs[k] = float(pot.fs[k])
+    s.n_knots = int(pot.n_knots)
+    s.r_min, s.r_cut = float(pot.r_min), float(pot.r_cut)
+    s.rho_min, s.rho_max = float(pot.rho_min), float(pot.rho_max)
+    s.tables = tb.ctypes.data_as(C.POINTER(C.c_double))
+    return s, (an, ms, tb)
+
+
+def make_config(n_atoms, box, skin, k_max, dt_fs, precision=MD_PREC_FP64, rebuild_every=0,
+                strict_skin=False, strain_rate_zz=0.0, stream=None):
+    c = md_config()
+    c.n_atoms = int(n_atoms)
+    for k in range(9):
+        c.h[k] = 0.0
+    for k in range(3):
+        c.h[4 * k] = float(box[k])
+    c.skin, c.k_max, c.rebuild_every, c.dt_fs = float(skin), int(k_max), int(rebuild_every), float(dt_fs)
+    c.precision, c.strict_skin, c.strain_rate_zz = int(precision), int(bool(strict_skin)), float(strain_rate_zz)
+    c.stream = C.c_void_p(stream) if stream else None
+    return c
+
+
+class System:
+    """One simulated system on the GPU (a context of libmd.so)."""
+
+    def __init__(self, w: _inputs.Workload, precision: str = "fp64", rebuild_every: int = 0,
+                 strict_skin: bool = False, stream=None, device_inputs: bool = False, k_max=None):
+        prec = MD_PREC_FP64 if precision == "fp64" else MD_PREC_MIXED
+        self.n = w.n_atoms
+        self.k_max = int(k_max or w.k_max)
+        self.config = make_config(w.n_atoms, w.box, w.skin, self.k_max, w.dt_fs, prec, rebuild_every,
+                                  strict_skin, w.strain_rate_zz, stream)
+        pot, keep = make_potential(w.potential)
+        pos = np.ascontiguousarray(w.pos, dtype=np.float64)
+        vel = np.ascontiguousarray(w.vel, dtype=np.float64)
+        spc = np.ascontiguousarray(w.species, dtype=np.int32)
+        if device_inputs:
+            import torch
+            pos, vel, spc = (torch.from_numpy(a).cuda() for a in (pos, vel, spc))
+            torch.cuda.synchronize()
+        self.ctx = md_create(self.config, pot, pos, vel, spc)
+        del keep
+
+    def build_neighbours(self):
+        md_build_neighbours(self.ctx)
+
+    def eam_forces(self) -> float:
+        return md_eam_forces(self.ctx)
+
+    def step(self, n: int = 1):
+        md_step(self.ctx, n)
+
+    def energy(self) -> dict:
+        return md_energy(self.ctx)
+
+    def get(self, what: int, out=None):
+        if out is None:
+            if what in (MD_GET_POS, MD_GET_VEL, MD_GET_FORCE):
+                out = np.empty((self.n, 3), np.float64)
+            elif what in (MD_GET_RHO, MD_GET_EATOM, MD_GET_DF):
+                out = np.empty(self.n, np.float64)
+            elif what in (MD_GET_NBR_COUNT, MD_GET_SPECIES):
+                out = np.empty(self.n, np.int32)
+            elif what == MD_GET_NBR_LIST:
+                out = np.empty((self.n, self.k_max), np.int32)
+            else:
+                raise ValueError(what)
+        return md_get(self.ctx, what, out)
+
+    def positions(self):
+        return self.get(MD_GET_POS)
+
+    def velocities(self):
+        return self.get(MD_GET_VEL)
+
+    def forces(self):
+        return self.get(MD_GET_FORCE)
+
+    def neighbours(self):
+        return self.get(MD_GET_NBR_COUNT), self.get(MD_GET_NBR_LIST)
+
+    def set_profiling(self, on: bool = True):
+        md_set_profiling(self.ctx, on)
+
+    def profile(self) -> dict:
+        return md_get_profile(self.ctx)
+
+    def set_state(self, pos=None, vel=None, force=None):
+        md_set_state(self.ctx, pos, vel, force)
+
+    def close(self):
+        if self.ctx:
+            md_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

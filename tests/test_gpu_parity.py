@@ -1,0 +1,306 @@
+"""CUDA path (through the C ABI) against the FP64 oracle, on the same seeded inputs.
+
+Bars: neighbour lists bit-exact as sets; FP64 forces, energies and virial within 1e-10
+relative (max-norm); the mixed path within its stated bound (below); trajectories of
+velocity Verlet within 1e-9 Å after 100 steps; edge cases and device-detected errors.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1107_2619_gb300 import inputs as I, md
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+# Mixed path: FP32 wrapped coordinates carry an absolute error of ~ulp32(L)/2 per coordinate;
+# with pair force constants of a few eV/Å^2 summed over the neighbours the force error stays
+# below 1e-4 of the largest force for box edges < 512 Å (measured values are recorded by
+# bench.py); PE is summed in FP64 from FP32 per-pair terms.
+MIXED_FORCE_TOL = 1e-4
+MIXED_PE_TOL = 1e-6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1107_2619_gb300 import build
+    build.build()
+
+
+def _rows(count, nl):
+    return [tuple(sorted(nl[i, :count[i]].tolist())) for i in range(count.shape[0])]
+
+
+def _random_box(n, seed, cells=(3.3, 4.1, 5.7), rl=3.869745):
+    box = np.array(cells) * rl
+    pos = I.random_uniform(seed, 5, 3 * n).reshape(n, 3) * box
+    pos[::4] += box * np.array([2.0, -1.0, 5.0])     # unwrapped images
+    pot = I.fs_fe_analytic()
+    return I.Workload(name="random", pos=pos, vel=np.zeros_like(pos), species=np.zeros(n, np.int32),
+                      box=box, potential=pot, skin=0.3, k_max=64, dt_fs=1.0, steps=1, temperature=0.0)
+
+
+def _near_cutoff(seed=9):
+    """Pairs placed so that |r_ij| sits within a few ulps of r_list (random directions)."""
+    pot = I.fs_fe_analytic()
+    rl = pot.r_cut + 0.3
+    box = np.array([40.0, 40.0, 40.0])
+    u = I.random_uniform(seed, 6, 4000).reshape(-1, 4)
+    pos = []
+    for k in range(300):
+        c = 4.0 + (np.array([k % 6, (k // 6) % 6, k // 36]) * 6.5)
+        v = u[k, :3] - 0.5
+        v /= np.linalg.norm(v)
+        d = rl * (1.0 + (k % 9 - 4) * 2.0 ** -52)
+        pos += [c, c + d * v]
+    pos = np.array(pos)
+    return I.Workload(name="near", pos=pos, vel=np.zeros_like(pos), species=np.zeros(len(pos), np.int32),
+                      box=box, potential=pot, skin=0.3, k_max=16, dt_fs=1.0, steps=1, temperature=0.0)
+
+
+def _workload(name):
+    if name == "fe2k":
+        return I.bcc_fe(10, seed=1)
+    if name == "fe_tables":
+        return I.bcc_fe(10, seed=11, tables=True)
+    if name == "cu2k":
+        return I.fcc_cu(8, seed=2, sigma=0.03)
+    if name == "fec":
+        return I.bcc_fe_c(10, seed=4)
+    if name == "random":
+        return _random_box(1001, seed=7)
+    if name == "near":
+        return _near_cutoff()
+    raise ValueError(name)
+
+
+def _gpu_system(w, precision="fp64", **kw):
+    return md.System(w, precision=precision, **kw)
+
+
+# --------------------------------------------------------------------------- neighbour lists
+@pytest.mark.parametrize("name", ["fe2k", "cu2k", "fec", "random", "near"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_neighbour_sets_bit_exact(name, precision):
+    w = _workload(name)
+    with _gpu_system(w, precision) as s:
+        s.build_neighbours()
+        cg, lg = s.neighbours()
+    co, lo, m = oracle.neighbours(w.pos, w.box, w.potential.r_cut + w.skin, w.k_max, "brute")
+    assert m <= w.k_max
+    assert np.array_equal(cg, co)
+    assert _rows(cg, lg) == _rows(co, lo)
+    assert np.all(lg[np.arange(w.k_max)[None, :] >= cg[:, None]] == -1)
+
+
+# --------------------------------------------------------------------------- FP64 parity
+@pytest.mark.parametrize("name", ["fe2k", "fe_tables", "cu2k", "fec", "random"])
+def test_fp64_forces_energies_virial_match_oracle(name):
+    w = _workload(name)
+    ref = oracle.forces(w.pos, w.species, w.box, w.potential, skin=w.skin, k_max=w.k_max, method="brute")
+    with _gpu_system(w) as s:
+        pe = s.eam_forces()
+        f = s.forces()
+        rho = s.get(md.MD_GET_RHO)
+        dF = s.get(md.MD_GET_DF)
+        ea = s.get(md.MD_GET_EATOM)
+        e = s.energy()
+    fs = np.abs(ref["force"]).max()
+    assert np.abs(f - ref["force"]).max() <= FP64_TOL * fs
+    assert abs(pe - ref["pe"]) <= FP64_TOL * abs(ref["pe"])
+    assert abs(e["pe"] - ref["pe"]) <= FP64_TOL * abs(ref["pe"])
+    assert np.abs(rho - ref["rho"]).max() <= FP64_TOL * np.abs(ref["rho"]).max()
+    assert np.abs(dF - ref["dF"]).max() <= FP64_TOL * np.abs(ref["dF"]).max()
+    assert np.abs(ea - ref["e_atom"]).max() <= FP64_TOL * np.abs(ref["e_atom"]).max()
+    ws = np.abs(ref["virial"]).max()
+    assert np.abs(e["virial"] - ref["virial"]).max() <= FP64_TOL * ws
+    k = oracle.kinetic(w.vel, w.species, w.potential.masses)
+    assert abs(e["ke"] - k["ke"]) <= FP64_TOL * max(k["ke"], 1e-300)
+    p = oracle.pressure_gpa(k["kin_tensor"], ref["virial"], w.box)
+    assert abs(e["pressure_gpa"] - p) <= FP64_TOL * max(abs(p), ws / np.prod(w.box) * 160.2)
+
+
+@pytest.mark.parametrize("name", ["fe2k", "fe_tables", "cu2k", "fec"])
+def test_mixed_forces_within_bound(name):
+    w = _workload(name)
+    ref = oracle.forces(w.pos, w.species, w.box, w.potential, skin=w.skin, k_max=w.k_max, method="brute")
+    with _gpu_system(w, "mixed") as s:
+        pe = s.eam_forces()
+        f = s.forces()
+        rho = s.get(md.MD_GET_RHO)
+    fs = np.abs(ref["force"]).max()
+    assert np.abs(f - ref["force"]).max() <= MIXED_FORCE_TOL * fs
+    assert abs(pe - ref["pe"]) <= MIXED_PE_TOL * abs(ref["pe"])
+    assert np.abs(rho - ref["rho"]).max() <= 1e-5 * np.abs(ref["rho"]).max()
+
+
+def test_unwrapped_images_give_the_same_forces():
+    w = I.bcc_fe(10, seed=12)
+    shifted = I.Workload(**{**w.__dict__, "pos": w.pos + w.box * np.array([3.0, -7.0, 1.0])})
+    with _gpu_system(w) as a, _gpu_system(shifted) as b:
+        a.eam_forces()
+        b.eam_forces()
+        fa, fb = a.forces(), b.forces()
+    assert np.abs(fa - fb).max() <= FP64_TOL * np.abs(fa).max()
+
+
+# --------------------------------------------------------------------------- dynamics
+def test_fp64_trajectory_matches_oracle_fe2k():
+    """The 2,000-atom bcc Fe workload: 100 velocity-Verlet steps of 1 fs (FP64)."""
+    w = I.bcc_fe(10, seed=1)
+    ref = oracle.run_vv(w.pos, w.vel, w.species, w.potential.masses, w.box, w.potential, w.dt_fs, 100,
+                        w.skin, w.k_max)
+    with _gpu_system(w) as s:
+        pes, kes = [], []
+        for _ in range(100):
+            s.step(1)
+            e = s.energy()
+            pes.append(e["pe"])
+            kes.append(e["ke"])
+        pos, vel = s.positions(), s.velocities()
+        e = s.energy()
+    scale = abs(ref["energies"][:, 0]).max()
+    assert np.abs(np.array(pes) - ref["energies"][:, 0]).max() <= FP64_TOL * scale
+    assert np.abs(np.array(kes) - ref["energies"][:, 1]).max() <= FP64_TOL * scale
+    assert np.abs(pos - ref["pos"]).max() < 1e-9
+    assert np.abs(vel - ref["vel"]).max() < 1e-11
+    assert e["n_rebuilds"] == ref["n_rebuilds"]
+    assert np.abs(e["momentum"]).max() < 1e-9
+
+
+def test_mixed_nve_energy_is_conserved():
+    w = I.bcc_fe(10, seed=13)
+    with _gpu_system(w, "mixed") as s:
+        s.eam_forces()
+        e0 = s.energy()
+        tes = []
+        for _ in range(20):
+            s.step(10)
+            tes.append(s.energy()["te"])
+    tes = np.array(tes)
+    assert np.abs(tes - e0["te"]).max() < 2e-3 * e0["ke"]
+
+
+def test_strain_ramp_matches_oracle():
+    w = I.bcc_fe(10, seed=14, tables=True)
+    w.strain_rate_zz = -1.0e9
+    ref = oracle.run_vv(w.pos, w.vel, w.species, w.potential.masses, w.box, w.potential, w.dt_fs, 30,
+                        w.skin, w.k_max, strain_rate_zz=w.strain_rate_zz)
+    with _gpu_system(w) as s:
+        s.step(30)
+        e = s.energy()
+        pos = s.positions()
+    assert np.array_equal(e["box"], ref["box"])
+    assert np.abs(pos - ref["pos"]).max() < 1e-9
+    assert abs(e["pe"] - ref["energies"][-1, 0]) <= FP64_TOL * abs(ref["energies"][-1, 0])
+
+
+def test_scheduled_rebuilds_and_determinism():
+    w = I.bcc_fe(10, seed=15)
+    with _gpu_system(w, "mixed", rebuild_every=5) as a, _gpu_system(w, "mixed", rebuild_every=5) as b:
+        a.step(20)
+        b.step(20)
+        ea = a.energy()
+        assert ea["n_rebuilds"] >= 5
+        assert np.array_equal(a.positions(), b.positions())
+        assert np.array_equal(a.velocities(), b.velocities())
+        assert ea["te"] == b.energy()["te"]
+
+
+def test_state_round_trip_continues_bitwise():
+    """Checkpoint/restart (§4.1.3): read the state, write it back, continue; no drift in bits."""
+    w = I.bcc_fe(10, seed=16)
+    with _gpu_system(w) as a, _gpu_system(w) as b:
+        a.step(10)
+        pos, vel, f = a.positions(), a.velocities(), a.forces()
+        a.set_state(pos, vel, f)
+        a.step(10)
+        b.step(20)
+        assert np.array_equal(a.positions(), b.positions())
+        assert np.array_equal(a.velocities(), b.velocities())
+
+
+def test_device_inputs_match_host_inputs():
+    w = I.bcc_fe(10, seed=17)
+    with _gpu_system(w) as a, _gpu_system(w, device_inputs=True) as b:
+        a.eam_forces()
+        b.eam_forces()
+        assert np.array_equal(a.forces(), b.forces())
+
+
+# --------------------------------------------------------------------------- edge cases
+def test_empty_and_single_atom_systems():
+    pot = I.fs_fe_analytic()
+    box = np.array([20.0, 20.0, 20.0])
+    empty = I.Workload(name="empty", pos=np.zeros((0, 3)), vel=np.zeros((0, 3)), species=np.zeros(0, np.int32),
+                       box=box, potential=pot, skin=0.3, k_max=8, dt_fs=1.0, steps=1, temperature=0.0)
+    with _gpu_system(empty) as s:
+        assert s.eam_forces() == 0.0
+        s.step(3)
+        e = s.energy()
+        assert e["pe"] == 0.0 and e["ke"] == 0.0
+    one = I.Workload(name="one", pos=np.array([[1.0, 2.0, 3.0]]), vel=np.array([[0.01, 0.02, -0.03]]),
+                     species=np.zeros(1, np.int32), box=box, potential=pot, skin=0.3, k_max=8, dt_fs=2.0,
+                     steps=1, temperature=0.0)
+    with _gpu_system(one) as s:
+        s.step(50)
+        assert np.allclose(s.positions(), [[1.0 + 1.0, 2.0 + 2.0, 3.0 - 3.0]], rtol=0, atol=1e-12)
+
+
+def test_overflow_is_reported():
+    w = I.bcc_fe(10, seed=18)
+    with _gpu_system(w, k_max=8) as s:
+        with pytest.raises(md.MDError) as ei:
+            s.eam_forces()
+        assert ei.value.status == md.MD_ERR_NBR_OVERFLOW
+
+
+def test_strict_skin_is_reported():
+    w = I.bcc_fe(10, seed=19)
+    with _gpu_system(w, strict_skin=True) as s:
+        s.step(2)
+        pos = s.positions()
+        pos[3] += 0.2          # teleport one atom by more than skin/2
+        s.set_state(pos=pos)
+        with pytest.raises(md.MDError) as ei:
+            s.step(1)
+        assert ei.value.status == md.MD_ERR_SKIN
+
+
+def test_coincident_atoms_are_reported_non_finite():
+    w = I.bcc_fe(8, seed=20)
+    w.pos[5] = w.pos[6]
+    with _gpu_system(w) as s:
+        with pytest.raises(md.MDError) as ei:
+            s.eam_forces()
+        assert ei.value.status == md.MD_ERR_NONFINITE
+
+
+# --------------------------------------------------------------------------- full size
+def test_full_size_cu500k_forces_and_lists():
+    """fcc Cu 50^3 = 500,000 atoms, Sutton-Chen 5,000-knot tables, in the benchmark's
+    configuration: every force (FP64 and mixed) and every neighbour set against the oracle."""
+    w = I.fcc_cu(50, seed=2)
+    ref = oracle.forces(w.pos, w.species, w.box, w.potential, skin=w.skin, k_max=w.k_max, method="cells")
+    fs = np.abs(ref["force"]).max()
+    with _gpu_system(w) as s:
+        pe = s.eam_forces()
+        f = s.forces()
+        cg, lg = s.neighbours()
+    assert np.array_equal(cg, ref["count"])
+    lg.sort(axis=1)
+    lo = np.where(ref["list"] < 0, np.iinfo(np.int32).max, ref["list"])
+    lg = np.where(lg < 0, np.iinfo(np.int32).max, lg)
+    lo.sort(axis=1)
+    lg.sort(axis=1)
+    assert np.array_equal(lg, lo)
+    assert np.abs(f - ref["force"]).max() <= FP64_TOL * fs
+    assert abs(pe - ref["pe"]) <= FP64_TOL * abs(ref["pe"])
+    with _gpu_system(w, "mixed") as s:
+        pe32 = s.eam_forces()
+        f32 = s.forces()
+    assert np.abs(f32 - ref["force"]).max() <= MIXED_FORCE_TOL * fs
+    assert abs(pe32 - ref["pe"]) <= MIXED_PE_TOL * abs(ref["pe"])
