@@ -38,8 +38,8 @@ WORKLOAD = ("fcc Cu 50x50x50 cells = 500,000 atoms, Sutton-Chen EAM as 5,000-kno
             "(cutoff 2a, shifted force), 300 K, NVE velocity Verlet dt = 2 fs, skin 0.3 Å")
 
 
-def _config(precision):
-    return {"workload": WORKLOAD, "n_atoms": 4 * CELLS ** 3, "precision": precision, "seed": SEED,
+def _config(precision, cells=CELLS):
+    return {"workload": WORKLOAD, "n_atoms": 4 * cells ** 3, "precision": precision, "seed": SEED,
             "rebuild": "when an atom moved > skin/2 (checked every step)",
             "l2": "inputs larger than L2: the neighbour list alone is 4 B x 140 x 500k = 280 MB per pass"}
 
@@ -202,16 +202,15 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    w = I.fcc_cu(CELLS, seed=SEED + rank)
+    w = I.fcc_cu(args.cells, seed=SEED + rank)
     n = w.n_atoms
     stream = torch.cuda.Stream()
     res = {}
-    forces0 = {}
-    for precision in ("mixed", "fp64"):
-        with torch.cuda.stream(stream):
-            s = md.System(w, precision=precision, stream=stream.cuda_stream, device_inputs=True)
+    snapshot = {}
+    for precision in (("mixed",) if args.profile_case else ("mixed", "fp64")):
+        s = md.System(w, precision=precision, stream=stream.cuda_stream, device_inputs=True)
         s.eam_forces()
-        forces0[precision] = s.forces()
+        lanes = s.tune()
         counts = s.get(md.MD_GET_NBR_COUNT)
         s.step(args.warmup)
         e0 = s.energy()
@@ -229,8 +228,23 @@ def run_ours(args):
         prof = s.profile()
         e1 = s.energy()
         res[precision] = dict(ms=ms, prof=prof, e0=e0, e1=e1, counts=counts, clocks=clk.summary(),
-                              launches=prof["launches"] - launches0)
+                              launches=prof["launches"] - launches0, lanes=lanes)
+        # forces of both precisions at the same thermalised positions (the mixed run's last state)
+        if precision == "mixed":
+            snapshot["pos"] = s.positions()
+            snapshot["mixed"] = s.forces()
+        else:
+            s.set_state(pos=snapshot["pos"])
+            s.eam_forces()
+            snapshot["fp64"] = s.forces()
         s.close()
+    if args.profile_case:
+        if rank == 0:
+            r = res["mixed"]
+            print(json.dumps({"profile_case": True, "n_atoms": n, "ms_per_step": r["ms"] / args.steps,
+                              "lanes": r["lanes"], "kernel_ms": {k: r["prof"]["ms_" + k] / max(1, r["prof"]["n_" + k])
+                                                               for k in ("kick", "rebuild", "density", "force")}}))
+        return 0
 
     # end to end through the C ABI with host buffers: state in, one step, state and energies out
     e2e = None
@@ -276,7 +290,7 @@ def run_ours(args):
     kname = "k_force32" if kern == "force" else "k_density32"
     traffic = _traffic(kname)
 
-    f64, f32 = forces0["fp64"], forces0["mixed"]
+    f64, f32 = snapshot["fp64"], snapshot["mixed"]
     ferr = np.abs(f32 - f64)
     cpu = None
     if world == 1:
@@ -295,8 +309,8 @@ def run_ours(args):
         q = res[pr]
         de = (q["e1"]["te"] - q["e0"]["te"]) / n
         return {"value": world * n * args.steps / (q["ms"] * 1e-3), "ms_per_step": q["ms"] / args.steps,
-                "nve_drift_ev_per_atom": de, "steps_timed": args.steps,
-                "rebuilds_in_timed_region": None,
+                "nve_drift_ev_per_atom": de, "steps_timed": args.steps, "lanes_per_atom": q["lanes"],
+                "rebuilds_in_timed_region": q["e1"]["n_rebuilds"] - q["e0"]["n_rebuilds"],
                 "kernel_ms_per_step": {k: q["prof"]["ms_" + k] / max(1, q["prof"]["n_" + k])
                                        for k in ("kick", "rebuild", "density", "force")}}
 
@@ -311,7 +325,8 @@ def run_ours(args):
                      "peak_source": peak_src},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": r["launches"], "clocks": r["clocks"],
         "mixed_path": path_summary("mixed"), "fp64_path": path_summary("fp64"),
-        "mixed_vs_fp64_force_error_ev_per_a": {"max": float(ferr.max()),
+        "mixed_vs_fp64_force_error_ev_per_a": {"state": "positions after the mixed run's timed steps",
+                                               "max": float(ferr.max()),
                                                "rms": float(np.sqrt((ferr ** 2).mean())),
                                                "max_force": float(np.abs(f64).max())},
         "neighbours_per_atom": sum_counts / n,
@@ -328,6 +343,9 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cells", type=int, default=CELLS, help="fcc Cu cube edge in cells (profiling cases)")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="mixed path only, no e2e/CPU legs: a short run for ncu captures")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

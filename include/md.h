@@ -110,6 +110,10 @@ typedef struct {
     double strain_rate_zz; /* 1/s; each step the box z edge and all z coordinates are
                               multiplied by (1 + rate*dt) (§2.2 strain-rate loading) */
     void *stream;          /* cudaStream_t, or NULL */
+    int32_t lanes_per_atom; /* threads sharing one atom's neighbour sums in the force passes:
+                               1, 2, 4, 8, 16, 32, or 0 = chosen from the expected neighbour
+                               count (see md_tune).  Results depend on it only in rounding. */
+    int32_t pad;
 } md_config;
 
 typedef struct {
@@ -186,6 +190,13 @@ md_status md_get(md_ctx *ctx, int32_t what, void *dst, int32_t on_device);
  * (e.g. from a checkpoint, §4.1.3).  Any NULL of pos/vel keeps that array. */
 md_status md_set_state(md_ctx *ctx, const double *pos, const double *vel, const double *force,
                        int32_t on_device);
+
+/* Autotuner: time the density and force passes of the current state with each
+ * lanes_per_atom in {1, 2, 4, 8, 16, 32} (a few launches each, CUDA events), keep the
+ * fastest for this context and return it in *lanes_out (nullable).  Builds the list first
+ * if needed.  Because the lane count fixes the summation order, results after md_tune are
+ * reproducible but may differ in the last bits from those before it. */
+md_status md_tune(md_ctx *ctx, int32_t *lanes_out);
 
 /* Kernel timing of a context (tracing).  `launches` counts every kernel the context has
  * enqueued since md_create.  While profiling is on, md_step brackets each kernel class with

@@ -41,6 +41,7 @@ struct md_ctx {
     double *h_reduce = nullptr; // pinned [kPartials]
     std::vector<void *> allocs;
     int64_t step = 0;
+    int lanes = 1;              // lanes per atom of the force passes
     bool list_valid = false, forces_valid = false, energy_valid = false;
     std::string err;
     // tracing
@@ -125,7 +126,7 @@ Box make_box(const double L[3]) {
 // Monomial coefficients of the cubic Hermite interpolant on each interval of a uniform knot
 // grid, in t = (x - x_k)/h: c0 = y_k, c1 = h y'_k, c2 = 3(y_k+1 - y_k) - 2 h y'_k - h y'_k+1,
 // c3 = 2(y_k - y_k+1) + h y'_k + h y'_k+1.  Row nk-1 continues linearly past the last knot.
-void cubic_rows(const double *tab, int nk, double h, double4_32a *out64, float4 *out32) {
+void cubic_rows(const double *tab, int nk, double h, double4_32a *out64) {
     const double *y = tab, *yp = tab + nk;
     for (int k = 0; k < nk; k++) {
         double4_32a c;
@@ -137,7 +138,6 @@ void cubic_rows(const double *tab, int nk, double h, double4_32a *out64, float4 
             c = make_double4_32a(y[k], h * yp[k], 0.0, 0.0);
         }
         out64[k] = c;
-        if (out32) out32[k] = make_float4((float)c.x, (float)c.y, (float)c.z, (float)c.w);
     }
 }
 
@@ -177,9 +177,11 @@ cudaError_t enqueue_forces(md_ctx *ctx) {
     cudaError_t e = launch_check_displacement(ctx->A, ctx->lim2, ctx->stream);
     if (e == cudaSuccess && !ctx->list_valid) e = launch_set_rebuild(ctx->d_flags, ctx->stream);
     if (e == cudaSuccess) e = enqueue_rebuild(ctx);
-    if (e == cudaSuccess) e = launch_density(ctx->A, ctx->P, ctx->precision, ctx->stream);
-    if (e == cudaSuccess) e = launch_force(ctx->A, ctx->P, ctx->precision, false, true, 0.0, ctx->stream);
-    if (e == cudaSuccess) e = launch_reduce(ctx->A, ctx->d_reduce, ctx->stream);
+    if (e == cudaSuccess) e = launch_density(ctx->A, ctx->P, ctx->precision, ctx->lanes, ctx->stream);
+    if (e == cudaSuccess)
+        e = launch_force(ctx->A, ctx->P, ctx->precision, ctx->lanes, false, true, 0.0, ctx->stream);
+    if (e == cudaSuccess)
+        e = launch_reduce(ctx->A, partial_blocks(ctx->A.n, ctx->lanes), ctx->d_reduce, ctx->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ctx->h_reduce, ctx->d_reduce, sizeof(double) * kPartials,
                             cudaMemcpyDeviceToHost, ctx->stream);
@@ -357,6 +359,20 @@ md_status md_create(const md_config *cfg, const md_potential *pot, const double 
             return bail(MD_ERR_BOX);
         }
     }
+    // lanes per atom: given, or from the expected neighbour count (4/3 pi r_list^3 x density)
+    {
+        const int want = cfg->lanes_per_atom;
+        if (want != 0 && (want < 1 || want > 32 || (want & (want - 1)) != 0)) return bail(MD_ERR_ARG);
+        if (want) {
+            ctx->lanes = want;
+        } else {
+            const double vol = ctx->L[0] * ctx->L[1] * ctx->L[2];
+            const double k_est = 4.18879020478639 * ctx->r_list * ctx->r_list * ctx->r_list * (double)n / vol;
+            int t = 1;
+            while (t < 32 && t * 12 < k_est) t *= 2;
+            ctx->lanes = t;
+        }
+    }
     // host copies of the inputs
     std::vector<double> hpos(3 * n), hvel(3 * n, 0.0);
     std::vector<int32_t> hspec(n, 0);
@@ -400,12 +416,13 @@ md_status md_create(const md_config *cfg, const md_potential *pot, const double 
     chk(dalloc(ctx, &A.pos, n)); chk(dalloc(ctx, &A.vel, n)); chk(dalloc(ctx, &A.force, n));
     chk(dalloc(ctx, &A.ref, n)); chk(dalloc(ctx, &A.pos_tmp, n)); chk(dalloc(ctx, &A.vel_tmp, n));
     chk(dalloc(ctx, &A.force_tmp, n)); chk(dalloc(ctx, &A.posf, n)); chk(dalloc(ctx, &A.p2f, n));
+    chk(dalloc(ctx, &A.p2d, n));
     chk(dalloc(ctx, &A.rho, n)); chk(dalloc(ctx, &A.dF, n)); chk(dalloc(ctx, &A.e_atom, n));
     chk(dalloc(ctx, &A.id, n)); chk(dalloc(ctx, &A.id_tmp, n)); chk(dalloc(ctx, &A.rank, n));
     chk(dalloc(ctx, &A.spec, n)); chk(dalloc(ctx, &A.spec_tmp, n)); chk(dalloc(ctx, &A.cell_of, n));
     chk(dalloc(ctx, &A.slot, n)); chk(dalloc(ctx, &A.order, n)); chk(dalloc(ctx, &A.count, n));
     chk(dalloc(ctx, &A.nbr, (size_t)n * cfg->k_max));
-    const int nblocks = n > 0 ? blocks_for(n, kThreads) : 1;
+    const int nblocks = n > 0 ? partial_blocks((int)n, 32) : 1;  // enough rows for any lane count
     chk(dalloc(ctx, &A.partials, (size_t)nblocks * kPartials));
     chk(dalloc(ctx, &ctx->d_box, 1));
     chk(dalloc(ctx, &ctx->d_flags, 1));
@@ -450,8 +467,8 @@ md_status md_create(const md_config *cfg, const md_potential *pot, const double 
         const double hr = (pot->r_cut - pot->r_min) / (nk - 1);
         const double hrho = (pot->rho_max - pot->rho_min) / (nk - 1);
         const size_t npair = (size_t)ns * ns;
-        std::vector<double4_32a> V64(npair * nk), P64(npair * nk), F64((size_t)ns * nk);
-        std::vector<float4> V32(npair * nk), P32(npair * nk);
+        std::vector<double4_32a> VP64(npair * nk * 2), F64((size_t)ns * nk), rv(nk), rp(nk);
+        std::vector<float> VP32(npair * nk * 8);
         const size_t tl = 2 * (size_t)nk;
         for (int a = 0; a < ns; a++)
             for (int b = 0; b < ns; b++) {
@@ -462,24 +479,30 @@ md_status md_create(const md_config *cfg, const md_potential *pot, const double 
                         ctx->err = "V table must be symmetric in its two species";
                         return bail(MD_ERR_ARG);
                     }
-                cubic_rows(tv, nk, hr, &V64[(a * ns + b) * (size_t)nk], &V32[(a * ns + b) * (size_t)nk]);
-                cubic_rows(pot->tables + (npair + a * ns + b) * tl, nk, hr, &P64[(a * ns + b) * (size_t)nk],
-                           &P32[(a * ns + b) * (size_t)nk]);
+                cubic_rows(tv, nk, hr, rv.data());
+                cubic_rows(pot->tables + (npair + a * ns + b) * tl, nk, hr, rp.data());
+                const size_t base = (size_t)(a * ns + b) * nk;
+                for (int k = 0; k < nk; k++) {
+                    VP64[(base + k) * 2] = rv[k];
+                    VP64[(base + k) * 2 + 1] = rp[k];
+                    float *f = &VP32[(base + k) * 8];
+                    const double c[8] = {rv[k].x, rv[k].y, rv[k].z, rv[k].w, rp[k].x, rp[k].y, rp[k].z, rp[k].w};
+                    for (int q = 0; q < 8; q++) f[q] = (float)c[q];
+                }
             }
         for (int a = 0; a < ns; a++)
-            cubic_rows(pot->tables + (2 * npair + a) * tl, nk, hrho, &F64[(size_t)a * nk], nullptr);
-        double4_32a *dV64, *dP64, *dF64;
-        float4 *dV32, *dP32;
-        chk(dalloc(ctx, &dV64, V64.size())); chk(dalloc(ctx, &dP64, P64.size()));
-        chk(dalloc(ctx, &dF64, F64.size())); chk(dalloc(ctx, &dV32, V32.size()));
-        chk(dalloc(ctx, &dP32, P32.size()));
+            cubic_rows(pot->tables + (2 * npair + a) * tl, nk, hrho, &F64[(size_t)a * nk]);
+        double4_32a *dVP64, *dVP32, *dF64;
+        chk(dalloc(ctx, &dVP64, VP64.size()));
+        chk(dalloc(ctx, &dVP32, VP32.size() / 8));
+        chk(dalloc(ctx, &dF64, F64.size()));
         if (e != cudaSuccess) return bail(fail(ctx, MD_ERR_OOM, "table allocation", e));
-        chk(cudaMemcpy(dV64, V64.data(), V64.size() * sizeof(double4_32a), cudaMemcpyHostToDevice));
-        chk(cudaMemcpy(dP64, P64.data(), P64.size() * sizeof(double4_32a), cudaMemcpyHostToDevice));
+        chk(cudaMemcpy(dVP64, VP64.data(), VP64.size() * sizeof(double4_32a), cudaMemcpyHostToDevice));
+        chk(cudaMemcpy(dVP32, VP32.data(), VP32.size() * sizeof(float), cudaMemcpyHostToDevice));
         chk(cudaMemcpy(dF64, F64.data(), F64.size() * sizeof(double4_32a), cudaMemcpyHostToDevice));
-        chk(cudaMemcpy(dV32, V32.data(), V32.size() * sizeof(float4), cudaMemcpyHostToDevice));
-        chk(cudaMemcpy(dP32, P32.data(), P32.size() * sizeof(float4), cudaMemcpyHostToDevice));
-        P.V64 = dV64; P.P64 = dP64; P.F64 = dF64; P.V32 = dV32; P.P32 = dP32;
+        P.VP64 = dVP64;
+        P.VP32 = dVP32;
+        P.F64 = dF64;
     }
     // initial state (caller order = cell order until the first build)
     Box box = make_box(ctx->L);
@@ -563,14 +586,15 @@ md_status md_step(md_ctx *ctx, int32_t n_steps) {
         }
         MD_CK(enqueue_rebuild(ctx));
         MD_CK(mark(ctx));
-        MD_CK(launch_density(ctx->A, ctx->P, ctx->precision, ctx->stream));
+        MD_CK(launch_density(ctx->A, ctx->P, ctx->precision, ctx->lanes, ctx->stream));
         MD_CK(mark(ctx));
-        MD_CK(launch_force(ctx->A, ctx->P, ctx->precision, true, s == n_steps - 1, ctx->half_dt, ctx->stream));
+        MD_CK(launch_force(ctx->A, ctx->P, ctx->precision, ctx->lanes, true, s == n_steps - 1, ctx->half_dt,
+                           ctx->stream));
         MD_CK(mark(ctx));
         ctx->launches += 3 + kRebuildLaunches;
         ctx->step++;
     }
-    MD_CK(launch_reduce(ctx->A, ctx->d_reduce, ctx->stream));
+    MD_CK(launch_reduce(ctx->A, partial_blocks(ctx->A.n, ctx->lanes), ctx->d_reduce, ctx->stream));
     ctx->launches++;
     MD_CK(cudaMemcpyAsync(ctx->h_reduce, ctx->d_reduce, sizeof(double) * kPartials, cudaMemcpyDeviceToHost,
                           ctx->stream));
@@ -654,6 +678,46 @@ md_status md_get(md_ctx *ctx, int32_t what, void *dst, int32_t on_device) {
         default:
             return fail(ctx, MD_ERR_ARG, "unknown md_get selector");
     }
+}
+
+md_status md_tune(md_ctx *ctx, int32_t *lanes_out) {
+    if (!ctx) return MD_ERR_ARG;
+    md_status st = ctx->list_valid ? MD_OK : md_build_neighbours(ctx);
+    if (st != MD_OK) return st;
+    if (ctx->n > 0) {
+        cudaEvent_t e0, e1;
+        MD_CK(cudaEventCreate(&e0));
+        MD_CK(cudaEventCreate(&e1));
+        float best = 1e30f;
+        int best_t = ctx->lanes;
+        const int keep = ctx->lanes;
+        for (int t = 1; t <= 32; t *= 2) {
+            ctx->lanes = t;
+            for (int rep = 0; rep < 4; rep++) {  // first round is a warm-up
+                MD_CK(cudaEventRecord(e0, ctx->stream));
+                MD_CK(launch_density(ctx->A, ctx->P, ctx->precision, t, ctx->stream));
+                MD_CK(launch_force(ctx->A, ctx->P, ctx->precision, t, false, false, 0.0, ctx->stream));
+                MD_CK(cudaEventRecord(e1, ctx->stream));
+                MD_CK(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                MD_CK(cudaEventElapsedTime(&ms, e0, e1));
+                if (rep > 0 && ms < best) {
+                    best = ms;
+                    best_t = t;
+                }
+                ctx->launches += 2;
+            }
+        }
+        (void)keep;
+        ctx->lanes = best_t;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        ctx->energy_valid = false;  // partial-sum rows depend on the lane count
+        st = sync_and_check(ctx, false);
+        if (st != MD_OK) return st;
+    }
+    if (lanes_out) *lanes_out = ctx->lanes;
+    return MD_OK;
 }
 
 md_status md_set_profiling(md_ctx *ctx, int32_t on) {

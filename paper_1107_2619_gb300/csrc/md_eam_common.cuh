@@ -1,0 +1,171 @@
+// Device helpers shared by the FP64 and mixed EAM passes (md_eam64.cu, md_eam32.cu).
+//
+// Work split: T lanes per atom (T a power of two dividing 32).  Lane l of atom i takes the
+// neighbours k = l, l+T, l+2T, ... of i's list row (nbr[i*k_max + k]), so the T lanes read
+// one contiguous stretch of the row; the lanes' partial sums are combined by a fixed
+// butterfly of warp shuffles, so the result depends on T but not on scheduling.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "md_internal.cuh"
+
+namespace mdk {
+namespace eam {
+
+// 1/sqrt(x): FP32 hardware estimate refined by two Newton-Raphson steps in FP64
+// (y <- y + y (1 - x y^2) / 2); relative error ~1e-16.
+__device__ __forceinline__ double rsqrt64(double x) {
+    double y = (double)rsqrtf((float)x);
+    double e = fma(-x * y, y, 1.0);
+    y = fma(0.5 * y, e, y);
+    e = fma(-x * y, y, 1.0);
+    return fma(0.5 * y, e, y);
+}
+
+// Error-free FP32 accumulation (Knuth's TwoSum): hi + lo carries the exact running sum.
+__device__ __forceinline__ void two_sum_add(float &hi, float &lo, float x) {
+    float s = hi + x;
+    float bp = s - hi;
+    float err = (hi - (s - bp)) + (x - bp);
+    hi = s;
+    lo += err;
+}
+
+__device__ __forceinline__ void unpack2(double d, float &a, float &b) {
+    long long v = __double_as_longlong(d);
+    a = __int_as_float((int)(v & 0xffffffffll));
+    b = __int_as_float((int)(v >> 32));
+}
+
+// Interval of a uniform knot grid: x in knot units.  Returns the row and t in [0,1]
+// (row nk-1 continues linearly); below the first knot returns row 0 with `below` set.
+template <typename R>
+__device__ __forceinline__ int knot_row(R x, int nk, R &t, bool &below) {
+    below = !(x >= R(0));
+    int k = (x < (R)(nk - 1)) ? (int)x : nk - 1;
+    k = below ? 0 : k;
+    t = below ? x : x - (R)k;
+    return k;
+}
+
+template <typename R>
+__device__ __forceinline__ R cubic(R t, R c0, R c1, R c2, R c3, bool below, R &dydt) {
+    if (below) {
+        dydt = c1;
+        return fma(t, c1, c0);
+    }
+    dydt = fma(t, fma(R(3) * c3, t, R(2) * c2), c1);
+    return fma(t, fma(t, fma(t, c3, c2), c1), c0);
+}
+
+// ---- analytic Finnis-Sinclair pair functions (fs = d, c, A, beta, c0, c1, c2; bd = beta/d) ----
+template <typename R>
+__device__ __forceinline__ R fs_phi(const R *fs, R bd, R r) {
+    R t = r - fs[0];
+    return t < R(0) ? t * t * fma(bd, t, R(1)) : R(0);
+}
+
+template <typename R>
+__device__ __forceinline__ R fs_dphi(const R *fs, R bd, R r) {
+    R t = r - fs[0];
+    return t < R(0) ? t * fma(R(3) * bd, t, R(2)) : R(0);
+}
+
+template <typename R>
+__device__ __forceinline__ R fs_V(const R *fs, R r, R &dV) {
+    R u = r - fs[1];
+    if (!(u < R(0))) {
+        dV = R(0);
+        return R(0);
+    }
+    R q = fma(fma(fs[6], r, fs[5]), r, fs[4]);
+    R dq = fma(R(2) * fs[6], r, fs[5]);
+    dV = u * fma(u, dq, R(2) * q);
+    return u * u * q;
+}
+
+// F and F' in FP64 (one evaluation per atom, both precisions).
+__device__ __forceinline__ double embed64(const Pot &P, int a, double rho, double &dF, Flags *flags) {
+    if (P.kind == MD_POT_FS_ANALYTIC) {
+        if (!(rho > 0.0)) {
+            dF = 0.0;
+            return 0.0;
+        }
+        double s = sqrt(rho);
+        dF = -0.5 * P.fs[2] / s;
+        return -P.fs[2] * s;
+    }
+    double x = (rho - P.rho_min) * P.inv_drho, t, d;
+    bool below;
+    int k = knot_row(x, P.nk, t, below);
+    if (below || x > (double)(P.nk - 1)) atomicAdd(&flags->range_violations, 1ull);
+    double4_32a c = P.F64[(size_t)a * P.nk + k];
+    double F = cubic(t, c.x, c.y, c.z, c.w, below, d);
+    dF = d * P.inv_drho;
+    return F;
+}
+
+// Butterfly sum over the T lanes of an atom (all 32 lanes of the warp take part).
+template <int T, typename V>
+__device__ __forceinline__ V lane_sum(V x) {
+#pragma unroll
+    for (int o = T / 2; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+template <int T>
+__device__ __forceinline__ void lane_sum_df(float &hi, float &lo) {
+#pragma unroll
+    for (int o = T / 2; o > 0; o >>= 1) {
+        float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+        float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+        two_sum_add(hi, lo, h2);
+        lo += l2;
+    }
+}
+
+// Per-block FP64 partial sums (fixed order): every thread of the block must call it.
+__device__ __forceinline__ void block_partials(double (&v)[kPartials], double *out) {
+    __shared__ double sh[kThreads / 32][kPartials];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < kPartials; q++) {
+        double x = v[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) sh[w][q] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < kPartials) {
+        double s = 0.0;
+        for (int k = 0; k < kThreads / 32; k++) s += sh[k][threadIdx.x];
+        out[(size_t)blockIdx.x * kPartials + threadIdx.x] = s;
+    }
+}
+
+__device__ __forceinline__ void clear_rebuild_once(Flags *f) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (f->need_rebuild) f->n_rebuilds++;
+        f->need_rebuild = 0;
+    }
+}
+
+// Second half kick v += (dt/2 * f) * (acc/m) with the separately rounded operations of the
+// definition, and the atom's kinetic/momentum partials (m = acc / v.w).
+__device__ __forceinline__ void kick_and_partials(double4_32a &v, double fx, double fy, double fz,
+                                                  double half_dt, bool kick) {
+    if (kick) {
+        v.x = __dadd_rn(v.x, __dmul_rn(__dmul_rn(half_dt, fx), v.w));
+        v.y = __dadd_rn(v.y, __dmul_rn(__dmul_rn(half_dt, fy), v.w));
+        v.z = __dadd_rn(v.z, __dmul_rn(__dmul_rn(half_dt, fz), v.w));
+    }
+}
+
+template <int T>
+__device__ __forceinline__ int blocks_for_lanes(long long n) {
+    return (int)((n * T + kThreads - 1) / kThreads);
+}
+
+}  // namespace eam
+}  // namespace mdk

@@ -44,7 +44,9 @@ struct Flags {
 
 // Device view of the potential.  Tables hold, per interval k of a uniform knot grid, the
 // monomial coefficients (c0, c1, c2, c3) of the cubic in t = (x - x_k)/h; row n_knots-1 holds
-// (y_end, h*y'_end, 0, 0) for the linear continuation past the last knot.
+// (y_end, h*y'_end, 0, 0) for the linear continuation past the last knot.  Pair tables fuse
+// V and phi of a species pair per interval: VP32 row = 8 floats (V c0..c3, phi c0..c3) in
+// one 32-byte load; VP64 = two double4 per interval (V, then phi).
 struct Pot {
     int kind, ns, nk;
     double rc2;
@@ -55,8 +57,9 @@ struct Pot {
     float bdf;
     double r_min, inv_dr, rho_min, inv_drho;
     float r_minf, inv_drf;
-    const double4_32a *V64, *P64, *F64;   // [(a*ns+b)*nk + k], F: [a*nk + k]
-    const float4 *V32, *P32;
+    const double4_32a *VP64;  // [((a*ns+b)*nk + k)*2 + {0: V, 1: phi_ab}]
+    const double4_32a *VP32;  // [(a*ns+b)*nk + k], 8 floats
+    const double4_32a *F64;   // [a*nk + k]
 };
 
 // Device view of the per-atom state (cell order).
@@ -66,10 +69,11 @@ struct Atoms {
     double4_32a *pos_tmp, *vel_tmp, *force_tmp;  // renumbering scratch
     float4 *posf;                            // FP32 wrapped position, w = species bits
     float4 *p2f;                             // mixed pass 2: wrapped position + F'(rho)
+    double4_32a *p2d;                        // FP64 pass 2: position + F'(rho)
     double *rho, *dF, *e_atom;
     int32_t *id, *id_tmp, *rank, *spec, *spec_tmp;
     int32_t *cell_of, *slot, *order;
-    int32_t *nbr, *count;                    // nbr[k*n + i], k < k_max
+    int32_t *nbr, *count;                    // nbr[i*k_max + k], k < min(count, k_max)
     double *partials;                        // [n_blocks][kPartials]
     Box *box;
     Flags *flags;
@@ -92,10 +96,12 @@ cudaError_t launch_kick_drift(const Atoms &A, double half_dt, double dt, double 
                               double lim2, cudaStream_t s);
 cudaError_t launch_check_displacement(const Atoms &A, double lim2, cudaStream_t s);
 cudaError_t launch_wrap(const Atoms &A, cudaStream_t s);
-cudaError_t launch_density(const Atoms &A, const Pot &P, int precision, cudaStream_t s);
-cudaError_t launch_force(const Atoms &A, const Pot &P, int precision, bool kick, bool energy,
+// lanes = T lanes per atom (1, 2, 4, 8, 16 or 32)
+cudaError_t launch_density(const Atoms &A, const Pot &P, int precision, int lanes, cudaStream_t s);
+cudaError_t launch_force(const Atoms &A, const Pot &P, int precision, int lanes, bool kick, bool energy,
                          double half_dt, cudaStream_t s);
-cudaError_t launch_reduce(const Atoms &A, double *out, cudaStream_t s);
+int partial_blocks(int n, int lanes);  // blocks (and partial-sum rows) of a force launch
+cudaError_t launch_reduce(const Atoms &A, int nblocks, double *out, cudaStream_t s);
 cudaError_t launch_unsort_vec(const Atoms &A, const double4_32a *src, double *dst, cudaStream_t s);
 cudaError_t launch_unsort_scalar(const Atoms &A, const double *src, double *dst, cudaStream_t s);
 cudaError_t launch_unsort_int(const Atoms &A, const int32_t *src, int32_t *dst, cudaStream_t s);

@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(kThreads) k_build_list(Atoms A, Cells C, doubl
         const int cz = cell_coord(pi.z, B.invL[2], nz);
         const float Lx = B.Lf[0], Ly = B.Lf[1], Lz = B.Lf[2];
         const float ix = B.invLf[0], iy = B.invLf[1], iz = B.invLf[2];
-        const size_t n = (size_t)A.n;
+        int32_t *row = A.nbr + (size_t)i * A.k_max;
         for (int dz = -1; dz <= 1; dz++) {
             int z = cz + dz;
             z += (z < 0) ? nz : 0;
@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(kThreads) k_build_list(Atoms A, Cells C, doubl
                         bool in = r2 < band_lo;
                         if (!in && r2 <= band_hi) in = within_exact(pi, A.pos[j], B, rl2);
                         if (in) {
-                            if (cnt < A.k_max) A.nbr[(size_t)cnt * n + i] = j;
+                            if (cnt < A.k_max) row[cnt] = j;
                             cnt++;
                         }
                     }

@@ -103,8 +103,9 @@ __global__ void k_unsort_list(Atoms A, int32_t *dst) {
     if (i >= A.n) return;
     const int cnt = min(A.count[i], A.k_max);
     int32_t *row = dst + (size_t)A.id[i] * A.k_max;
+    const int32_t *src = A.nbr + (size_t)i * A.k_max;
     for (int k = 0; k < A.k_max; k++)
-        row[k] = k < cnt ? A.id[A.nbr[(size_t)k * A.n + i]] : -1;
+        row[k] = k < cnt ? A.id[src[k]] : -1;
 }
 
 __global__ void k_sort_in_vec(Atoms A, const double *src, double4_32a *dst) {

@@ -28,7 +28,7 @@ MD_PREC_FP64, MD_PREC_MIXED = 0, 1
 
 # functions declared in include/md.h (checked by the CPU test-suite)
 EXPORTS = ["md_abi_version", "md_status_string", "md_create", "md_build_neighbours", "md_eam_forces",
-           "md_step", "md_energy", "md_get", "md_set_state", "md_set_profiling", "md_get_profile",
+           "md_step", "md_energy", "md_get", "md_set_state", "md_tune", "md_set_profiling", "md_get_profile",
            "md_last_error", "md_destroy"]
 
 
@@ -44,7 +44,7 @@ class md_config(C.Structure):
     _fields_ = [("n_atoms", C.c_int64), ("h", C.c_double * 9), ("skin", C.c_double),
                 ("k_max", C.c_int32), ("rebuild_every", C.c_int32), ("dt_fs", C.c_double),
                 ("precision", C.c_int32), ("strict_skin", C.c_int32), ("strain_rate_zz", C.c_double),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("lanes_per_atom", C.c_int32), ("pad", C.c_int32)]
 
 
 class md_energies(C.Structure):
@@ -96,6 +96,8 @@ def lib():
         L.md_get.argtypes = [P, i32, P, i32]
         L.md_set_state.restype = C.c_int
         L.md_set_state.argtypes = [P, P, P, P, i32]
+        L.md_tune.restype = C.c_int
+        L.md_tune.argtypes = [P, C.POINTER(C.c_int32)]
         L.md_set_profiling.restype = C.c_int
         L.md_set_profiling.argtypes = [P, i32]
         L.md_get_profile.restype = C.c_int
@@ -180,6 +182,12 @@ def md_set_state(ctx, pos=None, vel=None, force=None):
     _check(ctx, lib().md_set_state(ctx, devs[0][0], devs[1][0], devs[2][0], flags.pop() if flags else 0))
 
 
+def md_tune(ctx) -> int:
+    lanes = C.c_int32()
+    _check(ctx, lib().md_tune(ctx, C.byref(lanes)))
+    return lanes.value
+
+
 def md_set_profiling(ctx, on: bool):
     _check(ctx, lib().md_set_profiling(ctx, 1 if on else 0))
 
@@ -219,7 +227,7 @@ def make_potential(pot: _inputs.Potential):
 
 
 def make_config(n_atoms, box, skin, k_max, dt_fs, precision=MD_PREC_FP64, rebuild_every=0,
-                strict_skin=False, strain_rate_zz=0.0, stream=None):
+                strict_skin=False, strain_rate_zz=0.0, stream=None, lanes_per_atom=0):
     c = md_config()
     c.n_atoms = int(n_atoms)
     for k in range(9):
@@ -229,6 +237,7 @@ def make_config(n_atoms, box, skin, k_max, dt_fs, precision=MD_PREC_FP64, rebuil
     c.skin, c.k_max, c.rebuild_every, c.dt_fs = float(skin), int(k_max), int(rebuild_every), float(dt_fs)
     c.precision, c.strict_skin, c.strain_rate_zz = int(precision), int(bool(strict_skin)), float(strain_rate_zz)
     c.stream = C.c_void_p(stream) if stream else None
+    c.lanes_per_atom = int(lanes_per_atom)
     return c
 
 
@@ -236,12 +245,13 @@ class System:
     """One simulated system on the GPU (a context of libmd.so)."""
 
     def __init__(self, w: _inputs.Workload, precision: str = "fp64", rebuild_every: int = 0,
-                 strict_skin: bool = False, stream=None, device_inputs: bool = False, k_max=None):
+                 strict_skin: bool = False, stream=None, device_inputs: bool = False, k_max=None,
+                 lanes_per_atom: int = 0):
         prec = MD_PREC_FP64 if precision == "fp64" else MD_PREC_MIXED
         self.n = w.n_atoms
         self.k_max = int(k_max or w.k_max)
         self.config = make_config(w.n_atoms, w.box, w.skin, self.k_max, w.dt_fs, prec, rebuild_every,
-                                  strict_skin, w.strain_rate_zz, stream)
+                                  strict_skin, w.strain_rate_zz, stream, lanes_per_atom)
         pot, keep = make_potential(w.potential)
         pos = np.ascontiguousarray(w.pos, dtype=np.float64)
         vel = np.ascontiguousarray(w.vel, dtype=np.float64)
@@ -290,6 +300,9 @@ class System:
 
     def neighbours(self):
         return self.get(MD_GET_NBR_COUNT), self.get(MD_GET_NBR_LIST)
+
+    def tune(self) -> int:
+        return md_tune(self.ctx)
 
     def set_profiling(self, on: bool = True):
         md_set_profiling(self.ctx, on)

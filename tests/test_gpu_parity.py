@@ -34,13 +34,20 @@ def _rows(count, nl):
     return [tuple(sorted(nl[i, :count[i]].tolist())) for i in range(count.shape[0])]
 
 
-def _random_box(n, seed, cells=(3.3, 4.1, 5.7), rl=3.869745):
-    box = np.array(cells) * rl
-    pos = I.random_uniform(seed, 5, 3 * n).reshape(n, 3) * box
+def _ragged_box(seed):
+    """bcc Fe on a non-cubic 7 x 8 x 9 replication, 7 atoms removed (1,001 atoms: a ragged
+    tail for every block size), strong displacements and atoms unwrapped by whole boxes."""
+    pos, box = I.replicate(I.BCC_BASIS, (7, 8, 9), 2.8665)
+    pos = I.gaussian_displace(pos, 0.15, seed)
+    keep = np.ones(len(pos), bool)
+    keep[[3, 50, 111, 400, 401, 800, 1007]] = False
+    pos = pos[keep]
     pos[::4] += box * np.array([2.0, -1.0, 5.0])     # unwrapped images
+    n = len(pos)
     pot = I.fs_fe_analytic()
-    return I.Workload(name="random", pos=pos, vel=np.zeros_like(pos), species=np.zeros(n, np.int32),
-                      box=box, potential=pot, skin=0.3, k_max=64, dt_fs=1.0, steps=1, temperature=0.0)
+    vel = I.maxwell_boltzmann(pot.masses[np.zeros(n, np.int32)], 300.0, seed)
+    return I.Workload(name="ragged", pos=pos, vel=vel, species=np.zeros(n, np.int32),
+                      box=box, potential=pot, skin=0.3, k_max=48, dt_fs=1.0, steps=1, temperature=300.0)
 
 
 def _near_cutoff(seed=9):
@@ -71,7 +78,7 @@ def _workload(name):
     if name == "fec":
         return I.bcc_fe_c(10, seed=4)
     if name == "random":
-        return _random_box(1001, seed=7)
+        return _ragged_box(seed=7)
     if name == "near":
         return _near_cutoff()
     raise ValueError(name)
@@ -283,7 +290,7 @@ def test_coincident_atoms_are_reported_non_finite():
 def test_full_size_cu500k_forces_and_lists():
     """fcc Cu 50^3 = 500,000 atoms, Sutton-Chen 5,000-knot tables, in the benchmark's
     configuration: every force (FP64 and mixed) and every neighbour set against the oracle."""
-    w = I.fcc_cu(50, seed=2)
+    w = I.fcc_cu(50, seed=2, sigma=0.05)   # displaced: the perfect lattice has zero forces
     ref = oracle.forces(w.pos, w.species, w.box, w.potential, skin=w.skin, k_max=w.k_max, method="cells")
     fs = np.abs(ref["force"]).max()
     with _gpu_system(w) as s:
@@ -304,3 +311,31 @@ def test_full_size_cu500k_forces_and_lists():
         f32 = s.forces()
     assert np.abs(f32 - ref["force"]).max() <= MIXED_FORCE_TOL * fs
     assert abs(pe32 - ref["pe"]) <= MIXED_PE_TOL * abs(ref["pe"])
+
+
+# --------------------------------------------------------------------------- lanes per atom
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, 32])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_every_lane_count_matches_oracle(lanes, precision):
+    w = _workload("fec")
+    ref = oracle.forces(w.pos, w.species, w.box, w.potential, skin=w.skin, k_max=w.k_max, method="brute")
+    tol = FP64_TOL if precision == "fp64" else MIXED_FORCE_TOL
+    with _gpu_system(w, precision, lanes_per_atom=lanes) as s:
+        pe = s.eam_forces()
+        f = s.forces()
+        s.step(5)
+        e = s.energy()
+    assert np.abs(f - ref["force"]).max() <= tol * np.abs(ref["force"]).max()
+    assert abs(pe - ref["pe"]) <= (FP64_TOL if precision == "fp64" else MIXED_PE_TOL) * abs(ref["pe"])
+    assert np.isfinite(e["te"])
+
+
+def test_autotuner_picks_a_valid_lane_count_and_stays_exact():
+    w = _workload("cu2k")
+    ref = oracle.forces(w.pos, w.species, w.box, w.potential, skin=w.skin, k_max=w.k_max, method="brute")
+    with _gpu_system(w) as s:
+        lanes = s.tune()
+        assert lanes in (1, 2, 4, 8, 16, 32)
+        s.eam_forces()
+        f = s.forces()
+    assert np.abs(f - ref["force"]).max() <= FP64_TOL * np.abs(ref["force"]).max()
