@@ -162,8 +162,9 @@ __device__ __forceinline__ void kick_and_partials(double4_32a &v, double fx, dou
     }
 }
 
+// Host-side grid size of a T-lanes-per-atom launch.
 template <int T>
-__device__ __forceinline__ int blocks_for_lanes(long long n) {
+inline int blocks_for_lanes(long long n) {
     return (int)((n * T + kThreads - 1) / kThreads);
 }
 
