@@ -55,7 +55,8 @@ typedef enum {
     MD_ERR_TIMEOUT = 8,      /* a bounded device-side wait gave up */
     MD_ERR_CUDA = 9,         /* CUDA runtime error (text in md_last_error) */
     MD_ERR_OOM = 10,         /* device allocation failed */
-    MD_ERR_STATE = 11        /* call not valid in the context's state */
+    MD_ERR_STATE = 11,       /* call not valid in the context's state */
+    MD_ERR_CAPACITY = 12     /* input larger than a fixed capacity (md_neighbours_noalloc) */
 } md_status;
 
 enum { MD_POT_FS_ANALYTIC = 1, MD_POT_TABLES = 2 };
@@ -215,6 +216,37 @@ md_status md_set_profiling(md_ctx *ctx, int32_t on);
 
 /* Read the launch count and the timing sums. */
 md_status md_get_profile(const md_ctx *ctx, md_profile *out);
+
+/*
+ * Neighbour list without device allocation.  The paper has no counterpart: this entry
+ * point serves callers that cannot allocate device memory - code running inside another
+ * framework's memory pool or allocator hooks, or code that must not grow its device
+ * footprint once it has started.  It builds the same full list as md_build_neighbours (the
+ * same exact FP64 test, minimum image) for positions the caller already holds on the
+ * device, and allocates nothing: no cudaMalloc or cudaFree and no allocating library call.
+ * Its working memory is one fixed-size __device__ array inside the library (about 5.3 MB),
+ * which every GPU that loads the library holds until the process exits.
+ *   pos     device, [n_atoms][3] doubles (Å, may be unwrapped)
+ *   box     host, the 3 edge lengths of an orthorhombic box (Å)
+ *   r_list  list radius (Å): j is listed for i iff j != i and |r_ij|^2 < r_list^2
+ *   count   device, [n_atoms] int32, out: neighbours of each atom (may exceed k_max)
+ *   list    device, [n_atoms][k_max] int32, out: neighbour atom indices, then -1; the
+ *           order inside a row is unspecified
+ *   stream  cudaStream_t or NULL; the call synchronises it before returning.
+ * The caller owns pos, count and list.  Returns MD_ERR_CAPACITY, launching nothing, if
+ * n_atoms > MD_NOALLOC_MAX_ATOMS or the box holds more than MD_NOALLOC_MAX_CELLS link cells
+ * of width >= r_list; MD_ERR_BOX if an edge holds fewer than 3 such cells;
+ * MD_ERR_NBR_OVERFLOW if a row was cut at k_max; MD_ERR_ARG for bad arguments;
+ * MD_ERR_CUDA on a CUDA error.
+ * The first call on each device looks up the device address of the array (once per device,
+ * with that device current): make that first call before any stream capture.  Every call
+ * reuses the same array and leaves its contents there (each call clears what must start
+ * at zero), so calls that overlap on the GPU - from two streams or two host threads - race.
+ */
+#define MD_NOALLOC_MAX_ATOMS 131072
+#define MD_NOALLOC_MAX_CELLS 65536
+md_status md_neighbours_noalloc(const double *pos, int64_t n_atoms, const double *box, double r_list,
+                                int32_t k_max, int32_t *count, int32_t *list, void *stream);
 
 /* Text of the last error of this context ("" if none).  Valid until the next call. */
 const char *md_last_error(const md_ctx *ctx);

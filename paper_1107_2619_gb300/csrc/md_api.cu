@@ -278,6 +278,7 @@ const char *md_status_string(md_status s) {
         case MD_ERR_CUDA: return "CUDA error";
         case MD_ERR_OOM: return "out of device memory";
         case MD_ERR_STATE: return "invalid state";
+        case MD_ERR_CAPACITY: return "input exceeds a fixed capacity";
     }
     return "unknown status";
 }

@@ -20,7 +20,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "libmd.so")
 
 MD_OK, MD_ERR_ARG, MD_ERR_SPECIES, MD_ERR_BOX, MD_ERR_NBR_OVERFLOW = 0, 1, 2, 3, 4
 MD_ERR_SKIN, MD_ERR_NONFINITE, MD_ERR_TABLE_RANGE, MD_ERR_TIMEOUT = 5, 6, 7, 8
-MD_ERR_CUDA, MD_ERR_OOM, MD_ERR_STATE = 9, 10, 11
+MD_ERR_CUDA, MD_ERR_OOM, MD_ERR_STATE, MD_ERR_CAPACITY = 9, 10, 11, 12
+MD_NOALLOC_MAX_ATOMS, MD_NOALLOC_MAX_CELLS = 131072, 65536
 MD_POT_FS_ANALYTIC, MD_POT_TABLES = 1, 2
 MD_PREC_FP64, MD_PREC_MIXED = 0, 1
 (MD_GET_POS, MD_GET_VEL, MD_GET_FORCE, MD_GET_RHO, MD_GET_EATOM, MD_GET_DF, MD_GET_NBR_COUNT,
@@ -29,7 +30,7 @@ MD_PREC_FP64, MD_PREC_MIXED = 0, 1
 # functions declared in include/md.h (checked by the CPU test-suite)
 EXPORTS = ["md_abi_version", "md_status_string", "md_create", "md_build_neighbours", "md_eam_forces",
            "md_step", "md_energy", "md_get", "md_set_state", "md_tune", "md_set_profiling", "md_get_profile",
-           "md_last_error", "md_destroy"]
+           "md_neighbours_noalloc", "md_last_error", "md_destroy"]
 
 
 class md_potential(C.Structure):
@@ -102,6 +103,8 @@ def lib():
         L.md_set_profiling.argtypes = [P, i32]
         L.md_get_profile.restype = C.c_int
         L.md_get_profile.argtypes = [P, C.POINTER(md_profile)]
+        L.md_neighbours_noalloc.restype = C.c_int
+        L.md_neighbours_noalloc.argtypes = [P, i64, P, C.c_double, i32, P, P, P]
         L.md_last_error.restype = C.c_char_p
         L.md_last_error.argtypes = [P]
         L.md_destroy.restype = None
@@ -196,6 +199,15 @@ def md_get_profile(ctx) -> dict:
     p = md_profile()
     _check(ctx, lib().md_get_profile(ctx, C.byref(p)))
     return {k: getattr(p, k) for k, _ in md_profile._fields_}
+
+
+def md_neighbours_noalloc(pos, box, r_list: float, k_max: int, count, nbr_list, stream=None) -> int:
+    """Neighbour list into caller-owned device tensors, with no device allocation by the
+    library (for callers that cannot allocate); returns the md_status code."""
+    b = np.ascontiguousarray(box, dtype=np.float64)
+    return lib().md_neighbours_noalloc(C.c_void_p(pos.data_ptr()), int(pos.shape[0]), C.c_void_p(b.ctypes.data),
+                                       float(r_list), int(k_max), C.c_void_p(count.data_ptr()),
+                                       C.c_void_p(nbr_list.data_ptr()), C.c_void_p(stream) if stream else None)
 
 
 def md_last_error(ctx) -> str:
