@@ -112,8 +112,8 @@ typedef struct {
                               multiplied by (1 + rate*dt) (§2.2 strain-rate loading) */
     void *stream;          /* cudaStream_t, or NULL */
     int32_t lanes_per_atom; /* threads sharing one atom's neighbour sums in the force passes:
-                               1, 2, 4, 8, 16, 32, or 0 = chosen from the expected neighbour
-                               count (see md_tune).  Results depend on it only in rounding. */
+                               1, 2, 4 or 8, or 0 = chosen from the expected neighbour count
+                               (see md_tune).  Results depend on it only in rounding. */
     int32_t pad;
 } md_config;
 
@@ -162,6 +162,28 @@ const char *md_status_string(md_status s);
 md_status md_create(const md_config *cfg, const md_potential *pot, const double *pos,
                     const double *vel, const int32_t *species, int32_t on_device, md_ctx **out);
 
+/*
+ * Create one context for a batch of n_replicas independent systems (the paper's use of many
+ * runs for statistics, §2.6): replica r has cfgs[r].n_atoms atoms with positions pos[r],
+ * velocities vel[r] (vel or vel[r] may be NULL) and species species[r] (may be NULL), in the
+ * orthorhombic box cfgs[r].h.  The run settings (skin, k_max, dt_fs, precision,
+ * rebuild_every, strain_rate_zz) must be equal in all cfgs; stream, strict_skin and
+ * lanes_per_atom are taken from cfgs[0].  All replicas share the potential.  In the other
+ * entry points a batch behaves as one system whose atoms are the replicas' atoms in order
+ * (replica 0 first); md_step advances every replica in one launch; md_energy returns the
+ * batch totals (temperature with 3N - 3 n_replicas degrees of freedom) and
+ * md_replica_energies the values of each replica.  A list rebuild, when any replica needs
+ * one, rebuilds every replica.
+ */
+md_status md_create_batch(int32_t n_replicas, const md_config *cfgs, const md_potential *pot,
+                          const double *const *pos, const double *const *vel, const int32_t *const *species,
+                          int32_t on_device, md_ctx **out);
+
+/* Per-replica microstate values of the current state into out[n_replicas] (PE, KE, TE,
+ * T with 3n - 3 degrees of freedom, momentum, box, volume; pressure_gpa is NaN: the virial
+ * is reduced over the whole batch only).  A single system counts as one replica. */
+md_status md_replica_energies(md_ctx *ctx, md_energies *out);
+
 /* Bin the atoms into link cells (counting sort by cell, atoms renumbered in
  * cell order with a stable tie-break on atom id) and build the full Verlet list:
  * j is listed for i iff j != i and |r_ij|^2 < (r_cut + skin)^2 with the minimum
@@ -175,9 +197,24 @@ md_status md_eam_forces(md_ctx *ctx, double *pe_out);
 
 /* Advance n_steps velocity-Verlet steps (§2.3): half kick, drift, [strain],
  * [list rebuild when scheduled or when an atom moved > skin/2], density pass,
- * force pass, half kick.  Energies of the final state are then available from
+ * force pass, half kick.  All n_steps run in ONE cooperative launch of a persistent
+ * kernel (grid barriers between the phases, each wait bounded: a wait that gives up
+ * returns MD_ERR_TIMEOUT).  Energies of the final state are then available from
  * md_energy.  Synchronises the stream once, at the end. */
 md_status md_step(md_ctx *ctx, int32_t n_steps);
+
+/* Self-test of failure detection: runs one step in which one block of the persistent
+ * kernel withholds its first barrier arrival, so the other blocks' bounded wait runs out
+ * (about a millisecond of polling); every block then returns and the call reports
+ * MD_ERR_TIMEOUT with no fault.  Afterwards the state is not a clean step boundary
+ * (positions have been drifted once); the next call recomputes forces. */
+md_status md_selftest_timeout(md_ctx *ctx);
+
+/* Graph mode (on = 1): md_step(n) records its device work for this n (the persistent
+ * launch, the reduction, the copies back) as a CUDA graph the first time and replays the
+ * graph afterwards.  Not used while profiling or under a strain ramp; on = 0 frees the
+ * graphs.  md_tune or a change of link cells discards them. */
+md_status md_set_graph(md_ctx *ctx, int32_t on);
 
 /* Microstate thermodynamics of the current state (§2.1.2, §2.6), reduced in FP64
  * in a fixed order (bitwise reproducible). */
@@ -200,11 +237,11 @@ md_status md_set_state(md_ctx *ctx, const double *pos, const double *vel, const 
 md_status md_tune(md_ctx *ctx, int32_t *lanes_out);
 
 /* Kernel timing of a context (tracing).  `launches` counts every kernel the context has
- * enqueued since md_create.  While profiling is on, md_step brackets each kernel class with
- * CUDA events on the context's stream and adds their elapsed times here (ms) when the call
- * synchronises; the counts are the number of timed launches.  "rebuild" covers the skin
- * check's consequences: the binning, sort and list-build kernels of a step, which exit at
- * once when no rebuild is due. */
+ * enqueued since md_create.  While profiling is on, the step kernel stamps the GPU clock
+ * (%globaltimer) at each phase boundary and md_step adds the phase durations here (ms):
+ * kick = the first half kick + drift of each md_step call (later ones are fused into the
+ * force phase), rebuild = the list rebuild phases (0 when none is due), density and force
+ * per step; the counts are the numbers of timed phases. */
 typedef struct {
     int64_t launches;
     int64_t n_kick, n_rebuild, n_density, n_force;

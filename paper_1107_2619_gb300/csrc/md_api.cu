@@ -2,16 +2,22 @@
 //
 // Host-side orchestration of the hot path of the MOLDY method: argument checks (the paper
 // halts before the run on an unsupported species, §3.1), the potential tables, the device
-// buffers, and the order of the kernels in a velocity-Verlet step (§2.3):
-//   [box *= strain] -> half kick + drift + skin check -> [rebuild: bin, sort, list]
-//   -> density pass -> force pass + half kick (+ FP64 partial sums on the last step)
-// The host never waits inside a multi-step call; device conditions are collected in a
-// flags block and read once at the end.
+// buffers, and the launches.  A step sequence md_step(n) is ONE cooperative launch of the
+// persistent step kernel (md_step.cuh): half kick + drift + skin check, [list rebuild],
+// density pass, force pass + half kick, for n steps (§2.3), followed by the FP64 reduction
+// of the last step's energies.  The host never waits inside it; device conditions are
+// collected in a flags block and read once at the end.
+//
+// A context holds one system or a batch of independent replicas (md_create_batch): the
+// replicas' atoms are stored back to back, each replica with its own box and link cells,
+// and one launch advances all of them.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <map>
 #include <new>
 #include <string>
 #include <vector>
@@ -26,36 +32,49 @@ struct md_ctx {
     int64_t n = 0;
     int precision = MD_PREC_FP64;
     int ns = 1;
+    int n_rep = 1;
+    std::vector<int64_t> rep_off;        // [n_rep + 1] first atom of each replica
+    std::vector<double> L;               // [3 n_rep] host mirror of the device boxes
     double r_cut = 0, skin = 0, r_list = 0, rl2 = 0, lim2 = 0;
     double dt = 0, half_dt = 0, strain_scale = 1.0;
-    double L[3] = {0, 0, 0};  // host mirror of the device box
     Atoms A{};
     Cells C{};
     Pot P{};
-    Box *d_box = nullptr;
+    std::vector<RepCells> rc;            // host copy of the per-replica cell grids
+    Box *d_boxes = nullptr;
+    RepCells *d_rc = nullptr;
+    int32_t *d_rep_off = nullptr;
     Flags *d_flags = nullptr;
+    GridBarrier *d_bar = nullptr;
     double *d_reduce = nullptr;
+    double *d_rep_sums = nullptr;
+    unsigned long long *d_stamps = nullptr;
+    size_t stamps_cap = 0;
     void *d_stage = nullptr;
     size_t stage_bytes = 0;
-    Flags *h_flags = nullptr;   // pinned
-    double *h_reduce = nullptr; // pinned [kPartials]
+    Flags *h_flags = nullptr;            // pinned
+    double *h_reduce = nullptr;          // pinned [kPartials]
+    unsigned long long *h_stamps = nullptr;  // pinned
     std::vector<void *> allocs;
     int64_t step = 0;
-    int lanes = 1;              // lanes per atom of the force passes
+    int lanes = 1;
+    int part_rows = 0;                   // rows of partial sums written by the last energy pass
     bool list_valid = false, forces_valid = false, energy_valid = false;
     std::string err;
     // tracing
     int64_t launches = 0;
     bool profiling = false;
     md_profile prof{};
-    std::vector<cudaEvent_t> ev_pool;
-    size_t ev_used = 0;
+    // CUDA graphs of step sequences, keyed by the number of steps
+    bool use_graph = false;
+    std::map<int, cudaGraphExec_t> graphs;
+    std::map<int, int> graph_rows;
 };
 
 namespace {
 
-// Kernels enqueued by one launch_rebuild (kept in step with md_neighbour.cu).
-constexpr int kRebuildLaunches = 9;
+constexpr int kRebuildLaunches = 9;                     // kernels of one stand-alone launch_rebuild
+constexpr unsigned long long kSpinLimit = 20000000ull;  // barrier polls (~2 s) before giving up
 
 md_status fail(md_ctx *c, md_status s, const std::string &what, cudaError_t e = cudaSuccess) {
     if (c) {
@@ -91,13 +110,14 @@ float ulp32(double x) {
     return (float)std::ldexp(1.0, e - 24);
 }
 
-// FP32 screening band of the list build (see k_build_list).  Each wrapped FP32 coordinate is
+// FP32 screening band of the list build (ph::build_row).  Each wrapped FP32 coordinate is
 // within u/2 of its FP64 value (u = ulp32 of the largest box edge); the FP32 difference and
 // the minimum-image shift add at most 1.5u + ulp32(r_list)/2 more, so each component of d is
 // within delta = 2u + ulp32(r_list)/2 of the FP64 one.  Then |r2_32 - r2_64| <= 2 sqrt(3) r_list
 // delta + 3 delta^2 plus the FP32 rounding of r^2 (< 6e-7 r_list^2).  The band is 4x that.
 void list_band(const md_ctx *c, float &lo, float &hi) {
-    double Lmax = std::fmax(c->L[0], std::fmax(c->L[1], c->L[2]));
+    double Lmax = 0.0;
+    for (double l : c->L) Lmax = std::fmax(Lmax, l);
     double u = ulp32(Lmax);
     double delta = 2.0 * u + 0.5 * ulp32(c->r_list);
     double bound = 2.0 * std::sqrt(3.0) * c->r_list * delta + 3.0 * delta * delta + 6e-7 * c->rl2;
@@ -112,7 +132,7 @@ int cells_along(double L, double r_list) {
     return nc;
 }
 
-Box make_box(const double L[3]) {
+Box make_box(const double *L) {
     Box b;
     for (int k = 0; k < 3; k++) {
         b.L[k] = L[k];
@@ -133,7 +153,7 @@ void cubic_rows(const double *tab, int nk, double h, double4_32a *out64) {
         if (k < nk - 1) {
             double s0 = h * yp[k], s1 = h * yp[k + 1];
             c = make_double4_32a(y[k], s0, 3.0 * (y[k + 1] - y[k]) - 2.0 * s0 - s1,
-                             2.0 * (y[k] - y[k + 1]) + s0 + s1);
+                                 2.0 * (y[k] - y[k + 1]) + s0 + s1);
         } else {
             c = make_double4_32a(y[k], h * yp[k], 0.0, 0.0);
         }
@@ -145,6 +165,10 @@ md_status sync_and_check(md_ctx *ctx, bool strict_skin) {
     MD_CK(cudaMemcpyAsync(ctx->h_flags, ctx->d_flags, sizeof(Flags), cudaMemcpyDeviceToHost, ctx->stream));
     MD_CK(cudaStreamSynchronize(ctx->stream));
     const Flags &f = *ctx->h_flags;
+    if (f.error & FLAG_TIMEOUT) {
+        ctx->forces_valid = ctx->energy_valid = false;
+        return fail(ctx, MD_ERR_TIMEOUT, "a grid barrier of the step kernel gave up waiting");
+    }
     if (f.error & FLAG_OVERFLOW) {
         ctx->list_valid = false;
         return fail(ctx, MD_ERR_NBR_OVERFLOW,
@@ -170,8 +194,8 @@ cudaError_t enqueue_rebuild(md_ctx *ctx) {
     return launch_rebuild(ctx->A, ctx->C, ctx->rl2, lo, hi, ctx->stream);
 }
 
-// Pass 1 + pass 2 at the current positions (rebuilding first if needed), with the FP64
-// partial sums; enqueue only.
+// Pass 1 + pass 2 at the current positions with stand-alone kernels (rebuilding first if
+// needed), with the FP64 partial sums; enqueue only.
 cudaError_t enqueue_forces(md_ctx *ctx) {
     ctx->launches += 4 + kRebuildLaunches + (ctx->list_valid ? 0 : 1);
     cudaError_t e = launch_check_displacement(ctx->A, ctx->lim2, ctx->stream);
@@ -180,11 +204,11 @@ cudaError_t enqueue_forces(md_ctx *ctx) {
     if (e == cudaSuccess) e = launch_density(ctx->A, ctx->P, ctx->precision, ctx->lanes, ctx->stream);
     if (e == cudaSuccess)
         e = launch_force(ctx->A, ctx->P, ctx->precision, ctx->lanes, false, true, 0.0, ctx->stream);
+    ctx->part_rows = partial_blocks((int)ctx->n, ctx->lanes);
+    if (e == cudaSuccess) e = launch_reduce(ctx->A, ctx->part_rows, ctx->d_reduce, ctx->stream);
     if (e == cudaSuccess)
-        e = launch_reduce(ctx->A, partial_blocks(ctx->A.n, ctx->lanes), ctx->d_reduce, ctx->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(ctx->h_reduce, ctx->d_reduce, sizeof(double) * kPartials,
-                            cudaMemcpyDeviceToHost, ctx->stream);
+        e = cudaMemcpyAsync(ctx->h_reduce, ctx->d_reduce, sizeof(double) * kPartials, cudaMemcpyDeviceToHost,
+                            ctx->stream);
     return e;
 }
 
@@ -197,50 +221,9 @@ md_status compute_forces(md_ctx *ctx) {
     return MD_OK;
 }
 
-cudaEvent_t next_event(md_ctx *ctx) {
-    if (ctx->ev_used == ctx->ev_pool.size()) {
-        cudaEvent_t e;
-        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
-        ctx->ev_pool.push_back(e);
-    }
-    return ctx->ev_pool[ctx->ev_used++];
-}
-
-// Record a profiling mark on the stream (no-op when profiling is off).
-cudaError_t mark(md_ctx *ctx) {
-    if (!ctx->profiling) return cudaSuccess;
-    cudaEvent_t e = next_event(ctx);
-    if (!e) return cudaErrorMemoryAllocation;
-    return cudaEventRecord(e, ctx->stream);
-}
-
-// After a synchronisation: fold the marks of a step sequence (5 per step:
-// start, after kick, after rebuild, after density, after force) into the sums.
-void collect_marks(md_ctx *ctx) {
-    if (!ctx->profiling) {
-        ctx->ev_used = 0;
-        return;
-    }
-    for (size_t b = 0; b + 4 < ctx->ev_used; b += 5) {
-        float t[4];
-        for (int k = 0; k < 4; k++) cudaEventElapsedTime(&t[k], ctx->ev_pool[b + k], ctx->ev_pool[b + k + 1]);
-        ctx->prof.ms_kick += t[0];
-        ctx->prof.ms_rebuild += t[1];
-        ctx->prof.ms_density += t[2];
-        ctx->prof.ms_force += t[3];
-        ctx->prof.n_kick++;
-        ctx->prof.n_rebuild++;
-        ctx->prof.n_density++;
-        ctx->prof.n_force++;
-    }
-    ctx->ev_used = 0;
-}
-
 md_status ensure_stage(md_ctx *ctx, size_t bytes) {
     if (ctx->stage_bytes >= bytes) return MD_OK;
     if (ctx->d_stage) {
-        for (auto &p : ctx->allocs)
-            if (p == ctx->d_stage) p = nullptr;
         cudaFree(ctx->d_stage);
         ctx->d_stage = nullptr;
         ctx->stage_bytes = 0;
@@ -251,6 +234,19 @@ md_status ensure_stage(md_ctx *ctx, size_t bytes) {
     return MD_OK;
 }
 
+md_status ensure_stamps(md_ctx *ctx, size_t count) {
+    if (ctx->stamps_cap >= count) return MD_OK;
+    if (ctx->d_stamps) cudaFree(ctx->d_stamps);
+    if (ctx->h_stamps) cudaFreeHost(ctx->h_stamps);
+    ctx->d_stamps = nullptr;
+    ctx->h_stamps = nullptr;
+    ctx->stamps_cap = 0;
+    MD_CK(cudaMalloc(&ctx->d_stamps, count * sizeof(unsigned long long)));
+    MD_CK(cudaMallocHost(&ctx->h_stamps, count * sizeof(unsigned long long)));
+    ctx->stamps_cap = count;
+    return MD_OK;
+}
+
 md_status copy_out(md_ctx *ctx, const void *src, void *dst, size_t bytes, int on_device) {
     MD_CK(cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                           ctx->stream));
@@ -258,89 +254,102 @@ md_status copy_out(md_ctx *ctx, const void *src, void *dst, size_t bytes, int on
     return MD_OK;
 }
 
-}  // namespace
+StepParams step_params(md_ctx *ctx, int n_steps) {
+    StepParams sp{};
+    sp.n_steps = n_steps;
+    sp.energy_last = 1;
+    sp.half_dt = ctx->half_dt;
+    sp.dt = ctx->dt;
+    sp.strain_scale = ctx->strain_scale;
+    sp.lim2 = ctx->lim2;
+    sp.rebuild_every = ctx->cfg.rebuild_every;
+    sp.rl2 = ctx->rl2;
+    list_band(ctx, sp.band_lo, sp.band_hi);
+    sp.spin_limit = kSpinLimit;
+    return sp;
+}
 
-extern "C" {
+// The work of md_step(n) after any initial force evaluation: the persistent launch, the
+// energy reduction and the copies back.  `rows` receives the partial-sum rows written.
+cudaError_t enqueue_steps(md_ctx *ctx, int n_steps, unsigned long long *stamps, int *rows) {
+    const StepParams sp = step_params(ctx, n_steps);
+    cudaError_t e = reset_errors(ctx);
+    int grid = 0;
+    if (e == cudaSuccess)
+        e = launch_step(ctx->A, ctx->C, ctx->P, ctx->precision, ctx->lanes, sp, ctx->d_bar, stamps, &grid,
+                        ctx->stream);
+    if (e == cudaSuccess) e = launch_reduce(ctx->A, grid, ctx->d_reduce, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->h_reduce, ctx->d_reduce, sizeof(double) * kPartials, cudaMemcpyDeviceToHost,
+                            ctx->stream);
+    *rows = grid;
+    return e;
+}
 
-int32_t md_abi_version(void) { return MD_ABI_VERSION; }
-
-const char *md_status_string(md_status s) {
-    switch (s) {
-        case MD_OK: return "ok";
-        case MD_ERR_ARG: return "invalid argument";
-        case MD_ERR_SPECIES: return "unsupported species";
-        case MD_ERR_BOX: return "invalid box";
-        case MD_ERR_NBR_OVERFLOW: return "neighbour list overflow";
-        case MD_ERR_SKIN: return "skin exceeded";
-        case MD_ERR_NONFINITE: return "non-finite value";
-        case MD_ERR_TABLE_RANGE: return "table range";
-        case MD_ERR_TIMEOUT: return "device wait timed out";
-        case MD_ERR_CUDA: return "CUDA error";
-        case MD_ERR_OOM: return "out of device memory";
-        case MD_ERR_STATE: return "invalid state";
-        case MD_ERR_CAPACITY: return "input exceeds a fixed capacity";
+// Fold the %globaltimer stamps of one launch into the profile: per step, [start, after
+// rebuild, after density, after force]; row 0 = [launch start]; the first kick ends where
+// step 0 starts.
+void collect_stamps(md_ctx *ctx, int n_steps) {
+    const unsigned long long *t = ctx->h_stamps;
+    ctx->prof.ms_kick += (t[4] - t[0]) * 1e-6;
+    ctx->prof.n_kick += 1;
+    for (int s = 1; s <= n_steps; s++) {
+        const unsigned long long *r = t + 4 * s;
+        ctx->prof.ms_rebuild += (r[1] - r[0]) * 1e-6;
+        ctx->prof.ms_density += (r[2] - r[1]) * 1e-6;
+        ctx->prof.ms_force += (r[3] - r[2]) * 1e-6;
     }
-    return "unknown status";
+    ctx->prof.n_rebuild += n_steps;
+    ctx->prof.n_density += n_steps;
+    ctx->prof.n_force += n_steps;
 }
 
-const char *md_last_error(const md_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
-
-void md_destroy(md_ctx *ctx) {
-    if (!ctx) return;
-    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-    else cudaDeviceSynchronize();
-    for (void *p : ctx->allocs)
-        if (p) cudaFree(p);
-    if (ctx->d_stage) cudaFree(ctx->d_stage);
-    if (ctx->h_flags) cudaFreeHost(ctx->h_flags);
-    if (ctx->h_reduce) cudaFreeHost(ctx->h_reduce);
-    for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
-    delete ctx;
+void drop_graphs(md_ctx *ctx) {
+    for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.second);
+    ctx->graphs.clear();
+    ctx->graph_rows.clear();
 }
 
-md_status md_create(const md_config *cfg, const md_potential *pot, const double *pos, const double *vel,
-                    const int32_t *species, int32_t on_device, md_ctx **out) {
-    if (!out) return MD_ERR_ARG;
-    *out = nullptr;
-    if (!cfg || !pot || (!pos && cfg->n_atoms > 0)) return MD_ERR_ARG;
-    md_ctx *ctx = new (std::nothrow) md_ctx();
-    if (!ctx) return MD_ERR_OOM;
-    auto bail = [&](md_status s) {
-        std::string keep = ctx->err;
-        md_destroy(ctx);
-        (void)keep;
-        return s;
-    };
+// --------------------------------------------------------------------------- creation
+struct Inputs {
+    std::vector<double> pos, vel;
+    std::vector<int32_t> spec;
+};
+
+md_status create_common(md_ctx *ctx, const md_config *cfg, const md_potential *pot, const Inputs &in,
+                        const std::vector<int64_t> &rep_n, const std::vector<double> &L) {
+    const int n_rep = (int)rep_n.size();
+    int64_t n = 0;
+    ctx->rep_off.assign(n_rep + 1, 0);
+    for (int r = 0; r < n_rep; r++) {
+        ctx->rep_off[r + 1] = ctx->rep_off[r] + rep_n[r];
+        n += rep_n[r];
+    }
     ctx->cfg = *cfg;
     ctx->stream = static_cast<cudaStream_t>(cfg->stream);
-    const int64_t n = cfg->n_atoms;
-    if (n < 0 || n > INT32_MAX / 2) return bail(MD_ERR_ARG);
-    if (cfg->k_max < 1 || cfg->skin < 0.0 || !(cfg->dt_fs >= 0.0) || cfg->rebuild_every < 0)
-        return bail(MD_ERR_ARG);
-    if (cfg->precision != MD_PREC_FP64 && cfg->precision != MD_PREC_MIXED) return bail(MD_ERR_ARG);
-    for (int a = 0; a < 3; a++)
-        for (int b = 0; b < 3; b++)
-            if (a != b && cfg->h[3 * a + b] != 0.0) return bail(MD_ERR_BOX);
-    for (int k = 0; k < 3; k++) {
-        ctx->L[k] = cfg->h[4 * k];
-        if (!(ctx->L[k] > 0.0)) return bail(MD_ERR_BOX);
-    }
+    ctx->n_rep = n_rep;
+    ctx->L = L;
+    if (n < 0 || n > INT32_MAX / 8) return MD_ERR_ARG;
+    if (cfg->k_max < 1 || cfg->skin < 0.0 || !(cfg->dt_fs >= 0.0) || cfg->rebuild_every < 0) return MD_ERR_ARG;
+    if (cfg->precision != MD_PREC_FP64 && cfg->precision != MD_PREC_MIXED) return MD_ERR_ARG;
+    for (double l : L)
+        if (!(l > 0.0)) return MD_ERR_BOX;
     // potential (§3.1)
-    int ns = pot->n_species;
+    const int ns = pot->n_species;
     if (pot->kind == MD_POT_FS_ANALYTIC) {
-        if (ns != 1 || !(pot->r_cut > 0.0) || pot->fs[0] <= 0.0) return bail(MD_ERR_ARG);
+        if (ns != 1 || !(pot->r_cut > 0.0) || pot->fs[0] <= 0.0) return MD_ERR_ARG;
     } else if (pot->kind == MD_POT_TABLES) {
         if (ns < 1 || ns > 8 || pot->n_knots < 2 || !pot->tables || !(pot->r_cut > pot->r_min) ||
             !(pot->rho_max > pot->rho_min))
-            return bail(MD_ERR_ARG);
+            return MD_ERR_ARG;
     } else {
-        return bail(MD_ERR_ARG);
+        return MD_ERR_ARG;
     }
-    if (!pot->masses_amu) return bail(MD_ERR_ARG);
+    if (!pot->masses_amu) return MD_ERR_ARG;
     std::vector<double> mass(ns);
     for (int a = 0; a < ns; a++) {
         mass[a] = pot->masses_amu[a];
-        if (!(mass[a] > 0.0)) return bail(MD_ERR_ARG);
+        if (!(mass[a] > 0.0)) return MD_ERR_ARG;
     }
     ctx->ns = ns;
     ctx->n = n;
@@ -353,65 +362,63 @@ md_status md_create(const md_config *cfg, const md_potential *pot, const double 
     ctx->dt = cfg->dt_fs;
     ctx->half_dt = 0.5 * cfg->dt_fs;
     ctx->strain_scale = 1.0 + cfg->strain_rate_zz * cfg->dt_fs * 1.0e-15;
-    for (int k = 0; k < 3; k++) {
-        ctx->C.nc[k] = cells_along(ctx->L[k], ctx->r_list);
-        if (ctx->C.nc[k] < 3) {
-            ctx->err = "box edge holds fewer than 3 link cells of width r_cut + skin";
-            return bail(MD_ERR_BOX);
+    // link cells of each replica (fixed in fractional coordinates, >= r_list wide, >= 3 per edge)
+    ctx->rc.resize(n_rep);
+    long long ncell = 0;
+    for (int r = 0; r < n_rep; r++) {
+        for (int k = 0; k < 3; k++) {
+            ctx->rc[r].nc[k] = cells_along(L[3 * r + k], ctx->r_list);
+            if (ctx->rc[r].nc[k] < 3) {
+                ctx->err = "a box edge holds fewer than 3 link cells of width r_cut + skin";
+                return MD_ERR_BOX;
+            }
         }
+        ctx->rc[r].base = (int)ncell;
+        ncell += (long long)ctx->rc[r].nc[0] * ctx->rc[r].nc[1] * ctx->rc[r].nc[2];
+        if (ncell > INT32_MAX / 2) return MD_ERR_BOX;
     }
     // lanes per atom: given, or from the expected neighbour count (4/3 pi r_list^3 x density)
     {
         const int want = cfg->lanes_per_atom;
-        if (want != 0 && (want < 1 || want > 32 || (want & (want - 1)) != 0)) return bail(MD_ERR_ARG);
+        if (want != 0 && want != 1 && want != 2 && want != 4 && want != 8) return MD_ERR_ARG;
         if (want) {
             ctx->lanes = want;
         } else {
-            const double vol = ctx->L[0] * ctx->L[1] * ctx->L[2];
+            double vol = 0.0;
+            for (int r = 0; r < n_rep; r++) vol += L[3 * r] * L[3 * r + 1] * L[3 * r + 2];
             const double k_est = 4.18879020478639 * ctx->r_list * ctx->r_list * ctx->r_list * (double)n / vol;
             int t = 1;
-            while (t < 32 && t * 12 < k_est) t *= 2;
+            while (t < 8 && t * 12 < k_est) t *= 2;
             ctx->lanes = t;
         }
     }
-    // host copies of the inputs
-    std::vector<double> hpos(3 * n), hvel(3 * n, 0.0);
-    std::vector<int32_t> hspec(n, 0);
-    if (n > 0) {
-        auto fetch = [&](void *dst, const void *src, size_t bytes) {
-            if (!on_device) {
-                std::memcpy(dst, src, bytes);
-                return true;
-            }
-            return cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost) == cudaSuccess;
-        };
-        if (!fetch(hpos.data(), pos, sizeof(double) * 3 * n)) return bail(MD_ERR_CUDA);
-        if (vel && !fetch(hvel.data(), vel, sizeof(double) * 3 * n)) return bail(MD_ERR_CUDA);
-        if (species && !fetch(hspec.data(), species, sizeof(int32_t) * n)) return bail(MD_ERR_CUDA);
-    }
     for (int64_t i = 0; i < n; i++) {
-        if (hspec[i] < 0 || hspec[i] >= ns) {
-            ctx->err = "atom " + std::to_string(i) + " has species " + std::to_string(hspec[i]) +
+        if (in.spec[i] < 0 || in.spec[i] >= ns) {
+            ctx->err = "atom " + std::to_string(i) + " has species " + std::to_string(in.spec[i]) +
                        " not supported by the potential";
-            return bail(MD_ERR_SPECIES);
+            return MD_ERR_SPECIES;
         }
         for (int c = 0; c < 3; c++)
-            if (!std::isfinite(hpos[3 * i + c]) || !std::isfinite(hvel[3 * i + c])) return bail(MD_ERR_NONFINITE);
+            if (!std::isfinite(in.pos[3 * i + c]) || !std::isfinite(in.vel[3 * i + c])) return MD_ERR_NONFINITE;
     }
     const double acc = 1.0 / kMvv2e;  // (eV/Å)/amu -> Å/fs^2
     std::vector<double4_32a> p4(n), v4(n), f4(n);
-    std::vector<int32_t> iota(n);
+    std::vector<int32_t> iota(n), rep(n_rep > 1 ? n : 0);
+    if (n_rep > 1)
+        for (int r = 0; r < n_rep; r++)
+            for (int64_t i = ctx->rep_off[r]; i < ctx->rep_off[r + 1]; i++) rep[i] = r;
     for (int64_t i = 0; i < n; i++) {
-        double m = mass[hspec[i]];
-        p4[i] = make_double4_32a(hpos[3 * i], hpos[3 * i + 1], hpos[3 * i + 2], (double)hspec[i]);
-        v4[i] = make_double4_32a(hvel[3 * i], hvel[3 * i + 1], hvel[3 * i + 2], acc / m);
-        f4[i] = make_double4_32a(0.0, 0.0, 0.0, m);
+        const double m = mass[in.spec[i]];
+        p4[i] = make_double4_32a(in.pos[3 * i], in.pos[3 * i + 1], in.pos[3 * i + 2], (double)in.spec[i]);
+        v4[i] = make_double4_32a(in.vel[3 * i], in.vel[3 * i + 1], in.vel[3 * i + 2], acc / m);
+        f4[i] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
         iota[i] = (int32_t)i;
     }
     // device buffers
     Atoms &A = ctx->A;
     A.n = (int)n;
     A.k_max = cfg->k_max;
+    A.n_rep = n_rep;
     cudaError_t e = cudaSuccess;
     auto chk = [&](cudaError_t r) { if (r != cudaSuccess && e == cudaSuccess) e = r; };
     chk(dalloc(ctx, &A.pos, n)); chk(dalloc(ctx, &A.vel, n)); chk(dalloc(ctx, &A.force, n));
@@ -423,23 +430,31 @@ md_status md_create(const md_config *cfg, const md_potential *pot, const double 
     chk(dalloc(ctx, &A.spec, n)); chk(dalloc(ctx, &A.spec_tmp, n)); chk(dalloc(ctx, &A.cell_of, n));
     chk(dalloc(ctx, &A.slot, n)); chk(dalloc(ctx, &A.order, n)); chk(dalloc(ctx, &A.count, n));
     chk(dalloc(ctx, &A.nbr, (size_t)n * cfg->k_max));
-    const int nblocks = n > 0 ? partial_blocks((int)n, 32) : 1;  // enough rows for any lane count
-    chk(dalloc(ctx, &A.partials, (size_t)nblocks * kPartials));
-    chk(dalloc(ctx, &ctx->d_box, 1));
+    if (n_rep > 1) chk(dalloc(ctx, &A.rep, n));
+    // partial-sum rows: a stand-alone force launch (<= 8 lanes) or a persistent grid
+    const int rows = std::max(partial_blocks((int)n, 8), 8192);
+    A.part_stride = rows;
+    chk(dalloc(ctx, &A.partials, (size_t)rows * kPartials));
+    chk(dalloc(ctx, &ctx->d_boxes, n_rep));
+    chk(dalloc(ctx, &ctx->d_rc, n_rep));
+    chk(dalloc(ctx, &ctx->d_rep_off, n_rep + 1));
+    chk(dalloc(ctx, &ctx->d_rep_sums, (size_t)n_rep * 5));
     chk(dalloc(ctx, &ctx->d_flags, 1));
+    chk(dalloc(ctx, &ctx->d_bar, 1));
     chk(dalloc(ctx, &ctx->d_reduce, kPartials));
     Cells &C = ctx->C;
-    C.ncell = C.nc[0] * C.nc[1] * C.nc[2];
-    C.ntiles = (C.ncell + 4095) / 4096;
+    C.ncell = (int)ncell;
+    C.ntiles = (C.ncell + 511) / 512;   // tiles of the persistent kernel's scan (128 x 4 cells)
+    C.rc = ctx->d_rc;
     chk(dalloc(ctx, &C.cell_count, C.ncell));
     chk(dalloc(ctx, &C.cell_start, C.ncell + 1));
-    chk(dalloc(ctx, &C.tile_sums, C.ntiles));
-    if (e != cudaSuccess) return bail(fail(ctx, MD_ERR_OOM, "device allocation", e));
-    A.box = ctx->d_box;
+    chk(dalloc(ctx, &C.tile_sums, C.ntiles + 1));
+    if (e != cudaSuccess) return fail(ctx, MD_ERR_OOM, "device allocation", e);
+    A.boxes = ctx->d_boxes;
     A.flags = ctx->d_flags;
     if (cudaMallocHost(&ctx->h_flags, sizeof(Flags)) != cudaSuccess ||
         cudaMallocHost(&ctx->h_reduce, sizeof(double) * kPartials) != cudaSuccess)
-        return bail(MD_ERR_OOM);
+        return MD_ERR_OOM;
     std::memset(ctx->h_flags, 0, sizeof(Flags));
     std::memset(ctx->h_reduce, 0, sizeof(double) * kPartials);
     // potential tables
@@ -478,7 +493,7 @@ md_status md_create(const md_config *cfg, const md_potential *pot, const double 
                 for (size_t q = 0; q < tl; q++)
                     if (tv[q] != tvt[q]) {
                         ctx->err = "V table must be symmetric in its two species";
-                        return bail(MD_ERR_ARG);
+                        return MD_ERR_ARG;
                     }
                 cubic_rows(tv, nk, hr, rv.data());
                 cubic_rows(pot->tables + (npair + a * ns + b) * tl, nk, hr, rp.data());
@@ -497,7 +512,7 @@ md_status md_create(const md_config *cfg, const md_potential *pot, const double 
         chk(dalloc(ctx, &dVP64, VP64.size()));
         chk(dalloc(ctx, &dVP32, VP32.size() / 8));
         chk(dalloc(ctx, &dF64, F64.size()));
-        if (e != cudaSuccess) return bail(fail(ctx, MD_ERR_OOM, "table allocation", e));
+        if (e != cudaSuccess) return fail(ctx, MD_ERR_OOM, "table allocation", e);
         chk(cudaMemcpy(dVP64, VP64.data(), VP64.size() * sizeof(double4_32a), cudaMemcpyHostToDevice));
         chk(cudaMemcpy(dVP32, VP32.data(), VP32.size() * sizeof(float), cudaMemcpyHostToDevice));
         chk(cudaMemcpy(dF64, F64.data(), F64.size() * sizeof(double4_32a), cudaMemcpyHostToDevice));
@@ -506,7 +521,10 @@ md_status md_create(const md_config *cfg, const md_potential *pot, const double 
         P.F64 = dF64;
     }
     // initial state (caller order = cell order until the first build)
-    Box box = make_box(ctx->L);
+    std::vector<Box> boxes(n_rep);
+    for (int r = 0; r < n_rep; r++) boxes[r] = make_box(&L[3 * r]);
+    std::vector<int32_t> off32(n_rep + 1);
+    for (int r = 0; r <= n_rep; r++) off32[r] = (int32_t)ctx->rep_off[r];
     Flags flags{};
     flags.need_rebuild = 1;
     if (n > 0) {
@@ -516,16 +534,149 @@ md_status md_create(const md_config *cfg, const md_potential *pot, const double 
         chk(cudaMemcpy(A.force, f4.data(), n * sizeof(double4_32a), cudaMemcpyHostToDevice));
         chk(cudaMemcpy(A.id, iota.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice));
         chk(cudaMemcpy(A.rank, iota.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice));
-        chk(cudaMemcpy(A.spec, hspec.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice));
+        chk(cudaMemcpy(A.spec, in.spec.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice));
+        if (n_rep > 1) chk(cudaMemcpy(A.rep, rep.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice));
     }
-    chk(cudaMemcpy(ctx->d_box, &box, sizeof(Box), cudaMemcpyHostToDevice));
+    chk(cudaMemcpy(ctx->d_boxes, boxes.data(), n_rep * sizeof(Box), cudaMemcpyHostToDevice));
+    chk(cudaMemcpy(ctx->d_rc, ctx->rc.data(), n_rep * sizeof(RepCells), cudaMemcpyHostToDevice));
+    chk(cudaMemcpy(ctx->d_rep_off, off32.data(), (n_rep + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
     chk(cudaMemcpy(ctx->d_flags, &flags, sizeof(Flags), cudaMemcpyHostToDevice));
     chk(cudaMemset(C.cell_count, 0, sizeof(int32_t) * C.ncell));
-    chk(cudaMemset(A.partials, 0, sizeof(double) * nblocks * kPartials));
+    chk(cudaMemset(A.partials, 0, sizeof(double) * rows * kPartials));
     chk(cudaDeviceSynchronize());
     chk(launch_wrap(A, ctx->stream));
     chk(cudaStreamSynchronize(ctx->stream));
-    if (e != cudaSuccess) return bail(fail(ctx, MD_ERR_CUDA, "initial upload", e));
+    if (e != cudaSuccess) return fail(ctx, MD_ERR_CUDA, "initial upload", e);
+    return MD_OK;
+}
+
+bool fetch(void *dst, const void *src, size_t bytes, int on_device) {
+    if (bytes == 0) return true;
+    if (!on_device) {
+        std::memcpy(dst, src, bytes);
+        return true;
+    }
+    return cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost) == cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t md_abi_version(void) { return MD_ABI_VERSION; }
+
+const char *md_status_string(md_status s) {
+    switch (s) {
+        case MD_OK: return "ok";
+        case MD_ERR_ARG: return "invalid argument";
+        case MD_ERR_SPECIES: return "unsupported species";
+        case MD_ERR_BOX: return "invalid box";
+        case MD_ERR_NBR_OVERFLOW: return "neighbour list overflow";
+        case MD_ERR_SKIN: return "skin exceeded";
+        case MD_ERR_NONFINITE: return "non-finite value";
+        case MD_ERR_TABLE_RANGE: return "table range";
+        case MD_ERR_TIMEOUT: return "device wait timed out";
+        case MD_ERR_CUDA: return "CUDA error";
+        case MD_ERR_OOM: return "out of device memory";
+        case MD_ERR_STATE: return "invalid state";
+        case MD_ERR_CAPACITY: return "input exceeds a fixed capacity";
+    }
+    return "unknown status";
+}
+
+const char *md_last_error(const md_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+void md_destroy(md_ctx *ctx) {
+    if (!ctx) return;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    else cudaDeviceSynchronize();
+    drop_graphs(ctx);
+    for (void *p : ctx->allocs)
+        if (p) cudaFree(p);
+    if (ctx->d_stage) cudaFree(ctx->d_stage);
+    if (ctx->d_stamps) cudaFree(ctx->d_stamps);
+    if (ctx->h_flags) cudaFreeHost(ctx->h_flags);
+    if (ctx->h_reduce) cudaFreeHost(ctx->h_reduce);
+    if (ctx->h_stamps) cudaFreeHost(ctx->h_stamps);
+    delete ctx;
+}
+
+md_status md_create(const md_config *cfg, const md_potential *pot, const double *pos, const double *vel,
+                    const int32_t *species, int32_t on_device, md_ctx **out) {
+    if (!out) return MD_ERR_ARG;
+    *out = nullptr;
+    if (!cfg || !pot || (!pos && cfg->n_atoms > 0) || cfg->n_atoms < 0) return MD_ERR_ARG;
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++)
+            if (a != b && cfg->h[3 * a + b] != 0.0) return MD_ERR_BOX;
+    const int64_t n = cfg->n_atoms;
+    if (n > INT32_MAX / 8) return MD_ERR_ARG;
+    Inputs in;
+    in.pos.assign(3 * n, 0.0);
+    in.vel.assign(3 * n, 0.0);
+    in.spec.assign(n, 0);
+    if (!fetch(in.pos.data(), pos, sizeof(double) * 3 * n, on_device) ||
+        (vel && !fetch(in.vel.data(), vel, sizeof(double) * 3 * n, on_device)) ||
+        (species && !fetch(in.spec.data(), species, sizeof(int32_t) * n, on_device)))
+        return MD_ERR_CUDA;
+    md_ctx *ctx = new (std::nothrow) md_ctx();
+    if (!ctx) return MD_ERR_OOM;
+    std::vector<double> L = {cfg->h[0], cfg->h[4], cfg->h[8]};
+    md_status s = create_common(ctx, cfg, pot, in, {n}, L);
+    if (s != MD_OK) {
+        md_destroy(ctx);
+        return s;
+    }
+    *out = ctx;
+    return MD_OK;
+}
+
+md_status md_create_batch(int32_t n_replicas, const md_config *cfgs, const md_potential *pot,
+                          const double *const *pos, const double *const *vel, const int32_t *const *species,
+                          int32_t on_device, md_ctx **out) {
+    if (!out) return MD_ERR_ARG;
+    *out = nullptr;
+    if (n_replicas < 1 || !cfgs || !pot || !pos) return MD_ERR_ARG;
+    const md_config &c0 = cfgs[0];
+    std::vector<int64_t> rep_n(n_replicas);
+    std::vector<double> L(3 * (size_t)n_replicas);
+    int64_t n = 0;
+    for (int r = 0; r < n_replicas; r++) {
+        const md_config &c = cfgs[r];
+        if (c.n_atoms < 0 || (!pos[r] && c.n_atoms > 0)) return MD_ERR_ARG;
+        if (c.skin != c0.skin || c.k_max != c0.k_max || c.dt_fs != c0.dt_fs || c.precision != c0.precision ||
+            c.rebuild_every != c0.rebuild_every || c.strain_rate_zz != c0.strain_rate_zz)
+            return MD_ERR_ARG;
+        for (int a = 0; a < 3; a++)
+            for (int b = 0; b < 3; b++)
+                if (a != b && c.h[3 * a + b] != 0.0) return MD_ERR_BOX;
+        for (int k = 0; k < 3; k++) L[3 * r + k] = c.h[4 * k];
+        rep_n[r] = c.n_atoms;
+        n += c.n_atoms;
+    }
+    if (n > INT32_MAX / 8) return MD_ERR_ARG;
+    Inputs in;
+    in.pos.assign(3 * n, 0.0);
+    in.vel.assign(3 * n, 0.0);
+    in.spec.assign(n, 0);
+    int64_t off = 0;
+    for (int r = 0; r < n_replicas; r++) {
+        const int64_t m = rep_n[r];
+        if (!fetch(&in.pos[3 * off], pos[r], sizeof(double) * 3 * m, on_device) ||
+            (vel && vel[r] && !fetch(&in.vel[3 * off], vel[r], sizeof(double) * 3 * m, on_device)) ||
+            (species && species[r] && !fetch(&in.spec[off], species[r], sizeof(int32_t) * m, on_device)))
+            return MD_ERR_CUDA;
+        off += m;
+    }
+    md_ctx *ctx = new (std::nothrow) md_ctx();
+    if (!ctx) return MD_ERR_OOM;
+    md_config cfg = c0;
+    cfg.n_atoms = n;
+    md_status s = create_common(ctx, &cfg, pot, in, rep_n, L);
+    if (s != MD_OK) {
+        md_destroy(ctx);
+        return s;
+    }
     *out = ctx;
     return MD_OK;
 }
@@ -557,54 +708,76 @@ md_status md_step(md_ctx *ctx, int32_t n_steps) {
     if (n_steps == 0) return MD_OK;
     // link cells are fixed in fractional coordinates; under compression keep them >= r_list wide
     if (ctx->strain_scale != 1.0) {
-        double Lz = ctx->L[2];
-        for (int32_t s = 0; s < n_steps; s++) Lz *= ctx->strain_scale;
-        int nc = cells_along(std::fmin(Lz, ctx->L[2]), ctx->r_list);
-        if (nc < 3) return fail(ctx, MD_ERR_BOX, "strain made the box thinner than 3 link cells");
-        if (nc < ctx->C.nc[2]) {
-            ctx->C.nc[2] = nc;
-            ctx->C.ncell = ctx->C.nc[0] * ctx->C.nc[1] * nc;
-            ctx->C.ntiles = (ctx->C.ncell + 4095) / 4096;
+        bool changed = false;
+        for (int r = 0; r < ctx->n_rep; r++) {
+            double Lz = ctx->L[3 * r + 2];
+            for (int32_t s = 0; s < n_steps; s++) Lz *= ctx->strain_scale;
+            const int nc = cells_along(std::fmin(Lz, ctx->L[3 * r + 2]), ctx->r_list);
+            if (nc < 3) return fail(ctx, MD_ERR_BOX, "strain made a box thinner than 3 link cells");
+            if (nc < ctx->rc[r].nc[2]) {
+                ctx->rc[r].nc[2] = nc;
+                changed = true;
+            }
+        }
+        if (changed) {  // fewer cells: the bases move down, the allocation still fits
+            int base = 0;
+            for (int r = 0; r < ctx->n_rep; r++) {
+                ctx->rc[r].base = base;
+                base += ctx->rc[r].nc[0] * ctx->rc[r].nc[1] * ctx->rc[r].nc[2];
+            }
+            ctx->C.ncell = base;
+            MD_CK(cudaMemcpyAsync(ctx->d_rc, ctx->rc.data(), ctx->n_rep * sizeof(RepCells), cudaMemcpyHostToDevice,
+                                  ctx->stream));
+            MD_CK(cudaMemsetAsync(ctx->C.cell_count, 0, sizeof(int32_t) * ctx->C.ncell, ctx->stream));
+            drop_graphs(ctx);
         }
     }
-    MD_CK(reset_errors(ctx));
     if (!ctx->forces_valid) {
+        MD_CK(reset_errors(ctx));
         MD_CK(enqueue_forces(ctx));
     }
-    const int every = ctx->cfg.rebuild_every;
-    for (int32_t s = 0; s < n_steps; s++) {
-        MD_CK(mark(ctx));
-        if (ctx->strain_scale != 1.0) {
-            MD_CK(launch_box_update(ctx->d_box, ctx->strain_scale, ctx->stream));
-            ctx->L[2] *= ctx->strain_scale;
-            ctx->launches++;
-        }
-        MD_CK(launch_kick_drift(ctx->A, ctx->half_dt, ctx->dt, ctx->strain_scale, ctx->lim2, ctx->stream));
-        MD_CK(mark(ctx));
-        if (every > 0 && (ctx->step + 1) % every == 0) {
-            MD_CK(launch_set_rebuild(ctx->d_flags, ctx->stream));
-            ctx->launches++;
-        }
-        MD_CK(enqueue_rebuild(ctx));
-        MD_CK(mark(ctx));
-        MD_CK(launch_density(ctx->A, ctx->P, ctx->precision, ctx->lanes, ctx->stream));
-        MD_CK(mark(ctx));
-        MD_CK(launch_force(ctx->A, ctx->P, ctx->precision, ctx->lanes, true, s == n_steps - 1, ctx->half_dt,
-                           ctx->stream));
-        MD_CK(mark(ctx));
-        ctx->launches += 3 + kRebuildLaunches;
-        ctx->step++;
+    unsigned long long *stamps = nullptr;
+    if (ctx->profiling) {
+        md_status st = ensure_stamps(ctx, 4 * ((size_t)n_steps + 1));
+        if (st != MD_OK) return st;
+        stamps = ctx->d_stamps;
     }
-    MD_CK(launch_reduce(ctx->A, partial_blocks(ctx->A.n, ctx->lanes), ctx->d_reduce, ctx->stream));
-    ctx->launches++;
-    MD_CK(cudaMemcpyAsync(ctx->h_reduce, ctx->d_reduce, sizeof(double) * kPartials, cudaMemcpyDeviceToHost,
-                          ctx->stream));
+    const bool graph = ctx->use_graph && !ctx->profiling && ctx->strain_scale == 1.0;
+    int rows = 0;
+    if (graph) {
+        auto it = ctx->graphs.find(n_steps);
+        if (it == ctx->graphs.end()) {
+            cudaGraph_t g = nullptr;
+            cudaGraphExec_t ge = nullptr;
+            MD_CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = enqueue_steps(ctx, n_steps, nullptr, &rows);
+            cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
+            if (e == cudaSuccess) e = e2;
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+            if (g) cudaGraphDestroy(g);
+            if (e != cudaSuccess) return fail(ctx, MD_ERR_CUDA, "capturing the step graph", e);
+            it = ctx->graphs.emplace(n_steps, ge).first;
+            ctx->graph_rows[n_steps] = rows;
+        }
+        MD_CK(cudaGraphLaunch(it->second, ctx->stream));
+        rows = ctx->graph_rows[n_steps];
+    } else {
+        MD_CK(enqueue_steps(ctx, n_steps, stamps, &rows));
+    }
+    ctx->launches += 2;
+    ctx->part_rows = rows;
+    if (stamps)
+        MD_CK(cudaMemcpyAsync(ctx->h_stamps, stamps, 4 * ((size_t)n_steps + 1) * sizeof(unsigned long long),
+                              cudaMemcpyDeviceToHost, ctx->stream));
     md_status st = sync_and_check(ctx, ctx->cfg.strict_skin != 0);
-    collect_marks(ctx);
+    ctx->step += n_steps;
+    for (int r = 0; r < ctx->n_rep; r++)
+        for (int32_t s = 0; s < n_steps; s++) ctx->L[3 * r + 2] *= ctx->strain_scale;
     if (st != MD_OK) {
         ctx->forces_valid = ctx->energy_valid = false;
         return st;
     }
+    if (stamps) collect_stamps(ctx, n_steps);
     ctx->list_valid = ctx->forces_valid = ctx->energy_valid = true;
     return MD_OK;
 }
@@ -620,11 +793,14 @@ md_status md_energy(md_ctx *ctx, md_energies *out) {
     out->pe = r[0];
     out->ke = 0.5 * r[1] * kMvv2e;
     out->te = out->pe + out->ke;
-    out->temperature = ctx->n > 1 ? 2.0 * out->ke / ((double)(3 * ctx->n - 3) * kKb) : 0.0;
+    const int64_t dof = 3 * ctx->n - 3 * (int64_t)ctx->n_rep;
+    out->temperature = dof > 0 ? 2.0 * out->ke / ((double)dof * kKb) : 0.0;
     const double W[9] = {r[2], r[7], r[6], r[7], r[3], r[5], r[6], r[5], r[4]};
     std::memcpy(out->virial, W, sizeof(W));
-    out->volume = ctx->L[0] * ctx->L[1] * ctx->L[2];
-    out->pressure_gpa = (2.0 * out->ke + r[2] + r[3] + r[4]) / (3.0 * out->volume) * kEva3ToGpa;
+    double vol = 0.0;
+    for (int q = 0; q < ctx->n_rep; q++) vol += ctx->L[3 * q] * ctx->L[3 * q + 1] * ctx->L[3 * q + 2];
+    out->volume = vol;
+    out->pressure_gpa = (2.0 * out->ke + r[2] + r[3] + r[4]) / (3.0 * vol) * kEva3ToGpa;
     for (int k = 0; k < 3; k++) {
         out->momentum[k] = r[8 + k];
         out->box[k] = ctx->L[k];
@@ -633,6 +809,42 @@ md_status md_energy(md_ctx *ctx, md_energies *out) {
     out->n_rebuilds = (int64_t)ctx->h_flags->n_rebuilds;
     out->max_neighbours = ctx->h_flags->max_count;
     out->range_violations = (int64_t)ctx->h_flags->range_violations;
+    return MD_OK;
+}
+
+md_status md_replica_energies(md_ctx *ctx, md_energies *out) {
+    if (!ctx || !out) return MD_ERR_ARG;
+    if (!ctx->energy_valid) {
+        md_status s = compute_forces(ctx);
+        if (s != MD_OK) return s;
+    }
+    const int nr = ctx->n_rep;
+    MD_CK(launch_replica_sums(ctx->A, ctx->d_rep_off, nr, ctx->d_rep_sums, ctx->stream));
+    ctx->launches++;
+    std::vector<double> h(5 * (size_t)nr);
+    MD_CK(cudaMemcpyAsync(h.data(), ctx->d_rep_sums, h.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                          ctx->stream));
+    MD_CK(cudaStreamSynchronize(ctx->stream));
+    for (int r = 0; r < nr; r++) {
+        md_energies &o = out[r];
+        std::memset(&o, 0, sizeof(o));
+        const double *q = &h[5 * (size_t)r];
+        const int64_t m = ctx->rep_off[r + 1] - ctx->rep_off[r];
+        o.pe = q[0];
+        o.ke = 0.5 * q[1] * kMvv2e;
+        o.te = o.pe + o.ke;
+        o.temperature = m > 1 ? 2.0 * o.ke / ((double)(3 * m - 3) * kKb) : 0.0;
+        for (int k = 0; k < 3; k++) {
+            o.momentum[k] = q[2 + k];
+            o.box[k] = ctx->L[3 * r + k];
+        }
+        o.volume = o.box[0] * o.box[1] * o.box[2];
+        o.pressure_gpa = NAN;  // the virial is reduced over the whole batch only
+        o.step = ctx->step;
+        o.n_rebuilds = (int64_t)ctx->h_flags->n_rebuilds;
+        o.max_neighbours = ctx->h_flags->max_count;
+        o.range_violations = (int64_t)ctx->h_flags->range_violations;
+    }
     return MD_OK;
 }
 
@@ -691,9 +903,7 @@ md_status md_tune(md_ctx *ctx, int32_t *lanes_out) {
         MD_CK(cudaEventCreate(&e1));
         float best = 1e30f;
         int best_t = ctx->lanes;
-        const int keep = ctx->lanes;
-        for (int t = 1; t <= 32; t *= 2) {
-            ctx->lanes = t;
+        for (int t = 1; t <= 8; t *= 2) {
             for (int rep = 0; rep < 4; rep++) {  // first round is a warm-up
                 MD_CK(cudaEventRecord(e0, ctx->stream));
                 MD_CK(launch_density(ctx->A, ctx->P, ctx->precision, t, ctx->stream));
@@ -709,10 +919,10 @@ md_status md_tune(md_ctx *ctx, int32_t *lanes_out) {
                 ctx->launches += 2;
             }
         }
-        (void)keep;
-        ctx->lanes = best_t;
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
+        if (best_t != ctx->lanes) drop_graphs(ctx);
+        ctx->lanes = best_t;
         ctx->energy_valid = false;  // partial-sum rows depend on the lane count
         st = sync_and_check(ctx, false);
         if (st != MD_OK) return st;
@@ -721,13 +931,37 @@ md_status md_tune(md_ctx *ctx, int32_t *lanes_out) {
     return MD_OK;
 }
 
+md_status md_selftest_timeout(md_ctx *ctx) {
+    if (!ctx || ctx->n == 0) return MD_ERR_ARG;
+    if (!ctx->forces_valid) {
+        md_status st = compute_forces(ctx);
+        if (st != MD_OK) return st;
+    }
+    StepParams sp = step_params(ctx, 1);
+    sp.spin_limit = 20000;  // ~2-5 ms of polling
+    sp.withhold_arrival = 1;
+    MD_CK(reset_errors(ctx));
+    int grid = 0;
+    MD_CK(launch_step(ctx->A, ctx->C, ctx->P, ctx->precision, ctx->lanes, sp, ctx->d_bar, nullptr, &grid,
+                      ctx->stream));
+    ctx->launches++;
+    md_status st = sync_and_check(ctx, false);
+    // the state is no longer a clean step boundary: recompute before the next step
+    ctx->forces_valid = ctx->energy_valid = false;
+    return st;
+}
+
+md_status md_set_graph(md_ctx *ctx, int32_t on) {
+    if (!ctx) return MD_ERR_ARG;
+    if (!on) drop_graphs(ctx);
+    ctx->use_graph = on != 0;
+    return MD_OK;
+}
+
 md_status md_set_profiling(md_ctx *ctx, int32_t on) {
     if (!ctx) return MD_ERR_ARG;
     ctx->profiling = on != 0;
-    const int64_t launches = ctx->prof.launches;
     ctx->prof = md_profile{};
-    ctx->prof.launches = launches;
-    ctx->ev_used = 0;
     return MD_OK;
 }
 
@@ -752,6 +986,7 @@ md_status md_set_state(md_ctx *ctx, const double *pos, const double *vel, const 
         if (!src[q]) continue;
         MD_CK(cudaMemcpyAsync(ctx->d_stage, src[q], sizeof(double) * 3 * n, kind, ctx->stream));
         MD_CK(launch_sort_in_vec(ctx->A, static_cast<const double *>(ctx->d_stage), dst[q], ctx->stream));
+        ctx->launches++;
     }
     if (pos) MD_CK(launch_wrap(ctx->A, ctx->stream));
     MD_CK(cudaStreamSynchronize(ctx->stream));

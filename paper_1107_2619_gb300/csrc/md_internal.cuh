@@ -18,13 +18,13 @@ constexpr double kKb = 8.617333262e-5;
 constexpr double kMvv2e = kAmuKg * 1.0e10 / kEvJ;
 constexpr double kEva3ToGpa = kEvJ * 1.0e30 / 1.0e9;
 
-enum : int32_t { FLAG_OVERFLOW = 1, FLAG_NONFINITE = 2 };
+enum : int32_t { FLAG_OVERFLOW = 1, FLAG_NONFINITE = 2, FLAG_TIMEOUT = 4 };
 
 constexpr int kThreads = 128;     // threads per block of the per-atom kernels
 constexpr int kPartials = 11;     // per-block FP64 partial sums: pe, sum m v^2, W(6), p(3)
 
-// Current orthorhombic box (changes under the strain ramp; kept in device memory so that
-// a captured step reads the live value).
+// Current orthorhombic box of one system (changes under the strain ramp; kept in device
+// memory so that a captured step reads the live value).
 struct Box {
     double L[3];
     double invL[3];
@@ -40,6 +40,7 @@ struct Flags {
     int32_t skin_exceeded;  // an atom moved more than skin/2 since the last build
     unsigned long long n_rebuilds;
     unsigned long long range_violations;
+    long long step;         // steps taken (the rebuild schedule counts from here)
 };
 
 // Device view of the potential.  Tables hold, per interval k of a uniform knot grid, the
@@ -62,9 +63,25 @@ struct Pot {
     const double4_32a *F64;   // [a*nk + k]
 };
 
-// Device view of the per-atom state (cell order).
+// Link-cell grid of one replica: its cells are the global cells [base, base + nc0*nc1*nc2).
+struct RepCells {
+    int nc[3];
+    int base;
+};
+
+// Grid barrier of the persistent step kernel (see md_step.cu).
+struct GridBarrier {
+    unsigned int count;
+    unsigned int gen;
+    int abort;
+    int pad;
+};
+
+// Device view of the per-atom state (cell order).  A batch of replicas is stored as one
+// system whose atoms of replica r are contiguous; rep[i] is NULL for a single system.
 struct Atoms {
     int n, k_max;
+    int n_rep;
     double4_32a *pos, *vel, *force, *ref;        // pos.w = species; vel.w = (1/mvv2e)/m
     double4_32a *pos_tmp, *vel_tmp, *force_tmp;  // renumbering scratch
     float4 *posf;                            // FP32 wrapped position, w = species bits
@@ -74,15 +91,17 @@ struct Atoms {
     int32_t *id, *id_tmp, *rank, *spec, *spec_tmp;
     int32_t *cell_of, *slot, *order;
     int32_t *nbr, *count;                    // nbr[i*k_max + k], k < min(count, k_max)
-    double *partials;                        // [n_blocks][kPartials]
-    Box *box;
+    double *partials;                        // [kPartials][part_stride] per-block sums
+    int part_stride;
+    int32_t *rep;                            // replica of each slot (NULL: one system)
+    Box *boxes;                              // [n_rep]
     Flags *flags;
 };
 
 struct Cells {
-    int nc[3];
-    int ncell;
+    int ncell;   // all replicas
     int ntiles;
+    RepCells *rc;  // [n_rep], device
     int32_t *cell_count, *cell_start, *tile_sums;
 };
 
@@ -91,9 +110,6 @@ cudaError_t launch_set_rebuild(Flags *f, cudaStream_t s);
 cudaError_t launch_clear_rebuild(Flags *f, cudaStream_t s);
 cudaError_t launch_rebuild(const Atoms &A, const Cells &C, double rl2, float band_lo, float band_hi,
                            cudaStream_t s);
-cudaError_t launch_box_update(Box *box, double scale_z, cudaStream_t s);
-cudaError_t launch_kick_drift(const Atoms &A, double half_dt, double dt, double strain_scale,
-                              double lim2, cudaStream_t s);
 cudaError_t launch_check_displacement(const Atoms &A, double lim2, cudaStream_t s);
 cudaError_t launch_wrap(const Atoms &A, cudaStream_t s);
 // lanes = T lanes per atom (1, 2, 4, 8, 16 or 32)
@@ -107,6 +123,24 @@ cudaError_t launch_unsort_scalar(const Atoms &A, const double *src, double *dst,
 cudaError_t launch_unsort_int(const Atoms &A, const int32_t *src, int32_t *dst, cudaStream_t s);
 cudaError_t launch_unsort_list(const Atoms &A, int32_t *dst, cudaStream_t s);
 cudaError_t launch_sort_in_vec(const Atoms &A, const double *src, double4_32a *dst, cudaStream_t s);
+cudaError_t launch_replica_sums(const Atoms &A, const int32_t *off, int n_rep, double *out, cudaStream_t s);
+
+// Persistent step kernel (md_step.cu): n_steps velocity-Verlet steps in one cooperative
+// launch; grid barriers between phases; per-phase %globaltimer stamps when stamps != NULL.
+struct StepParams {
+    int n_steps;
+    int energy_last;      // FP64 partial sums on the last step
+    double half_dt, dt, strain_scale, lim2;
+    int rebuild_every;    // scheduled rebuild period (0: none)
+    double rl2;
+    float band_lo, band_hi;
+    unsigned long long spin_limit;
+    int withhold_arrival;  // self-test of the bounded wait: block 0 skips its first arrival
+};
+cudaError_t launch_step(const Atoms &A, const Cells &C, const Pot &P, int precision, int lanes,
+                        const StepParams &sp, GridBarrier *bar, unsigned long long *stamps, int *grid_out,
+                        cudaStream_t s);
+int step_grid(const Pot &P, int precision, int lanes);   // blocks of the persistent launch
 
 inline int blocks_for(long long n, int threads) { return (int)((n + threads - 1) / threads); }
 

@@ -1,0 +1,345 @@
+// Per-item device functions of the two EAM passes (the two sums of Eq. (1)), FP64 and mixed.
+// An item is one lane of one atom: item g -> atom i = g / T, lane g % T.  Every lane of a
+// warp must call an item function in the same iteration (the lane sums use shuffles), so
+// callers iterate over a range rounded up to whole warps and pass items past the end too.
+//
+//   density:  rho_i = sum_j phi_{s_i s_j}(r_ij);  F_i = F(rho_i), F'_i;  pass-2 copy of (r_i, F'_i)
+//   force:    f_i = sum_j [V'(r) + F'_i phi'_{s_i s_j}(r) + F'_j phi'_{s_j s_i}(r)] d / r, d = r_j - r_i,
+//             then (optionally) the second half kick v += (dt/2) f/m and the FP64 partial sums.
+// Mixed precision: pair and density terms FP32 from FP32 wrapped coordinates, density sum
+// error-free in an FP32 (hi, lo) pair rounded to FP64 before F(rho); F, F', kick, sums FP64.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "md_eam_common.cuh"
+#include "md_phases.cuh"
+
+namespace mdk {
+namespace ps {
+
+using namespace eam;
+
+__device__ __forceinline__ float mi32(float d, float L, float invL) { return fmaf(-L, rintf(d * invL), d); }
+__device__ __forceinline__ double mi64(double d, double L, double invL) { return fma(-L, rint(d * invL), d); }
+
+// Knot-table row of a species pair: (V c0..c3, phi c0..c3) as 8 floats in one 32-byte load.
+__device__ __forceinline__ void row32(const double4_32a *tab, size_t idx, float (&v)[4], float (&p)[4]) {
+    const double4_32a d = tab[idx];
+    unpack2(d.x, v[0], v[1]);
+    unpack2(d.y, v[2], v[3]);
+    unpack2(d.z, p[0], p[1]);
+    unpack2(d.w, p[2], p[3]);
+}
+
+__device__ __forceinline__ float4 phi_half32(const double4_32a *tab, size_t idx) {
+    return __ldg(reinterpret_cast<const float4 *>(tab + idx) + 1);
+}
+
+// ======================================================================= mixed precision
+template <int T, int KIND, bool MULTI>
+__device__ __forceinline__ void density32_item(const Atoms &A, const Pot &P, const Box *boxes, long long g) {
+    const int i = (int)(g / T), lane = (int)(g & (T - 1));
+    const bool live = i < A.n;
+    float hi = 0.f, lo = 0.f;
+    float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
+    int si = 0;
+    if (live) {
+        const Box &B = boxes[ph::replica_of(A, i)];
+        const float Lx = B.Lf[0], Ly = B.Lf[1], Lz = B.Lf[2];
+        const float ix = B.invLf[0], iy = B.invLf[1], iz = B.invLf[2];
+        pi = A.posf[i];
+        si = MULTI ? __float_as_int(pi.w) : 0;
+        const int cnt = min(A.count[i], A.k_max);
+        const int *__restrict__ row = A.nbr + (size_t)i * A.k_max;
+        for (int k = lane; k < cnt; k += T) {
+            const int j = __ldg(row + k);
+            const float4 pj = __ldg(A.posf + j);
+            const float dx = mi32(pj.x - pi.x, Lx, ix);
+            const float dy = mi32(pj.y - pi.y, Ly, iy);
+            const float dz = mi32(pj.z - pi.z, Lz, iz);
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            if (!(r2 < P.rc2f)) continue;
+            const float r = r2 * rsqrtf(r2);
+            float phi;
+            if (KIND == MD_POT_FS_ANALYTIC) {
+                phi = fs_phi<float>(P.fsf, P.bdf, r);
+            } else {
+                const int sj = MULTI ? __float_as_int(pj.w) : 0;
+                float t, d;
+                bool below;
+                const int kr = knot_row((r - P.r_minf) * P.inv_drf, P.nk, t, below);
+                if (below) atomicAdd(&A.flags->range_violations, 1ull);
+                const float4 c = phi_half32(P.VP32, (size_t)(si * P.ns + sj) * P.nk + kr);
+                phi = cubic(t, c.x, c.y, c.z, c.w, below, d);
+            }
+            two_sum_add(hi, lo, phi);
+        }
+    }
+    lane_sum_df<T>(hi, lo);
+    if (live && lane == 0) {
+        const double rho = (double)hi + (double)lo;
+        double dF;
+        const double F = embed64(P, si, rho, dF, A.flags);
+        A.rho[i] = rho;
+        A.dF[i] = dF;
+        A.e_atom[i] = F;
+        A.p2f[i] = make_float4(pi.x, pi.y, pi.z, (float)dF);
+    }
+}
+
+// Returns the atom index for the lane that finished atom i (lane 0 of a live atom), else -1.
+template <int T, int KIND, bool MULTI, bool ENERGY>
+__device__ __forceinline__ int force32_item(const Atoms &A, const Pot &P, const Box *boxes, long long g,
+                                            double half_dt, bool kick, double (&part)[kPartials]) {
+    const int i = (int)(g / T), lane = (int)(g & (T - 1));
+    const bool live = i < A.n;
+    float fx = 0.f, fy = 0.f, fz = 0.f, ep = 0.f;
+    float wxx = 0.f, wyy = 0.f, wzz = 0.f, wyz = 0.f, wxz = 0.f, wxy = 0.f;
+    if (live) {
+        const Box &B = boxes[ph::replica_of(A, i)];
+        const float Lx = B.Lf[0], Ly = B.Lf[1], Lz = B.Lf[2];
+        const float ix = B.invLf[0], iy = B.invLf[1], iz = B.invLf[2];
+        const float4 pi = A.p2f[i];
+        const float Fpi = pi.w;
+        const int si = MULTI ? A.spec[i] : 0;
+        const int cnt = min(A.count[i], A.k_max);
+        const int *__restrict__ row = A.nbr + (size_t)i * A.k_max;
+        for (int k = lane; k < cnt; k += T) {
+            const int j = __ldg(row + k);
+            const float4 pj = __ldg(A.p2f + j);
+            const float dx = mi32(pj.x - pi.x, Lx, ix);
+            const float dy = mi32(pj.y - pi.y, Ly, iy);
+            const float dz = mi32(pj.z - pi.z, Lz, iz);
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            if (!(r2 < P.rc2f)) continue;
+            const float rinv = rsqrtf(r2);
+            const float r = r2 * rinv;
+            const float Fpj = pj.w;
+            float V, gg;
+            if (KIND == MD_POT_FS_ANALYTIC) {
+                float dV;
+                V = fs_V<float>(P.fsf, r, dV);
+                gg = fmaf(Fpi + Fpj, fs_dphi<float>(P.fsf, P.bdf, r), dV);
+            } else {
+                const int sj = MULTI ? __ldg(A.spec + j) : 0;
+                float t;
+                bool below;
+                const int kr = knot_row((r - P.r_minf) * P.inv_drf, P.nk, t, below);
+                if (below) atomicAdd(&A.flags->range_violations, 1ull);
+                float cv[4], cp[4], dVk, dab;
+                row32(P.VP32, (size_t)(si * P.ns + sj) * P.nk + kr, cv, cp);
+                V = cubic(t, cv[0], cv[1], cv[2], cv[3], below, dVk);
+                cubic(t, cp[0], cp[1], cp[2], cp[3], below, dab);
+                float gk;
+                if (MULTI) {
+                    const float4 c = phi_half32(P.VP32, (size_t)(sj * P.ns + si) * P.nk + kr);
+                    float dba;
+                    cubic(t, c.x, c.y, c.z, c.w, below, dba);
+                    gk = fmaf(Fpi, dab, fmaf(Fpj, dba, dVk));
+                } else {
+                    gk = fmaf(Fpi + Fpj, dab, dVk);
+                }
+                gg = gk * P.inv_drf;
+            }
+            const float gr = gg * rinv;
+            fx = fmaf(gr, dx, fx);
+            fy = fmaf(gr, dy, fy);
+            fz = fmaf(gr, dz, fz);
+            if (ENERGY) {
+                ep = fmaf(0.5f, V, ep);
+                const float hg = -0.5f * gr;
+                wxx = fmaf(hg * dx, dx, wxx);
+                wyy = fmaf(hg * dy, dy, wyy);
+                wzz = fmaf(hg * dz, dz, wzz);
+                wyz = fmaf(hg * dy, dz, wyz);
+                wxz = fmaf(hg * dx, dz, wxz);
+                wxy = fmaf(hg * dx, dy, wxy);
+            }
+        }
+    }
+    fx = lane_sum<T>(fx);
+    fy = lane_sum<T>(fy);
+    fz = lane_sum<T>(fz);
+    if (ENERGY) {
+        ep = lane_sum<T>(ep);
+        wxx = lane_sum<T>(wxx); wyy = lane_sum<T>(wyy); wzz = lane_sum<T>(wzz);
+        wyz = lane_sum<T>(wyz); wxz = lane_sum<T>(wxz); wxy = lane_sum<T>(wxy);
+    }
+    if (!(live && lane == 0)) return -1;
+    A.force[i] = make_double4_32a(fx, fy, fz, 0.0);
+    if (!isfinite(fx + fy + fz)) atomicOr(&A.flags->error, FLAG_NONFINITE);
+    double4_32a v = A.vel[i];
+    kick_and_partials(v, fx, fy, fz, half_dt, kick);
+    if (kick) A.vel[i] = v;
+    if (ENERGY) {
+        const double e = A.e_atom[i] + (double)ep;
+        A.e_atom[i] = e;
+        const double m = 1.0 / (kMvv2e * v.w);
+        part[0] += e;
+        part[1] += m * fma(v.x, v.x, fma(v.y, v.y, v.z * v.z));
+        part[2] += wxx; part[3] += wyy; part[4] += wzz;
+        part[5] += wyz; part[6] += wxz; part[7] += wxy;
+        part[8] += m * v.x; part[9] += m * v.y; part[10] += m * v.z;
+    }
+    return i;
+}
+
+// ======================================================================= FP64
+template <int T, int KIND, bool MULTI>
+__device__ __forceinline__ void density64_item(const Atoms &A, const Pot &P, const Box *boxes, long long g) {
+    const int i = (int)(g / T), lane = (int)(g & (T - 1));
+    const bool live = i < A.n;
+    double rho = 0.0;
+    double4_32a pi = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+    int si = 0;
+    if (live) {
+        const Box &B = boxes[ph::replica_of(A, i)];
+        pi = A.pos[i];
+        si = MULTI ? A.spec[i] : 0;
+        const int cnt = min(A.count[i], A.k_max);
+        const int *__restrict__ row = A.nbr + (size_t)i * A.k_max;
+        for (int k = lane; k < cnt; k += T) {
+            const int j = __ldg(row + k);
+            const double4_32a pj = A.pos[j];
+            const double dx = mi64(pj.x - pi.x, B.L[0], B.invL[0]);
+            const double dy = mi64(pj.y - pi.y, B.L[1], B.invL[1]);
+            const double dz = mi64(pj.z - pi.z, B.L[2], B.invL[2]);
+            const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+            if (!(r2 < P.rc2)) continue;
+            const double r = r2 * rsqrt64(r2);
+            if (KIND == MD_POT_FS_ANALYTIC) {
+                rho += fs_phi<double>(P.fs, P.bd, r);
+            } else {
+                const int sj = MULTI ? (int)pj.w : 0;
+                double t, d;
+                bool below;
+                const int kr = knot_row((r - P.r_min) * P.inv_dr, P.nk, t, below);
+                if (below) atomicAdd(&A.flags->range_violations, 1ull);
+                const double4_32a c = P.VP64[((size_t)(si * P.ns + sj) * P.nk + kr) * 2 + 1];
+                rho += cubic(t, c.x, c.y, c.z, c.w, below, d);
+            }
+        }
+    }
+    rho = lane_sum<T>(rho);
+    if (live && lane == 0) {
+        double dF;
+        const double F = embed64(P, si, rho, dF, A.flags);
+        A.rho[i] = rho;
+        A.dF[i] = dF;
+        A.e_atom[i] = F;
+        A.p2d[i] = make_double4_32a(pi.x, pi.y, pi.z, dF);
+    }
+}
+
+template <int T, int KIND, bool MULTI, bool ENERGY>
+__device__ __forceinline__ int force64_item(const Atoms &A, const Pot &P, const Box *boxes, long long g,
+                                            double half_dt, bool kick, double (&part)[kPartials]) {
+    const int i = (int)(g / T), lane = (int)(g & (T - 1));
+    const bool live = i < A.n;
+    double fx = 0.0, fy = 0.0, fz = 0.0, ep = 0.0;
+    double wxx = 0.0, wyy = 0.0, wzz = 0.0, wyz = 0.0, wxz = 0.0, wxy = 0.0;
+    if (live) {
+        const Box &B = boxes[ph::replica_of(A, i)];
+        const double4_32a pi = A.p2d[i];
+        const double Fpi = pi.w;
+        const int si = MULTI ? A.spec[i] : 0;
+        const int cnt = min(A.count[i], A.k_max);
+        const int *__restrict__ row = A.nbr + (size_t)i * A.k_max;
+        for (int k = lane; k < cnt; k += T) {
+            const int j = __ldg(row + k);
+            const double4_32a pj = A.p2d[j];
+            const double dx = mi64(pj.x - pi.x, B.L[0], B.invL[0]);
+            const double dy = mi64(pj.y - pi.y, B.L[1], B.invL[1]);
+            const double dz = mi64(pj.z - pi.z, B.L[2], B.invL[2]);
+            const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+            if (!(r2 < P.rc2)) continue;
+            const double rinv = rsqrt64(r2);
+            const double r = r2 * rinv;
+            const double Fpj = pj.w;
+            double V, gg;
+            if (KIND == MD_POT_FS_ANALYTIC) {
+                double dV;
+                V = fs_V<double>(P.fs, r, dV);
+                gg = fma(Fpi + Fpj, fs_dphi<double>(P.fs, P.bd, r), dV);
+            } else {
+                const int sj = MULTI ? __ldg(A.spec + j) : 0;
+                double t;
+                bool below;
+                const int kr = knot_row((r - P.r_min) * P.inv_dr, P.nk, t, below);
+                if (below) atomicAdd(&A.flags->range_violations, 1ull);
+                const size_t ab = ((size_t)(si * P.ns + sj) * P.nk + kr) * 2;
+                const double4_32a cv = P.VP64[ab], cp = P.VP64[ab + 1];
+                double dVk, dab;
+                V = cubic(t, cv.x, cv.y, cv.z, cv.w, below, dVk);
+                cubic(t, cp.x, cp.y, cp.z, cp.w, below, dab);
+                double gk;
+                if (MULTI) {
+                    const double4_32a cb = P.VP64[((size_t)(sj * P.ns + si) * P.nk + kr) * 2 + 1];
+                    double dba;
+                    cubic(t, cb.x, cb.y, cb.z, cb.w, below, dba);
+                    gk = fma(Fpi, dab, fma(Fpj, dba, dVk));
+                } else {
+                    gk = fma(Fpi + Fpj, dab, dVk);
+                }
+                gg = gk * P.inv_dr;
+            }
+            const double gr = gg * rinv;
+            fx = fma(gr, dx, fx);
+            fy = fma(gr, dy, fy);
+            fz = fma(gr, dz, fz);
+            if (ENERGY) {
+                ep = fma(0.5, V, ep);
+                const double hg = -0.5 * gr;
+                wxx = fma(hg * dx, dx, wxx);
+                wyy = fma(hg * dy, dy, wyy);
+                wzz = fma(hg * dz, dz, wzz);
+                wyz = fma(hg * dy, dz, wyz);
+                wxz = fma(hg * dx, dz, wxz);
+                wxy = fma(hg * dx, dy, wxy);
+            }
+        }
+    }
+    fx = lane_sum<T>(fx);
+    fy = lane_sum<T>(fy);
+    fz = lane_sum<T>(fz);
+    if (ENERGY) {
+        ep = lane_sum<T>(ep);
+        wxx = lane_sum<T>(wxx); wyy = lane_sum<T>(wyy); wzz = lane_sum<T>(wzz);
+        wyz = lane_sum<T>(wyz); wxz = lane_sum<T>(wxz); wxy = lane_sum<T>(wxy);
+    }
+    if (!(live && lane == 0)) return -1;
+    A.force[i] = make_double4_32a(fx, fy, fz, 0.0);
+    if (!isfinite(fx + fy + fz)) atomicOr(&A.flags->error, FLAG_NONFINITE);
+    double4_32a v = A.vel[i];
+    kick_and_partials(v, fx, fy, fz, half_dt, kick);
+    if (kick) A.vel[i] = v;
+    if (ENERGY) {
+        const double e = A.e_atom[i] + ep;
+        A.e_atom[i] = e;
+        const double m = 1.0 / (kMvv2e * v.w);
+        part[0] += e;
+        part[1] += m * fma(v.x, v.x, fma(v.y, v.y, v.z * v.z));
+        part[2] += wxx; part[3] += wyy; part[4] += wzz;
+        part[5] += wyz; part[6] += wxz; part[7] += wxy;
+        part[8] += m * v.x; part[9] += m * v.y; part[10] += m * v.z;
+    }
+    return i;
+}
+
+// Precision-generic front ends.
+template <int PREC, int T, int KIND, bool MULTI>
+__device__ __forceinline__ void density_item(const Atoms &A, const Pot &P, const Box *boxes, long long g) {
+    if (PREC == MD_PREC_FP64) density64_item<T, KIND, MULTI>(A, P, boxes, g);
+    else density32_item<T, KIND, MULTI>(A, P, boxes, g);
+}
+
+template <int PREC, int T, int KIND, bool MULTI, bool ENERGY>
+__device__ __forceinline__ int force_item(const Atoms &A, const Pot &P, const Box *boxes, long long g,
+                                          double half_dt, bool kick, double (&part)[kPartials]) {
+    if (PREC == MD_PREC_FP64) return force64_item<T, KIND, MULTI, ENERGY>(A, P, boxes, g, half_dt, kick, part);
+    return force32_item<T, KIND, MULTI, ENERGY>(A, P, boxes, g, half_dt, kick, part);
+}
+
+}  // namespace ps
+}  // namespace mdk

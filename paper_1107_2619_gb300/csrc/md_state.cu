@@ -1,79 +1,23 @@
-// Per-atom state kernels: velocity-Verlet half kick + drift (§2.3), the strain-rate box
-// update (§2.2), the skin displacement check (§3.2.1), the FP32 wrapped position copy, and
-// the conversions between cell order and the caller's atom order.
+// Per-atom state kernels outside the step: the skin displacement check (§3.2.1), the FP32
+// wrapped position copy, and the conversions between cell order and the caller's atom order.
 #include <cuda_runtime.h>
 
-#include "md_internal.cuh"
+#include "md_phases.cuh"
 
 namespace mdk {
 
 namespace {
 
-__device__ __forceinline__ float wrap1(double x, double L, double invL) {
-    return (float)(x - L * floor(x * invL));
-}
-
-__device__ __forceinline__ float4 wrapped(const double4_32a &p, const Box &B, int species) {
-    return make_float4(wrap1(p.x, B.L[0], B.invL[0]), wrap1(p.y, B.L[1], B.invL[1]),
-                       wrap1(p.z, B.L[2], B.invL[2]), __int_as_float(species));
-}
-
-// The box matrix times the strain matrix diag(1, 1, s): one thread, once per step.
-__global__ void k_box_update(Box *box, double s) {
-    Box b = *box;
-    b.L[2] = __dmul_rn(b.L[2], s);
-    b.invL[2] = 1.0 / b.L[2];
-    b.Lf[2] = (float)b.L[2];
-    b.invLf[2] = (float)b.invL[2];
-    *box = b;
-}
-
-// v += (dt/2) F/m;  r += dt v;  [z *= s];  displacement since the list build vs skin/2.
-// The FP64 operations are the separately rounded ones of the definition (no contraction).
-template <bool STRAIN>
-__global__ void __launch_bounds__(kThreads) k_kick_drift(Atoms A, double half_dt, double dt, double s,
-                                                         double lim2) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= A.n) return;
-    const Box B = *A.box;
-    double4_32a v = A.vel[i];
-    const double4_32a f = A.force[i];
-    double4_32a p = A.pos[i];
-    v.x = __dadd_rn(v.x, __dmul_rn(__dmul_rn(half_dt, f.x), v.w));
-    v.y = __dadd_rn(v.y, __dmul_rn(__dmul_rn(half_dt, f.y), v.w));
-    v.z = __dadd_rn(v.z, __dmul_rn(__dmul_rn(half_dt, f.z), v.w));
-    p.x = __dadd_rn(p.x, __dmul_rn(dt, v.x));
-    p.y = __dadd_rn(p.y, __dmul_rn(dt, v.y));
-    p.z = __dadd_rn(p.z, __dmul_rn(dt, v.z));
-    if (STRAIN) p.z = __dmul_rn(p.z, s);
-    A.vel[i] = v;
-    A.pos[i] = p;
-    const double4_32a r = A.ref[i];
-    const double ex = __dsub_rn(p.x, r.x), ey = __dsub_rn(p.y, r.y), ez = __dsub_rn(p.z, r.z);
-    const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
-    if (d2 > lim2 || !(d2 == d2)) {
-        A.flags->need_rebuild = 1;
-        A.flags->skin_exceeded = 1;
-    }
-    A.posf[i] = wrapped(p, B, __float_as_int(A.posf[i].w));
-}
-
 __global__ void k_check_displacement(Atoms A, double lim2) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= A.n) return;
-    const double4_32a p = A.pos[i], r = A.ref[i];
-    const double ex = __dsub_rn(p.x, r.x), ey = __dsub_rn(p.y, r.y), ez = __dsub_rn(p.z, r.z);
-    const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
-    if (d2 > lim2 || !(d2 == d2)) {
-        A.flags->need_rebuild = 1;
-        A.flags->skin_exceeded = 1;
-    }
+    ph::check_displacement(A, i, lim2);
 }
 
 __global__ void k_wrap(Atoms A) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= A.n) return;
-    A.posf[i] = wrapped(A.pos[i], *A.box, A.spec[i]);
+    A.posf[i] = ph::wrapped(A.pos[i], A.boxes[ph::replica_of(A, i)], A.spec[i]);
 }
 
 __global__ void k_unsort_vec(Atoms A, const double4_32a *src, double *dst) {
@@ -104,8 +48,7 @@ __global__ void k_unsort_list(Atoms A, int32_t *dst) {
     const int cnt = min(A.count[i], A.k_max);
     int32_t *row = dst + (size_t)A.id[i] * A.k_max;
     const int32_t *src = A.nbr + (size_t)i * A.k_max;
-    for (int k = 0; k < A.k_max; k++)
-        row[k] = k < cnt ? A.id[src[k]] : -1;
+    for (int k = 0; k < A.k_max; k++) row[k] = k < cnt ? A.id[src[k]] : -1;
 }
 
 __global__ void k_sort_in_vec(Atoms A, const double *src, double4_32a *dst) {
@@ -119,21 +62,34 @@ __global__ void k_sort_in_vec(Atoms A, const double *src, double4_32a *dst) {
     dst[k] = v;
 }
 
-}  // namespace
-
-cudaError_t launch_box_update(Box *box, double scale_z, cudaStream_t s) {
-    k_box_update<<<1, 1, 0, s>>>(box, scale_z);
-    return cudaGetLastError();
+// Per-replica sums in a fixed order, one block per replica: PE (E_i), sum m v^2, momentum.
+__global__ void k_replica_sums(Atoms A, const int32_t *off, double *out) {
+    __shared__ double sh[5][256];
+    const int r = blockIdx.x;
+    double q[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int k = off[r] + threadIdx.x; k < off[r + 1]; k += 256) {
+        const double4_32a v = A.vel[k];
+        const double m = 1.0 / (kMvv2e * v.w);
+        q[0] += A.e_atom[k];
+        q[1] += m * fma(v.x, v.x, fma(v.y, v.y, v.z * v.z));
+        q[2] += m * v.x;
+        q[3] += m * v.y;
+        q[4] += m * v.z;
+    }
+    for (int c = 0; c < 5; c++) sh[c][threadIdx.x] = q[c];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int c = 0; c < 5; c++) sh[c][threadIdx.x] += sh[c][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 5) out[5 * r + threadIdx.x] = sh[threadIdx.x][0];
 }
 
-cudaError_t launch_kick_drift(const Atoms &A, double half_dt, double dt, double strain_scale, double lim2,
-                              cudaStream_t s) {
-    if (A.n == 0) return cudaSuccess;
-    const int nb = blocks_for(A.n, kThreads);
-    if (strain_scale != 1.0)
-        k_kick_drift<true><<<nb, kThreads, 0, s>>>(A, half_dt, dt, strain_scale, lim2);
-    else
-        k_kick_drift<false><<<nb, kThreads, 0, s>>>(A, half_dt, dt, strain_scale, lim2);
+}  // namespace
+
+cudaError_t launch_replica_sums(const Atoms &A, const int32_t *off, int n_rep, double *out, cudaStream_t s) {
+    k_replica_sums<<<n_rep, 256, 0, s>>>(A, off, out);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,243 @@
+// The persistent step kernel: n velocity-Verlet steps (§2.3) of one system or of a batch of
+// replicas in ONE cooperative launch.  Phases are separated by a grid barrier:
+//
+//   [box update (strain)] -> half kick + drift + skin check              (first step only)
+//   per step:  [rebuild: bin | scan x3 | scatter | cell sort | gather | copyback | list]
+//              -> density pass -> force pass + half kick [+ next step's half kick + drift]
+//
+// The next step's first half kick and drift are fused into the force pass (each atom does
+// them right after its own force): the force pass gathers only the pass-2 copies (p2f/p2d),
+// never the positions the drift writes.  Under a strain ramp the box changes every step, so
+// the fused form is replaced by a separate box update + kick phase.
+//
+// The grid barrier waits at most `spin_limit` polls; a block that gives up marks the launch
+// aborted (FLAG_TIMEOUT) and every block returns at its next barrier.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "md_passes.cuh"
+
+namespace mdk {
+namespace st {
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Generation barrier over all blocks of a cooperative launch (all co-resident).
+__device__ __forceinline__ bool grid_sync(GridBarrier *b, unsigned nblocks, unsigned long long limit, Flags *f) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vgen = &b->gen;
+        const unsigned gen = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(&b->count, 1u) + 1u;
+        if (arrived == nblocks) {
+            atomicExch(&b->count, 0u);
+            __threadfence();
+            atomicAdd(&b->gen, 1u);
+        } else {
+            unsigned long long polls = 0;
+            while (*vgen == gen) {
+                if (*reinterpret_cast<volatile int *>(&b->abort)) break;
+                if (++polls > limit) {
+                    atomicExch(&b->abort, 1);
+                    atomicOr(&f->error, FLAG_TIMEOUT);
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return *reinterpret_cast<volatile int *>(&b->abort) == 0;
+}
+
+// Box matrix times the strain matrix diag(1, 1, s) (§2.2), every replica.
+__device__ __forceinline__ void strain_boxes(Box *boxes, int n_rep, double s) {
+    for (int r = 0; r < n_rep; r++) {
+        Box b = boxes[r];
+        b.L[2] = __dmul_rn(b.L[2], s);
+        b.invL[2] = 1.0 / b.L[2];
+        b.Lf[2] = (float)b.L[2];
+        b.invLf[2] = (float)b.invL[2];
+        boxes[r] = b;
+    }
+}
+
+template <int PREC, int T, int KIND, bool MULTI>
+__global__ void __launch_bounds__(kThreads, 10) k_step(Atoms A, Cells C, Pot P, StepParams sp, GridBarrier *bar,
+                                                   unsigned long long *stamps) {
+    __shared__ int ws[32];
+    const unsigned nb = gridDim.x;
+    const long long tid = (long long)blockIdx.x * kThreads + threadIdx.x;
+    const long long stride = (long long)nb * kThreads;
+    const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+    const bool strain = sp.strain_scale != 1.0;
+    Box *boxes = A.boxes;
+    const long long items = ((long long)A.n * T + 31) / 32 * 32;  // whole warps (lane sums)
+    const long long wn = ((long long)A.n + 31) / 32 * 32;
+    long long step = 0;
+    if (lead) step = A.flags->step;
+#define MD_SYNC()                                                   \
+    do {                                                            \
+        if (!grid_sync(bar, nb, sp.spin_limit, A.flags)) return;   \
+    } while (0)
+
+    if (stamps && lead) stamps[0] = globaltimer();
+    // first half kick + drift of the first step
+    if (strain) {
+        if (lead) strain_boxes(boxes, A.n_rep, sp.strain_scale);
+        MD_SYNC();
+    }
+    if (lead && sp.rebuild_every > 0 && (step + 1) % sp.rebuild_every == 0) A.flags->need_rebuild = 1;
+    for (long long i = tid; i < A.n; i += stride)
+        ph::kick_drift(A, boxes, (int)i, sp.half_dt, sp.dt, sp.strain_scale, strain, sp.lim2);
+    if (sp.withhold_arrival && blockIdx.x == 0) {
+        // self-test of the bounded wait: this block never arrives; it waits (bounded) until
+        // the others have given up and marked the launch aborted, then leaves.
+        if (threadIdx.x == 0) {
+            unsigned long long polls = 0;
+            while (!*reinterpret_cast<volatile int *>(&bar->abort) && ++polls < 4 * sp.spin_limit) __nanosleep(100);
+            if (gridDim.x == 1) atomicOr(&A.flags->error, FLAG_TIMEOUT);  // nobody else to give up
+        }
+        __syncthreads();
+        return;
+    }
+    MD_SYNC();
+
+    for (int s = 0; s < sp.n_steps; s++) {
+        if (stamps && lead) stamps[4 * (s + 1)] = globaltimer();
+        // ------------------------------------------------ list rebuild when flagged
+        if (ph::rebuild_requested(A.flags)) {
+            for (long long i = tid; i < A.n; i += stride) ph::bin_atom(A, C, boxes, (int)i);
+            MD_SYNC();
+            const int ntiles = ph::scan_tiles(C);
+            for (int t = blockIdx.x; t < ntiles; t += nb) ph::scan_tile_sum(C, t, ws);
+            MD_SYNC();
+            if (blockIdx.x == 0) {
+                if (threadIdx.x == 0) A.flags->max_count = 0;
+                ph::scan_top(C, ws);
+            }
+            MD_SYNC();
+            for (int t = blockIdx.x; t < ntiles; t += nb) ph::scan_apply(C, t, ws);
+            MD_SYNC();
+            for (long long i = tid; i < A.n; i += stride) ph::scatter_atom(A, C, (int)i);
+            MD_SYNC();
+            for (long long c = tid; c < C.ncell; c += stride) ph::sort_cell(A, C, (int)c);
+            MD_SYNC();
+            for (long long k = tid; k < A.n; k += stride) ph::gather_atom(A, (int)k);
+            MD_SYNC();
+            for (long long k = tid; k < A.n; k += stride) ph::copyback_atom(A, boxes, (int)k);
+            MD_SYNC();
+            int m = 0;
+            for (long long i = tid; i < wn; i += stride) {
+                const int cnt = i < A.n ? ph::build_row(A, C, boxes, (int)i, sp.rl2, sp.band_lo, sp.band_hi) : 0;
+                m = max(m, cnt);
+            }
+            m = __reduce_max_sync(0xffffffffu, m);
+            if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(&A.flags->max_count, m);
+            MD_SYNC();
+        }
+        if (stamps && lead) stamps[4 * (s + 1) + 1] = globaltimer();
+        // ------------------------------------------------ density pass
+        if (lead && A.flags->need_rebuild) {  // every block has passed the rebuild decision
+            A.flags->n_rebuilds++;
+            A.flags->need_rebuild = 0;
+        }
+        for (long long g = tid; g < items; g += stride) ps::density_item<PREC, T, KIND, MULTI>(A, P, boxes, g);
+        MD_SYNC();
+        if (stamps && lead) stamps[4 * (s + 1) + 2] = globaltimer();
+        // ------------------------------------------------ force pass (+ kicks)
+        const bool last = s == sp.n_steps - 1;
+        const bool fuse = !last && !strain;
+        if (fuse && lead && sp.rebuild_every > 0 && (step + s + 2) % sp.rebuild_every == 0)
+            A.flags->need_rebuild = 1;
+        double part[kPartials];
+#pragma unroll
+        for (int q = 0; q < kPartials; q++) part[q] = 0.0;
+        if (last && sp.energy_last) {
+            for (long long g = tid; g < items; g += stride)
+                ps::force_item<PREC, T, KIND, MULTI, true>(A, P, boxes, g, sp.half_dt, true, part);
+            eam::block_partials(part, A.partials, A.part_stride);
+        } else {
+            for (long long g = tid; g < items; g += stride) {
+                const int i = ps::force_item<PREC, T, KIND, MULTI, false>(A, P, boxes, g, sp.half_dt, true, part);
+                if (fuse && i >= 0)
+                    ph::kick_drift(A, boxes, i, sp.half_dt, sp.dt, sp.strain_scale, false, sp.lim2);
+            }
+        }
+        MD_SYNC();
+        if (stamps && lead) stamps[4 * (s + 1) + 3] = globaltimer();
+        if (!last && strain) {
+            if (lead) {
+                strain_boxes(boxes, A.n_rep, sp.strain_scale);
+                if (sp.rebuild_every > 0 && (step + s + 2) % sp.rebuild_every == 0) A.flags->need_rebuild = 1;
+            }
+            MD_SYNC();
+            for (long long i = tid; i < A.n; i += stride)
+                ph::kick_drift(A, boxes, (int)i, sp.half_dt, sp.dt, sp.strain_scale, true, sp.lim2);
+            MD_SYNC();
+        }
+    }
+    if (lead) A.flags->step = step + sp.n_steps;
+#undef MD_SYNC
+}
+
+template <int PREC, int T, int KIND, bool MULTI>
+cudaError_t launch_t(const Atoms &A, const Cells &C, const Pot &P, const StepParams &sp, GridBarrier *bar,
+                     unsigned long long *stamps, int *grid_out, cudaStream_t s) {
+    static int per_sm = -1;
+    static int n_sm = 0;
+    if (per_sm < 0) {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<PREC, T, KIND, MULTI>, kThreads, 0);
+        if (e != cudaSuccess) return e;
+    }
+    const long long work = std::max<long long>((long long)A.n * T, (long long)C.ncell);
+    const int need = (int)std::max<long long>(1, (work + kThreads - 1) / kThreads);
+    const int grid = std::max(1, std::min(per_sm * n_sm, need));
+    if (grid_out) *grid_out = grid;
+    cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(GridBarrier), s);
+    if (e != cudaSuccess) return e;
+    Atoms a = A;
+    Cells c = C;
+    Pot p = P;
+    StepParams q = sp;
+    void *args[] = {&a, &c, &p, &q, &bar, &stamps};
+    return cudaLaunchCooperativeKernel((const void *)k_step<PREC, T, KIND, MULTI>, dim3(grid), dim3(kThreads), args,
+                                       0, s);
+}
+
+template <int PREC, int T>
+cudaError_t launch_kind(const Atoms &A, const Cells &C, const Pot &P, const StepParams &sp, GridBarrier *bar,
+                        unsigned long long *stamps, int *grid_out, cudaStream_t s) {
+    if (P.kind == MD_POT_FS_ANALYTIC)
+        return launch_t<PREC, T, MD_POT_FS_ANALYTIC, false>(A, C, P, sp, bar, stamps, grid_out, s);
+    if (P.ns == 1) return launch_t<PREC, T, MD_POT_TABLES, false>(A, C, P, sp, bar, stamps, grid_out, s);
+    return launch_t<PREC, T, MD_POT_TABLES, true>(A, C, P, sp, bar, stamps, grid_out, s);
+}
+
+template <int PREC>
+cudaError_t launch_prec(const Atoms &A, const Cells &C, const Pot &P, int lanes, const StepParams &sp,
+                        GridBarrier *bar, unsigned long long *stamps, int *grid_out, cudaStream_t s) {
+    switch (lanes) {
+        case 1: return launch_kind<PREC, 1>(A, C, P, sp, bar, stamps, grid_out, s);
+        case 2: return launch_kind<PREC, 2>(A, C, P, sp, bar, stamps, grid_out, s);
+        case 4: return launch_kind<PREC, 4>(A, C, P, sp, bar, stamps, grid_out, s);
+        case 8: return launch_kind<PREC, 8>(A, C, P, sp, bar, stamps, grid_out, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace st
+}  // namespace mdk

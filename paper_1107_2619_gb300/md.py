@@ -28,8 +28,9 @@ MD_PREC_FP64, MD_PREC_MIXED = 0, 1
  MD_GET_NBR_LIST, MD_GET_SPECIES) = range(9)
 
 # functions declared in include/md.h (checked by the CPU test-suite)
-EXPORTS = ["md_abi_version", "md_status_string", "md_create", "md_build_neighbours", "md_eam_forces",
-           "md_step", "md_energy", "md_get", "md_set_state", "md_tune", "md_set_profiling", "md_get_profile",
+EXPORTS = ["md_abi_version", "md_status_string", "md_create", "md_create_batch", "md_build_neighbours",
+           "md_eam_forces", "md_step", "md_set_graph", "md_energy", "md_replica_energies", "md_get",
+           "md_set_state", "md_tune", "md_set_profiling", "md_get_profile", "md_selftest_timeout",
            "md_neighbours_noalloc", "md_last_error", "md_destroy"]
 
 
@@ -85,6 +86,15 @@ def lib():
         L.md_status_string.argtypes = [C.c_int]
         L.md_create.restype = C.c_int
         L.md_create.argtypes = [C.POINTER(md_config), C.POINTER(md_potential), P, P, P, i32, C.POINTER(P)]
+        L.md_create_batch.restype = C.c_int
+        L.md_create_batch.argtypes = [i32, C.POINTER(md_config), C.POINTER(md_potential), P, P, P, i32,
+                                      C.POINTER(P)]
+        L.md_replica_energies.restype = C.c_int
+        L.md_replica_energies.argtypes = [P, C.POINTER(md_energies)]
+        L.md_selftest_timeout.restype = C.c_int
+        L.md_selftest_timeout.argtypes = [P]
+        L.md_set_graph.restype = C.c_int
+        L.md_set_graph.argtypes = [P, i32]
         L.md_build_neighbours.restype = C.c_int
         L.md_build_neighbours.argtypes = [P]
         L.md_eam_forces.restype = C.c_int
@@ -145,6 +155,43 @@ def md_create(config: md_config, potential: md_potential, pos, vel=None, species
     if st != MD_OK:
         raise MDError(st, "md_create failed")
     return out
+
+
+def md_create_batch(configs, potential: md_potential, positions, velocities=None, species=None):
+    """One context for a batch of replicas: configs is a sequence of md_config, the others
+    sequences of host arrays (one per replica)."""
+    n = len(configs)
+    cfgs = (md_config * n)(*configs)
+    keep = [np.ascontiguousarray(a, dtype=np.float64) for a in positions]
+    pp = (C.c_void_p * n)(*[a.ctypes.data for a in keep])
+    vv = ss = None
+    if velocities is not None:
+        keep_v = [np.ascontiguousarray(a, dtype=np.float64) for a in velocities]
+        vv = (C.c_void_p * n)(*[a.ctypes.data for a in keep_v])
+    if species is not None:
+        keep_s = [np.ascontiguousarray(a, dtype=np.int32) for a in species]
+        ss = (C.c_void_p * n)(*[a.ctypes.data for a in keep_s])
+    out = C.c_void_p()
+    st = lib().md_create_batch(n, cfgs, C.byref(potential), pp, vv, ss, 0, C.byref(out))
+    if st != MD_OK:
+        raise MDError(st, "md_create_batch failed")
+    return out
+
+
+def md_replica_energies(ctx, n_replicas: int) -> list:
+    arr = (md_energies * n_replicas)()
+    _check(ctx, lib().md_replica_energies(ctx, arr))
+    return [dict(pe=e.pe, ke=e.ke, te=e.te, temperature=e.temperature, momentum=np.array(e.momentum[:]),
+                 box=np.array(e.box[:]), volume=e.volume) for e in arr]
+
+
+def md_selftest_timeout(ctx) -> int:
+    """Run the bounded-wait self-test; returns the md_status (MD_ERR_TIMEOUT expected)."""
+    return lib().md_selftest_timeout(ctx)
+
+
+def md_set_graph(ctx, on: bool):
+    _check(ctx, lib().md_set_graph(ctx, 1 if on else 0))
 
 
 def md_build_neighbours(ctx):
@@ -273,6 +320,7 @@ class System:
             pos, vel, spc = (torch.from_numpy(a).cuda() for a in (pos, vel, spc))
             torch.cuda.synchronize()
         self.ctx = md_create(self.config, pot, pos, vel, spc)
+        self.n_replicas = 1
         del keep
 
     def build_neighbours(self):
@@ -316,6 +364,12 @@ class System:
     def tune(self) -> int:
         return md_tune(self.ctx)
 
+    def set_graph(self, on: bool = True):
+        md_set_graph(self.ctx, on)
+
+    def replica_energies(self) -> list:
+        return md_replica_energies(self.ctx, self.n_replicas)
+
     def set_profiling(self, on: bool = True):
         md_set_profiling(self.ctx, on)
 
@@ -341,3 +395,22 @@ class System:
 
     def __exit__(self, *a):
         self.close()
+
+
+class Batch(System):
+    """A batch of independent replicas in one context (md_create_batch)."""
+
+    def __init__(self, workloads, precision: str = "mixed", rebuild_every: int = 0, stream=None,
+                 k_max=None, lanes_per_atom: int = 0):
+        prec = MD_PREC_FP64 if precision == "fp64" else MD_PREC_MIXED
+        w0 = workloads[0]
+        self.k_max = int(k_max or max(w.k_max for w in workloads))
+        cfgs = [make_config(w.n_atoms, w.box, w0.skin, self.k_max, w0.dt_fs, prec, rebuild_every, False,
+                            w0.strain_rate_zz, stream, lanes_per_atom) for w in workloads]
+        pot, keep = make_potential(w0.potential)
+        self.ctx = md_create_batch(cfgs, pot, [w.pos for w in workloads], [w.vel for w in workloads],
+                                   [w.species for w in workloads])
+        self.n = sum(w.n_atoms for w in workloads)
+        self.n_replicas = len(workloads)
+        self.offsets = np.concatenate([[0], np.cumsum([w.n_atoms for w in workloads])])
+        del keep

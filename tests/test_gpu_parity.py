@@ -314,7 +314,7 @@ def test_full_size_cu500k_forces_and_lists():
 
 
 # --------------------------------------------------------------------------- lanes per atom
-@pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, 32])
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_every_lane_count_matches_oracle(lanes, precision):
     w = _workload("fec")
@@ -335,7 +335,110 @@ def test_autotuner_picks_a_valid_lane_count_and_stays_exact():
     ref = oracle.forces(w.pos, w.species, w.box, w.potential, skin=w.skin, k_max=w.k_max, method="brute")
     with _gpu_system(w) as s:
         lanes = s.tune()
-        assert lanes in (1, 2, 4, 8, 16, 32)
+        assert lanes in (1, 2, 4, 8)
         s.eam_forces()
         f = s.forces()
     assert np.abs(f - ref["force"]).max() <= FP64_TOL * np.abs(ref["force"]).max()
+
+
+
+# --------------------------------------------------------------------------- persistent step
+def test_graph_replay_equals_direct_launch():
+    w = I.bcc_fe(10, seed=21)
+    with _gpu_system(w, "mixed") as a, _gpu_system(w, "mixed") as b:
+        b.set_graph(True)
+        for _ in range(3):
+            a.step(7)
+            b.step(7)
+        assert np.array_equal(a.positions(), b.positions())
+        assert a.energy()["te"] == b.energy()["te"]
+
+
+def test_profile_stamps_cover_the_phases():
+    w = I.fcc_cu(10, seed=22)
+    with _gpu_system(w, "mixed", rebuild_every=3) as s:
+        s.eam_forces()
+        s.set_profiling(True)
+        s.step(9)
+        p = s.profile()
+    assert p["n_density"] == 9 and p["n_force"] == 9
+    assert p["ms_density"] > 0 and p["ms_force"] > 0 and p["ms_rebuild"] > 0
+
+
+def test_bounded_barrier_wait_reports_timeout_and_recovers():
+    """Failure detection without a fault: one block withholds a barrier arrival, the others'
+    bounded wait runs out, the call returns MD_ERR_TIMEOUT and the context stays usable."""
+    w = I.bcc_fe(10, seed=23)
+    ref = oracle.forces(w.pos, w.species, w.box, w.potential, skin=w.skin, k_max=w.k_max)
+    with _gpu_system(w) as s:
+        s.eam_forces()
+        assert md.md_selftest_timeout(s.ctx) == md.MD_ERR_TIMEOUT
+        s.set_state(pos=w.pos, vel=w.vel)
+        s.eam_forces()
+        assert np.abs(s.forces() - ref["force"]).max() <= FP64_TOL * np.abs(ref["force"]).max()
+        s.step(3)
+
+
+def _replicas(seeds, sizes, temps):
+    ws = []
+    for seed, n, t in zip(seeds, sizes, temps):
+        ws.append(I.bcc_fe(n, seed=seed, temperature=t))
+    return ws
+
+
+def test_batch_of_replicas_matches_replicas_alone():
+    ws = _replicas([3001, 3002, 3003], [6, 9, 7], [300.0, 900.0, 600.0])
+    with md.Batch(ws, precision="fp64") as b:
+        b.step(20)
+        pos_b = b.positions()
+        per = b.replica_energies()
+        tot = b.energy()
+    off = np.concatenate([[0], np.cumsum([w.n_atoms for w in ws])])
+    pe_sum = 0.0
+    for r, w in enumerate(ws):
+        with _gpu_system(w) as s:
+            s.step(20)
+            e = s.energy()
+            assert np.abs(pos_b[off[r]:off[r + 1]] - s.positions()).max() < 1e-9
+        assert abs(per[r]["pe"] - e["pe"]) <= FP64_TOL * abs(e["pe"])
+        assert abs(per[r]["ke"] - e["ke"]) <= 1e-9 * e["ke"]
+        assert abs(per[r]["temperature"] - e["temperature"]) <= 1e-9 * e["temperature"]
+        pe_sum += e["pe"]
+    assert abs(tot["pe"] - pe_sum) <= FP64_TOL * abs(pe_sum)
+
+
+def test_batch_against_oracle_trajectories():
+    ws = _replicas([3011, 3012], [6, 8], [1200.0, 300.0])
+    with md.Batch(ws, precision="fp64") as b:
+        b.step(30)
+        pos_b = b.positions()
+    off = np.concatenate([[0], np.cumsum([w.n_atoms for w in ws])])
+    for r, w in enumerate(ws):
+        ref = oracle.run_vv(w.pos, w.vel, w.species, w.potential.masses, w.box, w.potential, w.dt_fs, 30,
+                            w.skin, w.k_max)
+        assert np.abs(pos_b[off[r]:off[r + 1]] - ref["pos"]).max() < 1e-9
+
+
+def test_full_size_fe_c_forces_and_strain_steps():
+    """bcc Fe 128^3 + 0.1 % C (4,198,498 atoms), two-species tables, in the benchmark's
+    configuration: every force (FP64 and mixed) against the oracle, then strained steps."""
+    w = I.bcc_fe_c(128, seed=4)
+    assert w.n_atoms == 2 * 128 ** 3 + 4194
+    ref = oracle.forces(w.pos, w.species, w.box, w.potential, skin=w.skin, k_max=w.k_max, method="cells")
+    fs = np.abs(ref["force"]).max()
+    with _gpu_system(w) as s:
+        pe = s.eam_forces()
+        f = s.forces()
+        cg = s.get(md.MD_GET_NBR_COUNT)
+    assert np.array_equal(cg, ref["count"])
+    assert np.abs(f - ref["force"]).max() <= FP64_TOL * fs
+    assert abs(pe - ref["pe"]) <= FP64_TOL * abs(ref["pe"])
+    with _gpu_system(w, "mixed") as s:
+        pe32 = s.eam_forces()
+        f32 = s.forces()
+        assert np.abs(f32 - ref["force"]).max() <= MIXED_FORCE_TOL * fs
+        assert abs(pe32 - ref["pe"]) <= MIXED_PE_TOL * abs(ref["pe"])
+        s.step(20)
+        e = s.energy()
+    assert abs(e["box"][2] - w.box[2] * (1 - 1e-6) ** 20) < 1e-9 * w.box[2]
+    assert np.isfinite(e["te"])
