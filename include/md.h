@@ -246,6 +246,8 @@ typedef struct {
     int64_t launches;
     int64_t n_kick, n_rebuild, n_density, n_force;
     double ms_kick, ms_rebuild, ms_density, ms_force;
+    double ms_rebuild_part[9]; /* bin, tile sums, top scan, apply, scatter, cell sort, gather,
+                                  copyback, list build */
 } md_profile;
 
 /* Turn per-kernel event timing on (1) or off (0); turning it on clears the sums. */

@@ -33,15 +33,19 @@ def _stale() -> bool:
     return any(os.path.getmtime(p) > t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = None) -> str:
-    if not force and not _stale():
+def build(force: bool = False, verbose: bool = None, out: str = None, defines=()) -> str:
+    """Compile libmd.so (to `out`, default the in-tree _build/libmd.so); `defines` are extra
+    -D macros (tuning knobs such as MD_STEP_MIN_BLOCKS)."""
+    lib = out or LIB
+    if not force and out is None and not _stale():
         return LIB
     verbose = os.environ.get("MD_BUILD_VERBOSE") == "1" if verbose is None else verbose
-    obj_dir = os.path.join(OUT_DIR, "obj")
+    obj_dir = os.path.join(os.path.dirname(lib), "obj")
     os.makedirs(obj_dir, exist_ok=True)
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
     if verbose:
         flags += ["-Xptxas", "-v"]
+    flags += [f"-D{d}" for d in defines]
 
     def compile_one(src):
         obj = os.path.join(obj_dir, os.path.basename(src)[:-3] + ".o")
@@ -55,13 +59,13 @@ def build(force: bool = False, verbose: bool = None) -> str:
     if verbose:
         for _, log in results:
             print(log)
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     r = subprocess.run(["nvcc", "-shared"] + ARCH + ["-o", tmp] + [o for o, _ in results],
                        capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -273,7 +273,7 @@ StepParams step_params(md_ctx *ctx, int n_steps) {
 // energy reduction and the copies back.  `rows` receives the partial-sum rows written.
 cudaError_t enqueue_steps(md_ctx *ctx, int n_steps, unsigned long long *stamps, int *rows) {
     const StepParams sp = step_params(ctx, n_steps);
-    cudaError_t e = reset_errors(ctx);
+    cudaError_t e = cudaSuccess;
     int grid = 0;
     if (e == cudaSuccess)
         e = launch_step(ctx->A, ctx->C, ctx->P, ctx->precision, ctx->lanes, sp, ctx->d_bar, stamps, &grid,
@@ -286,18 +286,21 @@ cudaError_t enqueue_steps(md_ctx *ctx, int n_steps, unsigned long long *stamps, 
     return e;
 }
 
-// Fold the %globaltimer stamps of one launch into the profile: per step, [start, after
-// rebuild, after density, after force]; row 0 = [launch start]; the first kick ends where
-// step 0 starts.
+// Fold the %globaltimer stamps of one launch into the profile.  Row s+1 of kStampsPerStep
+// stamps belongs to step s: [0] start, [1..9] after each rebuild sub-phase (bin, tile sums,
+// top scan, apply, scatter, cell sort, gather, copyback, list; all equal to [0] when no
+// rebuild ran), [10] after the density pass, [11] after the force pass.  Row 0 holds the
+// launch start; the first half kick ends where step 0 starts.
 void collect_stamps(md_ctx *ctx, int n_steps) {
     const unsigned long long *t = ctx->h_stamps;
-    ctx->prof.ms_kick += (t[4] - t[0]) * 1e-6;
+    ctx->prof.ms_kick += (t[kStampsPerStep] - t[0]) * 1e-6;
     ctx->prof.n_kick += 1;
     for (int s = 1; s <= n_steps; s++) {
-        const unsigned long long *r = t + 4 * s;
-        ctx->prof.ms_rebuild += (r[1] - r[0]) * 1e-6;
-        ctx->prof.ms_density += (r[2] - r[1]) * 1e-6;
-        ctx->prof.ms_force += (r[3] - r[2]) * 1e-6;
+        const unsigned long long *r = t + kStampsPerStep * s;
+        ctx->prof.ms_rebuild += (r[9] - r[0]) * 1e-6;
+        for (int q = 0; q < 9; q++) ctx->prof.ms_rebuild_part[q] += (r[q + 1] - r[q]) * 1e-6;
+        ctx->prof.ms_density += (r[10] - r[9]) * 1e-6;
+        ctx->prof.ms_force += (r[11] - r[10]) * 1e-6;
     }
     ctx->prof.n_rebuild += n_steps;
     ctx->prof.n_density += n_steps;
@@ -732,13 +735,11 @@ md_status md_step(md_ctx *ctx, int32_t n_steps) {
             drop_graphs(ctx);
         }
     }
-    if (!ctx->forces_valid) {
-        MD_CK(reset_errors(ctx));
-        MD_CK(enqueue_forces(ctx));
-    }
+    MD_CK(reset_errors(ctx));
+    if (!ctx->forces_valid) MD_CK(enqueue_forces(ctx));
     unsigned long long *stamps = nullptr;
     if (ctx->profiling) {
-        md_status st = ensure_stamps(ctx, 4 * ((size_t)n_steps + 1));
+        md_status st = ensure_stamps(ctx, kStampsPerStep * ((size_t)n_steps + 1));
         if (st != MD_OK) return st;
         stamps = ctx->d_stamps;
     }
@@ -767,7 +768,7 @@ md_status md_step(md_ctx *ctx, int32_t n_steps) {
     ctx->launches += 2;
     ctx->part_rows = rows;
     if (stamps)
-        MD_CK(cudaMemcpyAsync(ctx->h_stamps, stamps, 4 * ((size_t)n_steps + 1) * sizeof(unsigned long long),
+        MD_CK(cudaMemcpyAsync(ctx->h_stamps, stamps, kStampsPerStep * ((size_t)n_steps + 1) * sizeof(unsigned long long),
                               cudaMemcpyDeviceToHost, ctx->stream));
     md_status st = sync_and_check(ctx, ctx->cfg.strict_skin != 0);
     ctx->step += n_steps;

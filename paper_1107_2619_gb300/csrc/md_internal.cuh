@@ -22,6 +22,7 @@ enum : int32_t { FLAG_OVERFLOW = 1, FLAG_NONFINITE = 2, FLAG_TIMEOUT = 4 };
 
 constexpr int kThreads = 128;     // threads per block of the per-atom kernels
 constexpr int kPartials = 11;     // per-block FP64 partial sums: pe, sum m v^2, W(6), p(3)
+constexpr int kStampsPerStep = 12;  // %globaltimer stamps per step of the persistent kernel
 
 // Current orthorhombic box of one system (changes under the strain ramp; kept in device
 // memory so that a captured step reads the live value).

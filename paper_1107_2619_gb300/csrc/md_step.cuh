@@ -112,30 +112,44 @@ __global__ void __launch_bounds__(kThreads, 10) k_step(Atoms A, Cells C, Pot P, 
     }
     MD_SYNC();
 
+    unsigned long long *srow = nullptr;
     for (int s = 0; s < sp.n_steps; s++) {
-        if (stamps && lead) stamps[4 * (s + 1)] = globaltimer();
+        if (stamps && lead) {
+            srow = stamps + kStampsPerStep * (s + 1);
+            srow[0] = globaltimer();
+        }
+#define MD_STAMP(q) \
+    if (srow) srow[q] = globaltimer()
         // ------------------------------------------------ list rebuild when flagged
         if (ph::rebuild_requested(A.flags)) {
             for (long long i = tid; i < A.n; i += stride) ph::bin_atom(A, C, boxes, (int)i);
             MD_SYNC();
+            MD_STAMP(1);
             const int ntiles = ph::scan_tiles(C);
             for (int t = blockIdx.x; t < ntiles; t += nb) ph::scan_tile_sum(C, t, ws);
             MD_SYNC();
+            MD_STAMP(2);
             if (blockIdx.x == 0) {
                 if (threadIdx.x == 0) A.flags->max_count = 0;
                 ph::scan_top(C, ws);
             }
             MD_SYNC();
+            MD_STAMP(3);
             for (int t = blockIdx.x; t < ntiles; t += nb) ph::scan_apply(C, t, ws);
             MD_SYNC();
+            MD_STAMP(4);
             for (long long i = tid; i < A.n; i += stride) ph::scatter_atom(A, C, (int)i);
             MD_SYNC();
+            MD_STAMP(5);
             for (long long c = tid; c < C.ncell; c += stride) ph::sort_cell(A, C, (int)c);
             MD_SYNC();
+            MD_STAMP(6);
             for (long long k = tid; k < A.n; k += stride) ph::gather_atom(A, (int)k);
             MD_SYNC();
+            MD_STAMP(7);
             for (long long k = tid; k < A.n; k += stride) ph::copyback_atom(A, boxes, (int)k);
             MD_SYNC();
+            MD_STAMP(8);
             int m = 0;
             for (long long i = tid; i < wn; i += stride) {
                 const int cnt = i < A.n ? ph::build_row(A, C, boxes, (int)i, sp.rl2, sp.band_lo, sp.band_hi) : 0;
@@ -144,8 +158,11 @@ __global__ void __launch_bounds__(kThreads, 10) k_step(Atoms A, Cells C, Pot P, 
             m = __reduce_max_sync(0xffffffffu, m);
             if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(&A.flags->max_count, m);
             MD_SYNC();
+            MD_STAMP(9);
+        } else if (srow) {
+            const unsigned long long t0 = srow[0];
+            for (int q = 1; q <= 9; q++) srow[q] = t0;
         }
-        if (stamps && lead) stamps[4 * (s + 1) + 1] = globaltimer();
         // ------------------------------------------------ density pass
         if (lead && A.flags->need_rebuild) {  // every block has passed the rebuild decision
             A.flags->n_rebuilds++;
@@ -153,7 +170,7 @@ __global__ void __launch_bounds__(kThreads, 10) k_step(Atoms A, Cells C, Pot P, 
         }
         for (long long g = tid; g < items; g += stride) ps::density_item<PREC, T, KIND, MULTI>(A, P, boxes, g);
         MD_SYNC();
-        if (stamps && lead) stamps[4 * (s + 1) + 2] = globaltimer();
+        MD_STAMP(10);
         // ------------------------------------------------ force pass (+ kicks)
         const bool last = s == sp.n_steps - 1;
         const bool fuse = !last && !strain;
@@ -174,7 +191,7 @@ __global__ void __launch_bounds__(kThreads, 10) k_step(Atoms A, Cells C, Pot P, 
             }
         }
         MD_SYNC();
-        if (stamps && lead) stamps[4 * (s + 1) + 3] = globaltimer();
+        MD_STAMP(11);
         if (!last && strain) {
             if (lead) {
                 strain_boxes(boxes, A.n_rep, sp.strain_scale);
@@ -187,6 +204,7 @@ __global__ void __launch_bounds__(kThreads, 10) k_step(Atoms A, Cells C, Pot P, 
         }
     }
     if (lead) A.flags->step = step + sp.n_steps;
+#undef MD_STAMP
 #undef MD_SYNC
 }
 

@@ -60,7 +60,8 @@ class md_energies(C.Structure):
 class md_profile(C.Structure):
     _fields_ = [("launches", C.c_int64), ("n_kick", C.c_int64), ("n_rebuild", C.c_int64),
                 ("n_density", C.c_int64), ("n_force", C.c_int64), ("ms_kick", C.c_double),
-                ("ms_rebuild", C.c_double), ("ms_density", C.c_double), ("ms_force", C.c_double)]
+                ("ms_rebuild", C.c_double), ("ms_density", C.c_double), ("ms_force", C.c_double),
+                ("ms_rebuild_part", C.c_double * 9)]
 
 
 class MDError(RuntimeError):
@@ -245,7 +246,9 @@ def md_set_profiling(ctx, on: bool):
 def md_get_profile(ctx) -> dict:
     p = md_profile()
     _check(ctx, lib().md_get_profile(ctx, C.byref(p)))
-    return {k: getattr(p, k) for k, _ in md_profile._fields_}
+    d = {k: getattr(p, k) for k, _ in md_profile._fields_}
+    d["ms_rebuild_part"] = list(p.ms_rebuild_part)
+    return d
 
 
 def md_neighbours_noalloc(pos, box, r_list: float, k_max: int, count, nbr_list, stream=None) -> int:
