@@ -111,15 +111,16 @@ float ulp32(double x) {
 }
 
 // FP32 screening band of the list build (ph::build_row).  Each wrapped FP32 coordinate is
-// within u/2 of its FP64 value (u = ulp32 of the largest box edge); the FP32 difference and
-// the minimum-image shift add at most 1.5u + ulp32(r_list)/2 more, so each component of d is
-// within delta = 2u + ulp32(r_list)/2 of the FP64 one.  Then |r2_32 - r2_64| <= 2 sqrt(3) r_list
-// delta + 3 delta^2 plus the FP32 rounding of r^2 (< 6e-7 r_list^2).  The band is 4x that.
+// within u/2 of its FP64 value (u = ulp32 of the largest box edge); adding the FP32 box edge
+// for a periodic neighbour cell (itself within u/2 of the FP64 edge) rounds once more (< u)
+// and the difference once more (< ulp32(r_list)/2 near the cutoff), so each component of d is
+// within delta = 3u + ulp32(r_list)/2 of the FP64 one.  Then |r2_32 - r2_64| <= 2 sqrt(3)
+// r_list delta + 3 delta^2 plus the FP32 rounding of r^2 (< 6e-7 r_list^2).  The band is 4x.
 void list_band(const md_ctx *c, float &lo, float &hi) {
     double Lmax = 0.0;
     for (double l : c->L) Lmax = std::fmax(Lmax, l);
     double u = ulp32(Lmax);
-    double delta = 2.0 * u + 0.5 * ulp32(c->r_list);
+    double delta = 3.0 * u + 0.5 * ulp32(c->r_list);
     double bound = 2.0 * std::sqrt(3.0) * c->r_list * delta + 3.0 * delta * delta + 6e-7 * c->rl2;
     double band = 4.0 * bound;
     lo = std::nextafter((float)(c->rl2 - band), -INFINITY);
@@ -434,6 +435,7 @@ md_status create_common(md_ctx *ctx, const md_config *cfg, const md_potential *p
     chk(dalloc(ctx, &A.slot, n)); chk(dalloc(ctx, &A.order, n)); chk(dalloc(ctx, &A.count, n));
     chk(dalloc(ctx, &A.nbr, (size_t)n * cfg->k_max));
     if (n_rep > 1) chk(dalloc(ctx, &A.rep, n));
+    A.sorted = A.cell_of;  // cell_of is consumed by the scatter before the in-cell sort writes
     // partial-sum rows: a stand-alone force launch (<= 8 lanes) or a persistent grid
     const int rows = std::max(partial_blocks((int)n, 8), 8192);
     A.part_stride = rows;

@@ -91,6 +91,7 @@ struct Atoms {
     double *rho, *dF, *e_atom;
     int32_t *id, *id_tmp, *rank, *spec, *spec_tmp;
     int32_t *cell_of, *slot, *order;
+    int32_t *sorted;                         // order after the in-cell sort (aliases cell_of)
     int32_t *nbr, *count;                    // nbr[i*k_max + k], k < min(count, k_max)
     double *partials;                        // [kPartials][part_stride] per-block sums
     int part_stride;

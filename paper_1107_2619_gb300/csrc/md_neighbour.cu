@@ -61,9 +61,9 @@ __global__ void k_scatter(Atoms A, Cells C) {
 }
 
 __global__ void k_cell_sort(Atoms A, Cells C) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;   // one warp per cell
     if (c >= C.ncell || !ph::rebuild_requested(A.flags)) return;
-    ph::sort_cell(A, C, c);
+    ph::sort_cell_warp(A, C, c, threadIdx.x & 31);
 }
 
 __global__ void k_gather(Atoms A) {
@@ -109,7 +109,7 @@ cudaError_t launch_rebuild(const Atoms &A, const Cells &C, double rl2, float ban
     k_scan_apply<<<ntiles, kScanThreads, 0, s>>>(C, A.flags);
     if (A.n > 0) {
         k_scatter<<<nb, kThreads, 0, s>>>(A, C);
-        k_cell_sort<<<blocks_for(C.ncell, kThreads), kThreads, 0, s>>>(A, C);
+        k_cell_sort<<<blocks_for((long long)C.ncell * 32, kThreads), kThreads, 0, s>>>(A, C);
         k_gather<<<nb, kThreads, 0, s>>>(A);
         k_copyback<<<nb, kThreads, 0, s>>>(A);
         k_build_list<<<nb, kThreads, 0, s>>>(A, C, rl2, band_lo, band_hi);

@@ -183,24 +183,24 @@ __device__ __forceinline__ void scatter_atom(const Atoms &A, const Cells &C, int
     A.order[C.cell_start[A.cell_of[i]] + A.slot[i]] = i;
 }
 
-// Inside each cell, order the atoms by caller id (deterministic renumbering); reset the count.
-__device__ __forceinline__ void sort_cell(const Atoms &A, const Cells &C, int c) {
+// Inside each cell, order the atoms by caller id (deterministic renumbering), one warp per
+// cell: the element with key rank q (the number of smaller keys in the cell) goes to slot
+// s + q.  Keys are unique, so the ranks are a permutation.  The sorted slots are written to
+// A.sorted (A.order is read while ranking); the cell count is reset for the next build.
+__device__ __forceinline__ void sort_cell_warp(const Atoms &A, const Cells &C, int c, int lane) {
     const int s = C.cell_start[c], e = C.cell_start[c + 1];
-    for (int a = s + 1; a < e; a++) {
+    for (int a = s + lane; a < e; a += 32) {
         const int v = A.order[a];
         const int key = A.id[v];
-        int b = a - 1;
-        while (b >= s && A.id[A.order[b]] > key) {
-            A.order[b + 1] = A.order[b];
-            b--;
-        }
-        A.order[b + 1] = v;
+        int rank = 0;
+        for (int b = s; b < e; b++) rank += A.id[A.order[b]] < key ? 1 : 0;
+        A.sorted[s + rank] = v;
     }
-    C.cell_count[c] = 0;
+    if (lane == 0) C.cell_count[c] = 0;
 }
 
 __device__ __forceinline__ void gather_atom(const Atoms &A, int k) {
-    const int o = A.order[k];
+    const int o = A.sorted[k];
     A.pos_tmp[k] = A.pos[o];
     A.vel_tmp[k] = A.vel[o];
     A.force_tmp[k] = A.force[o];
@@ -237,9 +237,12 @@ __device__ __forceinline__ bool within_exact(const double4_32a &pi, const double
 }
 
 // Full list row of atom i (cell order) from the 27 cells around its cell.  Candidates are
-// screened with FP32 wrapped coordinates; only one whose FP32 r^2 lies in [band_lo, band_hi]
-// (a band wider than the proven FP32 error) is decided by the exact FP64 test, so the row is
-// the exact FP64 set.  Returns the neighbour count (rows are cut at k_max).
+// screened with FP32 wrapped coordinates, shifted by whole box edges for neighbour cells
+// across the periodic boundary (no rounding to the nearest image per candidate), and a
+// neighbour cell whose nearest face is beyond r_list (plus the band) is skipped.  Only a
+// candidate whose FP32 r^2 lies in [band_lo, band_hi] (a band wider than the proven FP32
+// error) is decided by the exact FP64 test, so the row is the exact FP64 set.  Returns the
+// neighbour count (rows are cut at k_max).
 __device__ __forceinline__ int build_row(const Atoms &A, const Cells &C, const Box *boxes, int i, double rl2,
                                          float band_lo, float band_hi) {
     const int r = replica_of(A, i);
@@ -252,30 +255,39 @@ __device__ __forceinline__ int build_row(const Atoms &A, const Cells &C, const B
     const int cy = cell_coord(pi.y, B.invL[1], ny);
     const int cz = cell_coord(pi.z, B.invL[2], nz);
     const float Lx = B.Lf[0], Ly = B.Lf[1], Lz = B.Lf[2];
-    const float ix = B.invLf[0], iy = B.invLf[1], iz = B.invLf[2];
+    const float ex = Lx / nx, ey = Ly / ny, ez = Lz / nz;     // cell edges
+    // distance from the atom to the lower / upper face of its own cell, per axis
+    const float lox = fmaxf(fi.x - cx * ex, 0.f), hix = fmaxf((cx + 1) * ex - fi.x, 0.f);
+    const float loy = fmaxf(fi.y - cy * ey, 0.f), hiy = fmaxf((cy + 1) * ey - fi.y, 0.f);
+    const float loz = fmaxf(fi.z - cz * ez, 0.f), hiz = fmaxf((cz + 1) * ez - fi.z, 0.f);
     int32_t *row = A.nbr + (size_t)i * A.k_max;
     int cnt = 0;
     for (int dz = -1; dz <= 1; dz++) {
         int z = cz + dz;
-        z += (z < 0) ? nz : 0;
-        z -= (z >= nz) ? nz : 0;
+        float sz = 0.f;
+        if (z < 0) { z += nz; sz = -Lz; }
+        if (z >= nz) { z -= nz; sz = Lz; }
+        const float mz = dz < 0 ? loz : (dz > 0 ? hiz : 0.f);
         for (int dy = -1; dy <= 1; dy++) {
             int y = cy + dy;
-            y += (y < 0) ? ny : 0;
-            y -= (y >= ny) ? ny : 0;
+            float sy = 0.f;
+            if (y < 0) { y += ny; sy = -Ly; }
+            if (y >= ny) { y -= ny; sy = Ly; }
+            const float my = dy < 0 ? loy : (dy > 0 ? hiy : 0.f);
             for (int dx = -1; dx <= 1; dx++) {
                 int x = cx + dx;
-                x += (x < 0) ? nx : 0;
-                x -= (x >= nx) ? nx : 0;
+                float sx = 0.f;
+                if (x < 0) { x += nx; sx = -Lx; }
+                if (x >= nx) { x -= nx; sx = Lx; }
+                const float mx = dx < 0 ? lox : (dx > 0 ? hix : 0.f);
+                if (fmaf(mx, mx, fmaf(my, my, mz * mz)) > band_hi) continue;  // cell out of range
                 const int c = g.base + (z * ny + y) * nx + x;
                 const int s = C.cell_start[c], e = C.cell_start[c + 1];
+                const float ox = sx - fi.x, oy = sy - fi.y, oz = sz - fi.z;
                 for (int j = s; j < e; j++) {
                     if (j == i) continue;
                     const float4 fj = A.posf[j];
-                    float ddx = fj.x - fi.x, ddy = fj.y - fi.y, ddz = fj.z - fi.z;
-                    ddx = fmaf(-Lx, rintf(ddx * ix), ddx);
-                    ddy = fmaf(-Ly, rintf(ddy * iy), ddy);
-                    ddz = fmaf(-Lz, rintf(ddz * iz), ddz);
+                    const float ddx = fj.x + ox, ddy = fj.y + oy, ddz = fj.z + oz;
                     const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
                     bool in = r2 < band_lo;
                     if (!in && r2 <= band_hi) in = within_exact(pi, A.pos[j], B, rl2);

@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(kThreads, 10) k_step(Atoms A, Cells C, Pot P, 
             for (long long i = tid; i < A.n; i += stride) ph::scatter_atom(A, C, (int)i);
             MD_SYNC();
             MD_STAMP(5);
-            for (long long c = tid; c < C.ncell; c += stride) ph::sort_cell(A, C, (int)c);
+            for (long long c = tid >> 5; c < C.ncell; c += stride >> 5) ph::sort_cell_warp(A, C, (int)c, threadIdx.x & 31);
             MD_SYNC();
             MD_STAMP(6);
             for (long long k = tid; k < A.n; k += stride) ph::gather_atom(A, (int)k);
