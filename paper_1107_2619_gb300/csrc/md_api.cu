@@ -67,6 +67,7 @@ struct md_ctx {
     md_profile prof{};
     // CUDA graphs of step sequences, keyed by the number of steps
     bool use_graph = false;
+    cudaStream_t cap_stream = nullptr;   // private stream the graphs are recorded on
     std::map<int, cudaGraphExec_t> graphs;
     std::map<int, int> graph_rows;
 };
@@ -272,17 +273,15 @@ StepParams step_params(md_ctx *ctx, int n_steps) {
 
 // The work of md_step(n) after any initial force evaluation: the persistent launch, the
 // energy reduction and the copies back.  `rows` receives the partial-sum rows written.
-cudaError_t enqueue_steps(md_ctx *ctx, int n_steps, unsigned long long *stamps, int *rows) {
+cudaError_t enqueue_steps(md_ctx *ctx, int n_steps, unsigned long long *stamps, int *rows, cudaStream_t stream) {
     const StepParams sp = step_params(ctx, n_steps);
-    cudaError_t e = cudaSuccess;
     int grid = 0;
-    if (e == cudaSuccess)
-        e = launch_step(ctx->A, ctx->C, ctx->P, ctx->precision, ctx->lanes, sp, ctx->d_bar, stamps, &grid,
-                        ctx->stream);
-    if (e == cudaSuccess) e = launch_reduce(ctx->A, grid, ctx->d_reduce, ctx->stream);
+    cudaError_t e = launch_step(ctx->A, ctx->C, ctx->P, ctx->precision, ctx->lanes, sp, ctx->d_bar, stamps, &grid,
+                                stream);
+    if (e == cudaSuccess) e = launch_reduce(ctx->A, grid, ctx->d_reduce, stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ctx->h_reduce, ctx->d_reduce, sizeof(double) * kPartials, cudaMemcpyDeviceToHost,
-                            ctx->stream);
+                            stream);
     *rows = grid;
     return e;
 }
@@ -596,6 +595,7 @@ void md_destroy(md_ctx *ctx) {
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     else cudaDeviceSynchronize();
     drop_graphs(ctx);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     for (void *p : ctx->allocs)
         if (p) cudaFree(p);
     if (ctx->d_stage) cudaFree(ctx->d_stage);
@@ -752,9 +752,10 @@ md_status md_step(md_ctx *ctx, int32_t n_steps) {
         if (it == ctx->graphs.end()) {
             cudaGraph_t g = nullptr;
             cudaGraphExec_t ge = nullptr;
-            MD_CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-            cudaError_t e = enqueue_steps(ctx, n_steps, nullptr, &rows);
-            cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
+            if (!ctx->cap_stream) MD_CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+            MD_CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = enqueue_steps(ctx, n_steps, nullptr, &rows, ctx->cap_stream);
+            cudaError_t e2 = cudaStreamEndCapture(ctx->cap_stream, &g);
             if (e == cudaSuccess) e = e2;
             if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
             if (g) cudaGraphDestroy(g);
@@ -765,7 +766,7 @@ md_status md_step(md_ctx *ctx, int32_t n_steps) {
         MD_CK(cudaGraphLaunch(it->second, ctx->stream));
         rows = ctx->graph_rows[n_steps];
     } else {
-        MD_CK(enqueue_steps(ctx, n_steps, stamps, &rows));
+        MD_CK(enqueue_steps(ctx, n_steps, stamps, &rows, ctx->stream));
     }
     ctx->launches += 2;
     ctx->part_rows = rows;

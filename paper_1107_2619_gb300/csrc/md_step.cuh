@@ -82,7 +82,6 @@ __global__ void __launch_bounds__(kThreads, 10) k_step(Atoms A, Cells C, Pot P, 
     const bool strain = sp.strain_scale != 1.0;
     Box *boxes = A.boxes;
     const long long items = ((long long)A.n * T + 31) / 32 * 32;  // whole warps (lane sums)
-    const long long wn = ((long long)A.n + 31) / 32 * 32;
     long long step = 0;
     if (lead) step = A.flags->step;
 #define MD_SYNC()                                                   \
@@ -151,9 +150,22 @@ __global__ void __launch_bounds__(kThreads, 10) k_step(Atoms A, Cells C, Pot P, 
             MD_SYNC();
             MD_STAMP(8);
             int m = 0;
-            for (long long i = tid; i < wn; i += stride) {
-                const int cnt = i < A.n ? ph::build_row(A, C, boxes, (int)i, sp.rl2, sp.band_lo, sp.band_hi) : 0;
-                m = max(m, cnt);
+            if (ph::list_lanes((double)A.n / C.ncell) == 8) {
+                const unsigned gmask = 0xffu << ((threadIdx.x & 31) & ~7u);
+                for (long long q = tid; q < ((long long)A.n * 8 + 31) / 32 * 32; q += stride) {
+                    const int i = (int)(q >> 3);
+                    const int cnt = i < A.n ? ph::build_row<8>(A, C, boxes, i, (int)(q & 7), gmask, sp.rl2,
+                                                               sp.band_lo, sp.band_hi) : 0;
+                    m = max(m, cnt);
+                }
+            } else {
+                const unsigned gmask = 0xfu << ((threadIdx.x & 31) & ~3u);
+                for (long long q = tid; q < ((long long)A.n * 4 + 31) / 32 * 32; q += stride) {
+                    const int i = (int)(q >> 2);
+                    const int cnt = i < A.n ? ph::build_row<4>(A, C, boxes, i, (int)(q & 3), gmask, sp.rl2,
+                                                               sp.band_lo, sp.band_hi) : 0;
+                    m = max(m, cnt);
+                }
             }
             m = __reduce_max_sync(0xffffffffu, m);
             if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(&A.flags->max_count, m);

@@ -13,12 +13,18 @@ from paper_1107_2619_gb300 import inputs as I, md
 pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-10
-# Mixed path: FP32 wrapped coordinates carry an absolute error of ~ulp32(L)/2 per coordinate;
-# with pair force constants of a few eV/Å^2 summed over the neighbours the force error stays
-# below 1e-4 of the largest force for box edges < 512 Å (measured values are recorded by
-# bench.py); PE is summed in FP64 from FP32 per-pair terms.
+# Mixed path: FP32 wrapped coordinates carry an absolute error of ~ulp32(L)/2 per coordinate,
+# so the force error grows with the box: it is bounded by 100 eV/Å^2 x ulp32(L_max) (the
+# measured ratio is ~24 eV/Å^2: a few pair force constants of ~10 eV/Å^2), or 1e-4 of the
+# largest force when that is larger.  PE is summed in FP64 from FP32 per-pair terms.
 MIXED_FORCE_TOL = 1e-4
 MIXED_PE_TOL = 1e-6
+
+
+def mixed_force_bound(w, fmax):
+    lmax = float(np.max(w.box))
+    ulp32 = 2.0 ** (np.floor(np.log2(lmax)) - 23)
+    return max(MIXED_FORCE_TOL * fmax, 100.0 * ulp32)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -139,7 +145,7 @@ def test_mixed_forces_within_bound(name):
         f = s.forces()
         rho = s.get(md.MD_GET_RHO)
     fs = np.abs(ref["force"]).max()
-    assert np.abs(f - ref["force"]).max() <= MIXED_FORCE_TOL * fs
+    assert np.abs(f - ref["force"]).max() <= mixed_force_bound(w, fs)
     assert abs(pe - ref["pe"]) <= MIXED_PE_TOL * abs(ref["pe"])
     assert np.abs(rho - ref["rho"]).max() <= 1e-5 * np.abs(ref["rho"]).max()
 
@@ -309,7 +315,7 @@ def test_full_size_cu500k_forces_and_lists():
     with _gpu_system(w, "mixed") as s:
         pe32 = s.eam_forces()
         f32 = s.forces()
-    assert np.abs(f32 - ref["force"]).max() <= MIXED_FORCE_TOL * fs
+    assert np.abs(f32 - ref["force"]).max() <= mixed_force_bound(w, fs)
     assert abs(pe32 - ref["pe"]) <= MIXED_PE_TOL * abs(ref["pe"])
 
 
@@ -319,13 +325,14 @@ def test_full_size_cu500k_forces_and_lists():
 def test_every_lane_count_matches_oracle(lanes, precision):
     w = _workload("fec")
     ref = oracle.forces(w.pos, w.species, w.box, w.potential, skin=w.skin, k_max=w.k_max, method="brute")
-    tol = FP64_TOL if precision == "fp64" else MIXED_FORCE_TOL
+    fs = np.abs(ref["force"]).max()
+    tol = FP64_TOL * fs if precision == "fp64" else mixed_force_bound(w, fs)
     with _gpu_system(w, precision, lanes_per_atom=lanes) as s:
         pe = s.eam_forces()
         f = s.forces()
         s.step(5)
         e = s.energy()
-    assert np.abs(f - ref["force"]).max() <= tol * np.abs(ref["force"]).max()
+    assert np.abs(f - ref["force"]).max() <= tol
     assert abs(pe - ref["pe"]) <= (FP64_TOL if precision == "fp64" else MIXED_PE_TOL) * abs(ref["pe"])
     assert np.isfinite(e["te"])
 
@@ -436,7 +443,7 @@ def test_full_size_fe_c_forces_and_strain_steps():
     with _gpu_system(w, "mixed") as s:
         pe32 = s.eam_forces()
         f32 = s.forces()
-        assert np.abs(f32 - ref["force"]).max() <= MIXED_FORCE_TOL * fs
+        assert np.abs(f32 - ref["force"]).max() <= mixed_force_bound(w, fs)
         assert abs(pe32 - ref["pe"]) <= MIXED_PE_TOL * abs(ref["pe"])
         s.step(20)
         e = s.energy()
