@@ -78,15 +78,11 @@ __global__ void k_copyback(Atoms A) {
     ph::copyback_atom(A, A.boxes, k);
 }
 
-// L lanes per atom; whole warps stay together for the final maximum.
-template <int L>
 __global__ void __launch_bounds__(kThreads) k_build_list(Atoms A, Cells C, double rl2, float band_lo,
                                                          float band_hi) {
-    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = (int)(g / L), lane = (int)(g & (L - 1));
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = i < A.n && ph::rebuild_requested(A.flags);
-    const unsigned gmask = (L == 32 ? 0xffffffffu : ((1u << L) - 1u)) << ((threadIdx.x & 31) & ~(unsigned)(L - 1));
-    const int cnt = active ? ph::build_row<L>(A, C, A.boxes, i, lane, gmask, rl2, band_lo, band_hi) : 0;
+    const int cnt = active ? ph::build_row(A, C, A.boxes, i, rl2, band_lo, band_hi) : 0;
     const int m = __reduce_max_sync(0xffffffffu, cnt);
     if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(&A.flags->max_count, m);
 }
@@ -116,10 +112,7 @@ cudaError_t launch_rebuild(const Atoms &A, const Cells &C, double rl2, float ban
         k_cell_sort<<<blocks_for((long long)C.ncell * 32, kThreads), kThreads, 0, s>>>(A, C);
         k_gather<<<nb, kThreads, 0, s>>>(A);
         k_copyback<<<nb, kThreads, 0, s>>>(A);
-        const int L = ph::list_lanes((double)A.n / C.ncell);
-        const int nbl = (int)(((long long)A.n * L + kThreads - 1) / kThreads);
-        if (L == 8) k_build_list<8><<<nbl, kThreads, 0, s>>>(A, C, rl2, band_lo, band_hi);
-        else k_build_list<4><<<nbl, kThreads, 0, s>>>(A, C, rl2, band_lo, band_hi);
+        k_build_list<<<nb, kThreads, 0, s>>>(A, C, rl2, band_lo, band_hi);
     }
     return cudaGetLastError();
 }

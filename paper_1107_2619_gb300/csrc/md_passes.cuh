@@ -52,14 +52,14 @@ __device__ __forceinline__ void density32_item(const Atoms &A, const Pot &P, con
         si = MULTI ? __float_as_int(pi.w) : 0;
         const int cnt = min(A.count[i], A.k_max);
         const int *__restrict__ row = A.nbr + (size_t)i * A.k_max;
-        for (int k = lane; k < cnt; k += T) {
-            const int j = __ldg(row + k);
-            const float4 pj = __ldg(A.posf + j);
+        unsigned viol = 0;
+        // one neighbour: phi(r) if r < r_cut, else 0 (no branch, so loads of the next pair can issue)
+        auto term = [&](const float4 &pj) -> float {
             const float dx = mi32(pj.x - pi.x, Lx, ix);
             const float dy = mi32(pj.y - pi.y, Ly, iy);
             const float dz = mi32(pj.z - pi.z, Lz, iz);
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            if (!(r2 < P.rc2f)) continue;
+            const bool inside = r2 < P.rc2f;
             const float r = r2 * rsqrtf(r2);
             float phi;
             if (KIND == MD_POT_FS_ANALYTIC) {
@@ -69,12 +69,22 @@ __device__ __forceinline__ void density32_item(const Atoms &A, const Pot &P, con
                 float t, d;
                 bool below;
                 const int kr = knot_row((r - P.r_minf) * P.inv_drf, P.nk, t, below);
-                if (below) atomicAdd(&A.flags->range_violations, 1ull);
+                viol += (below && inside) ? 1u : 0u;
                 const float4 c = phi_half32(P.VP32, (size_t)(si * P.ns + sj) * P.nk + kr);
                 phi = cubic(t, c.x, c.y, c.z, c.w, below, d);
             }
-            two_sum_add(hi, lo, phi);
+            return inside ? phi : 0.f;
+        };
+        int k = lane;
+        for (; k + T < cnt; k += 2 * T) {
+            const int j0 = __ldg(row + k), j1 = __ldg(row + k + T);
+            const float4 p0 = __ldg(A.posf + j0), p1 = __ldg(A.posf + j1);
+            const float a0 = term(p0), a1 = term(p1);
+            two_sum_add(hi, lo, a0);
+            two_sum_add(hi, lo, a1);
         }
+        if (k < cnt) two_sum_add(hi, lo, term(__ldg(A.posf + __ldg(row + k))));
+        if (viol) atomicAdd(&A.flags->range_violations, (unsigned long long)viol);
     }
     lane_sum_df<T>(hi, lo);
     if (live && lane == 0) {
@@ -105,14 +115,15 @@ __device__ __forceinline__ int force32_item(const Atoms &A, const Pot &P, const 
         const int si = MULTI ? A.spec[i] : 0;
         const int cnt = min(A.count[i], A.k_max);
         const int *__restrict__ row = A.nbr + (size_t)i * A.k_max;
-        for (int k = lane; k < cnt; k += T) {
-            const int j = __ldg(row + k);
-            const float4 pj = __ldg(A.p2f + j);
+        unsigned viol = 0;
+        // one neighbour: its pair force (zero beyond r_cut; no branch, so loads of the next
+        // pair can issue early) and, on the energy step, its energy and virial
+        auto pair = [&](int j, const float4 &pj) {
             const float dx = mi32(pj.x - pi.x, Lx, ix);
             const float dy = mi32(pj.y - pi.y, Ly, iy);
             const float dz = mi32(pj.z - pi.z, Lz, iz);
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            if (!(r2 < P.rc2f)) continue;
+            const bool inside = r2 < P.rc2f;
             const float rinv = rsqrtf(r2);
             const float r = r2 * rinv;
             const float Fpj = pj.w;
@@ -126,7 +137,7 @@ __device__ __forceinline__ int force32_item(const Atoms &A, const Pot &P, const 
                 float t;
                 bool below;
                 const int kr = knot_row((r - P.r_minf) * P.inv_drf, P.nk, t, below);
-                if (below) atomicAdd(&A.flags->range_violations, 1ull);
+                viol += (below && inside) ? 1u : 0u;
                 float cv[4], cp[4], dVk, dab;
                 row32(P.VP32, (size_t)(si * P.ns + sj) * P.nk + kr, cv, cp);
                 V = cubic(t, cv[0], cv[1], cv[2], cv[3], below, dVk);
@@ -142,12 +153,12 @@ __device__ __forceinline__ int force32_item(const Atoms &A, const Pot &P, const 
                 }
                 gg = gk * P.inv_drf;
             }
-            const float gr = gg * rinv;
+            const float gr = inside ? gg * rinv : 0.f;
             fx = fmaf(gr, dx, fx);
             fy = fmaf(gr, dy, fy);
             fz = fmaf(gr, dz, fz);
             if (ENERGY) {
-                ep = fmaf(0.5f, V, ep);
+                ep = fmaf(0.5f, inside ? V : 0.f, ep);
                 const float hg = -0.5f * gr;
                 wxx = fmaf(hg * dx, dx, wxx);
                 wyy = fmaf(hg * dy, dy, wyy);
@@ -156,7 +167,19 @@ __device__ __forceinline__ int force32_item(const Atoms &A, const Pot &P, const 
                 wxz = fmaf(hg * dx, dz, wxz);
                 wxy = fmaf(hg * dx, dy, wxy);
             }
+        };
+        int k = lane;
+        for (; k + T < cnt; k += 2 * T) {
+            const int j0 = __ldg(row + k), j1 = __ldg(row + k + T);
+            const float4 p0 = __ldg(A.p2f + j0), p1 = __ldg(A.p2f + j1);
+            pair(j0, p0);
+            pair(j1, p1);
         }
+        if (k < cnt) {
+            const int j0 = __ldg(row + k);
+            pair(j0, __ldg(A.p2f + j0));
+        }
+        if (viol) atomicAdd(&A.flags->range_violations, (unsigned long long)viol);
     }
     fx = lane_sum<T>(fx);
     fy = lane_sum<T>(fy);

@@ -236,20 +236,17 @@ __device__ __forceinline__ bool within_exact(const double4_32a &pi, const double
     return r2 < rl2;
 }
 
-// Full list row of atom i (cell order) from the 27 cells around its cell, built by a group
-// of L lanes (lane = 0..L-1 within the group, gmask = the group's lanes in the warp, every
-// lane of the group calls this with the same i).  The group reads each neighbour cell in
-// chunks of L candidates; hits are compacted in lane order with a ballot, so the row lists
-// cells in (dz, dy, dx) order and atoms in ascending slot order, the same for every L.
-// Candidates are screened with FP32 wrapped coordinates, shifted by whole box edges for
-// neighbour cells across the periodic boundary (no rounding to the nearest image per
-// candidate); a neighbour cell whose nearest face is beyond r_list (plus the band) is
-// skipped.  Only a candidate whose FP32 r^2 lies in [band_lo, band_hi] (a band wider than
-// the proven FP32 error) is decided by the exact FP64 test, so the row is the exact FP64 set.
-// Returns the neighbour count (rows are cut at k_max).
-template <int L>
-__device__ __forceinline__ int build_row(const Atoms &A, const Cells &C, const Box *boxes, int i, int lane,
-                                         unsigned gmask, double rl2, float band_lo, float band_hi) {
+// Full list row of atom i (cell order) from the 27 cells around its cell, one thread per
+// atom: the threads of a warp, whose atoms share a link cell, read the same candidate at the
+// same time (one broadcast load each).  Candidates are screened with FP32 wrapped
+// coordinates, shifted by whole box edges for neighbour cells across the periodic boundary
+// (no rounding to the nearest image per candidate); a neighbour cell whose nearest face is
+// beyond r_list (plus the band) is skipped.  Only a candidate whose FP32 r^2 lies in
+// [band_lo, band_hi] (a band wider than the proven FP32 error) is decided by the exact FP64
+// test, so the row is the exact FP64 set, listed by cell in (dz, dy, dx) order and by
+// ascending slot inside a cell.  Returns the neighbour count (rows are cut at k_max).
+__device__ __forceinline__ int build_row(const Atoms &A, const Cells &C, const Box *boxes, int i, double rl2,
+                                         float band_lo, float band_hi) {
     const int r = replica_of(A, i);
     const Box &B = boxes[r];
     const RepCells g = C.rc[r];
@@ -265,8 +262,6 @@ __device__ __forceinline__ int build_row(const Atoms &A, const Cells &C, const B
     const float lox = fmaxf(fi.x - cx * ex, 0.f), hix = fmaxf((cx + 1) * ex - fi.x, 0.f);
     const float loy = fmaxf(fi.y - cy * ey, 0.f), hiy = fmaxf((cy + 1) * ey - fi.y, 0.f);
     const float loz = fmaxf(fi.z - cz * ez, 0.f), hiz = fmaxf((cz + 1) * ez - fi.z, 0.f);
-    const unsigned shift = (threadIdx.x & 31) & ~(unsigned)(L - 1);   // first lane of the group
-    const unsigned below = (1u << lane) - 1u;
     int32_t *row = A.nbr + (size_t)i * A.k_max;
     int cnt = 0;
     for (int dz = -1; dz <= 1; dz++) {
@@ -291,33 +286,25 @@ __device__ __forceinline__ int build_row(const Atoms &A, const Cells &C, const B
                 const int c = g.base + (z * ny + y) * nx + x;
                 const int s = C.cell_start[c], e = C.cell_start[c + 1];
                 const float ox = sx - fi.x, oy = sy - fi.y, oz = sz - fi.z;
-                for (int base = s; base < e; base += L) {
-                    const int j = base + lane;
-                    bool in = false;
-                    if (j < e && j != i) {
-                        const float4 fj = A.posf[j];
-                        const float ddx = fj.x + ox, ddy = fj.y + oy, ddz = fj.z + oz;
-                        const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
-                        in = r2 < band_lo;
-                        if (!in && r2 <= band_hi) in = within_exact(pi, A.pos[j], B, rl2);
+                for (int j = s; j < e; j++) {
+                    if (j == i) continue;
+                    const float4 fj = A.posf[j];
+                    const float ddx = fj.x + ox, ddy = fj.y + oy, ddz = fj.z + oz;
+                    const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
+                    bool in = r2 < band_lo;
+                    if (!in && r2 <= band_hi) in = within_exact(pi, A.pos[j], B, rl2);
+                    if (in) {
+                        if (cnt < A.k_max) row[cnt] = j;
+                        cnt++;
                     }
-                    const unsigned hits = (__ballot_sync(gmask, in) >> shift) & ((L == 32) ? 0xffffffffu : ((1u << L) - 1u));
-                    const int at = cnt + __popc(hits & below);
-                    if (in && at < A.k_max) row[at] = j;
-                    cnt += __popc(hits);
                 }
             }
         }
     }
-    if (lane == 0) {
-        A.count[i] = cnt;
-        if (cnt > A.k_max) atomicOr(&A.flags->error, FLAG_OVERFLOW);
-    }
+    A.count[i] = cnt;
+    if (cnt > A.k_max) atomicOr(&A.flags->error, FLAG_OVERFLOW);
     return cnt;
 }
-
-// Lanes per atom of the list build: enough to cover most of a link cell in one chunk.
-__host__ __device__ inline int list_lanes(double atoms_per_cell) { return atoms_per_cell >= 10.0 ? 8 : 4; }
 
 }  // namespace ph
 }  // namespace mdk

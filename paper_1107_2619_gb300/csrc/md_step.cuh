@@ -71,8 +71,13 @@ __device__ __forceinline__ void strain_boxes(Box *boxes, int n_rep, double s) {
     }
 }
 
+// Minimum resident blocks per SM requested from the compiler (caps registers per thread).
+#ifndef MD_STEP_MIN_BLOCKS
+#define MD_STEP_MIN_BLOCKS 8
+#endif
+
 template <int PREC, int T, int KIND, bool MULTI>
-__global__ void __launch_bounds__(kThreads, 10) k_step(Atoms A, Cells C, Pot P, StepParams sp, GridBarrier *bar,
+__global__ void __launch_bounds__(kThreads, MD_STEP_MIN_BLOCKS) k_step(Atoms A, Cells C, Pot P, StepParams sp, GridBarrier *bar,
                                                    unsigned long long *stamps) {
     __shared__ int ws[32];
     const unsigned nb = gridDim.x;
@@ -150,22 +155,10 @@ __global__ void __launch_bounds__(kThreads, 10) k_step(Atoms A, Cells C, Pot P, 
             MD_SYNC();
             MD_STAMP(8);
             int m = 0;
-            if (ph::list_lanes((double)A.n / C.ncell) == 8) {
-                const unsigned gmask = 0xffu << ((threadIdx.x & 31) & ~7u);
-                for (long long q = tid; q < ((long long)A.n * 8 + 31) / 32 * 32; q += stride) {
-                    const int i = (int)(q >> 3);
-                    const int cnt = i < A.n ? ph::build_row<8>(A, C, boxes, i, (int)(q & 7), gmask, sp.rl2,
-                                                               sp.band_lo, sp.band_hi) : 0;
-                    m = max(m, cnt);
-                }
-            } else {
-                const unsigned gmask = 0xfu << ((threadIdx.x & 31) & ~3u);
-                for (long long q = tid; q < ((long long)A.n * 4 + 31) / 32 * 32; q += stride) {
-                    const int i = (int)(q >> 2);
-                    const int cnt = i < A.n ? ph::build_row<4>(A, C, boxes, i, (int)(q & 3), gmask, sp.rl2,
-                                                               sp.band_lo, sp.band_hi) : 0;
-                    m = max(m, cnt);
-                }
+            for (long long q = tid; q < ((long long)A.n + 31) / 32 * 32; q += stride) {
+                const int i = (int)q;
+                const int cnt = i < A.n ? ph::build_row(A, C, boxes, i, sp.rl2, sp.band_lo, sp.band_hi) : 0;
+                m = max(m, cnt);
             }
             m = __reduce_max_sync(0xffffffffu, m);
             if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(&A.flags->max_count, m);
