@@ -48,6 +48,14 @@ def lib():
         L.orc_pair_value.argtypes = [P, C.c_int, C.c_int, C.c_int, dbl, P]
         L.orc_embed_value.restype = dbl
         L.orc_embed_value.argtypes = [P, C.c_int, dbl, P]
+        L.orc_sur_descriptors.restype = None
+        L.orc_sur_descriptors.argtypes = [i64, P, P, P, P, i32, P, P]
+        L.orc_sur_mlp.restype = None
+        L.orc_sur_mlp.argtypes = [i64, P, P, P, P, P]
+        L.orc_sur_forces.restype = None
+        L.orc_sur_forces.argtypes = [i64, P, P, P, P, i32, P, P, P]
+        L.orc_sur_loss_grad.restype = C.c_double
+        L.orc_sur_loss_grad.argtypes = [i32, P, P, P, P, P, i32, P, P, P, P, C.c_double, C.c_double, P, P]
         L.orc_num_threads.restype = C.c_int
         L.orc_set_threads.argtypes = [C.c_int]
         _lib = L
@@ -188,3 +196,92 @@ def embed_value(pot, a, rho):
     d = np.zeros(1)
     v = lib().orc_embed_value(P.ref, a, float(rho), _p(d))
     return float(v), float(d[0])
+
+
+# ----------------------------------------------------------------------------- surrogate
+class OrcSurSpec(C.Structure):
+    _fields_ = [("nb", C.c_int32), ("h1", C.c_int32), ("h2", C.c_int32), ("pad", C.c_int32),
+                ("mu0", C.c_double), ("dmu", C.c_double), ("width", C.c_double), ("rd", C.c_double)]
+
+
+def _sur_spec(spec):
+    s = OrcSurSpec()
+    s.nb, s.h1, s.h2 = int(spec["nb"]), int(spec["h1"]), int(spec["h2"])
+    s.mu0, s.dmu, s.width, s.rd = float(spec["mu0"]), float(spec["dmu"]), float(spec["width"]), float(spec["rd"])
+    return s
+
+
+def sur_descriptors(pos, box, count, nl, spec):
+    pos, box, count, nl = _f64(pos), _f64(box), _i32(count), _i32(nl)
+    n, k_max = nl.shape
+    sp = _sur_spec(spec)
+    G = np.zeros((n, sp.nb))
+    lib().orc_sur_descriptors(n, _p(pos), _p(box), _p(count), _p(nl), k_max, C.byref(sp), _p(G))
+    return G
+
+
+def sur_mlp(G, spec, weights):
+    G, w = _f64(G), _f64(weights)
+    n = G.shape[0]
+    sp = _sur_spec(spec)
+    E, g = np.zeros(n), np.zeros((n, sp.nb))
+    lib().orc_sur_mlp(n, _p(G), C.byref(sp), _p(w), _p(E), _p(g))
+    return E, g
+
+
+def sur_forces(pos, box, count, nl, spec, grad):
+    pos, box, count, nl, grad = _f64(pos), _f64(box), _i32(count), _i32(nl), _f64(grad)
+    n, k_max = nl.shape
+    sp = _sur_spec(spec)
+    F = np.zeros((n, 3))
+    lib().orc_sur_forces(n, _p(pos), _p(box), _p(count), _p(nl), k_max, C.byref(sp), _p(grad), _p(F))
+    return F
+
+
+def surrogate(pos, box, spec, weights, k_max=64, method="cells"):
+    """Energy (sum of E_i), per-atom energies, descriptors and forces of the surrogate."""
+    count, nl, m = neighbours(pos, box, float(spec["rd"]) + float(spec.get("skin", 0.3)), k_max, method)
+    if m > k_max:
+        raise ValueError(f"neighbour list overflow: {m} > {k_max}")
+    G = sur_descriptors(pos, box, count, nl, spec)
+    E, g = sur_mlp(G, spec, weights)
+    F = sur_forces(pos, box, count, nl, spec, g)
+    return dict(energy=float(E.sum()), e_atom=E, G=G, grad=g, force=F, count=count, list=nl)
+
+
+def sur_n_params(spec):
+    nb, h1, h2 = int(spec["nb"]), int(spec["h1"]), int(spec["h2"])
+    return h1 * nb + h1 + h2 * h1 + h2 + h2 + 1
+
+
+def sur_loss_grad(frames, spec, weights, w_e=1.0, w_f=1.0, k_max=64):
+    """Loss and parameter gradient over frames = [(pos, box, e_ref, f_ref), ...]."""
+    off = np.zeros(len(frames) + 1, dtype=np.int64)
+    pos, box, cnt, lists, eref, fref = [], [], [], [], [], []
+    r_list = float(spec["rd"]) + float(spec.get("skin", 0.3))
+    for s, (p, b, e, f) in enumerate(frames):
+        c, nl, m = neighbours(p, b, r_list, k_max, "cells")
+        if m > k_max:
+            raise ValueError(f"neighbour list overflow: {m} > {k_max}")
+        off[s + 1] = off[s] + len(p)
+        pos.append(_f64(p)); box.append(_f64(b)); cnt.append(_i32(c)); lists.append(_i32(nl))
+        eref.append(float(e)); fref.append(_f64(f))
+    pos, box = np.ascontiguousarray(np.concatenate(pos)), np.ascontiguousarray(np.concatenate(box))
+    cnt, lists = np.ascontiguousarray(np.concatenate(cnt)), np.ascontiguousarray(np.concatenate(lists))
+    eref, fref = np.array(eref), np.ascontiguousarray(np.concatenate(fref))
+    sp = _sur_spec(spec)
+    w = _f64(weights)
+    grad, parts = np.zeros(sur_n_params(spec)), np.zeros(2)
+    loss = lib().orc_sur_loss_grad(len(frames), _p(off), _p(pos), _p(box), _p(cnt), _p(lists), k_max,
+                                   _p(eref), _p(fref), C.byref(sp), _p(w), float(w_e), float(w_f),
+                                   _p(grad), _p(parts))
+    return dict(loss=float(loss), loss_e=float(parts[0]), loss_f=float(parts[1]), grad=grad)
+
+
+def adam_step(w, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update (Kingma & Ba, Algorithm 1): returns new (w, m, v); t counts from 1."""
+    m = beta1 * m + (1.0 - beta1) * g
+    v = beta2 * v + (1.0 - beta2) * g * g
+    mh = m / (1.0 - beta1 ** t)
+    vh = v / (1.0 - beta2 ** t)
+    return w - lr * mh / (np.sqrt(vh) + eps), m, v

@@ -503,3 +503,247 @@ int64_t orc_run_vv(int64_t n, double *pos, double *vel, const int32_t *species, 
     free(ea);
     return viol;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Learned surrogate of the per-atom energy (not in the paper; the EAM oracle above is its
+ * reference).  Descriptor of atom i: G_ik = sum_j b_k(r_ij) over neighbours with r < rd,
+ *   b_k(r) = exp(-(r - mu_k)^2 / (2 w^2)) fc(r),  mu_k = mu0 + k dmu,
+ *   fc(r) = (cos(pi r / rd) + 1) / 2.
+ * Energy E_i = f(G_i), f a multilayer perceptron nb -> h1 -> h2 -> 1 with SiLU
+ * s(z) = z / (1 + exp(-z)):  z1 = W1 G + b1, a1 = s(z1), z2 = W2 a1 + b2, a2 = s(z2),
+ * E_i = w3 . a2 + b3.  Weights packed as W1 [h1][nb], b1 [h1], W2 [h2][h1], b2 [h2],
+ * w3 [h2], b3.  With g_i = dE_i/dG_i, the force is F = -grad sum_i E_i:
+ *   F_m = sum_j [ sum_k (g_mk + g_jk) b_k'(r_mj) ] (r_j - r_m) / r_mj.                       */
+typedef struct {
+    int32_t nb, h1, h2, pad;
+    double mu0, dmu, width, rd;
+} orc_sur_spec;
+
+static double orc_silu(double z) { return z / (1.0 + exp(-z)); }
+static double orc_dsilu(double z) {
+    double s = 1.0 / (1.0 + exp(-z));
+    return s * (1.0 + z * (1.0 - s));
+}
+
+static void orc_basis(const orc_sur_spec *sp, double r, double *b, double *db) {
+    const double pi = 3.14159265358979323846;
+    double fc = 0.5 * (cos(pi * r / sp->rd) + 1.0);
+    double dfc = -0.5 * pi / sp->rd * sin(pi * r / sp->rd);
+    double w2 = sp->width * sp->width;
+    for (int k = 0; k < sp->nb; k++) {
+        double a = r - (sp->mu0 + k * sp->dmu);
+        double e = exp(-a * a / (2.0 * w2));
+        b[k] = e * fc;
+        db[k] = e * (dfc - a / w2 * fc);
+    }
+}
+
+/* G [n][nb] from the full neighbour list. */
+void orc_sur_descriptors(int64_t n, const double *pos, const double *box, const int32_t *count,
+                         const int32_t *list, int32_t k_max, const orc_sur_spec *sp, double *G) {
+    double L[3] = {box[0], box[1], box[2]};
+    double invL[3] = {1.0 / box[0], 1.0 / box[1], 1.0 / box[2]};
+    double rd2 = sp->rd * sp->rd;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; i++) {
+        double b[256], db[256];
+        double *g = G + i * sp->nb;
+        for (int k = 0; k < sp->nb; k++) g[k] = 0.0;
+        for (int32_t q = 0; q < count[i]; q++) {
+            int64_t j = list[i * k_max + q];
+            double r2 = orc_dist2(pos, i, j, L, invL, NULL);
+            if (!(r2 < rd2)) continue;
+            orc_basis(sp, sqrt(r2), b, db);
+            for (int k = 0; k < sp->nb; k++) g[k] += b[k];
+        }
+    }
+}
+
+/* Per-atom energy E_i and input gradient g_i = dE_i/dG_i (backpropagation of the MLP). */
+void orc_sur_mlp(int64_t n, const double *G, const orc_sur_spec *sp, const double *wts, double *E,
+                 double *grad) {
+    const int nb = sp->nb, h1 = sp->h1, h2 = sp->h2;
+    const double *W1 = wts, *b1 = W1 + h1 * nb, *W2 = b1 + h1, *b2 = W2 + h2 * h1, *w3 = b2 + h2;
+    const double b3 = w3[h2];
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; i++) {
+        double z1[256], a1[256], z2[256], d2[256], d1[256];
+        const double *x = G + i * nb;
+        for (int p = 0; p < h1; p++) {
+            double s = b1[p];
+            for (int k = 0; k < nb; k++) s += W1[p * nb + k] * x[k];
+            z1[p] = s;
+            a1[p] = orc_silu(s);
+        }
+        double e = b3;
+        for (int q = 0; q < h2; q++) {
+            double s = b2[q];
+            for (int p = 0; p < h1; p++) s += W2[q * h1 + p] * a1[p];
+            z2[q] = s;
+            e += w3[q] * orc_silu(s);
+            d2[q] = w3[q] * orc_dsilu(s);
+        }
+        E[i] = e;
+        for (int p = 0; p < h1; p++) {
+            double s = 0.0;
+            for (int q = 0; q < h2; q++) s += W2[q * h1 + p] * d2[q];
+            d1[p] = s * orc_dsilu(z1[p]);
+        }
+        for (int k = 0; k < nb; k++) {
+            double s = 0.0;
+            for (int p = 0; p < h1; p++) s += W1[p * nb + k] * d1[p];
+            grad[i * nb + k] = s;
+        }
+    }
+}
+
+/* Forces from the input gradients (see the header of this section). */
+void orc_sur_forces(int64_t n, const double *pos, const double *box, const int32_t *count,
+                    const int32_t *list, int32_t k_max, const orc_sur_spec *sp, const double *grad,
+                    double *force) {
+    double L[3] = {box[0], box[1], box[2]};
+    double invL[3] = {1.0 / box[0], 1.0 / box[1], 1.0 / box[2]};
+    double rd2 = sp->rd * sp->rd;
+#pragma omp parallel for schedule(static)
+    for (int64_t m = 0; m < n; m++) {
+        double b[256], db[256], f[3] = {0.0, 0.0, 0.0};
+        for (int32_t q = 0; q < count[m]; q++) {
+            int64_t j = list[m * k_max + q];
+            double dv[3];
+            double r2 = orc_dist2(pos, m, j, L, invL, dv);
+            if (!(r2 < rd2)) continue;
+            double r = sqrt(r2);
+            orc_basis(sp, r, b, db);
+            double c = 0.0;
+            for (int k = 0; k < sp->nb; k++) c += (grad[m * sp->nb + k] + grad[j * sp->nb + k]) * db[k];
+            for (int a = 0; a < 3; a++) f[a] += c * dv[a] / r;
+        }
+        for (int a = 0; a < 3; a++) force[3 * m + a] = f[a];
+    }
+}
+
+/* Training loss of the surrogate over S frames (frame s holds atoms [off[s], off[s+1]), box
+ * box[3s..3s+2]; list rows are stored per atom, and hold frame-local atom indices):
+ *   L = wE/S sum_s ((E_s - Eref_s)/N_s)^2 + wF/(3 Ntot) sum_i |F_i - Fref_i|^2.
+ * Gradient by the chain rule.  The energy term gives dL/dE_i = c_s = 2 wE (E_s - Eref_s)/(S N_s^2).
+ * With phi_i = dL/dF_i = 2 wF (F_i - Fref_i)/(3 Ntot) and F_m = -sum_i g_i . dG_i/dr_m, the force
+ * term of dL/dtheta is -sum_i d/dtheta (g_i . u_i), u_ik = sum_m dG_ik/dr_m . phi_m
+ *   = sum_j b_k'(r_ij) (r_j - r_i)/r_ij . (phi_j - phi_i),
+ * u held fixed.  g_i . u_i is the derivative of E_i along u_i (forward tangent), so each atom
+ * contributes the parameter gradient of J_i = c_s E_i - (tangent of E_i along u_i), taken by a
+ * reverse pass through the tangent-augmented network.  grad must hold the packed weight count. */
+double orc_sur_loss_grad(int32_t n_frames, const int64_t *off, const double *pos, const double *box,
+                         const int32_t *count, const int32_t *list, int32_t k_max,
+                         const double *e_ref, const double *f_ref, const orc_sur_spec *sp,
+                         const double *wts, double w_e, double w_f, double *grad, double *parts) {
+    const int nb = sp->nb, h1 = sp->h1, h2 = sp->h2;
+    const int64_t n = off[n_frames];
+    const int64_t n_par = (int64_t)h1 * nb + h1 + (int64_t)h2 * h1 + h2 + h2 + 1;
+    const double *W1 = wts, *b1 = W1 + h1 * nb, *W2 = b1 + h1, *b2 = W2 + h2 * h1, *w3 = b2 + h2;
+    double *G = (double *)malloc(sizeof(double) * (n > 0 ? n : 1) * nb);
+    double *g = (double *)malloc(sizeof(double) * (n > 0 ? n : 1) * nb);
+    double *u = (double *)malloc(sizeof(double) * (n > 0 ? n : 1) * nb);
+    double *E = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
+    double *F = (double *)malloc(sizeof(double) * (n > 0 ? n : 1) * 3);
+    double *phi = (double *)malloc(sizeof(double) * (n > 0 ? n : 1) * 3);
+    double *c = (double *)malloc(sizeof(double) * (n_frames > 0 ? n_frames : 1));
+    double loss_e = 0.0, loss_f = 0.0;
+    for (int64_t p = 0; p < n_par; p++) grad[p] = 0.0;
+
+    for (int32_t s = 0; s < n_frames; s++) {
+        const int64_t a = off[s], m = off[s + 1] - off[s];
+        orc_sur_descriptors(m, pos + 3 * a, box + 3 * s, count + a, list + a * k_max, k_max, sp, G + a * nb);
+    }
+    orc_sur_mlp(n, G, sp, wts, E, g);
+    for (int32_t s = 0; s < n_frames; s++) {
+        const int64_t a = off[s], m = off[s + 1] - off[s];
+        orc_sur_forces(m, pos + 3 * a, box + 3 * s, count + a, list + a * k_max, k_max, sp, g + a * nb, F + 3 * a);
+        double es = 0.0;
+        for (int64_t i = a; i < a + m; i++) es += E[i];
+        double de = (es - e_ref[s]) / (double)m;
+        loss_e += de * de;
+        c[s] = 2.0 * w_e * (es - e_ref[s]) / ((double)n_frames * (double)m * (double)m);
+    }
+    loss_e *= w_e / (double)n_frames;
+    for (int64_t i = 0; i < 3 * n; i++) {
+        double d = F[i] - f_ref[i];
+        loss_f += d * d;
+        phi[i] = 2.0 * w_f * d / (3.0 * (double)n);
+    }
+    loss_f *= w_f / (3.0 * (double)n);
+
+    /* u_i from the neighbour gather */
+    for (int32_t s = 0; s < n_frames; s++) {
+        const int64_t a = off[s], m = off[s + 1] - off[s];
+        const double *ps = pos + 3 * a;
+        double L[3] = {box[3 * s], box[3 * s + 1], box[3 * s + 2]};
+        double invL[3] = {1.0 / L[0], 1.0 / L[1], 1.0 / L[2]};
+        double b[256], db[256];
+        for (int64_t i = 0; i < m; i++) {
+            double *ui = u + (a + i) * nb;
+            for (int k = 0; k < nb; k++) ui[k] = 0.0;
+            for (int32_t q = 0; q < count[a + i]; q++) {
+                int64_t j = list[(a + i) * k_max + q];
+                double dv[3];
+                double r2 = orc_dist2(ps, i, j, L, invL, dv);
+                if (!(r2 < sp->rd * sp->rd)) continue;
+                double r = sqrt(r2);
+                orc_basis(sp, r, b, db);
+                double t = 0.0;
+                for (int x = 0; x < 3; x++) t += dv[x] / r * (phi[3 * (a + j) + x] - phi[3 * (a + i) + x]);
+                for (int k = 0; k < nb; k++) ui[k] += db[k] * t;
+            }
+        }
+    }
+
+    /* per-atom reverse pass of J_i = c E_i - tangent(E_i; u_i) */
+    double *gW1 = grad, *gb1 = gW1 + h1 * nb, *gW2 = gb1 + h1, *gb2 = gW2 + h2 * h1, *gw3 = gb2 + h2,
+           *gb3 = gw3 + h2;
+    for (int32_t s = 0; s < n_frames; s++) {
+        for (int64_t i = off[s]; i < off[s + 1]; i++) {
+            double z1[256], t1[256], a1[256], ta1[256], z2[256], t2[256], a2[256], ta2[256];
+            double bz2[256], btz2[256], ba1[256], bta1[256], bz1[256], btz1[256];
+            const double *x = G + i * nb, *v = u + i * nb;
+            const double ce = c[s], ct = -1.0;
+            for (int p = 0; p < h1; p++) {
+                double sz = b1[p], st = 0.0;
+                for (int k = 0; k < nb; k++) { sz += W1[p * nb + k] * x[k]; st += W1[p * nb + k] * v[k]; }
+                z1[p] = sz; t1[p] = st;
+                a1[p] = orc_silu(sz); ta1[p] = orc_dsilu(sz) * st;
+            }
+            for (int q = 0; q < h2; q++) {
+                double sz = b2[q], st = 0.0;
+                for (int p = 0; p < h1; p++) { sz += W2[q * h1 + p] * a1[p]; st += W2[q * h1 + p] * ta1[p]; }
+                z2[q] = sz; t2[q] = st;
+                a2[q] = orc_silu(sz); ta2[q] = orc_dsilu(sz) * st;
+            }
+            /* E = w3.a2 + b3, tangent = w3.ta2 */
+            *gb3 += ce;
+            for (int q = 0; q < h2; q++) {
+                gw3[q] += ce * a2[q] + ct * ta2[q];
+                double ba2 = ce * w3[q], bta2 = ct * w3[q];
+                double sg = 1.0 / (1.0 + exp(-z2[q]));
+                double d2s = sg * (1.0 - sg) * (2.0 + z2[q] * (1.0 - 2.0 * sg)); /* SiLU'' */
+                bz2[q] = ba2 * orc_dsilu(z2[q]) + bta2 * d2s * t2[q];
+                btz2[q] = bta2 * orc_dsilu(z2[q]);
+                gb2[q] += bz2[q];
+            }
+            for (int q = 0; q < h2; q++)
+                for (int p = 0; p < h1; p++) gW2[q * h1 + p] += bz2[q] * a1[p] + btz2[q] * ta1[p];
+            for (int p = 0; p < h1; p++) {
+                double sa = 0.0, st = 0.0;
+                for (int q = 0; q < h2; q++) { sa += W2[q * h1 + p] * bz2[q]; st += W2[q * h1 + p] * btz2[q]; }
+                ba1[p] = sa; bta1[p] = st;
+                double sg = 1.0 / (1.0 + exp(-z1[p]));
+                double d2s = sg * (1.0 - sg) * (2.0 + z1[p] * (1.0 - 2.0 * sg));
+                bz1[p] = ba1[p] * orc_dsilu(z1[p]) + bta1[p] * d2s * t1[p];
+                btz1[p] = bta1[p] * orc_dsilu(z1[p]);
+                gb1[p] += bz1[p];
+                for (int k = 0; k < nb; k++) gW1[p * nb + k] += bz1[p] * x[k] + btz1[p] * v[k];
+            }
+        }
+    }
+    if (parts) { parts[0] = loss_e; parts[1] = loss_f; }
+    free(G); free(g); free(u); free(E); free(F); free(phi); free(c);
+    return loss_e + loss_f;
+}

@@ -335,3 +335,26 @@ def bcc_fe_c(n: int, seed: int, temperature: float = 600.0, c_fraction: float = 
     return Workload(name=f"bcc Fe-C {n}^3 + {n_c} C", pos=pos, vel=vel, species=species, box=box,
                     potential=pot, skin=0.3, k_max=40, dt_fs=dt_fs, steps=steps,
                     temperature=temperature, strain_rate_zz=strain_rate_zz)
+
+
+# ----------------------------------------------------------------------------- surrogate
+# Radial-basis descriptor and network shape of the learned per-atom energy: 32 Gaussians of
+# width 0.1 Å centred evenly on 1.5-3.6 Å, cosine cutoff at 4.0 Å, list radius 4.3 Å; a
+# 32-64-64-1 network.
+SUR_FE = dict(nb=32, h1=64, h2=64, mu0=1.5, dmu=2.1 / 31.0, width=0.1, rd=4.0, skin=0.3, k_max=48)
+
+
+def sur_n_params(spec=SUR_FE) -> int:
+    nb, h1, h2 = spec["nb"], spec["h1"], spec["h2"]
+    return h1 * nb + h1 + h2 * h1 + h2 + h2 + 1
+
+
+def sur_init_weights(seed: int, spec=SUR_FE, scale: float = 1.0) -> np.ndarray:
+    """Seeded Glorot-uniform weights, zero biases, packed W1 [h1][nb], b1, W2 [h2][h1], b2, w3, b3."""
+    nb, h1, h2 = spec["nb"], spec["h1"], spec["h2"]
+    parts = []
+    for s, (fan_out, fan_in) in enumerate([(h1, nb), (h2, h1), (1, h2)]):
+        lim = scale * np.sqrt(6.0 / (fan_in + fan_out))
+        w = (2.0 * random_uniform(seed, 40 + s, fan_out * fan_in) - 1.0) * lim
+        parts += [w, np.zeros(fan_out)]
+    return np.concatenate(parts)
