@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define MD_ABI_VERSION 1
+#define MD_ABI_VERSION 2
 
 typedef struct md_ctx md_ctx; /* opaque, owned by the library */
 
@@ -59,7 +59,7 @@ typedef enum {
     MD_ERR_CAPACITY = 12     /* input larger than a fixed capacity (md_neighbours_noalloc) */
 } md_status;
 
-enum { MD_POT_FS_ANALYTIC = 1, MD_POT_TABLES = 2 };
+enum { MD_POT_FS_ANALYTIC = 1, MD_POT_TABLES = 2, MD_POT_SURROGATE = 3 };
 enum { MD_PREC_FP64 = 0, MD_PREC_MIXED = 1 };
 
 /*
@@ -79,6 +79,9 @@ enum { MD_PREC_FP64 = 0, MD_PREC_MIXED = 1 };
  *     polynomial through the end values and slopes; outside the span the table
  *     continues linearly from the end knot and the event is counted
  *     (md_energies.range_violations).
+ *   kind MD_POT_SURROGATE: the learned per-atom surrogate (md_set_surrogate); one
+ *     species (n_species 1, species 0), r_cut = the descriptor cutoff rd; fs, n_knots,
+ *     r_min, rho_min, rho_max and tables are ignored.
  * The library copies the tables at md_create.
  */
 typedef struct {
@@ -286,6 +289,81 @@ md_status md_get_profile(const md_ctx *ctx, md_profile *out);
 #define MD_NOALLOC_MAX_CELLS 65536
 md_status md_neighbours_noalloc(const double *pos, int64_t n_atoms, const double *box, double r_list,
                                 int32_t k_max, int32_t *count, int32_t *list, void *stream);
+
+/* ------------------------------------------------------------------------------------
+ * Learned surrogate of the per-atom energy.  This is an addition to the paper's method,
+ * which has no counterpart: the force field of Eq. (1) is replaced by a small network of
+ * each atom's neighbour environment, trained on forces and energies of the EAM model.
+ *
+ *   G_ik = sum_{j: r_ij < rd} b_k(r_ij),  k = 0..31,
+ *   b_k(r) = exp(-(r - mu0 - k dmu)^2 / (2 width^2)) (cos(pi r / rd) + 1) / 2,
+ *   x_i = (G_i - gmu) * ginv   (per-channel standardisation),
+ *   E_i = w3 . s(W2 s(W1 x_i + b1) + b2) + b3,  s(z) = z / (1 + exp(-z)),
+ *   U = sum_i E_i,  F_m = -dU/dr_m = sum_j [sum_k (g_mk + g_jk) b_k'(r_mj)] (r_j - r_m)/r_mj,
+ *   g_i = dE_i/dG_i.
+ * theta packs W1 [64][32], b1 [64], W2 [64][64], b2 [64], w3 [64], b3 (MD_SUR_PARAMS floats).
+ * The list radius is r_cut + skin with r_cut = rd.  The forces are central pair forces, so
+ * md_energy's virial and pressure keep their meaning.  md_eam_forces and md_step of a
+ * MD_POT_SURROGATE context evaluate the surrogate; md_get(MD_GET_EATOM) gives E_i;
+ * MD_GET_RHO and MD_GET_DF are not defined for it.
+ * Network arithmetic (md_surrogate.net):
+ *   MD_SUR_FP32  FP32 on the CUDA cores (the training path);
+ *   MD_SUR_BF16  tensor cores (tcgen05): bf16 x and weights, FP32 accumulation, FP32 biases
+ *                and activations, rounded to bf16 between layers.
+ * Descriptors and gathers are FP32; positions, velocities and reductions FP64.
+ */
+#define MD_SUR_NB 32
+#define MD_SUR_H1 64
+#define MD_SUR_H2 64
+#define MD_SUR_PARAMS 6337
+enum { MD_SUR_FP32 = 0, MD_SUR_BF16 = 1 };
+enum { MD_SUR_GET_G = 0, MD_SUR_GET_DEDG = 1 };
+
+typedef struct {
+    int32_t nb, h1, h2;  /* must be MD_SUR_NB, MD_SUR_H1, MD_SUR_H2 */
+    int32_t net;         /* MD_SUR_FP32 or MD_SUR_BF16 */
+    double mu0, dmu;     /* centre of channel k: mu0 + k dmu (Å) */
+    double width;        /* Gaussian width (Å) */
+    double rd;           /* cutoff (Å); must equal the potential's r_cut */
+} md_surrogate;
+
+/* Set the network of a MD_POT_SURROGATE context.  theta: host, MD_SUR_PARAMS floats;
+ * gmu, ginv: host, MD_SUR_NB floats each, or NULL for 0 and 1.  Copied.  Resets the
+ * optimiser state.  MD_ERR_STATE for another kind of context; MD_ERR_ARG for a bad spec. */
+md_status md_set_surrogate(md_ctx *ctx, const md_surrogate *spec, const float *theta, const float *gmu,
+                           const float *ginv);
+
+/* Network parameters and standardisation into host arrays (any may be NULL). */
+md_status md_sur_get_params(md_ctx *ctx, float *theta, float *gmu, float *ginv);
+
+/* Per-channel mean and 1/standard deviation of G over all atoms at the current positions
+ * become the standardisation; the network is re-expressed for it (the same function of G:
+ * W1 and b1 change).  Resets the optimiser state. */
+md_status md_sur_standardize(md_ctx *ctx);
+
+/* md_sur_get: MD_SUR_GET_G, float [N][32] descriptors G; MD_SUR_GET_DEDG, float [N][32]
+ * dE_i/dG_i of the last force evaluation; both in the caller's atom order. */
+md_status md_sur_get(md_ctx *ctx, int32_t what, float *dst, int32_t on_device);
+
+/* Training data: reference energies e_ref [n_replicas] (one per replica of a batch context)
+ * and reference forces f_ref [N][3] (caller order) at the current positions, which are then
+ * fixed (md_step or md_set_state invalidate them: MD_ERR_STATE).  Builds the neighbour
+ * list and caches the descriptors of every atom. */
+md_status md_sur_set_reference(md_ctx *ctx, const double *e_ref, const double *f_ref, int32_t on_device);
+
+/* Loss over replicas [rep_begin, rep_end) (S replicas, Nb atoms):
+ *   L = w_e/S sum_r ((E_r - Eref_r)/N_r)^2 + w_f/(3 Nb) sum_i |F_i - Fref_i|^2,
+ * E_r = sum of E_i over replica r; loss[0], loss[1] = the two terms (host).  grad (host,
+ * MD_SUR_PARAMS floats, or NULL) = dL/dtheta, from the FP32 network. */
+md_status md_sur_loss_grad(md_ctx *ctx, int32_t rep_begin, int32_t rep_end, double w_e, double w_f,
+                           double *loss, float *grad);
+
+/* n_iter Adam steps (Kingma & Ba; beta1 0.9, beta2 0.999, eps 1e-8; learning rate lr) on
+ * the loss of minibatches of batch_reps consecutive replicas; minibatch t starts at replica
+ * batch_reps * (h(seed, t) mod floor(n_replicas / batch_reps)), h = SplitMix64.  loss (host,
+ * 2 doubles, or NULL) = the terms of the last minibatch, before its update. */
+md_status md_sur_train(md_ctx *ctx, int32_t n_iter, int32_t batch_reps, double lr, double w_e, double w_f,
+                       uint64_t seed, double *loss);
 
 /* Text of the last error of this context ("" if none).  Valid until the next call. */
 const char *md_last_error(const md_ctx *ctx);

@@ -70,6 +70,19 @@ struct md_ctx {
     cudaStream_t cap_stream = nullptr;   // private stream the graphs are recorded on
     std::map<int, cudaGraphExec_t> graphs;
     std::map<int, int> graph_rows;
+    // learned surrogate (kind MD_POT_SURROGATE)
+    bool sur = false;          // context kind
+    bool sur_set = false;      // network given
+    bool sur_img_stale = true; // bf16 operand image older than theta
+    bool sur_ref = false;      // training references valid for the current positions
+    md_surrogate sur_spec{};
+    SurNet S{};
+    float *d_theta = nullptr, *d_adam_m = nullptr, *d_adam_v = nullptr, *d_gmu = nullptr, *d_ginv = nullptr;
+    float *d_grad = nullptr;
+    unsigned char *d_img = nullptr;
+    double4_32a *d_fref = nullptr;
+    int adam_t = 0;
+    int sur_part_blocks = 0;
 };
 
 namespace {
@@ -196,9 +209,58 @@ cudaError_t enqueue_rebuild(md_ctx *ctx) {
     return launch_rebuild(ctx->A, ctx->C, ctx->rl2, lo, hi, ctx->stream);
 }
 
+// Surrogate network at the current positions (list valid): descriptors, then energies and
+// dE/dG of every atom.
+cudaError_t enqueue_sur_net(md_ctx *ctx, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    if (ctx->S.bf16 && ctx->sur_img_stale) {
+        e = launch_sur_pack(ctx->d_theta, ctx->d_img, s);
+        ctx->sur_img_stale = false;
+        ctx->launches++;
+    }
+    if (e == cudaSuccess) e = launch_sur_descriptors(ctx->A, ctx->S, 0, (int)ctx->n, s);
+    if (e == cudaSuccess)
+        e = ctx->S.bf16 ? launch_sur_net_tc(ctx->A, ctx->S, s) : launch_sur_net32(ctx->A, ctx->S, 0, (int)ctx->n, s);
+    ctx->launches += 2;
+    return e;
+}
+
+// One velocity-Verlet step of the surrogate: half kick + drift (+ skin check), list rebuild
+// when flagged (the rebuild kernels return at once otherwise), network, force + half kick.
+cudaError_t enqueue_sur_step(md_ctx *ctx, bool energy, bool scheduled_rebuild, int *rows, cudaStream_t s) {
+    cudaError_t e = launch_sur_kick_drift(ctx->A, ctx->half_dt, ctx->dt, ctx->lim2, s);
+    if (e == cudaSuccess && scheduled_rebuild) e = launch_set_rebuild(ctx->d_flags, s);
+    float lo, hi;
+    list_band(ctx, lo, hi);
+    if (e == cudaSuccess) e = launch_rebuild(ctx->A, ctx->C, ctx->rl2, lo, hi, s);
+    if (e == cudaSuccess) e = launch_clear_rebuild(ctx->d_flags, s);
+    if (e == cudaSuccess) e = enqueue_sur_net(ctx, s);
+    if (e == cudaSuccess)
+        e = launch_sur_force(ctx->A, ctx->S, 0, (int)ctx->n, true, energy, ctx->half_dt, 0.0, rows, s);
+    ctx->launches += 3 + kRebuildLaunches + (scheduled_rebuild ? 1 : 0);
+    return e;
+}
+
 // Pass 1 + pass 2 at the current positions with stand-alone kernels (rebuilding first if
 // needed), with the FP64 partial sums; enqueue only.
 cudaError_t enqueue_forces(md_ctx *ctx) {
+    if (ctx->sur) {
+        ctx->launches += 4 + kRebuildLaunches + (ctx->list_valid ? 0 : 1);
+        cudaError_t e = launch_check_displacement(ctx->A, ctx->lim2, ctx->stream);
+        if (e == cudaSuccess && !ctx->list_valid) e = launch_set_rebuild(ctx->d_flags, ctx->stream);
+        if (e == cudaSuccess) e = enqueue_rebuild(ctx);
+        if (e == cudaSuccess) e = launch_clear_rebuild(ctx->d_flags, ctx->stream);
+        if (e == cudaSuccess) e = enqueue_sur_net(ctx, ctx->stream);
+        int rows = 0;
+        if (e == cudaSuccess)
+            e = launch_sur_force(ctx->A, ctx->S, 0, (int)ctx->n, false, true, 0.0, 0.0, &rows, ctx->stream);
+        ctx->part_rows = rows;
+        if (e == cudaSuccess) e = launch_reduce(ctx->A, rows, ctx->d_reduce, ctx->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ctx->h_reduce, ctx->d_reduce, sizeof(double) * kPartials, cudaMemcpyDeviceToHost,
+                                ctx->stream);
+        return e;
+    }
     ctx->launches += 4 + kRebuildLaunches + (ctx->list_valid ? 0 : 1);
     cudaError_t e = launch_check_displacement(ctx->A, ctx->lim2, ctx->stream);
     if (e == cudaSuccess && !ctx->list_valid) e = launch_set_rebuild(ctx->d_flags, ctx->stream);
@@ -215,6 +277,7 @@ cudaError_t enqueue_forces(md_ctx *ctx) {
 }
 
 md_status compute_forces(md_ctx *ctx) {
+    if (ctx->sur && !ctx->sur_set) return fail(ctx, MD_ERR_STATE, "surrogate network not set (md_set_surrogate)");
     MD_CK(reset_errors(ctx));
     MD_CK(enqueue_forces(ctx));
     md_status s = sync_and_check(ctx, false);
@@ -274,6 +337,19 @@ StepParams step_params(md_ctx *ctx, int n_steps) {
 // The work of md_step(n) after any initial force evaluation: the persistent launch, the
 // energy reduction and the copies back.  `rows` receives the partial-sum rows written.
 cudaError_t enqueue_steps(md_ctx *ctx, int n_steps, unsigned long long *stamps, int *rows, cudaStream_t stream) {
+    if (ctx->sur) {
+        cudaError_t e = cudaSuccess;
+        const int every = ctx->cfg.rebuild_every;
+        for (int q = 0; q < n_steps && e == cudaSuccess; q++) {
+            const bool sched = every > 0 && (ctx->step + q + 1) % every == 0;
+            e = enqueue_sur_step(ctx, q == n_steps - 1, sched, rows, stream);
+        }
+        if (e == cudaSuccess) e = launch_reduce(ctx->A, *rows, ctx->d_reduce, stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ctx->h_reduce, ctx->d_reduce, sizeof(double) * kPartials, cudaMemcpyDeviceToHost,
+                                stream);
+        return e;
+    }
     const StepParams sp = step_params(ctx, n_steps);
     int grid = 0;
     cudaError_t e = launch_step(ctx->A, ctx->C, ctx->P, ctx->precision, ctx->lanes, sp, ctx->d_bar, stamps, &grid,
@@ -345,6 +421,10 @@ md_status create_common(md_ctx *ctx, const md_config *cfg, const md_potential *p
         if (ns < 1 || ns > 8 || pot->n_knots < 2 || !pot->tables || !(pot->r_cut > pot->r_min) ||
             !(pot->rho_max > pot->rho_min))
             return MD_ERR_ARG;
+    } else if (pot->kind == MD_POT_SURROGATE) {
+        if (ns != 1 || !(pot->r_cut > 0.0)) return MD_ERR_ARG;
+        if (cfg->strain_rate_zz != 0.0) return MD_ERR_ARG;
+        ctx->sur = true;
     } else {
         return MD_ERR_ARG;
     }
@@ -563,6 +643,120 @@ bool fetch(void *dst, const void *src, size_t bytes, int on_device) {
     return cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost) == cudaSuccess;
 }
 
+
+// --------------------------------------------------------------------------- surrogate
+md_status sur_alloc(md_ctx *ctx) {
+    if (ctx->d_theta) return MD_OK;
+    const int64_t n = std::max<int64_t>(ctx->n, 1);
+    const int64_t ntiles = (n + kSurTile - 1) / kSurTile;
+    SurNet &S = ctx->S;
+    cudaError_t e = cudaSuccess;
+    auto chk = [&](cudaError_t r) { if (r != cudaSuccess && e == cudaSuccess) e = r; };
+    unsigned char *Gt = nullptr;
+    float *G = nullptr, *g = nullptr, *u = nullptr, *gpart = nullptr;
+    float4 *phi = nullptr;
+    double *eref = nullptr, *ce = nullptr;
+    chk(dalloc(ctx, &ctx->d_theta, kSurParams));
+    chk(dalloc(ctx, &ctx->d_adam_m, kSurParams));
+    chk(dalloc(ctx, &ctx->d_adam_v, kSurParams));
+    chk(dalloc(ctx, &ctx->d_grad, kSurParams));
+    chk(dalloc(ctx, &ctx->d_gmu, kSurNb));
+    chk(dalloc(ctx, &ctx->d_ginv, kSurNb));
+    chk(dalloc(ctx, &ctx->d_img, kSurImgBytes));
+    chk(dalloc(ctx, &Gt, (size_t)ntiles * kSurTileBytes));
+    chk(dalloc(ctx, &G, (size_t)n * kSurNb));
+    chk(dalloc(ctx, &g, (size_t)n * kSurNb));
+    chk(dalloc(ctx, &u, (size_t)n * kSurNb));
+    chk(dalloc(ctx, &phi, n));
+    chk(dalloc(ctx, &ctx->d_fref, n));
+    chk(dalloc(ctx, &eref, ctx->n_rep));
+    chk(dalloc(ctx, &ce, 2 * (size_t)ctx->n_rep));
+    ctx->sur_part_blocks = sur_net32_blocks((int)n);
+    chk(dalloc(ctx, &gpart, (size_t)ctx->sur_part_blocks * kSurParams));
+    if (e != cudaSuccess) return fail(ctx, MD_ERR_OOM, "surrogate buffers", e);
+    chk(cudaMemset(Gt, 0, (size_t)ntiles * kSurTileBytes));
+    chk(cudaMemset(g, 0, sizeof(float) * (size_t)n * kSurNb));
+    chk(cudaMemset(phi, 0, sizeof(float4) * (size_t)n));
+    chk(cudaMemset(ce, 0, sizeof(double) * 2 * (size_t)ctx->n_rep));
+    if (e != cudaSuccess) return fail(ctx, MD_ERR_CUDA, "surrogate buffers", e);
+    S.theta = ctx->d_theta;
+    S.gmu = ctx->d_gmu;
+    S.ginv = ctx->d_ginv;
+    S.img = ctx->d_img;
+    S.Gt = Gt;
+    S.G = G;
+    S.g = g;
+    S.u = u;
+    S.phi = phi;
+    S.fref = ctx->d_fref;
+    S.eref = eref;
+    S.ce = ce;
+    S.gpart = gpart;
+    return MD_OK;
+}
+
+// Neighbour list valid for the current positions (rebuilt when any atom moved > skin/2).
+md_status sur_ensure_list(md_ctx *ctx) {
+    MD_CK(reset_errors(ctx));
+    MD_CK(launch_check_displacement(ctx->A, ctx->lim2, ctx->stream));
+    if (!ctx->list_valid) MD_CK(launch_set_rebuild(ctx->d_flags, ctx->stream));
+    MD_CK(enqueue_rebuild(ctx));
+    MD_CK(launch_clear_rebuild(ctx->d_flags, ctx->stream));
+    ctx->launches += 3 + kRebuildLaunches;
+    md_status s = sync_and_check(ctx, false);
+    if (s == MD_OK) ctx->list_valid = true;
+    return s;
+}
+
+// FP32 descriptors of every atom into S.G.
+cudaError_t sur_descriptors32(md_ctx *ctx) {
+    SurNet S = ctx->S;
+    S.bf16 = 0;
+    ctx->launches++;
+    return launch_sur_descriptors(ctx->A, S, 0, (int)ctx->n, ctx->stream);
+}
+
+// Steps 1-5 of a training pass over replicas [r0, r1): network (FP32) -> per-replica energy
+// terms -> forces and phi = dL/dF -> descriptor tangents u -> per-block parameter gradients.
+cudaError_t sur_train_pass(md_ctx *ctx, int r0, int r1, double w_e, double w_f, int *rows, int *blocks) {
+    const int a0 = (int)ctx->rep_off[r0], a1 = (int)ctx->rep_off[r1];
+    const double phi_scale = 2.0 * w_f / (3.0 * (double)std::max(a1 - a0, 1));
+    cudaError_t e = launch_sur_net32(ctx->A, ctx->S, a0, a1, ctx->stream);
+    if (e == cudaSuccess) e = launch_sur_frame_terms(ctx->A, ctx->S, ctx->d_rep_off, r0, r1, w_e, ctx->stream);
+    if (e == cudaSuccess)
+        e = launch_sur_force(ctx->A, ctx->S, a0, a1, false, false, 0.0, phi_scale, rows, ctx->stream);
+    if (e == cudaSuccess) e = launch_sur_u(ctx->A, ctx->S, a0, a1, ctx->stream);
+    if (e == cudaSuccess) e = launch_sur_train_tiles(ctx->A, ctx->S, a0, a1, blocks, ctx->stream);
+    ctx->launches += 5;
+    return e;
+}
+
+// Energy and force loss terms of the last training pass over [r0, r1) (after the stream is idle).
+md_status sur_loss_terms(md_ctx *ctx, int r0, int r1, double w_f, double *loss) {
+    std::vector<double> ce(2 * (size_t)(r1 - r0));
+    MD_CK(cudaMemcpy(ce.data(), ctx->S.ce + 2 * (size_t)r0, ce.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    double le = 0.0;
+    for (int r = 0; r < r1 - r0; r++) le += ce[2 * (size_t)r + 1];
+    const double nb = (double)std::max<int64_t>(ctx->rep_off[r1] - ctx->rep_off[r0], 1);
+    loss[0] = le;
+    loss[1] = w_f / (3.0 * nb) * ctx->h_reduce[0];
+    return MD_OK;
+}
+
+md_status sur_check_train(md_ctx *ctx, double w_e, double w_f) {
+    if (!ctx->sur || !ctx->sur_set) return fail(ctx, MD_ERR_STATE, "no surrogate network in this context");
+    if (!ctx->sur_ref) return fail(ctx, MD_ERR_STATE, "no training references for the current positions");
+    if (!(w_e >= 0.0) || !(w_f > 0.0)) return fail(ctx, MD_ERR_ARG, "loss weights: w_e >= 0 and w_f > 0");
+    return MD_OK;
+}
+
+uint64_t splitmix64(uint64_t x) {
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
 }  // namespace
 
 extern "C" {
@@ -737,15 +931,24 @@ md_status md_step(md_ctx *ctx, int32_t n_steps) {
             drop_graphs(ctx);
         }
     }
+    if (ctx->sur) {
+        if (!ctx->sur_set) return fail(ctx, MD_ERR_STATE, "surrogate network not set (md_set_surrogate)");
+        ctx->sur_ref = false;
+        if (ctx->S.bf16 && ctx->sur_img_stale) {
+            MD_CK(launch_sur_pack(ctx->d_theta, ctx->d_img, ctx->stream));
+            ctx->sur_img_stale = false;
+        }
+    }
     MD_CK(reset_errors(ctx));
     if (!ctx->forces_valid) MD_CK(enqueue_forces(ctx));
     unsigned long long *stamps = nullptr;
-    if (ctx->profiling) {
+    if (ctx->profiling && !ctx->sur) {
         md_status st = ensure_stamps(ctx, kStampsPerStep * ((size_t)n_steps + 1));
         if (st != MD_OK) return st;
         stamps = ctx->d_stamps;
     }
-    const bool graph = ctx->use_graph && !ctx->profiling && ctx->strain_scale == 1.0;
+    const bool graph = ctx->use_graph && !ctx->profiling && ctx->strain_scale == 1.0 &&
+                       !(ctx->sur && ctx->cfg.rebuild_every > 0);
     int rows = 0;
     if (graph) {
         auto it = ctx->graphs.find(n_steps);
@@ -871,6 +1074,8 @@ md_status md_get(md_ctx *ctx, int32_t what, void *dst, int32_t on_device) {
         case MD_GET_RHO:
         case MD_GET_EATOM:
         case MD_GET_DF: {
+            if (ctx->sur && what != MD_GET_EATOM)
+                return fail(ctx, MD_ERR_STATE, "rho and F' are not defined for the surrogate");
             if (!ctx->energy_valid && (s = compute_forces(ctx)) != MD_OK) return s;
             if ((s = ensure_stage(ctx, sizeof(double) * n)) != MD_OK) return s;
             const double *src = what == MD_GET_RHO ? A.rho : (what == MD_GET_EATOM ? A.e_atom : A.dF);
@@ -899,6 +1104,10 @@ md_status md_get(md_ctx *ctx, int32_t what, void *dst, int32_t on_device) {
 
 md_status md_tune(md_ctx *ctx, int32_t *lanes_out) {
     if (!ctx) return MD_ERR_ARG;
+    if (ctx->sur) {  // the surrogate's gathers use one warp per atom
+        if (lanes_out) *lanes_out = 32;
+        return MD_OK;
+    }
     md_status st = ctx->list_valid ? MD_OK : md_build_neighbours(ctx);
     if (st != MD_OK) return st;
     if (ctx->n > 0) {
@@ -937,6 +1146,7 @@ md_status md_tune(md_ctx *ctx, int32_t *lanes_out) {
 
 md_status md_selftest_timeout(md_ctx *ctx) {
     if (!ctx || ctx->n == 0) return MD_ERR_ARG;
+    if (ctx->sur) return fail(ctx, MD_ERR_STATE, "the bounded-barrier self-test runs the EAM step kernel");
     if (!ctx->forces_valid) {
         md_status st = compute_forces(ctx);
         if (st != MD_OK) return st;
@@ -994,8 +1204,206 @@ md_status md_set_state(md_ctx *ctx, const double *pos, const double *vel, const 
     }
     if (pos) MD_CK(launch_wrap(ctx->A, ctx->stream));
     MD_CK(cudaStreamSynchronize(ctx->stream));
+    if (pos) ctx->sur_ref = false;
     if (pos || force) ctx->forces_valid = (force != nullptr);
     ctx->energy_valid = false;
+    return MD_OK;
+}
+
+md_status md_set_surrogate(md_ctx *ctx, const md_surrogate *spec, const float *theta, const float *gmu,
+                           const float *ginv) {
+    if (!ctx || !spec || !theta) return MD_ERR_ARG;
+    if (!ctx->sur) return fail(ctx, MD_ERR_STATE, "not a MD_POT_SURROGATE context");
+    if (spec->nb != kSurNb || spec->h1 != kSurH1 || spec->h2 != kSurH2 ||
+        (spec->net != MD_SUR_FP32 && spec->net != MD_SUR_BF16) || !(spec->width > 0.0) ||
+        !std::isfinite(spec->mu0) || !std::isfinite(spec->dmu) || !(spec->rd > 0.0) ||
+        std::fabs(spec->rd - ctx->r_cut) > 1e-12 * ctx->r_cut)
+        return fail(ctx, MD_ERR_ARG, "surrogate spec: 32-64-64 network, width > 0, rd = the potential's r_cut");
+    for (int p = 0; p < kSurParams; p++)
+        if (!std::isfinite(theta[p])) return fail(ctx, MD_ERR_ARG, "non-finite network parameter");
+    std::vector<float> mu(kSurNb, 0.f), iv(kSurNb, 1.f);
+    for (int k = 0; k < kSurNb; k++) {
+        if (gmu) mu[k] = gmu[k];
+        if (ginv) iv[k] = ginv[k];
+        if (!std::isfinite(mu[k]) || !std::isfinite(iv[k])) return fail(ctx, MD_ERR_ARG, "non-finite standardisation");
+    }
+    md_status st = sur_alloc(ctx);
+    if (st != MD_OK) return st;
+    MD_CK(cudaMemcpy(ctx->d_theta, theta, sizeof(float) * kSurParams, cudaMemcpyHostToDevice));
+    MD_CK(cudaMemcpy(ctx->d_gmu, mu.data(), sizeof(float) * kSurNb, cudaMemcpyHostToDevice));
+    MD_CK(cudaMemcpy(ctx->d_ginv, iv.data(), sizeof(float) * kSurNb, cudaMemcpyHostToDevice));
+    MD_CK(cudaMemset(ctx->d_adam_m, 0, sizeof(float) * kSurParams));
+    MD_CK(cudaMemset(ctx->d_adam_v, 0, sizeof(float) * kSurParams));
+    ctx->adam_t = 0;
+    SurNet &S = ctx->S;
+    const double w = spec->width;
+    S.mu0 = (float)spec->mu0;
+    S.dmu = (float)spec->dmu;
+    S.inv2w2 = (float)(1.0 / (2.0 * w * w));
+    S.invw2 = (float)(1.0 / (w * w));
+    S.rd = (float)spec->rd;
+    S.rd2 = (float)(spec->rd * spec->rd);
+    S.pi_rd = (float)(3.14159265358979323846 / spec->rd);
+    S.bf16 = spec->net == MD_SUR_BF16;
+    ctx->sur_spec = *spec;
+    ctx->sur_set = true;
+    ctx->sur_img_stale = true;
+    ctx->forces_valid = ctx->energy_valid = false;
+    drop_graphs(ctx);   // graphs hold the network view by value
+    return MD_OK;
+}
+
+md_status md_sur_get_params(md_ctx *ctx, float *theta, float *gmu, float *ginv) {
+    if (!ctx) return MD_ERR_ARG;
+    if (!ctx->sur || !ctx->sur_set) return fail(ctx, MD_ERR_STATE, "no surrogate network in this context");
+    MD_CK(cudaStreamSynchronize(ctx->stream));
+    if (theta) MD_CK(cudaMemcpy(theta, ctx->d_theta, sizeof(float) * kSurParams, cudaMemcpyDeviceToHost));
+    if (gmu) MD_CK(cudaMemcpy(gmu, ctx->d_gmu, sizeof(float) * kSurNb, cudaMemcpyDeviceToHost));
+    if (ginv) MD_CK(cudaMemcpy(ginv, ctx->d_ginv, sizeof(float) * kSurNb, cudaMemcpyDeviceToHost));
+    return MD_OK;
+}
+
+md_status md_sur_standardize(md_ctx *ctx) {
+    if (!ctx) return MD_ERR_ARG;
+    if (!ctx->sur || !ctx->sur_set) return fail(ctx, MD_ERR_STATE, "no surrogate network in this context");
+    if (ctx->n == 0) return MD_OK;
+    md_status st = sur_ensure_list(ctx);
+    if (st != MD_OK) return st;
+    MD_CK(sur_descriptors32(ctx));
+    const int blocks = std::min(1024, blocks_for(ctx->n, kThreads / 32));
+    const size_t bytes = sizeof(double) * 2 * kSurNb * blocks;
+    if ((st = ensure_stage(ctx, bytes)) != MD_OK) return st;
+    MD_CK(launch_sur_stats(ctx->A, ctx->S, static_cast<double *>(ctx->d_stage), blocks, ctx->stream));
+    ctx->launches++;
+    std::vector<double> part(2 * kSurNb * (size_t)blocks);
+    MD_CK(cudaMemcpyAsync(part.data(), ctx->d_stage, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    MD_CK(cudaStreamSynchronize(ctx->stream));
+    std::vector<float> th(kSurParams), mu0(kSurNb), iv0(kSurNb), mu1(kSurNb), iv1(kSurNb);
+    MD_CK(cudaMemcpy(th.data(), ctx->d_theta, sizeof(float) * kSurParams, cudaMemcpyDeviceToHost));
+    MD_CK(cudaMemcpy(mu0.data(), ctx->d_gmu, sizeof(float) * kSurNb, cudaMemcpyDeviceToHost));
+    MD_CK(cudaMemcpy(iv0.data(), ctx->d_ginv, sizeof(float) * kSurNb, cudaMemcpyDeviceToHost));
+    for (int k = 0; k < kSurNb; k++) {
+        double s1 = 0.0, s2 = 0.0;
+        for (int b = 0; b < blocks; b++) {
+            s1 += part[(size_t)b * 2 * kSurNb + k];
+            s2 += part[(size_t)b * 2 * kSurNb + kSurNb + k];
+        }
+        const double mean = s1 / (double)ctx->n;
+        const double var = std::fmax(s2 / (double)ctx->n - mean * mean, 0.0);
+        mu1[k] = (float)mean;
+        iv1[k] = (float)(1.0 / std::fmax(std::sqrt(var), 1e-3));   // near-empty channels stay near 0
+    }
+    // same function of G: W1' = W1 ginv0 / ginv1,  b1' = b1 + W1 ginv0 (mu1 - mu0)
+    for (int p = 0; p < kSurH1; p++) {
+        double b = th[kSurH1 * kSurNb + p];
+        for (int k = 0; k < kSurNb; k++) {
+            const double w = th[p * kSurNb + k];
+            b += w * iv0[k] * ((double)mu1[k] - (double)mu0[k]);
+            th[p * kSurNb + k] = (float)(w * iv0[k] / iv1[k]);
+        }
+        th[kSurH1 * kSurNb + p] = (float)b;
+    }
+    MD_CK(cudaMemcpy(ctx->d_theta, th.data(), sizeof(float) * kSurParams, cudaMemcpyHostToDevice));
+    MD_CK(cudaMemcpy(ctx->d_gmu, mu1.data(), sizeof(float) * kSurNb, cudaMemcpyHostToDevice));
+    MD_CK(cudaMemcpy(ctx->d_ginv, iv1.data(), sizeof(float) * kSurNb, cudaMemcpyHostToDevice));
+    MD_CK(cudaMemset(ctx->d_adam_m, 0, sizeof(float) * kSurParams));
+    MD_CK(cudaMemset(ctx->d_adam_v, 0, sizeof(float) * kSurParams));
+    ctx->adam_t = 0;
+    ctx->sur_img_stale = true;
+    ctx->forces_valid = ctx->energy_valid = false;
+    return MD_OK;
+}
+
+md_status md_sur_get(md_ctx *ctx, int32_t what, float *dst, int32_t on_device) {
+    if (!ctx || (!dst && ctx->n > 0)) return MD_ERR_ARG;
+    if (!ctx->sur || !ctx->sur_set) return fail(ctx, MD_ERR_STATE, "no surrogate network in this context");
+    if (what != MD_SUR_GET_G && what != MD_SUR_GET_DEDG) return fail(ctx, MD_ERR_ARG, "unknown md_sur_get selector");
+    if (ctx->n == 0) return MD_OK;
+    md_status st;
+    if (what == MD_SUR_GET_G) {
+        if ((st = sur_ensure_list(ctx)) != MD_OK) return st;
+        MD_CK(sur_descriptors32(ctx));
+    } else if (!ctx->forces_valid && (st = compute_forces(ctx)) != MD_OK) {
+        return st;
+    }
+    const size_t bytes = sizeof(float) * (size_t)ctx->n * kSurNb;
+    if ((st = ensure_stage(ctx, bytes)) != MD_OK) return st;
+    MD_CK(launch_sur_unsort_rows(ctx->A, what == MD_SUR_GET_G ? ctx->S.G : ctx->S.g,
+                                 static_cast<float *>(ctx->d_stage), ctx->stream));
+    ctx->launches++;
+    return copy_out(ctx, ctx->d_stage, dst, bytes, on_device);
+}
+
+md_status md_sur_set_reference(md_ctx *ctx, const double *e_ref, const double *f_ref, int32_t on_device) {
+    if (!ctx || !e_ref || (!f_ref && ctx->n > 0)) return MD_ERR_ARG;
+    if (!ctx->sur || !ctx->sur_set) return fail(ctx, MD_ERR_STATE, "no surrogate network in this context");
+    md_status st = sur_ensure_list(ctx);
+    if (st != MD_OK) return st;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    MD_CK(cudaMemcpyAsync(ctx->S.eref, e_ref, sizeof(double) * ctx->n_rep, kind, ctx->stream));
+    if (ctx->n > 0) {
+        if ((st = ensure_stage(ctx, sizeof(double) * 3 * ctx->n)) != MD_OK) return st;
+        MD_CK(cudaMemcpyAsync(ctx->d_stage, f_ref, sizeof(double) * 3 * ctx->n, kind, ctx->stream));
+        MD_CK(launch_sort_in_vec(ctx->A, static_cast<const double *>(ctx->d_stage), ctx->d_fref, ctx->stream));
+        MD_CK(sur_descriptors32(ctx));
+        ctx->launches++;
+    }
+    MD_CK(cudaStreamSynchronize(ctx->stream));
+    ctx->sur_ref = true;
+    return MD_OK;
+}
+
+md_status md_sur_loss_grad(md_ctx *ctx, int32_t rep_begin, int32_t rep_end, double w_e, double w_f,
+                           double *loss, float *grad) {
+    if (!ctx) return MD_ERR_ARG;
+    md_status st = sur_check_train(ctx, w_e, w_f);
+    if (st != MD_OK) return st;
+    if (rep_begin < 0 || rep_end > ctx->n_rep || rep_begin >= rep_end) return fail(ctx, MD_ERR_ARG, "replica range");
+    MD_CK(reset_errors(ctx));
+    int rows = 0, blocks = 0;
+    MD_CK(sur_train_pass(ctx, rep_begin, rep_end, w_e, w_f, &rows, &blocks));
+    MD_CK(launch_sur_update(ctx->S, ctx->d_theta, ctx->d_adam_m, ctx->d_adam_v, ctx->d_grad, blocks, 1, 0.f,
+                            ctx->stream));
+    MD_CK(launch_reduce(ctx->A, rows, ctx->d_reduce, ctx->stream));
+    MD_CK(cudaMemcpyAsync(ctx->h_reduce, ctx->d_reduce, sizeof(double) * kPartials, cudaMemcpyDeviceToHost,
+                          ctx->stream));
+    ctx->launches += 2;
+    ctx->forces_valid = ctx->energy_valid = false;   // forces and energies of a sub-range only
+    st = sync_and_check(ctx, false);
+    if (st != MD_OK) return st;
+    if (grad) MD_CK(cudaMemcpy(grad, ctx->d_grad, sizeof(float) * kSurParams, cudaMemcpyDeviceToHost));
+    if (loss) return sur_loss_terms(ctx, rep_begin, rep_end, w_f, loss);
+    return MD_OK;
+}
+
+md_status md_sur_train(md_ctx *ctx, int32_t n_iter, int32_t batch_reps, double lr, double w_e, double w_f,
+                       uint64_t seed, double *loss) {
+    if (!ctx || n_iter < 0 || batch_reps < 1) return MD_ERR_ARG;
+    md_status st = sur_check_train(ctx, w_e, w_f);
+    if (st != MD_OK) return st;
+    if (batch_reps > ctx->n_rep || !(lr > 0.0)) return fail(ctx, MD_ERR_ARG, "batch size or learning rate");
+    if (n_iter == 0) return MD_OK;
+    const uint64_t nbatch = (uint64_t)(ctx->n_rep / batch_reps);
+    MD_CK(reset_errors(ctx));
+    int rows = 0, blocks = 0, r0 = 0;
+    for (int it = 0; it < n_iter; it++) {
+        r0 = (int)(splitmix64(seed + (uint64_t)it) % nbatch) * batch_reps;
+        MD_CK(sur_train_pass(ctx, r0, r0 + batch_reps, w_e, w_f, &rows, &blocks));
+        if (it == n_iter - 1) {
+            MD_CK(launch_reduce(ctx->A, rows, ctx->d_reduce, ctx->stream));
+            MD_CK(cudaMemcpyAsync(ctx->h_reduce, ctx->d_reduce, sizeof(double) * kPartials, cudaMemcpyDeviceToHost,
+                                  ctx->stream));
+            ctx->launches++;
+        }
+        MD_CK(launch_sur_update(ctx->S, ctx->d_theta, ctx->d_adam_m, ctx->d_adam_v, nullptr, blocks, ++ctx->adam_t,
+                                (float)lr, ctx->stream));
+        ctx->launches++;
+    }
+    ctx->sur_img_stale = true;
+    ctx->forces_valid = ctx->energy_valid = false;
+    st = sync_and_check(ctx, false);
+    if (st != MD_OK) return st;
+    if (loss) return sur_loss_terms(ctx, r0, r0 + batch_reps, w_f, loss);
     return MD_OK;
 }
 

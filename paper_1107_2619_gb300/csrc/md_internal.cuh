@@ -144,6 +144,56 @@ cudaError_t launch_step(const Atoms &A, const Cells &C, const Pot &P, int precis
                         cudaStream_t s);
 int step_grid(const Pot &P, int precision, int lanes);   // blocks of the persistent launch
 
+// ---------------------------------------------------------------- learned surrogate
+// Per-atom energy E_i = f(x_i) of standardised radial-basis descriptors x_ik = (G_ik - gmu_k) ginv_k,
+// G_ik = sum_j b_k(r_ij), b_k(r) = exp(-(r - mu_k)^2 / (2 w^2)) (cos(pi r / rd) + 1) / 2 for r < rd;
+// f is a 32-64-64-1 SiLU network with parameters theta, packed W1 [64][32], b1, W2 [64][64], b2,
+// w3 [64], b3.  The input gradient kept per atom is the one with respect to G (dE_i/dx_i * ginv).
+constexpr int kSurNb = 32, kSurH1 = 64, kSurH2 = 64;
+constexpr int kSurParams = kSurH1 * kSurNb + kSurH1 + kSurH2 * kSurH1 + kSurH2 + kSurH2 + 1;  // 6337
+constexpr int kSurTile = 128;                      // atoms per tensor-core tile
+constexpr int kSurTileBytes = kSurTile * kSurNb * 2;  // bf16 descriptor tile, core-matrix layout
+// bf16 operand image of the tensor-core network, each matrix N x K in the no-swizzle
+// K-major core-matrix layout: W1 (64 x 32), W2 (64 x 64), W2^T (64 x 64), W1^T (32 x 64)
+constexpr int kSurImgW1 = 0, kSurImgW2 = 4096, kSurImgW2T = 12288, kSurImgW1T = 20480, kSurImgBytes = 24576;
+
+struct SurNet {
+    float mu0, dmu, inv2w2, invw2, rd, rd2, pi_rd;
+    int bf16;                 // 1: tensor-core BF16 network, 0: FP32 network
+    const float *theta;       // [kSurParams] parameters (FP32 master)
+    const float *gmu, *ginv;  // [kSurNb] input standardisation
+    const unsigned char *img; // [kSurImgBytes] bf16 operands (from theta)
+    unsigned char *Gt;        // bf16 descriptor tiles [ceil(n/128)][kSurTileBytes]
+    float *G;                 // FP32 descriptors [n][32] (FP32 network and training)
+    float *g;                 // dE_i/dG_i [n][32]
+    float4 *phi;              // training: dL/dF_i
+    float *u;                 // training: [n][32]
+    const double4_32a *fref;  // training: reference forces (cell order)
+    double *eref;             // training: reference energies [n_rep]
+    double *ce;               // training: per replica [2 r] = dL/dE_i, [2 r + 1] = its energy-loss term
+    float *gpart;             // training: per-block parameter gradients [blocks][kSurParams]
+};
+
+// Surrogate launchers (md_sur_*.cu).  Atom ranges [a0, a1) are contiguous replicas.
+cudaError_t launch_sur_kick_drift(const Atoms &A, double half_dt, double dt, double lim2, cudaStream_t s);
+cudaError_t launch_sur_descriptors(const Atoms &A, const SurNet &S, int a0, int a1, cudaStream_t s);
+cudaError_t launch_sur_net32(const Atoms &A, const SurNet &S, int a0, int a1, cudaStream_t s);
+cudaError_t launch_sur_net_tc(const Atoms &A, const SurNet &S, cudaStream_t s);
+cudaError_t launch_sur_force(const Atoms &A, const SurNet &S, int a0, int a1, bool kick, bool energy,
+                             double half_dt, double phi_scale, int *rows_out, cudaStream_t s);
+cudaError_t launch_sur_frame_terms(const Atoms &A, const SurNet &S, const int32_t *rep_off, int r0, int r1,
+                                   double w_e, cudaStream_t s);
+cudaError_t launch_sur_u(const Atoms &A, const SurNet &S, int a0, int a1, cudaStream_t s);
+cudaError_t launch_sur_train_tiles(const Atoms &A, const SurNet &S, int a0, int a1, int *blocks_out,
+                                   cudaStream_t s);
+cudaError_t launch_sur_update(const SurNet &S, float *theta, float *adam_m, float *adam_v, float *grad_out,
+                              int blocks, int t, float lr, cudaStream_t s);
+cudaError_t launch_sur_pack(const float *theta, unsigned char *img, cudaStream_t s);
+cudaError_t launch_sur_stats(const Atoms &A, const SurNet &S, double *part, int blocks, cudaStream_t s);
+cudaError_t launch_sur_unsort_rows(const Atoms &A, const float *src, float *dst, cudaStream_t s);
+int sur_net32_blocks(int n_atoms);
+int sur_force_blocks(int n_atoms);
+
 inline int blocks_for(long long n, int threads) { return (int)((n + threads - 1) / threads); }
 
 }  // namespace mdk

@@ -121,6 +121,7 @@ SC_CU = dict(eps=1.2382e-2, c=39.432, a=3.61, n=9, m=6)
 
 POT_FS_ANALYTIC = 1
 POT_TABLES = 2
+POT_SURROGATE = 3
 
 
 @dataclasses.dataclass
@@ -358,3 +359,15 @@ def sur_init_weights(seed: int, spec=SUR_FE, scale: float = 1.0) -> np.ndarray:
         w = (2.0 * random_uniform(seed, 40 + s, fan_out * fan_in) - 1.0) * lim
         parts += [w, np.zeros(fan_out)]
     return np.concatenate(parts)
+
+
+def surrogate_potential(spec=SUR_FE) -> Potential:
+    """The potential record of a surrogate context: Fe mass, range = descriptor cutoff."""
+    return Potential(kind=POT_SURROGATE, atomic_numbers=np.array([26], dtype=np.int32),
+                     masses=np.array([MASS_AMU[26]]), r_cut=float(spec["rd"]))
+
+
+def as_surrogate(w: Workload, spec=SUR_FE) -> Workload:
+    """The same atoms with the surrogate's potential record, list skin and capacity."""
+    return dataclasses.replace(w, potential=surrogate_potential(spec), skin=float(spec["skin"]),
+                               k_max=int(spec["k_max"]), name=w.name + " (surrogate)")

@@ -22,7 +22,10 @@ MD_OK, MD_ERR_ARG, MD_ERR_SPECIES, MD_ERR_BOX, MD_ERR_NBR_OVERFLOW = 0, 1, 2, 3,
 MD_ERR_SKIN, MD_ERR_NONFINITE, MD_ERR_TABLE_RANGE, MD_ERR_TIMEOUT = 5, 6, 7, 8
 MD_ERR_CUDA, MD_ERR_OOM, MD_ERR_STATE, MD_ERR_CAPACITY = 9, 10, 11, 12
 MD_NOALLOC_MAX_ATOMS, MD_NOALLOC_MAX_CELLS = 131072, 65536
-MD_POT_FS_ANALYTIC, MD_POT_TABLES = 1, 2
+MD_POT_FS_ANALYTIC, MD_POT_TABLES, MD_POT_SURROGATE = 1, 2, 3
+MD_SUR_FP32, MD_SUR_BF16 = 0, 1
+MD_SUR_GET_G, MD_SUR_GET_DEDG = 0, 1
+MD_SUR_NB, MD_SUR_H1, MD_SUR_H2, MD_SUR_PARAMS = 32, 64, 64, 6337
 MD_PREC_FP64, MD_PREC_MIXED = 0, 1
 (MD_GET_POS, MD_GET_VEL, MD_GET_FORCE, MD_GET_RHO, MD_GET_EATOM, MD_GET_DF, MD_GET_NBR_COUNT,
  MD_GET_NBR_LIST, MD_GET_SPECIES) = range(9)
@@ -31,7 +34,9 @@ MD_PREC_FP64, MD_PREC_MIXED = 0, 1
 EXPORTS = ["md_abi_version", "md_status_string", "md_create", "md_create_batch", "md_build_neighbours",
            "md_eam_forces", "md_step", "md_set_graph", "md_energy", "md_replica_energies", "md_get",
            "md_set_state", "md_tune", "md_set_profiling", "md_get_profile", "md_selftest_timeout",
-           "md_neighbours_noalloc", "md_last_error", "md_destroy"]
+           "md_neighbours_noalloc", "md_set_surrogate", "md_sur_get_params", "md_sur_standardize",
+           "md_sur_get", "md_sur_set_reference", "md_sur_loss_grad", "md_sur_train", "md_last_error",
+           "md_destroy"]
 
 
 class md_potential(C.Structure):
@@ -47,6 +52,11 @@ class md_config(C.Structure):
                 ("k_max", C.c_int32), ("rebuild_every", C.c_int32), ("dt_fs", C.c_double),
                 ("precision", C.c_int32), ("strict_skin", C.c_int32), ("strain_rate_zz", C.c_double),
                 ("stream", C.c_void_p), ("lanes_per_atom", C.c_int32), ("pad", C.c_int32)]
+
+
+class md_surrogate(C.Structure):
+    _fields_ = [("nb", C.c_int32), ("h1", C.c_int32), ("h2", C.c_int32), ("net", C.c_int32),
+                ("mu0", C.c_double), ("dmu", C.c_double), ("width", C.c_double), ("rd", C.c_double)]
 
 
 class md_energies(C.Structure):
@@ -116,6 +126,20 @@ def lib():
         L.md_get_profile.argtypes = [P, C.POINTER(md_profile)]
         L.md_neighbours_noalloc.restype = C.c_int
         L.md_neighbours_noalloc.argtypes = [P, i64, P, C.c_double, i32, P, P, P]
+        L.md_set_surrogate.restype = C.c_int
+        L.md_set_surrogate.argtypes = [P, C.POINTER(md_surrogate), P, P, P]
+        L.md_sur_get_params.restype = C.c_int
+        L.md_sur_get_params.argtypes = [P, P, P, P]
+        L.md_sur_standardize.restype = C.c_int
+        L.md_sur_standardize.argtypes = [P]
+        L.md_sur_get.restype = C.c_int
+        L.md_sur_get.argtypes = [P, i32, P, i32]
+        L.md_sur_set_reference.restype = C.c_int
+        L.md_sur_set_reference.argtypes = [P, P, P, i32]
+        L.md_sur_loss_grad.restype = C.c_int
+        L.md_sur_loss_grad.argtypes = [P, i32, i32, C.c_double, C.c_double, P, P]
+        L.md_sur_train.restype = C.c_int
+        L.md_sur_train.argtypes = [P, i32, i32, C.c_double, C.c_double, C.c_double, C.c_uint64, P]
         L.md_last_error.restype = C.c_char_p
         L.md_last_error.argtypes = [P]
         L.md_destroy.restype = None
@@ -258,6 +282,52 @@ def md_neighbours_noalloc(pos, box, r_list: float, k_max: int, count, nbr_list, 
     return lib().md_neighbours_noalloc(C.c_void_p(pos.data_ptr()), int(pos.shape[0]), C.c_void_p(b.ctypes.data),
                                        float(r_list), int(k_max), C.c_void_p(count.data_ptr()),
                                        C.c_void_p(nbr_list.data_ptr()), C.c_void_p(stream) if stream else None)
+
+
+def md_set_surrogate(ctx, spec: md_surrogate, theta, gmu=None, ginv=None):
+    th = np.ascontiguousarray(theta, dtype=np.float32)
+    mu = None if gmu is None else np.ascontiguousarray(gmu, dtype=np.float32)
+    iv = None if ginv is None else np.ascontiguousarray(ginv, dtype=np.float32)
+    _check(ctx, lib().md_set_surrogate(ctx, C.byref(spec), th.ctypes.data,
+                                       None if mu is None else mu.ctypes.data,
+                                       None if iv is None else iv.ctypes.data))
+
+
+def md_sur_get_params(ctx):
+    th, mu, iv = (np.empty(MD_SUR_PARAMS, np.float32), np.empty(MD_SUR_NB, np.float32),
+                  np.empty(MD_SUR_NB, np.float32))
+    _check(ctx, lib().md_sur_get_params(ctx, th.ctypes.data, mu.ctypes.data, iv.ctypes.data))
+    return th, mu, iv
+
+
+def md_sur_standardize(ctx):
+    _check(ctx, lib().md_sur_standardize(ctx))
+
+
+def md_sur_get(ctx, what: int, dst):
+    p, dev, _k = _ptr(dst)
+    _check(ctx, lib().md_sur_get(ctx, int(what), p, dev))
+    return dst
+
+
+def md_sur_set_reference(ctx, e_ref, f_ref):
+    e = np.ascontiguousarray(e_ref, dtype=np.float64)
+    f = np.ascontiguousarray(f_ref, dtype=np.float64)
+    _check(ctx, lib().md_sur_set_reference(ctx, e.ctypes.data, f.ctypes.data, 0))
+
+
+def md_sur_loss_grad(ctx, rep_begin: int, rep_end: int, w_e: float, w_f: float):
+    loss, grad = np.zeros(2), np.empty(MD_SUR_PARAMS, np.float32)
+    _check(ctx, lib().md_sur_loss_grad(ctx, int(rep_begin), int(rep_end), float(w_e), float(w_f),
+                                       loss.ctypes.data, grad.ctypes.data))
+    return loss, grad
+
+
+def md_sur_train(ctx, n_iter: int, batch_reps: int, lr: float, w_e: float, w_f: float, seed: int):
+    loss = np.zeros(2)
+    _check(ctx, lib().md_sur_train(ctx, int(n_iter), int(batch_reps), float(lr), float(w_e), float(w_f),
+                                   int(seed) & 0xFFFFFFFFFFFFFFFF, loss.ctypes.data))
+    return loss
 
 
 def md_last_error(ctx) -> str:
@@ -417,3 +487,60 @@ class Batch(System):
         self.n_replicas = len(workloads)
         self.offsets = np.concatenate([[0], np.cumsum([w.n_atoms for w in workloads])])
         del keep
+
+
+# ----------------------------------------------------------------------------- surrogate
+def make_surrogate(spec, net: str = "bf16"):
+    s = md_surrogate()
+    s.nb, s.h1, s.h2 = int(spec["nb"]), int(spec["h1"]), int(spec["h2"])
+    s.net = MD_SUR_BF16 if net == "bf16" else MD_SUR_FP32
+    s.mu0, s.dmu, s.width, s.rd = float(spec["mu0"]), float(spec["dmu"]), float(spec["width"]), float(spec["rd"])
+    return s
+
+
+class _SurrogateMixin:
+    def set_surrogate(self, theta, gmu=None, ginv=None, net: str = "bf16"):
+        self.sur_net = net
+        md_set_surrogate(self.ctx, make_surrogate(self.sur_spec, net), theta, gmu, ginv)
+
+    def sur_params(self):
+        return md_sur_get_params(self.ctx)
+
+    def standardize(self):
+        md_sur_standardize(self.ctx)
+
+    def descriptors(self):
+        return md_sur_get(self.ctx, MD_SUR_GET_G, np.empty((self.n, MD_SUR_NB), np.float32))
+
+    def dE_dG(self):
+        return md_sur_get(self.ctx, MD_SUR_GET_DEDG, np.empty((self.n, MD_SUR_NB), np.float32))
+
+    def set_reference(self, e_ref, f_ref):
+        md_sur_set_reference(self.ctx, e_ref, f_ref)
+
+    def loss_grad(self, rep_begin=0, rep_end=None, w_e=1.0, w_f=1.0):
+        return md_sur_loss_grad(self.ctx, rep_begin, self.n_replicas if rep_end is None else rep_end, w_e, w_f)
+
+    def train(self, n_iter, batch_reps, lr, w_e=1.0, w_f=1.0, seed=0):
+        return md_sur_train(self.ctx, n_iter, batch_reps, lr, w_e, w_f, seed)
+
+
+class SurrogateSystem(_SurrogateMixin, System):
+    """A system whose force field is the learned surrogate (kind MD_POT_SURROGATE)."""
+
+    def __init__(self, w: _inputs.Workload, theta=None, gmu=None, ginv=None, net: str = "bf16",
+                 spec=None, **kw):
+        self.sur_spec = dict(spec or _inputs.SUR_FE)
+        super().__init__(_inputs.as_surrogate(w, self.sur_spec), **kw)
+        if theta is not None:
+            self.set_surrogate(theta, gmu, ginv, net)
+
+
+class SurrogateBatch(_SurrogateMixin, Batch):
+    """Training frames as a batch of replicas with the surrogate force field."""
+
+    def __init__(self, workloads, theta=None, gmu=None, ginv=None, net: str = "fp32", spec=None, **kw):
+        self.sur_spec = dict(spec or _inputs.SUR_FE)
+        super().__init__([_inputs.as_surrogate(w, self.sur_spec) for w in workloads], **kw)
+        if theta is not None:
+            self.set_surrogate(theta, gmu, ginv, net)

@@ -41,9 +41,10 @@ def test_struct_layouts_match_header(tmp_path, libmd):
 #include <stddef.h>
 #include "md.h"
 int main(void) {
-  printf("%zu %zu %zu %zu\\n", sizeof(md_potential), sizeof(md_config), sizeof(md_energies), sizeof(md_profile));
-  printf("%zu %zu %zu %zu\\n", offsetof(md_potential, tables), offsetof(md_config, stream),
-         offsetof(md_energies, range_violations), offsetof(md_profile, ms_force));
+  printf("%zu %zu %zu %zu %zu\\n", sizeof(md_potential), sizeof(md_config), sizeof(md_energies), sizeof(md_profile),
+         sizeof(md_surrogate));
+  printf("%zu %zu %zu %zu %zu\\n", offsetof(md_potential, tables), offsetof(md_config, stream),
+         offsetof(md_energies, range_violations), offsetof(md_profile, ms_force), offsetof(md_surrogate, rd));
   return 0;
 }""")
     exe = tmp_path / "layout"
@@ -51,13 +52,14 @@ int main(void) {
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
     got = [int(x) for x in out]
     want = [C.sizeof(md.md_potential), C.sizeof(md.md_config), C.sizeof(md.md_energies),
-            C.sizeof(md.md_profile), md.md_potential.tables.offset, md.md_config.stream.offset,
-            md.md_energies.range_violations.offset, md.md_profile.ms_force.offset]
+            C.sizeof(md.md_profile), C.sizeof(md.md_surrogate), md.md_potential.tables.offset,
+            md.md_config.stream.offset, md.md_energies.range_violations.offset, md.md_profile.ms_force.offset,
+            md.md_surrogate.rd.offset]
     assert got == want
 
 
 def test_status_strings(libmd):
-    assert libmd.md_abi_version() == 1
+    assert libmd.md_abi_version() == 2
     assert md.status_string(md.MD_ERR_NBR_OVERFLOW) == "neighbour list overflow"
     assert md.status_string(md.MD_ERR_SPECIES) == "unsupported species"
 
