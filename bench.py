@@ -416,6 +416,77 @@ def run_extras(torch, md, stream, barrier, max_over_ranks, world):
                             "ms_per_step": ms / 200, "lanes_per_atom": lanes,
                             "value": world * w.n_atoms * 200 / (ms * 1e-3), "box_z": float(e["box"][2])}
     s.close()
+    if os.path.exists(SUR_WEIGHTS):
+        out["surrogate_fe_1m"] = surrogate_extra(torch, md, stream, barrier, max_over_ranks, world)
+    return out
+
+
+SUR_WEIGHTS = os.path.join(ROOT, "paper_1107_2619_gb300", "data", "surrogate_fe.npz")
+
+
+def surrogate_extra(torch, md, stream, barrier, max_over_ranks, world, path=SUR_WEIGHTS, md_steps=1000,
+                    k_time=100):
+    """Learned surrogate on bcc Fe 80^3 cells (1,024,000 atoms) at 600 K next to plain FS EAM
+    (FP64 and mixed) on the same GPU: force RMSE against the FP64 EAM forces at the same
+    thermalised positions, ms per velocity-Verlet step, and NVE drift over md_steps steps."""
+    import dataclasses
+    d = np.load(path)
+    th, gmu, ginv = d["theta"], d["gmu"], d["ginv"]
+    w = I.bcc_fe(80, seed=6, temperature=600.0, sigma=0.0)
+    n = w.n_atoms
+    cs = stream.cuda_stream
+    out = {"workload": "bcc Fe 80^3 cells (1,024,000 atoms), 600 K (300 mixed-EAM steps from the perfect "
+                       "lattice), dt 1 fs, FS Fe; surrogate: 32 RBF descriptors, 32-64-64-1 SiLU network "
+                       "trained on 2,000-atom oracle snapshots",
+           "n_atoms": n, "timed_steps": k_time, "nve_steps": md_steps, "paths": {}}
+    s = md.System(w, precision="mixed", stream=cs, device_inputs=True)
+    s.eam_forces()
+    s.tune()
+    s.step(300)
+    w = dataclasses.replace(w, pos=s.positions(), vel=s.velocities())
+    s.close()
+
+    def nve(sys_, label):
+        sys_.eam_forces()
+        F = sys_.forces()
+        sys_.step(3)
+        ms, _ = _time_steps(torch, sys_, stream, k_time, barrier)
+        ms = max_over_ranks(ms)
+        te = [sys_.energy()["te"]]
+        left = md_steps - k_time - 3
+        while left > 0:
+            q = min(left, 100)
+            sys_.step(q)
+            left -= q
+            te.append(sys_.energy()["te"])
+        te = np.array(te) / n
+        rec = {"ms_per_step": ms / k_time, "value": world * n * k_time / (ms * 1e-3),
+               "nve_drift_ev_per_atom": float(te[-1] - te[0]),
+               "nve_max_dev_ev_per_atom": float(np.abs(te - te[0]).max())}
+        out["paths"][label] = rec
+        return F, rec
+
+    s = md.System(w, precision="fp64", stream=cs, device_inputs=True)
+    f64, _ = nve(s, "eam_fp64")
+    s.close()
+    frms = float(np.sqrt((f64 ** 2).mean()))
+    out["force_rms_ev_per_a"] = frms
+    s = md.System(w, precision="mixed", stream=cs, device_inputs=True)
+    s.tune()
+    s.set_graph(True)
+    f, rec = nve(s, "eam_mixed")
+    rec["force_rmse_vs_fp64_ev_per_a"] = float(np.sqrt(((f - f64) ** 2).mean()))
+    s.close()
+    for net in ("bf16", "fp32"):
+        s = md.SurrogateSystem(w, th, gmu, ginv, net=net, stream=cs, device_inputs=True)
+        s.set_graph(True)
+        f, rec = nve(s, "surrogate_" + net)
+        rec["force_rmse_vs_fp64_ev_per_a"] = float(np.sqrt(((f - f64) ** 2).mean()))
+        rec["force_max_err_vs_fp64_ev_per_a"] = float(np.abs(f - f64).max())
+        s.close()
+    p = out["paths"]
+    out["speedup_surrogate_bf16_over_eam_fp64"] = p["eam_fp64"]["ms_per_step"] / p["surrogate_bf16"]["ms_per_step"]
+    out["speedup_surrogate_bf16_over_eam_mixed"] = p["eam_mixed"]["ms_per_step"] / p["surrogate_bf16"]["ms_per_step"]
     return out
 
 
@@ -429,11 +500,21 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="mixed path only, no e2e/CPU/extra legs: a short run for ncu captures")
     ap.add_argument("--no-extras", action="store_true", help="skip the non-headline workloads")
+    ap.add_argument("--surrogate-only", action="store_true",
+                    help="run only the learned-surrogate comparison and print its record")
+    ap.add_argument("--sur-weights", default=SUR_WEIGHTS, help="trained surrogate (.npz: theta, gmu, ginv)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.surrogate_only:
+        import torch
+        from paper_1107_2619_gb300 import md
+        stream = torch.cuda.Stream()
+        print(json.dumps({"surrogate_fe_1m": surrogate_extra(torch, md, stream, lambda: None, lambda x: x, 1,
+                                                             args.sur_weights)}))
+        return 0
     return run_ours(args)
 
 

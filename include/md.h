@@ -359,11 +359,13 @@ md_status md_sur_loss_grad(md_ctx *ctx, int32_t rep_begin, int32_t rep_end, doub
                            double *loss, float *grad);
 
 /* n_iter Adam steps (Kingma & Ba; beta1 0.9, beta2 0.999, eps 1e-8; learning rate lr) on
- * the loss of minibatches of batch_reps consecutive replicas; minibatch t starts at replica
- * batch_reps * (h(seed, t) mod floor(n_replicas / batch_reps)), h = SplitMix64.  loss (host,
- * 2 doubles, or NULL) = the terms of the last minibatch, before its update. */
-md_status md_sur_train(md_ctx *ctx, int32_t n_iter, int32_t batch_reps, double lr, double w_e, double w_f,
-                       uint64_t seed, double *loss);
+ * the loss of minibatches of batch_reps consecutive replicas of [rep_begin, rep_end); the
+ * minibatch of step t starts at replica rep_begin + batch_reps * (h(seed + t) mod
+ * floor((rep_end - rep_begin) / batch_reps)), h = SplitMix64.  loss (host, 2 doubles, or
+ * NULL) = the terms of the last minibatch, before its update.  The optimiser state (moments,
+ * step count) carries over between calls. */
+md_status md_sur_train(md_ctx *ctx, int32_t n_iter, int32_t rep_begin, int32_t rep_end, int32_t batch_reps,
+                       double lr, double w_e, double w_f, uint64_t seed, double *loss);
 
 /* Text of the last error of this context ("" if none).  Valid until the next call. */
 const char *md_last_error(const md_ctx *ctx);

@@ -1376,18 +1376,19 @@ md_status md_sur_loss_grad(md_ctx *ctx, int32_t rep_begin, int32_t rep_end, doub
     return MD_OK;
 }
 
-md_status md_sur_train(md_ctx *ctx, int32_t n_iter, int32_t batch_reps, double lr, double w_e, double w_f,
-                       uint64_t seed, double *loss) {
+md_status md_sur_train(md_ctx *ctx, int32_t n_iter, int32_t rep_begin, int32_t rep_end, int32_t batch_reps,
+                       double lr, double w_e, double w_f, uint64_t seed, double *loss) {
     if (!ctx || n_iter < 0 || batch_reps < 1) return MD_ERR_ARG;
     md_status st = sur_check_train(ctx, w_e, w_f);
     if (st != MD_OK) return st;
-    if (batch_reps > ctx->n_rep || !(lr > 0.0)) return fail(ctx, MD_ERR_ARG, "batch size or learning rate");
+    if (rep_begin < 0 || rep_end > ctx->n_rep || batch_reps > rep_end - rep_begin || !(lr > 0.0))
+        return fail(ctx, MD_ERR_ARG, "replica range, batch size or learning rate");
     if (n_iter == 0) return MD_OK;
-    const uint64_t nbatch = (uint64_t)(ctx->n_rep / batch_reps);
+    const uint64_t nbatch = (uint64_t)((rep_end - rep_begin) / batch_reps);
     MD_CK(reset_errors(ctx));
     int rows = 0, blocks = 0, r0 = 0;
     for (int it = 0; it < n_iter; it++) {
-        r0 = (int)(splitmix64(seed + (uint64_t)it) % nbatch) * batch_reps;
+        r0 = rep_begin + (int)(splitmix64(seed + (uint64_t)it) % nbatch) * batch_reps;
         MD_CK(sur_train_pass(ctx, r0, r0 + batch_reps, w_e, w_f, &rows, &blocks));
         if (it == n_iter - 1) {
             MD_CK(launch_reduce(ctx->A, rows, ctx->d_reduce, ctx->stream));

@@ -139,7 +139,7 @@ def lib():
         L.md_sur_loss_grad.restype = C.c_int
         L.md_sur_loss_grad.argtypes = [P, i32, i32, C.c_double, C.c_double, P, P]
         L.md_sur_train.restype = C.c_int
-        L.md_sur_train.argtypes = [P, i32, i32, C.c_double, C.c_double, C.c_double, C.c_uint64, P]
+        L.md_sur_train.argtypes = [P, i32, i32, i32, i32, C.c_double, C.c_double, C.c_double, C.c_uint64, P]
         L.md_last_error.restype = C.c_char_p
         L.md_last_error.argtypes = [P]
         L.md_destroy.restype = None
@@ -323,10 +323,11 @@ def md_sur_loss_grad(ctx, rep_begin: int, rep_end: int, w_e: float, w_f: float):
     return loss, grad
 
 
-def md_sur_train(ctx, n_iter: int, batch_reps: int, lr: float, w_e: float, w_f: float, seed: int):
+def md_sur_train(ctx, n_iter: int, rep_begin: int, rep_end: int, batch_reps: int, lr: float, w_e: float,
+                 w_f: float, seed: int):
     loss = np.zeros(2)
-    _check(ctx, lib().md_sur_train(ctx, int(n_iter), int(batch_reps), float(lr), float(w_e), float(w_f),
-                                   int(seed) & 0xFFFFFFFFFFFFFFFF, loss.ctypes.data))
+    _check(ctx, lib().md_sur_train(ctx, int(n_iter), int(rep_begin), int(rep_end), int(batch_reps), float(lr),
+                                   float(w_e), float(w_f), int(seed) & 0xFFFFFFFFFFFFFFFF, loss.ctypes.data))
     return loss
 
 
@@ -521,8 +522,9 @@ class _SurrogateMixin:
     def loss_grad(self, rep_begin=0, rep_end=None, w_e=1.0, w_f=1.0):
         return md_sur_loss_grad(self.ctx, rep_begin, self.n_replicas if rep_end is None else rep_end, w_e, w_f)
 
-    def train(self, n_iter, batch_reps, lr, w_e=1.0, w_f=1.0, seed=0):
-        return md_sur_train(self.ctx, n_iter, batch_reps, lr, w_e, w_f, seed)
+    def train(self, n_iter, batch_reps, lr, w_e=1.0, w_f=1.0, seed=0, rep_begin=0, rep_end=None):
+        rep_end = self.n_replicas if rep_end is None else rep_end
+        return md_sur_train(self.ctx, n_iter, rep_begin, rep_end, batch_reps, lr, w_e, w_f, seed)
 
 
 class SurrogateSystem(_SurrogateMixin, System):
