@@ -503,11 +503,28 @@ def main():
     ap.add_argument("--surrogate-only", action="store_true",
                     help="run only the learned-surrogate comparison and print its record")
     ap.add_argument("--sur-weights", default=SUR_WEIGHTS, help="trained surrogate (.npz: theta, gmu, ginv)")
+    ap.add_argument("--surrogate-profile", choices=["bf16", "fp32"], default=None,
+                    help="a short surrogate run on bcc Fe 80^3 cells (no graph) for ncu captures")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.surrogate_profile:
+        import torch
+        from paper_1107_2619_gb300 import md
+        d = np.load(args.sur_weights)
+        w = I.bcc_fe(80, seed=6, temperature=600.0, sigma=0.05)
+        stream = torch.cuda.Stream()
+        s = md.SurrogateSystem(w, d["theta"], d["gmu"], d["ginv"], net=args.surrogate_profile,
+                               stream=stream.cuda_stream, device_inputs=True)
+        s.eam_forces()
+        s.step(args.warmup)
+        ms, _ = _time_steps(torch, s, stream, args.steps, lambda: None)
+        print(json.dumps({"surrogate_profile": args.surrogate_profile, "n_atoms": w.n_atoms,
+                          "ms_per_step": ms / args.steps}))
+        s.close()
+        return 0
     if args.surrogate_only:
         import torch
         from paper_1107_2619_gb300 import md

@@ -233,3 +233,61 @@ def test_surrogate_rejects_eam_only_calls_and_bad_spec():
             s.get(md.MD_GET_RHO)
         with pytest.raises(md.MDError):
             s.loss_grad()                      # no references
+
+
+# --------------------------------------------------------------------------- the trained network
+WEIGHTS = __import__("os").path.join(__import__("os").path.dirname(__file__), "..", "paper_1107_2619_gb300",
+                                     "data", "surrogate_fe.npz")
+
+
+def _fresh_frame(T, seed):
+    """A thermalised 2,000-atom bcc Fe frame from the oracle (seeds outside the training set)."""
+    import dataclasses
+    w = I.bcc_fe(10, seed=seed, temperature=2.0 * T, sigma=0.0)
+    st = oracle.run_vv(w.pos, w.vel, w.species, w.potential.masses, w.box, w.potential, 1.0, 300, 0.3, 32)
+    o = oracle.forces(st["pos"], w.species, w.box, w.potential)
+    return dataclasses.replace(w, pos=st["pos"], vel=st["vel"]), o
+
+
+def test_trained_surrogate_reproduces_eam_and_beats_the_untrained_network():
+    d = np.load(WEIGHTS)
+    th, gmu, ginv = d["theta"], d["gmu"], d["ginv"]
+    untrained = I.sur_init_weights(5, SPEC).astype(np.float32)
+    untrained[-1] = th[-1]
+    for T, seed in ((450.0, 7001), (900.0, 7002), (1350.0, 7003)):
+        w, o = _fresh_frame(T, seed)
+        frms = np.sqrt((o["force"] ** 2).mean())
+        err = {}
+        for label, theta in (("trained", th), ("untrained", untrained)):
+            for net in ("bf16", "fp32"):
+                with md.SurrogateSystem(w, theta, gmu, ginv, net=net) as s:
+                    pe = s.eam_forces()
+                    F = s.forces()
+                err[label, net] = (np.sqrt(((F - o["force"]) ** 2).mean()), abs(pe - o["pe"]) / w.n_atoms)
+        for net in ("bf16", "fp32"):
+            f_rmse, e_err = err["trained", net]
+            assert f_rmse < 0.01 and f_rmse < 0.02 * frms, (T, net, f_rmse)
+            assert e_err < (5e-3 if net == "bf16" else 1e-3), (T, net, e_err)
+            assert err["untrained", net][0] > 10.0 * f_rmse
+
+def test_trained_surrogate_conserves_energy():
+    """NVE from a thermalised state: drift of the total energy per atom over 500 steps of 1 fs.
+    (From a perfect lattice every atom has the same descriptors, so the bf16 network's rounding
+    errors in E add up coherently instead of averaging out: an offset of ~5e-4 eV/atom in the
+    first energy, not a drift; the FP32 network is checked from that start too.)"""
+    import dataclasses
+    d = np.load(WEIGHTS)
+    w = I.bcc_fe(12, seed=8, temperature=1200.0, sigma=0.0)
+    with md.System(w, precision="fp64") as s:
+        s.eam_forces()
+        s.step(400)
+        wt = dataclasses.replace(w, pos=s.positions(), vel=s.velocities())
+    for start, net, bound in ((wt, "bf16", 2e-5), (wt, "fp32", 1e-5), (w, "fp32", 1e-4)):
+        with md.SurrogateSystem(start, d["theta"], d["gmu"], d["ginv"], net=net) as s:
+            s.eam_forces()
+            e0 = s.energy()
+            s.step(500)
+            e1 = s.energy()
+        assert abs(e1["te"] - e0["te"]) / w.n_atoms < bound, (net, e1["te"] - e0["te"])
+        assert e1["n_rebuilds"] > e0["n_rebuilds"]       # atoms moved: lists were rebuilt on the way
+        assert 300.0 < e1["temperature"] < 900.0
