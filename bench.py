@@ -8,9 +8,14 @@ pass, force pass + half kick.  All steps of one md_step call run in one persiste
 The headline is the mixed path (FP32 pair/density terms, FP64 positions, integration,
 density sum and reductions); the FP64 path is timed beside it.  Extra lines (not the
 headline): bcc Fe 2,000 atoms (FP64), 256 bcc Fe replicas of 2,000-54,000 atoms in one
-batch under a captured CUDA graph, and bcc Fe-C 4.2M atoms with a z strain ramp.
+batch under a captured CUDA graph, bcc Fe-C 4.2M atoms with a z strain ramp, and the learned
+surrogate on 1,024,000-atom bcc Fe next to FP64 and mixed EAM (force RMSE, ms per step,
+NVE drift).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-extras]
+  python bench.py --surrogate-only            # the surrogate comparison alone
+  python bench.py --profile-case --cells 40   # short mixed-EAM run for ncu captures
+  python bench.py --surrogate-profile bf16    # short surrogate run for ncu captures
 
 Under torchrun each rank advances its own replica (different seed) on its own GPU; there is
 no exchange on the data path (replicas only); timings are reduced with a max over ranks.
@@ -134,6 +139,21 @@ def _dist():
     return world, rank, local
 
 
+def reduce_max(dist, x, device):
+    """Max of a float over all ranks (x itself without a process group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(atoms_per_rank, world, steps, ms):
+    """Whole-job throughput: the atoms of all ranks x steps / the slowest rank's time."""
+    return world * atoms_per_rank * steps / (ms * 1e-3)
+
+
 def _oracle_rate(n_cells, steps, warmup=0):
     """Oracle atom-steps/s on an fcc Cu cube of n_cells^3 cells (same potential, temperature,
     time step and skin as the benchmark workload): velocity Verlet with the link-cell list."""
@@ -222,11 +242,7 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(dist, x, "cuda")
 
     w = I.fcc_cu(args.cells, seed=SEED + rank)
     n = w.n_atoms
@@ -244,9 +260,9 @@ def run_ours(args):
         ms = max_over_ranks(ms)
         launches = s.profile()["launches"] - launches0
         e1 = s.energy()
-        # phase breakdown: a second, profiled run of the same length (stamps at phase boundaries)
+        # phase breakdown: a second, profiled run (stamps at phase boundaries), at most 200 steps
         s.set_profiling(True)
-        s.step(args.steps)
+        s.step(min(args.steps, 200))
         prof = s.profile()
         s.set_profiling(False)
         res[precision] = dict(ms=ms, prof=prof, e0=e0, e1=e1, counts=counts, clocks=clocks,
@@ -334,14 +350,14 @@ def run_ours(args):
         q = res[pr]
         de = (q["e1"]["te"] - q["e0"]["te"]) / n
         qp = q["prof"]
-        return {"value": world * n * args.steps / (q["ms"] * 1e-3), "ms_per_step": q["ms"] / args.steps,
+        return {"value": job_value(n, world, args.steps, q["ms"]), "ms_per_step": q["ms"] / args.steps,
                 "nve_drift_ev_per_atom": de, "steps_timed": args.steps, "lanes_per_atom": q["lanes"],
                 "rebuilds_in_timed_region": q["e1"]["n_rebuilds"] - q["e0"]["n_rebuilds"],
                 "phase_ms_per_step_profiled_repeat": {k: qp["ms_" + k] / max(1, qp["n_" + k])
                                                        for k in ("kick", "rebuild", "density", "force")}}
 
     line = {
-        "metric": METRIC, "value": world * n * args.steps / (r["ms"] * 1e-3), "unit": UNIT,
+        "metric": METRIC, "value": job_value(n, world, args.steps, r["ms"]), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic", "config": _config("mixed: FP32 pair/density terms, FP64 integration and sums"),
@@ -378,7 +394,7 @@ def run_extras(torch, md, stream, barrier, max_over_ranks, world):
     ms, _ = _time_steps(torch, s, stream, 100, barrier)
     ms = max_over_ranks(ms)
     out["fe2k_fp64"] = {"workload": "bcc Fe 10^3 cells = 2,000 atoms, FS analytic, FP64, dt 1 fs",
-                        "steps": 100, "ms_per_step": ms / 100, "value": world * w.n_atoms * 100 / (ms * 1e-3)}
+                        "steps": 100, "ms_per_step": ms / 100, "value": job_value(w.n_atoms, world, 100, ms)}
     s.close()
     # 256 replicas, n ~ U{10..30}, T ~ U[300, 1200] K, seeds 3000 + r, mixed, graph, 500 steps
     u = I.random_uniform(3000, 11, 512)
@@ -398,7 +414,7 @@ def run_extras(torch, md, stream, barrier, max_over_ranks, world):
                                             "FS analytic, mixed, one persistent launch per 500-step call, "
                                             "replayed from a captured CUDA graph",
                                 "n_atoms": b.n, "steps": 500, "ms_per_step": ms / 500, "lanes_per_atom": lanes,
-                                "value": world * b.n * 500 / (ms * 1e-3),
+                                "value": job_value(b.n, world, 500, ms),
                                 "rebuilds": e1["n_rebuilds"] - e0["n_rebuilds"]}
     b.close()
     # bcc Fe-C 128^3 + 0.1 % C, tables, 600 K, strain -1e9/s, mixed, 200 steps of 1 fs
@@ -414,7 +430,7 @@ def run_extras(torch, md, stream, barrier, max_over_ranks, world):
                                         "two-species 5,000-knot tables, 600 K, strain rate -1e9/s along z, "
                                         "mixed, dt 1 fs", "n_atoms": w.n_atoms, "steps": 200,
                             "ms_per_step": ms / 200, "lanes_per_atom": lanes,
-                            "value": world * w.n_atoms * 200 / (ms * 1e-3), "box_z": float(e["box"][2])}
+                            "value": job_value(w.n_atoms, world, 200, ms), "box_z": float(e["box"][2])}
     s.close()
     if os.path.exists(SUR_WEIGHTS):
         out["surrogate_fe_1m"] = surrogate_extra(torch, md, stream, barrier, max_over_ranks, world)
@@ -460,7 +476,7 @@ def surrogate_extra(torch, md, stream, barrier, max_over_ranks, world, path=SUR_
             left -= q
             te.append(sys_.energy()["te"])
         te = np.array(te) / n
-        rec = {"ms_per_step": ms / k_time, "value": world * n * k_time / (ms * 1e-3),
+        rec = {"ms_per_step": ms / k_time, "value": job_value(n, world, k_time, ms),
                "nve_drift_ev_per_atom": float(te[-1] - te[0]),
                "nve_max_dev_ev_per_atom": float(np.abs(te - te[0]).max())}
         out["paths"][label] = rec
@@ -493,7 +509,7 @@ def surrogate_extra(torch, md, stream, barrier, max_over_ranks, world, path=SUR_
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cells", type=int, default=CELLS, help="fcc Cu cube edge in cells (profiling cases)")
