@@ -3,7 +3,8 @@
 // per-item functions inside one persistent launch).
 //
 // Rebuild pipeline, all on the launching stream and all returning at once when the device
-// flag `need_rebuild` is clear:
+// flag `need_rebuild` is clear.  The per-atom and per-cell kernels loop over their items with a
+// grid of at most 8 blocks per SM, so that a launch with nothing to do costs a few µs:
 //   k_bin        wrapped fractional coordinate -> link cell; per-cell counter -> slot
 //   k_scan_*     exclusive scan of the per-cell counts -> cell_start (3 phases)
 //   k_scatter    order[cell_start[c] + slot] = atom
@@ -13,6 +14,8 @@
 // Link cells are fixed in fractional coordinates and at least r_list wide, so every pair
 // closer than r_list lies in adjacent cells (the hybrid NL-LCM of §3.2.1).
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "md_phases.cuh"
 
@@ -29,10 +32,12 @@ __global__ void k_clear_rebuild(Flags *f) {
     f->need_rebuild = 0;
 }
 
+__device__ __forceinline__ long long gtid() { return (long long)blockIdx.x * blockDim.x + threadIdx.x; }
+__device__ __forceinline__ long long gstride() { return (long long)gridDim.x * blockDim.x; }
+
 __global__ void k_bin(Atoms A, Cells C) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= A.n || !ph::rebuild_requested(A.flags)) return;
-    ph::bin_atom(A, C, A.boxes, i);
+    if (!ph::rebuild_requested(A.flags)) return;
+    for (long long i = gtid(); i < A.n; i += gstride()) ph::bin_atom(A, C, A.boxes, (int)i);
 }
 
 __global__ void k_scan_tiles(Cells C, const Flags *f) {
@@ -55,36 +60,50 @@ __global__ void k_scan_apply(Cells C, const Flags *f) {
 }
 
 __global__ void k_scatter(Atoms A, Cells C) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= A.n || !ph::rebuild_requested(A.flags)) return;
-    ph::scatter_atom(A, C, i);
+    if (!ph::rebuild_requested(A.flags)) return;
+    for (long long i = gtid(); i < A.n; i += gstride()) ph::scatter_atom(A, C, (int)i);
 }
 
 __global__ void k_cell_sort(Atoms A, Cells C) {
-    const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;   // one warp per cell
-    if (c >= C.ncell || !ph::rebuild_requested(A.flags)) return;
-    ph::sort_cell_warp(A, C, c, threadIdx.x & 31);
+    if (!ph::rebuild_requested(A.flags)) return;
+    const long long warps = gstride() >> 5;
+    for (long long c = gtid() >> 5; c < C.ncell; c += warps)   // one warp per cell
+        ph::sort_cell_warp(A, C, (int)c, threadIdx.x & 31);
 }
 
 __global__ void k_gather(Atoms A) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= A.n || !ph::rebuild_requested(A.flags)) return;
-    ph::gather_atom(A, k);
+    if (!ph::rebuild_requested(A.flags)) return;
+    for (long long k = gtid(); k < A.n; k += gstride()) ph::gather_atom(A, (int)k);
 }
 
 __global__ void k_copyback(Atoms A) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= A.n || !ph::rebuild_requested(A.flags)) return;
-    ph::copyback_atom(A, A.boxes, k);
+    if (!ph::rebuild_requested(A.flags)) return;
+    for (long long k = gtid(); k < A.n; k += gstride()) ph::copyback_atom(A, A.boxes, (int)k);
 }
 
 __global__ void __launch_bounds__(kThreads) k_build_list(Atoms A, Cells C, double rl2, float band_lo,
                                                          float band_hi) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool active = i < A.n && ph::rebuild_requested(A.flags);
-    const int cnt = active ? ph::build_row(A, C, A.boxes, i, rl2, band_lo, band_hi) : 0;
-    const int m = __reduce_max_sync(0xffffffffu, cnt);
+    if (!ph::rebuild_requested(A.flags)) return;
+    int m = 0;
+    // whole warps iterate together (the max reduction below needs all 32 lanes)
+    const long long end = ((long long)A.n + 31) / 32 * 32;
+    for (long long i = gtid(); i < end; i += gstride()) {
+        const int cnt = i < A.n ? ph::build_row(A, C, A.boxes, (int)i, rl2, band_lo, band_hi) : 0;
+        m = max(m, cnt);
+    }
+    m = __reduce_max_sync(0xffffffffu, m);
     if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(&A.flags->max_count, m);
+}
+
+int capped_blocks(long long items, int threads) {
+    static int n_sm = 0;
+    if (!n_sm) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        if (n_sm <= 0) n_sm = 1;
+    }
+    return (int)std::max(1LL, std::min(blocks_for(items, threads) * 1LL, 8LL * n_sm));
 }
 
 }  // namespace
@@ -101,7 +120,7 @@ cudaError_t launch_clear_rebuild(Flags *f, cudaStream_t s) {
 
 cudaError_t launch_rebuild(const Atoms &A, const Cells &C, double rl2, float band_lo, float band_hi,
                            cudaStream_t s) {
-    const int nb = blocks_for(A.n, kThreads);
+    const int nb = capped_blocks(A.n, kThreads);
     const int ntiles = (C.ncell + kScanThreads * ph::kScanItems - 1) / (kScanThreads * ph::kScanItems);
     if (A.n > 0) k_bin<<<nb, kThreads, 0, s>>>(A, C);
     k_scan_tiles<<<ntiles, kScanThreads, 0, s>>>(C, A.flags);
@@ -109,7 +128,7 @@ cudaError_t launch_rebuild(const Atoms &A, const Cells &C, double rl2, float ban
     k_scan_apply<<<ntiles, kScanThreads, 0, s>>>(C, A.flags);
     if (A.n > 0) {
         k_scatter<<<nb, kThreads, 0, s>>>(A, C);
-        k_cell_sort<<<blocks_for((long long)C.ncell * 32, kThreads), kThreads, 0, s>>>(A, C);
+        k_cell_sort<<<capped_blocks((long long)C.ncell * 32, kThreads), kThreads, 0, s>>>(A, C);
         k_gather<<<nb, kThreads, 0, s>>>(A);
         k_copyback<<<nb, kThreads, 0, s>>>(A);
         k_build_list<<<nb, kThreads, 0, s>>>(A, C, rl2, band_lo, band_hi);

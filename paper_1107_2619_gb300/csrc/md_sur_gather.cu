@@ -25,15 +25,17 @@ constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ float mi(float d, float L, float iL) { return d - L * rintf(d * iL); }
 
+// Per-pair constants of one chunk of list entries, compacted: the pairs inside rd occupy
+// slots 0 .. n-1 in list order.  P0 = (r, fc, fc', j bits), P1 = (unit vector, fc / w^2).
 struct Stage {
-    float4 geo[kWarps][32];  // dx, dy, dz, r
-    float4 aux[kWarps][32];  // fc, dfc, j (bits), 1/r
+    float4 P0[kWarps][32];
+    float4 P1[kWarps][32];
 };
 
-// Geometry of list entries [base, base + 32) of atom i; returns the mask of entries inside rd.
-__device__ __forceinline__ unsigned stage_chunk(const Atoms &A, const SurNet &S, const float4 &pi, const Box &B,
-                                                const int *row, int cnt, int base, int lane, float4 *geo,
-                                                float4 *aux) {
+// Geometry of list entries [base, base + 32) of atom i into the compacted slots; returns the
+// number of pairs inside rd.
+__device__ __forceinline__ int stage_chunk(const Atoms &A, const SurNet &S, const float4 &pi, const Box &B,
+                                           const int *row, int cnt, int base, int lane, float4 *P0, float4 *P1) {
     const int q = base + lane;
     const bool valid = q < cnt;
     const int j = valid ? __ldg(row + q) : 0;
@@ -43,17 +45,29 @@ __device__ __forceinline__ unsigned stage_chunk(const Atoms &A, const SurNet &S,
     const float dz = mi(pj.z - pi.z, B.Lf[2], B.invLf[2]);
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     const bool inside = valid && r2 < S.rd2 && r2 > 0.f;
-    const float rinv = inside ? rsqrtf(r2) : 0.f;
-    const float r = r2 * rinv;
-    float sn, cs;
-    __sincosf(S.pi_rd * r, &sn, &cs);
-    geo[lane] = make_float4(dx, dy, dz, r);
-    aux[lane] = make_float4(0.5f * (cs + 1.f), -0.5f * S.pi_rd * sn, __int_as_float(j), rinv);
+    const unsigned m = __ballot_sync(kFull, inside);
+    if (inside) {
+        const float rinv = rsqrtf(r2);
+        const float r = r2 * rinv;
+        float sn, cs;
+        __sincosf(S.pi_rd * r, &sn, &cs);
+        const float fc = 0.5f * (cs + 1.f);
+        const int slot = __popc(m & ((1u << lane) - 1u));
+        P0[slot] = make_float4(r, fc, -0.5f * S.pi_rd * sn, __int_as_float(j));
+        P1[slot] = make_float4(dx * rinv, dy * rinv, dz * rinv, fc * S.invw2);
+    }
     __syncwarp();
-    return __ballot_sync(kFull, inside);
+    return __popc(m);
 }
 
-__device__ __forceinline__ float gauss(const SurNet &S, float a) { return __expf(-a * a * S.inv2w2); }
+// 2^x (PTX ex2.approx.ftz: relative error < 2^-22).
+__device__ __forceinline__ float ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+constexpr float kLog2e = 1.4426950408889634f;
 
 __device__ __forceinline__ float warp_sum(float x) {
 #pragma unroll
@@ -70,6 +84,7 @@ __global__ void __launch_bounds__(kThreads) k_sur_desc(Atoms A, SurNet S, int a0
     __shared__ __align__(16) __nv_bfloat16 out[kWarps][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const float mu = S.mu0 + S.dmu * (float)lane;
+    const float kx = -S.inv2w2 * kLog2e;   // b = 2^(kx a^2) fc
     const float gm = S.gmu[lane], gi = S.ginv[lane];
     for (long long i0 = a0 + (long long)blockIdx.x * kWarps + w; i0 < a1; i0 += (long long)gridDim.x * kWarps) {
         const int i = (int)i0;
@@ -77,16 +92,25 @@ __global__ void __launch_bounds__(kThreads) k_sur_desc(Atoms A, SurNet S, int a0
         const float4 pi = A.posf[i];
         const int cnt = min(A.count[i], A.k_max);
         const int *row = A.nbr + (size_t)i * A.k_max;
-        float G = 0.f;
+        float G = 0.f, G2 = 0.f;
         for (int base = 0; base < cnt; base += 32) {
-            unsigned m = stage_chunk(A, S, pi, B, row, cnt, base, lane, st.geo[w], st.aux[w]);
-            while (m) {
-                const int s = __ffs(m) - 1;
-                m &= m - 1;
-                G = fmaf(gauss(S, st.geo[w][s].w - mu), st.aux[w][s].x, G);
+            const int np = stage_chunk(A, S, pi, B, row, cnt, base, lane, st.P0[w], st.P1[w]);
+            int q = 0;
+            for (; q + 1 < np; q += 2) {
+                const float2 p0 = *reinterpret_cast<const float2 *>(&st.P0[w][q]);
+                const float2 p1 = *reinterpret_cast<const float2 *>(&st.P0[w][q + 1]);
+                const float a0_ = p0.x - mu, a1_ = p1.x - mu;
+                G = fmaf(ex2(kx * a0_ * a0_), p0.y, G);
+                G2 = fmaf(ex2(kx * a1_ * a1_), p1.y, G2);
+            }
+            if (q < np) {
+                const float2 p0 = *reinterpret_cast<const float2 *>(&st.P0[w][q]);
+                const float a0_ = p0.x - mu;
+                G = fmaf(ex2(kx * a0_ * a0_), p0.y, G);
             }
             __syncwarp();
         }
+        G += G2;
         if (bf16) {
             out[w][lane] = __float2bfloat16_rn((G - gm) * gi);
             __syncwarp();
@@ -110,6 +134,7 @@ __global__ void __launch_bounds__(kThreads) k_sur_force(Atoms A, SurNet S, int a
     __shared__ Stage st;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const float mu = S.mu0 + S.dmu * (float)lane;
+    const float kx = -S.inv2w2 * kLog2e;
     double part[kPartials];
 #pragma unroll
     for (int q = 0; q < kPartials; q++) part[q] = 0.0;
@@ -122,28 +147,39 @@ __global__ void __launch_bounds__(kThreads) k_sur_force(Atoms A, SurNet S, int a
         const float gi = S.g[(size_t)i * kSurNb + lane];
         float fx = 0.f, fy = 0.f, fz = 0.f;
         float wxx = 0.f, wyy = 0.f, wzz = 0.f, wyz = 0.f, wxz = 0.f, wxy = 0.f;
+        // one pair: c = (g_ik + g_jk) b_k'(r) (this lane's channel), f += c * unit vector;
+        // on the energy step the virial -1/2 c r u (x) u
+        auto pair = [&](const float4 &p0, const float4 &p1, float gj) {
+            const float a = p0.x - mu;
+            const float bp = ex2(kx * a * a) * fmaf(-a, p1.w, p0.z);   // b_k'(r)
+            const float c = (gi + gj) * bp;
+            fx = fmaf(c, p1.x, fx);
+            fy = fmaf(c, p1.y, fy);
+            fz = fmaf(c, p1.z, fz);
+            if (ENERGY && !TRAIN) {
+                const float h = -0.5f * c * p0.x;
+                wxx = fmaf(h * p1.x, p1.x, wxx);
+                wyy = fmaf(h * p1.y, p1.y, wyy);
+                wzz = fmaf(h * p1.z, p1.z, wzz);
+                wyz = fmaf(h * p1.y, p1.z, wyz);
+                wxz = fmaf(h * p1.x, p1.z, wxz);
+                wxy = fmaf(h * p1.x, p1.y, wxy);
+            }
+        };
         for (int base = 0; base < cnt; base += 32) {
-            unsigned m = stage_chunk(A, S, pi, B, row, cnt, base, lane, st.geo[w], st.aux[w]);
-            while (m) {
-                const int s = __ffs(m) - 1;
-                m &= m - 1;
-                const float4 gq = st.geo[w][s], ax = st.aux[w][s];
-                const int j = __float_as_int(ax.z);
-                const float a = gq.w - mu;
-                const float bp = gauss(S, a) * fmaf(-a * S.invw2, ax.x, ax.y);   // b_k'(r)
-                const float c = (gi + __ldg(S.g + (size_t)j * kSurNb + lane)) * bp * ax.w;
-                fx = fmaf(c, gq.x, fx);
-                fy = fmaf(c, gq.y, fy);
-                fz = fmaf(c, gq.z, fz);
-                if (ENERGY && !TRAIN) {
-                    const float h = -0.5f * c;
-                    wxx = fmaf(h * gq.x, gq.x, wxx);
-                    wyy = fmaf(h * gq.y, gq.y, wyy);
-                    wzz = fmaf(h * gq.z, gq.z, wzz);
-                    wyz = fmaf(h * gq.y, gq.z, wyz);
-                    wxz = fmaf(h * gq.x, gq.z, wxz);
-                    wxy = fmaf(h * gq.x, gq.y, wxy);
-                }
+            const int np = stage_chunk(A, S, pi, B, row, cnt, base, lane, st.P0[w], st.P1[w]);
+            int q = 0;
+            for (; q + 1 < np; q += 2) {
+                const float4 p0 = st.P0[w][q], p1 = st.P1[w][q];
+                const float4 r0 = st.P0[w][q + 1], r1 = st.P1[w][q + 1];
+                const float g0 = __ldg(S.g + (size_t)__float_as_int(p0.w) * kSurNb + lane);
+                const float g1 = __ldg(S.g + (size_t)__float_as_int(r0.w) * kSurNb + lane);
+                pair(p0, p1, g0);
+                pair(r0, r1, g1);
+            }
+            if (q < np) {
+                const float4 p0 = st.P0[w][q], p1 = st.P1[w][q];
+                pair(p0, p1, __ldg(S.g + (size_t)__float_as_int(p0.w) * kSurNb + lane));
             }
             __syncwarp();
         }
@@ -186,6 +222,7 @@ __global__ void __launch_bounds__(kThreads) k_sur_u(Atoms A, SurNet S, int a0, i
     __shared__ Stage st;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const float mu = S.mu0 + S.dmu * (float)lane;
+    const float kx = -S.inv2w2 * kLog2e;
     const float gi = S.ginv[lane];
     for (long long i0 = a0 + (long long)blockIdx.x * kWarps + w; i0 < a1; i0 += (long long)gridDim.x * kWarps) {
         const int i = (int)i0;
@@ -196,15 +233,13 @@ __global__ void __launch_bounds__(kThreads) k_sur_u(Atoms A, SurNet S, int a0, i
         const int *row = A.nbr + (size_t)i * A.k_max;
         float u = 0.f;
         for (int base = 0; base < cnt; base += 32) {
-            unsigned m = stage_chunk(A, S, pi, B, row, cnt, base, lane, st.geo[w], st.aux[w]);
-            while (m) {
-                const int s = __ffs(m) - 1;
-                m &= m - 1;
-                const float4 gq = st.geo[w][s], ax = st.aux[w][s];
-                const float4 fj = __ldg(S.phi + __float_as_int(ax.z));
-                const float t = (gq.x * (fj.x - fi.x) + gq.y * (fj.y - fi.y) + gq.z * (fj.z - fi.z)) * ax.w;
-                const float a = gq.w - mu;
-                u = fmaf(gauss(S, a) * fmaf(-a * S.invw2, ax.x, ax.y), t, u);
+            const int np = stage_chunk(A, S, pi, B, row, cnt, base, lane, st.P0[w], st.P1[w]);
+            for (int q = 0; q < np; q++) {
+                const float4 p0 = st.P0[w][q], p1 = st.P1[w][q];
+                const float4 fj = __ldg(S.phi + __float_as_int(p0.w));
+                const float t = p1.x * (fj.x - fi.x) + p1.y * (fj.y - fi.y) + p1.z * (fj.z - fi.z);
+                const float a = p0.x - mu;
+                u = fmaf(ex2(kx * a * a) * fmaf(-a, p1.w, p0.z), t, u);
             }
             __syncwarp();
         }

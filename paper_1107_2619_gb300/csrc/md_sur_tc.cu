@@ -2,9 +2,10 @@
 // of 128-atom tiles with BF16 operands and FP32 accumulation in tensor memory.
 //
 // Per tile (x: 128 x 32 standardised descriptors, bf16, written by the descriptor kernel in the
-// layout below), four MMAs of M = 128 rows, one per layer, each followed by an epilogue in which
-// thread t reads row t of the accumulator from TMEM (tcgen05.ld 32x32b), applies bias and SiLU
-// in FP32 and writes the next operand to shared memory as bf16:
+// layout below and brought in by one bulk TMA copy), four MMAs of M = 128 rows, one per layer,
+// each followed by an epilogue in which the two warpgroups of the CTA each take half of the
+// accumulator's columns: thread t of a warpgroup reads row t from TMEM (tcgen05.ld 32x32b),
+// applies bias and SiLU in FP32 and writes the next operand to shared memory as bf16:
 //   D0 [TMEM cols 0..63]   = x  W1^T           z1 = D0 + b1,  a1 = s(z1)            -> act
 //   D1 [cols 64..127]      = a1 W2^T           z2 = D1 + b2,  E = w3 . s(z2) + b3,
 //                                              d2 = w3 s'(z2)                       -> act
@@ -14,7 +15,9 @@
 // core matrix (128 contiguous bytes), core matrices adjacent along K 128 bytes apart (leading
 // byte offset), 8-row groups K/8 * 128 bytes apart (stride byte offset).  One thread issues the
 // MMAs and commits them to an mbarrier; every wait on it is bounded and ends the kernel with
-// FLAG_TIMEOUT (TMEM freed) if the MMAs do not complete.
+// FLAG_TIMEOUT (TMEM freed) if the MMAs do not complete.  The sigmoid of SiLU is taken as
+// (1 + tanh(z/2)) / 2 with the hardware tanh (tanh.approx.f32, relative error ~2^-11, below the
+// bf16 rounding of the activations).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -25,7 +28,7 @@ namespace mdk {
 
 namespace {
 
-constexpr int kTcThreads = 128;
+constexpr int kTcThreads = 256;   // two warpgroups
 constexpr int kTmemCols = 128;
 constexpr unsigned kWaitPolls = 4000000u;   // x >= 32 ns each: > 0.1 s before giving up
 // shared memory layout (bytes)
@@ -33,8 +36,9 @@ constexpr int kSmImg = 0;                       // weights image, kSurImgBytes
 constexpr int kSmG = kSmImg + kSurImgBytes;     // x tile, kSurTileBytes
 constexpr int kSmAct = kSmG + kSurTileBytes;    // 128 x 64 bf16 activations (16 KB)
 constexpr int kSmPar = kSmAct + 16384;          // b1, b2, w3, ginv (64+64+64+32 floats), b3
-constexpr int kSmBar = kSmPar + 1024;           // mbarrier (8 B) + TMEM address (4 B)
-constexpr int kSmBytes = kSmBar + 16;
+constexpr int kSmE = kSmPar + 1024;             // energy partials of warpgroup 1 (128 floats)
+constexpr int kSmBar = kSmE + 512;              // MMA mbarrier, TMA mbarrier (8 B each), TMEM address
+constexpr int kSmBytes = kSmBar + 32;
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -83,6 +87,18 @@ __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// Bulk (untiled) TMA copy global -> shared, completion counted on the mbarrier.  Both addresses
+// 16-byte aligned, size a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     for (unsigned it = 0; it < kWaitPolls; ++it) {
         if (mbar_test(bar, parity)) return true;
@@ -120,16 +136,21 @@ __device__ __forceinline__ void put_row16(unsigned char *act, int row, int c0, c
                                                         pack_bf16(v[12], v[13]), pack_bf16(v[14], v[15]));
 }
 
-__device__ __forceinline__ float sigm(float z) { return 1.f / (1.f + __expf(-z)); }
+__device__ __forceinline__ float sigm(float z) {
+    float t;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(0.5f * z));
+    return fmaf(0.5f, t, 0.5f);
+}
 
 __global__ void __launch_bounds__(kTcThreads, 4) k_sur_net_tc(Atoms A, SurNet S, int ntiles) {
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned char *img = sm + kSmImg, *gt = sm + kSmG, *act = sm + kSmAct;
     float *b1 = reinterpret_cast<float *>(sm + kSmPar), *b2 = b1 + 64, *w3 = b2 + 64, *ginv = w3 + 64, *b3 = ginv + 32;
+    float *epart = reinterpret_cast<float *>(sm + kSmE);
     uint64_t *bar_p = reinterpret_cast<uint64_t *>(sm + kSmBar);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + kSmBar + 8);
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const uint32_t bar = smem_addr(bar_p);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + kSmBar + 16);
+    const int tid = threadIdx.x, warp = tid >> 5, grp = tid >> 7, row = tid & 127;
+    const uint32_t bar = smem_addr(bar_p), bar_g = smem_addr(bar_p + 1);
 
     // weights (bf16 image) and FP32 biases
     for (int q = tid; q < kSurImgBytes / 16; q += kTcThreads)
@@ -144,6 +165,7 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_sur_net_tc(Atoms A, SurNet S,
     if (tid == 0) {
         *b3 = th[kSurParams - 1];
         mbar_init(bar, 1);
+        mbar_init(bar_g, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -157,21 +179,23 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_sur_net_tc(Atoms A, SurNet S,
     __syncthreads();
     tc_after();
     const uint32_t tmem = *tslot;
-    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;   // this warp's 32 TMEM lanes
+    const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;   // this warp's 32 TMEM lanes
     const uint32_t a_g = smem_addr(gt), a_act = smem_addr(act), a_img = smem_addr(img);
-    uint32_t phase = 0;
+    const int cA = 32 * grp;   // this warpgroup's columns of a 64-column accumulator
+    const int cB = 16 * grp;   // ... and of the 32-column input gradient
+    uint32_t phase = 0, phase_g = 0;
     bool ok = true;
 
     for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-        const int atom = tile * kSurTile + tid;
+        const int atom = tile * kSurTile + row;
         const bool live = atom < A.n;
-        {
-            const uint4 *src = reinterpret_cast<const uint4 *>(S.Gt + (size_t)tile * kSurTileBytes);
-            for (int q = tid; q < kSurTileBytes / 16; q += kTcThreads) reinterpret_cast<uint4 *>(gt)[q] = src[q];
+        if (tid == 0) {
+            mbar_expect_tx(bar_g, kSurTileBytes);
+            bulk_g2s(a_g, S.Gt + (size_t)tile * kSurTileBytes, kSurTileBytes, bar_g);
         }
-        async_smem_fence();
-        tc_before();
-        __syncthreads();
+        ok = __syncthreads_and(mbar_wait(bar_g, phase_g));
+        phase_g ^= 1;
+        if (!ok) break;
         // layer 1: D0 = x W1^T  (K = 32: 2 MMAs of K = 16)
         if (tid == 0) {
             tc_after();
@@ -187,7 +211,7 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_sur_net_tc(Atoms A, SurNet S,
         tc_after();
         // epilogue 1: a1 = s(D0 + b1)
 #pragma unroll
-        for (int c0 = 0; c0 < 64; c0 += 16) {
+        for (int c0 = cA; c0 < cA + 32; c0 += 16) {
             float v[16];
             tmem_ld16(tmem + lane_off + c0, v);
 #pragma unroll
@@ -195,7 +219,7 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_sur_net_tc(Atoms A, SurNet S,
                 const float z = v[i] + b1[c0 + i];
                 v[i] = z * sigm(z);
             }
-            put_row16(act, tid, c0, v);
+            put_row16(act, row, c0, v);
         }
         async_smem_fence();
         tc_before();
@@ -216,7 +240,7 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_sur_net_tc(Atoms A, SurNet S,
         // epilogue 2: E and d2 = w3 s'(z2)
         float e = 0.f;
 #pragma unroll
-        for (int c0 = 0; c0 < 64; c0 += 16) {
+        for (int c0 = cA; c0 < cA + 32; c0 += 16) {
             float v[16];
             tmem_ld16(tmem + lane_off + 64 + c0, v);
 #pragma unroll
@@ -226,9 +250,9 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_sur_net_tc(Atoms A, SurNet S,
                 e = fmaf(w3[c0 + i], z * sg, e);
                 v[i] = w3[c0 + i] * sg * fmaf(z, 1.f - sg, 1.f);
             }
-            put_row16(act, tid, c0, v);
+            put_row16(act, row, c0, v);
         }
-        if (live) A.e_atom[atom] = (double)(e + *b3);
+        if (grp == 1) epart[row] = e;
         async_smem_fence();
         tc_before();
         __syncthreads();
@@ -241,13 +265,14 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_sur_net_tc(Atoms A, SurNet S,
                          sdesc(a_img + kSurImgW2T + ks * 256, 128, 1024), idesc_bf16(128, 64), ks > 0);
             mma_commit(bar);
         }
+        if (grp == 0 && live) A.e_atom[atom] = (double)(e + epart[row] + *b3);
         ok = __syncthreads_and(mbar_wait(bar, phase));
         phase ^= 1;
         if (!ok) break;
         tc_after();
         // epilogue 3: d1 = D1 s'(z1), z1 = D0 + b1
 #pragma unroll
-        for (int c0 = 0; c0 < 64; c0 += 16) {
+        for (int c0 = cA; c0 < cA + 32; c0 += 16) {
             float v[16], z1[16];
             tmem_ld16(tmem + lane_off + 64 + c0, v);
             tmem_ld16(tmem + lane_off + c0, z1);
@@ -257,7 +282,7 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_sur_net_tc(Atoms A, SurNet S,
                 const float sg = sigm(z);
                 v[i] *= sg * fmaf(z, 1.f - sg, 1.f);
             }
-            put_row16(act, tid, c0, v);
+            put_row16(act, row, c0, v);
         }
         async_smem_fence();
         tc_before();
@@ -275,17 +300,16 @@ __global__ void __launch_bounds__(kTcThreads, 4) k_sur_net_tc(Atoms A, SurNet S,
         phase ^= 1;
         if (!ok) break;
         tc_after();
-        // epilogue 4: dE/dG = D0 * ginv
-#pragma unroll
-        for (int c0 = 0; c0 < 32; c0 += 16) {
+        // epilogue 4: dE/dG = D0 * ginv (16 columns per warpgroup)
+        {
             float v[16];
-            tmem_ld16(tmem + lane_off + c0, v);
+            tmem_ld16(tmem + lane_off + cB, v);
             if (live) {
-                float4 *dst = reinterpret_cast<float4 *>(S.g + (size_t)atom * kSurNb + c0);
+                float4 *dst = reinterpret_cast<float4 *>(S.g + (size_t)atom * kSurNb + cB);
 #pragma unroll
                 for (int q = 0; q < 4; q++)
-                    dst[q] = make_float4(v[4 * q] * ginv[c0 + 4 * q], v[4 * q + 1] * ginv[c0 + 4 * q + 1],
-                                         v[4 * q + 2] * ginv[c0 + 4 * q + 2], v[4 * q + 3] * ginv[c0 + 4 * q + 3]);
+                    dst[q] = make_float4(v[4 * q] * ginv[cB + 4 * q], v[4 * q + 1] * ginv[cB + 4 * q + 1],
+                                         v[4 * q + 2] * ginv[cB + 4 * q + 2], v[4 * q + 3] * ginv[cB + 4 * q + 3]);
             }
         }
         tc_before();
