@@ -207,6 +207,15 @@ def step_bytes(n, sum_counts, precision):
     return density + force, density, force
 
 
+REBUILD_PARTS = ("bin", "tile_sums", "top_scan", "apply", "scatter", "cell_sort", "gather", "copyback", "list")
+
+
+def rebuild_parts(prof):
+    """Sub-phase times of a list rebuild (ms per rebuild) from a profiled run's stamps."""
+    nr = max(1, int(prof.get("rebuilds", 0)))
+    return {name: prof["ms_rebuild_part"][q] / nr for q, name in enumerate(REBUILD_PARTS)} | {"rebuilds": nr}
+
+
 def _time_steps(torch, s, stream, k, barrier, clocks_index=None):
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
@@ -265,6 +274,7 @@ def run_ours(args):
         s.step(min(args.steps, 200))
         prof = s.profile()
         s.set_profiling(False)
+        prof["rebuilds"] = s.energy()["n_rebuilds"] - e1["n_rebuilds"]
         res[precision] = dict(ms=ms, prof=prof, e0=e0, e1=e1, counts=counts, clocks=clocks,
                               launches=launches, lanes=lanes)
         if precision == "mixed":
@@ -279,7 +289,7 @@ def run_ours(args):
         if rank == 0:
             r = res["mixed"]
             print(json.dumps({"profile_case": True, "n_atoms": n, "ms_per_step": r["ms"] / args.steps,
-                              "lanes": r["lanes"],
+                              "lanes": r["lanes"], "rebuild_ms_per_rebuild": rebuild_parts(r["prof"]),
                               "phase_ms": {k: r["prof"]["ms_" + k] / max(1, r["prof"]["n_" + k])
                                            for k in ("kick", "rebuild", "density", "force")}}))
         return 0
@@ -354,7 +364,8 @@ def run_ours(args):
                 "nve_drift_ev_per_atom": de, "steps_timed": args.steps, "lanes_per_atom": q["lanes"],
                 "rebuilds_in_timed_region": q["e1"]["n_rebuilds"] - q["e0"]["n_rebuilds"],
                 "phase_ms_per_step_profiled_repeat": {k: qp["ms_" + k] / max(1, qp["n_" + k])
-                                                       for k in ("kick", "rebuild", "density", "force")}}
+                                                       for k in ("kick", "rebuild", "density", "force")},
+                "rebuild_ms_per_rebuild": rebuild_parts(qp)}
 
     line = {
         "metric": METRIC, "value": job_value(n, world, args.steps, r["ms"]), "unit": UNIT,

@@ -115,8 +115,8 @@ typedef struct {
                               multiplied by (1 + rate*dt) (§2.2 strain-rate loading) */
     void *stream;          /* cudaStream_t, or NULL */
     int32_t lanes_per_atom; /* threads sharing one atom's neighbour sums in the force passes:
-                               1, 2, 4 or 8, or 0 = chosen from the expected neighbour count
-                               (see md_tune).  Results depend on it only in rounding. */
+                               1, 2, 4, 8, 16 or 32, or 0 = chosen from the expected neighbour
+                               count (see md_tune).  Results depend on it only in rounding. */
     int32_t pad;
 } md_config;
 

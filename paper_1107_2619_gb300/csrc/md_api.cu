@@ -124,7 +124,7 @@ float ulp32(double x) {
     return (float)std::ldexp(1.0, e - 24);
 }
 
-// FP32 screening band of the list build (ph::build_row).  Each wrapped FP32 coordinate is
+// FP32 screening band of the list build (ph::build_cell_group).  Each wrapped FP32 coordinate is
 // within u/2 of its FP64 value (u = ulp32 of the largest box edge); adding the FP32 box edge
 // for a periodic neighbour cell (itself within u/2 of the FP64 edge) rounds once more (< u)
 // and the difference once more (< ulp32(r_list)/2 near the cutoff), so each component of d is
@@ -139,6 +139,12 @@ void list_band(const md_ctx *c, float &lo, float &hi) {
     double band = 4.0 * bound;
     lo = std::nextafter((float)(c->rl2 - band), -INFINITY);
     hi = std::nextafter((float)(c->rl2 + band), INFINITY);
+}
+
+// Lanes per link cell of the list build, from the mean cell occupancy.
+int ph_list_group(const md_ctx *c) {
+    const double m = c->C.ncell > 0 ? (double)c->n / (double)c->C.ncell : 0.0;
+    return m <= 3.0 ? 4 : (m <= 6.0 ? 8 : (m <= 12.0 ? 16 : 32));
 }
 
 int cells_along(double L, double r_list) {
@@ -206,7 +212,7 @@ cudaError_t reset_errors(md_ctx *ctx) {
 cudaError_t enqueue_rebuild(md_ctx *ctx) {
     float lo, hi;
     list_band(ctx, lo, hi);
-    return launch_rebuild(ctx->A, ctx->C, ctx->rl2, lo, hi, ctx->stream);
+    return launch_rebuild(ctx->A, ctx->C, ctx->rl2, lo, hi, ph_list_group(ctx), ctx->stream);
 }
 
 // Surrogate network at the current positions (list valid): descriptors, then energies and
@@ -232,7 +238,7 @@ cudaError_t enqueue_sur_step(md_ctx *ctx, bool energy, bool scheduled_rebuild, i
     if (e == cudaSuccess && scheduled_rebuild) e = launch_set_rebuild(ctx->d_flags, s);
     float lo, hi;
     list_band(ctx, lo, hi);
-    if (e == cudaSuccess) e = launch_rebuild(ctx->A, ctx->C, ctx->rl2, lo, hi, s);
+    if (e == cudaSuccess) e = launch_rebuild(ctx->A, ctx->C, ctx->rl2, lo, hi, ph_list_group(ctx), s);
     if (e == cudaSuccess) e = launch_clear_rebuild(ctx->d_flags, s);
     if (e == cudaSuccess) e = enqueue_sur_net(ctx, s);
     if (e == cudaSuccess)
@@ -330,6 +336,7 @@ StepParams step_params(md_ctx *ctx, int n_steps) {
     sp.rebuild_every = ctx->cfg.rebuild_every;
     sp.rl2 = ctx->rl2;
     list_band(ctx, sp.band_lo, sp.band_hi);
+    sp.list_group = ph_list_group(ctx);
     sp.spin_limit = kSpinLimit;
     return sp;
 }
@@ -445,17 +452,38 @@ md_status create_common(md_ctx *ctx, const md_config *cfg, const md_potential *p
     ctx->dt = cfg->dt_fs;
     ctx->half_dt = 0.5 * cfg->dt_fs;
     ctx->strain_scale = 1.0 + cfg->strain_rate_zz * cfg->dt_fs * 1.0e-15;
-    // link cells of each replica (fixed in fractional coordinates, >= r_list wide, >= 3 per edge)
+    // link cells of each replica (fixed in fractional coordinates, >= 3 per edge), r_list wide.
+    // Built with MD_CELL_REACH_MAX=2, cells are r_list / 2 wide (a 5 x 5 x 5 stencil: 15.6 r_list^3
+    // of list candidates instead of 27 r_list^3) when every edge holds >= 5 of them and they hold
+    // >= 3 atoms on average: a faster list build, but on GB300 slightly slower passes (the coarser
+    // cell order keeps more of a warp's neighbours in the same lines), so it is off by default.
     ctx->rc.resize(n_rep);
+    for (int k = 0; k < n_rep * 3; k++)
+        if (cells_along(L[k], ctx->r_list) < 3) {
+            ctx->err = "a box edge holds fewer than 3 link cells of width r_cut + skin";
+            return MD_ERR_BOX;
+        }
+#ifndef MD_CELL_REACH_MAX
+#define MD_CELL_REACH_MAX 1
+#endif
+    int reach = MD_CELL_REACH_MAX >= 2 ? 2 : 1;
+    if (reach == 2) {
+        long long half_cells = 0;
+        for (int r = 0; r < n_rep; r++) {
+            long long c = 1;
+            for (int k = 0; k < 3; k++) {
+                const int nc = cells_along(L[3 * r + k], 0.5 * ctx->r_list);
+                if (nc < 5) reach = 1;
+                c *= nc;
+            }
+            half_cells += c;
+        }
+        if (half_cells <= 0 || (double)n < 3.0 * (double)half_cells) reach = 1;
+    }
+    ctx->C.reach = reach;
     long long ncell = 0;
     for (int r = 0; r < n_rep; r++) {
-        for (int k = 0; k < 3; k++) {
-            ctx->rc[r].nc[k] = cells_along(L[3 * r + k], ctx->r_list);
-            if (ctx->rc[r].nc[k] < 3) {
-                ctx->err = "a box edge holds fewer than 3 link cells of width r_cut + skin";
-                return MD_ERR_BOX;
-            }
-        }
+        for (int k = 0; k < 3; k++) ctx->rc[r].nc[k] = cells_along(L[3 * r + k], ctx->r_list / reach);
         ctx->rc[r].base = (int)ncell;
         ncell += (long long)ctx->rc[r].nc[0] * ctx->rc[r].nc[1] * ctx->rc[r].nc[2];
         if (ncell > INT32_MAX / 2) return MD_ERR_BOX;
@@ -463,7 +491,8 @@ md_status create_common(md_ctx *ctx, const md_config *cfg, const md_potential *p
     // lanes per atom: given, or from the expected neighbour count (4/3 pi r_list^3 x density)
     {
         const int want = cfg->lanes_per_atom;
-        if (want != 0 && want != 1 && want != 2 && want != 4 && want != 8) return MD_ERR_ARG;
+        if (want != 0 && want != 1 && want != 2 && want != 4 && want != 8 && want != 16 && want != 32)
+            return MD_ERR_ARG;
         if (want) {
             ctx->lanes = want;
         } else {
@@ -512,7 +541,7 @@ md_status create_common(md_ctx *ctx, const md_config *cfg, const md_potential *p
     chk(dalloc(ctx, &A.id, n)); chk(dalloc(ctx, &A.id_tmp, n)); chk(dalloc(ctx, &A.rank, n));
     chk(dalloc(ctx, &A.spec, n)); chk(dalloc(ctx, &A.spec_tmp, n)); chk(dalloc(ctx, &A.cell_of, n));
     chk(dalloc(ctx, &A.slot, n)); chk(dalloc(ctx, &A.order, n)); chk(dalloc(ctx, &A.count, n));
-    chk(dalloc(ctx, &A.nbr, (size_t)n * cfg->k_max));
+    chk(dalloc(ctx, &A.nbr, nbr_entries(n, cfg->k_max)));
     if (n_rep > 1) chk(dalloc(ctx, &A.rep, n));
     A.sorted = A.cell_of;  // cell_of is consumed by the scatter before the in-cell sort writes
     // partial-sum rows: a stand-alone force launch (<= 8 lanes) or a persistent grid
@@ -911,8 +940,8 @@ md_status md_step(md_ctx *ctx, int32_t n_steps) {
         for (int r = 0; r < ctx->n_rep; r++) {
             double Lz = ctx->L[3 * r + 2];
             for (int32_t s = 0; s < n_steps; s++) Lz *= ctx->strain_scale;
-            const int nc = cells_along(std::fmin(Lz, ctx->L[3 * r + 2]), ctx->r_list);
-            if (nc < 3) return fail(ctx, MD_ERR_BOX, "strain made a box thinner than 3 link cells");
+            const int nc = cells_along(std::fmin(Lz, ctx->L[3 * r + 2]), ctx->r_list / ctx->C.reach);
+            if (nc < 2 * ctx->C.reach + 1) return fail(ctx, MD_ERR_BOX, "strain made a box thinner than 3 link cells");
             if (nc < ctx->rc[r].nc[2]) {
                 ctx->rc[r].nc[2] = nc;
                 changed = true;
@@ -953,6 +982,12 @@ md_status md_step(md_ctx *ctx, int32_t n_steps) {
     if (graph) {
         auto it = ctx->graphs.find(n_steps);
         if (it == ctx->graphs.end()) {
+            if (!ctx->sur) {
+                StepParams prep = step_params(ctx, 0);
+                int pg = 0;
+                MD_CK(launch_step(ctx->A, ctx->C, ctx->P, ctx->precision, ctx->lanes, prep, ctx->d_bar, nullptr, &pg,
+                                  ctx->stream));
+            }
             cudaGraph_t g = nullptr;
             cudaGraphExec_t ge = nullptr;
             if (!ctx->cap_stream) MD_CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
@@ -1116,7 +1151,7 @@ md_status md_tune(md_ctx *ctx, int32_t *lanes_out) {
         MD_CK(cudaEventCreate(&e1));
         float best = 1e30f;
         int best_t = ctx->lanes;
-        for (int t = 1; t <= 8; t *= 2) {
+        for (int t = 1; t <= 32; t *= 2) {
             for (int rep = 0; rep < 4; rep++) {  // first round is a warm-up
                 MD_CK(cudaEventRecord(e0, ctx->stream));
                 MD_CK(launch_density(ctx->A, ctx->P, ctx->precision, t, ctx->stream));

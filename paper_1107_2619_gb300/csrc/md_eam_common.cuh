@@ -126,9 +126,10 @@ __device__ __forceinline__ void lane_sum_df(float &hi, float &lo) {
 }
 
 // Per-block FP64 partial sums (fixed order), stored as out[q * stride + block]: every thread of
-// the block must call it.
+// the block (NT threads) must call it.
+template <int NT = kThreads>
 __device__ __forceinline__ void block_partials(double (&v)[kPartials], double *out, int stride) {
-    __shared__ double sh[kThreads / 32][kPartials];
+    __shared__ double sh[NT / 32][kPartials];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int q = 0; q < kPartials; q++) {
@@ -140,7 +141,7 @@ __device__ __forceinline__ void block_partials(double (&v)[kPartials], double *o
     __syncthreads();
     if (threadIdx.x < kPartials) {
         double s = 0.0;
-        for (int k = 0; k < kThreads / 32; k++) s += sh[k][threadIdx.x];
+        for (int k = 0; k < NT / 32; k++) s += sh[k][threadIdx.x];
         out[(size_t)threadIdx.x * stride + blockIdx.x] = s;
     }
 }

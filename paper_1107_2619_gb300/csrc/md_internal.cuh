@@ -92,7 +92,7 @@ struct Atoms {
     int32_t *id, *id_tmp, *rank, *spec, *spec_tmp;
     int32_t *cell_of, *slot, *order;
     int32_t *sorted;                         // order after the in-cell sort (aliases cell_of)
-    int32_t *nbr, *count;                    // nbr[i*k_max + k], k < min(count, k_max)
+    int32_t *nbr, *count;                    // list entry k of atom i: see NbrRow; k < min(count, k_max)
     double *partials;                        // [kPartials][part_stride] per-block sums
     int part_stride;
     int32_t *rep;                            // replica of each slot (NULL: one system)
@@ -100,8 +100,24 @@ struct Atoms {
     Flags *flags;
 };
 
+// The neighbour list in planes of 4 entries: entry k of atom i is
+// nbr[((k / 4) * n + i) * 4 + k % 4], so the 4 lanes of 8 consecutive atoms that read entries
+// 4m..4m+3 read one 128-byte line, and a warp of 32 atoms writing entry k touches 4 lines.
+// Allocated as ceil(k_max / 4) planes of 4 n entries.
+struct NbrRow {
+    int32_t *p;        // &nbr[4 i]
+    long long plane;   // 4 n
+    __host__ __device__ int32_t *ptr(int k) const { return p + (long long)(k >> 2) * plane + (k & 3); }
+    __host__ __device__ int32_t &operator[](int k) const { return *ptr(k); }
+};
+__host__ __device__ inline NbrRow nbr_row(const Atoms &A, int i) {
+    return NbrRow{A.nbr + 4 * (size_t)i, 4LL * A.n};
+}
+inline size_t nbr_entries(int64_t n, int k_max) { return (size_t)((k_max + 3) / 4) * 4 * (size_t)n; }
+
 struct Cells {
     int ncell;   // all replicas
+    int reach;   // cells are r_list / reach wide; the list stencil is (2 reach + 1)^3 cells
     int ntiles;
     RepCells *rc;  // [n_rep], device
     int32_t *cell_count, *cell_start, *tile_sums;
@@ -111,7 +127,7 @@ struct Cells {
 cudaError_t launch_set_rebuild(Flags *f, cudaStream_t s);
 cudaError_t launch_clear_rebuild(Flags *f, cudaStream_t s);
 cudaError_t launch_rebuild(const Atoms &A, const Cells &C, double rl2, float band_lo, float band_hi,
-                           cudaStream_t s);
+                           int list_group, cudaStream_t s);
 cudaError_t launch_check_displacement(const Atoms &A, double lim2, cudaStream_t s);
 cudaError_t launch_wrap(const Atoms &A, cudaStream_t s);
 // lanes = T lanes per atom (1, 2, 4, 8, 16 or 32)
@@ -136,9 +152,12 @@ struct StepParams {
     int rebuild_every;    // scheduled rebuild period (0: none)
     double rl2;
     float band_lo, band_hi;
+    int list_group;       // lanes per link cell in the list build (8, 16 or 32)
     unsigned long long spin_limit;
     int withhold_arrival;  // self-test of the bounded wait: block 0 skips its first arrival
 };
+// With sp.n_steps == 0 it only prepares the launch (function attributes, occupancy query):
+// done before a stream capture, so that a captured launch makes no other API call.
 cudaError_t launch_step(const Atoms &A, const Cells &C, const Pot &P, int precision, int lanes,
                         const StepParams &sp, GridBarrier *bar, unsigned long long *stamps, int *grid_out,
                         cudaStream_t s);

@@ -10,7 +10,8 @@
 //   k_scatter    order[cell_start[c] + slot] = atom
 //   k_cell_sort  stable order inside a cell: ascending caller atom id (deterministic)
 //   k_gather / k_copyback   renumber every per-atom array into cell order
-//   k_build_list full list: the 27 cells around the atom's cell, |r_ij|^2 < r_list^2
+//   k_build_list full list: the 27 cells around each cell, |r_ij|^2 < r_list^2, a group of
+//                lanes per cell
 // Link cells are fixed in fractional coordinates and at least r_list wide, so every pair
 // closer than r_list lies in adjacent cells (the hybrid NL-LCM of §3.2.1).
 #include <cuda_runtime.h>
@@ -81,16 +82,11 @@ __global__ void k_copyback(Atoms A) {
     for (long long k = gtid(); k < A.n; k += gstride()) ph::copyback_atom(A, A.boxes, (int)k);
 }
 
+template <int G>
 __global__ void __launch_bounds__(kThreads) k_build_list(Atoms A, Cells C, double rl2, float band_lo,
                                                          float band_hi) {
     if (!ph::rebuild_requested(A.flags)) return;
-    int m = 0;
-    // whole warps iterate together (the max reduction below needs all 32 lanes)
-    const long long end = ((long long)A.n + 31) / 32 * 32;
-    for (long long i = gtid(); i < end; i += gstride()) {
-        const int cnt = i < A.n ? ph::build_row(A, C, A.boxes, (int)i, rl2, band_lo, band_hi) : 0;
-        m = max(m, cnt);
-    }
+    int m = ph::build_cells<G>(A, C, A.boxes, gtid() >> 5, gstride() >> 5, threadIdx.x & 31, rl2, band_lo, band_hi);
     m = __reduce_max_sync(0xffffffffu, m);
     if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(&A.flags->max_count, m);
 }
@@ -119,7 +115,7 @@ cudaError_t launch_clear_rebuild(Flags *f, cudaStream_t s) {
 }
 
 cudaError_t launch_rebuild(const Atoms &A, const Cells &C, double rl2, float band_lo, float band_hi,
-                           cudaStream_t s) {
+                           int list_group, cudaStream_t s) {
     const int nb = capped_blocks(A.n, kThreads);
     const int ntiles = (C.ncell + kScanThreads * ph::kScanItems - 1) / (kScanThreads * ph::kScanItems);
     if (A.n > 0) k_bin<<<nb, kThreads, 0, s>>>(A, C);
@@ -131,7 +127,11 @@ cudaError_t launch_rebuild(const Atoms &A, const Cells &C, double rl2, float ban
         k_cell_sort<<<capped_blocks((long long)C.ncell * 32, kThreads), kThreads, 0, s>>>(A, C);
         k_gather<<<nb, kThreads, 0, s>>>(A);
         k_copyback<<<nb, kThreads, 0, s>>>(A);
-        k_build_list<<<nb, kThreads, 0, s>>>(A, C, rl2, band_lo, band_hi);
+        const int nbl = capped_blocks((long long)C.ncell * list_group, kThreads);
+        if (list_group == 4) k_build_list<4><<<nbl, kThreads, 0, s>>>(A, C, rl2, band_lo, band_hi);
+        else if (list_group == 8) k_build_list<8><<<nbl, kThreads, 0, s>>>(A, C, rl2, band_lo, band_hi);
+        else if (list_group == 16) k_build_list<16><<<nbl, kThreads, 0, s>>>(A, C, rl2, band_lo, band_hi);
+        else k_build_list<32><<<nbl, kThreads, 0, s>>>(A, C, rl2, band_lo, band_hi);
     }
     return cudaGetLastError();
 }

@@ -36,8 +36,31 @@ __device__ __forceinline__ float4 phi_half32(const double4_32a *tab, size_t idx)
     return __ldg(reinterpret_cast<const float4 *>(tab + idx) + 1);
 }
 
+// The same rows from a copy of the table in the kernel's dynamic shared memory (SMT: one
+// species; row k = float4 V coefficients, float4 phi coefficients).
+template <bool SMT>
+__device__ __forceinline__ float4 phi_row(const Pot &P, size_t idx) {
+    if (SMT) {
+        extern __shared__ float4 sm_table_f4[];
+        return sm_table_f4[2 * idx + 1];
+    }
+    return phi_half32(P.VP32, idx);
+}
+
+template <bool SMT>
+__device__ __forceinline__ void vp_row(const Pot &P, size_t idx, float (&v)[4], float (&p)[4]) {
+    if (SMT) {
+        extern __shared__ float4 sm_table_f4[];
+        const float4 a = sm_table_f4[2 * idx], b = sm_table_f4[2 * idx + 1];
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        p[0] = b.x; p[1] = b.y; p[2] = b.z; p[3] = b.w;
+        return;
+    }
+    row32(P.VP32, idx, v, p);
+}
+
 // ======================================================================= mixed precision
-template <int T, int KIND, bool MULTI>
+template <int T, int KIND, bool MULTI, bool SMT = false>
 __device__ __forceinline__ void density32_item(const Atoms &A, const Pot &P, const Box *boxes, long long g) {
     const int i = (int)(g / T), lane = (int)(g & (T - 1));
     const bool live = i < A.n;
@@ -51,7 +74,7 @@ __device__ __forceinline__ void density32_item(const Atoms &A, const Pot &P, con
         pi = A.posf[i];
         si = MULTI ? __float_as_int(pi.w) : 0;
         const int cnt = min(A.count[i], A.k_max);
-        const int *__restrict__ row = A.nbr + (size_t)i * A.k_max;
+        const NbrRow row = nbr_row(A, i);
         unsigned viol = 0;
         // one neighbour: phi(r) if r < r_cut, else 0 (no branch, so loads of the next pair can issue)
         auto term = [&](const float4 &pj) -> float {
@@ -70,20 +93,29 @@ __device__ __forceinline__ void density32_item(const Atoms &A, const Pot &P, con
                 bool below;
                 const int kr = knot_row((r - P.r_minf) * P.inv_drf, P.nk, t, below);
                 viol += (below && inside) ? 1u : 0u;
-                const float4 c = phi_half32(P.VP32, (size_t)(si * P.ns + sj) * P.nk + kr);
+                const float4 c = phi_row<SMT>(P, (size_t)(si * P.ns + sj) * P.nk + kr);
                 phi = cubic(t, c.x, c.y, c.z, c.w, below, d);
             }
             return inside ? phi : 0.f;
         };
+        // two neighbours per iteration, software-pipelined: the positions of the next iteration
+        // and the list entries of the one after are loaded before this iteration's terms are
+        // computed, so the dependent loads of one neighbour overlap the arithmetic of others
+        auto entry = [&](int q) { return q < cnt ? __ldg(row.ptr(q)) : i; };
         int k = lane;
+        float4 p0 = __ldg(A.posf + entry(k)), p1 = __ldg(A.posf + entry(k + T));
+        int n0 = entry(k + 2 * T), n1 = entry(k + 3 * T);
         for (; k + T < cnt; k += 2 * T) {
-            const int j0 = __ldg(row + k), j1 = __ldg(row + k + T);
-            const float4 p0 = __ldg(A.posf + j0), p1 = __ldg(A.posf + j1);
+            const float4 q0 = __ldg(A.posf + n0), q1 = __ldg(A.posf + n1);
+            n0 = entry(k + 4 * T);
+            n1 = entry(k + 5 * T);
             const float a0 = term(p0), a1 = term(p1);
             two_sum_add(hi, lo, a0);
             two_sum_add(hi, lo, a1);
+            p0 = q0;
+            p1 = q1;
         }
-        if (k < cnt) two_sum_add(hi, lo, term(__ldg(A.posf + __ldg(row + k))));
+        if (k < cnt) two_sum_add(hi, lo, term(p0));
         if (viol) atomicAdd(&A.flags->range_violations, (unsigned long long)viol);
     }
     lane_sum_df<T>(hi, lo);
@@ -99,7 +131,7 @@ __device__ __forceinline__ void density32_item(const Atoms &A, const Pot &P, con
 }
 
 // Returns the atom index for the lane that finished atom i (lane 0 of a live atom), else -1.
-template <int T, int KIND, bool MULTI, bool ENERGY>
+template <int T, int KIND, bool MULTI, bool ENERGY, bool SMT = false>
 __device__ __forceinline__ int force32_item(const Atoms &A, const Pot &P, const Box *boxes, long long g,
                                             double half_dt, bool kick, double (&part)[kPartials]) {
     const int i = (int)(g / T), lane = (int)(g & (T - 1));
@@ -114,7 +146,7 @@ __device__ __forceinline__ int force32_item(const Atoms &A, const Pot &P, const 
         const float Fpi = pi.w;
         const int si = MULTI ? A.spec[i] : 0;
         const int cnt = min(A.count[i], A.k_max);
-        const int *__restrict__ row = A.nbr + (size_t)i * A.k_max;
+        const NbrRow row = nbr_row(A, i);
         unsigned viol = 0;
         // one neighbour: its pair force (zero beyond r_cut; no branch, so loads of the next
         // pair can issue early) and, on the energy step, its energy and virial
@@ -139,7 +171,7 @@ __device__ __forceinline__ int force32_item(const Atoms &A, const Pot &P, const 
                 const int kr = knot_row((r - P.r_minf) * P.inv_drf, P.nk, t, below);
                 viol += (below && inside) ? 1u : 0u;
                 float cv[4], cp[4], dVk, dab;
-                row32(P.VP32, (size_t)(si * P.ns + sj) * P.nk + kr, cv, cp);
+                vp_row<SMT>(P, (size_t)(si * P.ns + sj) * P.nk + kr, cv, cp);
                 V = cubic(t, cv[0], cv[1], cv[2], cv[3], below, dVk);
                 cubic(t, cp[0], cp[1], cp[2], cp[3], below, dab);
                 float gk;
@@ -168,17 +200,19 @@ __device__ __forceinline__ int force32_item(const Atoms &A, const Pot &P, const 
                 wxy = fmaf(hg * dx, dy, wxy);
             }
         };
+        // two neighbours per iteration; the list entries of the next iteration are loaded before
+        // this iteration's positions are used (one dependent load less on the critical path)
         int k = lane;
+        int j0 = k < cnt ? __ldg(row.ptr(k)) : 0, j1 = k + T < cnt ? __ldg(row.ptr(k + T)) : 0;
         for (; k + T < cnt; k += 2 * T) {
-            const int j0 = __ldg(row + k), j1 = __ldg(row + k + T);
             const float4 p0 = __ldg(A.p2f + j0), p1 = __ldg(A.p2f + j1);
-            pair(j0, p0);
-            pair(j1, p1);
+            const int ja = j0, jb = j1, kn = k + 2 * T;
+            j0 = kn < cnt ? __ldg(row.ptr(kn)) : 0;
+            j1 = kn + T < cnt ? __ldg(row.ptr(kn + T)) : 0;
+            pair(ja, p0);
+            pair(jb, p1);
         }
-        if (k < cnt) {
-            const int j0 = __ldg(row + k);
-            pair(j0, __ldg(A.p2f + j0));
-        }
+        if (k < cnt) pair(j0, __ldg(A.p2f + j0));
         if (viol) atomicAdd(&A.flags->range_violations, (unsigned long long)viol);
     }
     fx = lane_sum<T>(fx);
@@ -221,9 +255,9 @@ __device__ __forceinline__ void density64_item(const Atoms &A, const Pot &P, con
         pi = A.pos[i];
         si = MULTI ? A.spec[i] : 0;
         const int cnt = min(A.count[i], A.k_max);
-        const int *__restrict__ row = A.nbr + (size_t)i * A.k_max;
+        const NbrRow row = nbr_row(A, i);
         for (int k = lane; k < cnt; k += T) {
-            const int j = __ldg(row + k);
+            const int j = __ldg(row.ptr(k));
             const double4_32a pj = A.pos[j];
             const double dx = mi64(pj.x - pi.x, B.L[0], B.invL[0]);
             const double dy = mi64(pj.y - pi.y, B.L[1], B.invL[1]);
@@ -268,9 +302,9 @@ __device__ __forceinline__ int force64_item(const Atoms &A, const Pot &P, const 
         const double Fpi = pi.w;
         const int si = MULTI ? A.spec[i] : 0;
         const int cnt = min(A.count[i], A.k_max);
-        const int *__restrict__ row = A.nbr + (size_t)i * A.k_max;
+        const NbrRow row = nbr_row(A, i);
         for (int k = lane; k < cnt; k += T) {
-            const int j = __ldg(row + k);
+            const int j = __ldg(row.ptr(k));
             const double4_32a pj = A.p2d[j];
             const double dx = mi64(pj.x - pi.x, B.L[0], B.invL[0]);
             const double dy = mi64(pj.y - pi.y, B.L[1], B.invL[1]);
@@ -351,17 +385,17 @@ __device__ __forceinline__ int force64_item(const Atoms &A, const Pot &P, const 
 }
 
 // Precision-generic front ends.
-template <int PREC, int T, int KIND, bool MULTI>
+template <int PREC, int T, int KIND, bool MULTI, bool SMT = false>
 __device__ __forceinline__ void density_item(const Atoms &A, const Pot &P, const Box *boxes, long long g) {
     if (PREC == MD_PREC_FP64) density64_item<T, KIND, MULTI>(A, P, boxes, g);
-    else density32_item<T, KIND, MULTI>(A, P, boxes, g);
+    else density32_item<T, KIND, MULTI, SMT>(A, P, boxes, g);
 }
 
-template <int PREC, int T, int KIND, bool MULTI, bool ENERGY>
+template <int PREC, int T, int KIND, bool MULTI, bool ENERGY, bool SMT = false>
 __device__ __forceinline__ int force_item(const Atoms &A, const Pot &P, const Box *boxes, long long g,
                                           double half_dt, bool kick, double (&part)[kPartials]) {
     if (PREC == MD_PREC_FP64) return force64_item<T, KIND, MULTI, ENERGY>(A, P, boxes, g, half_dt, kick, part);
-    return force32_item<T, KIND, MULTI, ENERGY>(A, P, boxes, g, half_dt, kick, part);
+    return force32_item<T, KIND, MULTI, ENERGY, SMT>(A, P, boxes, g, half_dt, kick, part);
 }
 
 }  // namespace ps

@@ -236,74 +236,126 @@ __device__ __forceinline__ bool within_exact(const double4_32a &pi, const double
     return r2 < rl2;
 }
 
-// Full list row of atom i (cell order) from the 27 cells around its cell, one thread per
-// atom: the threads of a warp, whose atoms share a link cell, read the same candidate at the
-// same time (one broadcast load each).  Candidates are screened with FP32 wrapped
-// coordinates, shifted by whole box edges for neighbour cells across the periodic boundary
-// (no rounding to the nearest image per candidate); a neighbour cell whose nearest face is
-// beyond r_list (plus the band) is skipped.  Only a candidate whose FP32 r^2 lies in
-// [band_lo, band_hi] (a band wider than the proven FP32 error) is decided by the exact FP64
-// test, so the row is the exact FP64 set, listed by cell in (dz, dy, dx) order and by
-// ascending slot inside a cell.  Returns the neighbour count (rows are cut at k_max).
-__device__ __forceinline__ int build_row(const Atoms &A, const Cells &C, const Box *boxes, int i, double rl2,
-                                         float band_lo, float band_hi) {
-    const int r = replica_of(A, i);
+// Full list rows of the atoms of link cell c (§3.2.1: candidates from the cells around it, 27 for
+// cells r_list wide, 125 for cells r_list / 2 wide) by a group of G lanes (G = 4, 8, 16 or 32;
+// 32 / G cells per warp): lane a of the group takes atoms s + a, s + a + G, ... of the cell.  All
+// lanes of the group walk the same neighbour cells and
+// the same candidates in the same order, so a candidate is one broadcast load for the group and
+// the control flow is uniform inside it.  Candidates are screened with FP32 wrapped coordinates,
+// shifted by whole box edges for neighbour cells across the periodic boundary (no rounding to the
+// nearest image per candidate).  Only a candidate whose FP32 r^2 lies in [band_lo, band_hi] (a band
+// wider than the proven FP32 error) is decided by the exact FP64 test, so each row is the exact
+// FP64 set, listed by cell in (dz, dy, dx) order and by ascending slot inside a cell.  Rows are cut
+// at k_max (the count is kept).  Returns the longest row of this lane's atoms.  The stencil of
+// +-reach cells along each edge needs >= 2 reach + 1 cells per edge (no cell visited twice).
+// The exact test of a candidate in the FP32 band, kept out of line: it is rare, and inlined it
+// would be predicated into every iteration of the candidate loop.
+static __device__ __noinline__ bool within_exact_band(const double4_32a &pi, const double4_32a &pj, const Box &B,
+                                                      double rl2) {
+    return within_exact(pi, pj, B, rl2);
+}
+
+template <int G>
+__device__ __forceinline__ int build_cell_group(const Atoms &A, const Cells &C, const Box *boxes, int c, int gl,
+                                                double rl2, float band_lo, float band_hi) {
+    const int s = C.cell_start[c], e = C.cell_start[c + 1];
+    if (s == e) return 0;
+    const int r = replica_of(A, s);
     const Box &B = boxes[r];
     const RepCells g = C.rc[r];
-    const double4_32a pi = A.pos[i];
-    const float4 fi = A.posf[i];
     const int nx = g.nc[0], ny = g.nc[1], nz = g.nc[2];
-    const int cx = cell_coord(pi.x, B.invL[0], nx);
-    const int cy = cell_coord(pi.y, B.invL[1], ny);
-    const int cz = cell_coord(pi.z, B.invL[2], nz);
+    const int local = c - g.base;
+    const int cx = local % nx, cy = (local / nx) % ny, cz = local / (nx * ny);
     const float Lx = B.Lf[0], Ly = B.Lf[1], Lz = B.Lf[2];
-    const float ex = Lx / nx, ey = Ly / ny, ez = Lz / nz;     // cell edges
-    // distance from the atom to the lower / upper face of its own cell, per axis
-    const float lox = fmaxf(fi.x - cx * ex, 0.f), hix = fmaxf((cx + 1) * ex - fi.x, 0.f);
-    const float loy = fmaxf(fi.y - cy * ey, 0.f), hiy = fmaxf((cy + 1) * ey - fi.y, 0.f);
-    const float loz = fmaxf(fi.z - cz * ez, 0.f), hiz = fmaxf((cz + 1) * ez - fi.z, 0.f);
-    int32_t *row = A.nbr + (size_t)i * A.k_max;
-    int cnt = 0;
-    for (int dz = -1; dz <= 1; dz++) {
-        int z = cz + dz;
-        float sz = 0.f;
-        if (z < 0) { z += nz; sz = -Lz; }
-        if (z >= nz) { z -= nz; sz = Lz; }
-        const float mz = dz < 0 ? loz : (dz > 0 ? hiz : 0.f);
-        for (int dy = -1; dy <= 1; dy++) {
-            int y = cy + dy;
-            float sy = 0.f;
-            if (y < 0) { y += ny; sy = -Ly; }
-            if (y >= ny) { y -= ny; sy = Ly; }
-            const float my = dy < 0 ? loy : (dy > 0 ? hiy : 0.f);
-            for (int dx = -1; dx <= 1; dx++) {
-                int x = cx + dx;
-                float sx = 0.f;
-                if (x < 0) { x += nx; sx = -Lx; }
-                if (x >= nx) { x -= nx; sx = Lx; }
-                const float mx = dx < 0 ? lox : (dx > 0 ? hix : 0.f);
-                if (fmaf(mx, mx, fmaf(my, my, mz * mz)) > band_hi) continue;  // cell out of range
-                const int c = g.base + (z * ny + y) * nx + x;
-                const int s = C.cell_start[c], e = C.cell_start[c + 1];
-                const float ox = sx - fi.x, oy = sy - fi.y, oz = sz - fi.z;
-                for (int j = s; j < e; j++) {
-                    if (j == i) continue;
-                    const float4 fj = A.posf[j];
-                    const float ddx = fj.x + ox, ddy = fj.y + oy, ddz = fj.z + oz;
-                    const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
-                    bool in = r2 < band_lo;
-                    if (!in && r2 <= band_hi) in = within_exact(pi, A.pos[j], B, rl2);
-                    if (in) {
-                        if (cnt < A.k_max) row[cnt] = j;
-                        cnt++;
+    const int R = C.reach;
+    const int kmax = A.k_max;
+    const long long plane = 4LL * A.n;
+    int longest = 0;
+    for (int a0 = s; a0 < e; a0 += G) {
+        const int i = a0 + gl;
+        const bool act = i < e;
+        const int ii = act ? i : s;
+        const double4_32a pi = A.pos[ii];
+        const float4 fi = A.posf[ii];
+        int32_t *wp = A.nbr + 4 * (size_t)ii;   // entry cnt of the row (planes of 4 entries)
+        int cnt = 0;
+        // one candidate: append j to the row if it is a neighbour
+        auto visit = [&](int j, float r2) {
+            if (r2 <= band_hi) {
+                const bool in = r2 < band_lo || within_exact_band(pi, A.pos[j], B, rl2);
+                if (in && act && j != i) {
+                    if (cnt < kmax) *wp = j;
+                    cnt++;
+                    wp += (cnt & 3) ? 1 : plane - 3;
+                }
+            }
+        };
+        for (int dz = -R; dz <= R; dz++) {
+            int z = cz + dz;
+            float sz = 0.f;
+            if (z < 0) { z += nz; sz = -Lz; }
+            if (z >= nz) { z -= nz; sz = Lz; }
+            for (int dy = -R; dy <= R; dy++) {
+                int y = cy + dy;
+                float sy = 0.f;
+                if (y < 0) { y += ny; sy = -Ly; }
+                if (y >= ny) { y -= ny; sy = Ly; }
+                const int rowc = g.base + (z * ny + y) * nx;
+                for (int dx = -R; dx <= R; dx++) {
+                    int x = cx + dx;
+                    float sx = 0.f;
+                    if (x < 0) { x += nx; sx = -Lx; }
+                    if (x >= nx) { x -= nx; sx = Lx; }
+                    const int cc = rowc + x;
+                    const int js = C.cell_start[cc], je = C.cell_start[cc + 1];
+                    const float ox = sx - fi.x, oy = sy - fi.y, oz = sz - fi.z;
+                    int j = js;
+                    for (; j + 1 < je; j += 2) {
+                        const float4 f0 = A.posf[j], f1 = A.posf[j + 1];
+                        const float ax = f0.x + ox, ay = f0.y + oy, az = f0.z + oz;
+                        const float bx = f1.x + ox, by = f1.y + oy, bz = f1.z + oz;
+                        const float r0 = fmaf(ax, ax, fmaf(ay, ay, az * az));
+                        const float r1 = fmaf(bx, bx, fmaf(by, by, bz * bz));
+                        visit(j, r0);
+                        visit(j + 1, r1);
+                    }
+                    if (j < je) {
+                        const float4 f0 = A.posf[j];
+                        const float ax = f0.x + ox, ay = f0.y + oy, az = f0.z + oz;
+                        visit(j, fmaf(ax, ax, fmaf(ay, ay, az * az)));
                     }
                 }
             }
         }
+        if (act) {
+            A.count[i] = cnt;
+            if (cnt > kmax) atomicOr(&A.flags->error, FLAG_OVERFLOW);
+            longest = max(longest, cnt);
+        }
     }
-    A.count[i] = cnt;
-    if (cnt > A.k_max) atomicOr(&A.flags->error, FLAG_OVERFLOW);
-    return cnt;
+    return longest;
+}
+
+// The list phase over all cells: warp w of nwarps takes cell groups w, w + nwarps, ...; every
+// lane returns the longest row it built (all 32 lanes of a warp take part in every iteration).
+template <int G>
+__device__ __forceinline__ int build_cells(const Atoms &A, const Cells &C, const Box *boxes, long long warp,
+                                           long long nwarps, int lane, double rl2, float band_lo, float band_hi) {
+    constexpr int CPW = 32 / G;   // cells per warp
+    int m = 0;
+    for (long long c0 = warp * CPW; c0 < C.ncell; c0 += nwarps * CPW) {
+        const long long c = c0 + lane / G;
+        if (c < C.ncell) m = max(m, build_cell_group<G>(A, C, boxes, (int)c, lane & (G - 1), rl2, band_lo, band_hi));
+    }
+    return m;
+}
+
+__device__ __forceinline__ int build_cells_any(int G, const Atoms &A, const Cells &C, const Box *boxes, long long warp,
+                                               long long nwarps, int lane, double rl2, float band_lo, float band_hi) {
+    if (G == 4) return build_cells<4>(A, C, boxes, warp, nwarps, lane, rl2, band_lo, band_hi);
+    if (G == 8) return build_cells<8>(A, C, boxes, warp, nwarps, lane, rl2, band_lo, band_hi);
+    if (G == 16) return build_cells<16>(A, C, boxes, warp, nwarps, lane, rl2, band_lo, band_hi);
+    return build_cells<32>(A, C, boxes, warp, nwarps, lane, rl2, band_lo, band_hi);
 }
 
 }  // namespace ph

@@ -47,7 +47,7 @@ __global__ void k_unsort_list(Atoms A, int32_t *dst) {
     if (i >= A.n) return;
     const int cnt = min(A.count[i], A.k_max);
     int32_t *row = dst + (size_t)A.id[i] * A.k_max;
-    const int32_t *src = A.nbr + (size_t)i * A.k_max;
+    const NbrRow src = nbr_row(A, i);
     for (int k = 0; k < A.k_max; k++) row[k] = k < cnt ? A.id[src[k]] : -1;
 }
 

@@ -76,13 +76,21 @@ __device__ __forceinline__ void strain_boxes(Box *boxes, int n_rep, double s) {
 #define MD_STEP_MIN_BLOCKS 8
 #endif
 
-template <int PREC, int T, int KIND, bool MULTI>
-__global__ void __launch_bounds__(kThreads, MD_STEP_MIN_BLOCKS) k_step(Atoms A, Cells C, Pot P, StepParams sp, GridBarrier *bar,
-                                                   unsigned long long *stamps) {
+// NT threads per block.  SMT: the single-species knot table is copied into dynamic shared
+// memory at the start of the launch and the passes read it there (one 1024-thread block per SM).
+template <int PREC, int T, int KIND, bool MULTI, int NT, bool SMT>
+__global__ void __launch_bounds__(NT, NT == kThreads ? MD_STEP_MIN_BLOCKS : 1)
+    k_step(Atoms A, Cells C, Pot P, StepParams sp, GridBarrier *bar, unsigned long long *stamps) {
     __shared__ int ws[32];
     const unsigned nb = gridDim.x;
-    const long long tid = (long long)blockIdx.x * kThreads + threadIdx.x;
-    const long long stride = (long long)nb * kThreads;
+    const long long tid = (long long)blockIdx.x * NT + threadIdx.x;
+    const long long stride = (long long)nb * NT;
+    if (SMT) {
+        extern __shared__ float4 sm_table_f4[];
+        const float4 *src = reinterpret_cast<const float4 *>(P.VP32);
+        for (int q = threadIdx.x; q < 2 * P.nk; q += NT) sm_table_f4[q] = __ldg(src + q);
+        __syncthreads();
+    }
     const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
     const bool strain = sp.strain_scale != 1.0;
     Box *boxes = A.boxes;
@@ -154,12 +162,8 @@ __global__ void __launch_bounds__(kThreads, MD_STEP_MIN_BLOCKS) k_step(Atoms A, 
             for (long long k = tid; k < A.n; k += stride) ph::copyback_atom(A, boxes, (int)k);
             MD_SYNC();
             MD_STAMP(8);
-            int m = 0;
-            for (long long q = tid; q < ((long long)A.n + 31) / 32 * 32; q += stride) {
-                const int i = (int)q;
-                const int cnt = i < A.n ? ph::build_row(A, C, boxes, i, sp.rl2, sp.band_lo, sp.band_hi) : 0;
-                m = max(m, cnt);
-            }
+            int m = ph::build_cells_any(sp.list_group, A, C, boxes, tid >> 5, stride >> 5, threadIdx.x & 31, sp.rl2,
+                                        sp.band_lo, sp.band_hi);
             m = __reduce_max_sync(0xffffffffu, m);
             if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(&A.flags->max_count, m);
             MD_SYNC();
@@ -173,7 +177,7 @@ __global__ void __launch_bounds__(kThreads, MD_STEP_MIN_BLOCKS) k_step(Atoms A, 
             A.flags->n_rebuilds++;
             A.flags->need_rebuild = 0;
         }
-        for (long long g = tid; g < items; g += stride) ps::density_item<PREC, T, KIND, MULTI>(A, P, boxes, g);
+        for (long long g = tid; g < items; g += stride) ps::density_item<PREC, T, KIND, MULTI, SMT>(A, P, boxes, g);
         MD_SYNC();
         MD_STAMP(10);
         // ------------------------------------------------ force pass (+ kicks)
@@ -186,11 +190,12 @@ __global__ void __launch_bounds__(kThreads, MD_STEP_MIN_BLOCKS) k_step(Atoms A, 
         for (int q = 0; q < kPartials; q++) part[q] = 0.0;
         if (last && sp.energy_last) {
             for (long long g = tid; g < items; g += stride)
-                ps::force_item<PREC, T, KIND, MULTI, true>(A, P, boxes, g, sp.half_dt, true, part);
-            eam::block_partials(part, A.partials, A.part_stride);
+                ps::force_item<PREC, T, KIND, MULTI, true, SMT>(A, P, boxes, g, sp.half_dt, true, part);
+            eam::block_partials<NT>(part, A.partials, A.part_stride);
         } else {
             for (long long g = tid; g < items; g += stride) {
-                const int i = ps::force_item<PREC, T, KIND, MULTI, false>(A, P, boxes, g, sp.half_dt, true, part);
+                const int i =
+                    ps::force_item<PREC, T, KIND, MULTI, false, SMT>(A, P, boxes, g, sp.half_dt, true, part);
                 if (fuse && i >= 0)
                     ph::kick_drift(A, boxes, i, sp.half_dt, sp.dt, sp.strain_scale, false, sp.lim2);
             }
@@ -213,23 +218,42 @@ __global__ void __launch_bounds__(kThreads, MD_STEP_MIN_BLOCKS) k_step(Atoms A, 
 #undef MD_SYNC
 }
 
-template <int PREC, int T, int KIND, bool MULTI>
+// Largest single-species table (bytes) kept in shared memory by the SMT variant (MD_SMEM_TABLE=0
+// at build time turns the variant off).
+constexpr size_t kSmemTableMax = 200 * 1024;
+#ifndef MD_SMEM_TABLE
+#define MD_SMEM_TABLE 1
+#endif
+
+template <int PREC, int T, int KIND, bool MULTI, int NT = kThreads, bool SMT = false>
 cudaError_t launch_t(const Atoms &A, const Cells &C, const Pot &P, const StepParams &sp, GridBarrier *bar,
                      unsigned long long *stamps, int *grid_out, cudaStream_t s) {
     static int per_sm = -1;
     static int n_sm = 0;
-    if (per_sm < 0) {
+    static size_t per_sm_dyn = 0;
+    static bool attr = false;
+    const size_t dyn = SMT ? (size_t)P.nk * 32 : 0;
+    if (SMT && !attr) {  // opt in to a large dynamic shared-memory carve-out (once)
+        cudaError_t e = cudaFuncSetAttribute(k_step<PREC, T, KIND, MULTI, NT, SMT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTableMax);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    if (per_sm < 0 || dyn != per_sm_dyn) {
         int dev = 0;
         cudaError_t e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<PREC, T, KIND, MULTI>, kThreads, 0);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<PREC, T, KIND, MULTI, NT, SMT>, NT, dyn);
         if (e != cudaSuccess) return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        per_sm_dyn = dyn;
     }
     const long long work = std::max<long long>((long long)A.n * T, (long long)C.ncell);
-    const int need = (int)std::max<long long>(1, (work + kThreads - 1) / kThreads);
+    const int need = (int)std::max<long long>(1, (work + NT - 1) / NT);
     const int grid = std::max(1, std::min(per_sm * n_sm, need));
     if (grid_out) *grid_out = grid;
+    if (sp.n_steps <= 0) return cudaSuccess;  // preparation only (attributes, occupancy): no launch
     cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(GridBarrier), s);
     if (e != cudaSuccess) return e;
     Atoms a = A;
@@ -237,8 +261,8 @@ cudaError_t launch_t(const Atoms &A, const Cells &C, const Pot &P, const StepPar
     Pot p = P;
     StepParams q = sp;
     void *args[] = {&a, &c, &p, &q, &bar, &stamps};
-    return cudaLaunchCooperativeKernel((const void *)k_step<PREC, T, KIND, MULTI>, dim3(grid), dim3(kThreads), args,
-                                       0, s);
+    return cudaLaunchCooperativeKernel((const void *)k_step<PREC, T, KIND, MULTI, NT, SMT>, dim3(grid), dim3(NT), args,
+                                       dyn, s);
 }
 
 template <int PREC, int T>
@@ -246,7 +270,11 @@ cudaError_t launch_kind(const Atoms &A, const Cells &C, const Pot &P, const Step
                         unsigned long long *stamps, int *grid_out, cudaStream_t s) {
     if (P.kind == MD_POT_FS_ANALYTIC)
         return launch_t<PREC, T, MD_POT_FS_ANALYTIC, false>(A, C, P, sp, bar, stamps, grid_out, s);
-    if (P.ns == 1) return launch_t<PREC, T, MD_POT_TABLES, false>(A, C, P, sp, bar, stamps, grid_out, s);
+    if (P.ns == 1) {
+        if (MD_SMEM_TABLE && PREC == MD_PREC_MIXED && (size_t)P.nk * 32 <= kSmemTableMax)
+            return launch_t<PREC, T, MD_POT_TABLES, false, 1024, true>(A, C, P, sp, bar, stamps, grid_out, s);
+        return launch_t<PREC, T, MD_POT_TABLES, false>(A, C, P, sp, bar, stamps, grid_out, s);
+    }
     return launch_t<PREC, T, MD_POT_TABLES, true>(A, C, P, sp, bar, stamps, grid_out, s);
 }
 
@@ -258,6 +286,8 @@ cudaError_t launch_prec(const Atoms &A, const Cells &C, const Pot &P, int lanes,
         case 2: return launch_kind<PREC, 2>(A, C, P, sp, bar, stamps, grid_out, s);
         case 4: return launch_kind<PREC, 4>(A, C, P, sp, bar, stamps, grid_out, s);
         case 8: return launch_kind<PREC, 8>(A, C, P, sp, bar, stamps, grid_out, s);
+        case 16: return launch_kind<PREC, 16>(A, C, P, sp, bar, stamps, grid_out, s);
+        case 32: return launch_kind<PREC, 32>(A, C, P, sp, bar, stamps, grid_out, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -35,10 +35,11 @@ struct Stage {
 // Geometry of list entries [base, base + 32) of atom i into the compacted slots; returns the
 // number of pairs inside rd.
 __device__ __forceinline__ int stage_chunk(const Atoms &A, const SurNet &S, const float4 &pi, const Box &B,
-                                           const int *row, int cnt, int base, int lane, float4 *P0, float4 *P1) {
+                                           const NbrRow &row, int cnt, int base, int lane, float4 *P0,
+                                           float4 *P1) {
     const int q = base + lane;
     const bool valid = q < cnt;
-    const int j = valid ? __ldg(row + q) : 0;
+    const int j = valid ? __ldg(row.ptr(q)) : 0;
     const float4 pj = __ldg(A.posf + j);
     const float dx = mi(pj.x - pi.x, B.Lf[0], B.invLf[0]);
     const float dy = mi(pj.y - pi.y, B.Lf[1], B.invLf[1]);
@@ -91,7 +92,7 @@ __global__ void __launch_bounds__(kThreads) k_sur_desc(Atoms A, SurNet S, int a0
         const Box &B = A.boxes[ph::replica_of(A, i)];
         const float4 pi = A.posf[i];
         const int cnt = min(A.count[i], A.k_max);
-        const int *row = A.nbr + (size_t)i * A.k_max;
+        const NbrRow row = nbr_row(A, i);
         float G = 0.f, G2 = 0.f;
         for (int base = 0; base < cnt; base += 32) {
             const int np = stage_chunk(A, S, pi, B, row, cnt, base, lane, st.P0[w], st.P1[w]);
@@ -143,7 +144,7 @@ __global__ void __launch_bounds__(kThreads) k_sur_force(Atoms A, SurNet S, int a
         const Box &B = A.boxes[ph::replica_of(A, i)];
         const float4 pi = A.posf[i];
         const int cnt = min(A.count[i], A.k_max);
-        const int *row = A.nbr + (size_t)i * A.k_max;
+        const NbrRow row = nbr_row(A, i);
         const float gi = S.g[(size_t)i * kSurNb + lane];
         float fx = 0.f, fy = 0.f, fz = 0.f;
         float wxx = 0.f, wyy = 0.f, wzz = 0.f, wyz = 0.f, wxz = 0.f, wxy = 0.f;
@@ -230,7 +231,7 @@ __global__ void __launch_bounds__(kThreads) k_sur_u(Atoms A, SurNet S, int a0, i
         const float4 pi = A.posf[i];
         const float4 fi = S.phi[i];
         const int cnt = min(A.count[i], A.k_max);
-        const int *row = A.nbr + (size_t)i * A.k_max;
+        const NbrRow row = nbr_row(A, i);
         float u = 0.f;
         for (int base = 0; base < cnt; base += 32) {
             const int np = stage_chunk(A, S, pi, B, row, cnt, base, lane, st.P0[w], st.P1[w]);

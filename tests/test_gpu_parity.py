@@ -320,10 +320,11 @@ def test_full_size_cu500k_forces_and_lists():
 
 
 # --------------------------------------------------------------------------- lanes per atom
-@pytest.mark.parametrize("lanes", [1, 2, 4, 8])
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, 32])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_every_lane_count_matches_oracle(lanes, precision):
-    w = _workload("fec")
+@pytest.mark.parametrize("case", ["fec", "cu2k"])   # two species; one species (table in shared memory)
+def test_every_lane_count_matches_oracle(lanes, precision, case):
+    w = _workload(case)
     ref = oracle.forces(w.pos, w.species, w.box, w.potential, skin=w.skin, k_max=w.k_max, method="brute")
     fs = np.abs(ref["force"]).max()
     tol = FP64_TOL * fs if precision == "fp64" else mixed_force_bound(w, fs)
@@ -342,7 +343,7 @@ def test_autotuner_picks_a_valid_lane_count_and_stays_exact():
     ref = oracle.forces(w.pos, w.species, w.box, w.potential, skin=w.skin, k_max=w.k_max, method="brute")
     with _gpu_system(w) as s:
         lanes = s.tune()
-        assert lanes in (1, 2, 4, 8)
+        assert lanes in (1, 2, 4, 8, 16, 32)
         s.eam_forces()
         f = s.forces()
     assert np.abs(f - ref["force"]).max() <= FP64_TOL * np.abs(ref["force"]).max()
