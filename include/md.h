@@ -232,9 +232,10 @@ md_status md_get(md_ctx *ctx, int32_t what, void *dst, int32_t on_device);
 md_status md_set_state(md_ctx *ctx, const double *pos, const double *vel, const double *force,
                        int32_t on_device);
 
-/* Autotuner: time the density and force passes of the current state with each
- * lanes_per_atom in {1, 2, 4, 8, 16, 32} (a few launches each, CUDA events), keep the
- * fastest for this context and return it in *lanes_out (nullable).  Builds the list first
+/* Autotuner: time 3 velocity-Verlet steps of the persistent step kernel from the current state
+ * with each lanes_per_atom in {1, 2, 4, 8, 16, 32} (CUDA events; the trial steps rebuild no
+ * list, and positions, velocities, forces and counters are put back after each), keep the
+ * fastest for this context and return it in *lanes_out (nullable).  Computes the forces first
  * if needed.  Because the lane count fixes the summation order, results after md_tune are
  * reproducible but may differ in the last bits from those before it. */
 md_status md_tune(md_ctx *ctx, int32_t *lanes_out);

@@ -1143,35 +1143,76 @@ md_status md_tune(md_ctx *ctx, int32_t *lanes_out) {
         if (lanes_out) *lanes_out = 32;
         return MD_OK;
     }
-    md_status st = ctx->list_valid ? MD_OK : md_build_neighbours(ctx);
-    if (st != MD_OK) return st;
     if (ctx->n > 0) {
-        cudaEvent_t e0, e1;
-        MD_CK(cudaEventCreate(&e0));
-        MD_CK(cudaEventCreate(&e1));
+        md_status st = ctx->forces_valid ? MD_OK : compute_forces(ctx);
+        if (st != MD_OK) return st;
+        // Trials of the persistent step kernel itself: 3 steps from the current state at each
+        // lane count, with no list rebuild (no skin trigger, no schedule, no strain), so that no
+        // atom is renumbered; the state the steps change is saved first and put back after
+        // every trial.
+        const size_t n = (size_t)ctx->n;
+        const size_t bytes = n * (3 * sizeof(double4_32a) + sizeof(float4)) + sizeof(Flags);
+        unsigned char *snap = nullptr;
+        MD_CK(cudaMalloc(&snap, bytes));
+        double4_32a *s_pos = reinterpret_cast<double4_32a *>(snap), *s_vel = s_pos + n, *s_force = s_vel + n;
+        float4 *s_posf = reinterpret_cast<float4 *>(s_force + n);
+        Flags *s_flags = reinterpret_cast<Flags *>(s_posf + n);
+        Atoms &A = ctx->A;
+        auto copy = [&](bool save) {
+            const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
+            cudaError_t e = cudaMemcpyAsync(save ? s_pos : A.pos, save ? A.pos : s_pos, n * 32, k, ctx->stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(save ? s_vel : A.vel, save ? A.vel : s_vel, n * 32, k, ctx->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(save ? s_force : A.force, save ? A.force : s_force, n * 32, k, ctx->stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(save ? s_posf : A.posf, save ? A.posf : s_posf, n * 16, k, ctx->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(save ? s_flags : ctx->d_flags, save ? ctx->d_flags : s_flags, sizeof(Flags), k,
+                                    ctx->stream);
+            return e;
+        };
+        StepParams sp = step_params(ctx, 3);
+        sp.lim2 = 1e300;
+        sp.rebuild_every = 0;
+        sp.strain_scale = 1.0;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        cudaError_t e = copy(true);
+        if (e == cudaSuccess) e = cudaEventCreate(&e0);
+        if (e == cudaSuccess) e = cudaEventCreate(&e1);
         float best = 1e30f;
         int best_t = ctx->lanes;
-        for (int t = 1; t <= 32; t *= 2) {
-            for (int rep = 0; rep < 4; rep++) {  // first round is a warm-up
-                MD_CK(cudaEventRecord(e0, ctx->stream));
-                MD_CK(launch_density(ctx->A, ctx->P, ctx->precision, t, ctx->stream));
-                MD_CK(launch_force(ctx->A, ctx->P, ctx->precision, t, false, false, 0.0, ctx->stream));
-                MD_CK(cudaEventRecord(e1, ctx->stream));
-                MD_CK(cudaEventSynchronize(e1));
+        for (int t = 1; t <= 32 && e == cudaSuccess; t *= 2) {
+            for (int rep = 0; rep < 3 && e == cudaSuccess; rep++) {  // first round is a warm-up
+                int grid = 0;
+                StepParams prep = sp;
+                prep.n_steps = 0;  // attributes and occupancy before the timed launch
+                e = launch_step(A, ctx->C, ctx->P, ctx->precision, t, prep, ctx->d_bar, nullptr, &grid, ctx->stream);
+                if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
+                if (e == cudaSuccess)
+                    e = launch_step(A, ctx->C, ctx->P, ctx->precision, t, sp, ctx->d_bar, nullptr, &grid, ctx->stream);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
+                if (e == cudaSuccess) e = copy(false);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
                 float ms = 0.f;
-                MD_CK(cudaEventElapsedTime(&ms, e0, e1));
-                if (rep > 0 && ms < best) {
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (e == cudaSuccess && rep > 0 && ms < best) {
                     best = ms;
                     best_t = t;
                 }
-                ctx->launches += 2;
+                ctx->launches++;
             }
         }
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        cudaError_t e2 = cudaStreamSynchronize(ctx->stream);
+        cudaFree(snap);
+        if (e == cudaSuccess) e = e2;
+        if (e != cudaSuccess) {
+            ctx->forces_valid = ctx->energy_valid = false;
+            return fail(ctx, MD_ERR_CUDA, "md_tune trial steps", e);
+        }
         if (best_t != ctx->lanes) drop_graphs(ctx);
         ctx->lanes = best_t;
-        ctx->energy_valid = false;  // partial-sum rows depend on the lane count
+        ctx->energy_valid = false;  // the per-atom energies are those of a trial step
         st = sync_and_check(ctx, false);
         if (st != MD_OK) return st;
     }

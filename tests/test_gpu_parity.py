@@ -349,6 +349,23 @@ def test_autotuner_picks_a_valid_lane_count_and_stays_exact():
     assert np.abs(f - ref["force"]).max() <= FP64_TOL * np.abs(ref["force"]).max()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_autotuner_trial_steps_leave_the_state_unchanged(precision):
+    w = _workload("cu2k")
+    with _gpu_system(w, precision) as s:
+        s.eam_forces()
+        s.step(3)
+        before = [s.positions(), s.velocities(), s.forces()]
+        e0 = s.energy()
+        s.tune()
+        after = [s.positions(), s.velocities(), s.forces()]
+        e1 = s.energy()
+        for a, b in zip(before, after):
+            assert np.array_equal(a, b)
+        assert e1["step"] == e0["step"] and e1["n_rebuilds"] == e0["n_rebuilds"]
+        s.step(2)
+        assert np.isfinite(s.energy()["te"])
+
 
 # --------------------------------------------------------------------------- persistent step
 def test_graph_replay_equals_direct_launch():
