@@ -167,20 +167,21 @@ __global__ void __launch_bounds__(kThreads) k_sur_force(Atoms A, SurNet S, int a
                 wxy = fmaf(h * p1.x, p1.y, wxy);
             }
         };
+        // the g_j rows of 8 pairs are loaded before any of them is used (8 independent loads in
+        // flight per lane), then the 8 pairs are added
+        constexpr int kBatch = 8;
         for (int base = 0; base < cnt; base += 32) {
             const int np = stage_chunk(A, S, pi, B, row, cnt, base, lane, st.P0[w], st.P1[w]);
-            int q = 0;
-            for (; q + 1 < np; q += 2) {
-                const float4 p0 = st.P0[w][q], p1 = st.P1[w][q];
-                const float4 r0 = st.P0[w][q + 1], r1 = st.P1[w][q + 1];
-                const float g0 = __ldg(S.g + (size_t)__float_as_int(p0.w) * kSurNb + lane);
-                const float g1 = __ldg(S.g + (size_t)__float_as_int(r0.w) * kSurNb + lane);
-                pair(p0, p1, g0);
-                pair(r0, r1, g1);
-            }
-            if (q < np) {
-                const float4 p0 = st.P0[w][q], p1 = st.P1[w][q];
-                pair(p0, p1, __ldg(S.g + (size_t)__float_as_int(p0.w) * kSurNb + lane));
+            for (int q0 = 0; q0 < np; q0 += kBatch) {
+                float gj[kBatch];
+#pragma unroll
+                for (int u = 0; u < kBatch; u++) {
+                    const int q = min(q0 + u, np - 1);
+                    gj[u] = __ldg(S.g + (size_t)__float_as_int(st.P0[w][q].w) * kSurNb + lane);
+                }
+#pragma unroll
+                for (int u = 0; u < kBatch; u++)
+                    if (q0 + u < np) pair(st.P0[w][q0 + u], st.P1[w][q0 + u], gj[u]);
             }
             __syncwarp();
         }
