@@ -56,6 +56,8 @@ def lib():
         L.orc_sur_forces.argtypes = [i64, P, P, P, P, i32, P, P, P]
         L.orc_sur_loss_grad.restype = C.c_double
         L.orc_sur_loss_grad.argtypes = [i32, P, P, P, P, P, i32, P, P, P, P, C.c_double, C.c_double, P, P]
+        L.orc_run_nvt.restype = i64
+        L.orc_run_nvt.argtypes = [i64, P, P, P, P, P, P, dbl, i32, dbl, i32, dbl, P, P, i32, P]
         L.orc_num_threads.restype = C.c_int
         L.orc_set_threads.argtypes = [C.c_int]
         _lib = L
@@ -276,6 +278,23 @@ def sur_loss_grad(frames, spec, weights, w_e=1.0, w_f=1.0, k_max=64):
                                    _p(eref), _p(fref), C.byref(sp), _p(w), float(w_e), float(w_f),
                                    _p(grad), _p(parts))
     return dict(loss=float(loss), loss_e=float(parts[0]), loss_f=float(parts[1]), grad=grad)
+
+
+def run_nvt(pos, vel, species, masses, box, pot, dt_fs, n_steps, skin, k_max, t_kelvin, q_ev_fs2,
+            pi=0.0, xi=0.0, force=None):
+    """Nose-Hoover velocity Verlet; returns the final state, thermostat (pi, xi) and per-step
+    (PE, KE, extended energy H')."""
+    pos, vel, box = _f64(pos).copy(), _f64(vel).copy(), _f64(box).copy()
+    species, masses = _i32(species), _f64(masses)
+    n = pos.shape[0]
+    f = np.zeros((n, 3)) if force is None else _f64(force).copy()
+    energies = np.zeros((max(n_steps, 1), 3))
+    th = np.array([pi, xi, q_ev_fs2], dtype=np.float64)
+    P = _Pot(pot)
+    lib().orc_run_nvt(n, _p(pos), _p(vel), _p(species), _p(masses), _p(box), P.ref, float(dt_fs), int(n_steps),
+                      float(skin), int(k_max), float(t_kelvin), _p(th), _p(f), 0 if force is None else 1,
+                      _p(energies))
+    return dict(pos=pos, vel=vel, force=f, box=box, energies=energies[:n_steps], pi=float(th[0]), xi=float(th[1]))
 
 
 def adam_step(w, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):

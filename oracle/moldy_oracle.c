@@ -505,6 +505,54 @@ int64_t orc_run_vv(int64_t n, double *pos, double *vel, const int32_t *species, 
 }
 
 /* ------------------------------------------------------------------------- */
+/* Nose-Hoover thermostat (NVTp, §2.1.2): dp_i/dt = -dU/dq_i - pi_s p_i, Q_s dpi_s/dt = sum_i p_i^2/m_i
+ * - g k_B T with g = 3N - 3 (the printed right-hand side writes the kinetic term as p^2/2m; the
+ * reading taken here is the standard p^2/m, whose fixed point is the temperature the same section
+ * defines, sum p^2/2m = g k_B T / 2).  The thermostat friction integrates to xi (dxi/dt = pi_s) and
+ * H' = KE + U + Q_s pi_s^2 / 2 + g k_B T xi is conserved.  Integrator: a symmetric split, a
+ * thermostat half step before and after each velocity-Verlet step of orc_run_vv; a thermostat half
+ * step of length h = dt/2 is
+ *   pi += (h/2) (2 KE - g kT) / Q;  v *= exp(-pi h);  xi += pi h;  pi += (h/2) (2 KE' - g kT) / Q
+ * with KE' the kinetic energy of the scaled velocities.  Units: eV, fs, amu; Q in eV fs^2, pi in
+ * 1/fs.  thermo[3] = {pi, xi, Q} in/out (Q is read only); energies[3 s ..] = (PE, KE, H'). */
+static void orc_thermo_half(int64_t n, double *vel, const int32_t *species, const double *masses, double h,
+                            double gkt, double *thermo) {
+    double ke;
+    orc_kinetic(n, vel, species, masses, &ke, NULL, NULL, NULL);
+    double q = thermo[2];
+    thermo[0] += 0.5 * h * (2.0 * ke - gkt) / q;
+    double s = exp(-thermo[0] * h);
+    for (int64_t i = 0; i < 3 * n; i++) vel[i] *= s;
+    thermo[1] += thermo[0] * h;
+    orc_kinetic(n, vel, species, masses, &ke, NULL, NULL, NULL);
+    thermo[0] += 0.5 * h * (2.0 * ke - gkt) / q;
+}
+
+int64_t orc_run_nvt(int64_t n, double *pos, double *vel, const int32_t *species, const double *masses,
+                    double *box, const orc_potential *pot, double dt_fs, int32_t n_steps, double skin, int32_t k_max,
+                    double t_kelvin, double *thermo, double *force, int32_t forces_valid, double *energies) {
+    const double gkt = (double)(3 * n - 3) * ORC_KB * t_kelvin;
+    int64_t viol = 0;
+    int32_t fv = forces_valid, nr = 0, mc = 0;
+    for (int32_t step = 0; step < n_steps; step++) {
+        orc_thermo_half(n, vel, species, masses, 0.5 * dt_fs, gkt, thermo);
+        double e2[2];
+        viol += orc_run_vv(n, pos, vel, species, masses, box, pot, dt_fs, 1, skin, k_max, 0, 0.0, force, fv, e2,
+                           &nr, &mc);
+        fv = 1;
+        orc_thermo_half(n, vel, species, masses, 0.5 * dt_fs, gkt, thermo);
+        if (energies) {
+            double ke;
+            orc_kinetic(n, vel, species, masses, &ke, NULL, NULL, NULL);
+            energies[3 * step] = e2[0];
+            energies[3 * step + 1] = ke;
+            energies[3 * step + 2] = ke + e2[0] + 0.5 * thermo[2] * thermo[0] * thermo[0] + gkt * thermo[1];
+        }
+    }
+    return viol;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Learned surrogate of the per-atom energy (not in the paper; the EAM oracle above is its
  * reference).  Descriptor of atom i: G_ik = sum_j b_k(r_ij) over neighbours with r < rd,
  *   b_k(r) = exp(-(r - mu_k)^2 / (2 w^2)) fc(r),  mu_k = mu0 + k dmu,
