@@ -291,6 +291,24 @@ md_status md_get_profile(const md_ctx *ctx, md_profile *out);
 md_status md_neighbours_noalloc(const double *pos, int64_t n_atoms, const double *box, double r_list,
                                 int32_t k_max, int32_t *count, int32_t *list, void *stream);
 
+/* Nose-Hoover thermostat (NVTp, §2.1.2), one per replica.  With it on, md_step integrates
+ *   dp_i/dt = -dU/dq_i - pi_s p_i,   Q_s dpi_s/dt = sum_i p_i^2/m_i - g k_B T,   dxi/dt = pi_s,
+ * g = 3 N - 3 for a replica of N atoms (the kinetic term is read as p^2/m, the standard form whose
+ * fixed point is the section's temperature, sum p^2/2m = g k_B T / 2), by a thermostat half step
+ * (length dt/2) before and after each velocity-Verlet step:
+ *   pi += (dt/4)(2 KE - g kT)/Q;  v *= exp(-pi dt/2);  xi += pi dt/2;  pi += (dt/4)(2 KE' - g kT)/Q
+ * (KE' after the scaling).  H' = KE + U + Q pi^2/2 + g k_B T xi is conserved.
+ *   on: 1 = thermostat each replica r at t_kelvin[r] (K) with inertia q_ev_fs2[r] (eV fs^2; Q =
+ *       g k_B T tau^2 for a relaxation time tau), starting from pi = xi = 0; 0 = plain NVE (the
+ *       thermostat state is kept).  Host arrays of n_replicas, copied.
+ * MD_ERR_STATE for a surrogate context.  md_energy's te stays KE + U (§2.1: the reported total
+ * energy excludes the thermostat's degree of freedom). */
+md_status md_set_thermostat(md_ctx *ctx, int32_t on, const double *t_kelvin, const double *q_ev_fs2);
+
+/* Thermostat state per replica into out[n_replicas][4] (host): pi (1/fs), xi, Q (eV fs^2) and
+ * the conserved H' (eV). */
+md_status md_get_thermostat(md_ctx *ctx, double *out);
+
 /* ------------------------------------------------------------------------------------
  * Learned surrogate of the per-atom energy.  This is an addition to the paper's method,
  * which has no counterpart: the force field of Eq. (1) is replaced by a small network of

@@ -70,6 +70,12 @@ struct md_ctx {
     cudaStream_t cap_stream = nullptr;   // private stream the graphs are recorded on
     std::map<int, cudaGraphExec_t> graphs;
     std::map<int, int> graph_rows;
+    // Nose-Hoover thermostat (md_set_thermostat)
+    bool thermo_on = false;
+    Thermo *d_thermo = nullptr;
+    int2 *d_ke_chunks = nullptr;
+    int n_ke_chunks = 0;
+    std::vector<double> h_rep;           // [5 n_rep] replica sums after the last thermostatted md_step
     // learned surrogate (kind MD_POT_SURROGATE)
     bool sur = false;          // context kind
     bool sur_set = false;      // network given
@@ -284,6 +290,7 @@ cudaError_t enqueue_forces(md_ctx *ctx) {
 
 md_status compute_forces(md_ctx *ctx) {
     if (ctx->sur && !ctx->sur_set) return fail(ctx, MD_ERR_STATE, "surrogate network not set (md_set_surrogate)");
+    ctx->h_rep.clear();   // the partial sums below are of the current velocities
     MD_CK(reset_errors(ctx));
     MD_CK(enqueue_forces(ctx));
     md_status s = sync_and_check(ctx, false);
@@ -337,6 +344,12 @@ StepParams step_params(md_ctx *ctx, int n_steps) {
     sp.rl2 = ctx->rl2;
     list_band(ctx, sp.band_lo, sp.band_hi);
     sp.list_group = ph_list_group(ctx);
+    if (ctx->thermo_on) {
+        sp.thermo = ctx->d_thermo;
+        sp.ke_chunks = ctx->d_ke_chunks;
+        sp.n_ke_chunks = ctx->n_ke_chunks;
+        sp.rep_off = ctx->d_rep_off;
+    }
     sp.spin_limit = kSpinLimit;
     return sp;
 }
@@ -969,6 +982,7 @@ md_status md_step(md_ctx *ctx, int32_t n_steps) {
         }
     }
     MD_CK(reset_errors(ctx));
+    ctx->h_rep.clear();
     if (!ctx->forces_valid) MD_CK(enqueue_forces(ctx));
     unsigned long long *stamps = nullptr;
     if (ctx->profiling && !ctx->sur) {
@@ -1008,6 +1022,13 @@ md_status md_step(md_ctx *ctx, int32_t n_steps) {
     }
     ctx->launches += 2;
     ctx->part_rows = rows;
+    if (ctx->thermo_on) {  // the last half step rescaled the velocities after the energy sums
+        MD_CK(launch_replica_sums(ctx->A, ctx->d_rep_off, ctx->n_rep, ctx->d_rep_sums, ctx->stream));
+        ctx->h_rep.resize(5 * (size_t)ctx->n_rep);
+        MD_CK(cudaMemcpyAsync(ctx->h_rep.data(), ctx->d_rep_sums, ctx->h_rep.size() * sizeof(double),
+                              cudaMemcpyDeviceToHost, ctx->stream));
+        ctx->launches++;
+    }
     if (stamps)
         MD_CK(cudaMemcpyAsync(ctx->h_stamps, stamps, kStampsPerStep * ((size_t)n_steps + 1) * sizeof(unsigned long long),
                               cudaMemcpyDeviceToHost, ctx->stream));
@@ -1033,7 +1054,16 @@ md_status md_energy(md_ctx *ctx, md_energies *out) {
     const double *r = ctx->h_reduce;
     std::memset(out, 0, sizeof(*out));
     out->pe = r[0];
-    out->ke = 0.5 * r[1] * kMvv2e;
+    double mv2 = r[1], mom[3] = {r[8], r[9], r[10]};
+    if (!ctx->h_rep.empty()) {  // velocities rescaled after the partial sums (thermostat)
+        mv2 = 0.0;
+        mom[0] = mom[1] = mom[2] = 0.0;
+        for (int q = 0; q < ctx->n_rep; q++) {
+            mv2 += ctx->h_rep[5 * (size_t)q + 1];
+            for (int k = 0; k < 3; k++) mom[k] += ctx->h_rep[5 * (size_t)q + 2 + k];
+        }
+    }
+    out->ke = 0.5 * mv2 * kMvv2e;
     out->te = out->pe + out->ke;
     const int64_t dof = 3 * ctx->n - 3 * (int64_t)ctx->n_rep;
     out->temperature = dof > 0 ? 2.0 * out->ke / ((double)dof * kKb) : 0.0;
@@ -1044,7 +1074,7 @@ md_status md_energy(md_ctx *ctx, md_energies *out) {
     out->volume = vol;
     out->pressure_gpa = (2.0 * out->ke + r[2] + r[3] + r[4]) / (3.0 * vol) * kEva3ToGpa;
     for (int k = 0; k < 3; k++) {
-        out->momentum[k] = r[8 + k];
+        out->momentum[k] = mom[k];
         out->box[k] = ctx->L[k];
     }
     out->step = ctx->step;
@@ -1171,6 +1201,7 @@ md_status md_tune(md_ctx *ctx, int32_t *lanes_out) {
             return e;
         };
         StepParams sp = step_params(ctx, 3);
+        sp.thermo = nullptr;   // trial steps leave the thermostat alone
         sp.lim2 = 1e300;
         sp.rebuild_every = 0;
         sp.strain_scale = 1.0;
@@ -1228,6 +1259,7 @@ md_status md_selftest_timeout(md_ctx *ctx) {
         if (st != MD_OK) return st;
     }
     StepParams sp = step_params(ctx, 1);
+    sp.thermo = nullptr;
     sp.spin_limit = 20000;  // ~2-5 ms of polling
     sp.withhold_arrival = 1;
     MD_CK(reset_errors(ctx));
@@ -1481,6 +1513,68 @@ md_status md_sur_train(md_ctx *ctx, int32_t n_iter, int32_t rep_begin, int32_t r
     st = sync_and_check(ctx, false);
     if (st != MD_OK) return st;
     if (loss) return sur_loss_terms(ctx, r0, r0 + batch_reps, w_f, loss);
+    return MD_OK;
+}
+
+md_status md_set_thermostat(md_ctx *ctx, int32_t on, const double *t_kelvin, const double *q_ev_fs2) {
+    if (!ctx) return MD_ERR_ARG;
+    if (ctx->sur) return fail(ctx, MD_ERR_STATE, "the thermostat runs in the EAM step kernel");
+    if (!on) {
+        if (ctx->thermo_on) drop_graphs(ctx);
+        ctx->thermo_on = false;
+        return MD_OK;
+    }
+    if (!t_kelvin || !q_ev_fs2) return MD_ERR_ARG;
+    const int nr = ctx->n_rep;
+    for (int r = 0; r < nr; r++)
+        if (!(t_kelvin[r] >= 0.0) || !std::isfinite(t_kelvin[r]) || !(q_ev_fs2[r] > 0.0) || !std::isfinite(q_ev_fs2[r]))
+            return fail(ctx, MD_ERR_ARG, "thermostat: T >= 0 and Q > 0 for every replica");
+    std::vector<int2> chunks;
+    for (int r = 0; r < nr; r++)
+        for (int64_t a = ctx->rep_off[r]; a < ctx->rep_off[r + 1]; a += kKeChunk) chunks.push_back(make_int2(r, (int)a));
+    std::vector<Thermo> th(nr);
+    for (int r = 0; r < nr; r++) {
+        const int64_t m = ctx->rep_off[r + 1] - ctx->rep_off[r];
+        th[r] = Thermo{};
+        th[r].q = q_ev_fs2[r];
+        th[r].gkt = (double)(3 * m - 3) * kKb * t_kelvin[r];
+        th[r].s_b = th[r].s_a = 1.0;
+    }
+    if (!ctx->d_thermo) MD_CK(dalloc(ctx, &ctx->d_thermo, nr));
+    if (ctx->n_ke_chunks < (int)chunks.size()) MD_CK(dalloc(ctx, &ctx->d_ke_chunks, chunks.size()));
+    ctx->n_ke_chunks = (int)chunks.size();
+    MD_CK(cudaMemcpy(ctx->d_thermo, th.data(), nr * sizeof(Thermo), cudaMemcpyHostToDevice));
+    if (!chunks.empty())
+        MD_CK(cudaMemcpy(ctx->d_ke_chunks, chunks.data(), chunks.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    ctx->thermo_on = true;
+    ctx->h_rep.clear();
+    drop_graphs(ctx);   // graphs hold the step parameters by value
+    return MD_OK;
+}
+
+md_status md_get_thermostat(md_ctx *ctx, double *out) {
+    if (!ctx || !out) return MD_ERR_ARG;
+    if (!ctx->d_thermo) return fail(ctx, MD_ERR_STATE, "no thermostat was set");
+    if (!ctx->energy_valid) {
+        md_status s = compute_forces(ctx);
+        if (s != MD_OK) return s;
+    }
+    const int nr = ctx->n_rep;
+    MD_CK(launch_replica_sums(ctx->A, ctx->d_rep_off, nr, ctx->d_rep_sums, ctx->stream));
+    ctx->launches++;
+    std::vector<double> h(5 * (size_t)nr);
+    std::vector<Thermo> th(nr);
+    MD_CK(cudaMemcpyAsync(h.data(), ctx->d_rep_sums, h.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    MD_CK(cudaMemcpyAsync(th.data(), ctx->d_thermo, nr * sizeof(Thermo), cudaMemcpyDeviceToHost, ctx->stream));
+    MD_CK(cudaStreamSynchronize(ctx->stream));
+    for (int r = 0; r < nr; r++) {
+        const double pe = h[5 * (size_t)r], ke = 0.5 * h[5 * (size_t)r + 1] * kMvv2e;
+        const Thermo &t = th[r];
+        out[4 * r] = t.pi;
+        out[4 * r + 1] = t.xi;
+        out[4 * r + 2] = t.q;
+        out[4 * r + 3] = ke + pe + 0.5 * t.q * t.pi * t.pi + t.gkt * t.xi;
+    }
     return MD_OK;
 }
 

@@ -143,6 +143,17 @@ cudaError_t launch_unsort_list(const Atoms &A, int32_t *dst, cudaStream_t s);
 cudaError_t launch_sort_in_vec(const Atoms &A, const double *src, double4_32a *dst, cudaStream_t s);
 cudaError_t launch_replica_sums(const Atoms &A, const int32_t *off, int n_rep, double *out, cudaStream_t s);
 
+// Nose-Hoover thermostat of one replica (md_set_thermostat; §2.1.2).
+struct Thermo {
+    double pi, xi;          // friction (1/fs) and its time integral
+    double q, gkt;          // thermal inertia Q (eV fs^2); g k_B T (eV), g = 3 N_r - 3
+    double s_b, s_a;        // velocity scale factors of the half steps after / before a VV step
+    unsigned long long ke_fix;  // kinetic energy accumulator in units of 2^-40 eV
+    unsigned long long pad;
+};
+constexpr double kKeFix = 1099511627776.0;   // 2^40
+constexpr int kKeChunk = 1024;               // atoms per chunk of the kinetic-energy sums
+
 // Persistent step kernel (md_step.cu): n_steps velocity-Verlet steps in one cooperative
 // launch; grid barriers between phases; per-phase %globaltimer stamps when stamps != NULL.
 struct StepParams {
@@ -152,7 +163,11 @@ struct StepParams {
     int rebuild_every;    // scheduled rebuild period (0: none)
     double rl2;
     float band_lo, band_hi;
-    int list_group;       // lanes per link cell in the list build (8, 16 or 32)
+    int list_group;       // lanes per link cell in the list build (4, 8, 16 or 32)
+    Thermo *thermo;       // [n_rep] Nose-Hoover state, or NULL (NVE)
+    const int2 *ke_chunks;  // (replica, first atom) of each chunk of <= kKeChunk atoms
+    int n_ke_chunks;
+    const int32_t *rep_off;  // [n_rep + 1]
     unsigned long long spin_limit;
     int withhold_arrival;  // self-test of the bounded wait: block 0 skips its first arrival
 };

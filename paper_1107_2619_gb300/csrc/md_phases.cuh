@@ -76,8 +76,14 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int *warp_sums, int &
 // v += (dt/2) F/m;  r += dt v;  [z *= s];  skin check against the positions of the last build.
 // Separately rounded FP64 operations, as in the definition.
 __device__ __forceinline__ void kick_drift(const Atoms &A, const Box *boxes, int i, double half_dt, double dt,
-                                           double s, bool strain, double lim2) {
+                                           double s, bool strain, double lim2, const Thermo *th = nullptr) {
     double4_32a v = A.vel[i];
+    if (th) {  // the thermostat half steps before this kick: v *= s_b, then v *= s_a
+        const Thermo &t = th[replica_of(A, i)];
+        v.x = __dmul_rn(__dmul_rn(v.x, t.s_b), t.s_a);
+        v.y = __dmul_rn(__dmul_rn(v.y, t.s_b), t.s_a);
+        v.z = __dmul_rn(__dmul_rn(v.z, t.s_b), t.s_a);
+    }
     const double4_32a f = A.force[i];
     double4_32a p = A.pos[i];
     v.x = __dadd_rn(v.x, __dmul_rn(__dmul_rn(half_dt, f.x), v.w));

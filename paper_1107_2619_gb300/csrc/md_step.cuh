@@ -71,6 +71,53 @@ __device__ __forceinline__ void strain_boxes(Box *boxes, int n_rep, double s) {
     }
 }
 
+// ---- Nose-Hoover thermostat (§2.1.2), one per replica ----
+// Kinetic energy of every replica into its fixed-point accumulator: one warp per chunk of at most
+// kKeChunk atoms of one replica, one integer atomic per chunk (the sum does not depend on order).
+__device__ __forceinline__ void ke_sums(const Atoms &A, const StepParams &sp, long long tid, long long stride) {
+    const int lane = threadIdx.x & 31;
+    for (long long c = tid >> 5; c < sp.n_ke_chunks; c += stride >> 5) {
+        const int2 ch = sp.ke_chunks[c];
+        const int end = min(ch.y + kKeChunk, sp.rep_off[ch.x + 1]);
+        unsigned long long acc = 0;
+        for (int i = ch.y + lane; i < end; i += 32) {
+            const double4_32a v = A.vel[i];   // v.w = 1 / (m mvv2e): KE_i = |v|^2 / (2 v.w)
+            const double ke = 0.5 * fma(v.x, v.x, fma(v.y, v.y, v.z * v.z)) / v.w;
+            acc += (unsigned long long)llrint(ke * kKeFix);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (lane == 0) atomicAdd(&sp.thermo[ch.x].ke_fix, acc);
+    }
+}
+
+// One thermostat half step of length h from kinetic energy ke: pi += (h/2)(2 KE - g kT)/Q;
+// scale = exp(-pi h); xi += pi h; pi += (h/2)(2 KE scale^2 - g kT)/Q.  Returns KE scale^2.
+__device__ __forceinline__ double thermo_half(Thermo &t, double ke, double h, double &scale) {
+    t.pi += 0.5 * h * (2.0 * ke - t.gkt) / t.q;
+    scale = exp(-t.pi * h);
+    t.xi += t.pi * h;
+    const double ke2 = ke * scale * scale;
+    t.pi += 0.5 * h * (2.0 * ke2 - t.gkt) / t.q;
+    return ke2;
+}
+
+// The half step that closes a velocity-Verlet step (after) and / or the one that opens the next
+// (before), from the accumulated kinetic energy; every thread takes a share of the replicas.
+__device__ __forceinline__ void thermo_update(const StepParams &sp, int n_rep, long long tid, long long stride,
+                                              bool after, bool before) {
+    for (long long r = tid; r < n_rep; r += stride) {
+        Thermo &t = sp.thermo[r];
+        double ke = (double)t.ke_fix / kKeFix;
+        t.ke_fix = 0;
+        double sb = 1.0, sa = 1.0;
+        if (after) ke = thermo_half(t, ke, sp.half_dt, sb);
+        if (before) ke = thermo_half(t, ke, sp.half_dt, sa);
+        t.s_b = sb;
+        t.s_a = sa;
+    }
+}
+
 // Minimum resident blocks per SM requested from the compiler (caps registers per thread).
 #ifndef MD_STEP_MIN_BLOCKS
 #define MD_STEP_MIN_BLOCKS 8
@@ -109,8 +156,16 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? MD_STEP_MIN_BLOCKS : 1)
         MD_SYNC();
     }
     if (lead && sp.rebuild_every > 0 && (step + 1) % sp.rebuild_every == 0) A.flags->need_rebuild = 1;
+    const bool thermo = sp.thermo != nullptr;
+    if (thermo) {  // the thermostat half step that opens the first step
+        ke_sums(A, sp, tid, stride);
+        MD_SYNC();
+        thermo_update(sp, A.n_rep, tid, stride, false, true);
+        MD_SYNC();
+    }
     for (long long i = tid; i < A.n; i += stride)
-        ph::kick_drift(A, boxes, (int)i, sp.half_dt, sp.dt, sp.strain_scale, strain, sp.lim2);
+        ph::kick_drift(A, boxes, (int)i, sp.half_dt, sp.dt, sp.strain_scale, strain, sp.lim2,
+                       thermo ? sp.thermo : nullptr);
     if (sp.withhold_arrival && blockIdx.x == 0) {
         // self-test of the bounded wait: this block never arrives; it waits (bounded) until
         // the others have given up and marked the launch aborted, then leaves.
@@ -182,7 +237,7 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? MD_STEP_MIN_BLOCKS : 1)
         MD_STAMP(10);
         // ------------------------------------------------ force pass (+ kicks)
         const bool last = s == sp.n_steps - 1;
-        const bool fuse = !last && !strain;
+        const bool fuse = !last && !strain && !thermo;
         if (fuse && lead && sp.rebuild_every > 0 && (step + s + 2) % sp.rebuild_every == 0)
             A.flags->need_rebuild = 1;
         double part[kPartials];
@@ -202,7 +257,31 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? MD_STEP_MIN_BLOCKS : 1)
         }
         MD_SYNC();
         MD_STAMP(11);
-        if (!last && strain) {
+        if (thermo) {
+            // close this step and open the next with thermostat half steps
+            ke_sums(A, sp, tid, stride);
+            MD_SYNC();
+            thermo_update(sp, A.n_rep, tid, stride, true, !last);
+            if (!last && lead) {
+                if (strain) strain_boxes(boxes, A.n_rep, sp.strain_scale);
+                if (sp.rebuild_every > 0 && (step + s + 2) % sp.rebuild_every == 0) A.flags->need_rebuild = 1;
+            }
+            MD_SYNC();
+            if (!last) {
+                for (long long i = tid; i < A.n; i += stride)
+                    ph::kick_drift(A, boxes, (int)i, sp.half_dt, sp.dt, sp.strain_scale, strain, sp.lim2, sp.thermo);
+                MD_SYNC();
+            } else {
+                for (long long i = tid; i < A.n; i += stride) {
+                    const double sb = sp.thermo[ph::replica_of(A, (int)i)].s_b;
+                    double4_32a v = A.vel[i];
+                    v.x = __dmul_rn(v.x, sb);
+                    v.y = __dmul_rn(v.y, sb);
+                    v.z = __dmul_rn(v.z, sb);
+                    A.vel[i] = v;
+                }
+            }
+        } else if (!last && strain) {
             if (lead) {
                 strain_boxes(boxes, A.n_rep, sp.strain_scale);
                 if (sp.rebuild_every > 0 && (step + s + 2) % sp.rebuild_every == 0) A.flags->need_rebuild = 1;

@@ -34,7 +34,7 @@ MD_PREC_FP64, MD_PREC_MIXED = 0, 1
 EXPORTS = ["md_abi_version", "md_status_string", "md_create", "md_create_batch", "md_build_neighbours",
            "md_eam_forces", "md_step", "md_set_graph", "md_energy", "md_replica_energies", "md_get",
            "md_set_state", "md_tune", "md_set_profiling", "md_get_profile", "md_selftest_timeout",
-           "md_neighbours_noalloc", "md_set_surrogate", "md_sur_get_params", "md_sur_standardize",
+           "md_neighbours_noalloc", "md_set_thermostat", "md_get_thermostat", "md_set_surrogate", "md_sur_get_params", "md_sur_standardize",
            "md_sur_get", "md_sur_set_reference", "md_sur_loss_grad", "md_sur_train", "md_last_error",
            "md_destroy"]
 
@@ -126,6 +126,10 @@ def lib():
         L.md_get_profile.argtypes = [P, C.POINTER(md_profile)]
         L.md_neighbours_noalloc.restype = C.c_int
         L.md_neighbours_noalloc.argtypes = [P, i64, P, C.c_double, i32, P, P, P]
+        L.md_set_thermostat.restype = C.c_int
+        L.md_set_thermostat.argtypes = [P, i32, P, P]
+        L.md_get_thermostat.restype = C.c_int
+        L.md_get_thermostat.argtypes = [P, P]
         L.md_set_surrogate.restype = C.c_int
         L.md_set_surrogate.argtypes = [P, C.POINTER(md_surrogate), P, P, P]
         L.md_sur_get_params.restype = C.c_int
@@ -282,6 +286,21 @@ def md_neighbours_noalloc(pos, box, r_list: float, k_max: int, count, nbr_list, 
     return lib().md_neighbours_noalloc(C.c_void_p(pos.data_ptr()), int(pos.shape[0]), C.c_void_p(b.ctypes.data),
                                        float(r_list), int(k_max), C.c_void_p(count.data_ptr()),
                                        C.c_void_p(nbr_list.data_ptr()), C.c_void_p(stream) if stream else None)
+
+
+def md_set_thermostat(ctx, on: bool, t_kelvin=None, q_ev_fs2=None):
+    if not on:
+        _check(ctx, lib().md_set_thermostat(ctx, 0, None, None))
+        return
+    t = np.ascontiguousarray(np.atleast_1d(t_kelvin), dtype=np.float64)
+    q = np.ascontiguousarray(np.atleast_1d(q_ev_fs2), dtype=np.float64)
+    _check(ctx, lib().md_set_thermostat(ctx, 1, t.ctypes.data, q.ctypes.data))
+
+
+def md_get_thermostat(ctx, n_replicas: int = 1):
+    out = np.zeros((n_replicas, 4))
+    _check(ctx, lib().md_get_thermostat(ctx, out.ctypes.data))
+    return out
 
 
 def md_set_surrogate(ctx, spec: md_surrogate, theta, gmu=None, ginv=None):
@@ -452,6 +471,18 @@ class System:
 
     def set_state(self, pos=None, vel=None, force=None):
         md_set_state(self.ctx, pos, vel, force)
+
+    def set_thermostat(self, t_kelvin, tau_fs=None, q_ev_fs2=None):
+        """Nose-Hoover thermostat at t_kelvin (scalar or one per replica); Q from the relaxation
+        time tau_fs (Q = g k_B T tau^2) unless given."""
+        t = np.broadcast_to(np.asarray(t_kelvin, dtype=np.float64), (self.n_replicas,)).copy()
+        if q_ev_fs2 is None:
+            sizes = np.diff(self.offsets) if hasattr(self, "offsets") else np.array([self.n])
+            q_ev_fs2 = (3 * sizes - 3) * _inputs.KB_EV_PER_K * t * float(tau_fs) ** 2
+        md_set_thermostat(self.ctx, True, t, np.broadcast_to(q_ev_fs2, (self.n_replicas,)))
+
+    def thermostat(self):
+        return md_get_thermostat(self.ctx, self.n_replicas)
 
     def close(self):
         if self.ctx:
