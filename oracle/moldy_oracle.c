@@ -43,7 +43,7 @@
 #define ORC_EVA3_TO_GPA (ORC_EV_J * 1.0e30 / 1.0e9)
 
 typedef struct {
-    int32_t kind; /* 1: analytic Finnis-Sinclair (one species), 2: knot tables */
+    int32_t kind; /* 1: analytic Finnis-Sinclair (one species), 2: knot tables, 4: explicit knot sums */
     int32_t n_species;
     int32_t n_knots;
     int32_t pad;
@@ -220,9 +220,31 @@ static double orc_table(const double *tab, int n, double x0, double x1, double x
     return h00 * y[k] + h10 * h * yp[k] + h01 * y[k + 1] + h11 * h * yp[k + 1];
 }
 
+/* Explicit cubic knot sum of the generic potential files of §3.1.1:
+ *   f(r) = sum_k c_k (r_k - r)^3 H(r_k - r),  f'(r) = -3 sum_k c_k (r_k - r)^2 H(r_k - r),
+ * knot data = K coefficients c_k then K radii r_k. */
+static double orc_knots(const double *kd, int K, double r, double *d) {
+    double v = 0.0, g = 0.0;
+    for (int k = 0; k < K; k++) {
+        double u = kd[K + k] - r;
+        if (u > 0.0) {
+            v += kd[k] * u * u * u;
+            g -= 3.0 * kd[k] * u * u;
+        }
+    }
+    *d = g;
+    return v;
+}
+
 /* which = 0: V_ab (pair), 1: phi_ab (density at an atom of species a from one of species b). */
 static double orc_pair(const orc_potential *p, int which, int a, int b, double r, double *d,
                        int64_t *viol) {
+    if (p->kind == 4) {
+        int ns = p->n_species, K = p->n_knots;
+        int t = which * ns * ns + a * ns + b;
+        if (!(r < p->r_cut)) { *d = 0.0; return 0.0; }
+        return orc_knots(p->tables + (size_t)t * 2 * K, K, r, d);
+    }
     if (p->kind == 1) {
         const double dd = p->fs[0], c = p->fs[1], beta = p->fs[3];
         const double c0 = p->fs[4], c1 = p->fs[5], c2 = p->fs[6];
@@ -242,11 +264,14 @@ static double orc_pair(const orc_potential *p, int which, int a, int b, double r
 }
 
 static double orc_embed(const orc_potential *p, int a, double rho, double *dF, int64_t *viol) {
-    if (p->kind == 1) {
+    if (p->kind == 1 || p->kind == 4) {
+        /* Finnis-Sinclair F = -A sqrt(rho); kind 4 keeps A_a after the 2 ns^2 knot functions */
+        double A = p->kind == 1 ? p->fs[2]
+                                : p->tables[(size_t)2 * p->n_species * p->n_species * 2 * p->n_knots + a];
         if (!(rho > 0.0)) { *dF = 0.0; return 0.0; } /* F(0) = 0 with F' = 0 (finite at rho = 0) */
         double s = sqrt(rho);
-        *dF = -0.5 * p->fs[2] / s;
-        return -p->fs[2] * s;
+        *dF = -0.5 * A / s;
+        return -A * s;
     }
     int ns = p->n_species, n = p->n_knots;
     int t = 2 * ns * ns + a;

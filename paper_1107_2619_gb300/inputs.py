@@ -122,6 +122,7 @@ SC_CU = dict(eps=1.2382e-2, c=39.432, a=3.61, n=9, m=6)
 POT_FS_ANALYTIC = 1
 POT_TABLES = 2
 POT_SURROGATE = 3
+POT_KNOTS = 4
 
 
 @dataclasses.dataclass
@@ -231,6 +232,49 @@ def _knot_sum(coef, knots):
     return f, df
 
 
+def _fe_knot_fit():
+    """A Finnis-Sinclair-like Fe as 15 cubic knot terms (§3.1.1 form): 8 for V on knots evenly in
+    2.3..c, 7 for phi evenly in 2.1..d, coefficients from a least-squares fit of FS Fe's V and phi
+    on 1.8..d (the paper's iron of intermediate complexity: a sum of 15 cubic splines)."""
+    V, _, P, _ = _fs_fe_funcs()
+    d, cc = FS_FE["d"], FS_FE["c"]
+    r = np.linspace(1.8, d, 600)
+    rkv, rkp = np.linspace(2.3, cc, 8), np.linspace(2.1, d, 7)
+    basis = lambda rk: np.clip(rk[None, :] - r[:, None], 0.0, None) ** 3
+    av = np.linalg.lstsq(basis(rkv), V(r), rcond=None)[0]
+    ap = np.linalg.lstsq(basis(rkp), P(r), rcond=None)[0]
+    return (av, rkv), (ap, rkp)
+
+
+def fe_knots() -> Potential:
+    """bcc Fe potential given as explicit cubic knot sums (kind 4): V and phi = sum_k c_k (r_k - r)^3
+    for r < r_k, F = -A sqrt(rho).  `tables` = V (8 coefficients, 8 radii), phi (the same, the
+    8th term zero), then A.  r_cut = the largest knot."""
+    (av, rkv), (ap, rkp) = _fe_knot_fit()
+    K = 8
+    ap8, rkp8 = np.concatenate([ap, [0.0]]), np.concatenate([rkp, [rkp[-1]]])
+    tables = np.concatenate([av, rkv, ap8, rkp8, [FS_FE["A"]]])
+    return Potential(kind=POT_KNOTS, atomic_numbers=np.array([26], dtype=np.int32),
+                     masses=np.array([MASS_AMU[26]]), r_cut=float(max(rkv.max(), rkp.max())), n_knots=K,
+                     tables=tables)
+
+
+def fe_knot_tables(n_knots: int = 5000, r_min: float = 1.0) -> Potential:
+    """The same 15-term Fe potential sampled into cubic-Hermite knot tables (kind 2)."""
+    (av, rkv), (ap, rkp) = _fe_knot_fit()
+    V, dV = _knot_sum(av, rkv)
+    P, dP = _knot_sum(ap, rkp)
+    rc = float(max(rkv.max(), rkp.max()))
+    A = FS_FE["A"]
+    rho_min, rho_max = 0.3, 14.0
+    tables = np.concatenate([_sample(V, dV, r_min, rc, n_knots), _sample(P, dP, r_min, rc, n_knots),
+                             _sample(lambda x: -A * np.sqrt(x), lambda x: -0.5 * A / np.sqrt(x), rho_min, rho_max,
+                                     n_knots)])
+    return Potential(kind=POT_TABLES, atomic_numbers=np.array([26], dtype=np.int32),
+                     masses=np.array([MASS_AMU[26]]), r_cut=rc, n_knots=n_knots, r_min=r_min,
+                     rho_min=rho_min, rho_max=rho_max, tables=tables)
+
+
 def fe_c_tables(seed: int = 4, n_knots: int = 5000, r_min: float = 1.0) -> Potential:
     """Two-species Fe-C tables: Fe-Fe is FS Fe; every term involving C is a seeded knot sum
     with knots <= 3.5 Å (repulsive Fe-C and C-C cores, positive densities).  V is symmetric."""
@@ -295,11 +339,11 @@ class Workload:
 
 
 def bcc_fe(n: int, seed: int, temperature: float = 300.0, sigma: float = 0.05, tables: bool = False,
-           steps: int = 100, dt_fs: float = 1.0, a: float = 2.8665, cells=None) -> Workload:
+           steps: int = 100, dt_fs: float = 1.0, a: float = 2.8665, cells=None, potential=None) -> Workload:
     cells = cells or (n, n, n)
     pos, box = replicate(BCC_BASIS, cells, a)
     pos = gaussian_displace(pos, sigma, seed)
-    pot = fs_fe_tables() if tables else fs_fe_analytic()
+    pot = potential if potential is not None else (fs_fe_tables() if tables else fs_fe_analytic())
     species = np.zeros(pos.shape[0], dtype=np.int32)
     vel = maxwell_boltzmann(pot.masses[species], temperature, seed)
     return Workload(name=f"bcc Fe {cells[0]}x{cells[1]}x{cells[2]}", pos=pos, vel=vel, species=species,

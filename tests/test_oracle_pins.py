@@ -145,10 +145,12 @@ def _displaced(kind):
         w = I.bcc_fe_c(5, seed=24)
         w.potential  # two species with asymmetric densities
         return w
+    if kind == "knots":
+        return I.bcc_fe(5, seed=25, sigma=0.08, potential=I.fe_knots())
     raise ValueError(kind)
 
 
-@pytest.mark.parametrize("kind", ["fs", "fs_tables", "cu", "fec"])
+@pytest.mark.parametrize("kind", ["fs", "fs_tables", "cu", "fec", "knots"])
 def test_forces_are_minus_energy_gradient(kind):
     w = _displaced(kind)
     if kind == "fec":
@@ -170,6 +172,23 @@ def test_forces_are_minus_energy_gradient(kind):
     # Newton's third law: the total force vanishes up to summation rounding
     fsum = np.abs(out["force"].sum(axis=0)).max()
     assert fsum < 1e-12 * np.abs(out["force"]).sum()
+
+
+def test_explicit_knot_sums_equal_their_hermite_tables():
+    """The 15-term Fe potential evaluated term by term (kind 4) and through cubic-Hermite tables
+    of the same sums (kind 2, orc_table): two independent code paths agree to the tables'
+    interpolation error."""
+    w = I.bcc_fe(6, seed=26, sigma=0.1, potential=I.fe_knots())
+    a = oracle.forces(w.pos, w.species, w.box, I.fe_knots())
+    b = oracle.forces(w.pos, w.species, w.box, I.fe_knot_tables())
+    assert np.abs(a["force"] - b["force"]).max() < 1e-6
+    assert abs(a["pe"] - b["pe"]) < 1e-10 * abs(a["pe"])
+    assert np.array_equal(a["count"], b["count"])
+    # and the fit is an iron: near the FS cohesive energy at the FS lattice parameter
+    g = golden("fs_fe_bcc.txt")
+    w0 = I.bcc_fe(6, seed=1, sigma=0.0, a=g["lattice_a_angstrom"], potential=I.fe_knots())
+    e = oracle.forces(w0.pos, w0.species, w0.box, w0.potential)["pe"] / w0.n_atoms
+    assert abs(e - g["cohesive_energy_ev_per_atom"]) < 0.01
 
 
 def test_half_list_equals_full_list_two_species():
