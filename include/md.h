@@ -59,7 +59,7 @@ typedef enum {
     MD_ERR_CAPACITY = 12     /* input larger than a fixed capacity (md_neighbours_noalloc) */
 } md_status;
 
-enum { MD_POT_FS_ANALYTIC = 1, MD_POT_TABLES = 2, MD_POT_SURROGATE = 3 };
+enum { MD_POT_FS_ANALYTIC = 1, MD_POT_TABLES = 2, MD_POT_SURROGATE = 3, MD_POT_KNOTS = 4 };
 enum { MD_PREC_FP64 = 0, MD_PREC_MIXED = 1 };
 
 /*
@@ -79,6 +79,11 @@ enum { MD_PREC_FP64 = 0, MD_PREC_MIXED = 1 };
  *     polynomial through the end values and slopes; outside the span the table
  *     continues linearly from the end knot and the event is counted
  *     (md_energies.range_violations).
+ *   kind MD_POT_KNOTS: n_species species, explicit cubic knot sums (the generic potential
+ *     files of §3.1.1): V_ab and phi_ab = sum_k c_k (r_k - r)^3 for r < r_k, evaluated term by
+ *     term (no table), F_a = -A_a sqrt(rho).  n_knots = K terms per function (pad with c = 0);
+ *     `tables` holds the 2 ns^2 functions V[a][b] (V[a][b] must equal V[b][a]) then phi[a][b],
+ *     each K coefficients then K radii r_k <= r_cut, then A[a] (ns values); ns <= 8, K <= 32.
  *   kind MD_POT_SURROGATE: the learned per-atom surrogate (md_set_surrogate); one
  *     species (n_species 1, species 0), r_cut = the descriptor cutoff rd; fs, n_knots,
  *     r_min, rho_min, rho_max and tables are ignored.

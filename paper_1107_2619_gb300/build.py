@@ -54,7 +54,7 @@ def build(force: bool = False, verbose: bool = None, out: str = None, defines=()
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
         return obj, r.stderr
 
-    with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as ex:
+    with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4)) as ex:
         results = list(ex.map(compile_one, _sources()))
     if verbose:
         for _, log in results:

@@ -441,6 +441,22 @@ md_status create_common(md_ctx *ctx, const md_config *cfg, const md_potential *p
         if (ns < 1 || ns > 8 || pot->n_knots < 2 || !pot->tables || !(pot->r_cut > pot->r_min) ||
             !(pot->rho_max > pot->rho_min))
             return MD_ERR_ARG;
+    } else if (pot->kind == MD_POT_KNOTS) {
+        if (ns < 1 || ns > 8 || pot->n_knots < 1 || pot->n_knots > 32 || !pot->tables || !(pot->r_cut > 0.0))
+            return MD_ERR_ARG;
+        const int K = pot->n_knots;
+        for (int t = 0; t < 2 * ns * ns; t++)
+            for (int q = 0; q < K; q++) {
+                const double c = pot->tables[(size_t)t * 2 * K + q], rk = pot->tables[(size_t)t * 2 * K + K + q];
+                if (!std::isfinite(c) || !(rk <= pot->r_cut) || !std::isfinite(rk)) return MD_ERR_ARG;
+            }
+        for (int a = 0; a < ns; a++)
+            for (int b = 0; b < ns; b++)
+                for (int q = 0; q < 2 * K; q++)
+                    if (pot->tables[(size_t)(a * ns + b) * 2 * K + q] != pot->tables[(size_t)(b * ns + a) * 2 * K + q]) {
+                        ctx->err = "V knot sums must be symmetric in their two species";
+                        return MD_ERR_ARG;
+                    }
     } else if (pot->kind == MD_POT_SURROGATE) {
         if (ns != 1 || !(pot->r_cut > 0.0)) return MD_ERR_ARG;
         if (cfg->strain_rate_zz != 0.0) return MD_ERR_ARG;
@@ -645,6 +661,28 @@ md_status create_common(md_ctx *ctx, const md_config *cfg, const md_potential *p
         P.VP64 = dVP64;
         P.VP32 = dVP32;
         P.F64 = dF64;
+    }
+    if (pot->kind == MD_POT_KNOTS) {
+        const int K = pot->n_knots, nf = 2 * ns * ns;
+        P.nkt = K;
+        std::vector<double2> k64((size_t)nf * K);
+        std::vector<float2> k32((size_t)nf * K);
+        for (int t = 0; t < nf; t++)
+            for (int q = 0; q < K; q++) {
+                const double c = pot->tables[(size_t)t * 2 * K + q], rk = pot->tables[(size_t)t * 2 * K + K + q];
+                k64[(size_t)t * K + q] = make_double2(c, rk);
+                k32[(size_t)t * K + q] = make_float2((float)c, (float)rk);
+            }
+        for (int a = 0; a < ns; a++) P.A64[a] = pot->tables[(size_t)nf * 2 * K + a];
+        double2 *d64;
+        float2 *d32;
+        chk(dalloc(ctx, &d64, k64.size()));
+        chk(dalloc(ctx, &d32, k32.size()));
+        if (e != cudaSuccess) return fail(ctx, MD_ERR_OOM, "knot allocation", e);
+        chk(cudaMemcpy(d64, k64.data(), k64.size() * sizeof(double2), cudaMemcpyHostToDevice));
+        chk(cudaMemcpy(d32, k32.data(), k32.size() * sizeof(float2), cudaMemcpyHostToDevice));
+        P.K64 = d64;
+        P.K32 = d32;
     }
     // initial state (caller order = cell order until the first build)
     std::vector<Box> boxes(n_rep);

@@ -51,6 +51,8 @@ template <int T>
 void density_t(const Atoms &A, const Pot &P, cudaStream_t s) {
     const int nb = A.n > 0 ? blocks_for_lanes<T>(A.n) : 1;
     if (P.kind == MD_POT_FS_ANALYTIC) k_density64<T, MD_POT_FS_ANALYTIC, false><<<nb, kThreads, 0, s>>>(A, P);
+    else if (P.kind == MD_POT_KNOTS && P.ns == 1) k_density64<T, MD_POT_KNOTS, false><<<nb, kThreads, 0, s>>>(A, P);
+    else if (P.kind == MD_POT_KNOTS) k_density64<T, MD_POT_KNOTS, true><<<nb, kThreads, 0, s>>>(A, P);
     else if (P.ns == 1) k_density64<T, MD_POT_TABLES, false><<<nb, kThreads, 0, s>>>(A, P);
     else k_density64<T, MD_POT_TABLES, true><<<nb, kThreads, 0, s>>>(A, P);
 }
@@ -60,6 +62,10 @@ void force_te(const Atoms &A, const Pot &P, double half_dt, int kick, cudaStream
     const int nb = blocks_for_lanes<T>(A.n);
     if (P.kind == MD_POT_FS_ANALYTIC)
         k_force64<T, MD_POT_FS_ANALYTIC, false, ENERGY><<<nb, kThreads, 0, s>>>(A, P, half_dt, kick);
+    else if (P.kind == MD_POT_KNOTS && P.ns == 1)
+        k_force64<T, MD_POT_KNOTS, false, ENERGY><<<nb, kThreads, 0, s>>>(A, P, half_dt, kick);
+    else if (P.kind == MD_POT_KNOTS)
+        k_force64<T, MD_POT_KNOTS, true, ENERGY><<<nb, kThreads, 0, s>>>(A, P, half_dt, kick);
     else if (P.ns == 1)
         k_force64<T, MD_POT_TABLES, false, ENERGY><<<nb, kThreads, 0, s>>>(A, P, half_dt, kick);
     else

@@ -85,16 +85,33 @@ __device__ __forceinline__ R fs_V(const R *fs, R r, R &dV) {
     return u * u * q;
 }
 
+// Explicit cubic knot sum f(r) = sum_q c_q (r_q - r)^3 for r < r_q (the generic potential files'
+// form, §3.1.1) and df/dr; k[q] = (c_q, r_q).
+template <typename R, typename R2>
+__device__ __forceinline__ R knot_sum(const R2 *__restrict__ k, int n, R r, R &d) {
+    R v = R(0), g = R(0);
+    for (int q = 0; q < n; q++) {
+        const R2 c = k[q];
+        const R u = c.y > r ? c.y - r : R(0);
+        const R cu2 = c.x * u * u;
+        v = fma(cu2, u, v);
+        g = fma(R(-3), cu2, g);
+    }
+    d = g;
+    return v;
+}
+
 // F and F' in FP64 (one evaluation per atom, both precisions).
 __device__ __forceinline__ double embed64(const Pot &P, int a, double rho, double &dF, Flags *flags) {
-    if (P.kind == MD_POT_FS_ANALYTIC) {
+    if (P.kind == MD_POT_FS_ANALYTIC || P.kind == MD_POT_KNOTS) {
+        const double Aa = P.kind == MD_POT_KNOTS ? P.A64[a] : P.fs[2];
         if (!(rho > 0.0)) {
             dF = 0.0;
             return 0.0;
         }
         double s = sqrt(rho);
-        dF = -0.5 * P.fs[2] / s;
-        return -P.fs[2] * s;
+        dF = -0.5 * Aa / s;
+        return -Aa * s;
     }
     double x = (rho - P.rho_min) * P.inv_drho, t, d;
     bool below;

@@ -62,6 +62,12 @@ struct Pot {
     const double4_32a *VP64;  // [((a*ns+b)*nk + k)*2 + {0: V, 1: phi_ab}]
     const double4_32a *VP32;  // [(a*ns+b)*nk + k], 8 floats
     const double4_32a *F64;   // [a*nk + k]
+    // explicit knot sums (MD_POT_KNOTS): function t (V[a][b] = a*ns+b, phi[a][b] = ns*ns + a*ns+b)
+    // has nkt terms (coefficient, radius) at K64/K32 + t*nkt; F_a = -A[a] sqrt(rho)
+    int nkt;
+    const double2 *K64;
+    const float2 *K32;
+    double A64[8];
 };
 
 // Link-cell grid of one replica: its cells are the global cells [base, base + nc0*nc1*nc2).

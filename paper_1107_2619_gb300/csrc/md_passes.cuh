@@ -87,6 +87,10 @@ __device__ __forceinline__ void density32_item(const Atoms &A, const Pot &P, con
             float phi;
             if (KIND == MD_POT_FS_ANALYTIC) {
                 phi = fs_phi<float>(P.fsf, P.bdf, r);
+            } else if (KIND == MD_POT_KNOTS) {
+                const int sj = MULTI ? __float_as_int(pj.w) : 0;
+                float d;
+                phi = knot_sum<float, float2>(P.K32 + (size_t)(P.ns * P.ns + si * P.ns + sj) * P.nkt, P.nkt, r, d);
             } else {
                 const int sj = MULTI ? __float_as_int(pj.w) : 0;
                 float t, d;
@@ -164,6 +168,19 @@ __device__ __forceinline__ int force32_item(const Atoms &A, const Pot &P, const 
                 float dV;
                 V = fs_V<float>(P.fsf, r, dV);
                 gg = fmaf(Fpi + Fpj, fs_dphi<float>(P.fsf, P.bdf, r), dV);
+            } else if (KIND == MD_POT_KNOTS) {
+                const int sj = MULTI ? __ldg(A.spec + j) : 0;
+                const int nn = P.ns * P.ns;
+                float dVk, dab;
+                V = knot_sum<float, float2>(P.K32 + (size_t)(si * P.ns + sj) * P.nkt, P.nkt, r, dVk);
+                knot_sum<float, float2>(P.K32 + (size_t)(nn + si * P.ns + sj) * P.nkt, P.nkt, r, dab);
+                if (MULTI) {
+                    float dba;
+                    knot_sum<float, float2>(P.K32 + (size_t)(nn + sj * P.ns + si) * P.nkt, P.nkt, r, dba);
+                    gg = fmaf(Fpi, dab, fmaf(Fpj, dba, dVk));
+                } else {
+                    gg = fmaf(Fpi + Fpj, dab, dVk);
+                }
             } else {
                 const int sj = MULTI ? __ldg(A.spec + j) : 0;
                 float t;
@@ -267,6 +284,10 @@ __device__ __forceinline__ void density64_item(const Atoms &A, const Pot &P, con
             const double r = r2 * rsqrt64(r2);
             if (KIND == MD_POT_FS_ANALYTIC) {
                 rho += fs_phi<double>(P.fs, P.bd, r);
+            } else if (KIND == MD_POT_KNOTS) {
+                const int sj = MULTI ? (int)pj.w : 0;
+                double d;
+                rho += knot_sum<double, double2>(P.K64 + (size_t)(P.ns * P.ns + si * P.ns + sj) * P.nkt, P.nkt, r, d);
             } else {
                 const int sj = MULTI ? (int)pj.w : 0;
                 double t, d;
@@ -319,6 +340,19 @@ __device__ __forceinline__ int force64_item(const Atoms &A, const Pot &P, const 
                 double dV;
                 V = fs_V<double>(P.fs, r, dV);
                 gg = fma(Fpi + Fpj, fs_dphi<double>(P.fs, P.bd, r), dV);
+            } else if (KIND == MD_POT_KNOTS) {
+                const int sj = MULTI ? __ldg(A.spec + j) : 0;
+                const int nn = P.ns * P.ns;
+                double dVk, dab;
+                V = knot_sum<double, double2>(P.K64 + (size_t)(si * P.ns + sj) * P.nkt, P.nkt, r, dVk);
+                knot_sum<double, double2>(P.K64 + (size_t)(nn + si * P.ns + sj) * P.nkt, P.nkt, r, dab);
+                if (MULTI) {
+                    double dba;
+                    knot_sum<double, double2>(P.K64 + (size_t)(nn + sj * P.ns + si) * P.nkt, P.nkt, r, dba);
+                    gg = fma(Fpi, dab, fma(Fpj, dba, dVk));
+                } else {
+                    gg = fma(Fpi + Fpj, dab, dVk);
+                }
             } else {
                 const int sj = MULTI ? __ldg(A.spec + j) : 0;
                 double t;

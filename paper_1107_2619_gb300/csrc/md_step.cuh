@@ -349,6 +349,9 @@ cudaError_t launch_kind(const Atoms &A, const Cells &C, const Pot &P, const Step
                         unsigned long long *stamps, int *grid_out, cudaStream_t s) {
     if (P.kind == MD_POT_FS_ANALYTIC)
         return launch_t<PREC, T, MD_POT_FS_ANALYTIC, false>(A, C, P, sp, bar, stamps, grid_out, s);
+    if (P.kind == MD_POT_KNOTS)
+        return P.ns == 1 ? launch_t<PREC, T, MD_POT_KNOTS, false>(A, C, P, sp, bar, stamps, grid_out, s)
+                         : launch_t<PREC, T, MD_POT_KNOTS, true>(A, C, P, sp, bar, stamps, grid_out, s);
     if (P.ns == 1) {
         if (MD_SMEM_TABLE && PREC == MD_PREC_MIXED && (size_t)P.nk * 32 <= kSmemTableMax)
             return launch_t<PREC, T, MD_POT_TABLES, false, 1024, true>(A, C, P, sp, bar, stamps, grid_out, s);
@@ -357,19 +360,17 @@ cudaError_t launch_kind(const Atoms &A, const Cells &C, const Pot &P, const Step
     return launch_t<PREC, T, MD_POT_TABLES, true>(A, C, P, sp, bar, stamps, grid_out, s);
 }
 
-template <int PREC>
-cudaError_t launch_prec(const Atoms &A, const Cells &C, const Pot &P, int lanes, const StepParams &sp,
-                        GridBarrier *bar, unsigned long long *stamps, int *grid_out, cudaStream_t s) {
-    switch (lanes) {
-        case 1: return launch_kind<PREC, 1>(A, C, P, sp, bar, stamps, grid_out, s);
-        case 2: return launch_kind<PREC, 2>(A, C, P, sp, bar, stamps, grid_out, s);
-        case 4: return launch_kind<PREC, 4>(A, C, P, sp, bar, stamps, grid_out, s);
-        case 8: return launch_kind<PREC, 8>(A, C, P, sp, bar, stamps, grid_out, s);
-        case 16: return launch_kind<PREC, 16>(A, C, P, sp, bar, stamps, grid_out, s);
-        case 32: return launch_kind<PREC, 32>(A, C, P, sp, bar, stamps, grid_out, s);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
 }  // namespace st
+
+// One launcher per (precision, lanes per atom), each defined in its own translation unit
+// (md_step_{m,d}_{a,b,c}.cu: the instantiations compile in parallel); md_step_dispatch.cu picks.
+#define MD_STEP_FN(P, T) launch_step_##P##_l##T
+#define MD_STEP_DECL(P, T)                                                                                  \
+    cudaError_t MD_STEP_FN(P, T)(const Atoms &A, const Cells &C, const Pot &Pt, const StepParams &sp,     \
+                                 GridBarrier *bar, unsigned long long *stamps, int *grid_out, cudaStream_t s)
+#define MD_STEP_DEFINE(P, PREC, T)                                                                          \
+    MD_STEP_DECL(P, T) { return st::launch_kind<PREC, T>(A, C, Pt, sp, bar, stamps, grid_out, s); }
+MD_STEP_DECL(m, 1); MD_STEP_DECL(m, 2); MD_STEP_DECL(m, 4); MD_STEP_DECL(m, 8); MD_STEP_DECL(m, 16); MD_STEP_DECL(m, 32);
+MD_STEP_DECL(d, 1); MD_STEP_DECL(d, 2); MD_STEP_DECL(d, 4); MD_STEP_DECL(d, 8); MD_STEP_DECL(d, 16); MD_STEP_DECL(d, 32);
+
 }  // namespace mdk

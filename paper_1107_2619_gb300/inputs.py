@@ -275,6 +275,34 @@ def fe_knot_tables(n_knots: int = 5000, r_min: float = 1.0) -> Potential:
                      rho_min=rho_min, rho_max=rho_max, tables=tables)
 
 
+def fe_c_knots(seed: int = 4) -> Potential:
+    """Two-species Fe-C as explicit knot sums (kind 4): Fe-Fe is the 15-term Fe fit, the terms with
+    C are the seeded knot sums of fe_c_tables (same seed, same draws).  K = 8 terms per function."""
+    (av, rkv), (ap, rkp) = _fe_knot_fit()
+    u = random_uniform(seed, 7, 64)
+    K = 8
+
+    def pad(c, r):
+        c, r = list(c), list(r)
+        return np.array(c + [0.0] * (K - len(c))), np.array(r + [r[-1]] * (K - len(r)))
+
+    V = {(0, 0): (av, rkv),
+         (0, 1): pad([0.9 + 0.2 * u[0], 0.05 + 0.05 * u[1], 0.01 * u[2]], [1.9, 2.6, 3.5]),
+         (1, 1): pad([1.0 + 0.2 * u[3], 0.02 * u[4]], [2.2, 3.5])}
+    V[(1, 0)] = V[(0, 1)]
+    P = {(0, 0): pad(ap, rkp),
+         (0, 1): pad([0.30 + 0.1 * u[5], 0.02 + 0.02 * u[6]], [2.4, 3.5]),
+         (1, 0): pad([0.25 + 0.1 * u[7], 0.02 + 0.02 * u[8]], [2.6, 3.5]),
+         (1, 1): pad([0.05 + 0.02 * u[9]], [3.5])}
+    parts = [np.concatenate(V[(a, b)]) for a in range(2) for b in range(2)]
+    parts += [np.concatenate(P[(a, b)]) for a in range(2) for b in range(2)]
+    parts.append(np.array([FS_FE["A"], 1.0 + 0.3 * u[10]]))
+    rc = max(FS_FE["d"], FS_FE["c"], 3.5)
+    return Potential(kind=POT_KNOTS, atomic_numbers=np.array([26, 6], dtype=np.int32),
+                     masses=np.array([MASS_AMU[26], MASS_AMU[6]]), r_cut=float(rc), n_knots=K,
+                     tables=np.concatenate(parts))
+
+
 def fe_c_tables(seed: int = 4, n_knots: int = 5000, r_min: float = 1.0) -> Potential:
     """Two-species Fe-C tables: Fe-Fe is FS Fe; every term involving C is a seeded knot sum
     with knots <= 3.5 Å (repulsive Fe-C and C-C cores, positive densities).  V is symmetric."""

@@ -22,7 +22,7 @@ MD_OK, MD_ERR_ARG, MD_ERR_SPECIES, MD_ERR_BOX, MD_ERR_NBR_OVERFLOW = 0, 1, 2, 3,
 MD_ERR_SKIN, MD_ERR_NONFINITE, MD_ERR_TABLE_RANGE, MD_ERR_TIMEOUT = 5, 6, 7, 8
 MD_ERR_CUDA, MD_ERR_OOM, MD_ERR_STATE, MD_ERR_CAPACITY = 9, 10, 11, 12
 MD_NOALLOC_MAX_ATOMS, MD_NOALLOC_MAX_CELLS = 131072, 65536
-MD_POT_FS_ANALYTIC, MD_POT_TABLES, MD_POT_SURROGATE = 1, 2, 3
+MD_POT_FS_ANALYTIC, MD_POT_TABLES, MD_POT_SURROGATE, MD_POT_KNOTS = 1, 2, 3, 4
 MD_SUR_FP32, MD_SUR_BF16 = 0, 1
 MD_SUR_GET_G, MD_SUR_GET_DEDG = 0, 1
 MD_SUR_NB, MD_SUR_H1, MD_SUR_H2, MD_SUR_PARAMS = 32, 64, 64, 6337

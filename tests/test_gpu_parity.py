@@ -87,6 +87,11 @@ def _workload(name):
         return _ragged_box(seed=7)
     if name == "near":
         return _near_cutoff()
+    if name == "fe_knots":
+        return I.bcc_fe(10, seed=13, potential=I.fe_knots())
+    if name == "fec_knots":
+        import dataclasses
+        return dataclasses.replace(I.bcc_fe_c(10, seed=14), potential=I.fe_c_knots())
     raise ValueError(name)
 
 
@@ -110,7 +115,7 @@ def test_neighbour_sets_bit_exact(name, precision):
 
 
 # --------------------------------------------------------------------------- FP64 parity
-@pytest.mark.parametrize("name", ["fe2k", "fe_tables", "cu2k", "fec", "random"])
+@pytest.mark.parametrize("name", ["fe2k", "fe_tables", "cu2k", "fec", "random", "fe_knots", "fec_knots"])
 def test_fp64_forces_energies_virial_match_oracle(name):
     w = _workload(name)
     ref = oracle.forces(w.pos, w.species, w.box, w.potential, skin=w.skin, k_max=w.k_max, method="brute")
@@ -136,7 +141,7 @@ def test_fp64_forces_energies_virial_match_oracle(name):
     assert abs(e["pressure_gpa"] - p) <= FP64_TOL * max(abs(p), ws / np.prod(w.box) * 160.2)
 
 
-@pytest.mark.parametrize("name", ["fe2k", "fe_tables", "cu2k", "fec"])
+@pytest.mark.parametrize("name", ["fe2k", "fe_tables", "cu2k", "fec", "fe_knots", "fec_knots"])
 def test_mixed_forces_within_bound(name):
     w = _workload(name)
     ref = oracle.forces(w.pos, w.species, w.box, w.potential, skin=w.skin, k_max=w.k_max, method="brute")
@@ -148,6 +153,21 @@ def test_mixed_forces_within_bound(name):
     assert np.abs(f - ref["force"]).max() <= mixed_force_bound(w, fs)
     assert abs(pe - ref["pe"]) <= MIXED_PE_TOL * abs(ref["pe"])
     assert np.abs(rho - ref["rho"]).max() <= 1e-5 * np.abs(ref["rho"]).max()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_knot_sums_step_like_the_oracle(precision):
+    """Explicit knot sums through the persistent step kernel: 20 steps against the oracle."""
+    w = _workload("fec_knots")
+    ref = oracle.run_vv(w.pos, w.vel, w.species, w.potential.masses, w.box, w.potential, w.dt_fs, 20,
+                        w.skin, w.k_max, strain_rate_zz=w.strain_rate_zz)
+    with _gpu_system(w, precision) as s:
+        s.step(20)
+        pos = s.positions()
+        e = s.energy()
+    tol = 1e-9 if precision == "fp64" else 1e-5
+    assert np.abs(pos - ref["pos"]).max() < tol
+    assert abs(e["pe"] - ref["energies"][-1, 0]) <= (1e-10 if precision == "fp64" else 1e-6) * abs(ref["energies"][-1, 0])
 
 
 def test_unwrapped_images_give_the_same_forces():
