@@ -258,7 +258,8 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     res, snapshot = {}, {}
     for precision in (("mixed",) if args.profile_case else ("mixed", "fp64")):
-        s = md.System(w, precision=precision, stream=stream.cuda_stream, device_inputs=True)
+        s = md.System(w, precision=precision, stream=stream.cuda_stream, device_inputs=True,
+                      passes=args.passes if precision == "mixed" else "auto")
         s.eam_forces()
         lanes = s.tune()
         counts = s.get(md.MD_GET_NBR_COUNT)
@@ -289,7 +290,7 @@ def run_ours(args):
         if rank == 0:
             r = res["mixed"]
             print(json.dumps({"profile_case": True, "n_atoms": n, "ms_per_step": r["ms"] / args.steps,
-                              "lanes": r["lanes"], "rebuild_ms_per_rebuild": rebuild_parts(r["prof"]),
+                              "lanes": r["lanes"], "passes": args.passes, "rebuild_ms_per_rebuild": rebuild_parts(r["prof"]),
                               "phase_ms": {k: r["prof"]["ms_" + k] / max(1, r["prof"]["n_" + k])
                                            for k in ("kick", "rebuild", "density", "force")}}))
         return 0
@@ -557,6 +558,8 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="mixed path only, no e2e/CPU/extra legs: a short run for ncu captures")
     ap.add_argument("--no-extras", action="store_true", help="skip the non-headline workloads")
+    ap.add_argument("--passes", choices=["auto", "list", "staged", "cells"], default="auto",
+                    help="neighbour walk of the mixed-precision step kernel (md.h MD_PASSES_*)")
     ap.add_argument("--surrogate-only", action="store_true",
                     help="run only the learned-surrogate comparison and print its record")
     ap.add_argument("--sur-weights", default=SUR_WEIGHTS, help="trained surrogate (.npz: theta, gmu, ginv)")

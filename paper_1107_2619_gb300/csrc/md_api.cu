@@ -591,6 +591,60 @@ md_status create_common(md_ctx *ctx, const md_config *cfg, const md_potential *p
     chk(dalloc(ctx, &C.cell_count, C.ncell));
     chk(dalloc(ctx, &C.cell_start, C.ncell + 1));
     chk(dalloc(ctx, &C.tile_sums, C.ntiles + 1));
+    // staged and cell walks (MD_PASSES_STAGED, MD_PASSES_CELLS): groups of gx cells along x whose
+    // 3 x 3 x (gx + 2) neighbourhood fits the stage 30 % above the mean occupancy.  Staged walk:
+    // gx such that a group's home atoms fill whole rounds of a 1024-thread block at the context's
+    // lanes per atom (with a 10 % margin for the spread of cell occupancy), of nearly equal
+    // choices the larger; cell walk (a warp per atom): the largest gx (fewest stencil copies).
+    {
+        const size_t tbytes = pot->kind == MD_POT_TABLES ? smem_table_bytes(pot->kind, ns, cfg->precision, pot->n_knots)
+                                                         : 0;
+        const bool eligible = tbytes > 0 && n_rep == 1 && reach == 1 && !ctx->sur && cfg->strain_rate_zz == 0.0 &&
+                              ctx->lanes <= 8 && n > 0;
+        const bool grouped = cfg->passes == MD_PASSES_STAGED || cfg->passes == MD_PASSES_CELLS;
+        if (cfg->passes != MD_PASSES_AUTO && cfg->passes != MD_PASSES_LIST && !grouped) return MD_ERR_ARG;
+        if (grouped && !eligible) {
+            ctx->err = "staged and cell walks need mixed precision, one system, one species with a knot table "
+                       "that fits in shared memory, no strain ramp and at most 8 lanes per atom";
+            return MD_ERR_ARG;
+        }
+        C.tile = kWalkList;
+        if (eligible && grouped) {
+            const int walk = cfg->passes == MD_PASSES_STAGED ? kWalkStaged : kWalkCells;
+            const int nx = ctx->rc[0].nc[0];
+            const double m = (double)n / (double)ncell;
+            const size_t dyn_max = walk == kWalkCells ? kSmemDynMaxCells : kSmemDynMax;
+            const int cap = (int)std::min<size_t>((dyn_max - tbytes) / sizeof(float4), 65535);
+            int best = 0;
+            double best_eff = 0.0;
+            for (int g = 1; g <= std::min(8, nx); g++) {
+                if (9.0 * (g + 2) * m * 1.3 > cap) break;
+                if (walk == kWalkCells) {
+                    best = g;
+                    continue;
+                }
+                const double items = g * m * ctx->lanes;
+                const double eff = items / (std::ceil(items * 1.1 / 1024.0) * 1024.0);
+                if (eff >= 0.98 * best_eff) {
+                    best = g;
+                    best_eff = std::max(eff, best_eff);
+                }
+            }
+            if (best > 0) {
+                C.tile = walk;
+                C.gx = best;
+                C.ngx = (nx + best - 1) / best;
+                C.n_groups = C.ngx * ctx->rc[0].nc[1] * ctx->rc[0].nc[2];
+                C.st_cells = 9 * (best + 2);
+                C.cap = cap;
+                chk(dalloc(ctx, &C.grp_loc, (size_t)C.n_groups * (C.st_cells + 1)));
+                if (walk == kWalkStaged) chk(dalloc(ctx, &A.lnbr, nbr_entries(n, cfg->k_max)));
+            } else {
+                ctx->err = "staged and cell walks: the link-cell occupancy is too high for the stage";
+                return MD_ERR_ARG;
+            }
+        }
+    }
     if (e != cudaSuccess) return fail(ctx, MD_ERR_OOM, "device allocation", e);
     A.boxes = ctx->d_boxes;
     A.flags = ctx->d_flags;
@@ -1079,7 +1133,8 @@ md_status md_step(md_ctx *ctx, int32_t n_steps) {
         return st;
     }
     if (stamps) collect_stamps(ctx, n_steps);
-    ctx->list_valid = ctx->forces_valid = ctx->energy_valid = true;
+    ctx->forces_valid = ctx->energy_valid = true;
+    ctx->list_valid = ctx->C.tile != kWalkCells;   // a cell-walk rebuild leaves the list behind
     return MD_OK;
 }
 
@@ -1329,6 +1384,20 @@ md_status md_get_profile(const md_ctx *ctx, md_profile *out) {
     if (!ctx || !out) return MD_ERR_ARG;
     *out = ctx->prof;
     out->launches = ctx->launches;
+    return MD_OK;
+}
+
+md_status md_get_passes(md_ctx *ctx, md_passes *out) {
+    if (!ctx || !out) return MD_ERR_ARG;
+    MD_CK(cudaMemcpyAsync(ctx->h_flags, ctx->d_flags, sizeof(Flags), cudaMemcpyDeviceToHost, ctx->stream));
+    MD_CK(cudaStreamSynchronize(ctx->stream));
+    const Cells &C = ctx->C;
+    out->walk = C.tile == kWalkStaged ? MD_PASSES_STAGED : (C.tile == kWalkCells ? MD_PASSES_CELLS : MD_PASSES_LIST);
+    out->cells_per_group = C.tile ? C.gx : 0;
+    out->groups = C.tile ? C.n_groups : 0;
+    out->capacity = C.tile ? C.cap : 0;
+    out->last_max = C.tile ? ctx->h_flags->tile_max : 0;
+    out->active = C.tile && ctx->lanes <= 8 && !ctx->h_flags->tile_bad;
     return MD_OK;
 }
 

@@ -1,7 +1,8 @@
 // Internal declarations shared by the kernels and the C ABI layer of libmd.so.
-// Per-atom state on the device is kept in link-cell order (atoms renumbered at
-// every neighbour-list build, §3.2.1-3.2.2: "ordering the particles array by
-// increasing link-cell index"); id[] maps a slot to the caller's atom id.
+// Per-atom state on the device is kept in link-cell order: every neighbour-list build
+// renumbers the atoms so that the atoms of one link cell are adjacent and cells follow
+// their index (the cache-friendly ordering of §3.2.1-3.2.2); id[] maps a slot to the
+// caller's atom id.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -42,6 +43,8 @@ struct Flags {
     unsigned long long n_rebuilds;
     unsigned long long range_violations;
     long long step;         // steps taken (the rebuild schedule counts from here)
+    int32_t tile_bad;       // a cell group's neighbourhood exceeded the staging capacity at the last build
+    int32_t tile_max;       // largest cell-group neighbourhood (atoms) at the last build
 };
 
 // Device view of the potential.  Tables hold, per interval k of a uniform knot grid, the
@@ -99,6 +102,8 @@ struct Atoms {
     int32_t *cell_of, *slot, *order;
     int32_t *sorted;                         // order after the in-cell sort (aliases cell_of)
     int32_t *nbr, *count;                    // list entry k of atom i: see NbrRow; k < min(count, k_max)
+    uint16_t *lnbr;                          // staged passes: the same entries as slots of the atom's
+                                             // cell-group stencil (same plane layout as nbr)
     double *partials;                        // [kPartials][part_stride] per-block sums
     int part_stride;
     int32_t *rep;                            // replica of each slot (NULL: one system)
@@ -119,6 +124,14 @@ struct NbrRow {
 __host__ __device__ inline NbrRow nbr_row(const Atoms &A, int i) {
     return NbrRow{A.nbr + 4 * (size_t)i, 4LL * A.n};
 }
+struct NbrRow16 {
+    const uint16_t *p;
+    long long plane;
+    __host__ __device__ const uint16_t *ptr(int k) const { return p + (long long)(k >> 2) * plane + (k & 3); }
+};
+__host__ __device__ inline NbrRow16 lnbr_row(const Atoms &A, int i) {
+    return NbrRow16{A.lnbr + 4 * (size_t)i, 4LL * A.n};
+}
 inline size_t nbr_entries(int64_t n, int k_max) { return (size_t)((k_max + 3) / 4) * 4 * (size_t)n; }
 
 struct Cells {
@@ -127,7 +140,34 @@ struct Cells {
     int ntiles;
     RepCells *rc;  // [n_rep], device
     int32_t *cell_count, *cell_start, *tile_sums;
+    // Cell groups of the staged passes (one system, cells r_list wide): groups of gx consecutive
+    // cells along x.  The neighbourhood of a group is its 3 x 3 x (gx + 2) stencil of cells; stencil
+    // cell s = ((dz + 1) 3 + (dy + 1)) (gx + 2) + (x - x0 + 1) for the group starting at x0.
+    int tile;           // walk of the step kernel's passes: kWalkList (no groups), kWalkStaged (groups
+                        // and 16-bit local lists), kWalkCells (groups, no list unless a group overflows)
+    int gx, ngx, n_groups, st_cells;   // cells per group, groups per row, groups, 9 (gx + 2)
+    int cap;            // atoms a block can stage
+    int32_t *grp_loc;   // [n_groups][st_cells + 1]: staged slot of the first atom of each stencil cell, total
 };
+
+// Neighbour walks of the step kernel's passes (md_config.passes).
+enum : int { kWalkList = 0, kWalkStaged = 1, kWalkCells = 2 };
+
+// Shared memory of the mixed-precision step kernel: a single-species knot table (2 float4 per
+// knot) of at most kSmemTableMax bytes, and the stage of the staged passes; together at most
+// kSmemDynMax bytes (the static shared memory of a 1024-thread block comes on top).
+constexpr size_t kSmemTableMax = 200 * 1024;
+constexpr size_t kSmemDynMax = 222 * 1024;
+constexpr int kCellsQueue = 64;   // cell walk: hit queue (16-bit stage slots) per warp, static shared
+constexpr size_t kSmemDynMaxCells = kSmemDynMax - 32 * kCellsQueue * sizeof(uint16_t);
+#ifndef MD_SMEM_TABLE
+#define MD_SMEM_TABLE 1
+#endif
+inline size_t smem_table_bytes(int kind, int ns, int precision, int nk) {
+    const size_t b = (size_t)nk * 32;
+    return (MD_SMEM_TABLE && kind == MD_POT_TABLES && ns == 1 && precision == MD_PREC_MIXED && b <= kSmemTableMax)
+               ? b : 0;
+}
 
 // Launchers (stream-ordered, no synchronisation).
 cudaError_t launch_set_rebuild(Flags *f, cudaStream_t s);

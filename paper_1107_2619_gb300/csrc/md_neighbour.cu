@@ -7,11 +7,12 @@
 // grid of at most 8 blocks per SM, so that a launch with nothing to do costs a few µs:
 //   k_bin        wrapped fractional coordinate -> link cell; per-cell counter -> slot
 //   k_scan_*     exclusive scan of the per-cell counts -> cell_start (3 phases)
-//   k_scatter    order[cell_start[c] + slot] = atom
+//   k_scatter    order[cell_start[c] + slot] = atom; the stencil slot tables of the cell groups
+//                (staged passes)
 //   k_cell_sort  stable order inside a cell: ascending caller atom id (deterministic)
 //   k_gather / k_copyback   renumber every per-atom array into cell order
 //   k_build_list full list: the 27 cells around each cell, |r_ij|^2 < r_list^2, a group of
-//                lanes per cell
+//                lanes per cell (with the staged passes also the same list as stencil slots)
 // Link cells are fixed in fractional coordinates and at least r_list wide, so every pair
 // closer than r_list lies in adjacent cells (the hybrid NL-LCM of §3.2.1).
 #include <cuda_runtime.h>
@@ -50,7 +51,11 @@ __global__ void k_scan_tiles(Cells C, const Flags *f) {
 __global__ void k_scan_top(Cells C, Flags *f) {
     __shared__ int ws[32];
     if (!ph::rebuild_requested(f)) return;
-    if (threadIdx.x == 0) f->max_count = 0;  // k_build_list runs later
+    if (threadIdx.x == 0) {  // k_scatter and k_build_list run later
+        f->max_count = 0;
+        f->tile_bad = 0;
+        f->tile_max = 0;
+    }
     ph::scan_top(C, ws);
 }
 
@@ -63,6 +68,8 @@ __global__ void k_scan_apply(Cells C, const Flags *f) {
 __global__ void k_scatter(Atoms A, Cells C) {
     if (!ph::rebuild_requested(A.flags)) return;
     for (long long i = gtid(); i < A.n; i += gstride()) ph::scatter_atom(A, C, (int)i);
+    if (C.tile)
+        for (long long g = gtid(); g < C.n_groups; g += gstride()) ph::group_table(C, (int)g, A.flags);
 }
 
 __global__ void k_cell_sort(Atoms A, Cells C) {
@@ -82,11 +89,11 @@ __global__ void k_copyback(Atoms A) {
     for (long long k = gtid(); k < A.n; k += gstride()) ph::copyback_atom(A, A.boxes, (int)k);
 }
 
-template <int G>
+template <int G, bool LOCAL>
 __global__ void __launch_bounds__(kThreads) k_build_list(Atoms A, Cells C, double rl2, float band_lo,
                                                          float band_hi) {
     if (!ph::rebuild_requested(A.flags)) return;
-    int m = ph::build_cells<G>(A, C, A.boxes, gtid() >> 5, gstride() >> 5, threadIdx.x & 31, rl2, band_lo, band_hi);
+    int m = ph::build_cells<G, LOCAL>(A, C, A.boxes, gtid() >> 5, gstride() >> 5, threadIdx.x & 31, rl2, band_lo, band_hi);
     m = __reduce_max_sync(0xffffffffu, m);
     if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(&A.flags->max_count, m);
 }
@@ -128,10 +135,17 @@ cudaError_t launch_rebuild(const Atoms &A, const Cells &C, double rl2, float ban
         k_gather<<<nb, kThreads, 0, s>>>(A);
         k_copyback<<<nb, kThreads, 0, s>>>(A);
         const int nbl = capped_blocks((long long)C.ncell * list_group, kThreads);
-        if (list_group == 4) k_build_list<4><<<nbl, kThreads, 0, s>>>(A, C, rl2, band_lo, band_hi);
-        else if (list_group == 8) k_build_list<8><<<nbl, kThreads, 0, s>>>(A, C, rl2, band_lo, band_hi);
-        else if (list_group == 16) k_build_list<16><<<nbl, kThreads, 0, s>>>(A, C, rl2, band_lo, band_hi);
-        else k_build_list<32><<<nbl, kThreads, 0, s>>>(A, C, rl2, band_lo, band_hi);
+        if (C.tile == kWalkStaged) {
+            if (list_group == 4) k_build_list<4, true><<<nbl, kThreads, 0, s>>>(A, C, rl2, band_lo, band_hi);
+            else if (list_group == 8) k_build_list<8, true><<<nbl, kThreads, 0, s>>>(A, C, rl2, band_lo, band_hi);
+            else if (list_group == 16) k_build_list<16, true><<<nbl, kThreads, 0, s>>>(A, C, rl2, band_lo, band_hi);
+            else k_build_list<32, true><<<nbl, kThreads, 0, s>>>(A, C, rl2, band_lo, band_hi);
+        } else {
+            if (list_group == 4) k_build_list<4, false><<<nbl, kThreads, 0, s>>>(A, C, rl2, band_lo, band_hi);
+            else if (list_group == 8) k_build_list<8, false><<<nbl, kThreads, 0, s>>>(A, C, rl2, band_lo, band_hi);
+            else if (list_group == 16) k_build_list<16, false><<<nbl, kThreads, 0, s>>>(A, C, rl2, band_lo, band_hi);
+            else k_build_list<32, false><<<nbl, kThreads, 0, s>>>(A, C, rl2, band_lo, band_hi);
+        }
     }
     return cudaGetLastError();
 }

@@ -60,6 +60,147 @@ __device__ __forceinline__ void vp_row(const Pot &P, size_t idx, float (&v)[4], 
 }
 
 // ======================================================================= mixed precision
+// phi_{s_i s_j}(r) of one pair at separation d = (dx, dy, dz); 0 at or beyond r_cut (no branch,
+// so the loads of the next pair can issue early).  viol counts table lookups below r_min.
+template <int KIND, bool MULTI, bool SMT>
+__device__ __forceinline__ float rho_term32(const Pot &P, int si, int sj, float dx, float dy, float dz,
+                                            unsigned &viol) {
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const bool inside = r2 < P.rc2f;
+    const float r = r2 * rsqrtf(r2);
+    float phi;
+    if (KIND == MD_POT_FS_ANALYTIC) {
+        phi = fs_phi<float>(P.fsf, P.bdf, r);
+    } else if (KIND == MD_POT_KNOTS) {
+        float d;
+        phi = knot_sum<float, float2>(P.K32 + (size_t)(P.ns * P.ns + si * P.ns + sj) * P.nkt, P.nkt, r, d);
+    } else {
+        float t, d;
+        bool below;
+        const int kr = knot_row((r - P.r_minf) * P.inv_drf, P.nk, t, below);
+        viol += (below && inside) ? 1u : 0u;
+        const float4 c = phi_row<SMT>(P, (size_t)(si * P.ns + sj) * P.nk + kr);
+        phi = cubic(t, c.x, c.y, c.z, c.w, below, d);
+    }
+    return inside ? phi : 0.f;
+}
+
+// Per-atom sums of the force pass: force, and on the energy step the pair energy and virial.
+struct Acc32 {
+    float fx = 0.f, fy = 0.f, fz = 0.f, ep = 0.f;
+    float wxx = 0.f, wyy = 0.f, wzz = 0.f, wyz = 0.f, wxz = 0.f, wxy = 0.f;
+};
+
+// One pair of the force pass: V'(r) + F'_i phi'_{s_i s_j}(r) + F'_j phi'_{s_j s_i}(r) along
+// d = (dx, dy, dz) = r_j - r_i (zero at or beyond r_cut, without a branch), and on the energy
+// step V(r)/2 and the virial -d (x) f / 2.
+template <int KIND, bool MULTI, bool ENERGY, bool SMT>
+__device__ __forceinline__ void pair32(const Pot &P, int si, int sj, float Fpi, float Fpj, float dx, float dy,
+                                       float dz, Acc32 &a, unsigned &viol) {
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const bool inside = r2 < P.rc2f;
+    const float rinv = rsqrtf(r2);
+    const float r = r2 * rinv;
+    float V, gg;
+    if (KIND == MD_POT_FS_ANALYTIC) {
+        float dV;
+        V = fs_V<float>(P.fsf, r, dV);
+        gg = fmaf(Fpi + Fpj, fs_dphi<float>(P.fsf, P.bdf, r), dV);
+    } else if (KIND == MD_POT_KNOTS) {
+        const int nn = P.ns * P.ns;
+        float dVk, dab;
+        V = knot_sum<float, float2>(P.K32 + (size_t)(si * P.ns + sj) * P.nkt, P.nkt, r, dVk);
+        knot_sum<float, float2>(P.K32 + (size_t)(nn + si * P.ns + sj) * P.nkt, P.nkt, r, dab);
+        if (MULTI) {
+            float dba;
+            knot_sum<float, float2>(P.K32 + (size_t)(nn + sj * P.ns + si) * P.nkt, P.nkt, r, dba);
+            gg = fmaf(Fpi, dab, fmaf(Fpj, dba, dVk));
+        } else {
+            gg = fmaf(Fpi + Fpj, dab, dVk);
+        }
+    } else {
+        float t;
+        bool below;
+        const int kr = knot_row((r - P.r_minf) * P.inv_drf, P.nk, t, below);
+        viol += (below && inside) ? 1u : 0u;
+        float cv[4], cp[4], dVk, dab;
+        vp_row<SMT>(P, (size_t)(si * P.ns + sj) * P.nk + kr, cv, cp);
+        V = cubic(t, cv[0], cv[1], cv[2], cv[3], below, dVk);
+        cubic(t, cp[0], cp[1], cp[2], cp[3], below, dab);
+        float gk;
+        if (MULTI) {
+            const float4 c = phi_half32(P.VP32, (size_t)(sj * P.ns + si) * P.nk + kr);
+            float dba;
+            cubic(t, c.x, c.y, c.z, c.w, below, dba);
+            gk = fmaf(Fpi, dab, fmaf(Fpj, dba, dVk));
+        } else {
+            gk = fmaf(Fpi + Fpj, dab, dVk);
+        }
+        gg = gk * P.inv_drf;
+    }
+    const float gr = inside ? gg * rinv : 0.f;
+    a.fx = fmaf(gr, dx, a.fx);
+    a.fy = fmaf(gr, dy, a.fy);
+    a.fz = fmaf(gr, dz, a.fz);
+    if (ENERGY) {
+        a.ep = fmaf(0.5f, inside ? V : 0.f, a.ep);
+        const float hg = -0.5f * gr;
+        a.wxx = fmaf(hg * dx, dx, a.wxx);
+        a.wyy = fmaf(hg * dy, dy, a.wyy);
+        a.wzz = fmaf(hg * dz, dz, a.wzz);
+        a.wyz = fmaf(hg * dy, dz, a.wyz);
+        a.wxz = fmaf(hg * dx, dz, a.wxz);
+        a.wxy = fmaf(hg * dx, dy, a.wxy);
+    }
+}
+
+// End of the density pass for atom i (lane 0 after the lane sum): rho, F(rho), F'(rho) and the
+// pass-2 copy (position, F').
+__device__ __forceinline__ void density32_finish(const Atoms &A, const Pot &P, int i, int si, const float4 &pi,
+                                                 float hi, float lo) {
+    const double rho = (double)hi + (double)lo;
+    double dF;
+    const double F = embed64(P, si, rho, dF, A.flags);
+    A.rho[i] = rho;
+    A.dF[i] = dF;
+    A.e_atom[i] = F;
+    A.p2f[i] = make_float4(pi.x, pi.y, pi.z, (float)dF);
+}
+
+// Lane sums of the force-pass accumulators over the T lanes of an atom.
+template <int T, bool ENERGY>
+__device__ __forceinline__ void lane_sum_acc(Acc32 &a) {
+    a.fx = lane_sum<T>(a.fx);
+    a.fy = lane_sum<T>(a.fy);
+    a.fz = lane_sum<T>(a.fz);
+    if (ENERGY) {
+        a.ep = lane_sum<T>(a.ep);
+        a.wxx = lane_sum<T>(a.wxx); a.wyy = lane_sum<T>(a.wyy); a.wzz = lane_sum<T>(a.wzz);
+        a.wyz = lane_sum<T>(a.wyz); a.wxz = lane_sum<T>(a.wxz); a.wxy = lane_sum<T>(a.wxy);
+    }
+}
+
+// End of the force pass for atom i: the force, the second half kick and the FP64 partial sums.
+template <bool ENERGY>
+__device__ __forceinline__ void force32_finish(const Atoms &A, int i, const Acc32 &a, double half_dt, bool kick,
+                                               double (&part)[kPartials]) {
+    A.force[i] = make_double4_32a(a.fx, a.fy, a.fz, 0.0);
+    if (!isfinite(a.fx + a.fy + a.fz)) atomicOr(&A.flags->error, FLAG_NONFINITE);
+    double4_32a v = A.vel[i];
+    kick_and_partials(v, a.fx, a.fy, a.fz, half_dt, kick);
+    if (kick) A.vel[i] = v;
+    if (ENERGY) {
+        const double e = A.e_atom[i] + (double)a.ep;
+        A.e_atom[i] = e;
+        const double m = 1.0 / (kMvv2e * v.w);
+        part[0] += e;
+        part[1] += m * fma(v.x, v.x, fma(v.y, v.y, v.z * v.z));
+        part[2] += a.wxx; part[3] += a.wyy; part[4] += a.wzz;
+        part[5] += a.wyz; part[6] += a.wxz; part[7] += a.wxy;
+        part[8] += m * v.x; part[9] += m * v.y; part[10] += m * v.z;
+    }
+}
+
 template <int T, int KIND, bool MULTI, bool SMT = false>
 __device__ __forceinline__ void density32_item(const Atoms &A, const Pot &P, const Box *boxes, long long g) {
     const int i = (int)(g / T), lane = (int)(g & (T - 1));
@@ -76,31 +217,9 @@ __device__ __forceinline__ void density32_item(const Atoms &A, const Pot &P, con
         const int cnt = min(A.count[i], A.k_max);
         const NbrRow row = nbr_row(A, i);
         unsigned viol = 0;
-        // one neighbour: phi(r) if r < r_cut, else 0 (no branch, so loads of the next pair can issue)
         auto term = [&](const float4 &pj) -> float {
-            const float dx = mi32(pj.x - pi.x, Lx, ix);
-            const float dy = mi32(pj.y - pi.y, Ly, iy);
-            const float dz = mi32(pj.z - pi.z, Lz, iz);
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const bool inside = r2 < P.rc2f;
-            const float r = r2 * rsqrtf(r2);
-            float phi;
-            if (KIND == MD_POT_FS_ANALYTIC) {
-                phi = fs_phi<float>(P.fsf, P.bdf, r);
-            } else if (KIND == MD_POT_KNOTS) {
-                const int sj = MULTI ? __float_as_int(pj.w) : 0;
-                float d;
-                phi = knot_sum<float, float2>(P.K32 + (size_t)(P.ns * P.ns + si * P.ns + sj) * P.nkt, P.nkt, r, d);
-            } else {
-                const int sj = MULTI ? __float_as_int(pj.w) : 0;
-                float t, d;
-                bool below;
-                const int kr = knot_row((r - P.r_minf) * P.inv_drf, P.nk, t, below);
-                viol += (below && inside) ? 1u : 0u;
-                const float4 c = phi_row<SMT>(P, (size_t)(si * P.ns + sj) * P.nk + kr);
-                phi = cubic(t, c.x, c.y, c.z, c.w, below, d);
-            }
-            return inside ? phi : 0.f;
+            return rho_term32<KIND, MULTI, SMT>(P, si, MULTI ? __float_as_int(pj.w) : 0, mi32(pj.x - pi.x, Lx, ix),
+                                                mi32(pj.y - pi.y, Ly, iy), mi32(pj.z - pi.z, Lz, iz), viol);
         };
         // two neighbours per iteration, software-pipelined: the positions of the next iteration
         // and the list entries of the one after are loaded before this iteration's terms are
@@ -123,15 +242,7 @@ __device__ __forceinline__ void density32_item(const Atoms &A, const Pot &P, con
         if (viol) atomicAdd(&A.flags->range_violations, (unsigned long long)viol);
     }
     lane_sum_df<T>(hi, lo);
-    if (live && lane == 0) {
-        const double rho = (double)hi + (double)lo;
-        double dF;
-        const double F = embed64(P, si, rho, dF, A.flags);
-        A.rho[i] = rho;
-        A.dF[i] = dF;
-        A.e_atom[i] = F;
-        A.p2f[i] = make_float4(pi.x, pi.y, pi.z, (float)dF);
-    }
+    if (live && lane == 0) density32_finish(A, P, i, si, pi, hi, lo);
 }
 
 // Returns the atom index for the lane that finished atom i (lane 0 of a live atom), else -1.
@@ -140,82 +251,20 @@ __device__ __forceinline__ int force32_item(const Atoms &A, const Pot &P, const 
                                             double half_dt, bool kick, double (&part)[kPartials]) {
     const int i = (int)(g / T), lane = (int)(g & (T - 1));
     const bool live = i < A.n;
-    float fx = 0.f, fy = 0.f, fz = 0.f, ep = 0.f;
-    float wxx = 0.f, wyy = 0.f, wzz = 0.f, wyz = 0.f, wxz = 0.f, wxy = 0.f;
+    Acc32 a;
     if (live) {
         const Box &B = boxes[ph::replica_of(A, i)];
         const float Lx = B.Lf[0], Ly = B.Lf[1], Lz = B.Lf[2];
         const float ix = B.invLf[0], iy = B.invLf[1], iz = B.invLf[2];
         const float4 pi = A.p2f[i];
-        const float Fpi = pi.w;
         const int si = MULTI ? A.spec[i] : 0;
         const int cnt = min(A.count[i], A.k_max);
         const NbrRow row = nbr_row(A, i);
         unsigned viol = 0;
-        // one neighbour: its pair force (zero beyond r_cut; no branch, so loads of the next
-        // pair can issue early) and, on the energy step, its energy and virial
         auto pair = [&](int j, const float4 &pj) {
-            const float dx = mi32(pj.x - pi.x, Lx, ix);
-            const float dy = mi32(pj.y - pi.y, Ly, iy);
-            const float dz = mi32(pj.z - pi.z, Lz, iz);
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const bool inside = r2 < P.rc2f;
-            const float rinv = rsqrtf(r2);
-            const float r = r2 * rinv;
-            const float Fpj = pj.w;
-            float V, gg;
-            if (KIND == MD_POT_FS_ANALYTIC) {
-                float dV;
-                V = fs_V<float>(P.fsf, r, dV);
-                gg = fmaf(Fpi + Fpj, fs_dphi<float>(P.fsf, P.bdf, r), dV);
-            } else if (KIND == MD_POT_KNOTS) {
-                const int sj = MULTI ? __ldg(A.spec + j) : 0;
-                const int nn = P.ns * P.ns;
-                float dVk, dab;
-                V = knot_sum<float, float2>(P.K32 + (size_t)(si * P.ns + sj) * P.nkt, P.nkt, r, dVk);
-                knot_sum<float, float2>(P.K32 + (size_t)(nn + si * P.ns + sj) * P.nkt, P.nkt, r, dab);
-                if (MULTI) {
-                    float dba;
-                    knot_sum<float, float2>(P.K32 + (size_t)(nn + sj * P.ns + si) * P.nkt, P.nkt, r, dba);
-                    gg = fmaf(Fpi, dab, fmaf(Fpj, dba, dVk));
-                } else {
-                    gg = fmaf(Fpi + Fpj, dab, dVk);
-                }
-            } else {
-                const int sj = MULTI ? __ldg(A.spec + j) : 0;
-                float t;
-                bool below;
-                const int kr = knot_row((r - P.r_minf) * P.inv_drf, P.nk, t, below);
-                viol += (below && inside) ? 1u : 0u;
-                float cv[4], cp[4], dVk, dab;
-                vp_row<SMT>(P, (size_t)(si * P.ns + sj) * P.nk + kr, cv, cp);
-                V = cubic(t, cv[0], cv[1], cv[2], cv[3], below, dVk);
-                cubic(t, cp[0], cp[1], cp[2], cp[3], below, dab);
-                float gk;
-                if (MULTI) {
-                    const float4 c = phi_half32(P.VP32, (size_t)(sj * P.ns + si) * P.nk + kr);
-                    float dba;
-                    cubic(t, c.x, c.y, c.z, c.w, below, dba);
-                    gk = fmaf(Fpi, dab, fmaf(Fpj, dba, dVk));
-                } else {
-                    gk = fmaf(Fpi + Fpj, dab, dVk);
-                }
-                gg = gk * P.inv_drf;
-            }
-            const float gr = inside ? gg * rinv : 0.f;
-            fx = fmaf(gr, dx, fx);
-            fy = fmaf(gr, dy, fy);
-            fz = fmaf(gr, dz, fz);
-            if (ENERGY) {
-                ep = fmaf(0.5f, inside ? V : 0.f, ep);
-                const float hg = -0.5f * gr;
-                wxx = fmaf(hg * dx, dx, wxx);
-                wyy = fmaf(hg * dy, dy, wyy);
-                wzz = fmaf(hg * dz, dz, wzz);
-                wyz = fmaf(hg * dy, dz, wyz);
-                wxz = fmaf(hg * dx, dz, wxz);
-                wxy = fmaf(hg * dx, dy, wxy);
-            }
+            pair32<KIND, MULTI, ENERGY, SMT>(P, si, MULTI ? __ldg(A.spec + j) : 0, pi.w, pj.w,
+                                             mi32(pj.x - pi.x, Lx, ix), mi32(pj.y - pi.y, Ly, iy),
+                                             mi32(pj.z - pi.z, Lz, iz), a, viol);
         };
         // two neighbours per iteration; the list entries of the next iteration are loaded before
         // this iteration's positions are used (one dependent load less on the critical path)
@@ -232,30 +281,9 @@ __device__ __forceinline__ int force32_item(const Atoms &A, const Pot &P, const 
         if (k < cnt) pair(j0, __ldg(A.p2f + j0));
         if (viol) atomicAdd(&A.flags->range_violations, (unsigned long long)viol);
     }
-    fx = lane_sum<T>(fx);
-    fy = lane_sum<T>(fy);
-    fz = lane_sum<T>(fz);
-    if (ENERGY) {
-        ep = lane_sum<T>(ep);
-        wxx = lane_sum<T>(wxx); wyy = lane_sum<T>(wyy); wzz = lane_sum<T>(wzz);
-        wyz = lane_sum<T>(wyz); wxz = lane_sum<T>(wxz); wxy = lane_sum<T>(wxy);
-    }
+    lane_sum_acc<T, ENERGY>(a);
     if (!(live && lane == 0)) return -1;
-    A.force[i] = make_double4_32a(fx, fy, fz, 0.0);
-    if (!isfinite(fx + fy + fz)) atomicOr(&A.flags->error, FLAG_NONFINITE);
-    double4_32a v = A.vel[i];
-    kick_and_partials(v, fx, fy, fz, half_dt, kick);
-    if (kick) A.vel[i] = v;
-    if (ENERGY) {
-        const double e = A.e_atom[i] + (double)ep;
-        A.e_atom[i] = e;
-        const double m = 1.0 / (kMvv2e * v.w);
-        part[0] += e;
-        part[1] += m * fma(v.x, v.x, fma(v.y, v.y, v.z * v.z));
-        part[2] += wxx; part[3] += wyy; part[4] += wzz;
-        part[5] += wyz; part[6] += wxz; part[7] += wxy;
-        part[8] += m * v.x; part[9] += m * v.y; part[10] += m * v.z;
-    }
+    force32_finish<ENERGY>(A, i, a, half_dt, kick, part);
     return i;
 }
 

@@ -38,6 +38,17 @@ __device__ __forceinline__ float4 wrapped(const double4_32a &p, const Box &B, in
                        wrap1(p.z, B.L[2], B.invL[2]), __int_as_float(species));
 }
 
+// FP32 position in the periodic image its atom was wrapped into at the last list build (the
+// image of ref, the position at that build): the wrapped position until the atom crosses a box
+// face, continuous after it, so that it stays within skin/2 of its link cell (the staged passes
+// add each cell's image shift to these coordinates; the list passes take the minimum image).
+__device__ __forceinline__ float4 build_image(const double4_32a &p, const double4_32a &ref, const Box &B,
+                                              int species) {
+    return make_float4((float)(p.x - B.L[0] * floor(ref.x * B.invL[0])),
+                       (float)(p.y - B.L[1] * floor(ref.y * B.invL[1])),
+                       (float)(p.z - B.L[2] * floor(ref.z * B.invL[2])), __int_as_float(species));
+}
+
 __device__ __forceinline__ int global_cell(const double4_32a &p, const Box &B, const RepCells &g) {
     const int cx = cell_coord(p.x, B.invL[0], g.nc[0]);
     const int cy = cell_coord(p.y, B.invL[1], g.nc[1]);
@@ -102,7 +113,7 @@ __device__ __forceinline__ void kick_drift(const Atoms &A, const Box *boxes, int
         A.flags->need_rebuild = 1;
         A.flags->skin_exceeded = 1;
     }
-    A.posf[i] = wrapped(p, boxes[replica_of(A, i)], A.spec[i]);
+    A.posf[i] = build_image(p, r, boxes[replica_of(A, i)], A.spec[i]);
 }
 
 __device__ __forceinline__ void check_displacement(const Atoms &A, int i, double lim2) {
@@ -205,6 +216,34 @@ __device__ __forceinline__ void sort_cell_warp(const Atoms &A, const Cells &C, i
     if (lane == 0) C.cell_count[c] = 0;
 }
 
+// Stencil table of cell group g (one system): the staged slot of the first atom of each of its
+// 9 (gx + 2) stencil cells and the total; a group whose neighbourhood exceeds the staging capacity
+// sets tile_bad (the passes then take the list path until the next build).
+__device__ __forceinline__ void group_table(const Cells &C, int g, Flags *f) {
+    const RepCells rg = C.rc[0];
+    const int nx = rg.nc[0], ny = rg.nc[1], nz = rg.nc[2];
+    const int gxi = g % C.ngx, row = g / C.ngx, y = row % ny, z = row / ny;
+    const int x0 = gxi * C.gx, len = min(C.gx, nx - x0);
+    int32_t *loc = C.grp_loc + (size_t)g * (C.st_cells + 1);
+    int acc = 0, q = 0;
+    for (int dz = -1; dz <= 1; dz++) {
+        const int zz = (z + dz + nz) % nz;
+        for (int dy = -1; dy <= 1; dy++) {
+            const int yy = (y + dy + ny) % ny;
+            for (int dx = 0; dx < C.gx + 2; dx++, q++) {
+                loc[q] = acc;
+                if (dx > len + 1) continue;   // a shorter last group: empty slots
+                const int xx = (x0 - 1 + dx + nx) % nx;
+                const int c = rg.base + (zz * ny + yy) * nx + xx;
+                acc += C.cell_start[c + 1] - C.cell_start[c];
+            }
+        }
+    }
+    loc[C.st_cells] = acc;
+    atomicMax(&f->tile_max, acc);
+    if (acc > C.cap) f->tile_bad = 1;
+}
+
 __device__ __forceinline__ void gather_atom(const Atoms &A, int k) {
     const int o = A.sorted[k];
     A.pos_tmp[k] = A.pos[o];
@@ -242,18 +281,6 @@ __device__ __forceinline__ bool within_exact(const double4_32a &pi, const double
     return r2 < rl2;
 }
 
-// Full list rows of the atoms of link cell c (§3.2.1: candidates from the cells around it, 27 for
-// cells r_list wide, 125 for cells r_list / 2 wide) by a group of G lanes (G = 4, 8, 16 or 32;
-// 32 / G cells per warp): lane a of the group takes atoms s + a, s + a + G, ... of the cell.  All
-// lanes of the group walk the same neighbour cells and
-// the same candidates in the same order, so a candidate is one broadcast load for the group and
-// the control flow is uniform inside it.  Candidates are screened with FP32 wrapped coordinates,
-// shifted by whole box edges for neighbour cells across the periodic boundary (no rounding to the
-// nearest image per candidate).  Only a candidate whose FP32 r^2 lies in [band_lo, band_hi] (a band
-// wider than the proven FP32 error) is decided by the exact FP64 test, so each row is the exact
-// FP64 set, listed by cell in (dz, dy, dx) order and by ascending slot inside a cell.  Rows are cut
-// at k_max (the count is kept).  Returns the longest row of this lane's atoms.  The stencil of
-// +-reach cells along each edge needs >= 2 reach + 1 cells per edge (no cell visited twice).
 // The exact test of a candidate in the FP32 band, kept out of line: it is rare, and inlined it
 // would be predicated into every iteration of the candidate loop.
 static __device__ __noinline__ bool within_exact_band(const double4_32a &pi, const double4_32a &pj, const Box &B,
@@ -261,7 +288,22 @@ static __device__ __noinline__ bool within_exact_band(const double4_32a &pi, con
     return within_exact(pi, pj, B, rl2);
 }
 
-template <int G>
+// Full list rows of the atoms of link cell c (§3.2.1: candidates from the cells around it, 27 for
+// cells r_list wide, 125 for cells r_list / 2 wide) by a group of G lanes (G = 4, 8, 16 or 32;
+// 32 / G cells per warp): lane a of the group takes atoms s + a, s + a + G, ... of the cell.  All
+// lanes of the group walk the same neighbour cells and the same candidates in the same order,
+// so a candidate is one broadcast load for the group and
+// the control flow is uniform inside it.  Candidates are screened with FP32 wrapped coordinates,
+// shifted by whole box edges for neighbour cells across the periodic boundary (no rounding to the
+// nearest image per candidate).  Only a candidate whose FP32 r^2 lies in [band_lo, band_hi] (a band
+// wider than the proven FP32 error) is decided by the exact FP64 test, so each row is the exact
+// FP64 set, listed by cell in (dz, dy, dx) order and by ascending slot inside a cell.  Rows are cut
+// at k_max (the count is kept).  Returns the longest row of this lane's atoms.  The stencil of
+// +-reach cells along each edge needs >= 2 reach + 1 cells per edge (no cell visited twice).
+// LOCAL (staged passes, one system, reach 1): every entry is also written to the 16-bit local
+// list as the slot of the candidate in its cell group's stage (grp_loc of the stencil cell plus
+// the candidate's rank inside its cell).
+template <int G, bool LOCAL>
 __device__ __forceinline__ int build_cell_group(const Atoms &A, const Cells &C, const Box *boxes, int c, int gl,
                                                 double rl2, float band_lo, float band_hi) {
     const int s = C.cell_start[c], e = C.cell_start[c + 1];
@@ -284,18 +326,33 @@ __device__ __forceinline__ int build_cell_group(const Atoms &A, const Cells &C, 
         const double4_32a pi = A.pos[ii];
         const float4 fi = A.posf[ii];
         int32_t *wp = A.nbr + 4 * (size_t)ii;   // entry cnt of the row (planes of 4 entries)
+        uint16_t *lwp = LOCAL ? A.lnbr + 4 * (size_t)ii : nullptr;   // the same entry of the local list
         int cnt = 0;
+        int lbase = 0;   // staged slot of the first atom of the current candidate cell (local list)
         // one candidate: append j to the row if it is a neighbour
-        auto visit = [&](int j, float r2) {
+        auto visit = [&](int j, int js, float r2) {
             if (r2 <= band_hi) {
                 const bool in = r2 < band_lo || within_exact_band(pi, A.pos[j], B, rl2);
                 if (in && act && j != i) {
-                    if (cnt < kmax) *wp = j;
+                    if (cnt < kmax) {
+                        *wp = j;
+                        if constexpr (LOCAL) *lwp = (uint16_t)(lbase + (j - js));
+                    }
                     cnt++;
-                    wp += (cnt & 3) ? 1 : plane - 3;
+                    const long long adv = (cnt & 3) ? 1 : plane - 3;
+                    wp += adv;
+                    if constexpr (LOCAL) lwp += adv;
                 }
             }
         };
+        // cell group of the home cell (staged passes): stencil slots of this cell's neighbours
+        const int32_t *gloc = nullptr;
+        int gx0 = 0;
+        if constexpr (LOCAL) {
+            const int gxi = cx / C.gx;
+            gx0 = gxi * C.gx;
+            gloc = C.grp_loc + (size_t)((cz * ny + cy) * C.ngx + gxi) * (C.st_cells + 1);
+        }
         for (int dz = -R; dz <= R; dz++) {
             int z = cz + dz;
             float sz = 0.f;
@@ -314,6 +371,7 @@ __device__ __forceinline__ int build_cell_group(const Atoms &A, const Cells &C, 
                     if (x >= nx) { x -= nx; sx = Lx; }
                     const int cc = rowc + x;
                     const int js = C.cell_start[cc], je = C.cell_start[cc + 1];
+                    if constexpr (LOCAL) lbase = gloc[((dz + 1) * 3 + (dy + 1)) * (C.gx + 2) + (cx - gx0 + dx + 1)];
                     const float ox = sx - fi.x, oy = sy - fi.y, oz = sz - fi.z;
                     int j = js;
                     for (; j + 1 < je; j += 2) {
@@ -322,13 +380,13 @@ __device__ __forceinline__ int build_cell_group(const Atoms &A, const Cells &C, 
                         const float bx = f1.x + ox, by = f1.y + oy, bz = f1.z + oz;
                         const float r0 = fmaf(ax, ax, fmaf(ay, ay, az * az));
                         const float r1 = fmaf(bx, bx, fmaf(by, by, bz * bz));
-                        visit(j, r0);
-                        visit(j + 1, r1);
+                        visit(j, js, r0);
+                        visit(j + 1, js, r1);
                     }
                     if (j < je) {
                         const float4 f0 = A.posf[j];
                         const float ax = f0.x + ox, ay = f0.y + oy, az = f0.z + oz;
-                        visit(j, fmaf(ax, ax, fmaf(ay, ay, az * az)));
+                        visit(j, js, fmaf(ax, ax, fmaf(ay, ay, az * az)));
                     }
                 }
             }
@@ -344,24 +402,25 @@ __device__ __forceinline__ int build_cell_group(const Atoms &A, const Cells &C, 
 
 // The list phase over all cells: warp w of nwarps takes cell groups w, w + nwarps, ...; every
 // lane returns the longest row it built (all 32 lanes of a warp take part in every iteration).
-template <int G>
+template <int G, bool LOCAL>
 __device__ __forceinline__ int build_cells(const Atoms &A, const Cells &C, const Box *boxes, long long warp,
                                            long long nwarps, int lane, double rl2, float band_lo, float band_hi) {
     constexpr int CPW = 32 / G;   // cells per warp
     int m = 0;
     for (long long c0 = warp * CPW; c0 < C.ncell; c0 += nwarps * CPW) {
         const long long c = c0 + lane / G;
-        if (c < C.ncell) m = max(m, build_cell_group<G>(A, C, boxes, (int)c, lane & (G - 1), rl2, band_lo, band_hi));
+        if (c < C.ncell) m = max(m, build_cell_group<G, LOCAL>(A, C, boxes, (int)c, lane & (G - 1), rl2, band_lo, band_hi));
     }
     return m;
 }
 
+template <bool LOCAL>
 __device__ __forceinline__ int build_cells_any(int G, const Atoms &A, const Cells &C, const Box *boxes, long long warp,
                                                long long nwarps, int lane, double rl2, float band_lo, float band_hi) {
-    if (G == 4) return build_cells<4>(A, C, boxes, warp, nwarps, lane, rl2, band_lo, band_hi);
-    if (G == 8) return build_cells<8>(A, C, boxes, warp, nwarps, lane, rl2, band_lo, band_hi);
-    if (G == 16) return build_cells<16>(A, C, boxes, warp, nwarps, lane, rl2, band_lo, band_hi);
-    return build_cells<32>(A, C, boxes, warp, nwarps, lane, rl2, band_lo, band_hi);
+    if (G == 4) return build_cells<4, LOCAL>(A, C, boxes, warp, nwarps, lane, rl2, band_lo, band_hi);
+    if (G == 8) return build_cells<8, LOCAL>(A, C, boxes, warp, nwarps, lane, rl2, band_lo, band_hi);
+    if (G == 16) return build_cells<16, LOCAL>(A, C, boxes, warp, nwarps, lane, rl2, band_lo, band_hi);
+    return build_cells<32, LOCAL>(A, C, boxes, warp, nwarps, lane, rl2, band_lo, band_hi);
 }
 
 }  // namespace ph

@@ -1,5 +1,6 @@
 // Per-atom state kernels outside the step: the skin displacement check (§3.2.1), the FP32
-// wrapped position copy, and the conversions between cell order and the caller's atom order.
+// position copy (in the image of the last list build), and the conversions between cell
+// order and the caller's atom order.
 #include <cuda_runtime.h>
 
 #include "md_phases.cuh"
@@ -17,7 +18,7 @@ __global__ void k_check_displacement(Atoms A, double lim2) {
 __global__ void k_wrap(Atoms A) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= A.n) return;
-    A.posf[i] = ph::wrapped(A.pos[i], A.boxes[ph::replica_of(A, i)], A.spec[i]);
+    A.posf[i] = ph::build_image(A.pos[i], A.ref[i], A.boxes[ph::replica_of(A, i)], A.spec[i]);
 }
 
 __global__ void k_unsort_vec(Atoms A, const double4_32a *src, double *dst) {

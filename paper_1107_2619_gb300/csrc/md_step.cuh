@@ -19,6 +19,7 @@
 #include <algorithm>
 
 #include "md_passes.cuh"
+#include "md_tile.cuh"
 
 namespace mdk {
 namespace st {
@@ -125,15 +126,22 @@ __device__ __forceinline__ void thermo_update(const StepParams &sp, int n_rep, l
 
 // NT threads per block.  SMT: the single-species knot table is copied into dynamic shared
 // memory at the start of the launch and the passes read it there (one 1024-thread block per SM).
-template <int PREC, int T, int KIND, bool MULTI, int NT, bool SMT>
+// WALK (kWalkStaged, kWalkCells): the passes run over cell groups staged in shared memory
+// (md_tile.cuh) whenever every group's neighbourhood fitted the stage at the last build, else
+// over atoms through the list.  The cell walk builds no list at a rebuild unless a group did not
+// fit (the list walk then needs one).
+template <int PREC, int T, int KIND, bool MULTI, int NT, bool SMT, int WALK>
 __global__ void __launch_bounds__(NT, NT == kThreads ? MD_STEP_MIN_BLOCKS : 1)
     k_step(Atoms A, Cells C, Pot P, StepParams sp, GridBarrier *bar, unsigned long long *stamps) {
     __shared__ int ws[32];
+    __shared__ int tile_loc[WALK ? tl::kTileMaxSt + 1 : 1];
+    __shared__ uint16_t cells_q[WALK == kWalkCells ? NT / 32 : 1][kCellsQueue];
+    extern __shared__ float4 sm_table_f4[];   // [SMT table][stage]
+    float4 *const stage = sm_table_f4 + (SMT ? 2 * P.nk : 0);
     const unsigned nb = gridDim.x;
     const long long tid = (long long)blockIdx.x * NT + threadIdx.x;
     const long long stride = (long long)nb * NT;
     if (SMT) {
-        extern __shared__ float4 sm_table_f4[];
         const float4 *src = reinterpret_cast<const float4 *>(P.VP32);
         for (int q = threadIdx.x; q < 2 * P.nk; q += NT) sm_table_f4[q] = __ldg(src + q);
         __syncthreads();
@@ -197,7 +205,11 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? MD_STEP_MIN_BLOCKS : 1)
             MD_SYNC();
             MD_STAMP(2);
             if (blockIdx.x == 0) {
-                if (threadIdx.x == 0) A.flags->max_count = 0;
+                if (threadIdx.x == 0) {
+                    A.flags->max_count = 0;
+                    A.flags->tile_bad = 0;
+                    A.flags->tile_max = 0;
+                }
                 ph::scan_top(C, ws);
             }
             MD_SYNC();
@@ -206,6 +218,11 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? MD_STEP_MIN_BLOCKS : 1)
             MD_SYNC();
             MD_STAMP(4);
             for (long long i = tid; i < A.n; i += stride) ph::scatter_atom(A, C, (int)i);
+            if constexpr (WALK != kWalkList) {
+                for (long long g = tid; g < C.n_groups; g += stride) ph::group_table(C, (int)g, A.flags);
+            } else {
+                if (C.tile && lead) A.flags->tile_bad = 1;   // this build writes no local lists
+            }
             MD_SYNC();
             MD_STAMP(5);
             for (long long c = tid >> 5; c < C.ncell; c += stride >> 5) ph::sort_cell_warp(A, C, (int)c, threadIdx.x & 31);
@@ -217,10 +234,12 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? MD_STEP_MIN_BLOCKS : 1)
             for (long long k = tid; k < A.n; k += stride) ph::copyback_atom(A, boxes, (int)k);
             MD_SYNC();
             MD_STAMP(8);
-            int m = ph::build_cells_any(sp.list_group, A, C, boxes, tid >> 5, stride >> 5, threadIdx.x & 31, sp.rl2,
-                                        sp.band_lo, sp.band_hi);
-            m = __reduce_max_sync(0xffffffffu, m);
-            if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(&A.flags->max_count, m);
+            if (WALK != kWalkCells || *reinterpret_cast<volatile int32_t *>(&A.flags->tile_bad)) {
+                int m = ph::build_cells_any<WALK == kWalkStaged>(sp.list_group, A, C, boxes, tid >> 5, stride >> 5,
+                                                                 threadIdx.x & 31, sp.rl2, sp.band_lo, sp.band_hi);
+                m = __reduce_max_sync(0xffffffffu, m);
+                if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(&A.flags->max_count, m);
+            }
             MD_SYNC();
             MD_STAMP(9);
         } else if (srow) {
@@ -232,7 +251,24 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? MD_STEP_MIN_BLOCKS : 1)
             A.flags->n_rebuilds++;
             A.flags->need_rebuild = 0;
         }
-        for (long long g = tid; g < items; g += stride) ps::density_item<PREC, T, KIND, MULTI, SMT>(A, P, boxes, g);
+        bool tiled = false;
+        if constexpr (WALK != kWalkList) tiled = *reinterpret_cast<volatile int32_t *>(&A.flags->tile_bad) == 0;
+        if constexpr (WALK != kWalkList) {
+            if (tiled) {
+                for (int g = blockIdx.x; g < C.n_groups; g += nb) {
+                    const tl::Group G = tl::stage_group<NT>(C, boxes[0], A.posf, g, stage, tile_loc);
+                    if constexpr (WALK == kWalkStaged) {
+                        const int gi = ((G.h1 - G.h0) * T + 31) & ~31;
+                        for (int it = threadIdx.x; it < gi; it += NT)
+                            tl::density_item<T, KIND, SMT>(A, P, stage, G.h1, G.h0 + it / T, it & (T - 1));
+                    } else if constexpr (WALK == kWalkCells) {
+                        tl::density_cells<NT, KIND, SMT>(A, P, stage, tile_loc, C.gx + 2, G, cells_q[threadIdx.x >> 5]);
+                    }
+                }
+            }
+        }
+        if (!tiled)
+            for (long long g = tid; g < items; g += stride) ps::density_item<PREC, T, KIND, MULTI, SMT>(A, P, boxes, g);
         MD_SYNC();
         MD_STAMP(10);
         // ------------------------------------------------ force pass (+ kicks)
@@ -244,16 +280,55 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? MD_STEP_MIN_BLOCKS : 1)
 #pragma unroll
         for (int q = 0; q < kPartials; q++) part[q] = 0.0;
         if (last && sp.energy_last) {
-            for (long long g = tid; g < items; g += stride)
-                ps::force_item<PREC, T, KIND, MULTI, true, SMT>(A, P, boxes, g, sp.half_dt, true, part);
+            if constexpr (WALK != kWalkList) {
+                if (tiled) {
+                    for (int g = blockIdx.x; g < C.n_groups; g += nb) {
+                        const tl::Group G = tl::stage_group<NT>(C, boxes[0], A.p2f, g, stage, tile_loc);
+                        if constexpr (WALK == kWalkStaged) {
+                            const int gi = ((G.h1 - G.h0) * T + 31) & ~31;
+                            for (int it = threadIdx.x; it < gi; it += NT)
+                                tl::force_item<T, KIND, true, SMT>(A, P, stage, G.h1, G.h0 + it / T, it & (T - 1),
+                                                                   sp.half_dt, true, part);
+                        } else if constexpr (WALK == kWalkCells) {
+                            tl::force_cells<NT, KIND, true, SMT>(A, P, boxes, stage, tile_loc, C.gx + 2, G,
+                                                                 cells_q[threadIdx.x >> 5], sp.half_dt, sp.dt, sp.lim2,
+                                                                 false, part);
+                        }
+                    }
+                }
+            }
+            if (!tiled)
+                for (long long g = tid; g < items; g += stride)
+                    ps::force_item<PREC, T, KIND, MULTI, true, SMT>(A, P, boxes, g, sp.half_dt, true, part);
             eam::block_partials<NT>(part, A.partials, A.part_stride);
         } else {
-            for (long long g = tid; g < items; g += stride) {
-                const int i =
-                    ps::force_item<PREC, T, KIND, MULTI, false, SMT>(A, P, boxes, g, sp.half_dt, true, part);
-                if (fuse && i >= 0)
-                    ph::kick_drift(A, boxes, i, sp.half_dt, sp.dt, sp.strain_scale, false, sp.lim2);
+            if constexpr (WALK != kWalkList) {
+                if (tiled) {
+                    for (int g = blockIdx.x; g < C.n_groups; g += nb) {
+                        const tl::Group G = tl::stage_group<NT>(C, boxes[0], A.p2f, g, stage, tile_loc);
+                        if constexpr (WALK == kWalkStaged) {
+                            const int gi = ((G.h1 - G.h0) * T + 31) & ~31;
+                            for (int it = threadIdx.x; it < gi; it += NT) {
+                                const int i = tl::force_item<T, KIND, false, SMT>(A, P, stage, G.h1, G.h0 + it / T,
+                                                                                  it & (T - 1), sp.half_dt, true, part);
+                                if (fuse && i >= 0)
+                                    ph::kick_drift(A, boxes, i, sp.half_dt, sp.dt, sp.strain_scale, false, sp.lim2);
+                            }
+                        } else if constexpr (WALK == kWalkCells) {
+                            tl::force_cells<NT, KIND, false, SMT>(A, P, boxes, stage, tile_loc, C.gx + 2, G,
+                                                                  cells_q[threadIdx.x >> 5], sp.half_dt, sp.dt, sp.lim2,
+                                                                  fuse, part);
+                        }
+                    }
+                }
             }
+            if (!tiled)
+                for (long long g = tid; g < items; g += stride) {
+                    const int i =
+                        ps::force_item<PREC, T, KIND, MULTI, false, SMT>(A, P, boxes, g, sp.half_dt, true, part);
+                    if (fuse && i >= 0)
+                        ph::kick_drift(A, boxes, i, sp.half_dt, sp.dt, sp.strain_scale, false, sp.lim2);
+                }
         }
         MD_SYNC();
         MD_STAMP(11);
@@ -297,24 +372,20 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? MD_STEP_MIN_BLOCKS : 1)
 #undef MD_SYNC
 }
 
-// Largest single-species table (bytes) kept in shared memory by the SMT variant (MD_SMEM_TABLE=0
-// at build time turns the variant off).
-constexpr size_t kSmemTableMax = 200 * 1024;
-#ifndef MD_SMEM_TABLE
-#define MD_SMEM_TABLE 1
-#endif
 
-template <int PREC, int T, int KIND, bool MULTI, int NT = kThreads, bool SMT = false>
+template <int PREC, int T, int KIND, bool MULTI, int NT = kThreads, bool SMT = false, int WALK = kWalkList>
 cudaError_t launch_t(const Atoms &A, const Cells &C, const Pot &P, const StepParams &sp, GridBarrier *bar,
                      unsigned long long *stamps, int *grid_out, cudaStream_t s) {
     static int per_sm = -1;
     static int n_sm = 0;
     static size_t per_sm_dyn = 0;
     static bool attr = false;
-    const size_t dyn = SMT ? (size_t)P.nk * 32 : 0;
-    if (SMT && !attr) {  // opt in to a large dynamic shared-memory carve-out (once)
-        cudaError_t e = cudaFuncSetAttribute(k_step<PREC, T, KIND, MULTI, NT, SMT>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTableMax);
+    const size_t dyn_max = WALK == kWalkCells ? kSmemDynMaxCells : kSmemDynMax;
+    const size_t dyn = (SMT ? (size_t)P.nk * 32 : 0) + (WALK ? (size_t)C.cap * sizeof(float4) : 0);
+    if (dyn > dyn_max) return cudaErrorInvalidConfiguration;
+    if ((SMT || WALK) && !attr) {  // opt in to a large dynamic shared-memory carve-out (once)
+        cudaError_t e = cudaFuncSetAttribute(k_step<PREC, T, KIND, MULTI, NT, SMT, WALK>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max);
         if (e != cudaSuccess) return e;
         attr = true;
     }
@@ -323,7 +394,8 @@ cudaError_t launch_t(const Atoms &A, const Cells &C, const Pot &P, const StepPar
         cudaError_t e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<PREC, T, KIND, MULTI, NT, SMT>, NT, dyn);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<PREC, T, KIND, MULTI, NT, SMT, WALK>, NT,
+                                                              dyn);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) return cudaErrorInvalidConfiguration;
         per_sm_dyn = dyn;
@@ -340,8 +412,8 @@ cudaError_t launch_t(const Atoms &A, const Cells &C, const Pot &P, const StepPar
     Pot p = P;
     StepParams q = sp;
     void *args[] = {&a, &c, &p, &q, &bar, &stamps};
-    return cudaLaunchCooperativeKernel((const void *)k_step<PREC, T, KIND, MULTI, NT, SMT>, dim3(grid), dim3(NT), args,
-                                       dyn, s);
+    return cudaLaunchCooperativeKernel((const void *)k_step<PREC, T, KIND, MULTI, NT, SMT, WALK>, dim3(grid), dim3(NT),
+                                       args, dyn, s);
 }
 
 template <int PREC, int T>
@@ -353,8 +425,17 @@ cudaError_t launch_kind(const Atoms &A, const Cells &C, const Pot &P, const Step
         return P.ns == 1 ? launch_t<PREC, T, MD_POT_KNOTS, false>(A, C, P, sp, bar, stamps, grid_out, s)
                          : launch_t<PREC, T, MD_POT_KNOTS, true>(A, C, P, sp, bar, stamps, grid_out, s);
     if (P.ns == 1) {
-        if (MD_SMEM_TABLE && PREC == MD_PREC_MIXED && (size_t)P.nk * 32 <= kSmemTableMax)
+        if (smem_table_bytes(P.kind, P.ns, PREC, P.nk) > 0) {
+            if constexpr (PREC == MD_PREC_MIXED && T <= 8) {
+                if (C.tile == kWalkStaged)
+                    return launch_t<PREC, T, MD_POT_TABLES, false, 1024, true, kWalkStaged>(A, C, P, sp, bar, stamps,
+                                                                                           grid_out, s);
+                if (C.tile == kWalkCells)
+                    return launch_t<PREC, T, MD_POT_TABLES, false, 1024, true, kWalkCells>(A, C, P, sp, bar, stamps,
+                                                                                          grid_out, s);
+            }
             return launch_t<PREC, T, MD_POT_TABLES, false, 1024, true>(A, C, P, sp, bar, stamps, grid_out, s);
+        }
         return launch_t<PREC, T, MD_POT_TABLES, false>(A, C, P, sp, bar, stamps, grid_out, s);
     }
     return launch_t<PREC, T, MD_POT_TABLES, true>(A, C, P, sp, bar, stamps, grid_out, s);

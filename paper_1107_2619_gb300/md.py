@@ -33,7 +33,7 @@ MD_PREC_FP64, MD_PREC_MIXED = 0, 1
 # functions declared in include/md.h (checked by the CPU test-suite)
 EXPORTS = ["md_abi_version", "md_status_string", "md_create", "md_create_batch", "md_build_neighbours",
            "md_eam_forces", "md_step", "md_set_graph", "md_energy", "md_replica_energies", "md_get",
-           "md_set_state", "md_tune", "md_set_profiling", "md_get_profile", "md_selftest_timeout",
+           "md_set_state", "md_tune", "md_set_profiling", "md_get_profile", "md_get_passes", "md_selftest_timeout",
            "md_neighbours_noalloc", "md_set_thermostat", "md_get_thermostat", "md_set_surrogate", "md_sur_get_params", "md_sur_standardize",
            "md_sur_get", "md_sur_set_reference", "md_sur_loss_grad", "md_sur_train", "md_last_error",
            "md_destroy"]
@@ -51,7 +51,17 @@ class md_config(C.Structure):
     _fields_ = [("n_atoms", C.c_int64), ("h", C.c_double * 9), ("skin", C.c_double),
                 ("k_max", C.c_int32), ("rebuild_every", C.c_int32), ("dt_fs", C.c_double),
                 ("precision", C.c_int32), ("strict_skin", C.c_int32), ("strain_rate_zz", C.c_double),
-                ("stream", C.c_void_p), ("lanes_per_atom", C.c_int32), ("pad", C.c_int32)]
+                ("stream", C.c_void_p), ("lanes_per_atom", C.c_int32), ("passes", C.c_int32)]
+
+
+MD_PASSES_AUTO, MD_PASSES_LIST, MD_PASSES_STAGED, MD_PASSES_CELLS = 0, 1, 2, 3
+PASSES = {"auto": MD_PASSES_AUTO, "list": MD_PASSES_LIST, "staged": MD_PASSES_STAGED, "cells": MD_PASSES_CELLS}
+WALKS = {v: k for k, v in PASSES.items()}
+
+
+class md_passes(C.Structure):
+    _fields_ = [("walk", C.c_int32), ("cells_per_group", C.c_int32), ("groups", C.c_int32),
+                ("capacity", C.c_int32), ("last_max", C.c_int32), ("active", C.c_int32)]
 
 
 class md_surrogate(C.Structure):
@@ -124,6 +134,8 @@ def lib():
         L.md_set_profiling.argtypes = [P, i32]
         L.md_get_profile.restype = C.c_int
         L.md_get_profile.argtypes = [P, C.POINTER(md_profile)]
+        L.md_get_passes.restype = C.c_int
+        L.md_get_passes.argtypes = [P, C.POINTER(md_passes)]
         L.md_neighbours_noalloc.restype = C.c_int
         L.md_neighbours_noalloc.argtypes = [P, i64, P, C.c_double, i32, P, P, P]
         L.md_set_thermostat.restype = C.c_int
@@ -279,6 +291,14 @@ def md_get_profile(ctx) -> dict:
     return d
 
 
+def md_get_passes(ctx) -> dict:
+    p = md_passes()
+    _check(ctx, lib().md_get_passes(ctx, C.byref(p)))
+    d = {k: getattr(p, k) for k, _ in md_passes._fields_}
+    d["walk"] = WALKS[d["walk"]]
+    return d
+
+
 def md_neighbours_noalloc(pos, box, r_list: float, k_max: int, count, nbr_list, stream=None) -> int:
     """Neighbour list into caller-owned device tensors, with no device allocation by the
     library (for callers that cannot allocate); returns the md_status code."""
@@ -379,7 +399,7 @@ def make_potential(pot: _inputs.Potential):
 
 
 def make_config(n_atoms, box, skin, k_max, dt_fs, precision=MD_PREC_FP64, rebuild_every=0,
-                strict_skin=False, strain_rate_zz=0.0, stream=None, lanes_per_atom=0):
+                strict_skin=False, strain_rate_zz=0.0, stream=None, lanes_per_atom=0, passes="auto"):
     c = md_config()
     c.n_atoms = int(n_atoms)
     for k in range(9):
@@ -390,6 +410,7 @@ def make_config(n_atoms, box, skin, k_max, dt_fs, precision=MD_PREC_FP64, rebuil
     c.precision, c.strict_skin, c.strain_rate_zz = int(precision), int(bool(strict_skin)), float(strain_rate_zz)
     c.stream = C.c_void_p(stream) if stream else None
     c.lanes_per_atom = int(lanes_per_atom)
+    c.passes = PASSES[passes]
     return c
 
 
@@ -398,12 +419,12 @@ class System:
 
     def __init__(self, w: _inputs.Workload, precision: str = "fp64", rebuild_every: int = 0,
                  strict_skin: bool = False, stream=None, device_inputs: bool = False, k_max=None,
-                 lanes_per_atom: int = 0):
+                 lanes_per_atom: int = 0, passes: str = "auto"):
         prec = MD_PREC_FP64 if precision == "fp64" else MD_PREC_MIXED
         self.n = w.n_atoms
         self.k_max = int(k_max or w.k_max)
         self.config = make_config(w.n_atoms, w.box, w.skin, self.k_max, w.dt_fs, prec, rebuild_every,
-                                  strict_skin, w.strain_rate_zz, stream, lanes_per_atom)
+                                  strict_skin, w.strain_rate_zz, stream, lanes_per_atom, passes)
         pot, keep = make_potential(w.potential)
         pos = np.ascontiguousarray(w.pos, dtype=np.float64)
         vel = np.ascontiguousarray(w.vel, dtype=np.float64)
@@ -468,6 +489,12 @@ class System:
 
     def profile(self) -> dict:
         return md_get_profile(self.ctx)
+
+    def passes(self) -> dict:
+        """The step kernel's neighbour walk: walk ("list", "staged" or "cells": the walk prepared),
+        cells_per_group, groups, capacity, last_max (largest group neighbourhood at the last
+        build), active (the next md_step walks the prepared groups)."""
+        return md_get_passes(self.ctx)
 
     def set_state(self, pos=None, vel=None, force=None):
         md_set_state(self.ctx, pos, vel, force)

@@ -41,10 +41,11 @@ def test_struct_layouts_match_header(tmp_path, libmd):
 #include <stddef.h>
 #include "md.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu\\n", sizeof(md_potential), sizeof(md_config), sizeof(md_energies), sizeof(md_profile),
-         sizeof(md_surrogate));
-  printf("%zu %zu %zu %zu %zu\\n", offsetof(md_potential, tables), offsetof(md_config, stream),
-         offsetof(md_energies, range_violations), offsetof(md_profile, ms_force), offsetof(md_surrogate, rd));
+  printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(md_potential), sizeof(md_config), sizeof(md_energies),
+         sizeof(md_profile), sizeof(md_surrogate), sizeof(md_passes));
+  printf("%zu %zu %zu %zu %zu %zu %zu\\n", offsetof(md_potential, tables), offsetof(md_config, stream),
+         offsetof(md_energies, range_violations), offsetof(md_profile, ms_force), offsetof(md_surrogate, rd),
+         offsetof(md_config, passes), offsetof(md_passes, active));
   return 0;
 }""")
     exe = tmp_path / "layout"
@@ -52,14 +53,14 @@ int main(void) {
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
     got = [int(x) for x in out]
     want = [C.sizeof(md.md_potential), C.sizeof(md.md_config), C.sizeof(md.md_energies),
-            C.sizeof(md.md_profile), C.sizeof(md.md_surrogate), md.md_potential.tables.offset,
+            C.sizeof(md.md_profile), C.sizeof(md.md_surrogate), C.sizeof(md.md_passes), md.md_potential.tables.offset,
             md.md_config.stream.offset, md.md_energies.range_violations.offset, md.md_profile.ms_force.offset,
-            md.md_surrogate.rd.offset]
+            md.md_surrogate.rd.offset, md.md_config.passes.offset, md.md_passes.active.offset]
     assert got == want
 
 
 def test_status_strings(libmd):
-    assert libmd.md_abi_version() == 2
+    assert libmd.md_abi_version() == 3
     assert md.status_string(md.MD_ERR_NBR_OVERFLOW) == "neighbour list overflow"
     assert md.status_string(md.MD_ERR_SPECIES) == "unsupported species"
 

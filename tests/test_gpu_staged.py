@@ -1,0 +1,166 @@
+"""Group walks of the mixed-precision step kernel (MD_PASSES_STAGED, MD_PASSES_CELLS) against
+the FP64 oracle.
+
+Both walks read each atom's neighbours from a shared-memory copy of its cell group's
+neighbourhood: the staged walk through a 16-bit copy of its list row, the cell walk (no Verlet
+list) by testing every staged atom of the 27 cells around its own.  A wrong local index, a
+missed periodic shift, a stencil cell staged from the wrong place or a candidate range off by a
+cell changes a force by far more than the mixed bound, so element-wise force parity at the final
+positions of a trajectory checks the staging, the local lists written by both list builds (the
+stand-alone rebuild before the first step and the step kernel's own rebuild phases), the
+candidate ranges and the group slot tables.
+
+Workloads: fcc Cu (Sutton-Chen knot tables, 5,000 knots, held in shared memory) with Gaussian
+displacements, on 3 x 3 x 3 link cells (stencils that wrap onto the same cell twice), 4^3 cells,
+and a non-cubic 6 x 3 x 4 grid (a shorter last group in a row for most group lengths).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1107_2619_gb300 import inputs as I, md
+
+pytestmark = pytest.mark.gpu
+
+MIXED_PE_TOL = 1e-6
+
+
+def mixed_force_bound(w, fmax):
+    """The mixed-precision force bound of the list walk: 100 eV/Å^2 x ulp32(L_max), or 1e-4 of
+    the largest force.  The staged walk forms r_j - r_i from FP32 positions with the periodic
+    shift added in FP32 (one more rounding of a coordinate of magnitude <= L + r_list), within
+    the same bound."""
+    lmax = float(np.max(w.box))
+    ulp32 = 2.0 ** (np.floor(np.log2(lmax)) - 23)
+    return max(1e-4 * fmax, 100.0 * ulp32)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1107_2619_gb300 import build
+    build.build()
+
+
+def _case(name):
+    if name == "cu7":
+        return I.fcc_cu(7, seed=21, sigma=0.05, temperature=600.0)
+    if name == "cu10":
+        return I.fcc_cu(10, seed=22, sigma=0.05)
+    if name == "cu_rect":
+        w = I.fcc_cu(7, seed=23)
+        pos, box = I.replicate(I.FCC_BASIS, (13, 8, 9), 3.615)
+        pos = I.gaussian_displace(pos, 0.05, 23)
+        n = len(pos)
+        sp = np.zeros(n, np.int32)
+        vel = I.maxwell_boltzmann(w.potential.masses[sp], 300.0, 23)
+        return I.Workload(name="fcc Cu 13x8x9", pos=pos, vel=vel, species=sp, box=box, potential=w.potential,
+                          skin=w.skin, k_max=w.k_max, dt_fs=w.dt_fs, steps=1, temperature=300.0)
+    raise ValueError(name)
+
+
+@pytest.mark.parametrize("walk,lanes", [("staged", 1), ("staged", 2), ("staged", 4), ("staged", 8),
+                                        ("cells", 1), ("cells", 4)])
+@pytest.mark.parametrize("case", ["cu7", "cu10", "cu_rect"])
+def test_group_walk_steps_match_the_oracle(case, walk, lanes):
+    w = _case(case)
+    n_steps = 12
+    ref = oracle.run_vv(w.pos, w.vel, w.species, w.potential.masses, w.box, w.potential, w.dt_fs, n_steps,
+                        w.skin, w.k_max)
+    with md.System(w, precision="mixed", lanes_per_atom=lanes, passes=walk) as s:
+        p = s.passes()
+        assert p["walk"] == walk and p["groups"] > 0 and 1 <= p["cells_per_group"] <= 8
+        s.step(n_steps)
+        p = s.passes()
+        assert p["active"] == 1 and 0 < p["last_max"] <= p["capacity"]
+        pos, f, e = s.positions(), s.forces(), s.energy()
+    assert np.abs(pos - ref["pos"]).max() < 1e-5
+    assert abs(e["pe"] - ref["energies"][-1, 0]) <= MIXED_PE_TOL * abs(ref["energies"][-1, 0])
+    # the last force pass of the step kernel (staged) at the GPU's own final positions
+    fr = oracle.forces(pos, w.species, w.box, w.potential, skin=w.skin, k_max=w.k_max)["force"]
+    assert np.abs(f - fr).max() <= mixed_force_bound(w, np.abs(fr).max())
+
+
+@pytest.mark.parametrize("walk", ["staged", "cells"])
+def test_group_walk_rebuild_phases_inside_the_step_kernel(walk):
+    """Rebuilds every 3 steps: the group slot tables (and local lists) of the step kernel's own
+    rebuild phases, then steps that use them; after the cell walk's list-free rebuilds the list
+    is built again, at the current positions, when it is asked for."""
+    w = _case("cu10")
+    ref = oracle.run_vv(w.pos, w.vel, w.species, w.potential.masses, w.box, w.potential, w.dt_fs, 14,
+                        w.skin, w.k_max, rebuild_every=3)
+    with md.System(w, precision="mixed", rebuild_every=3, passes=walk) as s:
+        s.step(14)
+        e = s.energy()
+        assert s.passes()["active"] == 1
+        pos, f = s.positions(), s.forces()
+        counts = s.get(md.MD_GET_NBR_COUNT)
+    assert e["n_rebuilds"] >= 4
+    assert np.abs(pos - ref["pos"]).max() < 1e-5
+    fr = oracle.forces(pos, w.species, w.box, w.potential, skin=w.skin, k_max=w.k_max)["force"]
+    assert np.abs(f - fr).max() <= mixed_force_bound(w, np.abs(fr).max())
+    if walk == "cells":   # the list asked for after list-free steps is built at the current positions
+        ref_counts = oracle.neighbours(pos, w.box, w.potential.r_cut + w.skin, w.k_max, "brute")[0]
+        assert np.array_equal(counts, ref_counts)
+
+
+@pytest.mark.parametrize("walk", ["staged", "cells"])
+def test_group_and_list_walks_differ_in_rounding_only(walk):
+    w = _case("cu_rect")
+    with md.System(w, precision="mixed", lanes_per_atom=4, passes=walk) as a, \
+            md.System(w, precision="mixed", lanes_per_atom=4, passes="list") as b:
+        assert a.passes()["walk"] == walk and b.passes()["walk"] == "list"
+        a.step(10)
+        b.step(10)
+        assert b.passes()["active"] == 0
+        fa, fb = a.forces(), b.forces()
+        assert np.abs(a.positions() - b.positions()).max() < 1e-6
+        ea, eb = a.energy(), b.energy()
+    assert np.abs(fa - fb).max() <= mixed_force_bound(w, np.abs(fb).max())
+    assert abs(ea["pe"] - eb["pe"]) <= MIXED_PE_TOL * abs(eb["pe"])
+
+
+def test_auto_takes_the_list_walk():
+    with md.System(_case("cu7"), precision="mixed") as s:
+        s.step(2)
+        p = s.passes()
+        assert p["walk"] == "list" and p["active"] == 0
+
+
+@pytest.mark.parametrize("walk", ["staged", "cells"])
+@pytest.mark.parametrize("precision,name", [("fp64", "cu7"), ("mixed", "fe")])
+def test_group_walk_where_it_does_not_apply_is_an_argument_error(precision, name, walk):
+    w = _case("cu7") if name == "cu7" else I.bcc_fe(8, seed=3)
+    with pytest.raises(md.MDError) as ex:
+        md.System(w, precision=precision, passes=walk)
+    assert ex.value.status == md.MD_ERR_ARG
+
+
+@pytest.mark.parametrize("walk", ["staged", "cells"])
+def test_overfull_group_falls_back_to_the_list_walk_and_back(walk):
+    """Squeeze the crystal into half of the box along y (twice the density): the groups whose
+    3-cell-high neighbourhood lies inside the dense half hold about twice the atoms the stage
+    was sized for, so the build marks them and the step kernel walks the list; a state at the
+    original density restores the group walk."""
+    w = I.fcc_cu(13, seed=24, sigma=0.02)
+    k_max = 400   # the squeezed half has twice the neighbours
+    squeezed = w.pos.copy()
+    squeezed[:, 1] = np.mod(squeezed[:, 1], w.box[1]) * 0.5
+    with md.System(w, precision="mixed", lanes_per_atom=8, passes=walk, k_max=k_max) as s:
+        s.step(1)
+        assert s.passes()["active"] == 1
+        s.set_state(pos=squeezed, vel=np.zeros_like(squeezed))
+        s.step(1)
+        p = s.passes()
+        assert p["last_max"] > p["capacity"] and p["active"] == 0
+        pos, f = s.positions(), s.forces()
+        fr = oracle.forces(pos, w.species, w.box, w.potential, skin=w.skin, k_max=k_max)["force"]
+        assert np.abs(f - fr).max() <= mixed_force_bound(w, np.abs(fr).max())
+        s.set_state(pos=w.pos, vel=w.vel)
+        s.step(2)
+        assert s.passes()["active"] == 1
+        pos, f = s.positions(), s.forces()
+    fr = oracle.forces(pos, w.species, w.box, w.potential, skin=w.skin, k_max=k_max)["force"]
+    assert np.abs(f - fr).max() <= mixed_force_bound(w, np.abs(fr).max())
