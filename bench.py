@@ -259,9 +259,9 @@ def run_ours(args):
     res, snapshot = {}, {}
     for precision in (("mixed",) if args.profile_case else ("mixed", "fp64")):
         s = md.System(w, precision=precision, stream=stream.cuda_stream, device_inputs=True,
-                      passes=args.passes if precision == "mixed" else "auto")
+                      passes=args.passes if precision == "mixed" else "auto", lanes_per_atom=args.lanes)
         s.eam_forces()
-        lanes = s.tune()
+        lanes = args.lanes or s.tune()
         counts = s.get(md.MD_GET_NBR_COUNT)
         s.step(args.warmup)
         e0 = s.energy()
@@ -474,12 +474,45 @@ def run_extras(torch, md, stream, barrier, max_over_ranks, world):
     for prec in ("fp64", "mixed"):
         rec[f"explicit_over_tables_{prec}"] = rec[f"explicit_{prec}_ms_per_step"] / rec[f"tables_{prec}_ms_per_step"]
     out["fe_knots_vs_tables_1m"] = rec
+    out["cu500k_walks"] = walks_extra(torch, md, stream, barrier, max_over_ranks, world)
     if os.path.exists(SUR_WEIGHTS):
         out["surrogate_fe_1m"] = surrogate_extra(torch, md, stream, barrier, max_over_ranks, world)
     return out
 
 
 SUR_WEIGHTS = os.path.join(ROOT, "paper_1107_2619_gb300", "data", "surrogate_fe.npz")
+
+
+def walks_extra(torch, md, stream, barrier, max_over_ranks, world, k_time=200):
+    """The headline workload (fcc Cu 50^3 cells, mixed) with each neighbour walk of the step kernel
+    (md.h MD_PASSES_*): Verlet list from global memory, list rows as shared-memory stage slots,
+    the list-free link-cell walk over the staged cells, and the half list with Newton's third
+    law over the staged cells; ms per step and the phase split."""
+    w = I.fcc_cu(CELLS, seed=SEED)
+    out = {"workload": "fcc Cu 50^3 cells (500,000 atoms), 300 K, dt 2 fs, 5,000-knot tables, mixed",
+           "timed_steps": k_time, "walks": {}}
+    for walk, lanes in (("list", 0), ("staged", 4), ("cells", 4), ("half", 8)):
+        s = md.System(w, precision="mixed", stream=stream.cuda_stream, device_inputs=True, passes=walk,
+                      lanes_per_atom=lanes)
+        s.eam_forces()
+        lanes = lanes or s.tune()
+        s.step(10)
+        e0 = s.energy()
+        ms, _ = _time_steps(torch, s, stream, k_time, barrier)
+        ms = max_over_ranks(ms)
+        e1 = s.energy()
+        s.set_profiling(True)
+        s.step(k_time)
+        p = s.profile()
+        s.set_profiling(False)
+        out["walks"][walk] = {"ms_per_step": ms / k_time, "lanes_per_atom": lanes,
+                              "value": job_value(w.n_atoms, world, k_time, ms),
+                              "rebuilds": e1["n_rebuilds"] - e0["n_rebuilds"],
+                              "phase_ms": {k: p["ms_" + k] / max(1, p["n_" + k])
+                                           for k in ("kick", "rebuild", "density", "force")},
+                              "groups": s.passes()}
+        s.close()
+    return out
 
 
 def surrogate_extra(torch, md, stream, barrier, max_over_ranks, world, path=SUR_WEIGHTS, md_steps=1000,
@@ -558,8 +591,10 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="mixed path only, no e2e/CPU/extra legs: a short run for ncu captures")
     ap.add_argument("--no-extras", action="store_true", help="skip the non-headline workloads")
-    ap.add_argument("--passes", choices=["auto", "list", "staged", "cells"], default="auto",
+    ap.add_argument("--passes", choices=["auto", "list", "staged", "cells", "half"], default="auto",
                     help="neighbour walk of the mixed-precision step kernel (md.h MD_PASSES_*)")
+    ap.add_argument("--lanes", type=int, default=0, choices=[0, 1, 2, 4, 8, 16, 32],
+                    help="lanes per atom (0: the autotuner's choice)")
     ap.add_argument("--surrogate-only", action="store_true",
                     help="run only the learned-surrogate comparison and print its record")
     ap.add_argument("--sur-weights", default=SUR_WEIGHTS, help="trained surrogate (.npz: theta, gmu, ginv)")

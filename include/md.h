@@ -122,42 +122,50 @@ typedef struct {
     int32_t lanes_per_atom; /* threads sharing one atom's neighbour sums in the force passes:
                                1, 2, 4, 8, 16 or 32, or 0 = chosen from the expected neighbour
                                count (see md_tune).  Results depend on it only in rounding. */
-    int32_t passes;         /* MD_PASSES_AUTO (0), MD_PASSES_LIST, MD_PASSES_STAGED or MD_PASSES_CELLS:
-                               how the mixed-precision step kernel walks the neighbours */
+    int32_t passes;         /* MD_PASSES_AUTO (0), MD_PASSES_LIST, MD_PASSES_STAGED, MD_PASSES_CELLS or
+                               MD_PASSES_HALF: how the mixed-precision step kernel walks the neighbours */
 } md_config;
 
 /*
  * Neighbour walk of the two EAM passes in the step kernel (md_step).  LIST: every atom reads
- * its neighbours' positions through the Verlet list (§3.2.1) from global memory.  STAGED: the
- * link cells are taken in groups of consecutive cells along x; one thread block copies a
- * group's neighbourhood (the 3 x 3 x (gx + 2) stencil of cells around it, each periodic image
- * already shifted) into shared memory, and the group's atoms read their neighbours there
- * through a 16-bit copy of their list rows (the same entries, as stencil slots).  The list, the
- * pair terms and their order are those of LIST; the neighbour separations are formed from the
- * shifted FP32 positions instead of by the FP32 minimum image, so results differ from LIST in
- * rounding only.  CELLS: the same staged neighbourhoods, and no Verlet list: each atom tests
- * every staged atom of the 27 cells around its own (the link-cell method alone, §3.2.1), so a
- * rebuild re-bins the atoms and builds no list; pairs closer than r_cut are the same set, summed
- * in another order.  After md_step a CELLS context's list is rebuilt when it is next needed
- * (md_eam_forces, md_get of the list).  STAGED and CELLS apply to mixed precision, one system
- * (no batch), one species with a knot table that fits in shared memory, no strain ramp, and 1-8
- * lanes per atom (more lanes walk LIST); a build at which some group's neighbourhood exceeds the
- * stage's capacity makes the passes take the LIST walk until the next build (CELLS then builds
- * the list).  AUTO = LIST (on GB300 both group walks measured slower for fcc Cu with its
- * 5,000-knot table in shared memory: one 1024-thread block per SM stages, then computes);
- * STAGED or CELLS where they do not apply is MD_ERR_ARG at md_create.
+ * its neighbours' positions through the full Verlet list (§3.2.1) from global memory, and every
+ * pair is computed twice (once for each atom: no write conflicts, the symmetric scheme of
+ * §3.2.2).  The three group walks take the link cells in groups of consecutive cells along x;
+ * one thread block copies a group's neighbourhood (the 3 x 3 x (gx + 2) stencil of cells around
+ * it, each periodic image already shifted) into shared memory and walks it there:
+ *  - STAGED: the group's atoms read their neighbours through a 16-bit copy of their list rows
+ *    (the same entries, as stencil slots).  The list, the pair terms and their order are those
+ *    of LIST; the separations are formed from the shifted FP32 positions instead of by the FP32
+ *    minimum image, so results differ from LIST in rounding only.
+ *  - CELLS: no Verlet list: each atom tests every staged atom of the 27 cells around its own
+ *    (the link-cell method alone, §3.2.1), so a rebuild re-bins the atoms and builds no list;
+ *    pairs closer than r_cut are the same set, summed in another order.  After md_step a CELLS
+ *    context's list is rebuilt when it is next needed (md_eam_forces, md_get of the list).
+ *  - HALF: a half list and Newton's third law (§3.2.2's half list): each pair is computed once,
+ *    by the atom with the lower cell-order slot, through 16-bit half rows of stage slots.  The
+ *    other atom's density, force and pair energy are summed in shared memory per stage slot,
+ *    then added to FP64 accumulators with atomic adds, so that sums are exact to FP32 rounding
+ *    per term but their order, and hence the last bits, varies from run to run.  Two light
+ *    phases follow the passes: F(rho) after the density pass, the kicks after the force pass.
+ * The group walks apply to mixed precision, one system (no batch), one species with a knot
+ * table that fits in shared memory, no strain ramp, and 1-8 lanes per atom (more lanes walk
+ * LIST); a build at which some group's neighbourhood exceeds the stage's capacity makes the
+ * passes take the LIST walk until the next build (CELLS then builds the list).  AUTO = LIST (on
+ * GB300 every group walk measured slower for fcc Cu with its 5,000-knot table in shared memory:
+ * one 1024-thread block per SM stages, then computes); a group walk where it does not apply is
+ * MD_ERR_ARG at md_create.
  */
-enum { MD_PASSES_AUTO = 0, MD_PASSES_LIST = 1, MD_PASSES_STAGED = 2, MD_PASSES_CELLS = 3 };
+enum { MD_PASSES_AUTO = 0, MD_PASSES_LIST = 1, MD_PASSES_STAGED = 2, MD_PASSES_CELLS = 3, MD_PASSES_HALF = 4 };
 
 typedef struct {
-    int32_t walk;            /* the walk prepared: MD_PASSES_STAGED or MD_PASSES_CELLS (cell
-                                groups at every build), else MD_PASSES_LIST */
+    int32_t walk;            /* the walk prepared: MD_PASSES_STAGED, MD_PASSES_CELLS or
+                                MD_PASSES_HALF (cell groups at every build), else MD_PASSES_LIST */
     int32_t cells_per_group; /* gx */
     int32_t groups;          /* number of cell groups */
     int32_t capacity;        /* atoms one block can stage */
     int32_t last_max;        /* largest group neighbourhood (atoms) at the last list build */
-    int32_t active;          /* 1: the next md_step walks STAGED or CELLS (prepared, lanes <= 8,
-                                and every group fitted at the last build) */
+    int32_t active;          /* 1: the next md_step takes the prepared group walk (lanes <= 8, and
+                                every group fitted at the last build) */
 } md_passes;
 
 typedef struct {

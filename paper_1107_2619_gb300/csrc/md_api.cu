@@ -147,7 +147,9 @@ void list_band(const md_ctx *c, float &lo, float &hi) {
     hi = std::nextafter((float)(c->rl2 + band), INFINITY);
 }
 
-// Lanes per link cell of the list build, from the mean cell occupancy.
+// Lanes per link cell of the list build, from the mean cell occupancy (a whole warp per cell
+// above 12 atoms: on GB300 the single broadcast candidate stream of a warp-wide group built the
+// fcc Cu list faster than 8-lane groups with fewer idle lanes, 1.29 against about 1.8 ms per build).
 int ph_list_group(const md_ctx *c) {
     const double m = c->C.ncell > 0 ? (double)c->n / (double)c->C.ncell : 0.0;
     return m <= 3.0 ? 4 : (m <= 6.0 ? 8 : (m <= 12.0 ? 16 : 32));
@@ -591,34 +593,39 @@ md_status create_common(md_ctx *ctx, const md_config *cfg, const md_potential *p
     chk(dalloc(ctx, &C.cell_count, C.ncell));
     chk(dalloc(ctx, &C.cell_start, C.ncell + 1));
     chk(dalloc(ctx, &C.tile_sums, C.ntiles + 1));
-    // staged and cell walks (MD_PASSES_STAGED, MD_PASSES_CELLS): groups of gx cells along x whose
-    // 3 x 3 x (gx + 2) neighbourhood fits the stage 30 % above the mean occupancy.  Staged walk:
-    // gx such that a group's home atoms fill whole rounds of a 1024-thread block at the context's
-    // lanes per atom (with a 10 % margin for the spread of cell occupancy), of nearly equal
-    // choices the larger; cell walk (a warp per atom): the largest gx (fewest stencil copies).
+    // group walks (MD_PASSES_STAGED, _CELLS, _HALF): groups of gx cells along x whose
+    // 3 x 3 x (gx + 2) neighbourhood fits the stage 15 % above the mean occupancy.  Staged and
+    // half walks: gx such that a group's home atoms fill whole rounds of a 1024-thread block at
+    // the context's lanes per atom (with a 10 % margin for the spread of cell occupancy), of
+    // nearly equal choices the larger; cell walk (a warp per atom): the largest gx (fewest
+    // stencil copies).
     {
         const size_t tbytes = pot->kind == MD_POT_TABLES ? smem_table_bytes(pot->kind, ns, cfg->precision, pot->n_knots)
                                                          : 0;
         const bool eligible = tbytes > 0 && n_rep == 1 && reach == 1 && !ctx->sur && cfg->strain_rate_zz == 0.0 &&
                               ctx->lanes <= 8 && n > 0;
-        const bool grouped = cfg->passes == MD_PASSES_STAGED || cfg->passes == MD_PASSES_CELLS;
+        const bool grouped =
+            cfg->passes == MD_PASSES_STAGED || cfg->passes == MD_PASSES_CELLS || cfg->passes == MD_PASSES_HALF;
         if (cfg->passes != MD_PASSES_AUTO && cfg->passes != MD_PASSES_LIST && !grouped) return MD_ERR_ARG;
         if (grouped && !eligible) {
-            ctx->err = "staged and cell walks need mixed precision, one system, one species with a knot table "
-                       "that fits in shared memory, no strain ramp and at most 8 lanes per atom";
+            ctx->err = "group walks need mixed precision, one system, one species with a knot table that fits "
+                       "in shared memory, no strain ramp and at most 8 lanes per atom";
             return MD_ERR_ARG;
         }
         C.tile = kWalkList;
         if (eligible && grouped) {
-            const int walk = cfg->passes == MD_PASSES_STAGED ? kWalkStaged : kWalkCells;
+            const int walk = cfg->passes == MD_PASSES_STAGED ? kWalkStaged
+                                                              : (cfg->passes == MD_PASSES_CELLS ? kWalkCells : kWalkHalf);
             const int nx = ctx->rc[0].nc[0];
             const double m = (double)n / (double)ncell;
             const size_t dyn_max = walk == kWalkCells ? kSmemDynMaxCells : kSmemDynMax;
-            const int cap = (int)std::min<size_t>((dyn_max - tbytes) / sizeof(float4), 65535);
+            // a stage slot holds a float4 position, and for the half walk a float4 of sums
+            const size_t slot = sizeof(float4) * (walk == kWalkHalf ? 2 : 1);
+            const int cap = (int)std::min<size_t>((dyn_max - tbytes) / slot, 65535);
             int best = 0;
             double best_eff = 0.0;
             for (int g = 1; g <= std::min(8, nx); g++) {
-                if (9.0 * (g + 2) * m * 1.3 > cap) break;
+                if (9.0 * (g + 2) * m * 1.15 > cap) break;
                 if (walk == kWalkCells) {
                     best = g;
                     continue;
@@ -638,9 +645,14 @@ md_status create_common(md_ctx *ctx, const md_config *cfg, const md_potential *p
                 C.st_cells = 9 * (best + 2);
                 C.cap = cap;
                 chk(dalloc(ctx, &C.grp_loc, (size_t)C.n_groups * (C.st_cells + 1)));
-                if (walk == kWalkStaged) chk(dalloc(ctx, &A.lnbr, nbr_entries(n, cfg->k_max)));
+                if (walk == kWalkStaged || walk == kWalkHalf) chk(dalloc(ctx, &A.lnbr, nbr_entries(n, cfg->k_max)));
+                if (walk == kWalkHalf) {
+                    chk(dalloc(ctx, &A.lcount, n));
+                    chk(dalloc(ctx, &A.rho_acc, n));
+                    chk(dalloc(ctx, &A.f_acc, n));
+                }
             } else {
-                ctx->err = "staged and cell walks: the link-cell occupancy is too high for the stage";
+                ctx->err = "group walks: the link-cell occupancy is too high for the stage";
                 return MD_ERR_ARG;
             }
         }
@@ -1392,7 +1404,10 @@ md_status md_get_passes(md_ctx *ctx, md_passes *out) {
     MD_CK(cudaMemcpyAsync(ctx->h_flags, ctx->d_flags, sizeof(Flags), cudaMemcpyDeviceToHost, ctx->stream));
     MD_CK(cudaStreamSynchronize(ctx->stream));
     const Cells &C = ctx->C;
-    out->walk = C.tile == kWalkStaged ? MD_PASSES_STAGED : (C.tile == kWalkCells ? MD_PASSES_CELLS : MD_PASSES_LIST);
+    out->walk = C.tile == kWalkStaged  ? MD_PASSES_STAGED
+                : C.tile == kWalkCells ? MD_PASSES_CELLS
+                : C.tile == kWalkHalf  ? MD_PASSES_HALF
+                                       : MD_PASSES_LIST;
     out->cells_per_group = C.tile ? C.gx : 0;
     out->groups = C.tile ? C.n_groups : 0;
     out->capacity = C.tile ? C.cap : 0;

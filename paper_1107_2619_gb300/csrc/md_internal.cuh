@@ -103,7 +103,11 @@ struct Atoms {
     int32_t *sorted;                         // order after the in-cell sort (aliases cell_of)
     int32_t *nbr, *count;                    // list entry k of atom i: see NbrRow; k < min(count, k_max)
     uint16_t *lnbr;                          // staged passes: the same entries as slots of the atom's
-                                             // cell-group stencil (same plane layout as nbr)
+                                             // cell-group stencil (same plane layout as nbr); half walk:
+                                             // only the entries j > i, lcount of them
+    int32_t *lcount;                         // half walk: entries of each half row
+    double *rho_acc;                         // half walk: density accumulators [n]
+    double4_32a *f_acc;                      // half walk: force (x, y, z) and pair-energy (w) accumulators
     double *partials;                        // [kPartials][part_stride] per-block sums
     int part_stride;
     int32_t *rep;                            // replica of each slot (NULL: one system)
@@ -144,14 +148,15 @@ struct Cells {
     // cells along x.  The neighbourhood of a group is its 3 x 3 x (gx + 2) stencil of cells; stencil
     // cell s = ((dz + 1) 3 + (dy + 1)) (gx + 2) + (x - x0 + 1) for the group starting at x0.
     int tile;           // walk of the step kernel's passes: kWalkList (no groups), kWalkStaged (groups
-                        // and 16-bit local lists), kWalkCells (groups, no list unless a group overflows)
+                        // and 16-bit local lists), kWalkCells (groups, no list unless a group overflows),
+                        // kWalkHalf (groups, 16-bit half lists, shared-memory accumulation)
     int gx, ngx, n_groups, st_cells;   // cells per group, groups per row, groups, 9 (gx + 2)
     int cap;            // atoms a block can stage
     int32_t *grp_loc;   // [n_groups][st_cells + 1]: staged slot of the first atom of each stencil cell, total
 };
 
 // Neighbour walks of the step kernel's passes (md_config.passes).
-enum : int { kWalkList = 0, kWalkStaged = 1, kWalkCells = 2 };
+enum : int { kWalkList = 0, kWalkStaged = 1, kWalkCells = 2, kWalkHalf = 3 };
 
 // Shared memory of the mixed-precision step kernel: a single-species knot table (2 float4 per
 // knot) of at most kSmemTableMax bytes, and the stage of the staged passes; together at most

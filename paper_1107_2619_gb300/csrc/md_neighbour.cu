@@ -89,13 +89,22 @@ __global__ void k_copyback(Atoms A) {
     for (long long k = gtid(); k < A.n; k += gstride()) ph::copyback_atom(A, A.boxes, (int)k);
 }
 
-template <int G, bool LOCAL>
+template <int G, int LOCAL>
 __global__ void __launch_bounds__(kThreads) k_build_list(Atoms A, Cells C, double rl2, float band_lo,
                                                          float band_hi) {
     if (!ph::rebuild_requested(A.flags)) return;
     int m = ph::build_cells<G, LOCAL>(A, C, A.boxes, gtid() >> 5, gstride() >> 5, threadIdx.x & 31, rl2, band_lo, band_hi);
     m = __reduce_max_sync(0xffffffffu, m);
     if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(&A.flags->max_count, m);
+}
+
+template <int LOCAL>
+void launch_build(const Atoms &A, const Cells &C, double rl2, float band_lo, float band_hi, int list_group, int nbl,
+                  cudaStream_t s) {
+    if (list_group == 4) k_build_list<4, LOCAL><<<nbl, kThreads, 0, s>>>(A, C, rl2, band_lo, band_hi);
+    else if (list_group == 8) k_build_list<8, LOCAL><<<nbl, kThreads, 0, s>>>(A, C, rl2, band_lo, band_hi);
+    else if (list_group == 16) k_build_list<16, LOCAL><<<nbl, kThreads, 0, s>>>(A, C, rl2, band_lo, band_hi);
+    else k_build_list<32, LOCAL><<<nbl, kThreads, 0, s>>>(A, C, rl2, band_lo, band_hi);
 }
 
 int capped_blocks(long long items, int threads) {
@@ -135,17 +144,9 @@ cudaError_t launch_rebuild(const Atoms &A, const Cells &C, double rl2, float ban
         k_gather<<<nb, kThreads, 0, s>>>(A);
         k_copyback<<<nb, kThreads, 0, s>>>(A);
         const int nbl = capped_blocks((long long)C.ncell * list_group, kThreads);
-        if (C.tile == kWalkStaged) {
-            if (list_group == 4) k_build_list<4, true><<<nbl, kThreads, 0, s>>>(A, C, rl2, band_lo, band_hi);
-            else if (list_group == 8) k_build_list<8, true><<<nbl, kThreads, 0, s>>>(A, C, rl2, band_lo, band_hi);
-            else if (list_group == 16) k_build_list<16, true><<<nbl, kThreads, 0, s>>>(A, C, rl2, band_lo, band_hi);
-            else k_build_list<32, true><<<nbl, kThreads, 0, s>>>(A, C, rl2, band_lo, band_hi);
-        } else {
-            if (list_group == 4) k_build_list<4, false><<<nbl, kThreads, 0, s>>>(A, C, rl2, band_lo, band_hi);
-            else if (list_group == 8) k_build_list<8, false><<<nbl, kThreads, 0, s>>>(A, C, rl2, band_lo, band_hi);
-            else if (list_group == 16) k_build_list<16, false><<<nbl, kThreads, 0, s>>>(A, C, rl2, band_lo, band_hi);
-            else k_build_list<32, false><<<nbl, kThreads, 0, s>>>(A, C, rl2, band_lo, band_hi);
-        }
+        if (C.tile == kWalkStaged) launch_build<1>(A, C, rl2, band_lo, band_hi, list_group, nbl, s);
+        else if (C.tile == kWalkHalf) launch_build<2>(A, C, rl2, band_lo, band_hi, list_group, nbl, s);
+        else launch_build<0>(A, C, rl2, band_lo, band_hi, list_group, nbl, s);
     }
     return cudaGetLastError();
 }

@@ -37,12 +37,14 @@ __device__ __forceinline__ float4 phi_half32(const double4_32a *tab, size_t idx)
 }
 
 // The same rows from a copy of the table in the kernel's dynamic shared memory (SMT: one
-// species; row k = float4 V coefficients, float4 phi coefficients).
+// species).  The copy is split: the nk float4 rows of V coefficients, then the nk rows of phi
+// coefficients, so that the rows a warp reads at random spread over all eight 16-byte bank
+// groups (interleaved V/phi rows would put every phi row in four of them).
 template <bool SMT>
 __device__ __forceinline__ float4 phi_row(const Pot &P, size_t idx) {
     if (SMT) {
         extern __shared__ float4 sm_table_f4[];
-        return sm_table_f4[2 * idx + 1];
+        return sm_table_f4[P.nk + idx];
     }
     return phi_half32(P.VP32, idx);
 }
@@ -51,7 +53,7 @@ template <bool SMT>
 __device__ __forceinline__ void vp_row(const Pot &P, size_t idx, float (&v)[4], float (&p)[4]) {
     if (SMT) {
         extern __shared__ float4 sm_table_f4[];
-        const float4 a = sm_table_f4[2 * idx], b = sm_table_f4[2 * idx + 1];
+        const float4 a = sm_table_f4[idx], b = sm_table_f4[P.nk + idx];
         v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
         p[0] = b.x; p[1] = b.y; p[2] = b.z; p[3] = b.w;
         return;
@@ -91,17 +93,15 @@ struct Acc32 {
     float wxx = 0.f, wyy = 0.f, wzz = 0.f, wyz = 0.f, wxz = 0.f, wxy = 0.f;
 };
 
-// One pair of the force pass: V'(r) + F'_i phi'_{s_i s_j}(r) + F'_j phi'_{s_j s_i}(r) along
-// d = (dx, dy, dz) = r_j - r_i (zero at or beyond r_cut, without a branch), and on the energy
-// step V(r)/2 and the virial -d (x) f / 2.
-template <int KIND, bool MULTI, bool ENERGY, bool SMT>
-__device__ __forceinline__ void pair32(const Pot &P, int si, int sj, float Fpi, float Fpj, float dx, float dy,
-                                       float dz, Acc32 &a, unsigned &viol) {
-    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+// The scalar of one pair of the force pass: g = [V'(r) + F'_i phi'_{s_i s_j}(r) + F'_j phi'_{s_j s_i}(r)] / r
+// (the force on i is g d, d = r_j - r_i) and V(r), both zero at or beyond r_cut (no branch).
+template <int KIND, bool MULTI, bool SMT>
+__device__ __forceinline__ float pair_g32(const Pot &P, int si, int sj, float Fpi, float Fpj, float r2, float &V,
+                                          unsigned &viol) {
     const bool inside = r2 < P.rc2f;
     const float rinv = rsqrtf(r2);
     const float r = r2 * rinv;
-    float V, gg;
+    float gg;
     if (KIND == MD_POT_FS_ANALYTIC) {
         float dV;
         V = fs_V<float>(P.fsf, r, dV);
@@ -138,12 +138,22 @@ __device__ __forceinline__ void pair32(const Pot &P, int si, int sj, float Fpi, 
         }
         gg = gk * P.inv_drf;
     }
-    const float gr = inside ? gg * rinv : 0.f;
+    V = inside ? V : 0.f;
+    return inside ? gg * rinv : 0.f;
+}
+
+// One pair of the force pass along d = (dx, dy, dz) = r_j - r_i, added to atom i's sums: the
+// force g d, and on the energy step V(r)/2 and the virial -g d (x) d / 2.
+template <int KIND, bool MULTI, bool ENERGY, bool SMT>
+__device__ __forceinline__ void pair32(const Pot &P, int si, int sj, float Fpi, float Fpj, float dx, float dy,
+                                       float dz, Acc32 &a, unsigned &viol) {
+    float V;
+    const float gr = pair_g32<KIND, MULTI, SMT>(P, si, sj, Fpi, Fpj, fmaf(dx, dx, fmaf(dy, dy, dz * dz)), V, viol);
     a.fx = fmaf(gr, dx, a.fx);
     a.fy = fmaf(gr, dy, a.fy);
     a.fz = fmaf(gr, dz, a.fz);
     if (ENERGY) {
-        a.ep = fmaf(0.5f, inside ? V : 0.f, a.ep);
+        a.ep = fmaf(0.5f, V, a.ep);
         const float hg = -0.5f * gr;
         a.wxx = fmaf(hg * dx, dx, a.wxx);
         a.wyy = fmaf(hg * dy, dy, a.wyy);

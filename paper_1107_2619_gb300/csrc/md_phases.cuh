@@ -300,10 +300,11 @@ static __device__ __noinline__ bool within_exact_band(const double4_32a &pi, con
 // FP64 set, listed by cell in (dz, dy, dx) order and by ascending slot inside a cell.  Rows are cut
 // at k_max (the count is kept).  Returns the longest row of this lane's atoms.  The stencil of
 // +-reach cells along each edge needs >= 2 reach + 1 cells per edge (no cell visited twice).
-// LOCAL (staged passes, one system, reach 1): every entry is also written to the 16-bit local
+// LOCAL (group walks, one system, reach 1): 1, every entry is also written to the 16-bit local
 // list as the slot of the candidate in its cell group's stage (grp_loc of the stencil cell plus
-// the candidate's rank inside its cell).
-template <int G, bool LOCAL>
+// the candidate's rank inside its cell); 2, only the entries j > i are, as the half row of the
+// half walk (lcount of them).
+template <int G, int LOCAL>
 __device__ __forceinline__ int build_cell_group(const Atoms &A, const Cells &C, const Box *boxes, int c, int gl,
                                                 double rl2, float band_lo, float band_hi) {
     const int s = C.cell_start[c], e = C.cell_start[c + 1];
@@ -327,7 +328,7 @@ __device__ __forceinline__ int build_cell_group(const Atoms &A, const Cells &C, 
         const float4 fi = A.posf[ii];
         int32_t *wp = A.nbr + 4 * (size_t)ii;   // entry cnt of the row (planes of 4 entries)
         uint16_t *lwp = LOCAL ? A.lnbr + 4 * (size_t)ii : nullptr;   // the same entry of the local list
-        int cnt = 0;
+        int cnt = 0, lcnt = 0;
         int lbase = 0;   // staged slot of the first atom of the current candidate cell (local list)
         // one candidate: append j to the row if it is a neighbour
         auto visit = [&](int j, int js, float r2) {
@@ -336,12 +337,19 @@ __device__ __forceinline__ int build_cell_group(const Atoms &A, const Cells &C, 
                 if (in && act && j != i) {
                     if (cnt < kmax) {
                         *wp = j;
-                        if constexpr (LOCAL) *lwp = (uint16_t)(lbase + (j - js));
+                        if constexpr (LOCAL == 1) *lwp = (uint16_t)(lbase + (j - js));
+                        if constexpr (LOCAL == 2) {
+                            if (j > i) {
+                                *lwp = (uint16_t)(lbase + (j - js));
+                                lcnt++;
+                                lwp += (lcnt & 3) ? 1 : plane - 3;
+                            }
+                        }
                     }
                     cnt++;
                     const long long adv = (cnt & 3) ? 1 : plane - 3;
                     wp += adv;
-                    if constexpr (LOCAL) lwp += adv;
+                    if constexpr (LOCAL == 1) lwp += adv;
                 }
             }
         };
@@ -393,6 +401,7 @@ __device__ __forceinline__ int build_cell_group(const Atoms &A, const Cells &C, 
         }
         if (act) {
             A.count[i] = cnt;
+            if constexpr (LOCAL == 2) A.lcount[i] = lcnt;
             if (cnt > kmax) atomicOr(&A.flags->error, FLAG_OVERFLOW);
             longest = max(longest, cnt);
         }
@@ -402,7 +411,7 @@ __device__ __forceinline__ int build_cell_group(const Atoms &A, const Cells &C, 
 
 // The list phase over all cells: warp w of nwarps takes cell groups w, w + nwarps, ...; every
 // lane returns the longest row it built (all 32 lanes of a warp take part in every iteration).
-template <int G, bool LOCAL>
+template <int G, int LOCAL>
 __device__ __forceinline__ int build_cells(const Atoms &A, const Cells &C, const Box *boxes, long long warp,
                                            long long nwarps, int lane, double rl2, float band_lo, float band_hi) {
     constexpr int CPW = 32 / G;   // cells per warp
@@ -414,7 +423,7 @@ __device__ __forceinline__ int build_cells(const Atoms &A, const Cells &C, const
     return m;
 }
 
-template <bool LOCAL>
+template <int LOCAL>
 __device__ __forceinline__ int build_cells_any(int G, const Atoms &A, const Cells &C, const Box *boxes, long long warp,
                                                long long nwarps, int lane, double rl2, float band_lo, float band_hi) {
     if (G == 4) return build_cells<4, LOCAL>(A, C, boxes, warp, nwarps, lane, rl2, band_lo, band_hi);

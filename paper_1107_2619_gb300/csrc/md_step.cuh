@@ -126,10 +126,11 @@ __device__ __forceinline__ void thermo_update(const StepParams &sp, int n_rep, l
 
 // NT threads per block.  SMT: the single-species knot table is copied into dynamic shared
 // memory at the start of the launch and the passes read it there (one 1024-thread block per SM).
-// WALK (kWalkStaged, kWalkCells): the passes run over cell groups staged in shared memory
-// (md_tile.cuh) whenever every group's neighbourhood fitted the stage at the last build, else
-// over atoms through the list.  The cell walk builds no list at a rebuild unless a group did not
-// fit (the list walk then needs one).
+// WALK (kWalkStaged, kWalkCells, kWalkHalf): the passes run over cell groups staged in shared
+// memory (md_tile.cuh) whenever every group's neighbourhood fitted the stage at the last build,
+// else over atoms through the list.  The cell walk builds no list at a rebuild unless a group
+// did not fit (the list walk then needs one).  The half walk adds two phases: F(rho) after the
+// density pass and the kicks after the force pass (each waits for every group's shares).
 template <int PREC, int T, int KIND, bool MULTI, int NT, bool SMT, int WALK>
 __global__ void __launch_bounds__(NT, NT == kThreads ? MD_STEP_MIN_BLOCKS : 1)
     k_step(Atoms A, Cells C, Pot P, StepParams sp, GridBarrier *bar, unsigned long long *stamps) {
@@ -138,12 +139,13 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? MD_STEP_MIN_BLOCKS : 1)
     __shared__ uint16_t cells_q[WALK == kWalkCells ? NT / 32 : 1][kCellsQueue];
     extern __shared__ float4 sm_table_f4[];   // [SMT table][stage]
     float4 *const stage = sm_table_f4 + (SMT ? 2 * P.nk : 0);
+    float4 *const half_acc = stage + (WALK == kWalkHalf ? C.cap : 0);   // half walk: per-slot sums
     const unsigned nb = gridDim.x;
     const long long tid = (long long)blockIdx.x * NT + threadIdx.x;
     const long long stride = (long long)nb * NT;
     if (SMT) {
         const float4 *src = reinterpret_cast<const float4 *>(P.VP32);
-        for (int q = threadIdx.x; q < 2 * P.nk; q += NT) sm_table_f4[q] = __ldg(src + q);
+        for (int q = threadIdx.x; q < 2 * P.nk; q += NT) sm_table_f4[(q & 1) * P.nk + (q >> 1)] = __ldg(src + q);
         __syncthreads();
     }
     const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
@@ -171,9 +173,11 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? MD_STEP_MIN_BLOCKS : 1)
         thermo_update(sp, A.n_rep, tid, stride, false, true);
         MD_SYNC();
     }
-    for (long long i = tid; i < A.n; i += stride)
+    for (long long i = tid; i < A.n; i += stride) {
         ph::kick_drift(A, boxes, (int)i, sp.half_dt, sp.dt, sp.strain_scale, strain, sp.lim2,
                        thermo ? sp.thermo : nullptr);
+        if constexpr (WALK == kWalkHalf) A.rho_acc[i] = 0.0;
+    }
     if (sp.withhold_arrival && blockIdx.x == 0) {
         // self-test of the bounded wait: this block never arrives; it waits (bounded) until
         // the others have given up and marked the launch aborted, then leaves.
@@ -235,7 +239,7 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? MD_STEP_MIN_BLOCKS : 1)
             MD_SYNC();
             MD_STAMP(8);
             if (WALK != kWalkCells || *reinterpret_cast<volatile int32_t *>(&A.flags->tile_bad)) {
-                int m = ph::build_cells_any<WALK == kWalkStaged>(sp.list_group, A, C, boxes, tid >> 5, stride >> 5,
+                int m = ph::build_cells_any<WALK == kWalkStaged ? 1 : (WALK == kWalkHalf ? 2 : 0)>(sp.list_group, A, C, boxes, tid >> 5, stride >> 5,
                                                                  threadIdx.x & 31, sp.rl2, sp.band_lo, sp.band_hi);
                 m = __reduce_max_sync(0xffffffffu, m);
                 if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(&A.flags->max_count, m);
@@ -256,14 +260,25 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? MD_STEP_MIN_BLOCKS : 1)
         if constexpr (WALK != kWalkList) {
             if (tiled) {
                 for (int g = blockIdx.x; g < C.n_groups; g += nb) {
-                    const tl::Group G = tl::stage_group<NT>(C, boxes[0], A.posf, g, stage, tile_loc);
+                    const tl::Group G = tl::stage_group<NT>(C, boxes[0], A.posf, g, stage, tile_loc,
+                                                            WALK == kWalkHalf ? half_acc : nullptr);
                     if constexpr (WALK == kWalkStaged) {
                         const int gi = ((G.h1 - G.h0) * T + 31) & ~31;
                         for (int it = threadIdx.x; it < gi; it += NT)
                             tl::density_item<T, KIND, SMT>(A, P, stage, G.h1, G.h0 + it / T, it & (T - 1));
                     } else if constexpr (WALK == kWalkCells) {
                         tl::density_cells<NT, KIND, SMT>(A, P, stage, tile_loc, C.gx + 2, G, cells_q[threadIdx.x >> 5]);
+                    } else if constexpr (WALK == kWalkHalf) {
+                        const int gi = ((G.h1 - G.h0) * T + 31) & ~31;
+                        for (int it = threadIdx.x; it < gi; it += NT)
+                            tl::density_half_item<T, KIND, SMT>(A, P, stage, half_acc, G.h1, G.h0 + it / T,
+                                                                it & (T - 1));
+                        tl::flush_group<NT, false>(A, C, boxes[0], g, half_acc, tile_loc);
                     }
+                }
+                if constexpr (WALK == kWalkHalf) {   // F(rho) once every group has added its share
+                    MD_SYNC();
+                    for (long long i = tid; i < A.n; i += stride) tl::half_embed(A, P, (int)i);
                 }
             }
         }
@@ -283,7 +298,8 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? MD_STEP_MIN_BLOCKS : 1)
             if constexpr (WALK != kWalkList) {
                 if (tiled) {
                     for (int g = blockIdx.x; g < C.n_groups; g += nb) {
-                        const tl::Group G = tl::stage_group<NT>(C, boxes[0], A.p2f, g, stage, tile_loc);
+                        const tl::Group G = tl::stage_group<NT>(C, boxes[0], A.p2f, g, stage, tile_loc,
+                                                                WALK == kWalkHalf ? half_acc : nullptr);
                         if constexpr (WALK == kWalkStaged) {
                             const int gi = ((G.h1 - G.h0) * T + 31) & ~31;
                             for (int it = threadIdx.x; it < gi; it += NT)
@@ -293,7 +309,17 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? MD_STEP_MIN_BLOCKS : 1)
                             tl::force_cells<NT, KIND, true, SMT>(A, P, boxes, stage, tile_loc, C.gx + 2, G,
                                                                  cells_q[threadIdx.x >> 5], sp.half_dt, sp.dt, sp.lim2,
                                                                  false, part);
+                        } else if constexpr (WALK == kWalkHalf) {
+                            const int gi = ((G.h1 - G.h0) * T + 31) & ~31;
+                            for (int it = threadIdx.x; it < gi; it += NT)
+                                tl::force_half_item<T, KIND, true, SMT>(A, P, stage, half_acc, G.h1, G.h0 + it / T,
+                                                                        it & (T - 1), part);
+                            tl::flush_group<NT, true>(A, C, boxes[0], g, half_acc, tile_loc);
                         }
+                    }
+                    if constexpr (WALK == kWalkHalf) {   // the kick once every group has added its share
+                        MD_SYNC();
+                        for (long long i = tid; i < A.n; i += stride) tl::half_kick<true>(A, (int)i, sp.half_dt, part);
                     }
                 }
             }
@@ -305,7 +331,8 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? MD_STEP_MIN_BLOCKS : 1)
             if constexpr (WALK != kWalkList) {
                 if (tiled) {
                     for (int g = blockIdx.x; g < C.n_groups; g += nb) {
-                        const tl::Group G = tl::stage_group<NT>(C, boxes[0], A.p2f, g, stage, tile_loc);
+                        const tl::Group G = tl::stage_group<NT>(C, boxes[0], A.p2f, g, stage, tile_loc,
+                                                                WALK == kWalkHalf ? half_acc : nullptr);
                         if constexpr (WALK == kWalkStaged) {
                             const int gi = ((G.h1 - G.h0) * T + 31) & ~31;
                             for (int it = threadIdx.x; it < gi; it += NT) {
@@ -318,6 +345,19 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? MD_STEP_MIN_BLOCKS : 1)
                             tl::force_cells<NT, KIND, false, SMT>(A, P, boxes, stage, tile_loc, C.gx + 2, G,
                                                                   cells_q[threadIdx.x >> 5], sp.half_dt, sp.dt, sp.lim2,
                                                                   fuse, part);
+                        } else if constexpr (WALK == kWalkHalf) {
+                            const int gi = ((G.h1 - G.h0) * T + 31) & ~31;
+                            for (int it = threadIdx.x; it < gi; it += NT)
+                                tl::force_half_item<T, KIND, false, SMT>(A, P, stage, half_acc, G.h1, G.h0 + it / T,
+                                                                         it & (T - 1), part);
+                            tl::flush_group<NT, true>(A, C, boxes[0], g, half_acc, tile_loc);
+                        }
+                    }
+                    if constexpr (WALK == kWalkHalf) {   // the kicks once every group has added its share
+                        MD_SYNC();
+                        for (long long i = tid; i < A.n; i += stride) {
+                            tl::half_kick<false>(A, (int)i, sp.half_dt, part);
+                            if (fuse) ph::kick_drift(A, boxes, (int)i, sp.half_dt, sp.dt, sp.strain_scale, false, sp.lim2);
                         }
                     }
                 }
@@ -381,7 +421,8 @@ cudaError_t launch_t(const Atoms &A, const Cells &C, const Pot &P, const StepPar
     static size_t per_sm_dyn = 0;
     static bool attr = false;
     const size_t dyn_max = WALK == kWalkCells ? kSmemDynMaxCells : kSmemDynMax;
-    const size_t dyn = (SMT ? (size_t)P.nk * 32 : 0) + (WALK ? (size_t)C.cap * sizeof(float4) : 0);
+    const size_t dyn = (SMT ? (size_t)P.nk * 32 : 0) +
+                       (WALK ? (size_t)C.cap * sizeof(float4) * (WALK == kWalkHalf ? 2 : 1) : 0);
     if (dyn > dyn_max) return cudaErrorInvalidConfiguration;
     if ((SMT || WALK) && !attr) {  // opt in to a large dynamic shared-memory carve-out (once)
         cudaError_t e = cudaFuncSetAttribute(k_step<PREC, T, KIND, MULTI, NT, SMT, WALK>,
@@ -433,6 +474,9 @@ cudaError_t launch_kind(const Atoms &A, const Cells &C, const Pot &P, const Step
                 if (C.tile == kWalkCells)
                     return launch_t<PREC, T, MD_POT_TABLES, false, 1024, true, kWalkCells>(A, C, P, sp, bar, stamps,
                                                                                           grid_out, s);
+                if (C.tile == kWalkHalf)
+                    return launch_t<PREC, T, MD_POT_TABLES, false, 1024, true, kWalkHalf>(A, C, P, sp, bar, stamps,
+                                                                                         grid_out, s);
             }
             return launch_t<PREC, T, MD_POT_TABLES, false, 1024, true>(A, C, P, sp, bar, stamps, grid_out, s);
         }

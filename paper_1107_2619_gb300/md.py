@@ -54,8 +54,9 @@ class md_config(C.Structure):
                 ("stream", C.c_void_p), ("lanes_per_atom", C.c_int32), ("passes", C.c_int32)]
 
 
-MD_PASSES_AUTO, MD_PASSES_LIST, MD_PASSES_STAGED, MD_PASSES_CELLS = 0, 1, 2, 3
-PASSES = {"auto": MD_PASSES_AUTO, "list": MD_PASSES_LIST, "staged": MD_PASSES_STAGED, "cells": MD_PASSES_CELLS}
+MD_PASSES_AUTO, MD_PASSES_LIST, MD_PASSES_STAGED, MD_PASSES_CELLS, MD_PASSES_HALF = 0, 1, 2, 3, 4
+PASSES = {"auto": MD_PASSES_AUTO, "list": MD_PASSES_LIST, "staged": MD_PASSES_STAGED, "cells": MD_PASSES_CELLS,
+          "half": MD_PASSES_HALF}
 WALKS = {v: k for k, v in PASSES.items()}
 
 
@@ -491,7 +492,7 @@ class System:
         return md_get_profile(self.ctx)
 
     def passes(self) -> dict:
-        """The step kernel's neighbour walk: walk ("list", "staged" or "cells": the walk prepared),
+        """The step kernel's neighbour walk: walk ("list", "staged", "cells" or "half": the walk prepared),
         cells_per_group, groups, capacity, last_max (largest group neighbourhood at the last
         build), active (the next md_step walks the prepared groups)."""
         return md_get_passes(self.ctx)

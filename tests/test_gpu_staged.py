@@ -1,9 +1,12 @@
-"""Group walks of the mixed-precision step kernel (MD_PASSES_STAGED, MD_PASSES_CELLS) against
-the FP64 oracle.
+"""Group walks of the mixed-precision step kernel (MD_PASSES_STAGED, MD_PASSES_CELLS,
+MD_PASSES_HALF) against the FP64 oracle.
 
-Both walks read each atom's neighbours from a shared-memory copy of its cell group's
+The walks read each atom's neighbours from a shared-memory copy of its cell group's
 neighbourhood: the staged walk through a 16-bit copy of its list row, the cell walk (no Verlet
-list) by testing every staged atom of the 27 cells around its own.  A wrong local index, a
+list) by testing every staged atom of the 27 cells around its own, the half walk through the
+half row (j > i) with the neighbour's share summed per stage slot (Newton's third law); a pair
+missed or counted twice by the half walk, or a share added to the wrong slot, breaks the force
+and energy parity as surely as a wrong position.  A wrong local index, a
 missed periodic shift, a stencil cell staged from the wrong place or a candidate range off by a
 cell changes a force by far more than the mixed bound, so element-wise force parity at the final
 positions of a trajectory checks the staging, the local lists written by both list builds (the
@@ -62,7 +65,7 @@ def _case(name):
 
 
 @pytest.mark.parametrize("walk,lanes", [("staged", 1), ("staged", 2), ("staged", 4), ("staged", 8),
-                                        ("cells", 1), ("cells", 4)])
+                                        ("cells", 1), ("cells", 4), ("half", 1), ("half", 4), ("half", 8)])
 @pytest.mark.parametrize("case", ["cu7", "cu10", "cu_rect"])
 def test_group_walk_steps_match_the_oracle(case, walk, lanes):
     w = _case(case)
@@ -83,7 +86,7 @@ def test_group_walk_steps_match_the_oracle(case, walk, lanes):
     assert np.abs(f - fr).max() <= mixed_force_bound(w, np.abs(fr).max())
 
 
-@pytest.mark.parametrize("walk", ["staged", "cells"])
+@pytest.mark.parametrize("walk", ["staged", "cells", "half"])
 def test_group_walk_rebuild_phases_inside_the_step_kernel(walk):
     """Rebuilds every 3 steps: the group slot tables (and local lists) of the step kernel's own
     rebuild phases, then steps that use them; after the cell walk's list-free rebuilds the list
@@ -106,7 +109,7 @@ def test_group_walk_rebuild_phases_inside_the_step_kernel(walk):
         assert np.array_equal(counts, ref_counts)
 
 
-@pytest.mark.parametrize("walk", ["staged", "cells"])
+@pytest.mark.parametrize("walk", ["staged", "cells", "half"])
 def test_group_and_list_walks_differ_in_rounding_only(walk):
     w = _case("cu_rect")
     with md.System(w, precision="mixed", lanes_per_atom=4, passes=walk) as a, \
@@ -129,7 +132,7 @@ def test_auto_takes_the_list_walk():
         assert p["walk"] == "list" and p["active"] == 0
 
 
-@pytest.mark.parametrize("walk", ["staged", "cells"])
+@pytest.mark.parametrize("walk", ["staged", "cells", "half"])
 @pytest.mark.parametrize("precision,name", [("fp64", "cu7"), ("mixed", "fe")])
 def test_group_walk_where_it_does_not_apply_is_an_argument_error(precision, name, walk):
     w = _case("cu7") if name == "cu7" else I.bcc_fe(8, seed=3)
@@ -138,7 +141,7 @@ def test_group_walk_where_it_does_not_apply_is_an_argument_error(precision, name
     assert ex.value.status == md.MD_ERR_ARG
 
 
-@pytest.mark.parametrize("walk", ["staged", "cells"])
+@pytest.mark.parametrize("walk", ["staged", "cells", "half"])
 def test_overfull_group_falls_back_to_the_list_walk_and_back(walk):
     """Squeeze the crystal into half of the box along y (twice the density): the groups whose
     3-cell-high neighbourhood lies inside the dense half hold about twice the atoms the stage
