@@ -136,6 +136,22 @@ struct NbrRow16 {
 __host__ __device__ inline NbrRow16 lnbr_row(const Atoms &A, int i) {
     return NbrRow16{A.lnbr + 4 * (size_t)i, 4LL * A.n};
 }
+// Load of per-atom data that the persistent step kernel itself writes in an earlier phase
+// (positions, pass-2 copies, list rows, species: written before a grid barrier, read after it).
+// The read-only data path (ld.global.nc) is defined only for data no thread writes during the
+// launch, so these are ordinary global loads; MD_LDG_PHASED=1 at build time takes the read-only
+// path instead (for comparison).
+#ifndef MD_LDG_PHASED
+#define MD_LDG_PHASED 0
+#endif
+template <typename T>
+__device__ __forceinline__ T ld_phase(const T *p) {
+#if MD_LDG_PHASED
+    return __ldg(p);
+#else
+    return *p;
+#endif
+}
 inline size_t nbr_entries(int64_t n, int k_max) { return (size_t)((k_max + 3) / 4) * 4 * (size_t)n; }
 
 struct Cells {

@@ -62,6 +62,12 @@ __device__ __forceinline__ void vp_row(const Pot &P, size_t idx, float (&v)[4], 
 }
 
 // ======================================================================= mixed precision
+// List entries between r_cut and r_list (the skin shell, about a tenth of a Cu row) contribute
+// nothing; MD_TABLE_SKIP=1 skips their table-row loads (the loads are predicated, the
+// arithmetic is not).
+#ifndef MD_TABLE_SKIP
+#define MD_TABLE_SKIP 1
+#endif
 // phi_{s_i s_j}(r) of one pair at separation d = (dx, dy, dz); 0 at or beyond r_cut (no branch,
 // so the loads of the next pair can issue early).  viol counts table lookups below r_min.
 template <int KIND, bool MULTI, bool SMT>
@@ -81,7 +87,8 @@ __device__ __forceinline__ float rho_term32(const Pot &P, int si, int sj, float 
         bool below;
         const int kr = knot_row((r - P.r_minf) * P.inv_drf, P.nk, t, below);
         viol += (below && inside) ? 1u : 0u;
-        const float4 c = phi_row<SMT>(P, (size_t)(si * P.ns + sj) * P.nk + kr);
+        float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (!MD_TABLE_SKIP || inside) c = phi_row<SMT>(P, (size_t)(si * P.ns + sj) * P.nk + kr);
         phi = cubic(t, c.x, c.y, c.z, c.w, below, d);
     }
     return inside ? phi : 0.f;
@@ -123,8 +130,8 @@ __device__ __forceinline__ float pair_g32(const Pot &P, int si, int sj, float Fp
         bool below;
         const int kr = knot_row((r - P.r_minf) * P.inv_drf, P.nk, t, below);
         viol += (below && inside) ? 1u : 0u;
-        float cv[4], cp[4], dVk, dab;
-        vp_row<SMT>(P, (size_t)(si * P.ns + sj) * P.nk + kr, cv, cp);
+        float cv[4] = {0.f, 0.f, 0.f, 0.f}, cp[4] = {0.f, 0.f, 0.f, 0.f}, dVk, dab;
+        if (!MD_TABLE_SKIP || inside) vp_row<SMT>(P, (size_t)(si * P.ns + sj) * P.nk + kr, cv, cp);
         V = cubic(t, cv[0], cv[1], cv[2], cv[3], below, dVk);
         cubic(t, cp[0], cp[1], cp[2], cp[3], below, dab);
         float gk;
@@ -234,12 +241,12 @@ __device__ __forceinline__ void density32_item(const Atoms &A, const Pot &P, con
         // two neighbours per iteration, software-pipelined: the positions of the next iteration
         // and the list entries of the one after are loaded before this iteration's terms are
         // computed, so the dependent loads of one neighbour overlap the arithmetic of others
-        auto entry = [&](int q) { return q < cnt ? __ldg(row.ptr(q)) : i; };
+        auto entry = [&](int q) { return q < cnt ? ld_phase(row.ptr(q)) : i; };
         int k = lane;
-        float4 p0 = __ldg(A.posf + entry(k)), p1 = __ldg(A.posf + entry(k + T));
+        float4 p0 = ld_phase(A.posf + entry(k)), p1 = ld_phase(A.posf + entry(k + T));
         int n0 = entry(k + 2 * T), n1 = entry(k + 3 * T);
         for (; k + T < cnt; k += 2 * T) {
-            const float4 q0 = __ldg(A.posf + n0), q1 = __ldg(A.posf + n1);
+            const float4 q0 = ld_phase(A.posf + n0), q1 = ld_phase(A.posf + n1);
             n0 = entry(k + 4 * T);
             n1 = entry(k + 5 * T);
             const float a0 = term(p0), a1 = term(p1);
@@ -272,23 +279,23 @@ __device__ __forceinline__ int force32_item(const Atoms &A, const Pot &P, const 
         const NbrRow row = nbr_row(A, i);
         unsigned viol = 0;
         auto pair = [&](int j, const float4 &pj) {
-            pair32<KIND, MULTI, ENERGY, SMT>(P, si, MULTI ? __ldg(A.spec + j) : 0, pi.w, pj.w,
+            pair32<KIND, MULTI, ENERGY, SMT>(P, si, MULTI ? ld_phase(A.spec + j) : 0, pi.w, pj.w,
                                              mi32(pj.x - pi.x, Lx, ix), mi32(pj.y - pi.y, Ly, iy),
                                              mi32(pj.z - pi.z, Lz, iz), a, viol);
         };
         // two neighbours per iteration; the list entries of the next iteration are loaded before
         // this iteration's positions are used (one dependent load less on the critical path)
         int k = lane;
-        int j0 = k < cnt ? __ldg(row.ptr(k)) : 0, j1 = k + T < cnt ? __ldg(row.ptr(k + T)) : 0;
+        int j0 = k < cnt ? ld_phase(row.ptr(k)) : 0, j1 = k + T < cnt ? ld_phase(row.ptr(k + T)) : 0;
         for (; k + T < cnt; k += 2 * T) {
-            const float4 p0 = __ldg(A.p2f + j0), p1 = __ldg(A.p2f + j1);
+            const float4 p0 = ld_phase(A.p2f + j0), p1 = ld_phase(A.p2f + j1);
             const int ja = j0, jb = j1, kn = k + 2 * T;
-            j0 = kn < cnt ? __ldg(row.ptr(kn)) : 0;
-            j1 = kn + T < cnt ? __ldg(row.ptr(kn + T)) : 0;
+            j0 = kn < cnt ? ld_phase(row.ptr(kn)) : 0;
+            j1 = kn + T < cnt ? ld_phase(row.ptr(kn + T)) : 0;
             pair(ja, p0);
             pair(jb, p1);
         }
-        if (k < cnt) pair(j0, __ldg(A.p2f + j0));
+        if (k < cnt) pair(j0, ld_phase(A.p2f + j0));
         if (viol) atomicAdd(&A.flags->range_violations, (unsigned long long)viol);
     }
     lane_sum_acc<T, ENERGY>(a);
@@ -312,7 +319,7 @@ __device__ __forceinline__ void density64_item(const Atoms &A, const Pot &P, con
         const int cnt = min(A.count[i], A.k_max);
         const NbrRow row = nbr_row(A, i);
         for (int k = lane; k < cnt; k += T) {
-            const int j = __ldg(row.ptr(k));
+            const int j = ld_phase(row.ptr(k));
             const double4_32a pj = A.pos[j];
             const double dx = mi64(pj.x - pi.x, B.L[0], B.invL[0]);
             const double dy = mi64(pj.y - pi.y, B.L[1], B.invL[1]);
@@ -363,7 +370,7 @@ __device__ __forceinline__ int force64_item(const Atoms &A, const Pot &P, const 
         const int cnt = min(A.count[i], A.k_max);
         const NbrRow row = nbr_row(A, i);
         for (int k = lane; k < cnt; k += T) {
-            const int j = __ldg(row.ptr(k));
+            const int j = ld_phase(row.ptr(k));
             const double4_32a pj = A.p2d[j];
             const double dx = mi64(pj.x - pi.x, B.L[0], B.invL[0]);
             const double dy = mi64(pj.y - pi.y, B.L[1], B.invL[1]);
@@ -379,7 +386,7 @@ __device__ __forceinline__ int force64_item(const Atoms &A, const Pot &P, const 
                 V = fs_V<double>(P.fs, r, dV);
                 gg = fma(Fpi + Fpj, fs_dphi<double>(P.fs, P.bd, r), dV);
             } else if (KIND == MD_POT_KNOTS) {
-                const int sj = MULTI ? __ldg(A.spec + j) : 0;
+                const int sj = MULTI ? ld_phase(A.spec + j) : 0;
                 const int nn = P.ns * P.ns;
                 double dVk, dab;
                 V = knot_sum<double, double2>(P.K64 + (size_t)(si * P.ns + sj) * P.nkt, P.nkt, r, dVk);
@@ -392,7 +399,7 @@ __device__ __forceinline__ int force64_item(const Atoms &A, const Pot &P, const 
                     gg = fma(Fpi + Fpj, dab, dVk);
                 }
             } else {
-                const int sj = MULTI ? __ldg(A.spec + j) : 0;
+                const int sj = MULTI ? ld_phase(A.spec + j) : 0;
                 double t;
                 bool below;
                 const int kr = knot_row((r - P.r_min) * P.inv_dr, P.nk, t, below);

@@ -108,7 +108,7 @@ __device__ __forceinline__ void density_item(const Atoms &A, const Pot &P, const
         };
         // two neighbours per iteration; the local list entries of the next iteration are loaded
         // before this iteration's terms are computed
-        auto entry = [&](int q) { return q < cnt ? (int)__ldg(row.ptr(q)) : 0; };
+        auto entry = [&](int q) { return q < cnt ? (int)ld_phase(row.ptr(q)) : 0; };
         int k = lane;
         int n0 = entry(k), n1 = entry(k + T);
         for (; k + T < cnt; k += 2 * T) {
@@ -140,7 +140,7 @@ __device__ __forceinline__ int force_item(const Atoms &A, const Pot &P, const fl
         auto pair = [&](const float4 &pj) {
             ps::pair32<KIND, false, ENERGY, SMT>(P, 0, 0, pi.w, pj.w, pj.x - pi.x, pj.y - pi.y, pj.z - pi.z, a, viol);
         };
-        auto entry = [&](int q) { return q < cnt ? (int)__ldg(row.ptr(q)) : 0; };
+        auto entry = [&](int q) { return q < cnt ? (int)ld_phase(row.ptr(q)) : 0; };
         int k = lane;
         int n0 = entry(k), n1 = entry(k + T);
         for (; k + T < cnt; k += 2 * T) {
@@ -275,7 +275,7 @@ __device__ __forceinline__ void density_half_item(const Atoms &A, const Pot &P, 
             ps::two_sum_add(hi, lo, phi);
             if (phi != 0.f) atomicAdd(&acc[lj].x, phi);
         };
-        auto entry = [&](int q) { return q < cnt ? (int)__ldg(row.ptr(q)) : 0; };
+        auto entry = [&](int q) { return q < cnt ? (int)ld_phase(row.ptr(q)) : 0; };
         int k = lane;
         int n0 = entry(k), n1 = entry(k + T);
         for (; k + T < cnt; k += 2 * T) {
@@ -331,7 +331,7 @@ __device__ __forceinline__ void force_half_item(const Atoms &A, const Pot &P, co
                 wxy = fmaf(-ax, dy, wxy);
             }
         };
-        auto entry = [&](int q) { return q < cnt ? (int)__ldg(row.ptr(q)) : 0; };
+        auto entry = [&](int q) { return q < cnt ? (int)ld_phase(row.ptr(q)) : 0; };
         int k = lane;
         int n0 = entry(k), n1 = entry(k + T);
         for (; k + T < cnt; k += 2 * T) {
