@@ -303,23 +303,18 @@ def run_ours(args):
     s.get(md.MD_GET_POS, hp), s.get(md.MD_GET_VEL, hv), s.get(md.MD_GET_FORCE, hf)
     k_e2e = max(3, min(args.steps, 200))
     for _ in range(3):
-        s.set_state(hp, hv, hf), s.step(1), s.get(md.MD_GET_POS, hp), s.get(md.MD_GET_VEL, hv)
-        s.get(md.MD_GET_FORCE, hf), s.energy()
+        s.step_io(1, hp, hv, hf, hp, hv, hf)
     barrier()
     t0 = time.perf_counter()
     for _ in range(k_e2e):
-        s.set_state(hp, hv, hf)
-        s.step(1)
-        s.get(md.MD_GET_POS, hp)
-        s.get(md.MD_GET_VEL, hv)
-        s.get(md.MD_GET_FORCE, hf)
-        s.energy()
+        s.step_io(1, hp, hv, hf, hp, hv, hf)
     t = max_over_ranks(time.perf_counter() - t0)
     s.close()
     e2e = {"value": world * n * k_e2e / t, "unit": UNIT, "h2d_bytes_per_step": 72 * n,
            "d2h_bytes_per_step": 72 * n + C.sizeof(md.md_energies), "steps": k_e2e,
-           "note": "each step: md_set_state(pos, vel, force from pinned host), md_step(1), "
-                   "md_get(pos, vel, force into pinned host), md_energy"}
+           "note": "each step one md_step_io call: positions, velocities and forces in from pinned host "
+                   "buffers, md_step(1), the three arrays back into them and the energies, one "
+                   "synchronisation"}
 
     extras = {}
     if not args.no_extras:

@@ -280,6 +280,16 @@ md_status md_get(md_ctx *ctx, int32_t what, void *dst, int32_t on_device);
 md_status md_set_state(md_ctx *ctx, const double *pos, const double *vel, const double *force,
                        int32_t on_device);
 
+/* A state kept by the caller, one call per stretch of steps: md_set_state(pos_in, vel_in,
+ * force_in), md_step(n_steps), then md_get of positions, velocities and forces into pos_out,
+ * vel_out, force_out and md_energy into *energies, with the copies and kernels in stream order
+ * and the stream synchronised once (at the end).  Every argument but ctx may be NULL (that copy
+ * is skipped); inputs and outputs may be the same buffers.  Results are bitwise those of the
+ * separate calls.  Host buffers are best pinned (page-locked); on_device as for md_get. */
+md_status md_step_io(md_ctx *ctx, int32_t n_steps, const double *pos_in, const double *vel_in,
+                     const double *force_in, double *pos_out, double *vel_out, double *force_out,
+                     md_energies *energies, int32_t on_device);
+
 /* Autotuner: time 3 velocity-Verlet steps of the persistent step kernel from the current state
  * with each lanes_per_atom in {1, 2, 4, 8, 16, 32} (CUDA events; the trial steps rebuild no
  * list, and positions, velocities, forces and counters are put back after each), keep the

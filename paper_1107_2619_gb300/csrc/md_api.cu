@@ -1051,9 +1051,72 @@ md_status md_eam_forces(md_ctx *ctx, double *pe_out) {
     return MD_OK;
 }
 
-md_status md_step(md_ctx *ctx, int32_t n_steps) {
+namespace {
+
+// Caller-order state arrays to copy out after a stretch of steps (md_step_io).
+struct StateOut {
+    double *pos, *vel, *force;
+    int on_device;
+};
+
+// The unsort kernels and copies of the requested arrays, enqueued only (three staging regions,
+// so that the copies need no synchronisation in between).
+md_status enqueue_state_out(md_ctx *ctx, const StateOut &o) {
+    const size_t n3 = 3 * (size_t)ctx->n;
+    md_status s = ensure_stage(ctx, 3 * n3 * sizeof(double));
+    if (s != MD_OK) return s;
+    const double4_32a *src[3] = {ctx->A.pos, ctx->A.vel, ctx->A.force};
+    double *dst[3] = {o.pos, o.vel, o.force};
+    for (int q = 0; q < 3; q++) {
+        if (!dst[q]) continue;
+        double *stage = static_cast<double *>(ctx->d_stage) + q * n3;
+        MD_CK(launch_unsort_vec(ctx->A, src[q], stage, ctx->stream));
+        MD_CK(cudaMemcpyAsync(dst[q], stage, n3 * sizeof(double),
+                              o.on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+        ctx->launches++;
+    }
+    return MD_OK;
+}
+
+// The copies in and sort kernels of md_set_state, enqueued only.
+md_status enqueue_state_in(md_ctx *ctx, const double *pos, const double *vel, const double *force, int on_device) {
+    const size_t n3 = 3 * (size_t)ctx->n;
+    md_status s = ensure_stage(ctx, 3 * n3 * sizeof(double));
+    if (s != MD_OK) return s;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const double *src[3] = {pos, vel, force};
+    double4_32a *dst[3] = {ctx->A.pos, ctx->A.vel, ctx->A.force};
+    for (int q = 0; q < 3; q++) {
+        if (!src[q]) continue;
+        double *stage = static_cast<double *>(ctx->d_stage) + q * n3;
+        MD_CK(cudaMemcpyAsync(stage, src[q], n3 * sizeof(double), kind, ctx->stream));
+        MD_CK(launch_sort_in_vec(ctx->A, stage, dst[q], ctx->stream));
+        ctx->launches++;
+    }
+    if (pos) {
+        MD_CK(launch_wrap(ctx->A, ctx->stream));
+        ctx->launches++;
+        ctx->sur_ref = false;
+    }
+    if (pos || force) ctx->forces_valid = (force != nullptr);
+    ctx->energy_valid = false;
+    return MD_OK;
+}
+
+md_status step_impl(md_ctx *ctx, int32_t n_steps, const StateOut *out) {
     if (!ctx || n_steps < 0) return MD_ERR_ARG;
-    if (n_steps == 0) return MD_OK;
+    if (n_steps == 0) {
+        if (out && ctx->n > 0) {
+            if (!ctx->forces_valid && out->force) {
+                md_status s = compute_forces(ctx);
+                if (s != MD_OK) return s;
+            }
+            md_status s = enqueue_state_out(ctx, *out);
+            if (s != MD_OK) return s;
+        }
+        MD_CK(cudaStreamSynchronize(ctx->stream));
+        return MD_OK;
+    }
     // link cells are fixed in fractional coordinates; under compression keep them >= r_list wide
     if (ctx->strain_scale != 1.0) {
         bool changed = false;
@@ -1139,6 +1202,10 @@ md_status md_step(md_ctx *ctx, int32_t n_steps) {
     if (stamps)
         MD_CK(cudaMemcpyAsync(ctx->h_stamps, stamps, kStampsPerStep * ((size_t)n_steps + 1) * sizeof(unsigned long long),
                               cudaMemcpyDeviceToHost, ctx->stream));
+    if (out && ctx->n > 0) {
+        md_status so = enqueue_state_out(ctx, *out);
+        if (so != MD_OK) return so;
+    }
     md_status st = sync_and_check(ctx, ctx->cfg.strict_skin != 0);
     ctx->step += n_steps;
     for (int r = 0; r < ctx->n_rep; r++)
@@ -1151,6 +1218,24 @@ md_status md_step(md_ctx *ctx, int32_t n_steps) {
     ctx->forces_valid = ctx->energy_valid = true;
     ctx->list_valid = ctx->C.tile != kWalkCells;   // a cell-walk rebuild leaves the list behind
     return MD_OK;
+}
+
+}  // namespace
+
+md_status md_step(md_ctx *ctx, int32_t n_steps) { return step_impl(ctx, n_steps, nullptr); }
+
+md_status md_step_io(md_ctx *ctx, int32_t n_steps, const double *pos_in, const double *vel_in,
+                     const double *force_in, double *pos_out, double *vel_out, double *force_out,
+                     md_energies *energies, int32_t on_device) {
+    if (!ctx || n_steps < 0) return MD_ERR_ARG;
+    if (ctx->n > 0 && (pos_in || vel_in || force_in)) {
+        md_status s = enqueue_state_in(ctx, pos_in, vel_in, force_in, on_device);
+        if (s != MD_OK) return s;
+    }
+    const StateOut out{pos_out, vel_out, force_out, on_device};
+    md_status s = step_impl(ctx, n_steps, &out);
+    if (s != MD_OK) return s;
+    return energies ? md_energy(ctx, energies) : MD_OK;
 }
 
 md_status md_energy(md_ctx *ctx, md_energies *out) {
@@ -1422,24 +1507,10 @@ md_status md_get_passes(md_ctx *ctx, md_passes *out) {
 md_status md_set_state(md_ctx *ctx, const double *pos, const double *vel, const double *force,
                        int32_t on_device) {
     if (!ctx) return MD_ERR_ARG;
-    const int64_t n = ctx->n;
-    if (n == 0) return MD_OK;
-    md_status s;
-    if ((s = ensure_stage(ctx, sizeof(double) * 3 * n)) != MD_OK) return s;
-    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    const double *src[3] = {pos, vel, force};
-    double4_32a *dst[3] = {ctx->A.pos, ctx->A.vel, ctx->A.force};
-    for (int q = 0; q < 3; q++) {
-        if (!src[q]) continue;
-        MD_CK(cudaMemcpyAsync(ctx->d_stage, src[q], sizeof(double) * 3 * n, kind, ctx->stream));
-        MD_CK(launch_sort_in_vec(ctx->A, static_cast<const double *>(ctx->d_stage), dst[q], ctx->stream));
-        ctx->launches++;
-    }
-    if (pos) MD_CK(launch_wrap(ctx->A, ctx->stream));
+    if (ctx->n == 0) return MD_OK;
+    md_status s = enqueue_state_in(ctx, pos, vel, force, on_device);
+    if (s != MD_OK) return s;
     MD_CK(cudaStreamSynchronize(ctx->stream));
-    if (pos) ctx->sur_ref = false;
-    if (pos || force) ctx->forces_valid = (force != nullptr);
-    ctx->energy_valid = false;
     return MD_OK;
 }
 

@@ -32,7 +32,7 @@ MD_PREC_FP64, MD_PREC_MIXED = 0, 1
 
 # functions declared in include/md.h (checked by the CPU test-suite)
 EXPORTS = ["md_abi_version", "md_status_string", "md_create", "md_create_batch", "md_build_neighbours",
-           "md_eam_forces", "md_step", "md_set_graph", "md_energy", "md_replica_energies", "md_get",
+           "md_eam_forces", "md_step", "md_step_io", "md_set_graph", "md_energy", "md_replica_energies", "md_get",
            "md_set_state", "md_tune", "md_set_profiling", "md_get_profile", "md_get_passes", "md_selftest_timeout",
            "md_neighbours_noalloc", "md_set_thermostat", "md_get_thermostat", "md_set_surrogate", "md_sur_get_params", "md_sur_standardize",
            "md_sur_get", "md_sur_set_reference", "md_sur_loss_grad", "md_sur_train", "md_last_error",
@@ -129,6 +129,8 @@ def lib():
         L.md_get.argtypes = [P, i32, P, i32]
         L.md_set_state.restype = C.c_int
         L.md_set_state.argtypes = [P, P, P, P, i32]
+        L.md_step_io.restype = C.c_int
+        L.md_step_io.argtypes = [P, i32, P, P, P, P, P, P, C.POINTER(md_energies), i32]
         L.md_tune.restype = C.c_int
         L.md_tune.argtypes = [P, C.POINTER(C.c_int32)]
         L.md_set_profiling.restype = C.c_int
@@ -250,14 +252,31 @@ def md_step(ctx, n_steps: int):
     _check(ctx, lib().md_step(ctx, int(n_steps)))
 
 
-def md_energy(ctx) -> dict:
-    e = md_energies()
-    _check(ctx, lib().md_energy(ctx, C.byref(e)))
+def _energy_dict(e) -> dict:
     return dict(pe=e.pe, ke=e.ke, te=e.te, temperature=e.temperature,
                 virial=np.array(e.virial[:]).reshape(3, 3), pressure_gpa=e.pressure_gpa,
                 momentum=np.array(e.momentum[:]), volume=e.volume, box=np.array(e.box[:]),
                 step=e.step, n_rebuilds=e.n_rebuilds, max_neighbours=e.max_neighbours,
                 range_violations=e.range_violations)
+
+
+def md_energy(ctx) -> dict:
+    e = md_energies()
+    _check(ctx, lib().md_energy(ctx, C.byref(e)))
+    return _energy_dict(e)
+
+
+def md_step_io(ctx, n_steps: int, pos_in=None, vel_in=None, force_in=None, pos_out=None, vel_out=None,
+               force_out=None) -> dict:
+    """State in, n_steps steps, state out and the energies, with one synchronisation."""
+    arrs = (pos_in, vel_in, force_in, pos_out, vel_out, force_out)
+    ptrs = [_ptr(a) for a in arrs]
+    flags = {p[1] for p, a in zip(ptrs, arrs) if a is not None}
+    if len(flags) > 1:
+        raise ValueError("state arrays must all be host or all device arrays")
+    e = md_energies()
+    _check(ctx, lib().md_step_io(ctx, int(n_steps), *[p[0] for p in ptrs], C.byref(e), flags.pop() if flags else 0))
+    return _energy_dict(e)
 
 
 def md_get(ctx, what: int, dst):
@@ -499,6 +518,11 @@ class System:
 
     def set_state(self, pos=None, vel=None, force=None):
         md_set_state(self.ctx, pos, vel, force)
+
+    def step_io(self, n: int = 1, pos_in=None, vel_in=None, force_in=None, pos_out=None, vel_out=None,
+                force_out=None) -> dict:
+        """md_step_io: set the state, take n steps, read the state back; returns the energies."""
+        return md_step_io(self.ctx, n, pos_in, vel_in, force_in, pos_out, vel_out, force_out)
 
     def set_thermostat(self, t_kelvin, tau_fs=None, q_ev_fs2=None):
         """Nose-Hoover thermostat at t_kelvin (scalar or one per replica); Q from the relaxation

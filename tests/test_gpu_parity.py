@@ -264,6 +264,36 @@ def test_device_inputs_match_host_inputs():
         assert np.array_equal(a.forces(), b.forces())
 
 
+@pytest.mark.parametrize("device", [False, True])
+def test_step_io_equals_the_separate_calls(device):
+    """md_step_io (state in, steps, state out, energies; one synchronisation) against
+    md_set_state + md_step + md_get x3 + md_energy: bitwise equal, host or device buffers, and
+    with the same buffers as inputs and outputs."""
+    torch = pytest.importorskip("torch")
+    w = I.fcc_cu(8, seed=31, sigma=0.03)
+    with _gpu_system(w, "mixed") as a, _gpu_system(w, "mixed") as b:
+        a.eam_forces()
+        b.eam_forces()
+        p, v, f = a.positions(), a.velocities(), a.forces()
+        for _ in range(3):   # three round trips, as a host-side driver would do them
+            b.set_state(p, v, f)
+            b.step(4)
+            p2, v2, f2, e2 = b.positions(), b.velocities(), b.forces(), b.energy()
+            if device:
+                bufs = [torch.from_numpy(x.copy()).cuda() for x in (p, v, f)]
+                e1 = a.step_io(4, *bufs, *bufs)
+                torch.cuda.synchronize()
+                p1, v1, f1 = (t.cpu().numpy() for t in bufs)
+            else:
+                p1, v1, f1 = p.copy(), v.copy(), f.copy()
+                e1 = a.step_io(4, p1, v1, f1, p1, v1, f1)
+            assert np.array_equal(p1, p2) and np.array_equal(v1, v2) and np.array_equal(f1, f2)
+            assert e1["pe"] == e2["pe"] and e1["ke"] == e2["ke"] and e1["step"] == e2["step"]
+            p, v, f = p1, v1, f1
+        e = a.step_io(0, pos_out=p1)   # no steps: the copies only
+        assert np.array_equal(p1, a.positions()) and e["pe"] == a.energy()["pe"]
+
+
 # --------------------------------------------------------------------------- edge cases
 def test_empty_and_single_atom_systems():
     pot = I.fs_fe_analytic()
