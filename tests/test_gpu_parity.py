@@ -369,6 +369,23 @@ def test_full_size_cu500k_forces_and_lists():
     assert abs(pe32 - ref["pe"]) <= MIXED_PE_TOL * abs(ref["pe"])
 
 
+def test_full_size_cu500k_step_kernel_as_benchmarked():
+    """The benchmark's launch: fcc Cu 500,000 atoms, mixed, the autotuner's lane count, one
+    persistent launch of 30 steps (list rebuilds inside it); the forces of its last force pass
+    at its own final positions, and its energies, against the oracle."""
+    w = I.fcc_cu(50, seed=2)
+    with _gpu_system(w, "mixed") as s:
+        s.eam_forces()
+        s.tune()
+        s.step(30)
+        e = s.energy()
+        pos, f = s.positions(), s.forces()
+    assert e["n_rebuilds"] >= 1
+    ref = oracle.forces(pos, w.species, w.box, w.potential, skin=w.skin, k_max=w.k_max, method="cells")
+    assert np.abs(f - ref["force"]).max() <= mixed_force_bound(w, np.abs(ref["force"]).max())
+    assert abs(e["pe"] - ref["pe"]) <= MIXED_PE_TOL * abs(ref["pe"])
+
+
 # --------------------------------------------------------------------------- lanes per atom
 @pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, 32])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
