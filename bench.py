@@ -61,6 +61,29 @@ def _peaks():
         return 6800.0, "fallback (6.8 TB/s)"
 
 
+# FP64 operations per list entry of the FP64 passes, counted from the pair code (an add or a
+# multiply is 1 flop, an FMA 2; conversions and rounding to integer not counted).  Entries
+# inside r_cut: density 40 (minimum image 3 x 4, r^2 5, FP64 rsqrt refinement 12, r 1, knot
+# index 3, cubic 6, sum 1) + force 56 (minimum image 12, r^2 5, rsqrt 12, r 1, knot index 3,
+# the two cubic derivatives 12, the F' combination 3, scalings 2, force 6).  Entries in the skin
+# shell stop after r^2: 17 per pass.
+FP64_FLOP_IN, FP64_FLOP_SHELL = 96.0, 34.0
+FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 (no measured figure in MEASURED_PEAKS.json)
+
+
+def fp64_pipe(sum_counts, w, ms_per_step):
+    """FP64-pipe fraction of the FP64 path by the per-entry model above; the share of list
+    entries inside r_cut is taken as (r_cut / r_list)^3 (uniform density)."""
+    rc = float(w.potential.r_cut)
+    f_in = (rc / (rc + w.skin)) ** 3
+    flop = sum_counts * (f_in * FP64_FLOP_IN + (1.0 - f_in) * FP64_FLOP_SHELL)
+    tflops = flop / (ms_per_step * 1e-3) / 1e12
+    return {"flop_per_step": flop, "achieved_tflops": tflops, "peak_tflops": FP64_PEAK_TFLOPS,
+            "frac": tflops / FP64_PEAK_TFLOPS, "peak_source": "nominal",
+            "model": "96 flop per list entry inside r_cut (both passes), 34 in the skin shell; "
+                     "share inside r_cut (r_cut/r_list)^3"}
+
+
 def _traffic(kernel, n_steps):
     """DRAM bytes per launch from a committed ncu capture (per atom-step, scaled to this launch),
     if the kernel's sources are unchanged since the capture; else None."""
@@ -257,7 +280,7 @@ def run_ours(args):
     n = w.n_atoms
     stream = torch.cuda.Stream()
     res, snapshot = {}, {}
-    for precision in (("mixed",) if args.profile_case else ("mixed", "fp64")):
+    for precision in ((args.profile_precision,) if args.profile_case else ("mixed", "fp64")):
         s = md.System(w, precision=precision, stream=stream.cuda_stream, device_inputs=True,
                       passes=args.passes if precision == "mixed" else "auto", lanes_per_atom=args.lanes)
         s.eam_forces()
@@ -278,7 +301,9 @@ def run_ours(args):
         prof["rebuilds"] = s.energy()["n_rebuilds"] - e1["n_rebuilds"]
         res[precision] = dict(ms=ms, prof=prof, e0=e0, e1=e1, counts=counts, clocks=clocks,
                               launches=launches, lanes=lanes)
-        if precision == "mixed":
+        if args.profile_case:
+            pass
+        elif precision == "mixed":
             snapshot["pos"] = s.positions()
             snapshot["mixed"] = s.forces()
         else:  # forces of both precisions at the same thermalised positions
@@ -288,8 +313,9 @@ def run_ours(args):
         s.close()
     if args.profile_case:
         if rank == 0:
-            r = res["mixed"]
-            print(json.dumps({"profile_case": True, "n_atoms": n, "ms_per_step": r["ms"] / args.steps,
+            r = res[args.profile_precision]
+            print(json.dumps({"profile_case": True, "precision": args.profile_precision,
+                              "list_entries": float(r["counts"].sum()), "n_atoms": n, "ms_per_step": r["ms"] / args.steps,
                               "lanes": r["lanes"], "passes": args.passes, "rebuild_ms_per_rebuild": rebuild_parts(r["prof"]),
                               "phase_ms": {k: r["prof"]["ms_" + k] / max(1, r["prof"]["n_" + k])
                                            for k in ("kick", "rebuild", "density", "force")}}))
@@ -356,12 +382,15 @@ def run_ours(args):
         q = res[pr]
         de = (q["e1"]["te"] - q["e0"]["te"]) / n
         qp = q["prof"]
-        return {"value": job_value(n, world, args.steps, q["ms"]), "ms_per_step": q["ms"] / args.steps,
+        out = {"value": job_value(n, world, args.steps, q["ms"]), "ms_per_step": q["ms"] / args.steps,
                 "nve_drift_ev_per_atom": de, "steps_timed": args.steps, "lanes_per_atom": q["lanes"],
                 "rebuilds_in_timed_region": q["e1"]["n_rebuilds"] - q["e0"]["n_rebuilds"],
                 "phase_ms_per_step_profiled_repeat": {k: qp["ms_" + k] / max(1, qp["n_" + k])
                                                        for k in ("kick", "rebuild", "density", "force")},
                 "rebuild_ms_per_rebuild": rebuild_parts(qp)}
+        if pr == "fp64":
+            out["fp64_pipe"] = fp64_pipe(sum_counts, w, q["ms"] / args.steps)
+        return out
 
     line = {
         "metric": METRIC, "value": job_value(n, world, args.steps, r["ms"]), "unit": UNIT,
@@ -588,6 +617,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the non-headline workloads")
     ap.add_argument("--passes", choices=["auto", "list", "staged", "cells", "half"], default="auto",
                     help="neighbour walk of the mixed-precision step kernel (md.h MD_PASSES_*)")
+    ap.add_argument("--profile-precision", choices=["mixed", "fp64"], default="mixed",
+                    help="precision of the --profile-case run")
     ap.add_argument("--lanes", type=int, default=0, choices=[0, 1, 2, 4, 8, 16, 32],
                     help="lanes per atom (0: the autotuner's choice)")
     ap.add_argument("--surrogate-only", action="store_true",
