@@ -102,7 +102,7 @@ struct Atoms {
     int32_t *cell_of, *slot, *order;
     int32_t *sorted;                         // order after the in-cell sort (aliases cell_of)
     int32_t *nbr, *count;                    // list entry k of atom i: see NbrRow; k < min(count, k_max)
-    uint16_t *lnbr;                          // staged passes: the same entries as slots of the atom's
+    uint16_t *lnbr;                          // staged walk: the same entries as slots of the atom's
                                              // cell-group stencil (same plane layout as nbr); half walk:
                                              // only the entries j > i, lcount of them
     int32_t *lcount;                         // half walk: entries of each half row
@@ -160,7 +160,7 @@ struct Cells {
     int ntiles;
     RepCells *rc;  // [n_rep], device
     int32_t *cell_count, *cell_start, *tile_sums;
-    // Cell groups of the staged passes (one system, cells r_list wide): groups of gx consecutive
+    // Cell groups of the group walks (one system, cells r_list wide): groups of gx consecutive
     // cells along x.  The neighbourhood of a group is its 3 x 3 x (gx + 2) stencil of cells; stencil
     // cell s = ((dz + 1) 3 + (dy + 1)) (gx + 2) + (x - x0 + 1) for the group starting at x0.
     int tile;           // walk of the step kernel's passes: kWalkList (no groups), kWalkStaged (groups
@@ -175,7 +175,7 @@ struct Cells {
 enum : int { kWalkList = 0, kWalkStaged = 1, kWalkCells = 2, kWalkHalf = 3 };
 
 // Shared memory of the mixed-precision step kernel: a single-species knot table (2 float4 per
-// knot) of at most kSmemTableMax bytes, and the stage of the staged passes; together at most
+// knot) of at most kSmemTableMax bytes, and the stage of the group walks; together at most
 // kSmemDynMax bytes (the static shared memory of a 1024-thread block comes on top).
 constexpr size_t kSmemTableMax = 200 * 1024;
 constexpr size_t kSmemDynMax = 222 * 1024;

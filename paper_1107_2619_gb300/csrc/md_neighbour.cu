@@ -8,11 +8,11 @@
 //   k_bin        wrapped fractional coordinate -> link cell; per-cell counter -> slot
 //   k_scan_*     exclusive scan of the per-cell counts -> cell_start (3 phases)
 //   k_scatter    order[cell_start[c] + slot] = atom; the stencil slot tables of the cell groups
-//                (staged passes)
+//                (group walks)
 //   k_cell_sort  stable order inside a cell: ascending caller atom id (deterministic)
 //   k_gather / k_copyback   renumber every per-atom array into cell order
 //   k_build_list full list: the 27 cells around each cell, |r_ij|^2 < r_list^2, a group of
-//                lanes per cell (with the staged passes also the same list as stencil slots)
+//                lanes per cell (for the staged and half walks also as 16-bit stencil slots)
 // Link cells are fixed in fractional coordinates and at least r_list wide, so every pair
 // closer than r_list lies in adjacent cells (the hybrid NL-LCM of §3.2.1).
 #include <cuda_runtime.h>

@@ -40,7 +40,7 @@ __device__ __forceinline__ float4 wrapped(const double4_32a &p, const Box &B, in
 
 // FP32 position in the periodic image its atom was wrapped into at the last list build (the
 // image of ref, the position at that build): the wrapped position until the atom crosses a box
-// face, continuous after it, so that it stays within skin/2 of its link cell (the staged passes
+// face, continuous after it, so that it stays within skin/2 of its link cell (the group walks
 // add each cell's image shift to these coordinates; the list passes take the minimum image).
 __device__ __forceinline__ float4 build_image(const double4_32a &p, const double4_32a &ref, const Box &B,
                                               int species) {
@@ -358,7 +358,7 @@ __device__ __forceinline__ int build_cell_group(const Atoms &A, const Cells &C, 
                 }
             }
         };
-        // cell group of the home cell (staged passes): stencil slots of this cell's neighbours
+        // cell group of the home cell (group walks): stencil slots of this cell's neighbours
         const int32_t *gloc = nullptr;
         int gx0 = 0;
         if constexpr (LOCAL) {

@@ -120,6 +120,11 @@ __device__ __forceinline__ void thermo_update(const StepParams &sp, int n_rep, l
 }
 
 // Minimum resident blocks per SM requested from the compiler (caps registers per thread).
+// Threads per block of the list walk with the table in shared memory (one block per SM).
+#ifndef MD_SMT_THREADS
+#define MD_SMT_THREADS 1024
+#endif
+
 #ifndef MD_STEP_MIN_BLOCKS
 #define MD_STEP_MIN_BLOCKS 8
 #endif
@@ -478,7 +483,8 @@ cudaError_t launch_kind(const Atoms &A, const Cells &C, const Pot &P, const Step
                     return launch_t<PREC, T, MD_POT_TABLES, false, 1024, true, kWalkHalf>(A, C, P, sp, bar, stamps,
                                                                                          grid_out, s);
             }
-            return launch_t<PREC, T, MD_POT_TABLES, false, 1024, true>(A, C, P, sp, bar, stamps, grid_out, s);
+            return launch_t<PREC, T, MD_POT_TABLES, false, MD_SMT_THREADS, true>(A, C, P, sp, bar, stamps, grid_out,
+                                                                                s);
         }
         return launch_t<PREC, T, MD_POT_TABLES, false>(A, C, P, sp, bar, stamps, grid_out, s);
     }
