@@ -575,6 +575,11 @@ md_status create_common(md_ctx *ctx, const md_config *cfg, const md_potential *p
     chk(dalloc(ctx, &A.id, n)); chk(dalloc(ctx, &A.id_tmp, n)); chk(dalloc(ctx, &A.rank, n));
     chk(dalloc(ctx, &A.spec, n)); chk(dalloc(ctx, &A.spec_tmp, n)); chk(dalloc(ctx, &A.cell_of, n));
     chk(dalloc(ctx, &A.slot, n)); chk(dalloc(ctx, &A.order, n)); chk(dalloc(ctx, &A.count, n));
+    chk(dalloc(ctx, &A.wrap, n));
+#ifndef MD_IMAGE_SHORTCUT
+#define MD_IMAGE_SHORTCUT 1
+#endif
+    A.image_fixed = (MD_IMAGE_SHORTCUT && cfg->strain_rate_zz == 0.0) ? 1 : 0;
     chk(dalloc(ctx, &A.nbr, nbr_entries(n, cfg->k_max)));
     if (n_rep > 1) chk(dalloc(ctx, &A.rep, n));
     A.sorted = A.cell_of;  // cell_of is consumed by the scatter before the in-cell sort writes
@@ -775,6 +780,7 @@ md_status create_common(md_ctx *ctx, const md_config *cfg, const md_potential *p
     chk(cudaMemcpy(ctx->d_rep_off, off32.data(), (n_rep + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
     chk(cudaMemcpy(ctx->d_flags, &flags, sizeof(Flags), cudaMemcpyHostToDevice));
     chk(cudaMemset(C.cell_count, 0, sizeof(int32_t) * C.ncell));
+    chk(cudaMemset(A.wrap, 1, n));   // every atom takes the minimum image until the first build
     chk(cudaMemset(A.partials, 0, sizeof(double) * rows * kPartials));
     chk(cudaDeviceSynchronize());
     chk(launch_wrap(A, ctx->stream));

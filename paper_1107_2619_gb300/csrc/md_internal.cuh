@@ -102,6 +102,11 @@ struct Atoms {
     int32_t *cell_of, *slot, *order;
     int32_t *sorted;                         // order after the in-cell sort (aliases cell_of)
     int32_t *nbr, *count;                    // list entry k of atom i: see NbrRow; k < min(count, k_max)
+    uint8_t *wrap;                           // 1: the atom's link cell is on the box boundary at the
+                                             // last build (some neighbour cell is a periodic image)
+    int image_fixed;                         // 1: no strain ramp, so posf/p2f stay in the periodic
+                                             // image of the last build (then wrap == 0 means no
+                                             // minimum image is needed)
     uint16_t *lnbr;                          // staged walk: the same entries as slots of the atom's
                                              // cell-group stencil (same plane layout as nbr); half walk:
                                              // only the entries j > i, lcount of them

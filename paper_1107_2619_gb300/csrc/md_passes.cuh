@@ -12,6 +12,8 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "md_eam_common.cuh"
 #include "md_phases.cuh"
 
@@ -22,6 +24,20 @@ using namespace eam;
 
 __device__ __forceinline__ float mi32(float d, float L, float invL) { return fmaf(-L, rintf(d * invL), d); }
 __device__ __forceinline__ double mi64(double d, double L, double invL) { return fma(-L, rint(d * invL), d); }
+
+// The minimum image of a separation, or the separation itself for an atom whose link cell was not
+// on the box boundary at the last build (A.wrap) while the FP32 positions stay in the image of
+// that build (A.image_fixed: no strain ramp): none of its list entries is then a periodic image,
+// |d| < L/2, rint(d / L) = 0 and the minimum image returns d unchanged, so skipping it changes no
+// bit.  WRAP is a compile-time tag (std::true_type / std::false_type).
+template <typename WRAP>
+__device__ __forceinline__ float sep32(float d, float L, float invL) {
+    return WRAP::value ? mi32(d, L, invL) : d;
+}
+template <typename WRAP>
+__device__ __forceinline__ double sep64(double d, double L, double invL) {
+    return WRAP::value ? mi64(d, L, invL) : d;
+}
 
 // Knot-table row of a species pair: (V c0..c3, phi c0..c3) as 8 floats in one 32-byte load.
 __device__ __forceinline__ void row32(const double4_32a *tab, size_t idx, float (&v)[4], float (&p)[4]) {
@@ -234,28 +250,34 @@ __device__ __forceinline__ void density32_item(const Atoms &A, const Pot &P, con
         const int cnt = min(A.count[i], A.k_max);
         const NbrRow row = nbr_row(A, i);
         unsigned viol = 0;
-        auto term = [&](const float4 &pj) -> float {
-            return rho_term32<KIND, MULTI, SMT>(P, si, MULTI ? __float_as_int(pj.w) : 0, mi32(pj.x - pi.x, Lx, ix),
-                                                mi32(pj.y - pi.y, Ly, iy), mi32(pj.z - pi.z, Lz, iz), viol);
+        auto walk = [&](auto wrap) {
+            using W = decltype(wrap);
+            auto term = [&](const float4 &pj) -> float {
+                return rho_term32<KIND, MULTI, SMT>(P, si, MULTI ? __float_as_int(pj.w) : 0,
+                                                    sep32<W>(pj.x - pi.x, Lx, ix), sep32<W>(pj.y - pi.y, Ly, iy),
+                                                    sep32<W>(pj.z - pi.z, Lz, iz), viol);
+            };
+            // two neighbours per iteration, software-pipelined: the positions of the next iteration
+            // and the list entries of the one after are loaded before this iteration's terms are
+            // computed, so the dependent loads of one neighbour overlap the arithmetic of others
+            auto entry = [&](int q) { return q < cnt ? ld_phase(row.ptr(q)) : i; };
+            int k = lane;
+            float4 p0 = ld_phase(A.posf + entry(k)), p1 = ld_phase(A.posf + entry(k + T));
+            int n0 = entry(k + 2 * T), n1 = entry(k + 3 * T);
+            for (; k + T < cnt; k += 2 * T) {
+                const float4 q0 = ld_phase(A.posf + n0), q1 = ld_phase(A.posf + n1);
+                n0 = entry(k + 4 * T);
+                n1 = entry(k + 5 * T);
+                const float a0 = term(p0), a1 = term(p1);
+                two_sum_add(hi, lo, a0);
+                two_sum_add(hi, lo, a1);
+                p0 = q0;
+                p1 = q1;
+            }
+            if (k < cnt) two_sum_add(hi, lo, term(p0));
         };
-        // two neighbours per iteration, software-pipelined: the positions of the next iteration
-        // and the list entries of the one after are loaded before this iteration's terms are
-        // computed, so the dependent loads of one neighbour overlap the arithmetic of others
-        auto entry = [&](int q) { return q < cnt ? ld_phase(row.ptr(q)) : i; };
-        int k = lane;
-        float4 p0 = ld_phase(A.posf + entry(k)), p1 = ld_phase(A.posf + entry(k + T));
-        int n0 = entry(k + 2 * T), n1 = entry(k + 3 * T);
-        for (; k + T < cnt; k += 2 * T) {
-            const float4 q0 = ld_phase(A.posf + n0), q1 = ld_phase(A.posf + n1);
-            n0 = entry(k + 4 * T);
-            n1 = entry(k + 5 * T);
-            const float a0 = term(p0), a1 = term(p1);
-            two_sum_add(hi, lo, a0);
-            two_sum_add(hi, lo, a1);
-            p0 = q0;
-            p1 = q1;
-        }
-        if (k < cnt) two_sum_add(hi, lo, term(p0));
+        if (!A.image_fixed || ld_phase(A.wrap + i)) walk(std::true_type{});
+        else walk(std::false_type{});
         if (viol) atomicAdd(&A.flags->range_violations, (unsigned long long)viol);
     }
     lane_sum_df<T>(hi, lo);
@@ -278,24 +300,29 @@ __device__ __forceinline__ int force32_item(const Atoms &A, const Pot &P, const 
         const int cnt = min(A.count[i], A.k_max);
         const NbrRow row = nbr_row(A, i);
         unsigned viol = 0;
-        auto pair = [&](int j, const float4 &pj) {
-            pair32<KIND, MULTI, ENERGY, SMT>(P, si, MULTI ? ld_phase(A.spec + j) : 0, pi.w, pj.w,
-                                             mi32(pj.x - pi.x, Lx, ix), mi32(pj.y - pi.y, Ly, iy),
-                                             mi32(pj.z - pi.z, Lz, iz), a, viol);
+        auto walk = [&](auto wrap) {
+            using W = decltype(wrap);
+            auto pair = [&](int j, const float4 &pj) {
+                pair32<KIND, MULTI, ENERGY, SMT>(P, si, MULTI ? ld_phase(A.spec + j) : 0, pi.w, pj.w,
+                                                 sep32<W>(pj.x - pi.x, Lx, ix), sep32<W>(pj.y - pi.y, Ly, iy),
+                                                 sep32<W>(pj.z - pi.z, Lz, iz), a, viol);
+            };
+            // two neighbours per iteration; the list entries of the next iteration are loaded before
+            // this iteration's positions are used (one dependent load less on the critical path)
+            int k = lane;
+            int j0 = k < cnt ? ld_phase(row.ptr(k)) : 0, j1 = k + T < cnt ? ld_phase(row.ptr(k + T)) : 0;
+            for (; k + T < cnt; k += 2 * T) {
+                const float4 p0 = ld_phase(A.p2f + j0), p1 = ld_phase(A.p2f + j1);
+                const int ja = j0, jb = j1, kn = k + 2 * T;
+                j0 = kn < cnt ? ld_phase(row.ptr(kn)) : 0;
+                j1 = kn + T < cnt ? ld_phase(row.ptr(kn + T)) : 0;
+                pair(ja, p0);
+                pair(jb, p1);
+            }
+            if (k < cnt) pair(j0, ld_phase(A.p2f + j0));
         };
-        // two neighbours per iteration; the list entries of the next iteration are loaded before
-        // this iteration's positions are used (one dependent load less on the critical path)
-        int k = lane;
-        int j0 = k < cnt ? ld_phase(row.ptr(k)) : 0, j1 = k + T < cnt ? ld_phase(row.ptr(k + T)) : 0;
-        for (; k + T < cnt; k += 2 * T) {
-            const float4 p0 = ld_phase(A.p2f + j0), p1 = ld_phase(A.p2f + j1);
-            const int ja = j0, jb = j1, kn = k + 2 * T;
-            j0 = kn < cnt ? ld_phase(row.ptr(kn)) : 0;
-            j1 = kn + T < cnt ? ld_phase(row.ptr(kn + T)) : 0;
-            pair(ja, p0);
-            pair(jb, p1);
-        }
-        if (k < cnt) pair(j0, ld_phase(A.p2f + j0));
+        if (!A.image_fixed || ld_phase(A.wrap + i)) walk(std::true_type{});
+        else walk(std::false_type{});
         if (viol) atomicAdd(&A.flags->range_violations, (unsigned long long)viol);
     }
     lane_sum_acc<T, ENERGY>(a);

@@ -423,6 +423,7 @@ __device__ __forceinline__ int build_cell_group(const Atoms &A, const Cells &C, 
         }
         if (act) {
             A.count[i] = cnt;
+            A.wrap[i] = (cx < R || cx >= nx - R || cy < R || cy >= ny - R || cz < R || cz >= nz - R) ? 1 : 0;
             if constexpr (LOCAL == 2) A.lcount[i] = lcnt;
             if (cnt > kmax) atomicOr(&A.flags->error, FLAG_OVERFLOW);
             longest = max(longest, cnt);
