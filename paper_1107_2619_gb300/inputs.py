@@ -235,7 +235,7 @@ def _knot_sum(coef, knots):
 def _fe_knot_fit():
     """A Finnis-Sinclair-like Fe as 15 cubic knot terms (§3.1.1 form): 8 for V on knots evenly in
     2.3..c, 7 for phi evenly in 2.1..d, coefficients from a least-squares fit of FS Fe's V and phi
-    on 1.8..d (the paper's iron of intermediate complexity: a sum of 15 cubic splines)."""
+    on 1.8..d (the 15-term cubic-spline iron of the paper's scaling tests, §5.1)."""
     V, _, P, _ = _fs_fe_funcs()
     d, cc = FS_FE["d"], FS_FE["c"]
     r = np.linspace(1.8, d, 600)
