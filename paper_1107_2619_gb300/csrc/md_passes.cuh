@@ -52,13 +52,14 @@ __device__ __forceinline__ float4 phi_half32(const double4_32a *tab, size_t idx)
     return __ldg(reinterpret_cast<const float4 *>(tab + idx) + 1);
 }
 
-// The same rows from a copy of the table in the kernel's dynamic shared memory (SMT: one
-// species).  The copy is split: the nk float4 rows of V coefficients, then the nk rows of phi
-// coefficients, so that the rows a warp reads at random spread over all eight 16-byte bank
-// groups (interleaved V/phi rows would put every phi row in four of them).
+// The same rows from a copy of the table of species pair (0, 0) in the kernel's dynamic shared
+// memory (SMT; rows of other pairs, idx >= nk, come from the global table).  The copy is split:
+// the nk float4 rows of V coefficients, then the nk rows of phi coefficients, so that the rows a
+// warp reads at random spread over all eight 16-byte bank groups (interleaved V/phi rows would
+// put every phi row in four of them).
 template <bool SMT>
 __device__ __forceinline__ float4 phi_row(const Pot &P, size_t idx) {
-    if (SMT) {
+    if (SMT && idx < (size_t)P.nk) {
         extern __shared__ float4 sm_table_f4[];
         return sm_table_f4[P.nk + idx];
     }
@@ -67,7 +68,7 @@ __device__ __forceinline__ float4 phi_row(const Pot &P, size_t idx) {
 
 template <bool SMT>
 __device__ __forceinline__ void vp_row(const Pot &P, size_t idx, float (&v)[4], float (&p)[4]) {
-    if (SMT) {
+    if (SMT && idx < (size_t)P.nk) {
         extern __shared__ float4 sm_table_f4[];
         const float4 a = sm_table_f4[idx], b = sm_table_f4[P.nk + idx];
         v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
@@ -152,7 +153,8 @@ __device__ __forceinline__ float pair_g32(const Pot &P, int si, int sj, float Fp
         cubic(t, cp[0], cp[1], cp[2], cp[3], below, dab);
         float gk;
         if (MULTI) {
-            const float4 c = phi_half32(P.VP32, (size_t)(sj * P.ns + si) * P.nk + kr);
+            float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (!MD_TABLE_SKIP || inside) c = phi_row<SMT>(P, (size_t)(sj * P.ns + si) * P.nk + kr);
             float dba;
             cubic(t, c.x, c.y, c.z, c.w, below, dba);
             gk = fmaf(Fpi, dab, fmaf(Fpj, dba, dVk));

@@ -129,8 +129,9 @@ __device__ __forceinline__ void thermo_update(const StepParams &sp, int n_rep, l
 #define MD_STEP_MIN_BLOCKS 8
 #endif
 
-// NT threads per block.  SMT: the single-species knot table is copied into dynamic shared
-// memory at the start of the launch and the passes read it there (one 1024-thread block per SM).
+// NT threads per block.  SMT: the knot table of species pair (0, 0) (of the only species, or of
+// the host species of an alloy) is copied into dynamic shared memory at the start of the launch
+// and the passes read it there (one 1024-thread block per SM); other pairs read the global table.
 // WALK (kWalkStaged, kWalkCells, kWalkHalf): the passes run over cell groups staged in shared
 // memory (md_tile.cuh) whenever every group's neighbourhood fitted the stage at the last build,
 // else over atoms through the list.  The cell walk builds no list at a rebuild unless a group
@@ -488,6 +489,9 @@ cudaError_t launch_kind(const Atoms &A, const Cells &C, const Pot &P, const Step
         }
         return launch_t<PREC, T, MD_POT_TABLES, false>(A, C, P, sp, bar, stamps, grid_out, s);
     }
+    // several species: the table of pair (0, 0), the host species, in shared memory
+    if (MD_SMEM_TABLE && PREC == MD_PREC_MIXED && (size_t)P.nk * 32 <= kSmemTableMax)
+        return launch_t<PREC, T, MD_POT_TABLES, true, MD_SMT_THREADS, true>(A, C, P, sp, bar, stamps, grid_out, s);
     return launch_t<PREC, T, MD_POT_TABLES, true>(A, C, P, sp, bar, stamps, grid_out, s);
 }
 

@@ -170,6 +170,24 @@ def test_knot_sums_step_like_the_oracle(precision):
     assert abs(e["pe"] - ref["energies"][-1, 0]) <= (1e-10 if precision == "fp64" else 1e-6) * abs(ref["energies"][-1, 0])
 
 
+@pytest.mark.parametrize("lanes", [1, 4])
+def test_two_species_tables_step_like_the_oracle(lanes):
+    """Fe-C two-species tables (the Fe-Fe table in shared memory, the C rows from global memory)
+    through the persistent step kernel under the strain ramp: 20 steps against the oracle, and
+    the last force pass at the GPU's final positions."""
+    w = _workload("fec")
+    ref = oracle.run_vv(w.pos, w.vel, w.species, w.potential.masses, w.box, w.potential, w.dt_fs, 20,
+                        w.skin, w.k_max, strain_rate_zz=w.strain_rate_zz)
+    with _gpu_system(w, "mixed", lanes_per_atom=lanes) as s:
+        s.step(20)
+        pos, f, e = s.positions(), s.forces(), s.energy()
+    assert np.abs(pos - ref["pos"]).max() < 1e-5
+    assert abs(e["pe"] - ref["energies"][-1, 0]) <= MIXED_PE_TOL * abs(ref["energies"][-1, 0])
+    box = np.array(e["box"])
+    fr = oracle.forces(pos, w.species, box, w.potential, skin=w.skin, k_max=w.k_max)["force"]
+    assert np.abs(f - fr).max() <= mixed_force_bound(w, np.abs(fr).max())
+
+
 def test_unwrapped_images_give_the_same_forces():
     w = I.bcc_fe(10, seed=12)
     shifted = I.Workload(**{**w.__dict__, "pos": w.pos + w.box * np.array([3.0, -7.0, 1.0])})
