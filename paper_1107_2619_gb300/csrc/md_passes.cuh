@@ -39,6 +39,14 @@ __device__ __forceinline__ double sep64(double d, double L, double invL) {
     return WRAP::value ? mi64(d, L, invL) : d;
 }
 
+// Whether the warp of atom i (lane: every lane of the warp calls it together) takes the minimum
+// image: when any of its atoms needs it, all do (the same bits, and no divergence between the
+// two walks inside a warp).
+__device__ __forceinline__ bool needs_image(const Atoms &A, int i, bool live) {
+    const bool w = live && (!A.image_fixed || ld_phase(A.wrap + i) != 0);
+    return __any_sync(0xffffffffu, w);
+}
+
 // Knot-table row of a species pair: (V c0..c3, phi c0..c3) as 8 floats in one 32-byte load.
 __device__ __forceinline__ void row32(const double4_32a *tab, size_t idx, float (&v)[4], float (&p)[4]) {
     const double4_32a d = tab[idx];
@@ -57,18 +65,18 @@ __device__ __forceinline__ float4 phi_half32(const double4_32a *tab, size_t idx)
 // the nk float4 rows of V coefficients, then the nk rows of phi coefficients, so that the rows a
 // warp reads at random spread over all eight 16-byte bank groups (interleaved V/phi rows would
 // put every phi row in four of them).
-template <bool SMT>
+template <bool SMT, bool MULTI>
 __device__ __forceinline__ float4 phi_row(const Pot &P, size_t idx) {
-    if (SMT && idx < (size_t)P.nk) {
+    if (SMT && (!MULTI || idx < (size_t)P.nk)) {
         extern __shared__ float4 sm_table_f4[];
         return sm_table_f4[P.nk + idx];
     }
     return phi_half32(P.VP32, idx);
 }
 
-template <bool SMT>
+template <bool SMT, bool MULTI>
 __device__ __forceinline__ void vp_row(const Pot &P, size_t idx, float (&v)[4], float (&p)[4]) {
-    if (SMT && idx < (size_t)P.nk) {
+    if (SMT && (!MULTI || idx < (size_t)P.nk)) {
         extern __shared__ float4 sm_table_f4[];
         const float4 a = sm_table_f4[idx], b = sm_table_f4[P.nk + idx];
         v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
@@ -105,7 +113,7 @@ __device__ __forceinline__ float rho_term32(const Pot &P, int si, int sj, float 
         const int kr = knot_row((r - P.r_minf) * P.inv_drf, P.nk, t, below);
         viol += (below && inside) ? 1u : 0u;
         float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (!MD_TABLE_SKIP || inside) c = phi_row<SMT>(P, (size_t)(si * P.ns + sj) * P.nk + kr);
+        if (!MD_TABLE_SKIP || inside) c = phi_row<SMT, MULTI>(P, (size_t)(si * P.ns + sj) * P.nk + kr);
         phi = cubic(t, c.x, c.y, c.z, c.w, below, d);
     }
     return inside ? phi : 0.f;
@@ -148,13 +156,13 @@ __device__ __forceinline__ float pair_g32(const Pot &P, int si, int sj, float Fp
         const int kr = knot_row((r - P.r_minf) * P.inv_drf, P.nk, t, below);
         viol += (below && inside) ? 1u : 0u;
         float cv[4] = {0.f, 0.f, 0.f, 0.f}, cp[4] = {0.f, 0.f, 0.f, 0.f}, dVk, dab;
-        if (!MD_TABLE_SKIP || inside) vp_row<SMT>(P, (size_t)(si * P.ns + sj) * P.nk + kr, cv, cp);
+        if (!MD_TABLE_SKIP || inside) vp_row<SMT, MULTI>(P, (size_t)(si * P.ns + sj) * P.nk + kr, cv, cp);
         V = cubic(t, cv[0], cv[1], cv[2], cv[3], below, dVk);
         cubic(t, cp[0], cp[1], cp[2], cp[3], below, dab);
         float gk;
         if (MULTI) {
             float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (!MD_TABLE_SKIP || inside) c = phi_row<SMT>(P, (size_t)(sj * P.ns + si) * P.nk + kr);
+            if (!MD_TABLE_SKIP || inside) c = phi_row<SMT, MULTI>(P, (size_t)(sj * P.ns + si) * P.nk + kr);
             float dba;
             cubic(t, c.x, c.y, c.z, c.w, below, dba);
             gk = fmaf(Fpi, dab, fmaf(Fpj, dba, dVk));
@@ -243,6 +251,7 @@ __device__ __forceinline__ void density32_item(const Atoms &A, const Pot &P, con
     float hi = 0.f, lo = 0.f;
     float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
     int si = 0;
+    const bool wrap = needs_image(A, i, live);
     if (live) {
         const Box &B = boxes[ph::replica_of(A, i)];
         const float Lx = B.Lf[0], Ly = B.Lf[1], Lz = B.Lf[2];
@@ -278,7 +287,7 @@ __device__ __forceinline__ void density32_item(const Atoms &A, const Pot &P, con
             }
             if (k < cnt) two_sum_add(hi, lo, term(p0));
         };
-        if (!A.image_fixed || ld_phase(A.wrap + i)) walk(std::true_type{});
+        if (wrap) walk(std::true_type{});
         else walk(std::false_type{});
         if (viol) atomicAdd(&A.flags->range_violations, (unsigned long long)viol);
     }
@@ -293,6 +302,7 @@ __device__ __forceinline__ int force32_item(const Atoms &A, const Pot &P, const 
     const int i = (int)(g / T), lane = (int)(g & (T - 1));
     const bool live = i < A.n;
     Acc32 a;
+    const bool wrap = needs_image(A, i, live);
     if (live) {
         const Box &B = boxes[ph::replica_of(A, i)];
         const float Lx = B.Lf[0], Ly = B.Lf[1], Lz = B.Lf[2];
@@ -323,7 +333,7 @@ __device__ __forceinline__ int force32_item(const Atoms &A, const Pot &P, const 
             }
             if (k < cnt) pair(j0, ld_phase(A.p2f + j0));
         };
-        if (!A.image_fixed || ld_phase(A.wrap + i)) walk(std::true_type{});
+        if (wrap) walk(std::true_type{});
         else walk(std::false_type{});
         if (viol) atomicAdd(&A.flags->range_violations, (unsigned long long)viol);
     }
