@@ -149,13 +149,14 @@ void list_band(const md_ctx *c, float &lo, float &hi) {
 
 // Lanes per link cell of the list build, from the mean cell occupancy (a whole warp per cell
 // above 12 atoms: on GB300 the single broadcast candidate stream of a warp-wide group built the
-// fcc Cu list faster than 8-lane groups with fewer idle lanes, 1.29 against about 1.8 ms per build).
+// fcc Cu list faster than 8-lane groups with fewer idle lanes, 1.29 against about 1.8 ms per build;
+// 4 lanes up to 6 atoms: the bcc Fe lists about 4 % faster than with 8).
 #ifndef MD_LIST_GROUP_MAX
 #define MD_LIST_GROUP_MAX 32
 #endif
 int ph_list_group(const md_ctx *c) {
     const double m = c->C.ncell > 0 ? (double)c->n / (double)c->C.ncell : 0.0;
-    return std::min(MD_LIST_GROUP_MAX, m <= 3.0 ? 4 : (m <= 6.0 ? 8 : (m <= 12.0 ? 16 : 32)));
+    return std::min(MD_LIST_GROUP_MAX, m <= 6.0 ? 4 : (m <= 12.0 ? 16 : 32));
 }
 
 int cells_along(double L, double r_list) {
