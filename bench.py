@@ -84,9 +84,9 @@ def fp64_pipe(sum_counts, w, ms_per_step):
                      "share inside r_cut (r_cut/r_list)^3"}
 
 
-def _traffic(kernel, n_steps):
-    """DRAM bytes per launch from a committed ncu capture (per atom-step, scaled to this launch),
-    if the kernel's sources are unchanged since the capture; else None."""
+def _capture(kernel):
+    """The committed ncu record of a kernel (profiles/traffic.json) if its sources are unchanged
+    since the capture; else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
@@ -95,11 +95,15 @@ def _traffic(kernel, n_steps):
         for src in rec["sources"]:
             with open(os.path.join(ROOT, src), "rb") as fh:
                 h.update(fh.read())
-        if h.hexdigest() != rec["sha256"]:
-            return None
-        return float(rec["bytes_per_atom_step"]) * 4 * CELLS ** 3 * n_steps
+        return rec if h.hexdigest() == rec["sha256"] else None
     except Exception:
         return None
+
+
+def _traffic(kernel, n_steps):
+    """DRAM bytes per launch from the committed ncu capture (per atom-step, scaled to this launch)."""
+    rec = _capture(kernel)
+    return None if rec is None else float(rec["bytes_per_atom_step"]) * 4 * CELLS ** 3 * n_steps
 
 
 class Clocks:
@@ -399,6 +403,7 @@ def run_ours(args):
         "data": "synthetic", "config": _config("mixed: FP32 pair/density terms, FP64 integration and sums"),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": _traffic("k_step_mixed", args.steps),
+                     "limiter": (_capture("k_step_mixed") or {}).get("limiter"),
                      "kernel": "k_step (persistent: all phases of all K steps in one launch)",
                      "algorithmic_bytes_per_launch": launch_bytes, "avg_launch_ms": r["ms"],
                      "peak_source": peak_src, "rebuild_bytes": "not counted (list builds are extra work)",
