@@ -577,6 +577,7 @@ md_status create_common(md_ctx *ctx, const md_config *cfg, const md_potential *p
     chk(dalloc(ctx, &A.spec, n)); chk(dalloc(ctx, &A.spec_tmp, n)); chk(dalloc(ctx, &A.cell_of, n));
     chk(dalloc(ctx, &A.slot, n)); chk(dalloc(ctx, &A.order, n)); chk(dalloc(ctx, &A.count, n));
     chk(dalloc(ctx, &A.wrap, n));
+    if (cfg->precision == MD_PREC_FP64 && pot->kind != MD_POT_SURROGATE) chk(dalloc(ctx, &A.posd, n));
 #ifndef MD_IMAGE_SHORTCUT
 #define MD_IMAGE_SHORTCUT 1
 #endif
@@ -1381,11 +1382,12 @@ md_status md_tune(md_ctx *ctx, int32_t *lanes_out) {
         // atom is renumbered; the state the steps change is saved first and put back after
         // every trial.
         const size_t n = (size_t)ctx->n;
-        const size_t bytes = n * (3 * sizeof(double4_32a) + sizeof(float4)) + sizeof(Flags);
+        const size_t bytes = n * (4 * sizeof(double4_32a) + sizeof(float4)) + sizeof(Flags);
         unsigned char *snap = nullptr;
         MD_CK(cudaMalloc(&snap, bytes));
         double4_32a *s_pos = reinterpret_cast<double4_32a *>(snap), *s_vel = s_pos + n, *s_force = s_vel + n;
-        float4 *s_posf = reinterpret_cast<float4 *>(s_force + n);
+        double4_32a *s_posd = s_force + n;
+        float4 *s_posf = reinterpret_cast<float4 *>(s_posd + n);
         Flags *s_flags = reinterpret_cast<Flags *>(s_posf + n);
         Atoms &A = ctx->A;
         auto copy = [&](bool save) {
@@ -1395,6 +1397,8 @@ md_status md_tune(md_ctx *ctx, int32_t *lanes_out) {
             if (e == cudaSuccess)
                 e = cudaMemcpyAsync(save ? s_force : A.force, save ? A.force : s_force, n * 32, k, ctx->stream);
             if (e == cudaSuccess) e = cudaMemcpyAsync(save ? s_posf : A.posf, save ? A.posf : s_posf, n * 16, k, ctx->stream);
+            if (e == cudaSuccess && A.posd)
+                e = cudaMemcpyAsync(save ? s_posd : A.posd, save ? A.posd : s_posd, n * 32, k, ctx->stream);
             if (e == cudaSuccess)
                 e = cudaMemcpyAsync(save ? s_flags : ctx->d_flags, save ? ctx->d_flags : s_flags, sizeof(Flags), k,
                                     ctx->stream);

@@ -93,6 +93,8 @@ struct Atoms {
     int n, k_max;
     int n_rep;
     double4_32a *pos, *vel, *force, *ref;        // pos.w = species; vel.w = (1/mvv2e)/m
+    double4_32a *posd;                           // FP64 path: pos in the periodic image of the last
+                                                 // build (as posf; NULL on the mixed path)
     double4_32a *pos_tmp, *vel_tmp, *force_tmp;  // renumbering scratch
     float4 *posf;                            // FP32 wrapped position, w = species bits
     float4 *p2f;                             // mixed pass 2: wrapped position + F'(rho)

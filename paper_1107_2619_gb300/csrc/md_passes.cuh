@@ -351,37 +351,43 @@ __device__ __forceinline__ void density64_item(const Atoms &A, const Pot &P, con
     double rho = 0.0;
     double4_32a pi = make_double4_32a(0.0, 0.0, 0.0, 0.0);
     int si = 0;
+    const bool wrap = needs_image(A, i, live);
     if (live) {
         const Box &B = boxes[ph::replica_of(A, i)];
-        pi = A.pos[i];
+        pi = ld_phase(A.posd + i);
         si = MULTI ? A.spec[i] : 0;
         const int cnt = min(A.count[i], A.k_max);
         const NbrRow row = nbr_row(A, i);
-        for (int k = lane; k < cnt; k += T) {
-            const int j = ld_phase(row.ptr(k));
-            const double4_32a pj = A.pos[j];
-            const double dx = mi64(pj.x - pi.x, B.L[0], B.invL[0]);
-            const double dy = mi64(pj.y - pi.y, B.L[1], B.invL[1]);
-            const double dz = mi64(pj.z - pi.z, B.L[2], B.invL[2]);
-            const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-            if (!(r2 < P.rc2)) continue;
-            const double r = r2 * rsqrt64(r2);
-            if (KIND == MD_POT_FS_ANALYTIC) {
-                rho += fs_phi<double>(P.fs, P.bd, r);
-            } else if (KIND == MD_POT_KNOTS) {
-                const int sj = MULTI ? (int)pj.w : 0;
-                double d;
-                rho += knot_sum<double, double2>(P.K64 + (size_t)(P.ns * P.ns + si * P.ns + sj) * P.nkt, P.nkt, r, d);
-            } else {
-                const int sj = MULTI ? (int)pj.w : 0;
-                double t, d;
-                bool below;
-                const int kr = knot_row((r - P.r_min) * P.inv_dr, P.nk, t, below);
-                if (below) atomicAdd(&A.flags->range_violations, 1ull);
-                const double4_32a c = P.VP64[((size_t)(si * P.ns + sj) * P.nk + kr) * 2 + 1];
-                rho += cubic(t, c.x, c.y, c.z, c.w, below, d);
+        auto walk = [&](auto wrapt) {
+            using W = decltype(wrapt);
+            for (int k = lane; k < cnt; k += T) {
+                const int j = ld_phase(row.ptr(k));
+                const double4_32a pj = ld_phase(A.posd + j);
+                const double dx = sep64<W>(pj.x - pi.x, B.L[0], B.invL[0]);
+                const double dy = sep64<W>(pj.y - pi.y, B.L[1], B.invL[1]);
+                const double dz = sep64<W>(pj.z - pi.z, B.L[2], B.invL[2]);
+                const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+                if (!(r2 < P.rc2)) continue;
+                const double r = r2 * rsqrt64(r2);
+                if (KIND == MD_POT_FS_ANALYTIC) {
+                    rho += fs_phi<double>(P.fs, P.bd, r);
+                } else if (KIND == MD_POT_KNOTS) {
+                    const int sj = MULTI ? (int)pj.w : 0;
+                    double d;
+                    rho += knot_sum<double, double2>(P.K64 + (size_t)(P.ns * P.ns + si * P.ns + sj) * P.nkt, P.nkt, r, d);
+                } else {
+                    const int sj = MULTI ? (int)pj.w : 0;
+                    double t, d;
+                    bool below;
+                    const int kr = knot_row((r - P.r_min) * P.inv_dr, P.nk, t, below);
+                    if (below) atomicAdd(&A.flags->range_violations, 1ull);
+                    const double4_32a c = P.VP64[((size_t)(si * P.ns + sj) * P.nk + kr) * 2 + 1];
+                    rho += cubic(t, c.x, c.y, c.z, c.w, below, d);
+                }
             }
-        }
+        };
+        if (wrap) walk(std::true_type{});
+        else walk(std::false_type{});
     }
     rho = lane_sum<T>(rho);
     if (live && lane == 0) {
@@ -401,6 +407,7 @@ __device__ __forceinline__ int force64_item(const Atoms &A, const Pot &P, const 
     const bool live = i < A.n;
     double fx = 0.0, fy = 0.0, fz = 0.0, ep = 0.0;
     double wxx = 0.0, wyy = 0.0, wzz = 0.0, wyz = 0.0, wxz = 0.0, wxy = 0.0;
+    const bool wrap = needs_image(A, i, live);
     if (live) {
         const Box &B = boxes[ph::replica_of(A, i)];
         const double4_32a pi = A.p2d[i];
@@ -408,72 +415,77 @@ __device__ __forceinline__ int force64_item(const Atoms &A, const Pot &P, const 
         const int si = MULTI ? A.spec[i] : 0;
         const int cnt = min(A.count[i], A.k_max);
         const NbrRow row = nbr_row(A, i);
-        for (int k = lane; k < cnt; k += T) {
-            const int j = ld_phase(row.ptr(k));
-            const double4_32a pj = A.p2d[j];
-            const double dx = mi64(pj.x - pi.x, B.L[0], B.invL[0]);
-            const double dy = mi64(pj.y - pi.y, B.L[1], B.invL[1]);
-            const double dz = mi64(pj.z - pi.z, B.L[2], B.invL[2]);
-            const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-            if (!(r2 < P.rc2)) continue;
-            const double rinv = rsqrt64(r2);
-            const double r = r2 * rinv;
-            const double Fpj = pj.w;
-            double V, gg;
-            if (KIND == MD_POT_FS_ANALYTIC) {
-                double dV;
-                V = fs_V<double>(P.fs, r, dV);
-                gg = fma(Fpi + Fpj, fs_dphi<double>(P.fs, P.bd, r), dV);
-            } else if (KIND == MD_POT_KNOTS) {
-                const int sj = MULTI ? ld_phase(A.spec + j) : 0;
-                const int nn = P.ns * P.ns;
-                double dVk, dab;
-                V = knot_sum<double, double2>(P.K64 + (size_t)(si * P.ns + sj) * P.nkt, P.nkt, r, dVk);
-                knot_sum<double, double2>(P.K64 + (size_t)(nn + si * P.ns + sj) * P.nkt, P.nkt, r, dab);
-                if (MULTI) {
-                    double dba;
-                    knot_sum<double, double2>(P.K64 + (size_t)(nn + sj * P.ns + si) * P.nkt, P.nkt, r, dba);
-                    gg = fma(Fpi, dab, fma(Fpj, dba, dVk));
+        auto walk = [&](auto wrapt) {
+            using W = decltype(wrapt);
+            for (int k = lane; k < cnt; k += T) {
+                const int j = ld_phase(row.ptr(k));
+                const double4_32a pj = ld_phase(A.p2d + j);
+                const double dx = sep64<W>(pj.x - pi.x, B.L[0], B.invL[0]);
+                const double dy = sep64<W>(pj.y - pi.y, B.L[1], B.invL[1]);
+                const double dz = sep64<W>(pj.z - pi.z, B.L[2], B.invL[2]);
+                const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+                if (!(r2 < P.rc2)) continue;
+                const double rinv = rsqrt64(r2);
+                const double r = r2 * rinv;
+                const double Fpj = pj.w;
+                double V, gg;
+                if (KIND == MD_POT_FS_ANALYTIC) {
+                    double dV;
+                    V = fs_V<double>(P.fs, r, dV);
+                    gg = fma(Fpi + Fpj, fs_dphi<double>(P.fs, P.bd, r), dV);
+                } else if (KIND == MD_POT_KNOTS) {
+                    const int sj = MULTI ? ld_phase(A.spec + j) : 0;
+                    const int nn = P.ns * P.ns;
+                    double dVk, dab;
+                    V = knot_sum<double, double2>(P.K64 + (size_t)(si * P.ns + sj) * P.nkt, P.nkt, r, dVk);
+                    knot_sum<double, double2>(P.K64 + (size_t)(nn + si * P.ns + sj) * P.nkt, P.nkt, r, dab);
+                    if (MULTI) {
+                        double dba;
+                        knot_sum<double, double2>(P.K64 + (size_t)(nn + sj * P.ns + si) * P.nkt, P.nkt, r, dba);
+                        gg = fma(Fpi, dab, fma(Fpj, dba, dVk));
+                    } else {
+                        gg = fma(Fpi + Fpj, dab, dVk);
+                    }
                 } else {
-                    gg = fma(Fpi + Fpj, dab, dVk);
+                    const int sj = MULTI ? ld_phase(A.spec + j) : 0;
+                    double t;
+                    bool below;
+                    const int kr = knot_row((r - P.r_min) * P.inv_dr, P.nk, t, below);
+                    if (below) atomicAdd(&A.flags->range_violations, 1ull);
+                    const size_t ab = ((size_t)(si * P.ns + sj) * P.nk + kr) * 2;
+                    const double4_32a cv = P.VP64[ab], cp = P.VP64[ab + 1];
+                    double dVk, dab;
+                    V = cubic(t, cv.x, cv.y, cv.z, cv.w, below, dVk);
+                    cubic(t, cp.x, cp.y, cp.z, cp.w, below, dab);
+                    double gk;
+                    if (MULTI) {
+                        const double4_32a cb = P.VP64[((size_t)(sj * P.ns + si) * P.nk + kr) * 2 + 1];
+                        double dba;
+                        cubic(t, cb.x, cb.y, cb.z, cb.w, below, dba);
+                        gk = fma(Fpi, dab, fma(Fpj, dba, dVk));
+                    } else {
+                        gk = fma(Fpi + Fpj, dab, dVk);
+                    }
+                    gg = gk * P.inv_dr;
                 }
-            } else {
-                const int sj = MULTI ? ld_phase(A.spec + j) : 0;
-                double t;
-                bool below;
-                const int kr = knot_row((r - P.r_min) * P.inv_dr, P.nk, t, below);
-                if (below) atomicAdd(&A.flags->range_violations, 1ull);
-                const size_t ab = ((size_t)(si * P.ns + sj) * P.nk + kr) * 2;
-                const double4_32a cv = P.VP64[ab], cp = P.VP64[ab + 1];
-                double dVk, dab;
-                V = cubic(t, cv.x, cv.y, cv.z, cv.w, below, dVk);
-                cubic(t, cp.x, cp.y, cp.z, cp.w, below, dab);
-                double gk;
-                if (MULTI) {
-                    const double4_32a cb = P.VP64[((size_t)(sj * P.ns + si) * P.nk + kr) * 2 + 1];
-                    double dba;
-                    cubic(t, cb.x, cb.y, cb.z, cb.w, below, dba);
-                    gk = fma(Fpi, dab, fma(Fpj, dba, dVk));
-                } else {
-                    gk = fma(Fpi + Fpj, dab, dVk);
+                const double gr = gg * rinv;
+                fx = fma(gr, dx, fx);
+                fy = fma(gr, dy, fy);
+                fz = fma(gr, dz, fz);
+                if (ENERGY) {
+                    ep = fma(0.5, V, ep);
+                    const double hg = -0.5 * gr;
+                    wxx = fma(hg * dx, dx, wxx);
+                    wyy = fma(hg * dy, dy, wyy);
+                    wzz = fma(hg * dz, dz, wzz);
+                    wyz = fma(hg * dy, dz, wyz);
+                    wxz = fma(hg * dx, dz, wxz);
+                    wxy = fma(hg * dx, dy, wxy);
                 }
-                gg = gk * P.inv_dr;
             }
-            const double gr = gg * rinv;
-            fx = fma(gr, dx, fx);
-            fy = fma(gr, dy, fy);
-            fz = fma(gr, dz, fz);
-            if (ENERGY) {
-                ep = fma(0.5, V, ep);
-                const double hg = -0.5 * gr;
-                wxx = fma(hg * dx, dx, wxx);
-                wyy = fma(hg * dy, dy, wyy);
-                wzz = fma(hg * dz, dz, wzz);
-                wyz = fma(hg * dy, dz, wyz);
-                wxz = fma(hg * dx, dz, wxz);
-                wxy = fma(hg * dx, dy, wxy);
-            }
-        }
+        };
+        if (wrap) walk(std::true_type{});
+        else walk(std::false_type{});
     }
     fx = lane_sum<T>(fx);
     fy = lane_sum<T>(fy);

@@ -38,6 +38,16 @@ __device__ __forceinline__ float4 wrapped(const double4_32a &p, const Box &B, in
                        wrap1(p.z, B.L[2], B.invL[2]), __int_as_float(species));
 }
 
+// FP64 positions wrapped into the box, and in the image of the last build (as below).
+__device__ __forceinline__ double4_32a wrapped64(const double4_32a &p, const Box &B) {
+    return make_double4_32a(p.x - B.L[0] * floor(p.x * B.invL[0]), p.y - B.L[1] * floor(p.y * B.invL[1]),
+                            p.z - B.L[2] * floor(p.z * B.invL[2]), p.w);
+}
+__device__ __forceinline__ double4_32a build_image64(const double4_32a &p, const double4_32a &ref, const Box &B) {
+    return make_double4_32a(p.x - B.L[0] * floor(ref.x * B.invL[0]), p.y - B.L[1] * floor(ref.y * B.invL[1]),
+                            p.z - B.L[2] * floor(ref.z * B.invL[2]), p.w);
+}
+
 // FP32 position in the periodic image its atom was wrapped into at the last list build (the
 // image of ref, the position at that build): the wrapped position until the atom crosses a box
 // face, continuous after it, so that it stays within skin/2 of its link cell (the group walks
@@ -114,6 +124,7 @@ __device__ __forceinline__ void kick_drift(const Atoms &A, const Box *boxes, int
         A.flags->skin_exceeded = 1;
     }
     A.posf[i] = build_image(p, r, boxes[replica_of(A, i)], A.spec[i]);
+    if (A.posd) A.posd[i] = build_image64(p, r, boxes[replica_of(A, i)]);
 }
 
 __device__ __forceinline__ void check_displacement(const Atoms &A, int i, double lim2) {
@@ -264,6 +275,7 @@ __device__ __forceinline__ void copyback_atom(const Atoms &A, const Box *boxes, 
     A.spec[k] = sp;
     A.rank[id] = k;
     A.posf[k] = wrapped(p, boxes[replica_of(A, k)], sp);
+    if (A.posd) A.posd[k] = wrapped64(p, boxes[replica_of(A, k)]);
 }
 
 // The exact neighbour test: the IEEE operations, order and absence of contraction of the

@@ -19,6 +19,7 @@ __global__ void k_wrap(Atoms A) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= A.n) return;
     A.posf[i] = ph::build_image(A.pos[i], A.ref[i], A.boxes[ph::replica_of(A, i)], A.spec[i]);
+    if (A.posd) A.posd[i] = ph::build_image64(A.pos[i], A.ref[i], A.boxes[ph::replica_of(A, i)]);
 }
 
 __global__ void k_unsort_vec(Atoms A, const double4_32a *src, double *dst) {
