@@ -90,7 +90,7 @@ __global__ void k_copyback(Atoms A) {
 }
 
 template <int G, int LOCAL>
-__global__ void __launch_bounds__(kThreads) k_build_list(Atoms A, Cells C, double rl2, float band_lo,
+__global__ void __launch_bounds__(kThreads, 8) k_build_list(Atoms A, Cells C, double rl2, float band_lo,
                                                          float band_hi) {
     if (!ph::rebuild_requested(A.flags)) return;
     int m = ph::build_cells<G, LOCAL>(A, C, A.boxes, gtid() >> 5, gstride() >> 5, threadIdx.x & 31, rl2, band_lo, band_hi);

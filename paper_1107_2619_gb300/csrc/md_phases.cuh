@@ -322,6 +322,56 @@ static __device__ __noinline__ bool within_exact_band(const double4_32a *pos, in
 // list as the slot of the candidate in its cell group's stage (grp_loc of the stencil cell plus
 // the candidate's rank inside its cell); 2, only the entries j > i are, as the half row of the
 // half walk (lcount of them).
+// The cells of the stencil of link cell (cx, cy, cz) of a replica (+-R cells along each edge), in
+// (dz, dy, dx) order: fn(js, je, sx, sy, sz, dz, dy, dx) with the cell's slot range and the shift
+// by whole box edges that puts a cell across the periodic boundary next to the home cell.
+template <typename Fn>
+__device__ __forceinline__ void for_stencil(const Cells &C, const RepCells &g, int R, int cx, int cy, int cz,
+                                            float Lx, float Ly, float Lz, Fn &&fn) {
+    const int nx = g.nc[0], ny = g.nc[1], nz = g.nc[2];
+    for (int dz = -R; dz <= R; dz++) {
+        int z = cz + dz;
+        float sz = 0.f;
+        if (z < 0) { z += nz; sz = -Lz; }
+        if (z >= nz) { z -= nz; sz = Lz; }
+        for (int dy = -R; dy <= R; dy++) {
+            int y = cy + dy;
+            float sy = 0.f;
+            if (y < 0) { y += ny; sy = -Ly; }
+            if (y >= ny) { y -= ny; sy = Ly; }
+            const int rowc = g.base + (z * ny + y) * nx;
+            for (int dx = -R; dx <= R; dx++) {
+                int x = cx + dx;
+                float sx = 0.f;
+                if (x < 0) { x += nx; sx = -Lx; }
+                if (x >= nx) { x -= nx; sx = Lx; }
+                const int cc = rowc + x;
+                fn(C.cell_start[cc], C.cell_start[cc + 1], sx, sy, sz, dz, dy, dx);
+            }
+        }
+    }
+}
+
+// Full list rows of the atoms of link cell c (§3.2.1: candidates from the cells around it, 27 for
+// cells r_list wide, 125 for cells r_list / 2 wide) by a group of G lanes (G = 4, 8, 16 or 32;
+// 32 / G cells per warp): lane a of the group takes atoms s + a, s + a + G, ... of the cell.  All
+// lanes of the group walk the same neighbour cells and the same candidates in the same order,
+// so a candidate is one broadcast load for the group and
+// the control flow is uniform inside it.  Candidates are screened with FP32 wrapped coordinates,
+// shifted by whole box edges for neighbour cells across the periodic boundary (no rounding to the
+// nearest image per candidate).  Only a candidate whose FP32 r^2 lies in [band_lo, band_hi] (a band
+// wider than the proven FP32 error) is decided by the exact FP64 test, so each row is the exact
+// FP64 set, listed by cell in (dz, dy, dx) order and by ascending slot inside a cell.  Rows are cut
+// at k_max (the count is kept).  Returns the longest row of this lane's atoms.  The stencil of
+// +-reach cells along each edge needs >= 2 reach + 1 cells per edge (no cell visited twice).
+// The last atoms of a cell, when they fill at most half the group (the 4 atoms after the first 32
+// of a 36-atom fcc Cu cell, the fifth and sixth of a bcc Fe cell), take L = 2, 4, ... lanes each:
+// lane l of an atom tests candidates js + l, js + l + L, ... of every stencil cell, and a ballot
+// over the atom's L lanes places the accepted ones in slot order, so the rows are the same.
+// LOCAL (group walks, one system, reach 1): 1, every entry is also written to the 16-bit local
+// list as the slot of the candidate in its cell group's stage (grp_loc of the stencil cell plus
+// the candidate's rank inside its cell); 2, only the entries j > i are, as the half row of the
+// half walk (lcount of them).  Those builds keep one lane per atom.
 template <int G, int LOCAL>
 __device__ __forceinline__ int build_cell_group(const Atoms &A, const Cells &C, const Box *boxes, int c, int gl,
                                                 double rl2, float band_lo, float band_hi) {
@@ -337,8 +387,57 @@ __device__ __forceinline__ int build_cell_group(const Atoms &A, const Cells &C, 
     const int R = C.reach;
     const int kmax = A.k_max;
     const long long plane = 4LL * A.n;
+    const bool edge = cx < R || cx >= nx - R || cy < R || cy >= ny - R || cz < R || cz >= nz - R;
     int longest = 0;
     for (int a0 = s; a0 < e; a0 += G) {
+        if constexpr (LOCAL == 0) {
+            if (2 * (e - a0) <= G) {   // the last atoms of the cell: L lanes each
+                const int rem = e - a0;
+                int lg = 1;
+                while ((rem << (lg + 1)) <= G) lg++;
+                const int L = 1 << lg;
+                const int a = gl >> lg, sl = gl & (L - 1);
+                const bool act = a < rem;
+                const int i = a0 + a, ii = act ? i : s;
+                const float4 fi = A.posf[ii];
+                const int gbase = (int)(threadIdx.x & 31) & ~(G - 1);
+                const unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u) << gbase;
+                const unsigned lmask = L == 32 ? 0xffffffffu : (1u << L) - 1u;
+                const int sh = gbase + (a << lg);
+                int32_t *const row = A.nbr + 4 * (size_t)ii;
+                int cnt = 0;
+                for_stencil(C, g, R, cx, cy, cz, Lx, Ly, Lz,
+                            [&](int js, int je, float sx, float sy, float sz, int, int, int) {
+                    const float ox = sx - fi.x, oy = sy - fi.y, oz = sz - fi.z;
+                    for (int j0 = js; j0 < je; j0 += L) {   // the same trip count on every lane of the group
+                        const int j = j0 + sl;
+                        bool in = false;
+                        if (j < je) {
+                            const float4 f = A.posf[j];
+                            const float dx = f.x + ox, dy = f.y + oy, dz = f.z + oz;
+                            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                            if (r2 <= band_hi)
+                                in = (r2 < band_lo || within_exact_band(A.pos, ii, j, B, rl2)) && act && j != i;
+                        }
+                        const unsigned sub = (__ballot_sync(gmask, in) >> sh) & lmask;
+                        if (in) {
+                            const int k = cnt + __popc(sub & ((1u << sl) - 1u));
+                            if (k < kmax) row[(long long)(k >> 2) * plane + (k & 3)] = j;
+                        }
+                        cnt += __popc(sub);
+                    }
+                });
+                if (act) {
+                    if (sl == 0) {
+                        A.count[i] = cnt;
+                        A.wrap[i] = edge ? 1 : 0;
+                        if (cnt > kmax) atomicOr(&A.flags->error, FLAG_OVERFLOW);
+                    }
+                    longest = max(longest, cnt);
+                }
+                break;
+            }
+        }
         const int i = a0 + gl;
         const bool act = i < e;
         const int ii = act ? i : s;
@@ -378,64 +477,46 @@ __device__ __forceinline__ int build_cell_group(const Atoms &A, const Cells &C, 
             gx0 = gxi * C.gx;
             gloc = C.grp_loc + (size_t)((cz * ny + cy) * C.ngx + gxi) * (C.st_cells + 1);
         }
-        for (int dz = -R; dz <= R; dz++) {
-            int z = cz + dz;
-            float sz = 0.f;
-            if (z < 0) { z += nz; sz = -Lz; }
-            if (z >= nz) { z -= nz; sz = Lz; }
-            for (int dy = -R; dy <= R; dy++) {
-                int y = cy + dy;
-                float sy = 0.f;
-                if (y < 0) { y += ny; sy = -Ly; }
-                if (y >= ny) { y -= ny; sy = Ly; }
-                const int rowc = g.base + (z * ny + y) * nx;
-                for (int dx = -R; dx <= R; dx++) {
-                    int x = cx + dx;
-                    float sx = 0.f;
-                    if (x < 0) { x += nx; sx = -Lx; }
-                    if (x >= nx) { x -= nx; sx = Lx; }
-                    const int cc = rowc + x;
-                    const int js = C.cell_start[cc], je = C.cell_start[cc + 1];
-                    if constexpr (LOCAL) lbase = gloc[((dz + 1) * 3 + (dy + 1)) * (C.gx + 2) + (cx - gx0 + dx + 1)];
-                    const float ox = sx - fi.x, oy = sy - fi.y, oz = sz - fi.z;
-                    int j = js;
+        for_stencil(C, g, R, cx, cy, cz, Lx, Ly, Lz,
+                    [&](int js, int je, float sx, float sy, float sz, int dz, int dy, int dx) {
+            if constexpr (LOCAL) lbase = gloc[((dz + 1) * 3 + (dy + 1)) * (C.gx + 2) + (cx - gx0 + dx + 1)];
+            const float ox = sx - fi.x, oy = sy - fi.y, oz = sz - fi.z;
+            int j = js;
 #if MD_BUILD_UNROLL >= 4
-                    for (; j + 3 < je; j += 4) {
-                        const float4 f0 = A.posf[j], f1 = A.posf[j + 1], f2 = A.posf[j + 2], f3 = A.posf[j + 3];
-                        const float ax = f0.x + ox, ay = f0.y + oy, az = f0.z + oz;
-                        const float bx = f1.x + ox, by = f1.y + oy, bz = f1.z + oz;
-                        const float cx2 = f2.x + ox, cy2 = f2.y + oy, cz2 = f2.z + oz;
-                        const float dx2 = f3.x + ox, dy2 = f3.y + oy, dz2 = f3.z + oz;
-                        const float r0 = fmaf(ax, ax, fmaf(ay, ay, az * az));
-                        const float r1 = fmaf(bx, bx, fmaf(by, by, bz * bz));
-                        const float rr2 = fmaf(cx2, cx2, fmaf(cy2, cy2, cz2 * cz2));
-                        const float rr3 = fmaf(dx2, dx2, fmaf(dy2, dy2, dz2 * dz2));
-                        visit(j, js, r0);
-                        visit(j + 1, js, r1);
-                        visit(j + 2, js, rr2);
-                        visit(j + 3, js, rr3);
-                    }
-#endif
-                    for (; j + 1 < je; j += 2) {
-                        const float4 f0 = A.posf[j], f1 = A.posf[j + 1];
-                        const float ax = f0.x + ox, ay = f0.y + oy, az = f0.z + oz;
-                        const float bx = f1.x + ox, by = f1.y + oy, bz = f1.z + oz;
-                        const float r0 = fmaf(ax, ax, fmaf(ay, ay, az * az));
-                        const float r1 = fmaf(bx, bx, fmaf(by, by, bz * bz));
-                        visit(j, js, r0);
-                        visit(j + 1, js, r1);
-                    }
-                    if (j < je) {
-                        const float4 f0 = A.posf[j];
-                        const float ax = f0.x + ox, ay = f0.y + oy, az = f0.z + oz;
-                        visit(j, js, fmaf(ax, ax, fmaf(ay, ay, az * az)));
-                    }
-                }
+            for (; j + 3 < je; j += 4) {
+                const float4 f0 = A.posf[j], f1 = A.posf[j + 1], f2 = A.posf[j + 2], f3 = A.posf[j + 3];
+                const float ax = f0.x + ox, ay = f0.y + oy, az = f0.z + oz;
+                const float bx = f1.x + ox, by = f1.y + oy, bz = f1.z + oz;
+                const float cx2 = f2.x + ox, cy2 = f2.y + oy, cz2 = f2.z + oz;
+                const float dx2 = f3.x + ox, dy2 = f3.y + oy, dz2 = f3.z + oz;
+                const float r0 = fmaf(ax, ax, fmaf(ay, ay, az * az));
+                const float r1 = fmaf(bx, bx, fmaf(by, by, bz * bz));
+                const float rr2 = fmaf(cx2, cx2, fmaf(cy2, cy2, cz2 * cz2));
+                const float rr3 = fmaf(dx2, dx2, fmaf(dy2, dy2, dz2 * dz2));
+                visit(j, js, r0);
+                visit(j + 1, js, r1);
+                visit(j + 2, js, rr2);
+                visit(j + 3, js, rr3);
             }
-        }
+#endif
+            for (; j + 1 < je; j += 2) {
+                const float4 f0 = A.posf[j], f1 = A.posf[j + 1];
+                const float ax = f0.x + ox, ay = f0.y + oy, az = f0.z + oz;
+                const float bx = f1.x + ox, by = f1.y + oy, bz = f1.z + oz;
+                const float r0 = fmaf(ax, ax, fmaf(ay, ay, az * az));
+                const float r1 = fmaf(bx, bx, fmaf(by, by, bz * bz));
+                visit(j, js, r0);
+                visit(j + 1, js, r1);
+            }
+            if (j < je) {
+                const float4 f0 = A.posf[j];
+                const float ax = f0.x + ox, ay = f0.y + oy, az = f0.z + oz;
+                visit(j, js, fmaf(ax, ax, fmaf(ay, ay, az * az)));
+            }
+        });
         if (act) {
             A.count[i] = cnt;
-            A.wrap[i] = (cx < R || cx >= nx - R || cy < R || cy >= ny - R || cz < R || cz >= nz - R) ? 1 : 0;
+            A.wrap[i] = edge ? 1 : 0;
             if constexpr (LOCAL == 2) A.lcount[i] = lcnt;
             if (cnt > kmax) atomicOr(&A.flags->error, FLAG_OVERFLOW);
             longest = max(longest, cnt);
