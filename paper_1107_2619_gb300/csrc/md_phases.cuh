@@ -305,6 +305,12 @@ static __device__ __noinline__ bool within_exact_band(const double4_32a *pos, in
 #ifndef MD_BUILD_UNROLL
 #define MD_BUILD_UNROLL 4
 #endif
+// Smallest lane group whose last atoms take several lanes each: a warp-wide group only.  In the
+// 4-lane groups of bcc Fe cells (eight cells per warp, about five atoms each) it built the lists
+// 20 % slower on GB300 (0.78 against 0.63 ms per rebuild at 1.02M atoms).
+#ifndef MD_BUILD_SLICE_MIN_G
+#define MD_BUILD_SLICE_MIN_G 32
+#endif
 
 // Full list rows of the atoms of link cell c (§3.2.1: candidates from the cells around it, 27 for
 // cells r_list wide, 125 for cells r_list / 2 wide) by a group of G lanes (G = 4, 8, 16 or 32;
@@ -364,8 +370,8 @@ __device__ __forceinline__ void for_stencil(const Cells &C, const RepCells &g, i
 // FP64 set, listed by cell in (dz, dy, dx) order and by ascending slot inside a cell.  Rows are cut
 // at k_max (the count is kept).  Returns the longest row of this lane's atoms.  The stencil of
 // +-reach cells along each edge needs >= 2 reach + 1 cells per edge (no cell visited twice).
-// The last atoms of a cell, when they fill at most half the group (the 4 atoms after the first 32
-// of a 36-atom fcc Cu cell, the fifth and sixth of a bcc Fe cell), take L = 2, 4, ... lanes each:
+// In a warp-wide group (G = 32), the last atoms of a cell, when they fill at most half the warp (the
+// 4 atoms after the first 32 of a 36-atom fcc Cu cell), take L = 2, 4, ... lanes each:
 // lane l of an atom tests candidates js + l, js + l + L, ... of every stencil cell, and a ballot
 // over the atom's L lanes places the accepted ones in slot order, so the rows are the same.
 // LOCAL (group walks, one system, reach 1): 1, every entry is also written to the 16-bit local
@@ -390,7 +396,7 @@ __device__ __forceinline__ int build_cell_group(const Atoms &A, const Cells &C, 
     const bool edge = cx < R || cx >= nx - R || cy < R || cy >= ny - R || cz < R || cz >= nz - R;
     int longest = 0;
     for (int a0 = s; a0 < e; a0 += G) {
-        if constexpr (LOCAL == 0) {
+        if constexpr (LOCAL == 0 && G >= MD_BUILD_SLICE_MIN_G) {
             if (2 * (e - a0) <= G) {   // the last atoms of the cell: L lanes each
                 const int rem = e - a0;
                 int lg = 1;
