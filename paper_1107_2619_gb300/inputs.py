@@ -391,6 +391,25 @@ def fcc_cu(n: int, seed: int, temperature: float = 300.0, n_knots: int = 5000, s
                     potential=pot, skin=0.3, k_max=176, dt_fs=dt_fs, steps=steps, temperature=temperature)
 
 
+def cell_count_gas(counts, cells: int = 4, seed: int = 5, skin: float = 0.3, k_max: int = 320) -> Workload:
+    """Cu atoms (the Sutton-Chen tables' r_cut) in a cubic box of cells^3 link cells, each edge
+    cells x 1.01 r_list long, link cell c (x fastest) holding counts[c] atoms at uniform random
+    positions inside it, at least 2 % of its width from its faces; zero velocities.  A neighbour
+    list case only: atoms may sit arbitrarily close together."""
+    counts = np.asarray(counts, dtype=np.int64)
+    assert counts.shape == (cells ** 3,)
+    pot = sc_cu_tables(n_knots=500)
+    w = 1.01 * (pot.r_cut + skin)
+    u = random_uniform(seed, 12, 3 * int(counts.sum())).reshape(-1, 3)
+    c = np.repeat(np.arange(cells ** 3), counts)
+    corner = np.stack([c % cells, (c // cells) % cells, c // (cells * cells)], axis=1) * w
+    pos = corner + w * (0.02 + 0.96 * u)
+    n = pos.shape[0]
+    return Workload(name=f"gas {cells}^3 cells", pos=pos, vel=np.zeros_like(pos),
+                    species=np.zeros(n, dtype=np.int32), box=np.full(3, cells * w), potential=pot,
+                    skin=skin, k_max=k_max, dt_fs=2.0, steps=1, temperature=0.0)
+
+
 def bcc_fe_c(n: int, seed: int, temperature: float = 600.0, c_fraction: float = 0.001,
              steps: int = 200, dt_fs: float = 1.0, a: float = 2.8665,
              strain_rate_zz: float = -1.0e9) -> Workload:

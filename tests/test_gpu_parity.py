@@ -114,6 +114,21 @@ def test_neighbour_sets_bit_exact(name, precision):
     assert np.all(lg[np.arange(w.k_max)[None, :] >= cg[:, None]] == -1)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_neighbour_sets_bit_exact_for_every_cell_remainder(precision):
+    """Link cells of 25..56 atoms, built by warp-wide lane groups: after the first 32 atoms of a cell
+    the last 1..16 take 32, 16, 8, 4 or 2 lanes each (more than 16 take one each)."""
+    w = I.cell_count_gas(np.tile(np.arange(25, 57), 2))
+    with _gpu_system(w, precision) as s:
+        s.build_neighbours()
+        cg, lg = s.neighbours()
+    co, lo, m = oracle.neighbours(w.pos, w.box, w.potential.r_cut + w.skin, w.k_max, "brute")
+    assert m <= w.k_max
+    assert np.array_equal(cg, co)
+    assert _rows(cg, lg) == _rows(co, lo)
+    assert np.all(lg[np.arange(w.k_max)[None, :] >= cg[:, None]] == -1)
+
+
 # --------------------------------------------------------------------------- FP64 parity
 @pytest.mark.parametrize("name", ["fe2k", "fe_tables", "cu2k", "fec", "random", "fe_knots", "fec_knots"])
 def test_fp64_forces_energies_virial_match_oracle(name):

@@ -120,6 +120,28 @@ def test_link_cells_equal_brute_force(cells, n):
     assert _rows(c1, l1) == _rows(c2, l2)
 
 
+def test_cell_count_gas_fills_its_cells_as_prescribed_and_its_lists_agree():
+    """The list case for warp-wide lane groups: every link cell holds its prescribed count (each of
+    25..56 twice), so every remainder after a first 32 atoms occurs; on it the link-cell oracle
+    equals the brute-force definition."""
+    counts = np.tile(np.arange(25, 57), 2)
+    w = I.cell_count_gas(counts)
+    rl = w.potential.r_cut + w.skin
+    assert int(np.floor(w.box[0] / rl)) == 4
+    width = w.box / 4
+    c = np.floor(w.pos / width).astype(int)
+    assert c.min() >= 0 and c.max() <= 3
+    frac = w.pos / width - c
+    assert frac.min() >= 0.019 and frac.max() <= 0.981
+    assert np.array_equal(np.bincount(c[:, 0] + 4 * c[:, 1] + 16 * c[:, 2], minlength=64), counts)
+    assert set((counts - 32)[(counts > 32) & (counts <= 48)]) == set(range(1, 17))
+    c1, l1, m1 = oracle.neighbours(w.pos, w.box, rl, w.k_max, "brute")
+    c2, l2, m2 = oracle.neighbours(w.pos, w.box, rl, w.k_max, "cells")
+    assert m1 <= w.k_max and m1 == m2
+    assert np.array_equal(c1, c2)
+    assert _rows(c1, l1) == _rows(c2, l2)
+
+
 def test_neighbour_cutoff_is_strict_and_empty_box():
     box = np.array([20.0, 20.0, 20.0])
     pos = np.array([[1.0, 1.0, 1.0], [5.0, 1.0, 1.0], [1.0, 4.999999999, 1.0]])
