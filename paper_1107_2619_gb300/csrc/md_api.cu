@@ -11,6 +11,7 @@
 // A context holds one system or a batch of independent replicas (md_create_batch): the
 // replicas' atoms are stored back to back, each replica with its own box and link cells,
 // and one launch advances all of them.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -703,6 +704,7 @@ md_status create_common(md_ctx *ctx, const md_config *cfg, const md_potential *p
         const size_t npair = (size_t)ns * ns;
         std::vector<double4_32a> VP64(npair * nk * 2), F64((size_t)ns * nk), rv(nk), rp(nk);
         std::vector<float> VP32(npair * nk * 8);
+        std::vector<float4> D32;
         const size_t tl = 2 * (size_t)nk;
         for (int a = 0; a < ns; a++)
             for (int b = 0; b < ns; b++) {
@@ -716,6 +718,27 @@ md_status create_common(md_ctx *ctx, const md_config *cfg, const md_potential *p
                 cubic_rows(tv, nk, hr, rv.data());
                 cubic_rows(pot->tables + (npair + a * ns + b) * tl, nk, hr, rp.data());
                 const size_t base = (size_t)(a * ns + b) * nk;
+                if (ns == 1) {   // the force pass's derivative rows (see Pot::D32)
+                    auto scale = [&](const std::vector<double4_32a> &rw) {   // max |2 c2|, |3 c3| -> [2^14, 2^15)
+                        double m = 0.0;
+                        for (int k = 0; k < nk; k++) m = std::max(m, std::max(std::fabs(2.0 * rw[k].z), std::fabs(3.0 * rw[k].w)));
+                        return m > 0.0 ? std::ldexp(1.0, (int)std::floor(std::log2(m)) - 14) : 1.0;
+                    };
+                    auto pack = [](double a2, double a3) {   // (a2, a3) as binary16 in one 32-bit word
+                        const uint32_t u = (uint32_t)__half_as_ushort(__float2half_rn((float)a2)) |
+                                           ((uint32_t)__half_as_ushort(__float2half_rn((float)a3)) << 16);
+                        float f;
+                        std::memcpy(&f, &u, sizeof f);
+                        return f;
+                    };
+                    const double sv = scale(rv), sp = scale(rp);
+                    D32.resize(nk);
+                    for (int k = 0; k < nk; k++)
+                        D32[k] = make_float4((float)rv[k].y, (float)rp[k].y, pack(2.0 * rv[k].z / sv, 3.0 * rv[k].w / sv),
+                                             pack(2.0 * rp[k].z / sp, 3.0 * rp[k].w / sp));
+                    P.dsv = (float)sv;
+                    P.dsp = (float)sp;
+                }
                 for (int k = 0; k < nk; k++) {
                     VP64[(base + k) * 2] = rv[k];
                     VP64[(base + k) * 2 + 1] = rp[k];
@@ -737,6 +760,13 @@ md_status create_common(md_ctx *ctx, const md_config *cfg, const md_potential *p
         P.VP64 = dVP64;
         P.VP32 = dVP32;
         P.F64 = dF64;
+        if (!D32.empty()) {
+            float4 *dD32;
+            chk(dalloc(ctx, &dD32, D32.size()));
+            if (e != cudaSuccess) return fail(ctx, MD_ERR_OOM, "table allocation", e);
+            chk(cudaMemcpy(dD32, D32.data(), D32.size() * sizeof(float4), cudaMemcpyHostToDevice));
+            P.D32 = dD32;
+        }
     }
     if (pot->kind == MD_POT_KNOTS) {
         const int K = pot->n_knots, nf = 2 * ns * ns;

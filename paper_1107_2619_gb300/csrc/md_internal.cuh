@@ -65,6 +65,10 @@ struct Pot {
     const double4_32a *VP64;  // [((a*ns+b)*nk + k)*2 + {0: V, 1: phi_ab}]
     const double4_32a *VP32;  // [(a*ns+b)*nk + k], 8 floats
     const double4_32a *F64;   // [a*nk + k]
+    // one species: [k] derivative rows of the force pass (mixed, table in shared memory): c1 of V,
+    // c1 of phi, then (2 c2, 3 c3) of V and of phi as binary16 pairs scaled by 1/dsv and 1/dsp
+    const float4 *D32;
+    float dsv, dsp;
     // explicit knot sums (MD_POT_KNOTS): function t (V[a][b] = a*ns+b, phi[a][b] = ns*ns + a*ns+b)
     // has nkt terms (coefficient, radius) at K64/K32 + t*nkt; F_a = -A[a] sqrt(rho)
     int nkt;
@@ -188,6 +192,11 @@ constexpr size_t kSmemTableMax = 200 * 1024;
 constexpr size_t kSmemDynMax = 222 * 1024;
 constexpr int kCellsQueue = 64;   // cell walk: hit queue (16-bit stage slots) per warp, static shared
 constexpr size_t kSmemDynMaxCells = kSmemDynMax - 32 * kCellsQueue * sizeof(uint16_t);
+// 1: for one species the shared copy holds the force pass's derivative rows in place of the V
+// rows, so the force pass reads one row per pair instead of two.
+#ifndef MD_DTABLE
+#define MD_DTABLE 1
+#endif
 #ifndef MD_SMEM_TABLE
 #define MD_SMEM_TABLE 1
 #endif

@@ -10,6 +10,7 @@
 // error-free in an FP32 (hi, lo) pair rounded to FP64 before F(rho); F, F', kick, sums FP64.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <type_traits>
@@ -86,6 +87,15 @@ __device__ __forceinline__ void vp_row(const Pot &P, size_t idx, float (&v)[4], 
     row32(P.VP32, idx, v, p);
 }
 
+// d/dt of a table cubic from its derivative row: c1 + t (2 c2 + 3 c3 t), with (2 c2, 3 c3) packed
+// as a pair of binary16 values scaled by 1/s; below r_min the linear extension (c1).
+__device__ __forceinline__ float dtab(float c1, float packed, float s, float t, bool below) {
+    const unsigned u = __float_as_uint(packed);
+    const float a2 = __half2float(__ushort_as_half((unsigned short)(u & 0xffffu)));
+    const float a3 = __half2float(__ushort_as_half((unsigned short)(u >> 16)));
+    return below ? c1 : fmaf(s * t, fmaf(t, a3, a2), c1);
+}
+
 // ======================================================================= mixed precision
 // List entries between r_cut and r_list (the skin shell, about a tenth of a Cu row) contribute
 // nothing; MD_TABLE_SKIP=1 skips their table-row loads (the loads are predicated, the
@@ -127,7 +137,7 @@ struct Acc32 {
 
 // The scalar of one pair of the force pass: g = [V'(r) + F'_i phi'_{s_i s_j}(r) + F'_j phi'_{s_j s_i}(r)] / r
 // (the force on i is g d, d = r_j - r_i) and V(r), both zero at or beyond r_cut (no branch).
-template <int KIND, bool MULTI, bool SMT>
+template <int KIND, bool MULTI, bool SMT, bool ENERGY = true>
 __device__ __forceinline__ float pair_g32(const Pot &P, int si, int sj, float Fpi, float Fpj, float r2, float &V,
                                           unsigned &viol) {
     const bool inside = r2 < P.rc2f;
@@ -155,11 +165,31 @@ __device__ __forceinline__ float pair_g32(const Pot &P, int si, int sj, float Fp
         bool below;
         const int kr = knot_row((r - P.r_minf) * P.inv_drf, P.nk, t, below);
         viol += (below && inside) ? 1u : 0u;
-        float cv[4] = {0.f, 0.f, 0.f, 0.f}, cp[4] = {0.f, 0.f, 0.f, 0.f}, dVk, dab;
+        float dVk, dab, gk;
+        if constexpr (SMT && !MULTI && MD_DTABLE) {
+            // one row per pair: the derivative row in shared memory; V(r) itself only on the energy
+            // step, from the global table
+            extern __shared__ float4 sm_table_f4[];
+            float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (!MD_TABLE_SKIP || inside) d = sm_table_f4[kr];
+            dVk = dtab(d.x, d.z, P.dsv, t, below);
+            dab = dtab(d.y, d.w, P.dsp, t, below);
+            V = 0.f;
+            if (ENERGY) {
+                float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (inside) c = __ldg(reinterpret_cast<const float4 *>(P.VP32 + kr));
+                float unused;
+                V = cubic(t, c.x, c.y, c.z, c.w, below, unused);
+            }
+            gk = fmaf(Fpi + Fpj, dab, dVk);
+            gg = gk * P.inv_drf;
+            V = inside ? V : 0.f;
+            return inside ? gg * rinv : 0.f;
+        }
+        float cv[4] = {0.f, 0.f, 0.f, 0.f}, cp[4] = {0.f, 0.f, 0.f, 0.f};
         if (!MD_TABLE_SKIP || inside) vp_row<SMT, MULTI>(P, (size_t)(si * P.ns + sj) * P.nk + kr, cv, cp);
         V = cubic(t, cv[0], cv[1], cv[2], cv[3], below, dVk);
         cubic(t, cp[0], cp[1], cp[2], cp[3], below, dab);
-        float gk;
         if (MULTI) {
             float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
             if (!MD_TABLE_SKIP || inside) c = phi_row<SMT, MULTI>(P, (size_t)(sj * P.ns + si) * P.nk + kr);
@@ -181,7 +211,8 @@ template <int KIND, bool MULTI, bool ENERGY, bool SMT>
 __device__ __forceinline__ void pair32(const Pot &P, int si, int sj, float Fpi, float Fpj, float dx, float dy,
                                        float dz, Acc32 &a, unsigned &viol) {
     float V;
-    const float gr = pair_g32<KIND, MULTI, SMT>(P, si, sj, Fpi, Fpj, fmaf(dx, dx, fmaf(dy, dy, dz * dz)), V, viol);
+    const float gr =
+        pair_g32<KIND, MULTI, SMT, ENERGY>(P, si, sj, Fpi, Fpj, fmaf(dx, dx, fmaf(dy, dy, dz * dz)), V, viol);
     a.fx = fmaf(gr, dx, a.fx);
     a.fy = fmaf(gr, dy, a.fy);
     a.fz = fmaf(gr, dz, a.fz);

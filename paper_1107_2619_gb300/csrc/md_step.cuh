@@ -151,7 +151,14 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? MD_STEP_MIN_BLOCKS : 1)
     const long long stride = (long long)nb * NT;
     if (SMT) {
         const float4 *src = reinterpret_cast<const float4 *>(P.VP32);
-        for (int q = threadIdx.x; q < 2 * P.nk; q += NT) sm_table_f4[(q & 1) * P.nk + (q >> 1)] = __ldg(src + q);
+        if constexpr (!MULTI && MD_DTABLE) {   // derivative rows, then the phi rows
+            for (int q = threadIdx.x; q < P.nk; q += NT) {
+                sm_table_f4[q] = __ldg(P.D32 + q);
+                sm_table_f4[P.nk + q] = __ldg(src + 2 * q + 1);
+            }
+        } else {
+            for (int q = threadIdx.x; q < 2 * P.nk; q += NT) sm_table_f4[(q & 1) * P.nk + (q >> 1)] = __ldg(src + q);
+        }
         __syncthreads();
     }
     const bool lead = blockIdx.x == 0 && threadIdx.x == 0;

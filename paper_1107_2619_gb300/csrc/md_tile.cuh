@@ -310,7 +310,7 @@ __device__ __forceinline__ void force_half_item(const Atoms &A, const Pot &P, co
             const float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
             float V;
             const float gr =
-                ps::pair_g32<KIND, false, SMT>(P, 0, 0, pi.w, pj.w, fmaf(dx, dx, fmaf(dy, dy, dz * dz)), V, viol);
+                ps::pair_g32<KIND, false, SMT, ENERGY>(P, 0, 0, pi.w, pj.w, fmaf(dx, dx, fmaf(dy, dy, dz * dz)), V, viol);
             const float ax = gr * dx, ay = gr * dy, az = gr * dz;
             fx += ax;
             fy += ay;
