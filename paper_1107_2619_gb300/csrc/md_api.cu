@@ -705,6 +705,7 @@ md_status create_common(md_ctx *ctx, const md_config *cfg, const md_potential *p
         std::vector<double4_32a> VP64(npair * nk * 2), F64((size_t)ns * nk), rv(nk), rp(nk);
         std::vector<float> VP32(npair * nk * 8);
         std::vector<float4> D32;
+        std::vector<float> V0;
         const size_t tl = 2 * (size_t)nk;
         for (int a = 0; a < ns; a++)
             for (int b = 0; b < ns; b++) {
@@ -733,6 +734,8 @@ md_status create_common(md_ctx *ctx, const md_config *cfg, const md_potential *p
                     };
                     const double sv = scale(rv), sp = scale(rp);
                     D32.resize(nk);
+                    V0.resize(nk);
+                    for (int k = 0; k < nk; k++) V0[k] = (float)rv[k].x;
                     for (int k = 0; k < nk; k++)
                         D32[k] = make_float4((float)rv[k].y, (float)rp[k].y, pack(2.0 * rv[k].z / sv, 3.0 * rv[k].w / sv),
                                              pack(2.0 * rp[k].z / sp, 3.0 * rp[k].w / sp));
@@ -764,8 +767,13 @@ md_status create_common(md_ctx *ctx, const md_config *cfg, const md_potential *p
             float4 *dD32;
             chk(dalloc(ctx, &dD32, D32.size()));
             if (e != cudaSuccess) return fail(ctx, MD_ERR_OOM, "table allocation", e);
+            float *dV0;
+            chk(dalloc(ctx, &dV0, V0.size()));
+            if (e != cudaSuccess) return fail(ctx, MD_ERR_OOM, "table allocation", e);
             chk(cudaMemcpy(dD32, D32.data(), D32.size() * sizeof(float4), cudaMemcpyHostToDevice));
+            chk(cudaMemcpy(dV0, V0.data(), V0.size() * sizeof(float), cudaMemcpyHostToDevice));
             P.D32 = dD32;
+            P.V0 = dV0;
         }
     }
     if (pot->kind == MD_POT_KNOTS) {

@@ -68,6 +68,7 @@ struct Pot {
     // one species: [k] derivative rows of the force pass (mixed, table in shared memory): c1 of V,
     // c1 of phi, then (2 c2, 3 c3) of V and of phi as binary16 pairs scaled by 1/dsv and 1/dsp
     const float4 *D32;
+    const float *V0;          // one species: [k] c0 of the V rows (V itself on the energy step)
     float dsv, dsp;
     // explicit knot sums (MD_POT_KNOTS): function t (V[a][b] = a*ns+b, phi[a][b] = ns*ns + a*ns+b)
     // has nkt terms (coefficient, radius) at K64/K32 + t*nkt; F_a = -A[a] sqrt(rho)

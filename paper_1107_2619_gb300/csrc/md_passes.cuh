@@ -87,13 +87,16 @@ __device__ __forceinline__ void vp_row(const Pot &P, size_t idx, float (&v)[4], 
     row32(P.VP32, idx, v, p);
 }
 
-// d/dt of a table cubic from its derivative row: c1 + t (2 c2 + 3 c3 t), with (2 c2, 3 c3) packed
-// as a pair of binary16 values scaled by 1/s; below r_min the linear extension (c1).
-__device__ __forceinline__ float dtab(float c1, float packed, float s, float t, bool below) {
+// The pair (2 c2, 3 c3) of a derivative row, packed as two binary16 values scaled by 1/s.
+__device__ __forceinline__ float2 dtab_pair(float packed) {
     const unsigned u = __float_as_uint(packed);
-    const float a2 = __half2float(__ushort_as_half((unsigned short)(u & 0xffffu)));
-    const float a3 = __half2float(__ushort_as_half((unsigned short)(u >> 16)));
-    return below ? c1 : fmaf(s * t, fmaf(t, a3, a2), c1);
+    return make_float2(__half2float(__ushort_as_half((unsigned short)(u & 0xffffu))),
+                       __half2float(__ushort_as_half((unsigned short)(u >> 16))));
+}
+// d/dt of a table cubic from its derivative row: c1 + t (2 c2 + 3 c3 t); below r_min the linear
+// extension (c1).
+__device__ __forceinline__ float dtab(float c1, float2 a, float s, float t, bool below) {
+    return below ? c1 : fmaf(s * t, fmaf(t, a.y, a.x), c1);
 }
 
 // ======================================================================= mixed precision
@@ -168,18 +171,18 @@ __device__ __forceinline__ float pair_g32(const Pot &P, int si, int sj, float Fp
         float dVk, dab, gk;
         if constexpr (SMT && !MULTI && MD_DTABLE) {
             // one row per pair: the derivative row in shared memory; V(r) itself only on the energy
-            // step, from the global table
+            // step, with c0 from a small global table
             extern __shared__ float4 sm_table_f4[];
             float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
             if (!MD_TABLE_SKIP || inside) d = sm_table_f4[kr];
-            dVk = dtab(d.x, d.z, P.dsv, t, below);
-            dab = dtab(d.y, d.w, P.dsp, t, below);
+            const float2 av = dtab_pair(d.z);
+            dVk = dtab(d.x, av, P.dsv, t, below);
+            dab = dtab(d.y, dtab_pair(d.w), P.dsp, t, below);
             V = 0.f;
-            if (ENERGY) {
-                float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (inside) c = __ldg(reinterpret_cast<const float4 *>(P.VP32 + kr));
-                float unused;
-                V = cubic(t, c.x, c.y, c.z, c.w, below, unused);
+            if (ENERGY) {   // V = c0 + t (c1 + t (c2 + t c3)), c2 and c3 from the derivative row
+                const float c0 = inside ? __ldg(P.V0 + kr) : 0.f;
+                const float c2 = 0.5f * P.dsv * av.x, c3 = (1.f / 3.f) * P.dsv * av.y;
+                V = below ? fmaf(t, d.x, c0) : fmaf(t, fmaf(t, fmaf(t, c3, c2), d.x), c0);
             }
             gk = fmaf(Fpi + Fpj, dab, dVk);
             gg = gk * P.inv_drf;
