@@ -63,9 +63,10 @@ __device__ __forceinline__ float4 phi_half32(const double4_32a *tab, size_t idx)
 
 // The same rows from a copy of the table of species pair (0, 0) in the kernel's dynamic shared
 // memory (SMT; rows of other pairs, idx >= nk, come from the global table).  The copy is split:
-// the nk float4 rows of V coefficients, then the nk rows of phi coefficients, so that the rows a
-// warp reads at random spread over all eight 16-byte bank groups (interleaved V/phi rows would
-// put every phi row in four of them).
+// nk float4 rows, then the nk rows of phi coefficients, so that the rows a warp reads at random
+// spread over all eight 16-byte bank groups (interleaved V/phi rows would put every phi row in
+// four of them).  The first nk rows hold the V coefficients with two species (vp_row) and, with
+// one, the force pass's derivative rows (Pot::D32, read in pair_g32).
 template <bool SMT, bool MULTI>
 __device__ __forceinline__ float4 phi_row(const Pot &P, size_t idx) {
     if (SMT && (!MULTI || idx < (size_t)P.nk)) {
