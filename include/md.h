@@ -113,7 +113,10 @@ typedef struct {
     int32_t rebuild_every; /* `nbrupdate`: rebuild every n steps; 0 = only when needed */
     double dt_fs;          /* `deltat` */
     int32_t precision;     /* MD_PREC_FP64, or MD_PREC_MIXED (FP32 pair/density terms,
-                              FP64 positions, velocities, density sum and reductions) */
+                              FP64 positions, velocities, density sum and reductions; with
+                              one species and knot tables the force pass takes the quadratic
+                              and cubic coefficients of each table cubic's derivative as
+                              binary16, scaled per function by a power of two) */
     int32_t strict_skin;   /* 1: moving > skin/2 between scheduled rebuilds is MD_ERR_SKIN;
                               0: it triggers a rebuild */
     double strain_rate_zz; /* 1/s; each step the box z edge and all z coordinates are
