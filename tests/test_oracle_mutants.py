@@ -1,9 +1,9 @@
 """The oracle's pins catch plausible mistakes in the oracle.
 
 Each case plants one mistake in a copy of oracle/moldy_oracle.c (a dropped term, a wrong sign,
-a transposed index, a wrong rounding or comparison), compiles it with the oracle's own flags,
-points the oracle's Python wrapper at it, and runs the pin that should catch the mistake: the pin
-must fail.  An unmodified copy, built and loaded the same way, passes the same pins.  The oracle
+a transposed index, a wrong rounding, comparison or loop bound, a wrong function), compiles it
+with the oracle's own flags, points the oracle's Python wrapper at it, and runs the pin that
+should catch the mistake: the pin must fail.  An unmodified copy, built and loaded the same way, passes the same pins.  The oracle
 itself is never modified: the copies live in pytest's temporary directory.
 """
 import os
@@ -16,6 +16,8 @@ from oracle import build as oracle_build
 
 sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
 import test_oracle_pins as pins  # noqa: E402
+import test_surrogate_pins as sur_pins  # noqa: E402
+import test_thermostat_pins as nvt_pins  # noqa: E402
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "moldy_oracle.c")
 
@@ -60,6 +62,22 @@ MUTANTS = [
      "vel[3 * i + c] += half * force[3 * i + c] * im;\n                pos[3 * i + c]",
      "vel[3 * i + c] += dt_fs * force[3 * i + c] * im;\n                pos[3 * i + c]",
      [pins.test_velocity_verlet_conserves_energy_with_dt2_error, pins.test_velocity_verlet_is_time_reversible]),
+    ("link-cell stencil missing its upper layer of cells",
+     "for (int dz = -1; dz <= 1; dz++)\n            for (int dy = -1; dy <= 1; dy++)",
+     "for (int dz = -1; dz <= 0; dz++)\n            for (int dy = -1; dy <= 1; dy++)",
+     [lambda: pins.test_link_cells_equal_brute_force((3, 4, 5), 700)]),
+    ("Nose-Hoover friction with the wrong sign",
+     "double s = exp(-thermo[0] * h);", "double s = exp(thermo[0] * h);",
+     [nvt_pins.test_extended_energy_is_conserved_with_dt2_error, nvt_pins.test_temperature_settles_at_the_target]),
+    ("surrogate basis derivative without its Gaussian term",
+     "db[k] = e * (dfc - a / w2 * fc);", "db[k] = e * dfc;",
+     [sur_pins.test_surrogate_forces_are_minus_energy_gradient]),
+    ("surrogate backward pass through SiLU instead of its derivative",
+     "d1[p] = s * orc_dsilu(z1[p]);", "d1[p] = s * orc_silu(z1[p]);",
+     [sur_pins.test_mlp_energy_and_input_gradient_match_torch_autograd]),
+    ("surrogate force without the neighbour's gradient",
+     "c += (grad[m * sp->nb + k] + grad[j * sp->nb + k]) * db[k];", "c += grad[m * sp->nb + k] * db[k];",
+     [sur_pins.test_surrogate_forces_are_minus_energy_gradient]),
 ]
 
 
