@@ -70,3 +70,20 @@ def test_binary16_derivative_coefficients_stay_far_inside_the_mixed_bound():
     err = np.abs(rounded - exact).max()
     assert 0.0 < err <= 0.1 * MIXED_FORCE_TOL * fmax
     assert err <= 2e-5
+
+
+def test_binary16_scaling_bound_over_any_dynamic_range():
+    """The scale puts the largest magnitude in [2^14, 2^15): every coefficient is then within
+    2^-11 of itself (times 1 + 2^-12 for the rounding to FP32 on the way), or within 2^-25 of the
+    scale where it underflows, over twelve decades of magnitude."""
+    u = I.random_uniform(41, 1, 200000)
+    a = np.sign(u - 0.5) * 10.0 ** (-12.0 * I.random_uniform(41, 2, 200000))
+    a2, a3 = _binary16(a[:100000], a[100000:])
+    q = np.concatenate([a2, a3])
+    scale = 2.0 ** (np.floor(np.log2(np.abs(a).max())) - 14)
+    assert 2.0 ** 14 <= np.abs(a).max() / scale < 2.0 ** 15
+    err = np.abs(q - a)
+    rel = 2.0 ** -11 * (1.0 + 2.0 ** -12)
+    assert np.all(err <= np.maximum(rel * np.abs(a), 2.0 ** -25 * scale))
+    normal = np.abs(a) >= 2.0 ** -14 * scale
+    assert normal.sum() > 50000 and np.all(err[normal] <= rel * np.abs(a[normal]))
