@@ -5,12 +5,16 @@ cubic tables (cutoff 2a), 300 K seeded velocities, velocity-Verlet NVE with dt =
 0.3 Å skin and a list rebuild whenever an atom has moved more than skin/2.  One step is the
 whole path: half kick + drift + skin check, [link-cell binning, sort, list build], density
 pass, force pass + half kick.  All steps of one md_step call run in one persistent launch.
-The headline is the mixed path (FP32 pair/density terms, FP64 positions, integration,
-density sum and reductions); the FP64 path is timed beside it.  Extra lines (not the
-headline): bcc Fe 2,000 atoms (FP64), 256 bcc Fe replicas of 2,000-54,000 atoms in one
-batch under a captured CUDA graph, bcc Fe-C 4.2M atoms with a z strain ramp, and the learned
-surrogate on 1,024,000-atom bcc Fe next to FP64 and mixed EAM (force RMSE, ms per step,
-NVE drift).
+The headline is the FP64 path (the paper's arithmetic), with its roofline against the FP64
+FMA rate measured in the same run by the library's own FMA-chain kernel; the mixed path (FP32
+pair/density terms, FP64 positions, integration, density sum and reductions) is reported in
+the same line as its speedup over FP64 at its stated force error and NVE drift.  The other
+workloads print one line each ("extra <name>: {...}") before the headline line: bcc Fe 2,000
+atoms (FP64), 256 bcc Fe replicas of 2,000-54,000 atoms in one batch under a captured CUDA
+graph, bcc Fe-C 4.2M atoms with a z strain ramp, the table-versus-explicit potential
+comparison, the neighbour walks, and the learned surrogate on 1,024,000-atom bcc Fe next to
+FP64 and mixed EAM (force RMSE, ms per step, NVE drift); a summary of the surrogate line is
+carried in the headline line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-extras]
   python bench.py --surrogate-only            # the surrogate comparison alone
@@ -38,7 +42,7 @@ import numpy as np  # noqa: E402
 
 from paper_1107_2619_gb300 import inputs as I  # noqa: E402
 
-METRIC = "atom-steps/s (EAM force+integrate, 1 GB300)"
+METRIC = "atom-steps/s (EAM force+integrate, 1 GB300) & HBM roofline fraction; surrogate speedup at force err"
 UNIT = "atom-steps/s"
 CELLS = 50
 SEED = 2
@@ -68,20 +72,19 @@ def _peaks():
 # the two cubic derivatives 12, the F' combination 3, scalings 2, force 6).  Entries in the skin
 # shell stop after r^2: 17 per pass.
 FP64_FLOP_IN, FP64_FLOP_SHELL = 69.0, 34.0
-FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 (no measured figure in MEASURED_PEAKS.json)
 
 
-def fp64_pipe(sum_counts, w, ms_per_step):
-    """FP64-pipe fraction of the FP64 path by the per-entry model above; the share of list
+def fp64_flop_per_step(sum_counts, w):
+    """FP64 flop of one step of the FP64 passes by the per-entry model above; the share of list
     entries inside r_cut is taken as (r_cut / r_list)^3 (uniform density)."""
     rc = float(w.potential.r_cut)
     f_in = (rc / (rc + w.skin)) ** 3
-    flop = sum_counts * (f_in * FP64_FLOP_IN + (1.0 - f_in) * FP64_FLOP_SHELL)
-    tflops = flop / (ms_per_step * 1e-3) / 1e12
-    return {"flop_per_step": flop, "achieved_tflops": tflops, "peak_tflops": FP64_PEAK_TFLOPS,
-            "frac": tflops / FP64_PEAK_TFLOPS, "peak_source": "nominal",
-            "model": "69 flop per list entry inside r_cut (both passes), 34 in the skin shell; "
-                     "share inside r_cut (r_cut/r_list)^3"}
+    return sum_counts * (f_in * FP64_FLOP_IN + (1.0 - f_in) * FP64_FLOP_SHELL)
+
+
+def fp64_peak(md, stream, repeats=3, iters=20000):
+    """Best of `repeats` runs of the library's FP64 FMA-chain kernel (md_measure_fp64_peak)."""
+    return max(md.md_measure_fp64_peak(iters, stream)[0] for _ in range(repeats))
 
 
 def _capture(kernel):
@@ -100,10 +103,10 @@ def _capture(kernel):
         return None
 
 
-def _traffic(kernel, n_steps):
+def _traffic(kernel, n_atoms, n_steps):
     """DRAM bytes per launch from the committed ncu capture (per atom-step, scaled to this launch)."""
     rec = _capture(kernel)
-    return None if rec is None else float(rec["bytes_per_atom_step"]) * 4 * CELLS ** 3 * n_steps
+    return None if rec is None else float(rec["bytes_per_atom_step"]) * n_atoms * n_steps
 
 
 class Clocks:
@@ -222,16 +225,18 @@ def run_reference(args):
 
 
 def step_bytes(n, sum_counts, precision):
-    """Algorithmic HBM bytes of one step of the persistent kernel (no rebuild), neighbour
-    gathers counted as L2 hits (atoms are in cell order):
-      density: list 4/neighbour + count 4 + own position 16 (32 FP64) + rho, F', E_i 24 + copy 16 (32)
-      force:   list 4/neighbour + count 4 + own copy 16 (32) + force write 32 + velocity r/w 64
-               + fused next half kick and drift: position r/w 64 + reference 32 + species 4
-               + FP32 wrapped copy 16."""
-    pos = 16 if precision == "mixed" else 32
-    density = 4 * sum_counts + (4 + pos + 24 + pos) * n
-    force = 4 * sum_counts + (4 + pos + 32 + 64 + 64 + 32 + 4 + 16) * n
-    return density + force, density, force
+    """Algorithmic HBM bytes of one step (no rebuild) by the per-atom-step model of the hot-path
+    scope (neighbour gathers counted as L2 hits: atoms are in cell order), 8K + 170 for the
+    mixed path and 8K + 184 for FP64, K list entries per atom:
+      FP64:  list 2 x 4K + own position 2 x 24 + F' write and read 16 + force 24 + velocity
+             Verlet position and velocity read and write 96;
+      mixed: list 2 x 4K + the FP32 copy (16 written, 2 x 16 read) in place of the own
+             positions + F' 16 + force 12 + velocity Verlet 96 ... = 8K + 170.
+    The state the kernel actually moves is padded (double4 and float4 records), so its DRAM
+    traffic (ncu) runs above this model."""
+    per_atom = 170 if precision == "mixed" else 184
+    total = 8 * sum_counts + per_atom * n
+    return total, 4 * sum_counts + 0.5 * per_atom * n, 4 * sum_counts + 0.5 * per_atom * n
 
 
 REBUILD_PARTS = ("bin", "tile_sums", "top_scan", "apply", "scatter", "cell_sort", "gather", "copyback", "list")
@@ -325,13 +330,17 @@ def run_ours(args):
                                            for k in ("kick", "rebuild", "density", "force")}}))
         return 0
 
-    # end to end through the C ABI with host buffers: state in, one step, state and energies out
+    # FP64 FMA rate of this GPU (the denominator of the FP64 path's roofline), measured now
+    fp64_tflops = fp64_peak(md, stream.cuda_stream)
+
+    # end to end through the C ABI with host buffers (FP64 path): state in, one step, state and
+    # energies out
     pin = lambda shape: torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
     hp, hv, hf = pin((n, 3)), pin((n, 3)), pin((n, 3))
-    s = md.System(w, precision="mixed", lanes_per_atom=res["mixed"]["lanes"])
+    s = md.System(w, precision="fp64", lanes_per_atom=res["fp64"]["lanes"])
     s.eam_forces()
     s.get(md.MD_GET_POS, hp), s.get(md.MD_GET_VEL, hv), s.get(md.MD_GET_FORCE, hf)
-    k_e2e = max(3, min(args.steps, 200))
+    k_e2e = max(3, min(args.steps, 100))
     for _ in range(3):
         s.step_io(1, hp, hv, hf, hp, hv, hf)
     barrier()
@@ -342,9 +351,9 @@ def run_ours(args):
     s.close()
     e2e = {"value": world * n * k_e2e / t, "unit": UNIT, "h2d_bytes_per_step": 72 * n,
            "d2h_bytes_per_step": 72 * n + C.sizeof(md.md_energies), "steps": k_e2e,
-           "note": "each step one md_step_io call: positions, velocities and forces in from pinned host "
-                   "buffers, md_step(1), the three arrays back into them and the energies, one "
-                   "synchronisation"}
+           "note": "FP64 path; each step one md_step_io call: positions, velocities and forces in from "
+                   "pinned host buffers, md_step(1), the three arrays back into them and the energies, "
+                   "one synchronisation"}
 
     extras = {}
     if not args.no_extras:
@@ -359,14 +368,22 @@ def run_ours(args):
         return 0
 
     hbm_peak, peak_src = _peaks()
-    r = res["mixed"]
-    sum_counts = float(r["counts"].sum())
-    per_step, dens_b, force_b = step_bytes(n, sum_counts, "mixed")
-    launch_bytes = per_step * args.steps
-    achieved = launch_bytes / (r["ms"] * 1e-3) / 1e9
-    p = r["prof"]
-    phase = {k: p["ms_" + k] / max(1, p["n_" + k]) for k in ("kick", "rebuild", "density", "force")}
+    sum_counts = float(res["fp64"]["counts"].sum())
 
+    def phases(q):
+        p = q["prof"]
+        return {k: round(p["ms_" + k] / max(1, p["n_" + k]), 4) for k in ("kick", "rebuild", "density", "force")}
+
+    def hbm(q, precision):
+        b = step_bytes(n, sum_counts, precision)[0] * args.steps
+        a = b / (q["ms"] * 1e-3) / 1e9
+        return {"achieved": a, "peak": hbm_peak, "unit": "GB/s", "frac": a / hbm_peak,
+                "model": "8K + 170 B per atom-step" if precision == "mixed" else "8K + 184 B per atom-step",
+                "traffic": _traffic("k_step_" + precision, n, args.steps), "peak_source": peak_src}
+
+    r64, r32 = res["fp64"], res["mixed"]
+    flop = fp64_flop_per_step(sum_counts, w) * args.steps
+    achieved = flop / (r64["ms"] * 1e-3) / 1e12
     f64, f32 = snapshot["fp64"], snapshot["mixed"]
     ferr = np.abs(f32 - f64)
     cpu = None
@@ -382,42 +399,42 @@ def run_ours(args):
         except Exception as exc:  # the CPU leg must not hide the GPU line
             cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle", "sample": f"failed: {exc}"}
 
-    def path_summary(pr):
-        q = res[pr]
-        de = (q["e1"]["te"] - q["e0"]["te"]) / n
-        qp = q["prof"]
-        out = {"value": job_value(n, world, args.steps, q["ms"]), "ms_per_step": q["ms"] / args.steps,
-                "nve_drift_ev_per_atom": de, "steps_timed": args.steps, "lanes_per_atom": q["lanes"],
-                "rebuilds_in_timed_region": q["e1"]["n_rebuilds"] - q["e0"]["n_rebuilds"],
-                "phase_ms_per_step_profiled_repeat": {k: qp["ms_" + k] / max(1, qp["n_" + k])
-                                                       for k in ("kick", "rebuild", "density", "force")},
-                "rebuild_ms_per_rebuild": rebuild_parts(qp)}
-        if pr == "fp64":
-            out["fp64_pipe"] = fp64_pipe(sum_counts, w, q["ms"] / args.steps)
-        return out
-
+    mixed = {"value": job_value(n, world, args.steps, r32["ms"]), "ms_per_step": r32["ms"] / args.steps,
+             "dtype": "f32+f64", "speedup_vs_fp64": r64["ms"] / r32["ms"],
+             "force_err_vs_fp64_ev_per_a": {"max": float(ferr.max()), "rms": float(np.sqrt((ferr ** 2).mean())),
+                                            "max_force": float(np.abs(f64).max())},
+             "nve_drift_ev_per_atom": (r32["e1"]["te"] - r32["e0"]["te"]) / n,
+             "lanes_per_atom": r32["lanes"], "phase_ms": phases(r32), "roofline": hbm(r32, "mixed")}
     line = {
-        "metric": METRIC, "value": job_value(n, world, args.steps, r["ms"]), "unit": UNIT,
-        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
-        "data": "synthetic", "config": _config("mixed: FP32 pair/density terms, FP64 integration and sums"),
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak, "traffic": _traffic("k_step_mixed", args.steps),
-                     "limiter": (_capture("k_step_mixed") or {}).get("limiter"),
-                     "kernel": "k_step (persistent: all phases of all K steps in one launch)",
-                     "algorithmic_bytes_per_launch": launch_bytes, "avg_launch_ms": r["ms"],
-                     "peak_source": peak_src, "rebuild_bytes": "not counted (list builds are extra work)",
-                     "phases": {"density": {"ms": phase["density"], "GB/s": dens_b / (phase["density"] * 1e6)},
-                                "force": {"ms": phase["force"], "GB/s": force_b / (phase["force"] * 1e6)}}},
-        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": r["launches"], "clocks": r["clocks"],
-        "mixed_path": path_summary("mixed"), "fp64_path": path_summary("fp64"),
-        "mixed_vs_fp64_force_error_ev_per_a": {"state": "positions after the mixed run's timed steps",
-                                               "max": float(ferr.max()),
-                                               "rms": float(np.sqrt((ferr ** 2).mean())),
-                                               "max_force": float(np.abs(f64).max())},
+        "metric": METRIC, "value": job_value(n, world, args.steps, r64["ms"]), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": r64["ms"] / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": _config("fp64: every pair term, sum, integration and reduction in FP64"),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_tflops, "unit": "TFLOP/s",
+                     "frac": achieved / fp64_tflops, "traffic": _traffic("k_step_fp64", n, args.steps),
+                     "kernel": "k_step (persistent: all phases of all K steps in one launch), FP64 pipe",
+                     "peak_source": "measured in this run: md_measure_fp64_peak (FP64 FMA chains, CUDA events)",
+                     "flop_model": "69 FP64 flop per list entry inside r_cut over both passes, 34 in the skin "
+                                   "shell (an FMA counts 2)",
+                     "flop_per_launch": flop, "avg_launch_ms": r64["ms"], "hbm": hbm(r64, "fp64")},
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": r64["launches"], "clocks": r64["clocks"],
+        "nve_drift_ev_per_atom": (r64["e1"]["te"] - r64["e0"]["te"]) / n,
+        "lanes_per_atom": r64["lanes"], "phase_ms": phases(r64),
+        "rebuilds_in_timed_region": r64["e1"]["n_rebuilds"] - r64["e0"]["n_rebuilds"],
         "neighbours_per_atom": sum_counts / n,
-        "extras": extras,
+        "mixed": mixed,
     }
+    sur = extras.get("surrogate_fe_1m") if isinstance(extras, dict) else None
+    if sur and "paths" in sur:
+        p = sur["paths"]
+        line["surrogate"] = {
+            "workload": "bcc Fe 1,024,000 atoms, 600 K", "bf16_ms_per_step": p["surrogate_bf16"]["ms_per_step"],
+            "speedup_vs_eam_fp64": sur["speedup_surrogate_bf16_over_eam_fp64"],
+            "speedup_vs_eam_mixed": sur["speedup_surrogate_bf16_over_eam_mixed"],
+            "force_rmse_ev_per_a": p["surrogate_bf16"]["force_rmse_vs_fp64_ev_per_a"],
+            "nve_drift_ev_per_atom": p["surrogate_bf16"]["nve_drift_ev_per_atom"]}
+    for name, rec in (extras.items() if isinstance(extras, dict) else []):
+        print(f"extra {name}: " + json.dumps(rec), flush=True)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -438,10 +455,7 @@ def run_extras(torch, md, stream, barrier, max_over_ranks, world):
                         "steps": 100, "ms_per_step": ms / 100, "value": job_value(w.n_atoms, world, 100, ms)}
     s.close()
     # 256 replicas, n ~ U{10..30}, T ~ U[300, 1200] K, seeds 3000 + r, mixed, graph, 500 steps
-    u = I.random_uniform(3000, 11, 512)
-    sizes = (10 + np.floor(u[:256] * 21)).astype(int)
-    temps = 300.0 + 900.0 * u[256:]
-    ws = [I.bcc_fe(int(nc), seed=3000 + r, temperature=float(t)) for r, (nc, t) in enumerate(zip(sizes, temps))]
+    ws, temps = I.fe_replicas()
     b = md.Batch(ws, precision="mixed", stream=stream.cuda_stream)
     b.eam_forces()
     lanes = b.tune()

@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define MD_ABI_VERSION 3
+#define MD_ABI_VERSION 4
 
 typedef struct md_ctx md_ctx; /* opaque, owned by the library */
 
@@ -196,7 +196,11 @@ enum {
     MD_GET_DF = 5,        /* double [N]: F'(rho_i) */
     MD_GET_NBR_COUNT = 6, /* int32 [N]: neighbours of each atom (may exceed k_max on overflow) */
     MD_GET_NBR_LIST = 7,  /* int32 [N][k_max]: neighbour atom ids, unused slots -1, order unspecified */
-    MD_GET_SPECIES = 8    /* int32 [N] */
+    MD_GET_SPECIES = 8,   /* int32 [N] */
+    MD_GET_IMAGE = 9      /* double [N][3]: the coordinates the force passes take, in the periodic
+                             image of the last list build (wrapped into the box at the build and
+                             followed continuously since): the FP32 copy of the mixed path converted
+                             exactly to double, or the FP64 copy of the FP64 path (§2.2) */
 };
 
 /* Library ABI version (MD_ABI_VERSION). */
@@ -362,12 +366,15 @@ md_status md_neighbours_noalloc(const double *pos, int64_t n_atoms, const double
  * (length dt/2) before and after each velocity-Verlet step:
  *   pi += (dt/4)(2 KE - g kT)/Q;  v *= exp(-pi dt/2);  xi += pi dt/2;  pi += (dt/4)(2 KE' - g kT)/Q
  * (KE' after the scaling).  H' = KE + U + Q pi^2/2 + g k_B T xi is conserved.
- *   on: 1 = thermostat each replica r at t_kelvin[r] (K) with inertia q_ev_fs2[r] (eV fs^2; Q =
- *       g k_B T tau^2 for a relaxation time tau), starting from pi = xi = 0; 0 = plain NVE (the
- *       thermostat state is kept).  Host arrays of n_replicas, copied.
- * MD_ERR_STATE for a surrogate context.  md_energy's te stays KE + U (§2.1: the reported total
+ *   on: 1 = thermostat each replica r at t_kelvin[r] (K, > 0) with relaxation time tau_fs[r]
+ *       (fs, > 0), starting from pi = xi = 0; the library sets the thermal inertia
+ *       Q = g k_B T tau^2 (eV fs^2, read back with md_get_thermostat).  0 = plain NVE (the
+ *       thermostat state is kept; t_kelvin and tau_fs may be NULL).  Host arrays of n_replicas,
+ *       copied.
+ * MD_ERR_ARG for a T or tau that is not positive and finite, or a Q that overflows; MD_ERR_STATE
+ * for a surrogate context.  md_energy's te stays KE + U (§2.1: the reported total
  * energy excludes the thermostat's degree of freedom). */
-md_status md_set_thermostat(md_ctx *ctx, int32_t on, const double *t_kelvin, const double *q_ev_fs2);
+md_status md_set_thermostat(md_ctx *ctx, int32_t on, const double *t_kelvin, const double *tau_fs);
 
 /* Thermostat state per replica into out[n_replicas][4] (host): pi (1/fs), xi, Q (eV fs^2) and
  * the conserved H' (eV). */
@@ -449,6 +456,14 @@ md_status md_sur_loss_grad(md_ctx *ctx, int32_t rep_begin, int32_t rep_end, doub
  * step count) carries over between calls. */
 md_status md_sur_train(md_ctx *ctx, int32_t n_iter, int32_t rep_begin, int32_t rep_end, int32_t batch_reps,
                        double lr, double w_e, double w_f, uint64_t seed, double *loss);
+
+/* Measurement helper (the paper has no counterpart): the FP64 fused multiply-add rate of the
+ * current device, from one launch of independent FMA chains (2 flop each) filling every SM,
+ * timed with CUDA events on `stream` (cudaStream_t or NULL) after one short warm-up launch.
+ * iters = FMA iterations per chain (each thread runs 8 chains).  *tflops = achieved TFLOP/s,
+ * *ms (nullable) = the timed launch's duration.  Synchronises the stream.  MD_ERR_ARG for
+ * iters < 1 or a NULL tflops; MD_ERR_CUDA on a CUDA error. */
+md_status md_measure_fp64_peak(int64_t iters, double *tflops, double *ms, void *stream);
 
 /* Text of the last error of this context ("" if none).  Valid until the next call. */
 const char *md_last_error(const md_ctx *ctx);

@@ -36,6 +36,8 @@ def lib():
         L.orc_neighbours_cells.argtypes = [i64, P, P, dbl, i32, P, P]
         L.orc_eam_forces.restype = i64
         L.orc_eam_forces.argtypes = [i64, P, P, P, P, P, P, i32, P, P, P, P, P, P]
+        L.orc_eam_error_scales.restype = None
+        L.orc_eam_error_scales.argtypes = [i64, P, P, P, P, P, P, i32, P, P, P, P, P]
         L.orc_eam_forces_half.restype = i64
         L.orc_eam_forces_half.argtypes = [i64, P, P, P, P, P, P, i32, P, P]
         L.orc_kinetic.restype = None
@@ -132,6 +134,19 @@ def eam_forces(pos, species, box, pot, count, nl):
     out["virial"] = out["virial"].reshape(3, 3)
     out["range_violations"] = int(viol)
     return out
+
+
+def eam_error_scales(pos, species, box, pot, count, nl, dF):
+    """Per-atom scales of the force sum (moldy_oracle.c orc_eam_error_scales): m (sum of the
+    absolute pair terms), q (their radial sensitivity r |d/dr|), e (through F'') and c (the
+    quadratic and cubic terms of the table cubics' derivatives, knot tables only)."""
+    pos, box, species, count, nl, dF = _f64(pos), _f64(box), _i32(species), _i32(count), _i32(nl), _f64(dF)
+    n, k_max = nl.shape
+    P = _Pot(pot)
+    m, q, e, c = np.zeros(n), np.zeros(n), np.zeros(n), np.zeros(n)
+    lib().orc_eam_error_scales(n, _p(pos), _p(species), _p(box), P.ref, _p(count), _p(nl), k_max, _p(dF),
+                               _p(m), _p(q), _p(e), _p(c))
+    return dict(m=m, q=q, e=e, c=c)
 
 
 def eam_forces_half(pos, species, box, pot, count, nl):

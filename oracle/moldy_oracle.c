@@ -363,6 +363,124 @@ int64_t orc_eam_forces(int64_t n, const double *pos, const int32_t *species, con
     return viol;
 }
 
+/* sum_k |3 c_k (r_k - r)^2| over the terms with r < r_k of explicit knot function t (kind 4). */
+static double orc_knots_abs_slope(const orc_potential *p, int t, double r) {
+    int K = p->n_knots;
+    const double *kd = p->tables + (size_t)t * 2 * K;
+    double g = 0.0;
+    if (!(r < p->r_cut)) return 0.0;
+    for (int k = 0; k < K; k++) {
+        double u = kd[K + k] - r;
+        if (u > 0.0) g += fabs(3.0 * kd[k] * u * u);
+    }
+    return g;
+}
+
+/* Scales of the force sum of Eq. (1)'s gradient, for the error bound of a reduced-precision
+ * evaluation (test infrastructure).  For each atom i, over its list pairs with r < r_cut:
+ *   m_i = sum_j ( |V'_ab| + |F'_i phi'_ab| + |F'_j phi'_ba| )                (eV/Å)
+ *   q_i = sum_j r ( |V''_ab| + |F'_i phi''_ab| + |F'_j phi''_ba| )            (eV/Å)
+ *   e_i = sum_j ( |F''_i phi'_ab| R_i + |F''_j phi'_ba| R_j ),
+ *         R_a = sum_k ( phi_ak + r_ak |phi'_ak| )                             (eV/Å)
+ *   c_i = sum_j ( k_V + |F'_i| k_ab + |F'_j| k_ba ),  k = orc_table_curv at r (tables only)
+ * (a = s_i, b = s_j; for explicit knot sums |V'| and |phi'| are the sums of the absolute
+ * terms |3 c_k (r_k - r)^2|).  m_i bounds the terms of the pair sum, q_i their change under a relative
+ * change of r, and e_i the force change through F' under a relative change of every density
+ * term.  Second derivatives are central differences of the first (step 1e-5 Å, and 1e-6 rho
+ * for F), which is exact for a cubic within one table interval.  dF = F'(rho) of each atom. */
+/* For knot tables (kind 2): the size (|2 c2| + |3 c3|) / h of the quadratic and cubic terms of
+ * the derivative of the Hermite cubic of table t on the interval that holds r (c2, c3 the cubic's
+ * coefficients in t = (r - r_k) / h); 0 outside the span and for other kinds. */
+static double orc_table_curv(const orc_potential *p, int t, double r) {
+    if (p->kind != 2) return 0.0;
+    int nk = p->n_knots;
+    const double *y = p->tables + (size_t)t * 2 * nk, *yp = y + nk;
+    double h = (p->r_cut - p->r_min) / (double)(nk - 1);
+    if (r < p->r_min || r > p->r_cut) return 0.0;
+    int k = (int)floor((r - p->r_min) / h);
+    if (k > nk - 2) k = nk - 2;
+    double s0 = h * yp[k], s1 = h * yp[k + 1];
+    double c2 = 3.0 * (y[k + 1] - y[k]) - 2.0 * s0 - s1;
+    double c3 = 2.0 * (y[k] - y[k + 1]) + s0 + s1;
+    return (fabs(2.0 * c2) + fabs(3.0 * c3)) / h;
+}
+
+void orc_eam_error_scales(int64_t n, const double *pos, const int32_t *species, const double *box,
+                          const orc_potential *pot, const int32_t *count, const int32_t *list,
+                          int32_t k_max, const double *dF, double *m, double *q, double *e, double *c) {
+    double L[3] = {box[0], box[1], box[2]};
+    double invL[3] = {1.0 / box[0], 1.0 / box[1], 1.0 / box[2]};
+    double rc2 = pot->r_cut * pot->r_cut;
+    const double h = 1e-5;
+    double *R = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    double *d2F = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; i++) {
+        int64_t viol = 0;
+        double s = 0.0, rho = 0.0;
+        for (int32_t k = 0; k < count[i]; k++) {
+            int64_t j = list[i * k_max + k];
+            double r2 = orc_dist2(pos, i, j, L, invL, NULL);
+            if (!(r2 < rc2)) continue;
+            double r = sqrt(r2), dphi;
+            double phi = orc_pair(pot, 1, species[i], species[j], r, &dphi, &viol);
+            rho += phi;
+            s += fabs(phi) + r * fabs(dphi);
+        }
+        R[i] = s;
+        double hr = 1e-6 * (rho > 0.0 ? rho : 1.0), dp, dm;
+        orc_embed(pot, species[i], rho + hr, &dp, &viol);
+        orc_embed(pot, species[i], rho - hr, &dm, &viol);
+        d2F[i] = (dp - dm) / (2.0 * hr);
+    }
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; i++) {
+        int64_t viol = 0;
+        double sm = 0.0, sq = 0.0, se = 0.0, sc = 0.0;
+        int a = species[i];
+        for (int32_t k = 0; k < count[i]; k++) {
+            int64_t j = list[i * k_max + k];
+            double r2 = orc_dist2(pos, i, j, L, invL, NULL);
+            if (!(r2 < rc2)) continue;
+            double r = sqrt(r2);
+            int b = species[j];
+            double dV, dab, dba, p1, m1, vpp, abpp, bapp;
+            orc_pair(pot, 0, a, b, r, &dV, &viol);
+            orc_pair(pot, 1, a, b, r, &dab, &viol);
+            orc_pair(pot, 1, b, a, r, &dba, &viol);
+            if (pot->kind == 4) { /* explicit sums: the scale of a sum is the sum of |terms| */
+                int ns = pot->n_species;
+                dV = orc_knots_abs_slope(pot, 0 * ns * ns + a * ns + b, r);
+                dab = orc_knots_abs_slope(pot, 1 * ns * ns + a * ns + b, r);
+                dba = orc_knots_abs_slope(pot, 1 * ns * ns + b * ns + a, r);
+            }
+            orc_pair(pot, 0, a, b, r + h, &p1, &viol);
+            orc_pair(pot, 0, a, b, r - h, &m1, &viol);
+            vpp = (p1 - m1) / (2.0 * h);
+            orc_pair(pot, 1, a, b, r + h, &p1, &viol);
+            orc_pair(pot, 1, a, b, r - h, &m1, &viol);
+            abpp = (p1 - m1) / (2.0 * h);
+            orc_pair(pot, 1, b, a, r + h, &p1, &viol);
+            orc_pair(pot, 1, b, a, r - h, &m1, &viol);
+            bapp = (p1 - m1) / (2.0 * h);
+            sm += fabs(dV) + fabs(dF[i] * dab) + fabs(dF[j] * dba);
+            sq += r * (fabs(vpp) + fabs(dF[i] * abpp) + fabs(dF[j] * bapp));
+            se += fabs(d2F[i] * dab) * R[i] + fabs(d2F[j] * dba) * R[j];
+            {
+                int ns = pot->n_species;
+                sc += orc_table_curv(pot, a * ns + b, r) + fabs(dF[i]) * orc_table_curv(pot, ns * ns + a * ns + b, r) +
+                      fabs(dF[j]) * orc_table_curv(pot, ns * ns + b * ns + a, r);
+            }
+        }
+        m[i] = sm;
+        q[i] = sq;
+        e[i] = se;
+        c[i] = sc;
+    }
+    free(R);
+    free(d2F);
+}
+
 /* The paper's asymmetric (half) list with F_ij applied to i and j (§3.2.2), run
  * serially: a different order of operations for the same Eq. (1) gradient.
  * Uses the entries j > i of a full list.                                      */

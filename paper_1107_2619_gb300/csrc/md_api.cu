@@ -160,8 +160,11 @@ int ph_list_group(const md_ctx *c) {
     return std::min(MD_LIST_GROUP_MAX, m <= 6.0 ? 4 : (m <= 12.0 ? 16 : 32));
 }
 
+// Link cells of width >= r_list along an edge of length L.  The count is capped at 2^20 before
+// the integer conversion (a grid that large fails the total-cell check of md_create anyway).
 int cells_along(double L, double r_list) {
-    int nc = (int)std::floor(L / r_list);
+    const double q = std::floor(L / r_list);
+    int nc = q < 1048576.0 ? (int)q : 1048576;
     while (nc > 0 && L / nc < r_list * (1.0 + 1e-12)) nc--;
     return nc;
 }
@@ -1386,6 +1389,12 @@ md_status md_get(md_ctx *ctx, int32_t what, void *dst, int32_t on_device) {
             MD_CK(launch_unsort_scalar(A, src, static_cast<double *>(ctx->d_stage), ctx->stream));
             return copy_out(ctx, ctx->d_stage, dst, sizeof(double) * n, on_device);
         }
+        case MD_GET_IMAGE: {
+            if (!ctx->list_valid && (s = md_build_neighbours(ctx)) != MD_OK) return s;
+            if ((s = ensure_stage(ctx, sizeof(double) * 3 * n)) != MD_OK) return s;
+            MD_CK(launch_unsort_image(A, static_cast<double *>(ctx->d_stage), ctx->stream));
+            return copy_out(ctx, ctx->d_stage, dst, sizeof(double) * 3 * n, on_device);
+        }
         case MD_GET_NBR_COUNT:
         case MD_GET_SPECIES: {
             if (what == MD_GET_NBR_COUNT && !ctx->list_valid && (s = md_build_neighbours(ctx)) != MD_OK) return s;
@@ -1761,7 +1770,7 @@ md_status md_sur_train(md_ctx *ctx, int32_t n_iter, int32_t rep_begin, int32_t r
     return MD_OK;
 }
 
-md_status md_set_thermostat(md_ctx *ctx, int32_t on, const double *t_kelvin, const double *q_ev_fs2) {
+md_status md_set_thermostat(md_ctx *ctx, int32_t on, const double *t_kelvin, const double *tau_fs) {
     if (!ctx) return MD_ERR_ARG;
     if (ctx->sur) return fail(ctx, MD_ERR_STATE, "the thermostat runs in the EAM step kernel");
     if (!on) {
@@ -1769,11 +1778,11 @@ md_status md_set_thermostat(md_ctx *ctx, int32_t on, const double *t_kelvin, con
         ctx->thermo_on = false;
         return MD_OK;
     }
-    if (!t_kelvin || !q_ev_fs2) return MD_ERR_ARG;
+    if (!t_kelvin || !tau_fs) return MD_ERR_ARG;
     const int nr = ctx->n_rep;
     for (int r = 0; r < nr; r++)
-        if (!(t_kelvin[r] >= 0.0) || !std::isfinite(t_kelvin[r]) || !(q_ev_fs2[r] > 0.0) || !std::isfinite(q_ev_fs2[r]))
-            return fail(ctx, MD_ERR_ARG, "thermostat: T >= 0 and Q > 0 for every replica");
+        if (!(t_kelvin[r] > 0.0) || !std::isfinite(t_kelvin[r]) || !(tau_fs[r] > 0.0) || !std::isfinite(tau_fs[r]))
+            return fail(ctx, MD_ERR_ARG, "thermostat: T > 0 and tau > 0 for every replica");
     std::vector<int2> chunks;
     for (int r = 0; r < nr; r++)
         for (int64_t a = ctx->rep_off[r]; a < ctx->rep_off[r + 1]; a += kKeChunk) chunks.push_back(make_int2(r, (int)a));
@@ -1781,8 +1790,11 @@ md_status md_set_thermostat(md_ctx *ctx, int32_t on, const double *t_kelvin, con
     for (int r = 0; r < nr; r++) {
         const int64_t m = ctx->rep_off[r + 1] - ctx->rep_off[r];
         th[r] = Thermo{};
-        th[r].q = q_ev_fs2[r];
         th[r].gkt = (double)(3 * m - 3) * kKb * t_kelvin[r];
+        // thermal inertia from the relaxation time: Q = g k_B T tau^2 (eV fs^2)
+        th[r].q = th[r].gkt * tau_fs[r] * tau_fs[r];
+        if (!(th[r].q > 0.0) || !std::isfinite(th[r].q))
+            return fail(ctx, MD_ERR_ARG, "thermostat: Q = g k_B T tau^2 is not a positive finite number");
         th[r].s_b = th[r].s_a = 1.0;
     }
     if (!ctx->d_thermo) MD_CK(dalloc(ctx, &ctx->d_thermo, nr));

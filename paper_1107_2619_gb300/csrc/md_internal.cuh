@@ -222,6 +222,7 @@ int partial_blocks(int n, int lanes);  // blocks (and partial-sum rows) of a for
 cudaError_t launch_reduce(const Atoms &A, int nblocks, double *out, cudaStream_t s);
 cudaError_t launch_unsort_vec(const Atoms &A, const double4_32a *src, double *dst, cudaStream_t s);
 cudaError_t launch_unsort_scalar(const Atoms &A, const double *src, double *dst, cudaStream_t s);
+cudaError_t launch_unsort_image(const Atoms &A, double *dst, cudaStream_t s);
 cudaError_t launch_unsort_int(const Atoms &A, const int32_t *src, int32_t *dst, cudaStream_t s);
 cudaError_t launch_unsort_list(const Atoms &A, int32_t *dst, cudaStream_t s);
 cudaError_t launch_sort_in_vec(const Atoms &A, const double *src, double4_32a *dst, cudaStream_t s);

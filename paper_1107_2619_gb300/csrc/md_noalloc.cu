@@ -37,8 +37,12 @@ struct NoallocScratch {
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoallocScratch)];
 
+// Link cells of width >= r_list along an edge of length L; kNaMaxCells + 1 stands for "more
+// than the scratch holds" (L / r_list is range-checked before the integer conversion).
 int na_cells_along(double L, double r_list) {
-    int nc = (int)floor(L / r_list);
+    const double q = floor(L / r_list);
+    if (!(q <= (double)kNaMaxCells)) return kNaMaxCells + 1;
+    int nc = (int)q;
     while (nc > 0 && L / nc < r_list * (1.0 + 1e-12)) nc--;
     return nc;
 }
@@ -120,7 +124,10 @@ __global__ void k_na_scatter(NoallocScratch *S, int n) {
 }
 
 // Ascending caller index inside each cell (independent of the counter order of k_na_bin),
-// then the positions in cell order.
+// then the positions in cell order.  The coordinates are copied as the caller gave them,
+// unwrapped: the exact test forms d = r_j - r_i from them and takes the minimum image of d,
+// the operations md_build_neighbours applies to the same unwrapped coordinates, so both
+// decide every pair alike.
 __global__ void k_na_cell_sort(NoallocScratch *S, const double *__restrict__ pos, int ncell) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncell) return;
@@ -209,15 +216,19 @@ extern "C" md_status md_neighbours_noalloc(const double *pos, int64_t n_atoms, c
     if (n_atoms < 0 || !box || k_max < 1 || !(r_list > 0.0)) return MD_ERR_ARG;
     if (n_atoms > kNaMaxAtoms) return MD_ERR_CAPACITY;
     NaGeom G;
+    long long ncell = 1;
     for (int k = 0; k < 3; k++) {
-        if (!(box[k] > 0.0)) return MD_ERR_BOX;
+        if (!(box[k] > 0.0) || !(box[k] < INFINITY)) return MD_ERR_BOX;
         G.L[k] = box[k];
         G.invL[k] = 1.0 / box[k];
         G.nc[k] = na_cells_along(box[k], r_list);
         if (G.nc[k] < 3) return MD_ERR_BOX;
     }
-    const long long ncell = (long long)G.nc[0] * G.nc[1] * G.nc[2];
-    if (ncell > kNaMaxCells) return MD_ERR_CAPACITY;
+    for (int k = 0; k < 3; k++) {
+        // each factor is at most kNaMaxCells + 1, so the running product fits in 64 bits
+        ncell *= G.nc[k];
+        if (ncell > kNaMaxCells) return MD_ERR_CAPACITY;
+    }
     G.ncell = (int)ncell;
     G.rl2 = r_list * r_list;
     if (n_atoms == 0) return MD_OK;
@@ -225,6 +236,9 @@ extern "C" md_status md_neighbours_noalloc(const double *pos, int64_t n_atoms, c
     NoallocScratch *S = nullptr;
     if (na_scratch(&S) != cudaSuccess) return MD_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // An error left on this thread by an earlier, unrelated call must not be taken for one of
+    // these launches: clear it first (a sticky error shows again at the synchronisation below).
+    (void)cudaGetLastError();
     const int n = (int)n_atoms;
     const int nb = (n + kThreads - 1) / kThreads;
     k_na_clear<<<(G.ncell + 255) / 256, 256, 0, s>>>(S, G.ncell);

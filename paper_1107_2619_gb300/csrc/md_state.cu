@@ -32,6 +32,25 @@ __global__ void k_unsort_vec(Atoms A, const double4_32a *src, double *dst) {
     dst[o + 2] = v.z;
 }
 
+// The coordinates the passes take: the FP32 copy (mixed path) or the FP64 copy (FP64 path), both
+// in the periodic image of the last list build.
+__global__ void k_unsort_image(Atoms A, double *dst) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= A.n) return;
+    const size_t o = 3 * (size_t)A.id[k];
+    if (A.posd) {
+        const double4_32a v = A.posd[k];
+        dst[o] = v.x;
+        dst[o + 1] = v.y;
+        dst[o + 2] = v.z;
+    } else {
+        const float4 v = A.posf[k];
+        dst[o] = v.x;
+        dst[o + 1] = v.y;
+        dst[o + 2] = v.z;
+    }
+}
+
 __global__ void k_unsort_scalar(Atoms A, const double *src, double *dst) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= A.n) return;
@@ -110,6 +129,12 @@ cudaError_t launch_wrap(const Atoms &A, cudaStream_t s) {
 cudaError_t launch_unsort_vec(const Atoms &A, const double4_32a *src, double *dst, cudaStream_t s) {
     if (A.n == 0) return cudaSuccess;
     k_unsort_vec<<<blocks_for(A.n, kThreads), kThreads, 0, s>>>(A, src, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unsort_image(const Atoms &A, double *dst, cudaStream_t s) {
+    if (A.n == 0) return cudaSuccess;
+    k_unsort_image<<<blocks_for(A.n, kThreads), kThreads, 0, s>>>(A, dst);
     return cudaGetLastError();
 }
 

@@ -429,6 +429,24 @@ def bcc_fe_c(n: int, seed: int, temperature: float = 600.0, c_fraction: float = 
                     temperature=temperature, strain_rate_zz=strain_rate_zz)
 
 
+def replica_recipe(n_replicas: int = 256, seed: int = 3000):
+    """Sizes and temperatures of the uneven-replica workload: replica r is bcc Fe of 2 n_r^3 atoms
+    with n_r ~ U{10..30} and T_r ~ U[300, 1200] K, drawn from stream 11 of `seed` (the first
+    256 draws give the sizes, the next 256 the temperatures); its own seed is seed + r."""
+    u = random_uniform(seed, 11, 512)
+    sizes = (10 + np.floor(u[:256] * 21)).astype(int)[:n_replicas]
+    temps = (300.0 + 900.0 * u[256:])[:n_replicas]
+    return sizes, temps
+
+
+def fe_replicas(indices=None, n_replicas: int = 256, seed: int = 3000):
+    """Workloads of the replicas `indices` (default all) of replica_recipe, and their temperatures."""
+    sizes, temps = replica_recipe(n_replicas, seed)
+    idx = range(n_replicas) if indices is None else indices
+    ws = [bcc_fe(int(sizes[r]), seed=seed + r, temperature=float(temps[r])) for r in idx]
+    return ws, np.array([temps[r] for r in idx])
+
+
 # ----------------------------------------------------------------------------- surrogate
 # Radial-basis descriptor and network shape of the learned per-atom energy: 32 Gaussians of
 # width 0.1 Å centred evenly on 1.5-3.6 Å, cosine cutoff at 4.0 Å, list radius 4.3 Å; a

@@ -28,15 +28,15 @@ MD_SUR_GET_G, MD_SUR_GET_DEDG = 0, 1
 MD_SUR_NB, MD_SUR_H1, MD_SUR_H2, MD_SUR_PARAMS = 32, 64, 64, 6337
 MD_PREC_FP64, MD_PREC_MIXED = 0, 1
 (MD_GET_POS, MD_GET_VEL, MD_GET_FORCE, MD_GET_RHO, MD_GET_EATOM, MD_GET_DF, MD_GET_NBR_COUNT,
- MD_GET_NBR_LIST, MD_GET_SPECIES) = range(9)
+ MD_GET_NBR_LIST, MD_GET_SPECIES, MD_GET_IMAGE) = range(10)
 
 # functions declared in include/md.h (checked by the CPU test-suite)
 EXPORTS = ["md_abi_version", "md_status_string", "md_create", "md_create_batch", "md_build_neighbours",
            "md_eam_forces", "md_step", "md_step_io", "md_set_graph", "md_energy", "md_replica_energies", "md_get",
            "md_set_state", "md_tune", "md_set_profiling", "md_get_profile", "md_get_passes", "md_selftest_timeout",
            "md_neighbours_noalloc", "md_set_thermostat", "md_get_thermostat", "md_set_surrogate", "md_sur_get_params", "md_sur_standardize",
-           "md_sur_get", "md_sur_set_reference", "md_sur_loss_grad", "md_sur_train", "md_last_error",
-           "md_destroy"]
+           "md_sur_get", "md_sur_set_reference", "md_sur_loss_grad", "md_sur_train", "md_measure_fp64_peak",
+           "md_last_error", "md_destroy"]
 
 
 class md_potential(C.Structure):
@@ -159,6 +159,8 @@ def lib():
         L.md_sur_loss_grad.argtypes = [P, i32, i32, C.c_double, C.c_double, P, P]
         L.md_sur_train.restype = C.c_int
         L.md_sur_train.argtypes = [P, i32, i32, i32, i32, C.c_double, C.c_double, C.c_double, C.c_uint64, P]
+        L.md_measure_fp64_peak.restype = C.c_int
+        L.md_measure_fp64_peak.argtypes = [i64, C.POINTER(C.c_double), C.POINTER(C.c_double), P]
         L.md_last_error.restype = C.c_char_p
         L.md_last_error.argtypes = [P]
         L.md_destroy.restype = None
@@ -328,13 +330,13 @@ def md_neighbours_noalloc(pos, box, r_list: float, k_max: int, count, nbr_list, 
                                        C.c_void_p(nbr_list.data_ptr()), C.c_void_p(stream) if stream else None)
 
 
-def md_set_thermostat(ctx, on: bool, t_kelvin=None, q_ev_fs2=None):
+def md_set_thermostat(ctx, on: bool, t_kelvin=None, tau_fs=None):
     if not on:
         _check(ctx, lib().md_set_thermostat(ctx, 0, None, None))
         return
     t = np.ascontiguousarray(np.atleast_1d(t_kelvin), dtype=np.float64)
-    q = np.ascontiguousarray(np.atleast_1d(q_ev_fs2), dtype=np.float64)
-    _check(ctx, lib().md_set_thermostat(ctx, 1, t.ctypes.data, q.ctypes.data))
+    tau = np.ascontiguousarray(np.atleast_1d(tau_fs), dtype=np.float64)
+    _check(ctx, lib().md_set_thermostat(ctx, 1, t.ctypes.data, tau.ctypes.data))
 
 
 def md_get_thermostat(ctx, n_replicas: int = 1):
@@ -388,6 +390,15 @@ def md_sur_train(ctx, n_iter: int, rep_begin: int, rep_end: int, batch_reps: int
     _check(ctx, lib().md_sur_train(ctx, int(n_iter), int(rep_begin), int(rep_end), int(batch_reps), float(lr),
                                    float(w_e), float(w_f), int(seed) & 0xFFFFFFFFFFFFFFFF, loss.ctypes.data))
     return loss
+
+
+def md_measure_fp64_peak(iters: int = 20000, stream=None):
+    """(TFLOP/s, ms) of the library's FP64 FMA-chain kernel on the current device."""
+    tf, ms = C.c_double(), C.c_double()
+    st = lib().md_measure_fp64_peak(int(iters), C.byref(tf), C.byref(ms), C.c_void_p(stream) if stream else None)
+    if st != MD_OK:
+        raise MDError(st, "md_measure_fp64_peak failed")
+    return tf.value, ms.value
 
 
 def md_last_error(ctx) -> str:
@@ -471,7 +482,7 @@ class System:
 
     def get(self, what: int, out=None):
         if out is None:
-            if what in (MD_GET_POS, MD_GET_VEL, MD_GET_FORCE):
+            if what in (MD_GET_POS, MD_GET_VEL, MD_GET_FORCE, MD_GET_IMAGE):
                 out = np.empty((self.n, 3), np.float64)
             elif what in (MD_GET_RHO, MD_GET_EATOM, MD_GET_DF):
                 out = np.empty(self.n, np.float64)
@@ -524,16 +535,15 @@ class System:
         """md_step_io: set the state, take n steps, read the state back; returns the energies."""
         return md_step_io(self.ctx, n, pos_in, vel_in, force_in, pos_out, vel_out, force_out)
 
-    def set_thermostat(self, t_kelvin, tau_fs=None, q_ev_fs2=None):
-        """Nose-Hoover thermostat at t_kelvin (scalar or one per replica); Q from the relaxation
-        time tau_fs (Q = g k_B T tau^2) unless given."""
+    def set_thermostat(self, t_kelvin, tau_fs):
+        """Nose-Hoover thermostat at t_kelvin with relaxation time tau_fs (scalars or one per
+        replica); the library sets the thermal inertia Q (see thermostat())."""
         t = np.broadcast_to(np.asarray(t_kelvin, dtype=np.float64), (self.n_replicas,)).copy()
-        if q_ev_fs2 is None:
-            sizes = np.diff(self.offsets) if hasattr(self, "offsets") else np.array([self.n])
-            q_ev_fs2 = (3 * sizes - 3) * _inputs.KB_EV_PER_K * t * float(tau_fs) ** 2
-        md_set_thermostat(self.ctx, True, t, np.broadcast_to(q_ev_fs2, (self.n_replicas,)))
+        tau = np.broadcast_to(np.asarray(tau_fs, dtype=np.float64), (self.n_replicas,)).copy()
+        md_set_thermostat(self.ctx, True, t, tau)
 
     def thermostat(self):
+        """[n_replicas][4]: pi (1/fs), xi, Q (eV fs^2), the conserved H' (eV)."""
         return md_get_thermostat(self.ctx, self.n_replicas)
 
     def close(self):

@@ -16,7 +16,7 @@ HEADER = os.path.join(ROOT, "include", "md.h")
 
 def header_functions():
     txt = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
-    return sorted(set(re.findall(r"\b(md_[a-z_]+)\s*\(", txt)))
+    return sorted(set(re.findall(r"\b(md_[a-z0-9_]+)\s*\(", txt)))
 
 
 @pytest.fixture(scope="module")
@@ -60,7 +60,7 @@ int main(void) {
 
 
 def test_status_strings(libmd):
-    assert libmd.md_abi_version() == 3
+    assert libmd.md_abi_version() == 4
     assert md.status_string(md.MD_ERR_NBR_OVERFLOW) == "neighbour list overflow"
     assert md.status_string(md.MD_ERR_SPECIES) == "unsupported species"
 

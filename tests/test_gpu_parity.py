@@ -8,23 +8,16 @@ import numpy as np
 import pytest
 
 import oracle
+from mixed_bound import assert_mixed_forces
 from paper_1107_2619_gb300 import inputs as I, md
 
 pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-10
-# Mixed path: FP32 wrapped coordinates carry an absolute error of ~ulp32(L)/2 per coordinate,
-# so the force error grows with the box: it is bounded by 100 eV/Å^2 x ulp32(L_max) (the
-# measured ratio is ~24 eV/Å^2: a few pair force constants of ~10 eV/Å^2), or 1e-4 of the
-# largest force when that is larger.  PE is summed in FP64 from FP32 per-pair terms.
-MIXED_FORCE_TOL = 1e-4
+# Mixed path: every force component within the bound derived per atom from the potential and
+# the configuration (tests/mixed_bound.py: the exact share of the FP32 coordinates plus the FP32
+# arithmetic of the pair terms and their sums).  PE is summed in FP64 from FP32 per-pair terms.
 MIXED_PE_TOL = 1e-6
-
-
-def mixed_force_bound(w, fmax):
-    lmax = float(np.max(w.box))
-    ulp32 = 2.0 ** (np.floor(np.log2(lmax)) - 23)
-    return max(MIXED_FORCE_TOL * fmax, 100.0 * ulp32)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -164,9 +157,8 @@ def test_mixed_forces_within_bound(name):
         pe = s.eam_forces()
         f = s.forces()
         rho = s.get(md.MD_GET_RHO)
-    fs = np.abs(ref["force"]).max()
-    assert np.abs(f - ref["force"]).max() <= mixed_force_bound(w, fs)
-    assert abs(pe - ref["pe"]) <= MIXED_PE_TOL * abs(ref["pe"])
+        img = s.get(md.MD_GET_IMAGE)
+    assert_mixed_forces(w, w.pos, f, img, pe=pe, pe_tol=MIXED_PE_TOL)
     assert np.abs(rho - ref["rho"]).max() <= 1e-5 * np.abs(ref["rho"]).max()
 
 
@@ -195,12 +187,10 @@ def test_two_species_tables_step_like_the_oracle(lanes):
                         w.skin, w.k_max, strain_rate_zz=w.strain_rate_zz)
     with _gpu_system(w, "mixed", lanes_per_atom=lanes) as s:
         s.step(20)
-        pos, f, e = s.positions(), s.forces(), s.energy()
+        pos, f, e, img = s.positions(), s.forces(), s.energy(), s.get(md.MD_GET_IMAGE)
     assert np.abs(pos - ref["pos"]).max() < 1e-5
     assert abs(e["pe"] - ref["energies"][-1, 0]) <= MIXED_PE_TOL * abs(ref["energies"][-1, 0])
-    box = np.array(e["box"])
-    fr = oracle.forces(pos, w.species, box, w.potential, skin=w.skin, k_max=w.k_max)["force"]
-    assert np.abs(f - fr).max() <= mixed_force_bound(w, np.abs(fr).max())
+    assert_mixed_forces(w, pos, f, img, box=np.array(e["box"]), lanes=lanes, pe=e["pe"], pe_tol=MIXED_PE_TOL)
 
 
 def test_unwrapped_images_give_the_same_forces():
@@ -398,8 +388,9 @@ def test_full_size_cu500k_forces_and_lists():
     with _gpu_system(w, "mixed") as s:
         pe32 = s.eam_forces()
         f32 = s.forces()
-    assert np.abs(f32 - ref["force"]).max() <= mixed_force_bound(w, fs)
-    assert abs(pe32 - ref["pe"]) <= MIXED_PE_TOL * abs(ref["pe"])
+        img = s.get(md.MD_GET_IMAGE)
+    ratio, _ = assert_mixed_forces(w, w.pos, f32, img, pe=pe32, pe_tol=MIXED_PE_TOL)
+    print(f"Cu 500k mixed: largest error / derived bound = {ratio:.3f}")
 
 
 def test_full_size_cu500k_step_kernel_as_benchmarked():
@@ -409,14 +400,13 @@ def test_full_size_cu500k_step_kernel_as_benchmarked():
     w = I.fcc_cu(50, seed=2)
     with _gpu_system(w, "mixed") as s:
         s.eam_forces()
-        s.tune()
+        lanes = s.tune()
         s.step(30)
         e = s.energy()
-        pos, f = s.positions(), s.forces()
+        pos, f, img = s.positions(), s.forces(), s.get(md.MD_GET_IMAGE)
     assert e["n_rebuilds"] >= 1
-    ref = oracle.forces(pos, w.species, w.box, w.potential, skin=w.skin, k_max=w.k_max, method="cells")
-    assert np.abs(f - ref["force"]).max() <= mixed_force_bound(w, np.abs(ref["force"]).max())
-    assert abs(e["pe"] - ref["pe"]) <= MIXED_PE_TOL * abs(ref["pe"])
+    ratio, _ = assert_mixed_forces(w, pos, f, img, lanes=lanes, pe=e["pe"], pe_tol=MIXED_PE_TOL)
+    print(f"Cu 500k step kernel: largest error / derived bound = {ratio:.3f}")
 
 
 # --------------------------------------------------------------------------- lanes per atom
@@ -427,14 +417,17 @@ def test_every_lane_count_matches_oracle(lanes, precision, case):
     w = _workload(case)
     ref = oracle.forces(w.pos, w.species, w.box, w.potential, skin=w.skin, k_max=w.k_max, method="brute")
     fs = np.abs(ref["force"]).max()
-    tol = FP64_TOL * fs if precision == "fp64" else mixed_force_bound(w, fs)
     with _gpu_system(w, precision, lanes_per_atom=lanes) as s:
         pe = s.eam_forces()
         f = s.forces()
+        img = s.get(md.MD_GET_IMAGE)
         s.step(5)
         e = s.energy()
-    assert np.abs(f - ref["force"]).max() <= tol
-    assert abs(pe - ref["pe"]) <= (FP64_TOL if precision == "fp64" else MIXED_PE_TOL) * abs(ref["pe"])
+    if precision == "fp64":
+        assert np.abs(f - ref["force"]).max() <= FP64_TOL * fs
+        assert abs(pe - ref["pe"]) <= FP64_TOL * abs(ref["pe"])
+    else:
+        assert_mixed_forces(w, w.pos, f, img, lanes=lanes, pe=pe, pe_tol=MIXED_PE_TOL)
     assert np.isfinite(e["te"])
 
 
@@ -561,8 +554,9 @@ def test_full_size_fe_c_forces_and_strain_steps():
     with _gpu_system(w, "mixed") as s:
         pe32 = s.eam_forces()
         f32 = s.forces()
-        assert np.abs(f32 - ref["force"]).max() <= mixed_force_bound(w, fs)
-        assert abs(pe32 - ref["pe"]) <= MIXED_PE_TOL * abs(ref["pe"])
+        img = s.get(md.MD_GET_IMAGE)
+        ratio, _ = assert_mixed_forces(w, w.pos, f32, img, pe=pe32, pe_tol=MIXED_PE_TOL)
+        print(f"Fe-C 4.2M mixed: largest error / derived bound = {ratio:.3f}")
         s.step(20)
         e = s.energy()
     assert abs(e["box"][2] - w.box[2] * (1 - 1e-6) ** 20) < 1e-9 * w.box[2]

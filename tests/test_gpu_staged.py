@@ -21,21 +21,14 @@ import numpy as np
 import pytest
 
 import oracle
+from mixed_bound import assert_mixed_forces
 from paper_1107_2619_gb300 import inputs as I, md
 
 pytestmark = pytest.mark.gpu
 
+# Forces: the bound derived per atom (tests/mixed_bound.py) with the group walks' FP32 periodic
+# shift of the staged coordinates (staged=True) and the longest sequential sum (lanes=1).
 MIXED_PE_TOL = 1e-6
-
-
-def mixed_force_bound(w, fmax):
-    """The mixed-precision force bound of the list walk: 100 eV/Å^2 x ulp32(L_max), or 1e-4 of
-    the largest force.  The staged walk forms r_j - r_i from FP32 positions with the periodic
-    shift added in FP32 (one more rounding of a coordinate of magnitude <= L + r_list), within
-    the same bound."""
-    lmax = float(np.max(w.box))
-    ulp32 = 2.0 ** (np.floor(np.log2(lmax)) - 23)
-    return max(1e-4 * fmax, 100.0 * ulp32)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -78,12 +71,11 @@ def test_group_walk_steps_match_the_oracle(case, walk, lanes):
         s.step(n_steps)
         p = s.passes()
         assert p["active"] == 1 and 0 < p["last_max"] <= p["capacity"]
-        pos, f, e = s.positions(), s.forces(), s.energy()
+        pos, f, e, img = s.positions(), s.forces(), s.energy(), s.get(md.MD_GET_IMAGE)
     assert np.abs(pos - ref["pos"]).max() < 1e-5
     assert abs(e["pe"] - ref["energies"][-1, 0]) <= MIXED_PE_TOL * abs(ref["energies"][-1, 0])
     # the last force pass of the step kernel (staged) at the GPU's own final positions
-    fr = oracle.forces(pos, w.species, w.box, w.potential, skin=w.skin, k_max=w.k_max)["force"]
-    assert np.abs(f - fr).max() <= mixed_force_bound(w, np.abs(fr).max())
+    assert_mixed_forces(w, pos, f, img, staged=True, pe=e["pe"], pe_tol=MIXED_PE_TOL)
 
 
 @pytest.mark.parametrize("walk", ["staged", "cells", "half"])
@@ -98,12 +90,11 @@ def test_group_walk_rebuild_phases_inside_the_step_kernel(walk):
         s.step(14)
         e = s.energy()
         assert s.passes()["active"] == 1
-        pos, f = s.positions(), s.forces()
+        pos, f, img = s.positions(), s.forces(), s.get(md.MD_GET_IMAGE)
         counts = s.get(md.MD_GET_NBR_COUNT)
     assert e["n_rebuilds"] >= 4
     assert np.abs(pos - ref["pos"]).max() < 1e-5
-    fr = oracle.forces(pos, w.species, w.box, w.potential, skin=w.skin, k_max=w.k_max)["force"]
-    assert np.abs(f - fr).max() <= mixed_force_bound(w, np.abs(fr).max())
+    assert_mixed_forces(w, pos, f, img, staged=True)
     if walk == "cells":   # the list asked for after list-free steps is built at the current positions
         ref_counts = oracle.neighbours(pos, w.box, w.potential.r_cut + w.skin, w.k_max, "brute")[0]
         assert np.array_equal(counts, ref_counts)
@@ -119,9 +110,12 @@ def test_group_and_list_walks_differ_in_rounding_only(walk):
         b.step(10)
         assert b.passes()["active"] == 0
         fa, fb = a.forces(), b.forces()
-        assert np.abs(a.positions() - b.positions()).max() < 1e-6
+        pa, pb = a.positions(), b.positions()
+        assert np.abs(pa - pb).max() < 1e-6
+        ia, ib = a.get(md.MD_GET_IMAGE), b.get(md.MD_GET_IMAGE)
         ea, eb = a.energy(), b.energy()
-    assert np.abs(fa - fb).max() <= mixed_force_bound(w, np.abs(fb).max())
+    assert_mixed_forces(w, pa, fa, ia, lanes=4, staged=True)
+    assert_mixed_forces(w, pb, fb, ib, lanes=4)
     assert abs(ea["pe"] - eb["pe"]) <= MIXED_PE_TOL * abs(eb["pe"])
 
 
@@ -158,12 +152,11 @@ def test_overfull_group_falls_back_to_the_list_walk_and_back(walk):
         s.step(1)
         p = s.passes()
         assert p["last_max"] > p["capacity"] and p["active"] == 0
-        pos, f = s.positions(), s.forces()
-        fr = oracle.forces(pos, w.species, w.box, w.potential, skin=w.skin, k_max=k_max)["force"]
-        assert np.abs(f - fr).max() <= mixed_force_bound(w, np.abs(fr).max())
+        pos, f, img = s.positions(), s.forces(), s.get(md.MD_GET_IMAGE)
+        wk = I.Workload(**{**w.__dict__, "k_max": k_max})
+        assert_mixed_forces(wk, pos, f, img, lanes=8)
         s.set_state(pos=w.pos, vel=w.vel)
         s.step(2)
         assert s.passes()["active"] == 1
-        pos, f = s.positions(), s.forces()
-    fr = oracle.forces(pos, w.species, w.box, w.potential, skin=w.skin, k_max=k_max)["force"]
-    assert np.abs(f - fr).max() <= mixed_force_bound(w, np.abs(fr).max())
+        pos, f, img = s.positions(), s.forces(), s.get(md.MD_GET_IMAGE)
+    assert_mixed_forces(wk, pos, f, img, staged=True)

@@ -180,6 +180,27 @@ def test_first_adam_step_matches_its_definition():
     assert np.abs(th1 - w1).max() <= 1e-6
 
 
+def test_adam_steps_beyond_the_first_match_the_oracle():
+    """Six single-iteration training calls on one full minibatch: before each, the GPU gradient
+    at the current parameters (md_sur_loss_grad) feeds the oracle's Adam, whose moments carry
+    over; each GPU update must land on the oracle's parameters.  From step 2 on the bias
+    corrections no longer cancel, so this checks both decay rates and the step count."""
+    ws, eref, fref = frames(k=2, seed=70)
+    th, gmu, ginv = params(12, scale=1.0)
+    lr = 1e-3
+    with md.SurrogateBatch(ws, th, gmu, ginv) as b:
+        b.set_reference(eref, np.concatenate(fref))
+        w = th.astype(np.float64)
+        m = np.zeros_like(w)
+        v = np.zeros_like(w)
+        for t in range(1, 7):
+            _, g = b.loss_grad(0, 2, 1.0, 1.0)
+            w_ref, m, v = oracle.adam_step(b.sur_params()[0].astype(np.float64), g.astype(np.float64), m, v, t, lr)
+            b.train(1, 2, lr, 1.0, 1.0, seed=t)
+            th_t = b.sur_params()[0]
+            assert np.abs(th_t - w_ref).max() <= 2e-6 * lr / 1e-3, t
+
+
 def test_training_lowers_the_loss_and_is_deterministic():
     ws, eref, fref = frames(k=6, seed=90)
     th, _, _ = params(9, scale=0.5)

@@ -12,17 +12,23 @@ pytestmark = pytest.mark.gpu
 KB = I.KB_EV_PER_K
 
 
-def _q(n, T, tau):
-    return (3 * n - 3) * KB * T * tau ** 2
+def test_library_sets_q_from_tau():
+    w = I.bcc_fe(5, seed=3)
+    with md.System(w, precision="fp64") as s:
+        s.set_thermostat(900.0, tau_fs=40.0)
+        q = s.thermostat()[0, 2]
+    assert abs(q - (3 * w.n_atoms - 3) * KB * 900.0 * 40.0 ** 2) <= 1e-14 * q
 
 
 def test_fp64_nvt_trajectory_matches_oracle():
     w = I.bcc_fe(5, seed=3, temperature=300.0, sigma=0.05)
-    T, q = 900.0, _q(w.n_atoms, 900.0, 40.0)
-    ref = oracle.run_nvt(w.pos, w.vel, w.species, w.potential.masses, w.box, w.potential, 1.0, 60, 0.3, 32, T, q)
+    T = 900.0
     with md.System(w, precision="fp64") as s:
-        s.set_thermostat(T, q_ev_fs2=q)
+        s.set_thermostat(T, tau_fs=40.0)
         s.eam_forces()
+        q = s.thermostat()[0, 2]
+        ref = oracle.run_nvt(w.pos, w.vel, w.species, w.potential.masses, w.box, w.potential, 1.0, 60, 0.3, 32, T,
+                             q)
         s.step(60)
         pos, vel = s.positions(), s.velocities()
         th = s.thermostat()[0]
@@ -38,10 +44,10 @@ def test_fp64_nvt_trajectory_matches_oracle():
 def test_batch_replicas_each_follow_their_own_thermostat():
     temps = [300.0, 700.0, 1200.0]
     ws = [I.bcc_fe(5 + r % 2, seed=60 + r, temperature=400.0, sigma=0.05) for r in range(3)]
-    qs = [_q(w.n_atoms, T, 30.0) for w, T in zip(ws, temps)]
     with md.Batch(ws, precision="fp64") as b:
-        b.set_thermostat(temps, q_ev_fs2=qs)
+        b.set_thermostat(temps, tau_fs=30.0)
         b.eam_forces()
+        qs = b.thermostat()[:, 2]
         b.step(40)
         pos, th = b.positions(), b.thermostat()
     for r, (w, T, q) in enumerate(zip(ws, temps, qs)):
@@ -56,7 +62,7 @@ def test_batch_replicas_each_follow_their_own_thermostat():
 def test_infinite_thermal_inertia_is_nve(precision):
     w = I.bcc_fe(6, seed=4, temperature=600.0)
     with md.System(w, precision=precision) as a, md.System(w, precision=precision) as b:
-        a.set_thermostat(600.0, q_ev_fs2=1e40)
+        a.set_thermostat(600.0, tau_fs=1e20)
         for s in (a, b):
             s.eam_forces()
             s.step(25)

@@ -151,3 +151,42 @@ def test_adam_first_step_is_signed_learning_rate():
     g = np.array([3.0, -1e-3, 2.5e4])
     w, m, v = oracle.adam_step(np.zeros(3), g, np.zeros(3), np.zeros(3), 1, lr=0.01, eps=0.0)
     assert np.allclose(w, -0.01 * np.sign(g), rtol=1e-14)
+
+
+def test_adam_constant_gradient_moves_by_the_learning_rate_at_every_step():
+    """With the same gradient at every step the bias-corrected moments are exactly g and g^2
+    (m_t = (1 - beta1^t) g, v_t = (1 - beta2^t) g^2), so with eps = 0 every step is -lr sign(g).
+    A wrong bias-correction exponent, beta1 and beta2 exchanged in a correction, or a moment
+    without its (1 - beta) factor moves by another amount from step 2 on."""
+    g = np.array([3.0, -1e-3, 2.5e4, -7.0])
+    w, m, v = np.zeros(4), np.zeros(4), np.zeros(4)
+    for t in range(1, 31):
+        w1, m, v = oracle.adam_step(w, g, m, v, t, lr=0.01, eps=0.0)
+        assert np.allclose(w1 - w, -0.01 * np.sign(g), rtol=1e-12, atol=0), t
+        w = w1
+
+
+def test_adam_second_step_after_a_zero_gradient_closed_form():
+    """g_1 = g, g_2 = 0: m_2 = beta1 (1 - beta1) g and v_2 = beta2 (1 - beta2) g^2, so the bias-
+    corrected moments are beta1 g / (1 + beta1) and beta2 g^2 / (1 + beta2), and the second
+    step is lr (beta1 / (1 + beta1)) / sqrt(beta2 / (1 + beta2)) sign(g) = 0.670058... lr sign(g)
+    for beta1 = 0.9, beta2 = 0.999 (eps = 0).  This fixes the two decay rates, which a constant
+    gradient does not."""
+    g = np.array([2.0, -0.5])
+    w, m, v = oracle.adam_step(np.zeros(2), g, np.zeros(2), np.zeros(2), 1, lr=1.0, eps=0.0)
+    w2, _, _ = oracle.adam_step(w, np.zeros(2), m, v, 2, lr=1.0, eps=0.0)
+    step = (0.9 / 1.9) / math.sqrt(0.999 / 1.999)
+    assert abs(step - 0.6700583) < 1e-6
+    assert np.allclose(w - w2, step * np.sign(g), rtol=1e-13, atol=0)
+
+
+def test_adam_is_invariant_to_the_gradient_scale():
+    """With eps = 0 the update depends on the gradients only through their ratios."""
+    rng = np.random.default_rng(3)
+    gs = rng.normal(size=(8, 5))
+    wa = wb = np.zeros(5)
+    ma = va = mb = vb = np.zeros(5)
+    for t in range(1, 9):
+        wa, ma, va = oracle.adam_step(wa, gs[t - 1], ma, va, t, lr=0.1, eps=0.0)
+        wb, mb, vb = oracle.adam_step(wb, 1e3 * gs[t - 1], mb, vb, t, lr=0.1, eps=0.0)
+    assert np.allclose(wa, wb, rtol=1e-12, atol=1e-15)
