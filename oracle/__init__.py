@@ -36,6 +36,8 @@ def lib():
         L.orc_neighbours_cells.argtypes = [i64, P, P, dbl, i32, P, P]
         L.orc_eam_forces.restype = i64
         L.orc_eam_forces.argtypes = [i64, P, P, P, P, P, P, i32, P, P, P, P, P, P]
+        L.orc_run_pc3.restype = i64
+        L.orc_run_pc3.argtypes = [i64, P, P, P, P, P, P, dbl, i32, dbl, i32, i32, P, i32, P, P, P]
         L.orc_eam_error_scales.restype = None
         L.orc_eam_error_scales.argtypes = [i64, P, P, P, P, P, P, i32, P, P, P, P, P]
         L.orc_eam_forces_half.restype = i64
@@ -293,6 +295,25 @@ def sur_loss_grad(frames, spec, weights, w_e=1.0, w_f=1.0, k_max=64):
                                    _p(eref), _p(fref), C.byref(sp), _p(w), float(w_e), float(w_f),
                                    _p(grad), _p(parts))
     return dict(loss=float(loss), loss_e=float(parts[0]), loss_f=float(parts[1]), grad=grad)
+
+
+def run_pc3(pos, vel, species, masses, box, pot, dt_fs, n_steps, skin, k_max, rebuild_every=0, force=None,
+            gear3=None):
+    """Third-order predictor-corrector (moldy_oracle.c orc_run_pc3) from (pos, vel); gear3 the
+    third-derivative term (dt^3/6) da/dt of a previous call (None: zero).  Returns the final
+    state (force at the last predicted positions, gear3) and per-step (PE, KE)."""
+    pos, vel, box = _f64(pos).copy(), _f64(vel).copy(), _f64(box).copy()
+    species, masses = _i32(species), _f64(masses)
+    n = pos.shape[0]
+    f = np.zeros((n, 3)) if force is None else _f64(force).copy()
+    g3 = np.zeros((n, 3)) if gear3 is None else _f64(gear3).copy()
+    energies = np.zeros((max(n_steps, 1), 2))
+    nreb = np.zeros(1, np.int32)
+    P = _Pot(pot)
+    lib().orc_run_pc3(n, _p(pos), _p(vel), _p(species), _p(masses), _p(box), P.ref, float(dt_fs), int(n_steps),
+                      float(skin), int(k_max), int(rebuild_every), _p(f), 0 if force is None else 1, _p(g3),
+                      _p(energies), _p(nreb))
+    return dict(pos=pos, vel=vel, force=f, gear3=g3, energies=energies[:n_steps], n_rebuilds=int(nreb[0]))
 
 
 def run_nvt(pos, vel, species, masses, box, pot, dt_fs, n_steps, skin, k_max, t_kelvin, q_ev_fs2,

@@ -648,6 +648,110 @@ int64_t orc_run_vv(int64_t n, double *pos, double *vel, const int32_t *species, 
 }
 
 /* ------------------------------------------------------------------------- */
+/* Third-order predictor-corrector (§2.3, the paper's second integrator, after Gear), for the
+ * second-order equations of motion r'' = F/m.  The state of each atom is the scaled Taylor
+ * (Nordsieck) vector of its trajectory up to the third derivative,
+ *   q0 = r,  q1 = dt v,  q2 = (dt^2/2) a,  q3 = (dt^3/6) b   (a = r'', b = da/dt),
+ * and one step is:
+ *   predict:  q0 <- q0 + q1 + q2 + q3,  q1 <- q1 + 2 q2 + 3 q3,  q2 <- q2 + 3 q3  (the Taylor
+ *             series to third order; q3 is unchanged);
+ *   evaluate: the forces at the predicted positions (the one force evaluation of the step);
+ *   correct:  D = (dt^2/2) F/m - q2 (the error of the predicted acceleration term), then
+ *             q_k <- q_k + c_k D with Gear's coefficients for a second-order equation and four
+ *             values, c = (1/6, 5/6, 1, 1/3).
+ * Start: q2 from the forces at the initial positions (computed unless forces_valid), and q3 from
+ * `gear3` ([N][3], the third-derivative term of a previous call; zero to start afresh).  On exit
+ * pos, vel hold q0 and q1 / dt, force the forces at the last predicted positions (so q2 =
+ * (dt^2/2) F/m), gear3 the final q3.  energies[2 s ..] = (PE at the step's predicted positions,
+ * KE of its corrected velocities).  The list is rebuilt as in orc_run_vv, from the predicted
+ * positions.  No strain ramp.                                                                 */
+int64_t orc_run_pc3(int64_t n, double *pos, double *vel, const int32_t *species, const double *masses,
+                    const double *box, const orc_potential *pot, double dt_fs, int32_t n_steps, double skin,
+                    int32_t k_max, int32_t rebuild_every, double *force, int32_t forces_valid, double *gear3,
+                    double *energies, int32_t *n_rebuilds) {
+    const double c0 = 1.0 / 6.0, c1 = 5.0 / 6.0, c3 = 1.0 / 3.0; /* c2 = 1 */
+    double r_list = pot->r_cut + skin;
+    size_t nn = (size_t)(n > 0 ? n : 1);
+    int32_t *count = (int32_t *)malloc(sizeof(int32_t) * nn);
+    int32_t *list = (int32_t *)malloc(sizeof(int32_t) * nn * k_max);
+    double *ref = (double *)malloc(sizeof(double) * 3 * nn);
+    double *rho = (double *)malloc(sizeof(double) * nn);
+    double *dF = (double *)malloc(sizeof(double) * nn);
+    double *ea = (double *)malloc(sizeof(double) * nn);
+    double *q1 = (double *)malloc(sizeof(double) * 3 * nn);
+    double *q2 = (double *)malloc(sizeof(double) * 3 * nn);
+    double acc = 1.0 / ORC_MVV2E; /* (eV/Å)/amu -> Å/fs^2 */
+    double h2 = 0.5 * dt_fs * dt_fs;
+    double lim2 = 0.25 * skin * skin;
+    int64_t viol = 0;
+    int32_t rebuilds = 0;
+    double L[3] = {box[0], box[1], box[2]};
+#define ORC_BUILD3()                                                                            \
+    do {                                                                                        \
+        if (orc_neighbours_cells(n, pos, L, r_list, k_max, count, list) < 0)                    \
+            orc_neighbours_brute(n, pos, L, r_list, k_max, count, list);                        \
+        memcpy(ref, pos, sizeof(double) * 3 * n);                                               \
+        rebuilds++;                                                                             \
+    } while (0)
+    ORC_BUILD3();
+    if (!forces_valid)
+        viol += orc_eam_forces(n, pos, species, L, pot, count, list, k_max, rho, dF, force, ea, NULL, NULL);
+    for (int64_t i = 0; i < n; i++) {
+        double im = acc / masses[species[i]];
+        for (int c = 0; c < 3; c++) {
+            q1[3 * i + c] = dt_fs * vel[3 * i + c];
+            q2[3 * i + c] = h2 * force[3 * i + c] * im;
+        }
+    }
+    for (int32_t step = 0; step < n_steps; step++) {
+        for (size_t k = 0; k < 3 * (size_t)n; k++) { /* predict */
+            pos[k] += q1[k] + q2[k] + gear3[k];
+            q1[k] += 2.0 * q2[k] + 3.0 * gear3[k];
+            q2[k] += 3.0 * gear3[k];
+        }
+        int rebuild = (rebuild_every > 0 && (step + 1) % rebuild_every == 0);
+        for (int64_t i = 0; i < n && !rebuild; i++) {
+            double dx = pos[3 * i] - ref[3 * i], dy = pos[3 * i + 1] - ref[3 * i + 1];
+            double dz = pos[3 * i + 2] - ref[3 * i + 2];
+            if ((dx * dx + dy * dy) + dz * dz > lim2) rebuild = 1;
+        }
+        if (rebuild) ORC_BUILD3();
+        double pe = 0.0;
+        viol += orc_eam_forces(n, pos, species, L, pot, count, list, k_max, rho, dF, force, ea, NULL, &pe);
+        for (int64_t i = 0; i < n; i++) { /* correct */
+            double im = acc / masses[species[i]];
+            for (int c = 0; c < 3; c++) {
+                size_t k = 3 * (size_t)i + c;
+                double D = h2 * force[k] * im - q2[k];
+                pos[k] += c0 * D;
+                q1[k] += c1 * D;
+                q2[k] += D;
+                gear3[k] += c3 * D;
+            }
+        }
+        if (energies) {
+            for (size_t k = 0; k < 3 * (size_t)n; k++) vel[k] = q1[k] / dt_fs;
+            double ke;
+            orc_kinetic(n, vel, species, masses, &ke, NULL, NULL, NULL);
+            energies[2 * step] = pe;
+            energies[2 * step + 1] = ke;
+        }
+    }
+#undef ORC_BUILD3
+    for (size_t k = 0; k < 3 * (size_t)n; k++) vel[k] = q1[k] / dt_fs;
+    if (n_rebuilds) *n_rebuilds = rebuilds;
+    free(count);
+    free(list);
+    free(ref);
+    free(rho);
+    free(dF);
+    free(ea);
+    free(q1);
+    free(q2);
+    return viol;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Nose-Hoover thermostat (NVTp, §2.1.2): dp_i/dt = -dU/dq_i - pi_s p_i, Q_s dpi_s/dt = sum_i p_i^2/m_i
  * - g k_B T with g = 3N - 3 (the printed right-hand side writes the kinetic term as p^2/2m; the
  * reading taken here is the standard p^2/m, whose fixed point is the temperature the same section

@@ -587,6 +587,12 @@ md_status create_common(md_ctx *ctx, const md_config *cfg, const md_potential *p
 #endif
     A.image_fixed = (MD_IMAGE_SHORTCUT && cfg->strain_rate_zz == 0.0) ? 1 : 0;
     chk(dalloc(ctx, &A.nbr, nbr_entries(n, cfg->k_max)));
+#ifndef MD_FP64_DCACHE
+#define MD_FP64_DCACHE 1
+#endif
+    // FP64, one species: the per-entry derivative cache of the force pass (16 B per list entry)
+    if (MD_FP64_DCACHE && cfg->precision == MD_PREC_FP64 && pot->kind != MD_POT_SURROGATE && ns == 1)
+        chk(dalloc(ctx, &A.dcache, nbr_entries(n, cfg->k_max)));
     if (n_rep > 1) chk(dalloc(ctx, &A.rep, n));
     A.sorted = A.cell_of;  // cell_of is consumed by the scatter before the in-cell sort writes
     // partial-sum rows: a stand-alone force launch (<= 8 lanes) or a persistent grid

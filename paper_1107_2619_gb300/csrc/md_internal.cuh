@@ -109,6 +109,11 @@ struct Atoms {
     int32_t *cell_of, *slot, *order;
     int32_t *sorted;                         // order after the in-cell sort (aliases cell_of)
     int32_t *nbr, *count;                    // list entry k of atom i: see NbrRow; k < min(count, k_max)
+    double2 *dcache;                         // FP64 path, one species: per list entry (same plane layout
+                                             // as nbr) the radial factors of the pair force, (V'(r) / r,
+                                             // phi'(r) / r), written by the density pass and read by
+                                             // the force passes that need no energy; (0, 0) beyond
+                                             // r_cut.  NULL: not kept
     uint8_t *wrap;                           // 1: the atom's link cell is on the box boundary at the
                                              // last build (some neighbour cell is a periodic image)
     int image_fixed;                         // 1: no strain ramp, so posf/p2f stay in the periodic
@@ -139,6 +144,15 @@ struct NbrRow {
 };
 __host__ __device__ inline NbrRow nbr_row(const Atoms &A, int i) {
     return NbrRow{A.nbr + 4 * (size_t)i, 4LL * A.n};
+}
+// The derivative cache of atom i in the list's plane layout (entry k at the offset of nbr[k]).
+struct DRow {
+    double2 *p;        // &dcache[4 i]
+    long long plane;   // 4 n
+    __host__ __device__ double2 *ptr(int k) const { return p + (long long)(k >> 2) * plane + (k & 3); }
+};
+__host__ __device__ inline DRow dcache_row(const Atoms &A, int i) {
+    return DRow{A.dcache + 4 * (size_t)i, 4LL * A.n};
 }
 struct NbrRow16 {
     const uint16_t *p;

@@ -393,6 +393,9 @@ __device__ __forceinline__ void density64_item(const Atoms &A, const Pot &P, con
         si = MULTI ? A.spec[i] : 0;
         const int cnt = min(A.count[i], A.k_max);
         const NbrRow row = nbr_row(A, i);
+        // one species: keep (V'/r, phi'/r) of every entry for the force passes without energies
+        const bool keep = !MULTI && A.dcache != nullptr;
+        const DRow drow = dcache_row(A, i);
         auto walk = [&](auto wrapt) {
             using W = decltype(wrapt);
             for (int k = lane; k < cnt; k += T) {
@@ -402,22 +405,44 @@ __device__ __forceinline__ void density64_item(const Atoms &A, const Pot &P, con
                 const double dy = sep64<W>(pj.y - pi.y, B.L[1], B.invL[1]);
                 const double dz = sep64<W>(pj.z - pi.z, B.L[2], B.invL[2]);
                 const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-                if (!(r2 < P.rc2)) continue;
-                const double r = r2 * rsqrt64(r2);
+                if (!(r2 < P.rc2)) {
+                    if (keep) *drow.ptr(k) = make_double2(0.0, 0.0);
+                    continue;
+                }
+                const double rinv = rsqrt64(r2);
+                const double r = r2 * rinv;
                 if (KIND == MD_POT_FS_ANALYTIC) {
                     rho += fs_phi<double>(P.fs, P.bd, r);
+                    if (keep) {
+                        double dV;
+                        fs_V<double>(P.fs, r, dV);
+                        *drow.ptr(k) = make_double2(dV * rinv, fs_dphi<double>(P.fs, P.bd, r) * rinv);
+                    }
                 } else if (KIND == MD_POT_KNOTS) {
                     const int sj = MULTI ? (int)pj.w : 0;
                     double d;
                     rho += knot_sum<double, double2>(P.K64 + (size_t)(P.ns * P.ns + si * P.ns + sj) * P.nkt, P.nkt, r, d);
+                    if (keep) {
+                        double dV;
+                        knot_sum<double, double2>(P.K64, P.nkt, r, dV);
+                        *drow.ptr(k) = make_double2(dV * rinv, d * rinv);
+                    }
                 } else {
                     const int sj = MULTI ? (int)pj.w : 0;
                     double t, d;
                     bool below;
                     const int kr = knot_row((r - P.r_min) * P.inv_dr, P.nk, t, below);
                     if (below) atomicAdd(&A.flags->range_violations, 1ull);
-                    const double4_32a c = P.VP64[((size_t)(si * P.ns + sj) * P.nk + kr) * 2 + 1];
+                    const size_t ab = ((size_t)(si * P.ns + sj) * P.nk + kr) * 2;
+                    const double4_32a c = P.VP64[ab + 1];
                     rho += cubic(t, c.x, c.y, c.z, c.w, below, d);
+                    if (keep) {
+                        const double4_32a cv = P.VP64[ab];
+                        double dV;
+                        cubic(t, cv.x, cv.y, cv.z, cv.w, below, dV);
+                        const double sc = P.inv_dr * rinv;
+                        *drow.ptr(k) = make_double2(dV * sc, d * sc);
+                    }
                 }
             }
         };
@@ -435,9 +460,59 @@ __device__ __forceinline__ void density64_item(const Atoms &A, const Pot &P, con
     }
 }
 
+// The FP64 force pass from the derivative cache of the density pass (one species, no energies):
+// per entry the separation, then f_i += [V'/r + (F'_i + F'_j) phi'/r] d.  The same terms as the
+// full evaluation below, in another order of rounding.
+template <int T>
+__device__ __forceinline__ int force64_cached_item(const Atoms &A, const Box *boxes, long long g, double half_dt,
+                                                   bool kick) {
+    const int i = (int)(g / T), lane = (int)(g & (T - 1));
+    const bool live = i < A.n;
+    double fx = 0.0, fy = 0.0, fz = 0.0;
+    const bool wrap = needs_image(A, i, live);
+    if (live) {
+        const Box &B = boxes[ph::replica_of(A, i)];
+        const double4_32a pi = A.p2d[i];
+        const double Fpi = pi.w;
+        const int cnt = min(A.count[i], A.k_max);
+        const NbrRow row = nbr_row(A, i);
+        const DRow drow = dcache_row(A, i);
+        auto walk = [&](auto wrapt) {
+            using W = decltype(wrapt);
+            for (int k = lane; k < cnt; k += T) {
+                const int j = ld_phase(row.ptr(k));
+                const double4_32a pj = ld_phase(A.p2d + j);
+                const double2 e = ld_phase(drow.ptr(k));
+                const double dx = sep64<W>(pj.x - pi.x, B.L[0], B.invL[0]);
+                const double dy = sep64<W>(pj.y - pi.y, B.L[1], B.invL[1]);
+                const double dz = sep64<W>(pj.z - pi.z, B.L[2], B.invL[2]);
+                const double gr = fma(Fpi + pj.w, e.y, e.x);
+                fx = fma(gr, dx, fx);
+                fy = fma(gr, dy, fy);
+                fz = fma(gr, dz, fz);
+            }
+        };
+        if (wrap) walk(std::true_type{});
+        else walk(std::false_type{});
+    }
+    fx = lane_sum<T>(fx);
+    fy = lane_sum<T>(fy);
+    fz = lane_sum<T>(fz);
+    if (!(live && lane == 0)) return -1;
+    A.force[i] = make_double4_32a(fx, fy, fz, 0.0);
+    if (!isfinite(fx + fy + fz)) atomicOr(&A.flags->error, FLAG_NONFINITE);
+    double4_32a v = A.vel[i];
+    kick_and_partials(v, fx, fy, fz, half_dt, kick);
+    if (kick) A.vel[i] = v;
+    return i;
+}
+
 template <int T, int KIND, bool MULTI, bool ENERGY>
 __device__ __forceinline__ int force64_item(const Atoms &A, const Pot &P, const Box *boxes, long long g,
                                             double half_dt, bool kick, double (&part)[kPartials]) {
+    if constexpr (!MULTI && !ENERGY) {
+        if (A.dcache) return force64_cached_item<T>(A, boxes, g, half_dt, kick);
+    }
     const int i = (int)(g / T), lane = (int)(g & (T - 1));
     const bool live = i < A.n;
     double fx = 0.0, fy = 0.0, fz = 0.0, ep = 0.0;

@@ -10,9 +10,16 @@ roundoff u = 2^-24:
         the passes read (md_get MD_GET_IMAGE) in the box rounded to FP32 (the periodic shifts
         of the FP32 minimum image), minus its force at the FP64 positions;
   12 u q_i   the FP32 evaluation of r: r^2 (3 roundings), the reciprocal square root (<= 2 ulp),
-        r = r^2 / sqrt(r^2) (1), the FP32 periodic shift of boundary pairs (<= 3 u of r at the
+        r = r^2 / sqrt(r^2) (1), the subtraction of the periodic shift (<= 3 u of r at the
         shortest pair) and the knot index (2): a relative change of r of at most 12 u, whose
         effect on the force is at most 12 u q_i (q_i: r |d/dr| of every pair term);
+  B_i   atoms within r_list + skin of a box face only: a pair that crosses the face is formed
+        from coordinates on opposite sides, as x_j - x_i of size ~L rounded to FP32 before the
+        periodic shift (the minimum image of the list walk; the group walks instead add the
+        stencil's shift to a coordinate, a rounding of the same size): up to half an ulp of
+        L + r_list + skin per component, i.e. a change of the separation of at most
+        sqrt(3) ulp / 2, relative sqrt(3) ulp / (2 r_min) of r and of its direction, hence
+        B_i = (q_i + m_i) sqrt(3) ulp / (2 r_min);
   (9 + n_i + log2 T + K_t) u m_i   the FP32 pair term (F' rounded to FP32, the derivative
         cubic, the combination, the scaling by 1/r: 9 roundings of each term's size) and its
         recursive summation over n_i = ceil(K_i / T) list entries per lane, then log2 T lane
@@ -39,14 +46,11 @@ U32 = 2.0 ** -24
 U16 = 2.0 ** -11
 
 
-def mixed_force_bound(w, pos, image, box=None, lanes=1, staged=False):
+def mixed_force_bound(w, pos, image, box=None, lanes=1):
     """Per-atom bound (N,) on |F_mixed - F_oracle| (any component) at positions `pos` (FP64,
     caller order), where `image` is the context's MD_GET_IMAGE at those positions; `box` the
     current box (default w.box); `lanes` the lanes per atom of the force pass (1 when unknown:
-    the longest sequential sum).  staged: the group walks, which add each stencil cell's
-    periodic shift to the FP32 coordinates in FP32 (one more rounding of a coordinate of size
-    up to L + r_list, at most half its ulp per component: a change of r and of the direction of
-    at most sqrt(3) ulp / (2 r) relative, hence (q_i + m_i) times that)."""
+    the longest sequential sum; the group walks' shared-memory sums are no longer)."""
     box = np.asarray(w.box if box is None else box, np.float64)
     pot = w.potential
     ref = oracle.forces(pos, w.species, box, pot, skin=w.skin, k_max=w.k_max, method="cells")
@@ -70,17 +74,19 @@ def mixed_force_bound(w, pos, image, box=None, lanes=1, staged=False):
     arith = U32 * (12.0 * sc["q"] + (9.0 + n_seq + math.log2(max(1, int(lanes))) + k_terms) * sc["m"]
                    + 12.0 * sc["e"])
     b16 = U16 * sc["c"]
-    if staged:
-        top = float(np.max(box)) + rc + float(w.skin)
-        ulp = 2.0 ** (math.floor(math.log2(top)) - 23)
-        arith = arith + (sc["q"] + sc["m"]) * math.sqrt(3.0) * ulp / (2.0 * r_lo)
-    return C + arith + b16, ref
+    reach = rc + 2.0 * float(w.skin)
+    img = np.asarray(image, np.float64)
+    near = np.any((img < reach) | (img > box - reach), axis=1)
+    top = float(np.max(box)) + reach
+    ulp = 2.0 ** (math.floor(math.log2(top)) - 23)
+    edge = np.where(near, (sc["q"] + sc["m"]) * math.sqrt(3.0) * ulp / (2.0 * r_lo), 0.0)
+    return C + arith + b16 + edge, ref
 
 
-def assert_mixed_forces(w, pos, f_gpu, image, box=None, lanes=1, pe=None, pe_tol=1e-6, staged=False):
+def assert_mixed_forces(w, pos, f_gpu, image, box=None, lanes=1, pe=None, pe_tol=1e-6):
     """Every component of every mixed force within its atom's derived bound; returns the ratio
     of the largest error to the bound of its atom (for the record) and the oracle's result."""
-    bound, ref = mixed_force_bound(w, pos, image, box, lanes, staged)
+    bound, ref = mixed_force_bound(w, pos, image, box, lanes)
     err = np.abs(np.asarray(f_gpu) - ref["force"]).max(axis=1)
     bad = np.nonzero(err > bound)[0]
     assert bad.size == 0, (f"{bad.size} atoms outside the derived bound; worst atom {bad[0]}: "

@@ -26,8 +26,8 @@ from paper_1107_2619_gb300 import inputs as I, md
 
 pytestmark = pytest.mark.gpu
 
-# Forces: the bound derived per atom (tests/mixed_bound.py) with the group walks' FP32 periodic
-# shift of the staged coordinates (staged=True) and the longest sequential sum (lanes=1).
+# Forces: the bound derived per atom (tests/mixed_bound.py), which covers the group walks' FP32
+# periodic shift of the staged coordinates, with the longest sequential sum (lanes=1).
 MIXED_PE_TOL = 1e-6
 
 
@@ -75,7 +75,7 @@ def test_group_walk_steps_match_the_oracle(case, walk, lanes):
     assert np.abs(pos - ref["pos"]).max() < 1e-5
     assert abs(e["pe"] - ref["energies"][-1, 0]) <= MIXED_PE_TOL * abs(ref["energies"][-1, 0])
     # the last force pass of the step kernel (staged) at the GPU's own final positions
-    assert_mixed_forces(w, pos, f, img, staged=True, pe=e["pe"], pe_tol=MIXED_PE_TOL)
+    assert_mixed_forces(w, pos, f, img, pe=e["pe"], pe_tol=MIXED_PE_TOL)
 
 
 @pytest.mark.parametrize("walk", ["staged", "cells", "half"])
@@ -94,7 +94,7 @@ def test_group_walk_rebuild_phases_inside_the_step_kernel(walk):
         counts = s.get(md.MD_GET_NBR_COUNT)
     assert e["n_rebuilds"] >= 4
     assert np.abs(pos - ref["pos"]).max() < 1e-5
-    assert_mixed_forces(w, pos, f, img, staged=True)
+    assert_mixed_forces(w, pos, f, img)
     if walk == "cells":   # the list asked for after list-free steps is built at the current positions
         ref_counts = oracle.neighbours(pos, w.box, w.potential.r_cut + w.skin, w.k_max, "brute")[0]
         assert np.array_equal(counts, ref_counts)
@@ -114,7 +114,7 @@ def test_group_and_list_walks_differ_in_rounding_only(walk):
         assert np.abs(pa - pb).max() < 1e-6
         ia, ib = a.get(md.MD_GET_IMAGE), b.get(md.MD_GET_IMAGE)
         ea, eb = a.energy(), b.energy()
-    assert_mixed_forces(w, pa, fa, ia, lanes=4, staged=True)
+    assert_mixed_forces(w, pa, fa, ia, lanes=4)
     assert_mixed_forces(w, pb, fb, ib, lanes=4)
     assert abs(ea["pe"] - eb["pe"]) <= MIXED_PE_TOL * abs(eb["pe"])
 
@@ -159,4 +159,4 @@ def test_overfull_group_falls_back_to_the_list_walk_and_back(walk):
         s.step(2)
         assert s.passes()["active"] == 1
         pos, f, img = s.positions(), s.forces(), s.get(md.MD_GET_IMAGE)
-    assert_mixed_forces(wk, pos, f, img, staged=True)
+    assert_mixed_forces(wk, pos, f, img)

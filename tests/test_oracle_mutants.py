@@ -16,6 +16,7 @@ from oracle import build as oracle_build
 
 sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
 import test_oracle_pins as pins  # noqa: E402
+import test_pc3_pins as pc3_pins  # noqa: E402
 import test_surrogate_pins as sur_pins  # noqa: E402
 import test_thermostat_pins as nvt_pins  # noqa: E402
 
@@ -69,6 +70,12 @@ MUTANTS = [
     ("Nose-Hoover friction with the wrong sign",
      "double s = exp(-thermo[0] * h);", "double s = exp(thermo[0] * h);",
      [nvt_pins.test_extended_energy_is_conserved_with_dt2_error, nvt_pins.test_temperature_settles_at_the_target]),
+    ("predictor-corrector velocity coefficient 3/4 (another scheme's) instead of 5/6",
+     "c1 = 5.0 / 6.0", "c1 = 3.0 / 4.0",
+     [pc3_pins.test_error_order_from_a_consistent_start_and_from_a_zero_third_derivative]),
+    ("predictor without the third-derivative term of the velocity",
+     "q1[k] += 2.0 * q2[k] + 3.0 * gear3[k];", "q1[k] += 2.0 * q2[k];",
+     [pc3_pins.test_error_order_from_a_consistent_start_and_from_a_zero_third_derivative]),
     ("surrogate basis derivative without its Gaussian term",
      "db[k] = e * (dfc - a / w2 * fc);", "db[k] = e * dfc;",
      [sur_pins.test_surrogate_forces_are_minus_energy_gradient]),
