@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define MD_ABI_VERSION 4
+#define MD_ABI_VERSION 5
 
 typedef struct md_ctx md_ctx; /* opaque, owned by the library */
 
@@ -127,7 +127,27 @@ typedef struct {
                                count (see md_tune).  Results depend on it only in rounding. */
     int32_t passes;         /* MD_PASSES_AUTO (0), MD_PASSES_LIST, MD_PASSES_STAGED, MD_PASSES_CELLS or
                                MD_PASSES_HALF: how the mixed-precision step kernel walks the neighbours */
+    int32_t integrator;     /* MD_INTEGRATOR_VERLET (0) or MD_INTEGRATOR_PC3 (Table 1 `iverlet`: 1 and 0
+                               respectively; see below) */
 } md_config;
+
+/*
+ * Time integrator of md_step (§2.3: the paper offers two).
+ *   VERLET: velocity Verlet (time reversible, bounded energy error in NVE).
+ *   PC3: the third-order predictor-corrector (after Gear) for r'' = F/m on the scaled Taylor
+ *     vector (r, dt v, (dt^2/2) a, (dt^3/6) b), b = da/dt: predict by the Taylor series to third
+ *     order, evaluate the forces once at the predicted positions, then correct every term by
+ *     c_k D with D = (dt^2/2) F/m - (the predicted acceleration term) and c = (1/6, 5/6, 1, 1/3).
+ *     After md_step the forces (md_get) and the potential energy (md_energy) are those of the last
+ *     predicted positions, the positions and velocities the corrected ones.  The third-derivative
+ *     term is kept per atom between md_step calls; it starts at zero at md_create and is set to
+ *     zero by md_set_state (and md_step_io, which calls it): the predictor restarts.  The
+ *     acceleration term comes from the stored forces at each md_step, so an md_eam_forces call
+ *     between steps restarts it from the forces at the current positions.  PC3 takes the list
+ *     walk and no strain ramp, thermostat or surrogate (MD_ERR_ARG at md_create, MD_ERR_STATE at
+ *     md_set_thermostat).
+ */
+enum { MD_INTEGRATOR_VERLET = 0, MD_INTEGRATOR_PC3 = 1 };
 
 /*
  * Neighbour walk of the two EAM passes in the step kernel (md_step).  LIST: every atom reads

@@ -361,6 +361,7 @@ StepParams step_params(md_ctx *ctx, int n_steps) {
         sp.rep_off = ctx->d_rep_off;
     }
     sp.spin_limit = kSpinLimit;
+    sp.motion = ctx->cfg.integrator == MD_INTEGRATOR_PC3 ? kMotionPC3 : kMotionVerlet;
     return sp;
 }
 
@@ -441,6 +442,13 @@ md_status create_common(md_ctx *ctx, const md_config *cfg, const md_potential *p
     if (n < 0 || n > INT32_MAX / 8) return MD_ERR_ARG;
     if (cfg->k_max < 1 || cfg->skin < 0.0 || !(cfg->dt_fs >= 0.0) || cfg->rebuild_every < 0) return MD_ERR_ARG;
     if (cfg->precision != MD_PREC_FP64 && cfg->precision != MD_PREC_MIXED) return MD_ERR_ARG;
+    if (cfg->integrator != MD_INTEGRATOR_VERLET && cfg->integrator != MD_INTEGRATOR_PC3) return MD_ERR_ARG;
+    if (cfg->integrator == MD_INTEGRATOR_PC3 &&
+        (cfg->strain_rate_zz != 0.0 || pot->kind == MD_POT_SURROGATE ||
+         (cfg->passes != MD_PASSES_AUTO && cfg->passes != MD_PASSES_LIST))) {
+        ctx->err = "the predictor-corrector takes the list walk, no strain ramp and no surrogate";
+        return MD_ERR_ARG;
+    }
     for (double l : L)
         if (!(l > 0.0)) return MD_ERR_BOX;
     // potential (§3.1)
@@ -593,6 +601,12 @@ md_status create_common(md_ctx *ctx, const md_config *cfg, const md_potential *p
     // FP64, one species: the per-entry derivative cache of the force pass (16 B per list entry)
     if (MD_FP64_DCACHE && cfg->precision == MD_PREC_FP64 && pot->kind != MD_POT_SURROGATE && ns == 1)
         chk(dalloc(ctx, &A.dcache, nbr_entries(n, cfg->k_max)));
+    if (cfg->integrator == MD_INTEGRATOR_PC3) {
+        chk(dalloc(ctx, &A.g2, n)); chk(dalloc(ctx, &A.g3, n));
+        chk(dalloc(ctx, &A.g2_tmp, n)); chk(dalloc(ctx, &A.g3_tmp, n));
+        if (e == cudaSuccess) e = cudaMemset(A.g2, 0, sizeof(double4_32a) * (size_t)(n > 0 ? n : 1));
+        if (e == cudaSuccess) e = cudaMemset(A.g3, 0, sizeof(double4_32a) * (size_t)(n > 0 ? n : 1));
+    }
     if (n_rep > 1) chk(dalloc(ctx, &A.rep, n));
     A.sorted = A.cell_of;  // cell_of is consumed by the scatter before the in-cell sort writes
     // partial-sum rows: a stand-alone force launch (<= 8 lanes) or a persistent grid
@@ -715,6 +729,7 @@ md_status create_common(md_ctx *ctx, const md_config *cfg, const md_potential *p
         std::vector<float> VP32(npair * nk * 8);
         std::vector<float4> D32;
         std::vector<float> V0;
+        std::vector<double4_32a> D64;
         const size_t tl = 2 * (size_t)nk;
         for (int a = 0; a < ns; a++)
             for (int b = 0; b < ns; b++) {
@@ -750,6 +765,12 @@ md_status create_common(md_ctx *ctx, const md_config *cfg, const md_potential *p
                                              pack(2.0 * rp[k].z / sp, 3.0 * rp[k].w / sp));
                     P.dsv = (float)sv;
                     P.dsp = (float)sp;
+                    D64.resize(2 * (size_t)nk);
+                    const double s = P.inv_dr;
+                    for (int k = 0; k < nk; k++) {
+                        D64[2 * k] = make_double4_32a(rv[k].y * s, 2.0 * rv[k].z * s, 3.0 * rv[k].w * s, 0.0);
+                        D64[2 * k + 1] = make_double4_32a(rp[k].y * s, 2.0 * rp[k].z * s, 3.0 * rp[k].w * s, 0.0);
+                    }
                 }
                 for (int k = 0; k < nk; k++) {
                     VP64[(base + k) * 2] = rv[k];
@@ -772,6 +793,13 @@ md_status create_common(md_ctx *ctx, const md_config *cfg, const md_potential *p
         P.VP64 = dVP64;
         P.VP32 = dVP32;
         P.F64 = dF64;
+        if (!D64.empty()) {
+            double4_32a *dD64;
+            chk(dalloc(ctx, &dD64, D64.size()));
+            if (e != cudaSuccess) return fail(ctx, MD_ERR_OOM, "table allocation", e);
+            chk(cudaMemcpy(dD64, D64.data(), D64.size() * sizeof(double4_32a), cudaMemcpyHostToDevice));
+            P.D64 = dD64;
+        }
         if (!D32.empty()) {
             float4 *dD32;
             chk(dalloc(ctx, &dD32, D32.size()));
@@ -1048,7 +1076,8 @@ md_status md_create_batch(int32_t n_replicas, const md_config *cfgs, const md_po
         const md_config &c = cfgs[r];
         if (c.n_atoms < 0 || (!pos[r] && c.n_atoms > 0)) return MD_ERR_ARG;
         if (c.skin != c0.skin || c.k_max != c0.k_max || c.dt_fs != c0.dt_fs || c.precision != c0.precision ||
-            c.rebuild_every != c0.rebuild_every || c.strain_rate_zz != c0.strain_rate_zz)
+            c.rebuild_every != c0.rebuild_every || c.strain_rate_zz != c0.strain_rate_zz ||
+            c.integrator != c0.integrator)
             return MD_ERR_ARG;
         for (int a = 0; a < 3; a++)
             for (int b = 0; b < 3; b++)
@@ -1153,6 +1182,8 @@ md_status enqueue_state_in(md_ctx *ctx, const double *pos, const double *vel, co
         ctx->launches++;
         ctx->sur_ref = false;
     }
+    if (ctx->A.g3 && (pos || vel || force))   // the predictor-corrector restarts from this state
+        MD_CK(cudaMemsetAsync(ctx->A.g3, 0, sizeof(double4_32a) * ctx->n, ctx->stream));
     if (pos || force) ctx->forces_valid = (force != nullptr);
     ctx->energy_valid = false;
     return MD_OK;
@@ -1459,6 +1490,7 @@ md_status md_tune(md_ctx *ctx, int32_t *lanes_out) {
         };
         StepParams sp = step_params(ctx, 3);
         sp.thermo = nullptr;   // trial steps leave the thermostat alone
+        sp.motion = kMotionVerlet;   // and the predictor-corrector's Taylor terms (same passes)
         sp.lim2 = 1e300;
         sp.rebuild_every = 0;
         sp.strain_scale = 1.0;
@@ -1779,6 +1811,8 @@ md_status md_sur_train(md_ctx *ctx, int32_t n_iter, int32_t rep_begin, int32_t r
 md_status md_set_thermostat(md_ctx *ctx, int32_t on, const double *t_kelvin, const double *tau_fs) {
     if (!ctx) return MD_ERR_ARG;
     if (ctx->sur) return fail(ctx, MD_ERR_STATE, "the thermostat runs in the EAM step kernel");
+    if (ctx->cfg.integrator == MD_INTEGRATOR_PC3 && on)
+        return fail(ctx, MD_ERR_STATE, "the thermostat steps with velocity Verlet, not the predictor-corrector");
     if (!on) {
         if (ctx->thermo_on) drop_graphs(ctx);
         ctx->thermo_on = false;

@@ -187,6 +187,41 @@ __device__ __forceinline__ void kick_and_partials(double4_32a &v, double fx, dou
     }
 }
 
+// Gear's corrector coefficients of the third-order predictor-corrector for a second-order equation
+// (four Taylor terms): position, velocity (scaled by dt), acceleration (1), third derivative.
+constexpr double kPcPos = 1.0 / 6.0, kPcVel = 5.0 / 6.0, kPcJerk = 1.0 / 3.0;
+
+// What follows atom i's force f: motion kMotionVerlet: the second half kick v += (dt/2) f/m;
+// kMotionPC3: the corrector, D = (dt^2/2) f/m - g2 (g2 = the predicted acceleration term), then
+// r += D/6, v += (5/6) D/dt, g3 += D/3 (the acceleration term becomes (dt^2/2) f/m, which the
+// next predictor takes from the stored force).  v (in/out) is the atom's velocity record.
+__device__ __forceinline__ void finish_motion(const Atoms &A, int i, double4_32a &v, double fx, double fy, double fz,
+                                              double half_dt, int motion) {
+    if (motion == kMotionVerlet) {
+        kick_and_partials(v, fx, fy, fz, half_dt, true);
+        A.vel[i] = v;
+    } else if (motion == kMotionPC3) {
+        const double dt = 2.0 * half_dt, h2 = 0.5 * dt * dt;
+        const double4_32a q2 = A.g2[i];
+        double4_32a q3 = A.g3[i], p = A.pos[i];
+        const double Dx = __dsub_rn(__dmul_rn(__dmul_rn(h2, fx), v.w), q2.x);
+        const double Dy = __dsub_rn(__dmul_rn(__dmul_rn(h2, fy), v.w), q2.y);
+        const double Dz = __dsub_rn(__dmul_rn(__dmul_rn(h2, fz), v.w), q2.z);
+        p.x = __dadd_rn(p.x, __dmul_rn(kPcPos, Dx));
+        p.y = __dadd_rn(p.y, __dmul_rn(kPcPos, Dy));
+        p.z = __dadd_rn(p.z, __dmul_rn(kPcPos, Dz));
+        v.x = __dadd_rn(v.x, __ddiv_rn(__dmul_rn(kPcVel, Dx), dt));
+        v.y = __dadd_rn(v.y, __ddiv_rn(__dmul_rn(kPcVel, Dy), dt));
+        v.z = __dadd_rn(v.z, __ddiv_rn(__dmul_rn(kPcVel, Dz), dt));
+        q3.x = __dadd_rn(q3.x, __dmul_rn(kPcJerk, Dx));
+        q3.y = __dadd_rn(q3.y, __dmul_rn(kPcJerk, Dy));
+        q3.z = __dadd_rn(q3.z, __dmul_rn(kPcJerk, Dz));
+        A.pos[i] = p;
+        A.vel[i] = v;
+        A.g3[i] = q3;
+    }
+}
+
 // Host-side grid size of a T-lanes-per-atom launch.
 template <int T>
 inline int blocks_for_lanes(long long n) {

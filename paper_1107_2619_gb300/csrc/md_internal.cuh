@@ -22,6 +22,9 @@ constexpr double kEva3ToGpa = kEvJ * 1.0e30 / 1.0e9;
 enum : int32_t { FLAG_OVERFLOW = 1, FLAG_NONFINITE = 2, FLAG_TIMEOUT = 4 };
 
 constexpr int kThreads = 128;     // threads per block of the per-atom kernels
+// After an atom's force: nothing, the second half kick of velocity Verlet, or the corrector of the
+// third-order predictor-corrector (md.h MD_INTEGRATOR_PC3).
+enum : int { kMotionNone = 0, kMotionVerlet = 1, kMotionPC3 = 2 };
 constexpr int kPartials = 11;     // per-block FP64 partial sums: pe, sum m v^2, W(6), p(3)
 constexpr int kStampsPerStep = 12;  // %globaltimer stamps per step of the persistent kernel
 
@@ -69,6 +72,9 @@ struct Pot {
     // c1 of phi, then (2 c2, 3 c3) of V and of phi as binary16 pairs scaled by 1/dsv and 1/dsp
     const float4 *D32;
     const float *V0;          // one species: [k] c0 of the V rows (V itself on the energy step)
+    // one species, FP64 derivative cache: [2k + {0: V, 1: phi}] = (c1, 2 c2, 3 c3, 0) * inv_dr, the
+    // r-derivative of the interval's cubic as a quadratic in t
+    const double4_32a *D64;
     float dsv, dsp;
     // explicit knot sums (MD_POT_KNOTS): function t (V[a][b] = a*ns+b, phi[a][b] = ns*ns + a*ns+b)
     // has nkt terms (coefficient, radius) at K64/K32 + t*nkt; F_a = -A[a] sqrt(rho)
@@ -125,6 +131,10 @@ struct Atoms {
     int32_t *lcount;                         // half walk: entries of each half row
     double *rho_acc;                         // half walk: density accumulators [n]
     double4_32a *f_acc;                      // half walk: force (x, y, z) and pair-energy (w) accumulators
+    double4_32a *g2, *g3;                    // predictor-corrector (md.h MD_INTEGRATOR_PC3): the predicted
+                                             // acceleration term (dt^2/2) a and the third-derivative term
+                                             // (dt^3/6) da/dt of each atom (NULL under velocity Verlet)
+    double4_32a *g2_tmp, *g3_tmp;            // their renumbering scratch
     double *partials;                        // [kPartials][part_stride] per-block sums
     int part_stride;
     int32_t *rep;                            // replica of each slot (NULL: one system)
@@ -269,6 +279,9 @@ struct StepParams {
     const int32_t *rep_off;  // [n_rep + 1]
     unsigned long long spin_limit;
     int withhold_arrival;  // self-test of the bounded wait: block 0 skips its first arrival
+    int motion;            // kMotionVerlet or kMotionPC3: what the force pass does to each atom after
+                           // its force (second half kick, or the corrector) and what opens a step
+                           // (half kick + drift, or the predictor)
 };
 // With sp.n_steps == 0 it only prepares the launch (function attributes, occupancy query):
 // done before a stream capture, so that a captured launch makes no other API call.

@@ -260,13 +260,12 @@ __device__ __forceinline__ void lane_sum_acc(Acc32 &a) {
 
 // End of the force pass for atom i: the force, the second half kick and the FP64 partial sums.
 template <bool ENERGY>
-__device__ __forceinline__ void force32_finish(const Atoms &A, int i, const Acc32 &a, double half_dt, bool kick,
+__device__ __forceinline__ void force32_finish(const Atoms &A, int i, const Acc32 &a, double half_dt, int motion,
                                                double (&part)[kPartials]) {
     A.force[i] = make_double4_32a(a.fx, a.fy, a.fz, 0.0);
     if (!isfinite(a.fx + a.fy + a.fz)) atomicOr(&A.flags->error, FLAG_NONFINITE);
     double4_32a v = A.vel[i];
-    kick_and_partials(v, a.fx, a.fy, a.fz, half_dt, kick);
-    if (kick) A.vel[i] = v;
+    finish_motion(A, i, v, a.fx, a.fy, a.fz, half_dt, motion);
     if (ENERGY) {
         const double e = A.e_atom[i] + (double)a.ep;
         A.e_atom[i] = e;
@@ -333,7 +332,7 @@ __device__ __forceinline__ void density32_item(const Atoms &A, const Pot &P, con
 // Returns the atom index for the lane that finished atom i (lane 0 of a live atom), else -1.
 template <int T, int KIND, bool MULTI, bool ENERGY, bool SMT = false>
 __device__ __forceinline__ int force32_item(const Atoms &A, const Pot &P, const Box *boxes, long long g,
-                                            double half_dt, bool kick, double (&part)[kPartials]) {
+                                            double half_dt, int motion, double (&part)[kPartials]) {
     const int i = (int)(g / T), lane = (int)(g & (T - 1));
     const bool live = i < A.n;
     Acc32 a;
@@ -374,7 +373,7 @@ __device__ __forceinline__ int force32_item(const Atoms &A, const Pot &P, const 
     }
     lane_sum_acc<T, ENERGY>(a);
     if (!(live && lane == 0)) return -1;
-    force32_finish<ENERGY>(A, i, a, half_dt, kick, part);
+    force32_finish<ENERGY>(A, i, a, half_dt, motion, part);
     return i;
 }
 
@@ -436,12 +435,11 @@ __device__ __forceinline__ void density64_item(const Atoms &A, const Pot &P, con
                     const size_t ab = ((size_t)(si * P.ns + sj) * P.nk + kr) * 2;
                     const double4_32a c = P.VP64[ab + 1];
                     rho += cubic(t, c.x, c.y, c.z, c.w, below, d);
-                    if (keep) {
-                        const double4_32a cv = P.VP64[ab];
-                        double dV;
-                        cubic(t, cv.x, cv.y, cv.z, cv.w, below, dV);
-                        const double sc = P.inv_dr * rinv;
-                        *drow.ptr(k) = make_double2(dV * sc, d * sc);
+                    if (keep) {   // r-derivatives from the interval's derivative rows (inv_dr folded in)
+                        const double4_32a dv = P.D64[2 * kr], dp = P.D64[2 * kr + 1];
+                        const double dV = below ? dv.x : fma(t, fma(dv.z, t, dv.y), dv.x);
+                        const double dphi = below ? dp.x : fma(t, fma(dp.z, t, dp.y), dp.x);
+                        *drow.ptr(k) = make_double2(dV * rinv, dphi * rinv);
                     }
                 }
             }
@@ -460,15 +458,18 @@ __device__ __forceinline__ void density64_item(const Atoms &A, const Pot &P, con
     }
 }
 
-// The FP64 force pass from the derivative cache of the density pass (one species, no energies):
-// per entry the separation, then f_i += [V'/r + (F'_i + F'_j) phi'/r] d.  The same terms as the
-// full evaluation below, in another order of rounding.
-template <int T>
-__device__ __forceinline__ int force64_cached_item(const Atoms &A, const Box *boxes, long long g, double half_dt,
-                                                   bool kick) {
+// The FP64 force pass from the derivative cache of the density pass (one species): per entry the
+// separation, then f_i += [V'/r + (F'_i + F'_j) phi'/r] d, the same terms as the full evaluation
+// below in another order of rounding.  With ENERGY the pair energy V(r) and the virial are added
+// (r from the separation), while the force takes the same operations as without, so that a run
+// does not depend on which of its steps evaluate energies.
+template <int T, int KIND, bool ENERGY>
+__device__ __forceinline__ int force64_cached_item(const Atoms &A, const Pot &P, const Box *boxes, long long g,
+                                                   double half_dt, int motion, double (&part)[kPartials]) {
     const int i = (int)(g / T), lane = (int)(g & (T - 1));
     const bool live = i < A.n;
-    double fx = 0.0, fy = 0.0, fz = 0.0;
+    double fx = 0.0, fy = 0.0, fz = 0.0, ep = 0.0;
+    double wxx = 0.0, wyy = 0.0, wzz = 0.0, wyz = 0.0, wxz = 0.0, wxy = 0.0;
     const bool wrap = needs_image(A, i, live);
     if (live) {
         const Box &B = boxes[ph::replica_of(A, i)];
@@ -490,6 +491,32 @@ __device__ __forceinline__ int force64_cached_item(const Atoms &A, const Box *bo
                 fx = fma(gr, dx, fx);
                 fy = fma(gr, dy, fy);
                 fz = fma(gr, dz, fz);
+                if (ENERGY) {
+                    const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+                    if (r2 < P.rc2) {
+                        const double r = r2 * rsqrt64(r2);
+                        double V, dV;
+                        if (KIND == MD_POT_FS_ANALYTIC) {
+                            V = fs_V<double>(P.fs, r, dV);
+                        } else if (KIND == MD_POT_KNOTS) {
+                            V = knot_sum<double, double2>(P.K64, P.nkt, r, dV);
+                        } else {
+                            double t;
+                            bool below;
+                            const int kr = knot_row((r - P.r_min) * P.inv_dr, P.nk, t, below);
+                            const double4_32a cv = P.VP64[(size_t)kr * 2];
+                            V = cubic(t, cv.x, cv.y, cv.z, cv.w, below, dV);
+                        }
+                        ep = fma(0.5, V, ep);
+                    }
+                    const double hg = -0.5 * gr;
+                    wxx = fma(hg * dx, dx, wxx);
+                    wyy = fma(hg * dy, dy, wyy);
+                    wzz = fma(hg * dz, dz, wzz);
+                    wyz = fma(hg * dy, dz, wyz);
+                    wxz = fma(hg * dx, dz, wxz);
+                    wxy = fma(hg * dx, dy, wxy);
+                }
             }
         };
         if (wrap) walk(std::true_type{});
@@ -498,20 +525,34 @@ __device__ __forceinline__ int force64_cached_item(const Atoms &A, const Box *bo
     fx = lane_sum<T>(fx);
     fy = lane_sum<T>(fy);
     fz = lane_sum<T>(fz);
+    if (ENERGY) {
+        ep = lane_sum<T>(ep);
+        wxx = lane_sum<T>(wxx); wyy = lane_sum<T>(wyy); wzz = lane_sum<T>(wzz);
+        wyz = lane_sum<T>(wyz); wxz = lane_sum<T>(wxz); wxy = lane_sum<T>(wxy);
+    }
     if (!(live && lane == 0)) return -1;
     A.force[i] = make_double4_32a(fx, fy, fz, 0.0);
     if (!isfinite(fx + fy + fz)) atomicOr(&A.flags->error, FLAG_NONFINITE);
     double4_32a v = A.vel[i];
-    kick_and_partials(v, fx, fy, fz, half_dt, kick);
-    if (kick) A.vel[i] = v;
+    finish_motion(A, i, v, fx, fy, fz, half_dt, motion);
+    if (ENERGY) {
+        const double e = A.e_atom[i] + ep;
+        A.e_atom[i] = e;
+        const double m = 1.0 / (kMvv2e * v.w);
+        part[0] += e;
+        part[1] += m * fma(v.x, v.x, fma(v.y, v.y, v.z * v.z));
+        part[2] += wxx; part[3] += wyy; part[4] += wzz;
+        part[5] += wyz; part[6] += wxz; part[7] += wxy;
+        part[8] += m * v.x; part[9] += m * v.y; part[10] += m * v.z;
+    }
     return i;
 }
 
 template <int T, int KIND, bool MULTI, bool ENERGY>
 __device__ __forceinline__ int force64_item(const Atoms &A, const Pot &P, const Box *boxes, long long g,
-                                            double half_dt, bool kick, double (&part)[kPartials]) {
-    if constexpr (!MULTI && !ENERGY) {
-        if (A.dcache) return force64_cached_item<T>(A, boxes, g, half_dt, kick);
+                                            double half_dt, int motion, double (&part)[kPartials]) {
+    if constexpr (!MULTI) {
+        if (A.dcache) return force64_cached_item<T, KIND, ENERGY>(A, P, boxes, g, half_dt, motion, part);
     }
     const int i = (int)(g / T), lane = (int)(g & (T - 1));
     const bool live = i < A.n;
@@ -609,8 +650,7 @@ __device__ __forceinline__ int force64_item(const Atoms &A, const Pot &P, const 
     A.force[i] = make_double4_32a(fx, fy, fz, 0.0);
     if (!isfinite(fx + fy + fz)) atomicOr(&A.flags->error, FLAG_NONFINITE);
     double4_32a v = A.vel[i];
-    kick_and_partials(v, fx, fy, fz, half_dt, kick);
-    if (kick) A.vel[i] = v;
+    finish_motion(A, i, v, fx, fy, fz, half_dt, motion);
     if (ENERGY) {
         const double e = A.e_atom[i] + ep;
         A.e_atom[i] = e;
@@ -633,9 +673,9 @@ __device__ __forceinline__ void density_item(const Atoms &A, const Pot &P, const
 
 template <int PREC, int T, int KIND, bool MULTI, bool ENERGY, bool SMT = false>
 __device__ __forceinline__ int force_item(const Atoms &A, const Pot &P, const Box *boxes, long long g,
-                                          double half_dt, bool kick, double (&part)[kPartials]) {
-    if (PREC == MD_PREC_FP64) return force64_item<T, KIND, MULTI, ENERGY>(A, P, boxes, g, half_dt, kick, part);
-    return force32_item<T, KIND, MULTI, ENERGY, SMT>(A, P, boxes, g, half_dt, kick, part);
+                                          double half_dt, int motion, double (&part)[kPartials]) {
+    if (PREC == MD_PREC_FP64) return force64_item<T, KIND, MULTI, ENERGY>(A, P, boxes, g, half_dt, motion, part);
+    return force32_item<T, KIND, MULTI, ENERGY, SMT>(A, P, boxes, g, half_dt, motion, part);
 }
 
 }  // namespace ps

@@ -127,6 +127,44 @@ __device__ __forceinline__ void kick_drift(const Atoms &A, const Box *boxes, int
     if (A.posd) A.posd[i] = build_image64(p, r, boxes[replica_of(A, i)]);
 }
 
+// The predictor of the third-order predictor-corrector (md.h MD_INTEGRATOR_PC3): from the force f
+// of the last evaluation (acceleration term q2 = (dt^2/2) f/m) and the third-derivative term q3,
+//   r += dt v + q2 + q3,  v += (2 q2 + 3 q3) / dt,  g2 = q2 + 3 q3 (the predicted acceleration
+// term, for the corrector), then the skin check and the pass copies, as after a drift.
+__device__ __forceinline__ void predict_pc3(const Atoms &A, const Box *boxes, int i, double dt, double lim2) {
+    double4_32a v = A.vel[i], p = A.pos[i];
+    const double4_32a f = A.force[i], q3 = A.g3[i];
+    const double h2 = 0.5 * dt * dt;
+    const double ax = __dmul_rn(__dmul_rn(h2, f.x), v.w), ay = __dmul_rn(__dmul_rn(h2, f.y), v.w),
+                 az = __dmul_rn(__dmul_rn(h2, f.z), v.w);
+    p.x = __dadd_rn(p.x, __dadd_rn(__dadd_rn(__dmul_rn(dt, v.x), ax), q3.x));
+    p.y = __dadd_rn(p.y, __dadd_rn(__dadd_rn(__dmul_rn(dt, v.y), ay), q3.y));
+    p.z = __dadd_rn(p.z, __dadd_rn(__dadd_rn(__dmul_rn(dt, v.z), az), q3.z));
+    const double bx = __dmul_rn(3.0, q3.x), by = __dmul_rn(3.0, q3.y), bz = __dmul_rn(3.0, q3.z);
+    v.x = __dadd_rn(v.x, __ddiv_rn(__dadd_rn(__dmul_rn(2.0, ax), bx), dt));
+    v.y = __dadd_rn(v.y, __ddiv_rn(__dadd_rn(__dmul_rn(2.0, ay), by), dt));
+    v.z = __dadd_rn(v.z, __ddiv_rn(__dadd_rn(__dmul_rn(2.0, az), bz), dt));
+    A.g2[i] = make_double4_32a(__dadd_rn(ax, bx), __dadd_rn(ay, by), __dadd_rn(az, bz), 0.0);
+    A.vel[i] = v;
+    A.pos[i] = p;
+    const double4_32a r = A.ref[i];
+    const double ex = __dsub_rn(p.x, r.x), ey = __dsub_rn(p.y, r.y), ez = __dsub_rn(p.z, r.z);
+    const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
+    if (d2 > lim2 || !(d2 == d2)) {
+        A.flags->need_rebuild = 1;
+        A.flags->skin_exceeded = 1;
+    }
+    A.posf[i] = build_image(p, r, boxes[replica_of(A, i)], A.spec[i]);
+    if (A.posd) A.posd[i] = build_image64(p, r, boxes[replica_of(A, i)]);
+}
+
+// What opens a step: the half kick and drift of velocity Verlet, or the predictor.
+__device__ __forceinline__ void open_step(const Atoms &A, const Box *boxes, int i, int motion, double half_dt,
+                                          double dt, double s, bool strain, double lim2, const Thermo *th = nullptr) {
+    if (motion == kMotionPC3) predict_pc3(A, boxes, i, dt, lim2);
+    else kick_drift(A, boxes, i, half_dt, dt, s, strain, lim2, th);
+}
+
 __device__ __forceinline__ void check_displacement(const Atoms &A, int i, double lim2) {
     const double4_32a p = A.pos[i], r = A.ref[i];
     const double ex = __dsub_rn(p.x, r.x), ey = __dsub_rn(p.y, r.y), ez = __dsub_rn(p.z, r.z);
@@ -262,6 +300,10 @@ __device__ __forceinline__ void gather_atom(const Atoms &A, int k) {
     A.force_tmp[k] = A.force[o];
     A.id_tmp[k] = A.id[o];
     A.spec_tmp[k] = A.spec[o];
+    if (A.g3) {
+        A.g2_tmp[k] = A.g2[o];
+        A.g3_tmp[k] = A.g3[o];
+    }
 }
 
 __device__ __forceinline__ void copyback_atom(const Atoms &A, const Box *boxes, int k) {
@@ -274,6 +316,10 @@ __device__ __forceinline__ void copyback_atom(const Atoms &A, const Box *boxes, 
     A.id[k] = id;
     A.spec[k] = sp;
     A.rank[id] = k;
+    if (A.g3) {
+        A.g2[k] = A.g2_tmp[k];
+        A.g3[k] = A.g3_tmp[k];
+    }
     A.posf[k] = wrapped(p, boxes[replica_of(A, k)], sp);
     if (A.posd) A.posd[k] = wrapped64(p, boxes[replica_of(A, k)]);
 }

@@ -1,5 +1,7 @@
-// The persistent step kernel: n velocity-Verlet steps (§2.3) of one system or of a batch of
-// replicas in ONE cooperative launch.  Phases are separated by a grid barrier:
+// The persistent step kernel: n time steps (§2.3: velocity Verlet, or the third-order
+// predictor-corrector, sp.motion) of one system or of a batch of replicas in ONE cooperative
+// launch.  Under the predictor-corrector "half kick + drift" below reads "predictor" and "half
+// kick" after the force reads "corrector".  Phases are separated by a grid barrier:
 //
 //   [box update (strain)] -> half kick + drift + skin check              (first step only)
 //   per step:  [rebuild: bin | scan x3 | scatter | cell sort | gather | copyback | list]
@@ -187,8 +189,8 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? MD_STEP_MIN_BLOCKS : 1)
         MD_SYNC();
     }
     for (long long i = tid; i < A.n; i += stride) {
-        ph::kick_drift(A, boxes, (int)i, sp.half_dt, sp.dt, sp.strain_scale, strain, sp.lim2,
-                       thermo ? sp.thermo : nullptr);
+        ph::open_step(A, boxes, (int)i, sp.motion, sp.half_dt, sp.dt, sp.strain_scale, strain, sp.lim2,
+                      thermo ? sp.thermo : nullptr);
         if constexpr (WALK == kWalkHalf) A.rho_acc[i] = 0.0;
     }
     if (sp.withhold_arrival && blockIdx.x == 0) {
@@ -338,7 +340,7 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? MD_STEP_MIN_BLOCKS : 1)
             }
             if (!tiled)
                 for (long long g = tid; g < items; g += stride)
-                    ps::force_item<PREC, T, KIND, MULTI, true, SMT>(A, P, boxes, g, sp.half_dt, true, part);
+                    ps::force_item<PREC, T, KIND, MULTI, true, SMT>(A, P, boxes, g, sp.half_dt, sp.motion, part);
             eam::block_partials<NT>(part, A.partials, A.part_stride);
         } else {
             if constexpr (WALK != kWalkList) {
@@ -377,10 +379,10 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? MD_STEP_MIN_BLOCKS : 1)
             }
             if (!tiled)
                 for (long long g = tid; g < items; g += stride) {
-                    const int i =
-                        ps::force_item<PREC, T, KIND, MULTI, false, SMT>(A, P, boxes, g, sp.half_dt, true, part);
+                    const int i = ps::force_item<PREC, T, KIND, MULTI, false, SMT>(A, P, boxes, g, sp.half_dt,
+                                                                                   sp.motion, part);
                     if (fuse && i >= 0)
-                        ph::kick_drift(A, boxes, i, sp.half_dt, sp.dt, sp.strain_scale, false, sp.lim2);
+                        ph::open_step(A, boxes, i, sp.motion, sp.half_dt, sp.dt, sp.strain_scale, false, sp.lim2);
                 }
         }
         MD_SYNC();

@@ -51,10 +51,13 @@ class md_config(C.Structure):
     _fields_ = [("n_atoms", C.c_int64), ("h", C.c_double * 9), ("skin", C.c_double),
                 ("k_max", C.c_int32), ("rebuild_every", C.c_int32), ("dt_fs", C.c_double),
                 ("precision", C.c_int32), ("strict_skin", C.c_int32), ("strain_rate_zz", C.c_double),
-                ("stream", C.c_void_p), ("lanes_per_atom", C.c_int32), ("passes", C.c_int32)]
+                ("stream", C.c_void_p), ("lanes_per_atom", C.c_int32), ("passes", C.c_int32),
+                ("integrator", C.c_int32)]
 
 
 MD_PASSES_AUTO, MD_PASSES_LIST, MD_PASSES_STAGED, MD_PASSES_CELLS, MD_PASSES_HALF = 0, 1, 2, 3, 4
+MD_INTEGRATOR_VERLET, MD_INTEGRATOR_PC3 = 0, 1
+INTEGRATORS = {"verlet": MD_INTEGRATOR_VERLET, "pc3": MD_INTEGRATOR_PC3}
 PASSES = {"auto": MD_PASSES_AUTO, "list": MD_PASSES_LIST, "staged": MD_PASSES_STAGED, "cells": MD_PASSES_CELLS,
           "half": MD_PASSES_HALF}
 WALKS = {v: k for k, v in PASSES.items()}
@@ -430,7 +433,8 @@ def make_potential(pot: _inputs.Potential):
 
 
 def make_config(n_atoms, box, skin, k_max, dt_fs, precision=MD_PREC_FP64, rebuild_every=0,
-                strict_skin=False, strain_rate_zz=0.0, stream=None, lanes_per_atom=0, passes="auto"):
+                strict_skin=False, strain_rate_zz=0.0, stream=None, lanes_per_atom=0, passes="auto",
+                integrator="verlet"):
     c = md_config()
     c.n_atoms = int(n_atoms)
     for k in range(9):
@@ -442,6 +446,7 @@ def make_config(n_atoms, box, skin, k_max, dt_fs, precision=MD_PREC_FP64, rebuil
     c.stream = C.c_void_p(stream) if stream else None
     c.lanes_per_atom = int(lanes_per_atom)
     c.passes = PASSES[passes]
+    c.integrator = INTEGRATORS[integrator]
     return c
 
 
@@ -450,12 +455,12 @@ class System:
 
     def __init__(self, w: _inputs.Workload, precision: str = "fp64", rebuild_every: int = 0,
                  strict_skin: bool = False, stream=None, device_inputs: bool = False, k_max=None,
-                 lanes_per_atom: int = 0, passes: str = "auto"):
+                 lanes_per_atom: int = 0, passes: str = "auto", integrator: str = "verlet"):
         prec = MD_PREC_FP64 if precision == "fp64" else MD_PREC_MIXED
         self.n = w.n_atoms
         self.k_max = int(k_max or w.k_max)
         self.config = make_config(w.n_atoms, w.box, w.skin, self.k_max, w.dt_fs, prec, rebuild_every,
-                                  strict_skin, w.strain_rate_zz, stream, lanes_per_atom, passes)
+                                  strict_skin, w.strain_rate_zz, stream, lanes_per_atom, passes, integrator)
         pot, keep = make_potential(w.potential)
         pos = np.ascontiguousarray(w.pos, dtype=np.float64)
         vel = np.ascontiguousarray(w.vel, dtype=np.float64)
@@ -568,12 +573,13 @@ class Batch(System):
     """A batch of independent replicas in one context (md_create_batch)."""
 
     def __init__(self, workloads, precision: str = "mixed", rebuild_every: int = 0, stream=None,
-                 k_max=None, lanes_per_atom: int = 0):
+                 k_max=None, lanes_per_atom: int = 0, integrator: str = "verlet"):
         prec = MD_PREC_FP64 if precision == "fp64" else MD_PREC_MIXED
         w0 = workloads[0]
         self.k_max = int(k_max or max(w.k_max for w in workloads))
         cfgs = [make_config(w.n_atoms, w.box, w0.skin, self.k_max, w0.dt_fs, prec, rebuild_every, False,
-                            w0.strain_rate_zz, stream, lanes_per_atom) for w in workloads]
+                            w0.strain_rate_zz, stream, lanes_per_atom, integrator=integrator)
+                for w in workloads]
         pot, keep = make_potential(w0.potential)
         self.ctx = md_create_batch(cfgs, pot, [w.pos for w in workloads], [w.vel for w in workloads],
                                    [w.species for w in workloads])

@@ -46,6 +46,7 @@ int main(void) {
   printf("%zu %zu %zu %zu %zu %zu %zu\\n", offsetof(md_potential, tables), offsetof(md_config, stream),
          offsetof(md_energies, range_violations), offsetof(md_profile, ms_force), offsetof(md_surrogate, rd),
          offsetof(md_config, passes), offsetof(md_passes, active));
+  printf("%zu\\n", offsetof(md_config, integrator));
   return 0;
 }""")
     exe = tmp_path / "layout"
@@ -55,12 +56,13 @@ int main(void) {
     want = [C.sizeof(md.md_potential), C.sizeof(md.md_config), C.sizeof(md.md_energies),
             C.sizeof(md.md_profile), C.sizeof(md.md_surrogate), C.sizeof(md.md_passes), md.md_potential.tables.offset,
             md.md_config.stream.offset, md.md_energies.range_violations.offset, md.md_profile.ms_force.offset,
-            md.md_surrogate.rd.offset, md.md_config.passes.offset, md.md_passes.active.offset]
+            md.md_surrogate.rd.offset, md.md_config.passes.offset, md.md_passes.active.offset,
+            md.md_config.integrator.offset]
     assert got == want
 
 
 def test_status_strings(libmd):
-    assert libmd.md_abi_version() == 4
+    assert libmd.md_abi_version() == 5
     assert md.status_string(md.MD_ERR_NBR_OVERFLOW) == "neighbour list overflow"
     assert md.status_string(md.MD_ERR_SPECIES) == "unsupported species"
 
