@@ -289,7 +289,7 @@ def run_ours(args):
     n = w.n_atoms
     stream = torch.cuda.Stream()
     res, snapshot = {}, {}
-    for precision in ((args.profile_precision,) if args.profile_case else ("mixed", "fp64")):
+    for precision in ((args.profile_precision,) if args.profile_case else ("mixed", "fp64", "df")):
         s = md.System(w, precision=precision, stream=stream.cuda_stream, device_inputs=True,
                       passes=args.passes if precision == "mixed" else "auto", lanes_per_atom=args.lanes)
         s.eam_forces()
@@ -315,10 +315,10 @@ def run_ours(args):
         elif precision == "mixed":
             snapshot["pos"] = s.positions()
             snapshot["mixed"] = s.forces()
-        else:  # forces of both precisions at the same thermalised positions
+        else:  # forces of every precision at the same thermalised positions
             s.set_state(pos=snapshot["pos"])
             s.eam_forces()
-            snapshot["fp64"] = s.forces()
+            snapshot[precision] = s.forces()
         s.close()
     if args.profile_case:
         if rank == 0:
@@ -405,6 +405,14 @@ def run_ours(args):
                                             "max_force": float(np.abs(f64).max())},
              "nve_drift_ev_per_atom": (r32["e1"]["te"] - r32["e0"]["te"]) / n,
              "lanes_per_atom": r32["lanes"], "phase_ms": phases(r32), "roofline": hbm(r32, "mixed")}
+    rdf = res["df"]
+    fdf = np.abs(snapshot["df"] - f64)
+    df_line = {"value": job_value(n, world, args.steps, rdf["ms"]), "ms_per_step": rdf["ms"] / args.steps,
+               "dtype": "f32x2 (double-float pair and density terms) + f64",
+               "speedup_vs_fp64": r64["ms"] / rdf["ms"],
+               "force_err_vs_fp64_rel_maxnorm": float(fdf.max() / np.abs(f64).max()),
+               "nve_drift_ev_per_atom": (rdf["e1"]["te"] - rdf["e0"]["te"]) / n,
+               "lanes_per_atom": rdf["lanes"], "phase_ms": phases(rdf)}
     line = {
         "metric": METRIC, "value": job_value(n, world, args.steps, r64["ms"]), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": r64["ms"] / args.steps,
@@ -423,6 +431,7 @@ def run_ours(args):
         "rebuilds_in_timed_region": r64["e1"]["n_rebuilds"] - r64["e0"]["n_rebuilds"],
         "neighbours_per_atom": sum_counts / n,
         "mixed": mixed,
+        "double_float": df_line,
     }
     sur = extras.get("surrogate_fe_1m") if isinstance(extras, dict) else None
     if sur and "paths" in sur:
@@ -636,7 +645,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the non-headline workloads")
     ap.add_argument("--passes", choices=["auto", "list", "staged", "cells", "half"], default="auto",
                     help="neighbour walk of the mixed-precision step kernel (md.h MD_PASSES_*)")
-    ap.add_argument("--profile-precision", choices=["mixed", "fp64"], default="mixed",
+    ap.add_argument("--profile-precision", choices=["mixed", "fp64", "df"], default="mixed",
                     help="precision of the --profile-case run")
     ap.add_argument("--lanes", type=int, default=0, choices=[0, 1, 2, 4, 8, 16, 32],
                     help="lanes per atom (0: the autotuner's choice)")

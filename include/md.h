@@ -60,7 +60,7 @@ typedef enum {
 } md_status;
 
 enum { MD_POT_FS_ANALYTIC = 1, MD_POT_TABLES = 2, MD_POT_SURROGATE = 3, MD_POT_KNOTS = 4 };
-enum { MD_PREC_FP64 = 0, MD_PREC_MIXED = 1 };
+enum { MD_PREC_FP64 = 0, MD_PREC_MIXED = 1, MD_PREC_DF = 2 };
 
 /*
  * The potential as data (the paper's potential interface, §3.1: V, phi, F and their
@@ -116,7 +116,13 @@ typedef struct {
                               FP64 positions, velocities, density sum and reductions; with
                               one species and knot tables the force pass takes the quadratic
                               and cubic coefficients of each table cubic's derivative as
-                              binary16, scaled per function by a power of two) */
+                              binary16, scaled per function by a power of two), or MD_PREC_DF
+                              (one species, knot tables: the pair and density terms in
+                              double-float arithmetic, each quantity the unevaluated sum of two
+                              FP32 numbers, 48-bit significand, on the FP32 pipes; coordinates
+                              offset so that their FP32 high parts subtract exactly; positions,
+                              velocities, F(rho) and reductions FP64; results within 1e-11 of
+                              the FP64 ones for boxes of a few hundred Å) */
     int32_t strict_skin;   /* 1: moving > skin/2 between scheduled rebuilds is MD_ERR_SKIN;
                               0: it triggers a rebuild */
     double strain_rate_zz; /* 1/s; each step the box z edge and all z coordinates are

@@ -23,6 +23,7 @@
 #include <string>
 #include <vector>
 
+#include "md_df.cuh"
 #include "md_internal.cuh"
 
 using namespace mdk;
@@ -169,13 +170,19 @@ int cells_along(double L, double r_list) {
     return nc;
 }
 
-Box make_box(const double *L) {
+// skin: the double-float offset xoff = 2 (L + skin) + 1 keeps every image coordinate plus xoff
+// within a factor of two of every other (image coordinates lie in [-skin/2, L + skin/2)), also
+// while a strain ramp shrinks the box, so that differences of their FP32 high parts are exact.
+Box make_box(const double *L, double skin) {
     Box b;
     for (int k = 0; k < 3; k++) {
         b.L[k] = L[k];
         b.invL[k] = 1.0 / L[k];
         b.Lf[k] = (float)L[k];
         b.invLf[k] = (float)b.invL[k];
+        b.Lh[k] = (float)L[k];
+        b.Ll[k] = (float)(L[k] - (double)b.Lh[k]);
+        b.xoff[k] = 2.0 * (L[k] + skin) + 1.0;
     }
     return b;
 }
@@ -441,7 +448,12 @@ md_status create_common(md_ctx *ctx, const md_config *cfg, const md_potential *p
     ctx->L = L;
     if (n < 0 || n > INT32_MAX / 8) return MD_ERR_ARG;
     if (cfg->k_max < 1 || cfg->skin < 0.0 || !(cfg->dt_fs >= 0.0) || cfg->rebuild_every < 0) return MD_ERR_ARG;
-    if (cfg->precision != MD_PREC_FP64 && cfg->precision != MD_PREC_MIXED) return MD_ERR_ARG;
+    if (cfg->precision != MD_PREC_FP64 && cfg->precision != MD_PREC_MIXED && cfg->precision != MD_PREC_DF)
+        return MD_ERR_ARG;
+    if (cfg->precision == MD_PREC_DF && (pot->kind != MD_POT_TABLES || pot->n_species != 1)) {
+        ctx->err = "double-float precision takes one species with knot tables";
+        return MD_ERR_ARG;
+    }
     if (cfg->integrator != MD_INTEGRATOR_VERLET && cfg->integrator != MD_INTEGRATOR_PC3) return MD_ERR_ARG;
     if (cfg->integrator == MD_INTEGRATOR_PC3 &&
         (cfg->strain_rate_zz != 0.0 || pot->kind == MD_POT_SURROGATE ||
@@ -589,7 +601,11 @@ md_status create_common(md_ctx *ctx, const md_config *cfg, const md_potential *p
     chk(dalloc(ctx, &A.spec, n)); chk(dalloc(ctx, &A.spec_tmp, n)); chk(dalloc(ctx, &A.cell_of, n));
     chk(dalloc(ctx, &A.slot, n)); chk(dalloc(ctx, &A.order, n)); chk(dalloc(ctx, &A.count, n));
     chk(dalloc(ctx, &A.wrap, n));
-    if (cfg->precision == MD_PREC_FP64 && pot->kind != MD_POT_SURROGATE) chk(dalloc(ctx, &A.posd, n));
+    if (cfg->precision != MD_PREC_MIXED && pot->kind != MD_POT_SURROGATE) chk(dalloc(ctx, &A.posd, n));
+    if (cfg->precision == MD_PREC_DF) {   // double-float coordinates: high and low parts per atom
+        chk(dalloc(ctx, &A.posx, 2 * (size_t)n));
+        chk(dalloc(ctx, &A.p2x, 2 * (size_t)n));
+    }
 #ifndef MD_IMAGE_SHORTCUT
 #define MD_IMAGE_SHORTCUT 1
 #endif
@@ -599,7 +615,8 @@ md_status create_common(md_ctx *ctx, const md_config *cfg, const md_potential *p
 #define MD_FP64_DCACHE 1
 #endif
     // FP64, one species: the per-entry derivative cache of the force pass (16 B per list entry)
-    if (MD_FP64_DCACHE && cfg->precision == MD_PREC_FP64 && pot->kind != MD_POT_SURROGATE && ns == 1)
+    if ((cfg->precision == MD_PREC_DF || (MD_FP64_DCACHE && cfg->precision == MD_PREC_FP64)) &&
+        pot->kind != MD_POT_SURROGATE && ns == 1)
         chk(dalloc(ctx, &A.dcache, nbr_entries(n, cfg->k_max)));
     if (cfg->integrator == MD_INTEGRATOR_PC3) {
         chk(dalloc(ctx, &A.g2, n)); chk(dalloc(ctx, &A.g3, n));
@@ -730,6 +747,7 @@ md_status create_common(md_ctx *ctx, const md_config *cfg, const md_potential *p
         std::vector<float4> D32;
         std::vector<float> V0;
         std::vector<double4_32a> D64;
+        std::vector<float4> TX, TVx;
         const size_t tl = 2 * (size_t)nk;
         for (int a = 0; a < ns; a++)
             for (int b = 0; b < ns; b++) {
@@ -771,6 +789,27 @@ md_status create_common(md_ctx *ctx, const md_config *cfg, const md_potential *p
                         D64[2 * k] = make_double4_32a(rv[k].y * s, 2.0 * rv[k].z * s, 3.0 * rv[k].w * s, 0.0);
                         D64[2 * k + 1] = make_double4_32a(rp[k].y * s, 2.0 * rp[k].z * s, 3.0 * rp[k].w * s, 0.0);
                     }
+                    // double-float rows (see Pot::TX, Pot::TVx)
+                    TX.resize(4 * (size_t)nk);
+                    TVx.resize(2 * (size_t)nk);
+                    auto hl = [](double x) { return df::from_double(x); };
+                    for (int k = 0; k < nk; k++) {
+                        const df::F2 p0 = hl(rp[k].x), p1 = hl(rp[k].y), v0 = hl(rv[k].x), v1 = hl(rv[k].y);
+                        const df::F2 pd1 = hl(rp[k].y * s), pd2 = hl(2.0 * rp[k].z * s);
+                        const df::F2 vd1 = hl(rv[k].y * s), vd2 = hl(2.0 * rv[k].z * s);
+                        TX[4 * k] = make_float4(p0.h, p0.l, p1.h, p1.l);
+                        TX[4 * k + 1] = make_float4((float)rp[k].z, (float)rp[k].w, (float)(3.0 * rp[k].w * s),
+                                                    (float)(3.0 * rv[k].w * s));
+                        TX[4 * k + 2] = make_float4(pd1.h, pd1.l, pd2.h, pd2.l);
+                        TX[4 * k + 3] = make_float4(vd1.h, vd1.l, vd2.h, vd2.l);
+                        TVx[2 * k] = make_float4(v0.h, v0.l, v1.h, v1.l);
+                        TVx[2 * k + 1] = make_float4((float)rv[k].z, (float)rv[k].w, 0.f, 0.f);
+                    }
+                    const df::F2 idr = hl(P.inv_dr), x0 = hl(P.r_min * P.inv_dr);
+                    P.idr_h = idr.h;
+                    P.idr_l = idr.l;
+                    P.x0_h = x0.h;
+                    P.x0_l = x0.l;
                 }
                 for (int k = 0; k < nk; k++) {
                     VP64[(base + k) * 2] = rv[k];
@@ -795,10 +834,17 @@ md_status create_common(md_ctx *ctx, const md_config *cfg, const md_potential *p
         P.F64 = dF64;
         if (!D64.empty()) {
             double4_32a *dD64;
+            float4 *dTX, *dTV;
             chk(dalloc(ctx, &dD64, D64.size()));
+            chk(dalloc(ctx, &dTX, TX.size()));
+            chk(dalloc(ctx, &dTV, TVx.size()));
             if (e != cudaSuccess) return fail(ctx, MD_ERR_OOM, "table allocation", e);
             chk(cudaMemcpy(dD64, D64.data(), D64.size() * sizeof(double4_32a), cudaMemcpyHostToDevice));
+            chk(cudaMemcpy(dTX, TX.data(), TX.size() * sizeof(float4), cudaMemcpyHostToDevice));
+            chk(cudaMemcpy(dTV, TVx.data(), TVx.size() * sizeof(float4), cudaMemcpyHostToDevice));
             P.D64 = dD64;
+            P.TX = dTX;
+            P.TVx = dTV;
         }
         if (!D32.empty()) {
             float4 *dD32;
@@ -837,7 +883,7 @@ md_status create_common(md_ctx *ctx, const md_config *cfg, const md_potential *p
     }
     // initial state (caller order = cell order until the first build)
     std::vector<Box> boxes(n_rep);
-    for (int r = 0; r < n_rep; r++) boxes[r] = make_box(&L[3 * r]);
+    for (int r = 0; r < n_rep; r++) boxes[r] = make_box(&L[3 * r], cfg->skin);
     std::vector<int32_t> off32(n_rep + 1);
     for (int r = 0; r <= n_rep; r++) off32[r] = (int32_t)ctx->rep_off[r];
     Flags flags{};

@@ -9,6 +9,9 @@ namespace mdk {
 using namespace eam;
 
 cudaError_t launch_density32(const Atoms &A, const Pot &P, int lanes, cudaStream_t s);
+cudaError_t launch_density_df(const Atoms &A, const Pot &P, int lanes, cudaStream_t s);
+cudaError_t launch_force_df(const Atoms &A, const Pot &P, int lanes, bool kick, bool energy, double half_dt,
+                            cudaStream_t s);
 cudaError_t launch_force32(const Atoms &A, const Pot &P, int lanes, bool kick, bool energy, double half_dt,
                            cudaStream_t s);
 
@@ -113,11 +116,13 @@ int partial_blocks(int n, int lanes) {
 }
 
 cudaError_t launch_density(const Atoms &A, const Pot &P, int precision, int lanes, cudaStream_t s) {
+    if (precision == MD_PREC_DF) return launch_density_df(A, P, lanes, s);
     return precision == MD_PREC_FP64 ? density64(A, P, lanes, s) : launch_density32(A, P, lanes, s);
 }
 
 cudaError_t launch_force(const Atoms &A, const Pot &P, int precision, int lanes, bool kick, bool energy,
                          double half_dt, cudaStream_t s) {
+    if (precision == MD_PREC_DF) return launch_force_df(A, P, lanes, kick, energy, half_dt, s);
     return precision == MD_PREC_FP64 ? force64(A, P, lanes, kick, energy, half_dt, s)
                                      : launch_force32(A, P, lanes, kick, energy, half_dt, s);
 }

@@ -35,6 +35,11 @@ struct Box {
     double invL[3];
     float Lf[3];
     float invLf[3];
+    // double-float path (MD_PREC_DF): L as hi + lo, and the offset added to every image
+    // coordinate before it is split into hi + lo, so that all high parts lie within a factor of
+    // two of each other and their differences are exact
+    float Lh[3], Ll[3];
+    double xoff[3];
 };
 
 // Device-side status, read by the host after each synchronising call.
@@ -75,6 +80,14 @@ struct Pot {
     // one species, FP64 derivative cache: [2k + {0: V, 1: phi}] = (c1, 2 c2, 3 c3, 0) * inv_dr, the
     // r-derivative of the interval's cubic as a quadratic in t
     const double4_32a *D64;
+    // one species, double-float path: [4k + q], q = 0: phi (c0 hi, lo, c1 hi, lo); 1: (phi c2, phi c3,
+    // phi' e3, V' e3); 2: phi' (d1 hi, lo, d2 hi, lo); 3: V' (d1 hi, lo, d2 hi, lo) with d1 = c1 s,
+    // d2 = 2 c2 s, e3 = 3 c3 s, s = inv_dr (the r-derivative); TVx [2k + q]: V (c0 hi, lo, c1 hi, lo),
+    // (c2, c3, 0, 0) for the energy
+    const float4 *TX;
+    const float4 *TVx;
+    float idr_h, idr_l;       // inv_dr as hi + lo
+    float x0_h, x0_l;         // r_min inv_dr as hi + lo
     float dsv, dsp;
     // explicit knot sums (MD_POT_KNOTS): function t (V[a][b] = a*ns+b, phi[a][b] = ns*ns + a*ns+b)
     // has nkt terms (coefficient, radius) at K64/K32 + t*nkt; F_a = -A[a] sqrt(rho)
@@ -108,6 +121,9 @@ struct Atoms {
                                                  // build (as posf; NULL on the mixed path)
     double4_32a *pos_tmp, *vel_tmp, *force_tmp;  // renumbering scratch
     float4 *posf;                            // FP32 wrapped position, w = species bits
+    float4 *posx;                            // double-float path: [2 i] = high parts, [2 i + 1] = low parts
+                                             // of the image coordinates plus Box::xoff
+    float4 *p2x;                             // double-float pass 2: as posx, w = F'(rho) (hi, then lo)
     float4 *p2f;                             // mixed pass 2: wrapped position + F'(rho)
     double4_32a *p2d;                        // FP64 pass 2: position + F'(rho)
     double *rho, *dF, *e_atom;

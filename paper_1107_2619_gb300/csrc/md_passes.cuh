@@ -15,6 +15,7 @@
 
 #include <type_traits>
 
+#include "md_df.cuh"
 #include "md_eam_common.cuh"
 #include "md_phases.cuh"
 
@@ -664,18 +665,237 @@ __device__ __forceinline__ int force64_item(const Atoms &A, const Pot &P, const 
     return i;
 }
 
+// ======================================================================= double-float (MD_PREC_DF)
+// One species, knot tables.  The separation of two atoms is formed from the double-float image
+// coordinates (md_df.cuh; posx/p2x): the high parts lie within a factor of two of each other
+// (Box::xoff), so their difference is exact, and so is the subtraction of the periodic shift
+// L_hi; the low parts carry the rest.  Every later quantity of the pair term (r^2, 1/r by one
+// Newton step from the FP32 estimate, r, the knot index and t, the cubic of phi and the
+// derivatives of V and phi) is double-float; the quadratic and cubic coefficients enter in FP32
+// where their share of the result is below 2^-40 of it.  rho is summed in double-float and F(rho)
+// is taken in FP64.  The force pass combines the per-entry (V'/r, phi'/r) of the density pass with
+// F' as in the FP64 path, in double-float.
+
+template <typename W>
+__device__ __forceinline__ df::F2 sep_df(float xjh, float xih, float xjl, float xil, float Lh, float Ll, float invL) {
+    float dh = __fsub_rn(xjh, xih);   // exact: both within a factor of two (Box::xoff)
+    float dl = __fsub_rn(xjl, xil);
+    if (W::value) {
+        const float k = rintf(__fmul_rn(dh, invL));
+        dh = __fmaf_rn(-k, Lh, dh);    // exact (|dh| and |k Lh| within a factor of two)
+        dl = __fmaf_rn(-k, Ll, dl);
+    }
+    return df::two_sum(dh, dl);
+}
+
+__device__ __forceinline__ df::F2 r2_df(df::F2 dx, df::F2 dy, df::F2 dz) {
+    auto sq = [](df::F2 d) {
+        df::F2 p = df::two_prod(d.h, d.h);
+        p.l = __fmaf_rn(2.f * d.h, d.l, p.l);
+        return p;
+    };
+    return df::add(df::add(sq(dx), sq(dy)), sq(dz));
+}
+
+// 1/sqrt(r2) from the FP32 estimate and one Newton step in double-float, and r = r2 / sqrt(r2).
+__device__ __forceinline__ void rinv_df(df::F2 r2, df::F2 &rinv, df::F2 &r) {
+    const float y = rsqrtf(r2.h);
+    const df::F2 q = df::mul(r2, df::two_prod(y, y));
+    const float e = __fsub_rn(__fsub_rn(1.f, q.h), q.l);   // 1 - r2 y^2 (1 - q.h exact)
+    rinv = df::fast_two_sum(y, __fmul_rn(0.5f * y, e));
+    r = df::mul(r2, rinv);
+}
+
+// Knot interval and t of r (x = r inv_dr - r_min inv_dr); below r_min: row 0, t = x (negative).
+__device__ __forceinline__ int knot_df(const Pot &P, df::F2 r, df::F2 &t, bool &below) {
+    const df::F2 x = df::add(df::mul(r, df::make(P.idr_h, P.idr_l)), df::make(-P.x0_h, -P.x0_l));
+    below = x.h < 0.f;
+    int k = below ? 0 : min((int)x.h, P.nk - 1);
+    t = below ? x : df::two_sum(__fsub_rn(x.h, (float)k), x.l);   // x.h - k exact
+    return k;
+}
+
+// Value of the interval's cubic c0 + t (c1 + t (c2 + t c3)): r0 = (c0 hi, lo, c1 hi, lo), c2, c3.
+__device__ __forceinline__ df::F2 cubic_df(df::F2 t, float4 r0, float c2, float c3, bool below) {
+    const float q = below ? 0.f : __fmaf_rn(t.h, c3, c2);
+    df::F2 u = df::two_prod(t.h, q);
+    u.l = __fmaf_rn(t.l, q, u.l);
+    const df::F2 w = df::add(df::make(r0.z, r0.w), u);
+    return df::add(df::make(r0.x, r0.y), df::mul(t, w));
+}
+
+// r-derivative of the interval's cubic: d1 + t (d2 + t e3) with r1 = (d1 hi, lo, d2 hi, lo).
+__device__ __forceinline__ df::F2 dcubic_df(df::F2 t, float4 r1, float e3, bool below) {
+    if (below) return df::make(r1.x, r1.y);
+    const df::F2 q = df::two_sum(r1.z, __fmaf_rn(t.h, e3, r1.w));
+    df::F2 u = df::two_prod(t.h, q.h);
+    u.l = __fmaf_rn(t.h, q.l, __fmaf_rn(t.l, q.h, u.l));
+    return df::add(df::make(r1.x, r1.y), u);
+}
+
+template <int T>
+__device__ __forceinline__ void density_df_item(const Atoms &A, const Pot &P, const Box *boxes, long long g) {
+    const int i = (int)(g / T), lane = (int)(g & (T - 1));
+    const bool live = i < A.n;
+    df::F2 rho = df::make(0.f);
+    float4 pih = make_float4(0.f, 0.f, 0.f, 0.f), pil = pih;
+    const bool wrap = needs_image(A, i, live);
+    if (live) {
+        const Box &B = boxes[ph::replica_of(A, i)];
+        pih = ld_phase(A.posx + 2 * (size_t)i);
+        pil = ld_phase(A.posx + 2 * (size_t)i + 1);
+        const int cnt = min(A.count[i], A.k_max);
+        const NbrRow row = nbr_row(A, i);
+        const DRow drow = dcache_row(A, i);
+        auto walk = [&](auto wrapt) {
+            using W = decltype(wrapt);
+            for (int k = lane; k < cnt; k += T) {
+                const int j = ld_phase(row.ptr(k));
+                const float4 pjh = ld_phase(A.posx + 2 * (size_t)j), pjl = ld_phase(A.posx + 2 * (size_t)j + 1);
+                const df::F2 dx = sep_df<W>(pjh.x, pih.x, pjl.x, pil.x, B.Lh[0], B.Ll[0], B.invLf[0]);
+                const df::F2 dy = sep_df<W>(pjh.y, pih.y, pjl.y, pil.y, B.Lh[1], B.Ll[1], B.invLf[1]);
+                const df::F2 dz = sep_df<W>(pjh.z, pih.z, pjl.z, pil.z, B.Lh[2], B.Ll[2], B.invLf[2]);
+                const df::F2 r2 = r2_df(dx, dy, dz);
+                float4 *dc = reinterpret_cast<float4 *>(drow.ptr(k));
+                if (!(r2.h < P.rc2f)) {
+                    *dc = make_float4(0.f, 0.f, 0.f, 0.f);
+                    continue;
+                }
+                df::F2 rinv, r, t;
+                rinv_df(r2, rinv, r);
+                bool below;
+                const int kr = knot_df(P, r, t, below);
+                if (below) atomicAdd(&A.flags->range_violations, 1ull);
+                const float4 *tx = P.TX + 4 * (size_t)kr;
+                const float4 x1 = tx[1];
+                rho = df::add(rho, cubic_df(t, tx[0], x1.x, x1.y, below));
+                const df::F2 dphi = dcubic_df(t, tx[2], x1.z, below);
+                const df::F2 dV = dcubic_df(t, tx[3], x1.w, below);
+                const df::F2 gV = df::mul(dV, rinv), gP = df::mul(dphi, rinv);
+                *dc = make_float4(gV.h, gV.l, gP.h, gP.l);
+            }
+        };
+        if (wrap) walk(std::true_type{});
+        else walk(std::false_type{});
+    }
+    rho = df::lane_sum<T>(rho);
+    if (live && lane == 0) {
+        const double rr = df::to_double(rho);
+        double dF;
+        const double F = embed64(P, 0, rr, dF, A.flags);
+        A.rho[i] = rr;
+        A.dF[i] = dF;
+        A.e_atom[i] = F;
+        const df::F2 f2 = df::from_double(dF);
+        A.p2x[2 * (size_t)i] = make_float4(pih.x, pih.y, pih.z, f2.h);
+        A.p2x[2 * (size_t)i + 1] = make_float4(pil.x, pil.y, pil.z, f2.l);
+    }
+}
+
+template <int T, bool ENERGY>
+__device__ __forceinline__ int force_df_item(const Atoms &A, const Pot &P, const Box *boxes, long long g,
+                                             double half_dt, int motion, double (&part)[kPartials]) {
+    const int i = (int)(g / T), lane = (int)(g & (T - 1));
+    const bool live = i < A.n;
+    df::F2 fx = df::make(0.f), fy = fx, fz = fx, ep = fx;
+    df::F2 wv[6] = {fx, fx, fx, fx, fx, fx};
+    const bool wrap = needs_image(A, i, live);
+    if (live) {
+        const Box &B = boxes[ph::replica_of(A, i)];
+        const float4 pih = A.p2x[2 * (size_t)i], pil = A.p2x[2 * (size_t)i + 1];
+        const df::F2 Fpi = df::make(pih.w, pil.w);
+        const int cnt = min(A.count[i], A.k_max);
+        const NbrRow row = nbr_row(A, i);
+        const DRow drow = dcache_row(A, i);
+        auto walk = [&](auto wrapt) {
+            using W = decltype(wrapt);
+            for (int k = lane; k < cnt; k += T) {
+                const int j = ld_phase(row.ptr(k));
+                const float4 pjh = ld_phase(A.p2x + 2 * (size_t)j), pjl = ld_phase(A.p2x + 2 * (size_t)j + 1);
+                const float4 e = ld_phase(reinterpret_cast<const float4 *>(drow.ptr(k)));
+                const df::F2 dx = sep_df<W>(pjh.x, pih.x, pjl.x, pil.x, B.Lh[0], B.Ll[0], B.invLf[0]);
+                const df::F2 dy = sep_df<W>(pjh.y, pih.y, pjl.y, pil.y, B.Lh[1], B.Ll[1], B.invLf[1]);
+                const df::F2 dz = sep_df<W>(pjh.z, pih.z, pjl.z, pil.z, B.Lh[2], B.Ll[2], B.invLf[2]);
+                const df::F2 sF = df::add(Fpi, df::make(pjh.w, pjl.w));
+                const df::F2 gr = df::add(df::make(e.x, e.y), df::mul(sF, df::make(e.z, e.w)));
+                fx = df::add(fx, df::mul(gr, dx));
+                fy = df::add(fy, df::mul(gr, dy));
+                fz = df::add(fz, df::mul(gr, dz));
+                if (ENERGY) {
+                    const df::F2 r2 = r2_df(dx, dy, dz);
+                    if (r2.h < P.rc2f) {
+                        df::F2 rinv, r, t;
+                        rinv_df(r2, rinv, r);
+                        bool below;
+                        const int kr = knot_df(P, r, t, below);
+                        const float4 v0 = P.TVx[2 * (size_t)kr], v1 = P.TVx[2 * (size_t)kr + 1];
+                        const df::F2 V = cubic_df(t, v0, v1.x, v1.y, below);
+                        ep = df::add(ep, df::make(0.5f * V.h, 0.5f * V.l));
+                    }
+                    const df::F2 hg = df::make(-0.5f * gr.h, -0.5f * gr.l);
+                    const df::F2 hx = df::mul(hg, dx), hy = df::mul(hg, dy);
+                    wv[0] = df::add(wv[0], df::mul(hx, dx));
+                    wv[1] = df::add(wv[1], df::mul(hy, dy));
+                    wv[2] = df::add(wv[2], df::mul(df::mul(hg, dz), dz));
+                    wv[3] = df::add(wv[3], df::mul(hy, dz));
+                    wv[4] = df::add(wv[4], df::mul(hx, dz));
+                    wv[5] = df::add(wv[5], df::mul(hx, dy));
+                }
+            }
+        };
+        if (wrap) walk(std::true_type{});
+        else walk(std::false_type{});
+    }
+    fx = df::lane_sum<T>(fx);
+    fy = df::lane_sum<T>(fy);
+    fz = df::lane_sum<T>(fz);
+    if (ENERGY) {
+        ep = df::lane_sum<T>(ep);
+#pragma unroll
+        for (int q = 0; q < 6; q++) wv[q] = df::lane_sum<T>(wv[q]);
+    }
+    if (!(live && lane == 0)) return -1;
+    const double Fx = df::to_double(fx), Fy = df::to_double(fy), Fz = df::to_double(fz);
+    A.force[i] = make_double4_32a(Fx, Fy, Fz, 0.0);
+    if (!isfinite(Fx + Fy + Fz)) atomicOr(&A.flags->error, FLAG_NONFINITE);
+    double4_32a v = A.vel[i];
+    finish_motion(A, i, v, Fx, Fy, Fz, half_dt, motion);
+    if (ENERGY) {
+        const double e = A.e_atom[i] + df::to_double(ep);
+        A.e_atom[i] = e;
+        const double m = 1.0 / (kMvv2e * v.w);
+        part[0] += e;
+        part[1] += m * fma(v.x, v.x, fma(v.y, v.y, v.z * v.z));
+#pragma unroll
+        for (int q = 0; q < 6; q++) part[2 + q] += df::to_double(wv[q]);
+        part[8] += m * v.x; part[9] += m * v.y; part[10] += m * v.z;
+    }
+    return i;
+}
+
 // Precision-generic front ends.
 template <int PREC, int T, int KIND, bool MULTI, bool SMT = false>
 __device__ __forceinline__ void density_item(const Atoms &A, const Pot &P, const Box *boxes, long long g) {
-    if (PREC == MD_PREC_FP64) density64_item<T, KIND, MULTI>(A, P, boxes, g);
-    else density32_item<T, KIND, MULTI, SMT>(A, P, boxes, g);
+    if constexpr (PREC == MD_PREC_DF) {
+        if constexpr (KIND == MD_POT_TABLES && !MULTI) density_df_item<T>(A, P, boxes, g);
+    } else if constexpr (PREC == MD_PREC_FP64) {
+        density64_item<T, KIND, MULTI>(A, P, boxes, g);
+    } else {
+        density32_item<T, KIND, MULTI, SMT>(A, P, boxes, g);
+    }
 }
 
 template <int PREC, int T, int KIND, bool MULTI, bool ENERGY, bool SMT = false>
 __device__ __forceinline__ int force_item(const Atoms &A, const Pot &P, const Box *boxes, long long g,
                                           double half_dt, int motion, double (&part)[kPartials]) {
-    if (PREC == MD_PREC_FP64) return force64_item<T, KIND, MULTI, ENERGY>(A, P, boxes, g, half_dt, motion, part);
-    return force32_item<T, KIND, MULTI, ENERGY, SMT>(A, P, boxes, g, half_dt, motion, part);
+    if constexpr (PREC == MD_PREC_DF) {
+        if constexpr (KIND == MD_POT_TABLES && !MULTI) return force_df_item<T, ENERGY>(A, P, boxes, g, half_dt, motion, part);
+        return -1;
+    } else if constexpr (PREC == MD_PREC_FP64) {
+        return force64_item<T, KIND, MULTI, ENERGY>(A, P, boxes, g, half_dt, motion, part);
+    } else {
+        return force32_item<T, KIND, MULTI, ENERGY, SMT>(A, P, boxes, g, half_dt, motion, part);
+    }
 }
 
 }  // namespace ps

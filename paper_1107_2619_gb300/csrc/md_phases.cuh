@@ -59,6 +59,15 @@ __device__ __forceinline__ float4 build_image(const double4_32a &p, const double
                        (float)(p.z - B.L[2] * floor(ref.z * B.invL[2])), __int_as_float(species));
 }
 
+// Double-float copy of an FP64 image coordinate q (MD_PREC_DF): q + xoff split into an FP32 high
+// part and the FP32 rounding of the remainder.
+__device__ __forceinline__ void store_dfpos(const Atoms &A, int i, const double4_32a &q, const Box &B) {
+    const double x = q.x + B.xoff[0], y = q.y + B.xoff[1], z = q.z + B.xoff[2];
+    const float xh = (float)x, yh = (float)y, zh = (float)z;
+    A.posx[2 * (size_t)i] = make_float4(xh, yh, zh, 0.f);
+    A.posx[2 * (size_t)i + 1] = make_float4((float)(x - (double)xh), (float)(y - (double)yh), (float)(z - (double)zh), 0.f);
+}
+
 __device__ __forceinline__ int global_cell(const double4_32a &p, const Box &B, const RepCells &g) {
     const int cx = cell_coord(p.x, B.invL[0], g.nc[0]);
     const int cy = cell_coord(p.y, B.invL[1], g.nc[1]);
@@ -124,7 +133,12 @@ __device__ __forceinline__ void kick_drift(const Atoms &A, const Box *boxes, int
         A.flags->skin_exceeded = 1;
     }
     A.posf[i] = build_image(p, r, boxes[replica_of(A, i)], A.spec[i]);
-    if (A.posd) A.posd[i] = build_image64(p, r, boxes[replica_of(A, i)]);
+    if (A.posd) {
+        const Box &B = boxes[replica_of(A, i)];
+        const double4_32a q = build_image64(p, r, B);
+        A.posd[i] = q;
+        if (A.posx) store_dfpos(A, i, q, B);
+    }
 }
 
 // The predictor of the third-order predictor-corrector (md.h MD_INTEGRATOR_PC3): from the force f
@@ -155,7 +169,12 @@ __device__ __forceinline__ void predict_pc3(const Atoms &A, const Box *boxes, in
         A.flags->skin_exceeded = 1;
     }
     A.posf[i] = build_image(p, r, boxes[replica_of(A, i)], A.spec[i]);
-    if (A.posd) A.posd[i] = build_image64(p, r, boxes[replica_of(A, i)]);
+    if (A.posd) {
+        const Box &B = boxes[replica_of(A, i)];
+        const double4_32a q = build_image64(p, r, B);
+        A.posd[i] = q;
+        if (A.posx) store_dfpos(A, i, q, B);
+    }
 }
 
 // What opens a step: the half kick and drift of velocity Verlet, or the predictor.
@@ -321,7 +340,12 @@ __device__ __forceinline__ void copyback_atom(const Atoms &A, const Box *boxes, 
         A.g3[k] = A.g3_tmp[k];
     }
     A.posf[k] = wrapped(p, boxes[replica_of(A, k)], sp);
-    if (A.posd) A.posd[k] = wrapped64(p, boxes[replica_of(A, k)]);
+    if (A.posd) {
+        const Box &B = boxes[replica_of(A, k)];
+        const double4_32a q = wrapped64(p, B);
+        A.posd[k] = q;
+        if (A.posx) store_dfpos(A, k, q, B);
+    }
 }
 
 // The exact neighbour test: the IEEE operations, order and absence of contraction of the

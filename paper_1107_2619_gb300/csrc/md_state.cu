@@ -19,7 +19,12 @@ __global__ void k_wrap(Atoms A) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= A.n) return;
     A.posf[i] = ph::build_image(A.pos[i], A.ref[i], A.boxes[ph::replica_of(A, i)], A.spec[i]);
-    if (A.posd) A.posd[i] = ph::build_image64(A.pos[i], A.ref[i], A.boxes[ph::replica_of(A, i)]);
+    if (A.posd) {
+        const Box &B = A.boxes[ph::replica_of(A, i)];
+        const double4_32a q = ph::build_image64(A.pos[i], A.ref[i], B);
+        A.posd[i] = q;
+        if (A.posx) ph::store_dfpos(A, i, q, B);
+    }
 }
 
 __global__ void k_unsort_vec(Atoms A, const double4_32a *src, double *dst) {

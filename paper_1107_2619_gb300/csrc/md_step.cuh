@@ -70,6 +70,8 @@ __device__ __forceinline__ void strain_boxes(Box *boxes, int n_rep, double s) {
         b.invL[2] = 1.0 / b.L[2];
         b.Lf[2] = (float)b.L[2];
         b.invLf[2] = (float)b.invL[2];
+        b.Lh[2] = (float)b.L[2];
+        b.Ll[2] = (float)(b.L[2] - (double)b.Lh[2]);
         boxes[r] = b;
     }
 }
@@ -475,6 +477,10 @@ cudaError_t launch_t(const Atoms &A, const Cells &C, const Pot &P, const StepPar
 template <int PREC, int T>
 cudaError_t launch_kind(const Atoms &A, const Cells &C, const Pot &P, const StepParams &sp, GridBarrier *bar,
                         unsigned long long *stamps, int *grid_out, cudaStream_t s) {
+    if constexpr (PREC == MD_PREC_DF) {   // one species, knot tables
+        if (P.kind != MD_POT_TABLES || P.ns != 1) return cudaErrorInvalidValue;
+        return launch_t<PREC, T, MD_POT_TABLES, false>(A, C, P, sp, bar, stamps, grid_out, s);
+    }
     if (P.kind == MD_POT_FS_ANALYTIC)
         return launch_t<PREC, T, MD_POT_FS_ANALYTIC, false>(A, C, P, sp, bar, stamps, grid_out, s);
     if (P.kind == MD_POT_KNOTS)
@@ -516,5 +522,6 @@ cudaError_t launch_kind(const Atoms &A, const Cells &C, const Pot &P, const Step
     MD_STEP_DECL(P, T) { return st::launch_kind<PREC, T>(A, C, Pt, sp, bar, stamps, grid_out, s); }
 MD_STEP_DECL(m, 1); MD_STEP_DECL(m, 2); MD_STEP_DECL(m, 4); MD_STEP_DECL(m, 8); MD_STEP_DECL(m, 16); MD_STEP_DECL(m, 32);
 MD_STEP_DECL(d, 1); MD_STEP_DECL(d, 2); MD_STEP_DECL(d, 4); MD_STEP_DECL(d, 8); MD_STEP_DECL(d, 16); MD_STEP_DECL(d, 32);
+MD_STEP_DECL(e, 1); MD_STEP_DECL(e, 2); MD_STEP_DECL(e, 4); MD_STEP_DECL(e, 8); MD_STEP_DECL(e, 16); MD_STEP_DECL(e, 32);
 
 }  // namespace mdk

@@ -1,5 +1,5 @@
 // Persistent step kernel: the precision and lane-count dispatch (the instantiations live in
-// md_step_{m,d}_{a,b,c}.cu).
+// md_step_{m,d,e}_{a,b,c}.cu: mixed, FP64, double-float).
 #include "md_step.cuh"
 
 namespace mdk {
@@ -7,22 +7,21 @@ namespace mdk {
 cudaError_t launch_step(const Atoms &A, const Cells &C, const Pot &P, int precision, int lanes,
                         const StepParams &sp, GridBarrier *bar, unsigned long long *stamps, int *grid_out,
                         cudaStream_t s) {
-    const bool fp64 = precision == MD_PREC_FP64;
+#define MD_STEP_CASE(T)                                                                  \
+    case T:                                                                              \
+        if (precision == MD_PREC_FP64) return MD_STEP_FN(d, T)(A, C, P, sp, bar, stamps, grid_out, s); \
+        if (precision == MD_PREC_DF) return MD_STEP_FN(e, T)(A, C, P, sp, bar, stamps, grid_out, s);   \
+        return MD_STEP_FN(m, T)(A, C, P, sp, bar, stamps, grid_out, s);
     switch (lanes) {
-        case 1: return fp64 ? MD_STEP_FN(d, 1)(A, C, P, sp, bar, stamps, grid_out, s)
-                            : MD_STEP_FN(m, 1)(A, C, P, sp, bar, stamps, grid_out, s);
-        case 2: return fp64 ? MD_STEP_FN(d, 2)(A, C, P, sp, bar, stamps, grid_out, s)
-                            : MD_STEP_FN(m, 2)(A, C, P, sp, bar, stamps, grid_out, s);
-        case 4: return fp64 ? MD_STEP_FN(d, 4)(A, C, P, sp, bar, stamps, grid_out, s)
-                            : MD_STEP_FN(m, 4)(A, C, P, sp, bar, stamps, grid_out, s);
-        case 8: return fp64 ? MD_STEP_FN(d, 8)(A, C, P, sp, bar, stamps, grid_out, s)
-                            : MD_STEP_FN(m, 8)(A, C, P, sp, bar, stamps, grid_out, s);
-        case 16: return fp64 ? MD_STEP_FN(d, 16)(A, C, P, sp, bar, stamps, grid_out, s)
-                             : MD_STEP_FN(m, 16)(A, C, P, sp, bar, stamps, grid_out, s);
-        case 32: return fp64 ? MD_STEP_FN(d, 32)(A, C, P, sp, bar, stamps, grid_out, s)
-                             : MD_STEP_FN(m, 32)(A, C, P, sp, bar, stamps, grid_out, s);
+        MD_STEP_CASE(1)
+        MD_STEP_CASE(2)
+        MD_STEP_CASE(4)
+        MD_STEP_CASE(8)
+        MD_STEP_CASE(16)
+        MD_STEP_CASE(32)
         default: return cudaErrorInvalidValue;
     }
+#undef MD_STEP_CASE
 }
 
 }  // namespace mdk

@@ -26,7 +26,8 @@ MD_POT_FS_ANALYTIC, MD_POT_TABLES, MD_POT_SURROGATE, MD_POT_KNOTS = 1, 2, 3, 4
 MD_SUR_FP32, MD_SUR_BF16 = 0, 1
 MD_SUR_GET_G, MD_SUR_GET_DEDG = 0, 1
 MD_SUR_NB, MD_SUR_H1, MD_SUR_H2, MD_SUR_PARAMS = 32, 64, 64, 6337
-MD_PREC_FP64, MD_PREC_MIXED = 0, 1
+MD_PREC_FP64, MD_PREC_MIXED, MD_PREC_DF = 0, 1, 2
+PRECISIONS = {"fp64": MD_PREC_FP64, "mixed": MD_PREC_MIXED, "df": MD_PREC_DF}
 (MD_GET_POS, MD_GET_VEL, MD_GET_FORCE, MD_GET_RHO, MD_GET_EATOM, MD_GET_DF, MD_GET_NBR_COUNT,
  MD_GET_NBR_LIST, MD_GET_SPECIES, MD_GET_IMAGE) = range(10)
 
@@ -456,7 +457,7 @@ class System:
     def __init__(self, w: _inputs.Workload, precision: str = "fp64", rebuild_every: int = 0,
                  strict_skin: bool = False, stream=None, device_inputs: bool = False, k_max=None,
                  lanes_per_atom: int = 0, passes: str = "auto", integrator: str = "verlet"):
-        prec = MD_PREC_FP64 if precision == "fp64" else MD_PREC_MIXED
+        prec = PRECISIONS[precision]
         self.n = w.n_atoms
         self.k_max = int(k_max or w.k_max)
         self.config = make_config(w.n_atoms, w.box, w.skin, self.k_max, w.dt_fs, prec, rebuild_every,
@@ -574,7 +575,7 @@ class Batch(System):
 
     def __init__(self, workloads, precision: str = "mixed", rebuild_every: int = 0, stream=None,
                  k_max=None, lanes_per_atom: int = 0, integrator: str = "verlet"):
-        prec = MD_PREC_FP64 if precision == "fp64" else MD_PREC_MIXED
+        prec = PRECISIONS[precision]
         w0 = workloads[0]
         self.k_max = int(k_max or max(w.k_max for w in workloads))
         cfgs = [make_config(w.n_atoms, w.box, w0.skin, self.k_max, w0.dt_fs, prec, rebuild_every, False,
