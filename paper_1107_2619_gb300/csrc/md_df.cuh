@@ -61,6 +61,18 @@ __device__ __forceinline__ F2 mul_f(F2 a, float b) {
     return fast_two_sum(p.h, p.l);
 }
 
+// Compensated accumulator of many terms: the running FP32 sum s and the FP32 sum e of the exact
+// rounding errors of the additions and of the terms' low parts (normalised once, at the end).
+struct Acc {
+    float s, e;
+};
+__device__ __forceinline__ void acc_add(Acc &a, F2 x) {
+    const F2 t = two_sum(a.s, x.h);
+    a.s = t.h;
+    a.e = __fadd_rn(a.e, __fadd_rn(t.l, x.l));
+}
+__device__ __forceinline__ F2 acc_value(Acc a) { return fast_two_sum(a.s, a.e); }
+
 // Value as FP64 (exact: both parts convert exactly).
 __device__ __forceinline__ double to_double(F2 a) { return (double)a.h + (double)a.l; }
 

@@ -685,13 +685,15 @@ __device__ __forceinline__ df::F2 sep_df(float xjh, float xih, float xjl, float 
         dh = __fmaf_rn(-k, Lh, dh);    // exact (|dh| and |k Lh| within a factor of two)
         dl = __fmaf_rn(-k, Ll, dl);
     }
-    return df::two_sum(dh, dl);
+    // left unnormalised (|dl| <= ulp(xoff), which can exceed ulp(dh)): the products below take dh
+    // and dl separately, and the square keeps the dl^2 term
+    return df::make(dh, dl);
 }
 
 __device__ __forceinline__ df::F2 r2_df(df::F2 dx, df::F2 dy, df::F2 dz) {
-    auto sq = [](df::F2 d) {
+    auto sq = [](df::F2 d) {   // d unnormalised: its low part may exceed ulp(d.h), so keep d.l^2
         df::F2 p = df::two_prod(d.h, d.h);
-        p.l = __fmaf_rn(2.f * d.h, d.l, p.l);
+        p.l = __fmaf_rn(2.f * d.h, d.l, __fmaf_rn(d.l, d.l, p.l));
         return p;
     };
     return df::add(df::add(sq(dx), sq(dy)), sq(dz));
@@ -737,7 +739,7 @@ template <int T>
 __device__ __forceinline__ void density_df_item(const Atoms &A, const Pot &P, const Box *boxes, long long g) {
     const int i = (int)(g / T), lane = (int)(g & (T - 1));
     const bool live = i < A.n;
-    df::F2 rho = df::make(0.f);
+    df::Acc rho_acc{0.f, 0.f};
     float4 pih = make_float4(0.f, 0.f, 0.f, 0.f), pil = pih;
     const bool wrap = needs_image(A, i, live);
     if (live) {
@@ -768,7 +770,7 @@ __device__ __forceinline__ void density_df_item(const Atoms &A, const Pot &P, co
                 if (below) atomicAdd(&A.flags->range_violations, 1ull);
                 const float4 *tx = P.TX + 4 * (size_t)kr;
                 const float4 x1 = tx[1];
-                rho = df::add(rho, cubic_df(t, tx[0], x1.x, x1.y, below));
+                df::acc_add(rho_acc, cubic_df(t, tx[0], x1.x, x1.y, below));
                 const df::F2 dphi = dcubic_df(t, tx[2], x1.z, below);
                 const df::F2 dV = dcubic_df(t, tx[3], x1.w, below);
                 const df::F2 gV = df::mul(dV, rinv), gP = df::mul(dphi, rinv);
@@ -778,7 +780,7 @@ __device__ __forceinline__ void density_df_item(const Atoms &A, const Pot &P, co
         if (wrap) walk(std::true_type{});
         else walk(std::false_type{});
     }
-    rho = df::lane_sum<T>(rho);
+    const df::F2 rho = df::lane_sum<T>(df::acc_value(rho_acc));
     if (live && lane == 0) {
         const double rr = df::to_double(rho);
         double dF;
@@ -797,8 +799,9 @@ __device__ __forceinline__ int force_df_item(const Atoms &A, const Pot &P, const
                                              double half_dt, int motion, double (&part)[kPartials]) {
     const int i = (int)(g / T), lane = (int)(g & (T - 1));
     const bool live = i < A.n;
-    df::F2 fx = df::make(0.f), fy = fx, fz = fx, ep = fx;
-    df::F2 wv[6] = {fx, fx, fx, fx, fx, fx};
+    df::Acc ax{0.f, 0.f}, ay = ax, az = ax;
+    df::F2 ep = df::make(0.f);
+    df::F2 wv[6] = {ep, ep, ep, ep, ep, ep};
     const bool wrap = needs_image(A, i, live);
     if (live) {
         const Box &B = boxes[ph::replica_of(A, i)];
@@ -818,9 +821,9 @@ __device__ __forceinline__ int force_df_item(const Atoms &A, const Pot &P, const
                 const df::F2 dz = sep_df<W>(pjh.z, pih.z, pjl.z, pil.z, B.Lh[2], B.Ll[2], B.invLf[2]);
                 const df::F2 sF = df::add(Fpi, df::make(pjh.w, pjl.w));
                 const df::F2 gr = df::add(df::make(e.x, e.y), df::mul(sF, df::make(e.z, e.w)));
-                fx = df::add(fx, df::mul(gr, dx));
-                fy = df::add(fy, df::mul(gr, dy));
-                fz = df::add(fz, df::mul(gr, dz));
+                df::acc_add(ax, df::mul(gr, dx));
+                df::acc_add(ay, df::mul(gr, dy));
+                df::acc_add(az, df::mul(gr, dz));
                 if (ENERGY) {
                     const df::F2 r2 = r2_df(dx, dy, dz);
                     if (r2.h < P.rc2f) {
@@ -846,9 +849,8 @@ __device__ __forceinline__ int force_df_item(const Atoms &A, const Pot &P, const
         if (wrap) walk(std::true_type{});
         else walk(std::false_type{});
     }
-    fx = df::lane_sum<T>(fx);
-    fy = df::lane_sum<T>(fy);
-    fz = df::lane_sum<T>(fz);
+    const df::F2 fx = df::lane_sum<T>(df::acc_value(ax)), fy = df::lane_sum<T>(df::acc_value(ay)),
+                 fz = df::lane_sum<T>(df::acc_value(az));
     if (ENERGY) {
         ep = df::lane_sum<T>(ep);
 #pragma unroll

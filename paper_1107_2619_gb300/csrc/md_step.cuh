@@ -129,6 +129,9 @@ __device__ __forceinline__ void thermo_update(const StepParams &sp, int n_rep, l
 #define MD_SMT_THREADS 1024
 #endif
 
+#ifndef MD_STEP_MIN_BLOCKS_DF   // the double-float passes hold more live values per lane
+#define MD_STEP_MIN_BLOCKS_DF 8
+#endif
 #ifndef MD_STEP_MIN_BLOCKS
 #define MD_STEP_MIN_BLOCKS 8
 #endif
@@ -142,7 +145,7 @@ __device__ __forceinline__ void thermo_update(const StepParams &sp, int n_rep, l
 // did not fit (the list walk then needs one).  The half walk adds two phases: F(rho) after the
 // density pass and the kicks after the force pass (each waits for every group's shares).
 template <int PREC, int T, int KIND, bool MULTI, int NT, bool SMT, int WALK>
-__global__ void __launch_bounds__(NT, NT == kThreads ? MD_STEP_MIN_BLOCKS : 1)
+__global__ void __launch_bounds__(NT, NT == kThreads ? (PREC == MD_PREC_DF ? MD_STEP_MIN_BLOCKS_DF : MD_STEP_MIN_BLOCKS) : 1)
     k_step(Atoms A, Cells C, Pot P, StepParams sp, GridBarrier *bar, unsigned long long *stamps) {
     __shared__ int ws[32];
     __shared__ int tile_loc[WALK ? tl::kTileMaxSt + 1 : 1];
@@ -480,40 +483,41 @@ cudaError_t launch_kind(const Atoms &A, const Cells &C, const Pot &P, const Step
     if constexpr (PREC == MD_PREC_DF) {   // one species, knot tables
         if (P.kind != MD_POT_TABLES || P.ns != 1) return cudaErrorInvalidValue;
         return launch_t<PREC, T, MD_POT_TABLES, false>(A, C, P, sp, bar, stamps, grid_out, s);
-    }
-    if (P.kind == MD_POT_FS_ANALYTIC)
-        return launch_t<PREC, T, MD_POT_FS_ANALYTIC, false>(A, C, P, sp, bar, stamps, grid_out, s);
-    if (P.kind == MD_POT_KNOTS)
-        return P.ns == 1 ? launch_t<PREC, T, MD_POT_KNOTS, false>(A, C, P, sp, bar, stamps, grid_out, s)
-                         : launch_t<PREC, T, MD_POT_KNOTS, true>(A, C, P, sp, bar, stamps, grid_out, s);
-    if (P.ns == 1) {
-        if (smem_table_bytes(P.kind, P.ns, PREC, P.nk) > 0) {
-            if constexpr (PREC == MD_PREC_MIXED && T <= 8) {
-                if (C.tile == kWalkStaged)
-                    return launch_t<PREC, T, MD_POT_TABLES, false, 1024, true, kWalkStaged>(A, C, P, sp, bar, stamps,
-                                                                                           grid_out, s);
-                if (C.tile == kWalkCells)
-                    return launch_t<PREC, T, MD_POT_TABLES, false, 1024, true, kWalkCells>(A, C, P, sp, bar, stamps,
-                                                                                          grid_out, s);
-                if (C.tile == kWalkHalf)
-                    return launch_t<PREC, T, MD_POT_TABLES, false, 1024, true, kWalkHalf>(A, C, P, sp, bar, stamps,
-                                                                                         grid_out, s);
+    } else {
+        if (P.kind == MD_POT_FS_ANALYTIC)
+            return launch_t<PREC, T, MD_POT_FS_ANALYTIC, false>(A, C, P, sp, bar, stamps, grid_out, s);
+        if (P.kind == MD_POT_KNOTS)
+            return P.ns == 1 ? launch_t<PREC, T, MD_POT_KNOTS, false>(A, C, P, sp, bar, stamps, grid_out, s)
+                             : launch_t<PREC, T, MD_POT_KNOTS, true>(A, C, P, sp, bar, stamps, grid_out, s);
+        if (P.ns == 1) {
+            if (smem_table_bytes(P.kind, P.ns, PREC, P.nk) > 0) {
+                if constexpr (PREC == MD_PREC_MIXED && T <= 8) {
+                    if (C.tile == kWalkStaged)
+                        return launch_t<PREC, T, MD_POT_TABLES, false, 1024, true, kWalkStaged>(A, C, P, sp, bar, stamps,
+                                                                                               grid_out, s);
+                    if (C.tile == kWalkCells)
+                        return launch_t<PREC, T, MD_POT_TABLES, false, 1024, true, kWalkCells>(A, C, P, sp, bar, stamps,
+                                                                                              grid_out, s);
+                    if (C.tile == kWalkHalf)
+                        return launch_t<PREC, T, MD_POT_TABLES, false, 1024, true, kWalkHalf>(A, C, P, sp, bar, stamps,
+                                                                                             grid_out, s);
+                }
+                return launch_t<PREC, T, MD_POT_TABLES, false, MD_SMT_THREADS, true>(A, C, P, sp, bar, stamps, grid_out,
+                                                                                    s);
             }
-            return launch_t<PREC, T, MD_POT_TABLES, false, MD_SMT_THREADS, true>(A, C, P, sp, bar, stamps, grid_out,
-                                                                                s);
+            return launch_t<PREC, T, MD_POT_TABLES, false>(A, C, P, sp, bar, stamps, grid_out, s);
         }
-        return launch_t<PREC, T, MD_POT_TABLES, false>(A, C, P, sp, bar, stamps, grid_out, s);
+        // several species: the table of pair (0, 0), the host species, in shared memory
+        if (MD_SMEM_TABLE && PREC == MD_PREC_MIXED && (size_t)P.nk * 32 <= kSmemTableMax)
+            return launch_t<PREC, T, MD_POT_TABLES, true, MD_SMT_THREADS, true>(A, C, P, sp, bar, stamps, grid_out, s);
+        return launch_t<PREC, T, MD_POT_TABLES, true>(A, C, P, sp, bar, stamps, grid_out, s);
     }
-    // several species: the table of pair (0, 0), the host species, in shared memory
-    if (MD_SMEM_TABLE && PREC == MD_PREC_MIXED && (size_t)P.nk * 32 <= kSmemTableMax)
-        return launch_t<PREC, T, MD_POT_TABLES, true, MD_SMT_THREADS, true>(A, C, P, sp, bar, stamps, grid_out, s);
-    return launch_t<PREC, T, MD_POT_TABLES, true>(A, C, P, sp, bar, stamps, grid_out, s);
 }
 
 }  // namespace st
 
 // One launcher per (precision, lanes per atom), each defined in its own translation unit
-// (md_step_{m,d}_{a,b,c}.cu: the instantiations compile in parallel); md_step_dispatch.cu picks.
+// (md_step_{m,d,e}_{a,b,c}.cu: the instantiations compile in parallel); md_step_dispatch.cu picks.
 #define MD_STEP_FN(P, T) launch_step_##P##_l##T
 #define MD_STEP_DECL(P, T)                                                                                  \
     cudaError_t MD_STEP_FN(P, T)(const Atoms &A, const Cells &C, const Pot &Pt, const StepParams &sp,     \
