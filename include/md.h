@@ -179,7 +179,14 @@ enum { MD_INTEGRATOR_VERLET = 0, MD_INTEGRATOR_PC3 = 1 };
  * The group walks apply to mixed precision, one system (no batch), one species with a knot
  * table that fits in shared memory, no strain ramp, and 1-8 lanes per atom (more lanes walk
  * LIST); a build at which some group's neighbourhood exceeds the stage's capacity makes the
- * passes take the LIST walk until the next build (CELLS then builds the list).  AUTO = LIST (on
+ * passes take the LIST walk until the next build (CELLS then builds the list).
+ * On the FP64 path HALF is the half list over the full list instead (one species, FS analytic or
+ * knot tables, k_max <= 256; batches, strain, thermostat and both integrators allowed): each build
+ * reorders every row so that its entries j > i (cell order) come first, each pass computes every
+ * pair once from those entries and adds the neighbour's share of rho, force and pair energy to
+ * FP64 accumulators with atomic adds, and F(rho) and the kick follow in phases of their own.
+ * Results equal LIST's to FP64 rounding; the order of the atomic adds, and so the last bits,
+ * varies from run to run.  AUTO = LIST (on
  * GB300 every group walk measured slower for fcc Cu with its 5,000-knot table in shared memory:
  * one 1024-thread block per SM stages, then computes); a group walk where it does not apply is
  * MD_ERR_ARG at md_create.

@@ -297,7 +297,7 @@ cudaError_t enqueue_forces(md_ctx *ctx) {
     if (e == cudaSuccess) e = launch_density(ctx->A, ctx->P, ctx->precision, ctx->lanes, ctx->stream);
     if (e == cudaSuccess)
         e = launch_force(ctx->A, ctx->P, ctx->precision, ctx->lanes, false, true, 0.0, ctx->stream);
-    ctx->part_rows = partial_blocks((int)ctx->n, ctx->lanes);
+    ctx->part_rows = partial_blocks((int)ctx->n, ctx->lanes) + (ctx->A.pairs ? partial_blocks((int)ctx->n, 1) : 0);
     if (e == cudaSuccess) e = launch_reduce(ctx->A, ctx->part_rows, ctx->d_reduce, ctx->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ctx->h_reduce, ctx->d_reduce, sizeof(double) * kPartials, cudaMemcpyDeviceToHost,
@@ -626,8 +626,9 @@ md_status create_common(md_ctx *ctx, const md_config *cfg, const md_potential *p
     }
     if (n_rep > 1) chk(dalloc(ctx, &A.rep, n));
     A.sorted = A.cell_of;  // cell_of is consumed by the scatter before the in-cell sort writes
-    // partial-sum rows: a stand-alone force launch (<= 8 lanes) or a persistent grid
-    const int rows = std::max(partial_blocks((int)n, 8), 8192);
+    // partial-sum rows: a stand-alone force launch at up to 32 lanes per atom (and, for the FP64
+    // pair walk, the per-atom phase after it), or a persistent grid
+    const int rows = std::max(partial_blocks((int)n, 32) + partial_blocks((int)n, 1), 8192);
     A.part_stride = rows;
     chk(dalloc(ctx, &A.partials, (size_t)rows * kPartials));
     chk(dalloc(ctx, &ctx->d_boxes, n_rep));
@@ -655,9 +656,24 @@ md_status create_common(md_ctx *ctx, const md_config *cfg, const md_potential *p
                                                          : 0;
         const bool eligible = tbytes > 0 && n_rep == 1 && reach == 1 && !ctx->sur && cfg->strain_rate_zz == 0.0 &&
                               ctx->lanes <= 8 && n > 0;
-        const bool grouped =
-            cfg->passes == MD_PASSES_STAGED || cfg->passes == MD_PASSES_CELLS || cfg->passes == MD_PASSES_HALF;
-        if (cfg->passes != MD_PASSES_AUTO && cfg->passes != MD_PASSES_LIST && !grouped) return MD_ERR_ARG;
+        // FP64 and the half list: the pair walk over the full list's entries j > i (kWalkPairs)
+        const bool pairs = cfg->precision == MD_PREC_FP64 && cfg->passes == MD_PASSES_HALF;
+        if (pairs) {
+            if (ns != 1 || ctx->sur || (pot->kind != MD_POT_TABLES && pot->kind != MD_POT_FS_ANALYTIC) ||
+                cfg->k_max > kPairsKMax) {
+                ctx->err = "the FP64 half list takes one species (FS or tables) and k_max <= 256";
+                return MD_ERR_ARG;
+            }
+            A.pairs = 1;
+            chk(dalloc(ctx, &A.cup, n));
+            chk(dalloc(ctx, &A.rho_acc, n));
+            chk(dalloc(ctx, &A.f_acc, n));
+            if (e == cudaSuccess) e = cudaMemset(A.rho_acc, 0, sizeof(double) * (size_t)(n > 0 ? n : 1));
+            if (e == cudaSuccess) e = cudaMemset(A.f_acc, 0, sizeof(double4_32a) * (size_t)(n > 0 ? n : 1));
+        }
+        const bool grouped = !pairs && (cfg->passes == MD_PASSES_STAGED || cfg->passes == MD_PASSES_CELLS ||
+                                        cfg->passes == MD_PASSES_HALF);
+        if (cfg->passes != MD_PASSES_AUTO && cfg->passes != MD_PASSES_LIST && !grouped && !pairs) return MD_ERR_ARG;
         if (grouped && !eligible) {
             ctx->err = "group walks need mixed precision, one system, one species with a knot table that fits "
                        "in shared memory, no strain ramp and at most 8 lanes per atom";
@@ -1643,6 +1659,10 @@ md_status md_get_passes(md_ctx *ctx, md_passes *out) {
     out->capacity = C.tile ? C.cap : 0;
     out->last_max = C.tile ? ctx->h_flags->tile_max : 0;
     out->active = C.tile && ctx->lanes <= 8 && !ctx->h_flags->tile_bad;
+    if (ctx->A.pairs) {   // the FP64 half list over the full list's rows
+        out->walk = MD_PASSES_HALF;
+        out->active = 1;
+    }
     return MD_OK;
 }
 

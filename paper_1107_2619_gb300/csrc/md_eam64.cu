@@ -33,6 +33,43 @@ __global__ void __launch_bounds__(kThreads) k_force64(Atoms A, Pot P, double hal
     if (ENERGY) block_partials(part, A.partials, A.part_stride);
 }
 
+// The pair walk (A.pairs): each pair once, then the per-atom phase that needs every share.
+template <int T, int KIND>
+__global__ void __launch_bounds__(kThreads) k_density64_pairs(Atoms A, Pot P) {
+    clear_rebuild_once(A.flags);
+    ps::density64_pairs_item<T, KIND>(A, P, A.boxes, (long long)blockIdx.x * kThreads + threadIdx.x);
+}
+
+__global__ void __launch_bounds__(kThreads) k_embed64_pairs(Atoms A, Pot P) {
+    const int i = blockIdx.x * kThreads + threadIdx.x;
+    if (i < A.n) ps::pairs_embed64(A, P, i);
+}
+
+template <int T, int KIND, bool ENERGY>
+__global__ void __launch_bounds__(kThreads) k_force64_pairs(Atoms A, Pot P) {
+    double part[kPartials];
+#pragma unroll
+    for (int q = 0; q < kPartials; q++) part[q] = 0.0;
+    ps::force64_pairs_item<T, KIND, ENERGY>(A, P, A.boxes, (long long)blockIdx.x * kThreads + threadIdx.x, part);
+    if (ENERGY) block_partials(part, A.partials, A.part_stride);
+}
+
+// The per-atom phase after the pair force pass; its partial sums go to the block rows after the
+// force pass's (virial) rows, and the reduction adds both sets.
+template <bool ENERGY>
+__global__ void __launch_bounds__(kThreads) k_finish64_pairs(Atoms A, double half_dt, int kick, int row0) {
+    double part[kPartials];
+#pragma unroll
+    for (int q = 0; q < kPartials; q++) part[q] = 0.0;
+    const int i = blockIdx.x * kThreads + threadIdx.x;
+    if (i < A.n) ps::pairs_kick64<ENERGY>(A, i, half_dt, kick ? kMotionVerlet : kMotionNone, part);
+    if (ENERGY) {
+        Atoms B = A;
+        B.partials = A.partials + row0;
+        block_partials(part, B.partials, A.part_stride);
+    }
+}
+
 // Deterministic final reduction of the per-block partials: one block per quantity, a fixed
 // thread-to-row mapping (coalesced rows partials[q*stride + b]) and a fixed tree, so repeated
 // runs give bitwise identical totals.
@@ -53,6 +90,12 @@ __global__ void k_reduce(const double *__restrict__ partials, int nblocks, int s
 template <int T>
 void density_t(const Atoms &A, const Pot &P, cudaStream_t s) {
     const int nb = A.n > 0 ? blocks_for_lanes<T>(A.n) : 1;
+    if (A.pairs) {
+        if (P.kind == MD_POT_FS_ANALYTIC) k_density64_pairs<T, MD_POT_FS_ANALYTIC><<<nb, kThreads, 0, s>>>(A, P);
+        else k_density64_pairs<T, MD_POT_TABLES><<<nb, kThreads, 0, s>>>(A, P);
+        k_embed64_pairs<<<blocks_for(A.n > 0 ? A.n : 1, kThreads), kThreads, 0, s>>>(A, P);
+        return;
+    }
     if (P.kind == MD_POT_FS_ANALYTIC) k_density64<T, MD_POT_FS_ANALYTIC, false><<<nb, kThreads, 0, s>>>(A, P);
     else if (P.kind == MD_POT_KNOTS && P.ns == 1) k_density64<T, MD_POT_KNOTS, false><<<nb, kThreads, 0, s>>>(A, P);
     else if (P.kind == MD_POT_KNOTS) k_density64<T, MD_POT_KNOTS, true><<<nb, kThreads, 0, s>>>(A, P);
@@ -63,6 +106,12 @@ void density_t(const Atoms &A, const Pot &P, cudaStream_t s) {
 template <int T, bool ENERGY>
 void force_te(const Atoms &A, const Pot &P, double half_dt, int kick, cudaStream_t s) {
     const int nb = blocks_for_lanes<T>(A.n);
+    if (A.pairs) {   // the pair force pass, then the per-atom phase (partial rows after the pass's)
+        if (P.kind == MD_POT_FS_ANALYTIC) k_force64_pairs<T, MD_POT_FS_ANALYTIC, ENERGY><<<nb, kThreads, 0, s>>>(A, P);
+        else k_force64_pairs<T, MD_POT_TABLES, ENERGY><<<nb, kThreads, 0, s>>>(A, P);
+        k_finish64_pairs<ENERGY><<<blocks_for(A.n > 0 ? A.n : 1, kThreads), kThreads, 0, s>>>(A, half_dt, kick, nb);
+        return;
+    }
     if (P.kind == MD_POT_FS_ANALYTIC)
         k_force64<T, MD_POT_FS_ANALYTIC, false, ENERGY><<<nb, kThreads, 0, s>>>(A, P, half_dt, kick);
     else if (P.kind == MD_POT_KNOTS && P.ns == 1)

@@ -145,6 +145,8 @@ struct Atoms {
                                              // cell-group stencil (same plane layout as nbr); half walk:
                                              // only the entries j > i, lcount of them
     int32_t *lcount;                         // half walk: entries of each half row
+    int32_t *cup;                            // FP64 pair walk: entries j > i at the front of each row
+    int pairs;                               // 1: the FP64 pair walk (kWalkPairs)
     double *rho_acc;                         // half walk: density accumulators [n]
     double4_32a *f_acc;                      // half walk: force (x, y, z) and pair-energy (w) accumulators
     double4_32a *g2, *g3;                    // predictor-corrector (md.h MD_INTEGRATOR_PC3): the predicted
@@ -224,7 +226,11 @@ struct Cells {
 };
 
 // Neighbour walks of the step kernel's passes (md_config.passes).
-enum : int { kWalkList = 0, kWalkStaged = 1, kWalkCells = 2, kWalkHalf = 3 };
+enum : int { kWalkList = 0, kWalkStaged = 1, kWalkCells = 2, kWalkHalf = 3, kWalkPairs = 4 };
+// kWalkPairs: FP64, one species, the list walk with each pair computed once (each row partitioned
+// at every build so that its entries j > i come first, cup[i] of them), the neighbour's share
+// added with FP64 atomics (md_config.passes = MD_PASSES_HALF on the FP64 path)
+constexpr int kPairsKMax = 256;   // rows partitioned in registers: k_max <= 8 x 32
 
 // Shared memory of the mixed-precision step kernel: a single-species knot table (2 float4 per
 // knot) of at most kSmemTableMax bytes, and the stage of the group walks; together at most

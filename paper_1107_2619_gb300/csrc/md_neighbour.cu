@@ -130,6 +130,12 @@ cudaError_t launch_clear_rebuild(Flags *f, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// FP64 pair walk: each row's entries j > i first (one warp per atom).
+__global__ void k_partition_rows(Atoms A) {
+    const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w < A.n) ph::partition_row_warp(A, (int)w, threadIdx.x & 31);
+}
+
 cudaError_t launch_rebuild(const Atoms &A, const Cells &C, double rl2, float band_lo, float band_hi,
                            int list_group, cudaStream_t s) {
     const int nb = capped_blocks(A.n, kThreads);
@@ -147,6 +153,7 @@ cudaError_t launch_rebuild(const Atoms &A, const Cells &C, double rl2, float ban
         if (C.tile == kWalkStaged) launch_build<1>(A, C, rl2, band_lo, band_hi, list_group, nbl, s);
         else if (C.tile == kWalkHalf) launch_build<2>(A, C, rl2, band_lo, band_hi, list_group, nbl, s);
         else launch_build<0>(A, C, rl2, band_lo, band_hi, list_group, nbl, s);
+        if (A.pairs) k_partition_rows<<<(int)(((long long)A.n * 32 + kThreads - 1) / kThreads), kThreads, 0, s>>>(A);
     }
     return cudaGetLastError();
 }

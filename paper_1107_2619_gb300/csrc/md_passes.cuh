@@ -665,6 +665,187 @@ __device__ __forceinline__ int force64_item(const Atoms &A, const Pot &P, const 
     return i;
 }
 
+// ======================================================================= FP64, each pair once
+// The half list of §3.2.2 taken from the full list: atom i handles only its entries j > i (cell
+// order; the rows are partitioned at every build so that these come first, cup[i] of them),
+// computes the pair term once and adds the neighbour's share to FP64 accumulators with atomic
+// adds (Newton's third law).  The density pass leaves each atom's own share in rho and
+// the neighbours' shares in rho_acc; F(rho) follows in a phase of its own (pairs_embed64) once
+// every share is in, the force pass likewise leaves its own share in force and the others' in
+// f_acc, and the kick follows in a phase of its own (pairs_kick64).  The per-entry derivative
+// cache holds the entries j > i only.  The order of the atomic adds, and so the last bits of the
+// sums, varies from run to run.  One species.
+template <int T, int KIND>
+__device__ __forceinline__ void density64_pairs_item(const Atoms &A, const Pot &P, const Box *boxes, long long g) {
+    const int i = (int)(g / T), lane = (int)(g & (T - 1));
+    const bool live = i < A.n;
+    double rho = 0.0;
+    const bool wrap = needs_image(A, i, live);
+    if (live) {
+        const Box &B = boxes[ph::replica_of(A, i)];
+        const double4_32a pi = ld_phase(A.posd + i);
+        const int cnt = ld_phase(A.cup + i);
+        const NbrRow row = nbr_row(A, i);
+        const DRow drow = dcache_row(A, i);
+        auto walk = [&](auto wrapt) {
+            using W = decltype(wrapt);
+            for (int k = lane; k < cnt; k += T) {
+                const int j = ld_phase(row.ptr(k));
+                const double4_32a pj = ld_phase(A.posd + j);
+                const double dx = sep64<W>(pj.x - pi.x, B.L[0], B.invL[0]);
+                const double dy = sep64<W>(pj.y - pi.y, B.L[1], B.invL[1]);
+                const double dz = sep64<W>(pj.z - pi.z, B.L[2], B.invL[2]);
+                const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+                if (!(r2 < P.rc2)) {
+                    *drow.ptr(k) = make_double2(0.0, 0.0);
+                    continue;
+                }
+                const double rinv = rsqrt64(r2);
+                const double r = r2 * rinv;
+                double phi, dV, dphi;
+                if (KIND == MD_POT_FS_ANALYTIC) {
+                    phi = fs_phi<double>(P.fs, P.bd, r);
+                    fs_V<double>(P.fs, r, dV);
+                    dphi = fs_dphi<double>(P.fs, P.bd, r);
+                } else {
+                    double t, d;
+                    bool below;
+                    const int kr = knot_row((r - P.r_min) * P.inv_dr, P.nk, t, below);
+                    if (below) atomicAdd(&A.flags->range_violations, 1ull);
+                    const double4_32a c = P.VP64[(size_t)kr * 2 + 1];
+                    phi = cubic(t, c.x, c.y, c.z, c.w, below, d);
+                    const double4_32a dv = P.D64[2 * kr], dp = P.D64[2 * kr + 1];
+                    dV = below ? dv.x : fma(t, fma(dv.z, t, dv.y), dv.x);
+                    dphi = below ? dp.x : fma(t, fma(dp.z, t, dp.y), dp.x);
+                }
+                rho += phi;
+                atomicAdd(A.rho_acc + j, phi);
+                *drow.ptr(k) = make_double2(dV * rinv, dphi * rinv);
+            }
+        };
+        if (wrap) walk(std::true_type{});
+        else walk(std::false_type{});
+    }
+    rho = lane_sum<T>(rho);
+    if (live && lane == 0) A.rho[i] = rho;
+}
+
+// After the pair density pass, per atom: rho = own share + the neighbours' shares; F, F'; the
+// pass-2 copy; the accumulators cleared for the force pass.
+__device__ __forceinline__ void pairs_embed64(const Atoms &A, const Pot &P, int i) {
+    const double rho = A.rho[i] + A.rho_acc[i];
+    double dF;
+    const double F = embed64(P, 0, rho, dF, A.flags);
+    A.rho[i] = rho;
+    A.dF[i] = dF;
+    A.e_atom[i] = F;
+    const double4_32a p = A.posd[i];
+    A.p2d[i] = make_double4_32a(p.x, p.y, p.z, dF);
+    A.rho_acc[i] = 0.0;
+    A.f_acc[i] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+}
+
+template <int T, int KIND, bool ENERGY>
+__device__ __forceinline__ void force64_pairs_item(const Atoms &A, const Pot &P, const Box *boxes, long long g,
+                                                   double (&part)[kPartials]) {
+    const int i = (int)(g / T), lane = (int)(g & (T - 1));
+    const bool live = i < A.n;
+    double fx = 0.0, fy = 0.0, fz = 0.0, ep = 0.0;
+    double wxx = 0.0, wyy = 0.0, wzz = 0.0, wyz = 0.0, wxz = 0.0, wxy = 0.0;
+    const bool wrap = needs_image(A, i, live);
+    if (live) {
+        const Box &B = boxes[ph::replica_of(A, i)];
+        const double4_32a pi = A.p2d[i];
+        const int cnt = ld_phase(A.cup + i);
+        const NbrRow row = nbr_row(A, i);
+        const DRow drow = dcache_row(A, i);
+        auto walk = [&](auto wrapt) {
+            using W = decltype(wrapt);
+            for (int k = lane; k < cnt; k += T) {
+                const int j = ld_phase(row.ptr(k));
+                const double4_32a pj = ld_phase(A.p2d + j);
+                const double2 e = ld_phase(drow.ptr(k));
+                const double dx = sep64<W>(pj.x - pi.x, B.L[0], B.invL[0]);
+                const double dy = sep64<W>(pj.y - pi.y, B.L[1], B.invL[1]);
+                const double dz = sep64<W>(pj.z - pi.z, B.L[2], B.invL[2]);
+                const double gr = fma(pi.w + pj.w, e.y, e.x);
+                const double gx = gr * dx, gy = gr * dy, gz = gr * dz;
+                fx += gx;
+                fy += gy;
+                fz += gz;
+                double vj = 0.0;
+                if (ENERGY) {
+                    const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+                    if (r2 < P.rc2) {
+                        const double r = r2 * rsqrt64(r2);
+                        double V, dV;
+                        if (KIND == MD_POT_FS_ANALYTIC) {
+                            V = fs_V<double>(P.fs, r, dV);
+                        } else {
+                            double t;
+                            bool below;
+                            const int kr = knot_row((r - P.r_min) * P.inv_dr, P.nk, t, below);
+                            const double4_32a cv = P.VP64[(size_t)kr * 2];
+                            V = cubic(t, cv.x, cv.y, cv.z, cv.w, below, dV);
+                        }
+                        ep = fma(0.5, V, ep);
+                        vj = 0.5 * V;
+                    }
+                    // the pair's whole virial, once
+                    wxx = fma(-gx, dx, wxx);
+                    wyy = fma(-gy, dy, wyy);
+                    wzz = fma(-gz, dz, wzz);
+                    wyz = fma(-gy, dz, wyz);
+                    wxz = fma(-gx, dz, wxz);
+                    wxy = fma(-gx, dy, wxy);
+                }
+                double *acc = reinterpret_cast<double *>(A.f_acc + j);
+                atomicAdd(acc, -gx);
+                atomicAdd(acc + 1, -gy);
+                atomicAdd(acc + 2, -gz);
+                if (ENERGY) atomicAdd(acc + 3, vj);
+            }
+        };
+        if (wrap) walk(std::true_type{});
+        else walk(std::false_type{});
+    }
+    fx = lane_sum<T>(fx);
+    fy = lane_sum<T>(fy);
+    fz = lane_sum<T>(fz);
+    if (ENERGY) {
+        ep = lane_sum<T>(ep);
+        wxx = lane_sum<T>(wxx); wyy = lane_sum<T>(wyy); wzz = lane_sum<T>(wzz);
+        wyz = lane_sum<T>(wyz); wxz = lane_sum<T>(wxz); wxy = lane_sum<T>(wxy);
+    }
+    if (!(live && lane == 0)) return;
+    A.force[i] = make_double4_32a(fx, fy, fz, ep);
+    if (ENERGY) {
+        part[2] += wxx; part[3] += wyy; part[4] += wzz;
+        part[5] += wyz; part[6] += wxz; part[7] += wxy;
+    }
+}
+
+// After the pair force pass, per atom: the force = own share + the neighbours' shares, then what
+// follows it (the kick or the corrector), on the energy step the atom's energy and partial sums.
+template <bool ENERGY>
+__device__ __forceinline__ void pairs_kick64(const Atoms &A, int i, double half_dt, int motion,
+                                             double (&part)[kPartials]) {
+    const double4_32a own = A.force[i], acc = A.f_acc[i];
+    const double fx = own.x + acc.x, fy = own.y + acc.y, fz = own.z + acc.z;
+    A.force[i] = make_double4_32a(fx, fy, fz, 0.0);
+    if (!isfinite(fx + fy + fz)) atomicOr(&A.flags->error, FLAG_NONFINITE);
+    double4_32a v = A.vel[i];
+    finish_motion(A, i, v, fx, fy, fz, half_dt, motion);
+    if (ENERGY) {
+        const double e = A.e_atom[i] + own.w + acc.w;
+        A.e_atom[i] = e;
+        const double m = 1.0 / (kMvv2e * v.w);
+        part[0] += e;
+        part[1] += m * fma(v.x, v.x, fma(v.y, v.y, v.z * v.z));
+        part[8] += m * v.x; part[9] += m * v.y; part[10] += m * v.z;
+    }
+}
+
 // ======================================================================= double-float (MD_PREC_DF)
 // One species, knot tables.  The separation of two atoms is formed from the double-float image
 // coordinates (md_df.cuh; posx/p2x): the high parts lie within a factor of two of each other

@@ -348,6 +348,39 @@ __device__ __forceinline__ void copyback_atom(const Atoms &A, const Box *boxes, 
     }
 }
 
+// The FP64 pair walk's row order (one warp per atom): the entries j > i first, then the others,
+// each group in its order, and cup[i] = the number of the first.  The whole row (k_max <=
+// kPairsKMax) is read into registers before any entry is written back.
+__device__ __forceinline__ void partition_row_warp(const Atoms &A, int i, int lane) {
+    const int cnt = min(A.count[i], A.k_max);
+    const NbrRow row = nbr_row(A, i);
+    int v[kPairsKMax / 32];
+#pragma unroll
+    for (int c = 0; c < kPairsKMax / 32; c++) {
+        const int k = 32 * c + lane;
+        v[c] = k < cnt ? *row.ptr(k) : -1;
+    }
+    __syncwarp();
+    const unsigned below = (1u << lane) - 1u;
+    int nup = 0;
+#pragma unroll
+    for (int c = 0; c < kPairsKMax / 32; c++) {
+        const bool up = v[c] > i;
+        const unsigned m = __ballot_sync(0xffffffffu, up);
+        if (up) *row.ptr(nup + __popc(m & below)) = v[c];
+        nup += __popc(m);
+    }
+    int pos = nup;
+#pragma unroll
+    for (int c = 0; c < kPairsKMax / 32; c++) {
+        const bool lo = v[c] >= 0 && v[c] < i;
+        const unsigned m = __ballot_sync(0xffffffffu, lo);
+        if (lo) *row.ptr(pos + __popc(m & below)) = v[c];
+        pos += __popc(m);
+    }
+    if (lane == 0) A.cup[i] = nup;
+}
+
 // The exact neighbour test: the IEEE operations, order and absence of contraction of the
 // definition d = r_j - r_i; d -= L*rint(d*(1/L)); r2 = (dx dx + dy dy) + dz dz.
 __device__ __forceinline__ double mi_exact(double d, double L, double invL) {

@@ -144,11 +144,15 @@ __device__ __forceinline__ void thermo_update(const StepParams &sp, int n_rep, l
 // else over atoms through the list.  The cell walk builds no list at a rebuild unless a group
 // did not fit (the list walk then needs one).  The half walk adds two phases: F(rho) after the
 // density pass and the kicks after the force pass (each waits for every group's shares).
+// The walks over cell groups staged in shared memory (md_tile.cuh).
+template <int WALK>
+constexpr bool kGroupWalk = WALK == kWalkStaged || WALK == kWalkCells || WALK == kWalkHalf;
+
 template <int PREC, int T, int KIND, bool MULTI, int NT, bool SMT, int WALK>
 __global__ void __launch_bounds__(NT, NT == kThreads ? (PREC == MD_PREC_DF ? MD_STEP_MIN_BLOCKS_DF : MD_STEP_MIN_BLOCKS) : 1)
     k_step(Atoms A, Cells C, Pot P, StepParams sp, GridBarrier *bar, unsigned long long *stamps) {
     __shared__ int ws[32];
-    __shared__ int tile_loc[WALK ? tl::kTileMaxSt + 1 : 1];
+    __shared__ int tile_loc[kGroupWalk<WALK> ? tl::kTileMaxSt + 1 : 1];
     __shared__ uint16_t cells_q[WALK == kWalkCells ? NT / 32 : 1][kCellsQueue];
     extern __shared__ float4 sm_table_f4[];   // [SMT table][stage]
     float4 *const stage = sm_table_f4 + (SMT ? 2 * P.nk : 0);
@@ -242,7 +246,7 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? (PREC == MD_PREC_DF ? MD_
             MD_SYNC();
             MD_STAMP(4);
             for (long long i = tid; i < A.n; i += stride) ph::scatter_atom(A, C, (int)i);
-            if constexpr (WALK != kWalkList) {
+            if constexpr (kGroupWalk<WALK>) {
                 for (long long g = tid; g < C.n_groups; g += stride) ph::group_table(C, (int)g, A.flags);
             } else {
                 if (C.tile && lead) A.flags->tile_bad = 1;   // this build writes no local lists
@@ -264,6 +268,10 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? (PREC == MD_PREC_DF ? MD_
                 m = __reduce_max_sync(0xffffffffu, m);
                 if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(&A.flags->max_count, m);
             }
+            if constexpr (WALK == kWalkPairs) {   // each row's entries j > i first
+                MD_SYNC();
+                for (long long i = tid >> 5; i < A.n; i += stride >> 5) ph::partition_row_warp(A, (int)i, threadIdx.x & 31);
+            }
             MD_SYNC();
             MD_STAMP(9);
         } else if (srow) {
@@ -276,8 +284,8 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? (PREC == MD_PREC_DF ? MD_
             A.flags->need_rebuild = 0;
         }
         bool tiled = false;
-        if constexpr (WALK != kWalkList) tiled = *reinterpret_cast<volatile int32_t *>(&A.flags->tile_bad) == 0;
-        if constexpr (WALK != kWalkList) {
+        if constexpr (kGroupWalk<WALK>) tiled = *reinterpret_cast<volatile int32_t *>(&A.flags->tile_bad) == 0;
+        if constexpr (kGroupWalk<WALK>) {
             if (tiled) {
                 for (int g = blockIdx.x; g < C.n_groups; g += nb) {
                     const tl::Group G = tl::stage_group<NT>(C, boxes[0], A.posf, g, stage, tile_loc,
@@ -302,8 +310,13 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? (PREC == MD_PREC_DF ? MD_
                 }
             }
         }
-        if (!tiled)
+        if constexpr (WALK == kWalkPairs) {   // each pair once, then F(rho) once every share is in
+            for (long long g = tid; g < items; g += stride) ps::density64_pairs_item<T, KIND>(A, P, boxes, g);
+            MD_SYNC();
+            for (long long i = tid; i < A.n; i += stride) ps::pairs_embed64(A, P, (int)i);
+        } else if (!tiled) {
             for (long long g = tid; g < items; g += stride) ps::density_item<PREC, T, KIND, MULTI, SMT>(A, P, boxes, g);
+        }
         MD_SYNC();
         MD_STAMP(10);
         // ------------------------------------------------ force pass (+ kicks)
@@ -315,7 +328,7 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? (PREC == MD_PREC_DF ? MD_
 #pragma unroll
         for (int q = 0; q < kPartials; q++) part[q] = 0.0;
         if (last && sp.energy_last) {
-            if constexpr (WALK != kWalkList) {
+            if constexpr (kGroupWalk<WALK>) {
                 if (tiled) {
                     for (int g = blockIdx.x; g < C.n_groups; g += nb) {
                         const tl::Group G = tl::stage_group<NT>(C, boxes[0], A.p2f, g, stage, tile_loc,
@@ -343,12 +356,18 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? (PREC == MD_PREC_DF ? MD_
                     }
                 }
             }
-            if (!tiled)
+            if constexpr (WALK == kWalkPairs) {   // each pair once, then the kicks once every share is in
+                for (long long g = tid; g < items; g += stride)
+                    ps::force64_pairs_item<T, KIND, true>(A, P, boxes, g, part);
+                MD_SYNC();
+                for (long long i = tid; i < A.n; i += stride) ps::pairs_kick64<true>(A, (int)i, sp.half_dt, sp.motion, part);
+            } else if (!tiled) {
                 for (long long g = tid; g < items; g += stride)
                     ps::force_item<PREC, T, KIND, MULTI, true, SMT>(A, P, boxes, g, sp.half_dt, sp.motion, part);
+            }
             eam::block_partials<NT>(part, A.partials, A.part_stride);
         } else {
-            if constexpr (WALK != kWalkList) {
+            if constexpr (kGroupWalk<WALK>) {
                 if (tiled) {
                     for (int g = blockIdx.x; g < C.n_groups; g += nb) {
                         const tl::Group G = tl::stage_group<NT>(C, boxes[0], A.p2f, g, stage, tile_loc,
@@ -382,13 +401,22 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? (PREC == MD_PREC_DF ? MD_
                     }
                 }
             }
-            if (!tiled)
+            if constexpr (WALK == kWalkPairs) {
+                for (long long g = tid; g < items; g += stride)
+                    ps::force64_pairs_item<T, KIND, false>(A, P, boxes, g, part);
+                MD_SYNC();
+                for (long long i = tid; i < A.n; i += stride) {
+                    ps::pairs_kick64<false>(A, (int)i, sp.half_dt, sp.motion, part);
+                    if (fuse) ph::open_step(A, boxes, (int)i, sp.motion, sp.half_dt, sp.dt, sp.strain_scale, false, sp.lim2);
+                }
+            } else if (!tiled) {
                 for (long long g = tid; g < items; g += stride) {
                     const int i = ps::force_item<PREC, T, KIND, MULTI, false, SMT>(A, P, boxes, g, sp.half_dt,
                                                                                    sp.motion, part);
                     if (fuse && i >= 0)
                         ph::open_step(A, boxes, i, sp.motion, sp.half_dt, sp.dt, sp.strain_scale, false, sp.lim2);
                 }
+            }
         }
         MD_SYNC();
         MD_STAMP(11);
@@ -442,9 +470,9 @@ cudaError_t launch_t(const Atoms &A, const Cells &C, const Pot &P, const StepPar
     static bool attr = false;
     const size_t dyn_max = WALK == kWalkCells ? kSmemDynMaxCells : kSmemDynMax;
     const size_t dyn = (SMT ? (size_t)P.nk * 32 : 0) +
-                       (WALK ? (size_t)C.cap * sizeof(float4) * (WALK == kWalkHalf ? 2 : 1) : 0);
+                       (kGroupWalk<WALK> ? (size_t)C.cap * sizeof(float4) * (WALK == kWalkHalf ? 2 : 1) : 0);
     if (dyn > dyn_max) return cudaErrorInvalidConfiguration;
-    if ((SMT || WALK) && !attr) {  // opt in to a large dynamic shared-memory carve-out (once)
+    if ((SMT || kGroupWalk<WALK>) && !attr) {  // opt in to a large dynamic shared-memory carve-out (once)
         cudaError_t e = cudaFuncSetAttribute(k_step<PREC, T, KIND, MULTI, NT, SMT, WALK>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max);
         if (e != cudaSuccess) return e;
@@ -484,6 +512,17 @@ cudaError_t launch_kind(const Atoms &A, const Cells &C, const Pot &P, const Step
         if (P.kind != MD_POT_TABLES || P.ns != 1) return cudaErrorInvalidValue;
         return launch_t<PREC, T, MD_POT_TABLES, false>(A, C, P, sp, bar, stamps, grid_out, s);
     } else {
+        if constexpr (PREC == MD_PREC_FP64) {   // each pair once: one species, FS or tables
+            if (A.pairs) {
+                if (P.kind == MD_POT_FS_ANALYTIC)
+                    return launch_t<PREC, T, MD_POT_FS_ANALYTIC, false, kThreads, false, kWalkPairs>(A, C, P, sp, bar,
+                                                                                                    stamps, grid_out, s);
+                if (P.kind == MD_POT_TABLES && P.ns == 1)
+                    return launch_t<PREC, T, MD_POT_TABLES, false, kThreads, false, kWalkPairs>(A, C, P, sp, bar, stamps,
+                                                                                               grid_out, s);
+                return cudaErrorInvalidValue;
+            }
+        }
         if (P.kind == MD_POT_FS_ANALYTIC)
             return launch_t<PREC, T, MD_POT_FS_ANALYTIC, false>(A, C, P, sp, bar, stamps, grid_out, s);
         if (P.kind == MD_POT_KNOTS)

@@ -574,12 +574,12 @@ class Batch(System):
     """A batch of independent replicas in one context (md_create_batch)."""
 
     def __init__(self, workloads, precision: str = "mixed", rebuild_every: int = 0, stream=None,
-                 k_max=None, lanes_per_atom: int = 0, integrator: str = "verlet"):
+                 k_max=None, lanes_per_atom: int = 0, integrator: str = "verlet", passes: str = "auto"):
         prec = PRECISIONS[precision]
         w0 = workloads[0]
         self.k_max = int(k_max or max(w.k_max for w in workloads))
         cfgs = [make_config(w.n_atoms, w.box, w0.skin, self.k_max, w0.dt_fs, prec, rebuild_every, False,
-                            w0.strain_rate_zz, stream, lanes_per_atom, integrator=integrator)
+                            w0.strain_rate_zz, stream, lanes_per_atom, passes=passes, integrator=integrator)
                 for w in workloads]
         pot, keep = make_potential(w0.potential)
         self.ctx = md_create_batch(cfgs, pot, [w.pos for w in workloads], [w.vel for w in workloads],
