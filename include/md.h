@@ -150,8 +150,8 @@ typedef struct {
  *     zero by md_set_state (and md_step_io, which calls it): the predictor restarts.  The
  *     acceleration term comes from the stored forces at each md_step, so an md_eam_forces call
  *     between steps restarts it from the forces at the current positions.  PC3 takes the list
- *     walk and no strain ramp, thermostat or surrogate (MD_ERR_ARG at md_create, MD_ERR_STATE at
- *     md_set_thermostat).
+ *     walk (or the FP64 half list) and no strain ramp, thermostat or surrogate (MD_ERR_ARG at
+ *     md_create, MD_ERR_STATE at md_set_thermostat).
  */
 enum { MD_INTEGRATOR_VERLET = 0, MD_INTEGRATOR_PC3 = 1 };
 

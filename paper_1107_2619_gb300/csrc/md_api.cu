@@ -457,8 +457,10 @@ md_status create_common(md_ctx *ctx, const md_config *cfg, const md_potential *p
     if (cfg->integrator != MD_INTEGRATOR_VERLET && cfg->integrator != MD_INTEGRATOR_PC3) return MD_ERR_ARG;
     if (cfg->integrator == MD_INTEGRATOR_PC3 &&
         (cfg->strain_rate_zz != 0.0 || pot->kind == MD_POT_SURROGATE ||
-         (cfg->passes != MD_PASSES_AUTO && cfg->passes != MD_PASSES_LIST))) {
-        ctx->err = "the predictor-corrector takes the list walk, no strain ramp and no surrogate";
+         (cfg->passes != MD_PASSES_AUTO && cfg->passes != MD_PASSES_LIST &&
+          !(cfg->passes == MD_PASSES_HALF && cfg->precision == MD_PREC_FP64)))) {
+        ctx->err = "the predictor-corrector takes the list walks (full, or the FP64 half list), no strain ramp and "
+                   "no surrogate";
         return MD_ERR_ARG;
     }
     for (double l : L)
