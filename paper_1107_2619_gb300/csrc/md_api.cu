@@ -670,7 +670,9 @@ md_status create_common(md_ctx *ctx, const md_config *cfg, const md_potential *p
             chk(dalloc(ctx, &A.cup, n));
             chk(dalloc(ctx, &A.rho_acc, n));
             chk(dalloc(ctx, &A.f_acc, n));
+            chk(dalloc(ctx, &A.e_acc, n));
             if (e == cudaSuccess) e = cudaMemset(A.rho_acc, 0, sizeof(double) * (size_t)(n > 0 ? n : 1));
+            if (e == cudaSuccess) e = cudaMemset(A.e_acc, 0, sizeof(double) * (size_t)(n > 0 ? n : 1));
             if (e == cudaSuccess) e = cudaMemset(A.f_acc, 0, sizeof(double4_32a) * (size_t)(n > 0 ? n : 1));
         }
         const bool grouped = !pairs && (cfg->passes == MD_PASSES_STAGED || cfg->passes == MD_PASSES_CELLS ||

@@ -20,7 +20,7 @@ namespace {
 template <int T, int KIND, bool MULTI>
 __global__ void __launch_bounds__(kThreads) k_density64(Atoms A, Pot P) {
     clear_rebuild_once(A.flags);
-    ps::density64_item<T, KIND, MULTI>(A, P, A.boxes, (long long)blockIdx.x * kThreads + threadIdx.x);
+    ps::density64_item<T, KIND, MULTI>(A, P, A.boxes, (long long)blockIdx.x * kThreads + threadIdx.x, true);
 }
 
 template <int T, int KIND, bool MULTI, bool ENERGY>
@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(kThreads) k_force64(Atoms A, Pot P, double hal
 template <int T, int KIND>
 __global__ void __launch_bounds__(kThreads) k_density64_pairs(Atoms A, Pot P) {
     clear_rebuild_once(A.flags);
-    ps::density64_pairs_item<T, KIND>(A, P, A.boxes, (long long)blockIdx.x * kThreads + threadIdx.x);
+    ps::density64_pairs_item<T, KIND>(A, P, A.boxes, (long long)blockIdx.x * kThreads + threadIdx.x, true);
 }
 
 __global__ void __launch_bounds__(kThreads) k_embed64_pairs(Atoms A, Pot P) {

@@ -13,7 +13,7 @@ namespace {
 template <int T>
 __global__ void __launch_bounds__(kThreads) k_density_df(Atoms A, Pot P) {
     clear_rebuild_once(A.flags);
-    ps::density_df_item<T>(A, P, A.boxes, (long long)blockIdx.x * kThreads + threadIdx.x);
+    ps::density_df_item<T>(A, P, A.boxes, (long long)blockIdx.x * kThreads + threadIdx.x, true);
 }
 
 template <int T, bool ENERGY>

@@ -148,6 +148,7 @@ struct Atoms {
     int32_t *cup;                            // FP64 pair walk: entries j > i at the front of each row
     int pairs;                               // 1: the FP64 pair walk (kWalkPairs)
     double *rho_acc;                         // half walk: density accumulators [n]
+    double *e_acc;                           // FP64 pair walk: pair-energy accumulators [n]
     double4_32a *f_acc;                      // half walk: force (x, y, z) and pair-energy (w) accumulators
     double4_32a *g2, *g3;                    // predictor-corrector (md.h MD_INTEGRATOR_PC3): the predicted
                                              // acceleration term (dt^2/2) a and the third-derivative term

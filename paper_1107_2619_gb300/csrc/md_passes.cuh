@@ -379,11 +379,14 @@ __device__ __forceinline__ int force32_item(const Atoms &A, const Pot &P, const 
 }
 
 // ======================================================================= FP64
+// energy (one species, derivative cache kept): the pair energies 1/2 V(r) of the atom are summed
+// here too, into E_i, and the force pass adds only the virial.
 template <int T, int KIND, bool MULTI>
-__device__ __forceinline__ void density64_item(const Atoms &A, const Pot &P, const Box *boxes, long long g) {
+__device__ __forceinline__ void density64_item(const Atoms &A, const Pot &P, const Box *boxes, long long g,
+                                               bool energy = false) {
     const int i = (int)(g / T), lane = (int)(g & (T - 1));
     const bool live = i < A.n;
-    double rho = 0.0;
+    double rho = 0.0, ep = 0.0;
     double4_32a pi = make_double4_32a(0.0, 0.0, 0.0, 0.0);
     int si = 0;
     const bool wrap = needs_image(A, i, live);
@@ -415,7 +418,8 @@ __device__ __forceinline__ void density64_item(const Atoms &A, const Pot &P, con
                     rho += fs_phi<double>(P.fs, P.bd, r);
                     if (keep) {
                         double dV;
-                        fs_V<double>(P.fs, r, dV);
+                        const double V = fs_V<double>(P.fs, r, dV);
+                        if (energy) ep = fma(0.5, V, ep);
                         *drow.ptr(k) = make_double2(dV * rinv, fs_dphi<double>(P.fs, P.bd, r) * rinv);
                     }
                 } else if (KIND == MD_POT_KNOTS) {
@@ -424,7 +428,8 @@ __device__ __forceinline__ void density64_item(const Atoms &A, const Pot &P, con
                     rho += knot_sum<double, double2>(P.K64 + (size_t)(P.ns * P.ns + si * P.ns + sj) * P.nkt, P.nkt, r, d);
                     if (keep) {
                         double dV;
-                        knot_sum<double, double2>(P.K64, P.nkt, r, dV);
+                        const double V = knot_sum<double, double2>(P.K64, P.nkt, r, dV);
+                        if (energy) ep = fma(0.5, V, ep);
                         *drow.ptr(k) = make_double2(dV * rinv, d * rinv);
                     }
                 } else {
@@ -441,6 +446,11 @@ __device__ __forceinline__ void density64_item(const Atoms &A, const Pot &P, con
                         const double dV = below ? dv.x : fma(t, fma(dv.z, t, dv.y), dv.x);
                         const double dphi = below ? dp.x : fma(t, fma(dp.z, t, dp.y), dp.x);
                         *drow.ptr(k) = make_double2(dV * rinv, dphi * rinv);
+                        if (energy) {
+                            const double4_32a cv = P.VP64[ab];
+                            double dd;
+                            ep = fma(0.5, cubic(t, cv.x, cv.y, cv.z, cv.w, below, dd), ep);
+                        }
                     }
                 }
             }
@@ -449,21 +459,22 @@ __device__ __forceinline__ void density64_item(const Atoms &A, const Pot &P, con
         else walk(std::false_type{});
     }
     rho = lane_sum<T>(rho);
+    if (energy) ep = lane_sum<T>(ep);
     if (live && lane == 0) {
         double dF;
         const double F = embed64(P, si, rho, dF, A.flags);
         A.rho[i] = rho;
         A.dF[i] = dF;
-        A.e_atom[i] = F;
+        A.e_atom[i] = F + ep;
         A.p2d[i] = make_double4_32a(pi.x, pi.y, pi.z, dF);
     }
 }
 
 // The FP64 force pass from the derivative cache of the density pass (one species): per entry the
 // separation, then f_i += [V'/r + (F'_i + F'_j) phi'/r] d, the same terms as the full evaluation
-// below in another order of rounding.  With ENERGY the pair energy V(r) and the virial are added
-// (r from the separation), while the force takes the same operations as without, so that a run
-// does not depend on which of its steps evaluate energies.
+// below in another order of rounding.  With ENERGY the virial is added (the pair energies were
+// summed into E_i by the density pass of the same step), while the force takes the same
+// operations as without, so that a run does not depend on which of its steps evaluate energies.
 template <int T, int KIND, bool ENERGY>
 __device__ __forceinline__ int force64_cached_item(const Atoms &A, const Pot &P, const Box *boxes, long long g,
                                                    double half_dt, int motion, double (&part)[kPartials]) {
@@ -492,24 +503,7 @@ __device__ __forceinline__ int force64_cached_item(const Atoms &A, const Pot &P,
                 fx = fma(gr, dx, fx);
                 fy = fma(gr, dy, fy);
                 fz = fma(gr, dz, fz);
-                if (ENERGY) {
-                    const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-                    if (r2 < P.rc2) {
-                        const double r = r2 * rsqrt64(r2);
-                        double V, dV;
-                        if (KIND == MD_POT_FS_ANALYTIC) {
-                            V = fs_V<double>(P.fs, r, dV);
-                        } else if (KIND == MD_POT_KNOTS) {
-                            V = knot_sum<double, double2>(P.K64, P.nkt, r, dV);
-                        } else {
-                            double t;
-                            bool below;
-                            const int kr = knot_row((r - P.r_min) * P.inv_dr, P.nk, t, below);
-                            const double4_32a cv = P.VP64[(size_t)kr * 2];
-                            V = cubic(t, cv.x, cv.y, cv.z, cv.w, below, dV);
-                        }
-                        ep = fma(0.5, V, ep);
-                    }
+                if (ENERGY) {   // the pair energies are in E_i already (density pass)
                     const double hg = -0.5 * gr;
                     wxx = fma(hg * dx, dx, wxx);
                     wyy = fma(hg * dy, dy, wyy);
@@ -670,16 +664,18 @@ __device__ __forceinline__ int force64_item(const Atoms &A, const Pot &P, const 
 // order; the rows are partitioned at every build so that these come first, cup[i] of them),
 // computes the pair term once and adds the neighbour's share to FP64 accumulators with atomic
 // adds (Newton's third law).  The density pass leaves each atom's own share in rho and
-// the neighbours' shares in rho_acc; F(rho) follows in a phase of its own (pairs_embed64) once
-// every share is in, the force pass likewise leaves its own share in force and the others' in
+// the neighbours' shares in rho_acc (on an energy step the pair energies, 1/2 V to each atom, in
+// e_acc); F(rho) follows in a phase of its own (pairs_embed64) once every share is in, the force
+// pass likewise leaves its own share in force and the others' in
 // f_acc, and the kick follows in a phase of its own (pairs_kick64).  The per-entry derivative
 // cache holds the entries j > i only.  The order of the atomic adds, and so the last bits of the
 // sums, varies from run to run.  One species.
 template <int T, int KIND>
-__device__ __forceinline__ void density64_pairs_item(const Atoms &A, const Pot &P, const Box *boxes, long long g) {
+__device__ __forceinline__ void density64_pairs_item(const Atoms &A, const Pot &P, const Box *boxes, long long g,
+                                                     bool energy = false) {
     const int i = (int)(g / T), lane = (int)(g & (T - 1));
     const bool live = i < A.n;
-    double rho = 0.0;
+    double rho = 0.0, ep = 0.0;
     const bool wrap = needs_image(A, i, live);
     if (live) {
         const Box &B = boxes[ph::replica_of(A, i)];
@@ -702,10 +698,10 @@ __device__ __forceinline__ void density64_pairs_item(const Atoms &A, const Pot &
                 }
                 const double rinv = rsqrt64(r2);
                 const double r = r2 * rinv;
-                double phi, dV, dphi;
+                double phi, dV, dphi, V = 0.0;
                 if (KIND == MD_POT_FS_ANALYTIC) {
                     phi = fs_phi<double>(P.fs, P.bd, r);
-                    fs_V<double>(P.fs, r, dV);
+                    V = fs_V<double>(P.fs, r, dV);
                     dphi = fs_dphi<double>(P.fs, P.bd, r);
                 } else {
                     double t, d;
@@ -717,9 +713,17 @@ __device__ __forceinline__ void density64_pairs_item(const Atoms &A, const Pot &
                     const double4_32a dv = P.D64[2 * kr], dp = P.D64[2 * kr + 1];
                     dV = below ? dv.x : fma(t, fma(dv.z, t, dv.y), dv.x);
                     dphi = below ? dp.x : fma(t, fma(dp.z, t, dp.y), dp.x);
+                    if (energy) {
+                        const double4_32a cv = P.VP64[(size_t)kr * 2];
+                        V = cubic(t, cv.x, cv.y, cv.z, cv.w, below, d);
+                    }
                 }
                 rho += phi;
                 atomicAdd(A.rho_acc + j, phi);
+                if (energy) {   // each atom of the pair gets half its pair energy
+                    ep = fma(0.5, V, ep);
+                    atomicAdd(A.e_acc + j, 0.5 * V);
+                }
                 *drow.ptr(k) = make_double2(dV * rinv, dphi * rinv);
             }
         };
@@ -727,7 +731,11 @@ __device__ __forceinline__ void density64_pairs_item(const Atoms &A, const Pot &
         else walk(std::false_type{});
     }
     rho = lane_sum<T>(rho);
-    if (live && lane == 0) A.rho[i] = rho;
+    if (energy) ep = lane_sum<T>(ep);
+    if (live && lane == 0) {
+        A.rho[i] = rho;
+        if (energy) atomicAdd(A.e_acc + i, ep);
+    }
 }
 
 // After the pair density pass, per atom: rho = own share + the neighbours' shares; F, F'; the
@@ -738,7 +746,8 @@ __device__ __forceinline__ void pairs_embed64(const Atoms &A, const Pot &P, int 
     const double F = embed64(P, 0, rho, dF, A.flags);
     A.rho[i] = rho;
     A.dF[i] = dF;
-    A.e_atom[i] = F;
+    A.e_atom[i] = F + A.e_acc[i];   // the pair energies (energy steps; else 0)
+    A.e_acc[i] = 0.0;
     const double4_32a p = A.posd[i];
     A.p2d[i] = make_double4_32a(p.x, p.y, p.z, dF);
     A.rho_acc[i] = 0.0;
@@ -773,25 +782,7 @@ __device__ __forceinline__ void force64_pairs_item(const Atoms &A, const Pot &P,
                 fx += gx;
                 fy += gy;
                 fz += gz;
-                double vj = 0.0;
-                if (ENERGY) {
-                    const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-                    if (r2 < P.rc2) {
-                        const double r = r2 * rsqrt64(r2);
-                        double V, dV;
-                        if (KIND == MD_POT_FS_ANALYTIC) {
-                            V = fs_V<double>(P.fs, r, dV);
-                        } else {
-                            double t;
-                            bool below;
-                            const int kr = knot_row((r - P.r_min) * P.inv_dr, P.nk, t, below);
-                            const double4_32a cv = P.VP64[(size_t)kr * 2];
-                            V = cubic(t, cv.x, cv.y, cv.z, cv.w, below, dV);
-                        }
-                        ep = fma(0.5, V, ep);
-                        vj = 0.5 * V;
-                    }
-                    // the pair's whole virial, once
+                if (ENERGY) {   // the pair's whole virial, once (its energy is in E_i and E_j)
                     wxx = fma(-gx, dx, wxx);
                     wyy = fma(-gy, dy, wyy);
                     wzz = fma(-gz, dz, wzz);
@@ -803,7 +794,6 @@ __device__ __forceinline__ void force64_pairs_item(const Atoms &A, const Pot &P,
                 atomicAdd(acc, -gx);
                 atomicAdd(acc + 1, -gy);
                 atomicAdd(acc + 2, -gz);
-                if (ENERGY) atomicAdd(acc + 3, vj);
             }
         };
         if (wrap) walk(std::true_type{});
@@ -818,7 +808,7 @@ __device__ __forceinline__ void force64_pairs_item(const Atoms &A, const Pot &P,
         wyz = lane_sum<T>(wyz); wxz = lane_sum<T>(wxz); wxy = lane_sum<T>(wxy);
     }
     if (!(live && lane == 0)) return;
-    A.force[i] = make_double4_32a(fx, fy, fz, ep);
+    A.force[i] = make_double4_32a(fx, fy, fz, 0.0);
     if (ENERGY) {
         part[2] += wxx; part[3] += wyy; part[4] += wzz;
         part[5] += wyz; part[6] += wxz; part[7] += wxy;
@@ -837,8 +827,7 @@ __device__ __forceinline__ void pairs_kick64(const Atoms &A, int i, double half_
     double4_32a v = A.vel[i];
     finish_motion(A, i, v, fx, fy, fz, half_dt, motion);
     if (ENERGY) {
-        const double e = A.e_atom[i] + own.w + acc.w;
-        A.e_atom[i] = e;
+        const double e = A.e_atom[i];
         const double m = 1.0 / (kMvv2e * v.w);
         part[0] += e;
         part[1] += m * fma(v.x, v.x, fma(v.y, v.y, v.z * v.z));
@@ -917,10 +906,11 @@ __device__ __forceinline__ df::F2 dcubic_df(df::F2 t, float4 r1, float e3, bool 
 }
 
 template <int T>
-__device__ __forceinline__ void density_df_item(const Atoms &A, const Pot &P, const Box *boxes, long long g) {
+__device__ __forceinline__ void density_df_item(const Atoms &A, const Pot &P, const Box *boxes, long long g,
+                                                bool energy = false) {
     const int i = (int)(g / T), lane = (int)(g & (T - 1));
     const bool live = i < A.n;
-    df::Acc rho_acc{0.f, 0.f};
+    df::Acc rho_acc{0.f, 0.f}, e_acc{0.f, 0.f};
     float4 pih = make_float4(0.f, 0.f, 0.f, 0.f), pil = pih;
     const bool wrap = needs_image(A, i, live);
     if (live) {
@@ -956,19 +946,25 @@ __device__ __forceinline__ void density_df_item(const Atoms &A, const Pot &P, co
                 const df::F2 dV = dcubic_df(t, tx[3], x1.w, below);
                 const df::F2 gV = df::mul(dV, rinv), gP = df::mul(dphi, rinv);
                 *dc = make_float4(gV.h, gV.l, gP.h, gP.l);
+                if (energy) {   // the pair energy 1/2 V(r) into E_i
+                    const float4 v0 = P.TVx[2 * (size_t)kr], v1 = P.TVx[2 * (size_t)kr + 1];
+                    const df::F2 V = cubic_df(t, v0, v1.x, v1.y, below);
+                    df::acc_add(e_acc, df::make(0.5f * V.h, 0.5f * V.l));
+                }
             }
         };
         if (wrap) walk(std::true_type{});
         else walk(std::false_type{});
     }
     const df::F2 rho = df::lane_sum<T>(df::acc_value(rho_acc));
+    const df::F2 ep = energy ? df::lane_sum<T>(df::acc_value(e_acc)) : df::make(0.f);
     if (live && lane == 0) {
         const double rr = df::to_double(rho);
         double dF;
         const double F = embed64(P, 0, rr, dF, A.flags);
         A.rho[i] = rr;
         A.dF[i] = dF;
-        A.e_atom[i] = F;
+        A.e_atom[i] = F + df::to_double(ep);
         const df::F2 f2 = df::from_double(dF);
         A.p2x[2 * (size_t)i] = make_float4(pih.x, pih.y, pih.z, f2.h);
         A.p2x[2 * (size_t)i + 1] = make_float4(pil.x, pil.y, pil.z, f2.l);
@@ -1005,17 +1001,7 @@ __device__ __forceinline__ int force_df_item(const Atoms &A, const Pot &P, const
                 df::acc_add(ax, df::mul(gr, dx));
                 df::acc_add(ay, df::mul(gr, dy));
                 df::acc_add(az, df::mul(gr, dz));
-                if (ENERGY) {
-                    const df::F2 r2 = r2_df(dx, dy, dz);
-                    if (r2.h < P.rc2f) {
-                        df::F2 rinv, r, t;
-                        rinv_df(r2, rinv, r);
-                        bool below;
-                        const int kr = knot_df(P, r, t, below);
-                        const float4 v0 = P.TVx[2 * (size_t)kr], v1 = P.TVx[2 * (size_t)kr + 1];
-                        const df::F2 V = cubic_df(t, v0, v1.x, v1.y, below);
-                        ep = df::add(ep, df::make(0.5f * V.h, 0.5f * V.l));
-                    }
+                if (ENERGY) {   // the virial (the pair energies are in E_i: density pass)
                     const df::F2 hg = df::make(-0.5f * gr.h, -0.5f * gr.l);
                     const df::F2 hx = df::mul(hg, dx), hy = df::mul(hg, dy);
                     wv[0] = df::add(wv[0], df::mul(hx, dx));
@@ -1057,12 +1043,15 @@ __device__ __forceinline__ int force_df_item(const Atoms &A, const Pot &P, const
 }
 
 // Precision-generic front ends.
+// energy: the step's energies are wanted (the FP64 path with the derivative cache and the
+// double-float path sum the pair energies in this pass; the mixed path in the force pass).
 template <int PREC, int T, int KIND, bool MULTI, bool SMT = false>
-__device__ __forceinline__ void density_item(const Atoms &A, const Pot &P, const Box *boxes, long long g) {
+__device__ __forceinline__ void density_item(const Atoms &A, const Pot &P, const Box *boxes, long long g,
+                                             bool energy = false) {
     if constexpr (PREC == MD_PREC_DF) {
-        if constexpr (KIND == MD_POT_TABLES && !MULTI) density_df_item<T>(A, P, boxes, g);
+        if constexpr (KIND == MD_POT_TABLES && !MULTI) density_df_item<T>(A, P, boxes, g, energy);
     } else if constexpr (PREC == MD_PREC_FP64) {
-        density64_item<T, KIND, MULTI>(A, P, boxes, g);
+        density64_item<T, KIND, MULTI>(A, P, boxes, g, energy);
     } else {
         density32_item<T, KIND, MULTI, SMT>(A, P, boxes, g);
     }

@@ -310,12 +310,15 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? (PREC == MD_PREC_DF ? MD_
                 }
             }
         }
+        const bool energy_step = s == sp.n_steps - 1 && sp.energy_last;
         if constexpr (WALK == kWalkPairs) {   // each pair once, then F(rho) once every share is in
-            for (long long g = tid; g < items; g += stride) ps::density64_pairs_item<T, KIND>(A, P, boxes, g);
+            for (long long g = tid; g < items; g += stride)
+                ps::density64_pairs_item<T, KIND>(A, P, boxes, g, energy_step);
             MD_SYNC();
             for (long long i = tid; i < A.n; i += stride) ps::pairs_embed64(A, P, (int)i);
         } else if (!tiled) {
-            for (long long g = tid; g < items; g += stride) ps::density_item<PREC, T, KIND, MULTI, SMT>(A, P, boxes, g);
+            for (long long g = tid; g < items; g += stride)
+                ps::density_item<PREC, T, KIND, MULTI, SMT>(A, P, boxes, g, energy_step);
         }
         MD_SYNC();
         MD_STAMP(10);
