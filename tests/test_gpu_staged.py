@@ -129,6 +129,8 @@ def test_auto_takes_the_list_walk():
 @pytest.mark.parametrize("walk", ["staged", "cells", "half"])
 @pytest.mark.parametrize("precision,name", [("fp64", "cu7"), ("mixed", "fe")])
 def test_group_walk_where_it_does_not_apply_is_an_argument_error(precision, name, walk):
+    if precision == "fp64" and walk == "half":
+        pytest.skip("on the FP64 path 'half' is the half list over the full list (tests/test_gpu_pairs.py)")
     w = _case("cu7") if name == "cu7" else I.bcc_fe(8, seed=3)
     with pytest.raises(md.MDError) as ex:
         md.System(w, precision=precision, passes=walk)
