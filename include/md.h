@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define MD_ABI_VERSION 5
+#define MD_ABI_VERSION 6
 
 typedef struct md_ctx md_ctx; /* opaque, owned by the library */
 
@@ -160,8 +160,11 @@ enum { MD_INTEGRATOR_VERLET = 0, MD_INTEGRATOR_PC3 = 1 };
  * its neighbours' positions through the full Verlet list (§3.2.1) from global memory, and every
  * pair is computed twice (once for each atom: no write conflicts, the symmetric scheme of
  * §3.2.2).  The three group walks take the link cells in groups of consecutive cells along x;
- * one thread block copies a group's neighbourhood (the 3 x 3 x (gx + 2) stencil of cells around
- * it, each periodic image already shifted) into shared memory and walks it there:
+ * a group's neighbourhood (the 3 x 3 x (gx + 2) stencil of cells around it, each periodic image
+ * already shifted) is copied into shared memory and walked there.  In each 1024-thread block one
+ * warp stages the block's next groups with bulk copies into 2 to 4 buffers while the other 31
+ * warps compute the current ones, claiming work a warp at a time; the shared copy of the knot
+ * table then holds only the rows of the pass under way:
  *  - STAGED: the group's atoms read their neighbours through a 16-bit copy of their list rows
  *    (the same entries, as stencil slots).  The list, the pair terms and their order are those
  *    of LIST; the separations are formed from the shifted FP32 positions instead of by the FP32
@@ -186,10 +189,10 @@ enum { MD_INTEGRATOR_VERLET = 0, MD_INTEGRATOR_PC3 = 1 };
  * pair once from those entries and adds the neighbour's share of rho, force and pair energy to
  * FP64 accumulators with atomic adds, and F(rho) and the kick follow in phases of their own.
  * Results equal LIST's to FP64 rounding; the order of the atomic adds, and so the last bits,
- * varies from run to run.  AUTO = LIST (on
- * GB300 every group walk measured slower for fcc Cu with its 5,000-knot table in shared memory:
- * one 1024-thread block per SM stages, then computes); a group walk where it does not apply is
- * MD_ERR_ARG at md_create.
+ * varies from run to run.  AUTO = LIST (on GB300, fcc Cu 500,000 atoms with its 5,000-knot
+ *  table: LIST 0.58 ms per step, STAGED 0.67, HALF 1.40, CELLS 2.75; STAGED's passes take about
+ * as long as LIST's, its list build longer); a group walk where it does not apply is MD_ERR_ARG
+ * at md_create.
  */
 enum { MD_PASSES_AUTO = 0, MD_PASSES_LIST = 1, MD_PASSES_STAGED = 2, MD_PASSES_CELLS = 3, MD_PASSES_HALF = 4 };
 
@@ -198,10 +201,12 @@ typedef struct {
                                 MD_PASSES_HALF (cell groups at every build), else MD_PASSES_LIST */
     int32_t cells_per_group; /* gx */
     int32_t groups;          /* number of cell groups */
-    int32_t capacity;        /* atoms one block can stage */
+    int32_t capacity;        /* atoms one stage buffer holds */
     int32_t last_max;        /* largest group neighbourhood (atoms) at the last list build */
     int32_t active;          /* 1: the next md_step takes the prepared group walk (lanes <= 8, and
                                 every group fitted at the last build) */
+    int32_t stage_buffers;   /* stage buffers per block (2 to 4; 1 where a group fits only once):
+                                the next groups are staged by bulk copies while one is computed */
 } md_passes;
 
 typedef struct {

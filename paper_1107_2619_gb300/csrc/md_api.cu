@@ -690,23 +690,18 @@ md_status create_common(md_ctx *ctx, const md_config *cfg, const md_potential *p
             const int nx = ctx->rc[0].nc[0];
             const double m = (double)n / (double)ncell;
             const size_t dyn_max = walk == kWalkCells ? kSmemDynMaxCells : kSmemDynMax;
-            // a stage slot holds a float4 position, and for the half walk a float4 of sums
+            // a stage slot holds a float4 position, and for the half walk a float4 of sums; as many
+            // stage buffers (up to MD_STAGE_BUFS, 2 for the half walk) as hold a group of at least
+            // one cell
             const size_t slot = sizeof(float4) * (walk == kWalkHalf ? 2 : 1);
-            const int cap = (int)std::min<size_t>((dyn_max - tbytes) / slot, 65535);
-            int best = 0;
-            double best_eff = 0.0;
-            for (int g = 1; g <= std::min(8, nx); g++) {
-                if (9.0 * (g + 2) * m * 1.15 > cap) break;
-                if (walk == kWalkCells) {
-                    best = g;
-                    continue;
-                }
-                const double items = g * m * ctx->lanes;
-                const double eff = items / (std::ceil(items * 1.1 / 1024.0) * 1024.0);
-                if (eff >= 0.98 * best_eff) {
-                    best = g;
-                    best_eff = std::max(eff, best_eff);
-                }
+            int best = 0, cap = 0, nbuf = 0;
+            for (int nb = walk == kWalkHalf ? std::min(2, MD_STAGE_BUFS) : MD_STAGE_BUFS; nb >= 1 && best == 0; nb--) {
+                // the group walks hold one of the table's two row sets at a time
+                cap = (int)std::min<size_t>((dyn_max - (MD_DTABLE ? tbytes / 2 : tbytes)) / (slot * nb), 65535);
+                nbuf = nb;
+                // the widest group whose neighbourhood fits with 15 % to spare
+                for (int g = 1; g <= std::min(kGroupMaxGx, nx); g++)
+                    if (9.0 * (g + 2) * m * 1.15 <= cap) best = g;
             }
             if (best > 0) {
                 C.tile = walk;
@@ -715,6 +710,7 @@ md_status create_common(md_ctx *ctx, const md_config *cfg, const md_potential *p
                 C.n_groups = C.ngx * ctx->rc[0].nc[1] * ctx->rc[0].nc[2];
                 C.st_cells = 9 * (best + 2);
                 C.cap = cap;
+                C.nbuf = nbuf;
                 chk(dalloc(ctx, &C.grp_loc, (size_t)C.n_groups * (C.st_cells + 1)));
                 if (walk == kWalkStaged || walk == kWalkHalf) chk(dalloc(ctx, &A.lnbr, nbr_entries(n, cfg->k_max)));
                 if (walk == kWalkHalf) {
@@ -753,6 +749,7 @@ md_status create_common(md_ctx *ctx, const md_config *cfg, const md_potential *p
     if (pot->kind == MD_POT_TABLES) {
         const int nk = pot->n_knots;
         P.nk = nk;
+        P.smt_phi = nk;
         P.r_min = pot->r_min;
         P.inv_dr = (nk - 1) / (pot->r_cut - pot->r_min);
         P.rho_min = pot->rho_min;
@@ -1663,6 +1660,7 @@ md_status md_get_passes(md_ctx *ctx, md_passes *out) {
     out->capacity = C.tile ? C.cap : 0;
     out->last_max = C.tile ? ctx->h_flags->tile_max : 0;
     out->active = C.tile && ctx->lanes <= 8 && !ctx->h_flags->tile_bad;
+    out->stage_buffers = C.tile ? C.nbuf : 0;
     if (ctx->A.pairs) {   // the FP64 half list over the full list's rows
         out->walk = MD_PASSES_HALF;
         out->active = 1;

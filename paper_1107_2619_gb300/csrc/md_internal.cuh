@@ -62,6 +62,7 @@ struct Flags {
 // one 32-byte load; VP64 = two double4 per interval (V, then phi).
 struct Pot {
     int kind, ns, nk;
+    int smt_phi;   // table copy in shared memory: first phi row (nk; 0 where a pass holds only its own rows)
     double rc2;
     float rc2f;
     double fs[7];   // d, c, A, beta, c0, c1, c2
@@ -222,9 +223,20 @@ struct Cells {
                         // and 16-bit local lists), kWalkCells (groups, no list unless a group overflows),
                         // kWalkHalf (groups, 16-bit half lists, shared-memory accumulation)
     int gx, ngx, n_groups, st_cells;   // cells per group, groups per row, groups, 9 (gx + 2)
-    int cap;            // atoms a block can stage
+    int cap;            // atoms one stage buffer holds
+    int nbuf;           // stage buffers per block (2: the next group is staged while one is computed)
     int32_t *grp_loc;   // [n_groups][st_cells + 1]: staged slot of the first atom of each stencil cell, total
 };
+
+constexpr int kGroupMaxGx = 8;   // cells per group at most (the stencil row is kGroupMaxGx + 2 cells)
+// Stage buffers per block of the group walks at most (fewer where the neighbourhoods do not fit):
+// the staged and cell walks take up to MD_STAGE_BUFS, the half walk (whose per-slot sums double a
+// buffer) up to 2.  Measured on fcc Cu 500,000 atoms: staged 0.75 ms per step with 2 buffers of
+// 8-cell groups, 0.68 ms with 3 of 6 cells, 0.67 ms with 4 of 4 cells; half 1.40 ms with 2 of 4
+// cells, 1.91 ms with 3 of 2.
+#ifndef MD_STAGE_BUFS
+#define MD_STAGE_BUFS 4
+#endif
 
 // Neighbour walks of the step kernel's passes (md_config.passes).
 enum : int { kWalkList = 0, kWalkStaged = 1, kWalkCells = 2, kWalkHalf = 3, kWalkPairs = 4 };

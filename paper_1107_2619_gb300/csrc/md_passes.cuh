@@ -72,7 +72,7 @@ template <bool SMT, bool MULTI>
 __device__ __forceinline__ float4 phi_row(const Pot &P, size_t idx) {
     if (SMT && (!MULTI || idx < (size_t)P.nk)) {
         extern __shared__ float4 sm_table_f4[];
-        return sm_table_f4[P.nk + idx];
+        return sm_table_f4[P.smt_phi + idx];
     }
     return phi_half32(P.VP32, idx);
 }

@@ -152,15 +152,19 @@ template <int PREC, int T, int KIND, bool MULTI, int NT, bool SMT, int WALK>
 __global__ void __launch_bounds__(NT, NT == kThreads ? (PREC == MD_PREC_DF ? MD_STEP_MIN_BLOCKS_DF : MD_STEP_MIN_BLOCKS) : 1)
     k_step(Atoms A, Cells C, Pot P, StepParams sp, GridBarrier *bar, unsigned long long *stamps) {
     __shared__ int ws[32];
-    __shared__ int tile_loc[kGroupWalk<WALK> ? tl::kTileMaxSt + 1 : 1];
+    __shared__ std::conditional_t<kGroupWalk<WALK>, tl::Pipe, int> pipe;   // the group walks' pipeline
     __shared__ uint16_t cells_q[WALK == kWalkCells ? NT / 32 : 1][kCellsQueue];
     extern __shared__ float4 sm_table_f4[];   // [SMT table][stage]
-    float4 *const stage = sm_table_f4 + (SMT ? 2 * P.nk : 0);
-    float4 *const half_acc = stage + (WALK == kWalkHalf ? C.cap : 0);   // half walk: per-slot sums
+    // The group walks' stage needs the room: their shared copy holds only the rows of the pass
+    // under way (the phi rows in the density pass, the derivative rows in the force pass), loaded
+    // at the start of each pass (Pot::smt_phi = 0).
+    constexpr bool kSplitTable = SMT && kGroupWalk<WALK> && !MULTI && MD_DTABLE;
+    float4 *const stage = sm_table_f4 + (SMT ? (kSplitTable ? 1 : 2) * P.nk : 0);
+    float4 *const half_acc = stage + (WALK == kWalkHalf ? (size_t)C.nbuf * C.cap : 0);   // half walk: per-slot sums
     const unsigned nb = gridDim.x;
     const long long tid = (long long)blockIdx.x * NT + threadIdx.x;
     const long long stride = (long long)nb * NT;
-    if (SMT) {
+    if (SMT && !kSplitTable) {
         const float4 *src = reinterpret_cast<const float4 *>(P.VP32);
         if constexpr (!MULTI && MD_DTABLE) {   // derivative rows, then the phi rows
             for (int q = threadIdx.x; q < P.nk; q += NT) {
@@ -172,6 +176,12 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? (PREC == MD_PREC_DF ? MD_
         }
         __syncthreads();
     }
+    if constexpr (kGroupWalk<WALK>) {
+        if (threadIdx.x == 0) tl::pipe_init<NT>(pipe);
+        __syncthreads();
+    }
+    unsigned seq = 0;   // groups this block has taken in this launch: the pipeline's phase count
+    const tl::PassCtl ctl{sp.spin_limit, &bar->abort, A.flags};
     const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
     const bool strain = sp.strain_scale != 1.0;
     Box *boxes = A.boxes;
@@ -279,6 +289,11 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? (PREC == MD_PREC_DF ? MD_
             for (int q = 1; q <= 9; q++) srow[q] = t0;
         }
         // ------------------------------------------------ density pass
+        if constexpr (kSplitTable) {
+            const float4 *src = reinterpret_cast<const float4 *>(P.VP32);
+            for (int q = threadIdx.x; q < P.nk; q += NT) sm_table_f4[q] = __ldg(src + 2 * q + 1);
+            __syncthreads();
+        }
         if (lead && A.flags->need_rebuild) {  // every block has passed the rebuild decision
             A.flags->n_rebuilds++;
             A.flags->need_rebuild = 0;
@@ -287,23 +302,33 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? (PREC == MD_PREC_DF ? MD_
         if constexpr (kGroupWalk<WALK>) tiled = *reinterpret_cast<volatile int32_t *>(&A.flags->tile_bad) == 0;
         if constexpr (kGroupWalk<WALK>) {
             if (tiled) {
-                for (int g = blockIdx.x; g < C.n_groups; g += nb) {
-                    const tl::Group G = tl::stage_group<NT>(C, boxes[0], A.posf, g, stage, tile_loc,
-                                                            WALK == kWalkHalf ? half_acc : nullptr);
-                    if constexpr (WALK == kWalkStaged) {
-                        const int gi = ((G.h1 - G.h0) * T + 31) & ~31;
-                        for (int it = threadIdx.x; it < gi; it += NT)
-                            tl::density_item<T, KIND, SMT>(A, P, stage, G.h1, G.h0 + it / T, it & (T - 1));
-                    } else if constexpr (WALK == kWalkCells) {
-                        tl::density_cells<NT, KIND, SMT>(A, P, stage, tile_loc, C.gx + 2, G, cells_q[threadIdx.x >> 5]);
-                    } else if constexpr (WALK == kWalkHalf) {
-                        const int gi = ((G.h1 - G.h0) * T + 31) & ~31;
-                        for (int it = threadIdx.x; it < gi; it += NT)
-                            tl::density_half_item<T, KIND, SMT>(A, P, stage, half_acc, G.h1, G.h0 + it / T,
-                                                                it & (T - 1));
-                        tl::flush_group<NT, false>(A, C, boxes[0], g, half_acc, tile_loc);
+                if (tl::is_producer<NT>()) {
+                    tl::produce<WALK == kWalkHalf ? 0 : -1>(A, C, boxes[0], A.posf, pipe, stage, half_acc, seq, ctl);
+                } else {
+                    for (unsigned q = seq, qe = seq + tl::block_groups(C); q < qe; q++) {
+                        int b;
+                        if (!tl::acquire(C, pipe, q, ctl, b)) break;
+                        const tl::Group G{pipe.hdr[b][1], pipe.hdr[b][2], pipe.hdr[b][3]};
+                        const float4 *st = stage + (size_t)b * C.cap;
+                        if constexpr (WALK == kWalkCells) {
+                            for (int c = tl::claim(pipe, b, 1); c < G.h1 - G.h0; c = tl::claim(pipe, b, 1))
+                                tl::density_cell_atom<KIND, SMT>(A, P, st, pipe.loc[b], C.gx + 2, G, G.h0 + c,
+                                                                 cells_q[threadIdx.x >> 5]);
+                        } else {
+                            const int gi = ((G.h1 - G.h0) * T + 31) & ~31;
+                            for (int c = tl::claim(pipe, b, 32); c < gi; c = tl::claim(pipe, b, 32)) {
+                                const int it = c + (threadIdx.x & 31);
+                                if constexpr (WALK == kWalkStaged)
+                                    tl::density_item<T, KIND, SMT>(A, P, st, G.h1, G.h0 + it / T, it & (T - 1));
+                                else
+                                    tl::density_half_item<T, KIND, SMT>(A, P, st, half_acc + (size_t)b * C.cap, G.h1,
+                                                                        G.h0 + it / T, it & (T - 1));
+                            }
+                        }
+                        tl::release(pipe, b);
                     }
                 }
+                seq += tl::block_groups(C);
                 if constexpr (WALK == kWalkHalf) {   // F(rho) once every group has added its share
                     MD_SYNC();
                     for (long long i = tid; i < A.n; i += stride) tl::half_embed(A, P, (int)i);
@@ -322,6 +347,10 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? (PREC == MD_PREC_DF ? MD_
         }
         MD_SYNC();
         MD_STAMP(10);
+        if constexpr (kSplitTable) {   // every warp of the block has left the density pass (barrier above)
+            for (int q = threadIdx.x; q < P.nk; q += NT) sm_table_f4[q] = __ldg(P.D32 + q);
+            __syncthreads();
+        }
         // ------------------------------------------------ force pass (+ kicks)
         const bool last = s == sp.n_steps - 1;
         const bool fuse = !last && !strain && !thermo;
@@ -333,26 +362,35 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? (PREC == MD_PREC_DF ? MD_
         if (last && sp.energy_last) {
             if constexpr (kGroupWalk<WALK>) {
                 if (tiled) {
-                    for (int g = blockIdx.x; g < C.n_groups; g += nb) {
-                        const tl::Group G = tl::stage_group<NT>(C, boxes[0], A.p2f, g, stage, tile_loc,
-                                                                WALK == kWalkHalf ? half_acc : nullptr);
-                        if constexpr (WALK == kWalkStaged) {
-                            const int gi = ((G.h1 - G.h0) * T + 31) & ~31;
-                            for (int it = threadIdx.x; it < gi; it += NT)
-                                tl::force_item<T, KIND, true, SMT>(A, P, stage, G.h1, G.h0 + it / T, it & (T - 1),
-                                                                   sp.half_dt, true, part);
-                        } else if constexpr (WALK == kWalkCells) {
-                            tl::force_cells<NT, KIND, true, SMT>(A, P, boxes, stage, tile_loc, C.gx + 2, G,
-                                                                 cells_q[threadIdx.x >> 5], sp.half_dt, sp.dt, sp.lim2,
-                                                                 false, part);
-                        } else if constexpr (WALK == kWalkHalf) {
-                            const int gi = ((G.h1 - G.h0) * T + 31) & ~31;
-                            for (int it = threadIdx.x; it < gi; it += NT)
-                                tl::force_half_item<T, KIND, true, SMT>(A, P, stage, half_acc, G.h1, G.h0 + it / T,
-                                                                        it & (T - 1), part);
-                            tl::flush_group<NT, true>(A, C, boxes[0], g, half_acc, tile_loc);
+                    if (tl::is_producer<NT>()) {
+                        tl::produce<WALK == kWalkHalf ? 1 : -1>(A, C, boxes[0], A.p2f, pipe, stage, half_acc, seq, ctl);
+                    } else {
+                        for (unsigned q = seq, qe = seq + tl::block_groups(C); q < qe; q++) {
+                            int b;
+                            if (!tl::acquire(C, pipe, q, ctl, b)) break;
+                            const tl::Group G{pipe.hdr[b][1], pipe.hdr[b][2], pipe.hdr[b][3]};
+                            const float4 *st = stage + (size_t)b * C.cap;
+                            if constexpr (WALK == kWalkCells) {
+                                for (int c = tl::claim(pipe, b, 1); c < G.h1 - G.h0; c = tl::claim(pipe, b, 1))
+                                    tl::force_cell_atom<KIND, true, SMT>(A, P, boxes, st, pipe.loc[b], C.gx + 2, G,
+                                                                         G.h0 + c, cells_q[threadIdx.x >> 5], sp.half_dt,
+                                                                         sp.dt, sp.lim2, false, part);
+                            } else {
+                                const int gi = ((G.h1 - G.h0) * T + 31) & ~31;
+                                for (int c = tl::claim(pipe, b, 32); c < gi; c = tl::claim(pipe, b, 32)) {
+                                    const int it = c + (threadIdx.x & 31);
+                                    if constexpr (WALK == kWalkStaged)
+                                        tl::force_item<T, KIND, true, SMT>(A, P, st, G.h1, G.h0 + it / T, it & (T - 1),
+                                                                           sp.half_dt, true, part);
+                                    else
+                                        tl::force_half_item<T, KIND, true, SMT>(A, P, st, half_acc + (size_t)b * C.cap,
+                                                                                G.h1, G.h0 + it / T, it & (T - 1), part);
+                                }
+                            }
+                            tl::release(pipe, b);
                         }
                     }
+                    seq += tl::block_groups(C);
                     if constexpr (WALK == kWalkHalf) {   // the kick once every group has added its share
                         MD_SYNC();
                         for (long long i = tid; i < A.n; i += stride) tl::half_kick<true>(A, (int)i, sp.half_dt, part);
@@ -372,29 +410,39 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? (PREC == MD_PREC_DF ? MD_
         } else {
             if constexpr (kGroupWalk<WALK>) {
                 if (tiled) {
-                    for (int g = blockIdx.x; g < C.n_groups; g += nb) {
-                        const tl::Group G = tl::stage_group<NT>(C, boxes[0], A.p2f, g, stage, tile_loc,
-                                                                WALK == kWalkHalf ? half_acc : nullptr);
-                        if constexpr (WALK == kWalkStaged) {
-                            const int gi = ((G.h1 - G.h0) * T + 31) & ~31;
-                            for (int it = threadIdx.x; it < gi; it += NT) {
-                                const int i = tl::force_item<T, KIND, false, SMT>(A, P, stage, G.h1, G.h0 + it / T,
-                                                                                  it & (T - 1), sp.half_dt, true, part);
-                                if (fuse && i >= 0)
-                                    ph::kick_drift(A, boxes, i, sp.half_dt, sp.dt, sp.strain_scale, false, sp.lim2);
+                    if (tl::is_producer<NT>()) {
+                        tl::produce<WALK == kWalkHalf ? 1 : -1>(A, C, boxes[0], A.p2f, pipe, stage, half_acc, seq, ctl);
+                    } else {
+                        for (unsigned q = seq, qe = seq + tl::block_groups(C); q < qe; q++) {
+                            int b;
+                            if (!tl::acquire(C, pipe, q, ctl, b)) break;
+                            const tl::Group G{pipe.hdr[b][1], pipe.hdr[b][2], pipe.hdr[b][3]};
+                            const float4 *st = stage + (size_t)b * C.cap;
+                            if constexpr (WALK == kWalkCells) {
+                                for (int c = tl::claim(pipe, b, 1); c < G.h1 - G.h0; c = tl::claim(pipe, b, 1))
+                                    tl::force_cell_atom<KIND, false, SMT>(A, P, boxes, st, pipe.loc[b], C.gx + 2, G,
+                                                                         G.h0 + c, cells_q[threadIdx.x >> 5], sp.half_dt,
+                                                                         sp.dt, sp.lim2, fuse, part);
+                            } else {
+                                const int gi = ((G.h1 - G.h0) * T + 31) & ~31;
+                                for (int c = tl::claim(pipe, b, 32); c < gi; c = tl::claim(pipe, b, 32)) {
+                                    const int it = c + (threadIdx.x & 31);
+                                    if constexpr (WALK == kWalkStaged) {
+                                        const int i = tl::force_item<T, KIND, false, SMT>(
+                                            A, P, st, G.h1, G.h0 + it / T, it & (T - 1), sp.half_dt, true, part);
+                                        if (fuse && i >= 0)
+                                            ph::kick_drift(A, boxes, i, sp.half_dt, sp.dt, sp.strain_scale, false,
+                                                           sp.lim2);
+                                    } else {
+                                        tl::force_half_item<T, KIND, false, SMT>(A, P, st, half_acc + (size_t)b * C.cap,
+                                                                                 G.h1, G.h0 + it / T, it & (T - 1), part);
+                                    }
+                                }
                             }
-                        } else if constexpr (WALK == kWalkCells) {
-                            tl::force_cells<NT, KIND, false, SMT>(A, P, boxes, stage, tile_loc, C.gx + 2, G,
-                                                                  cells_q[threadIdx.x >> 5], sp.half_dt, sp.dt, sp.lim2,
-                                                                  fuse, part);
-                        } else if constexpr (WALK == kWalkHalf) {
-                            const int gi = ((G.h1 - G.h0) * T + 31) & ~31;
-                            for (int it = threadIdx.x; it < gi; it += NT)
-                                tl::force_half_item<T, KIND, false, SMT>(A, P, stage, half_acc, G.h1, G.h0 + it / T,
-                                                                         it & (T - 1), part);
-                            tl::flush_group<NT, true>(A, C, boxes[0], g, half_acc, tile_loc);
+                            tl::release(pipe, b);
                         }
                     }
+                    seq += tl::block_groups(C);
                     if constexpr (WALK == kWalkHalf) {   // the kicks once every group has added its share
                         MD_SYNC();
                         for (long long i = tid; i < A.n; i += stride) {
@@ -472,8 +520,9 @@ cudaError_t launch_t(const Atoms &A, const Cells &C, const Pot &P, const StepPar
     static size_t per_sm_dyn = 0;
     static bool attr = false;
     const size_t dyn_max = WALK == kWalkCells ? kSmemDynMaxCells : kSmemDynMax;
-    const size_t dyn = (SMT ? (size_t)P.nk * 32 : 0) +
-                       (kGroupWalk<WALK> ? (size_t)C.cap * sizeof(float4) * (WALK == kWalkHalf ? 2 : 1) : 0);
+    constexpr bool kSplitTable = SMT && kGroupWalk<WALK> && !MULTI && MD_DTABLE;
+    const size_t dyn = (SMT ? (size_t)P.nk * (kSplitTable ? 16 : 32) : 0) +
+                       (kGroupWalk<WALK> ? (size_t)C.nbuf * C.cap * sizeof(float4) * (WALK == kWalkHalf ? 2 : 1) : 0);
     if (dyn > dyn_max) return cudaErrorInvalidConfiguration;
     if ((SMT || kGroupWalk<WALK>) && !attr) {  // opt in to a large dynamic shared-memory carve-out (once)
         cudaError_t e = cudaFuncSetAttribute(k_step<PREC, T, KIND, MULTI, NT, SMT, WALK>,
@@ -502,6 +551,7 @@ cudaError_t launch_t(const Atoms &A, const Cells &C, const Pot &P, const StepPar
     Atoms a = A;
     Cells c = C;
     Pot p = P;
+    if (kSplitTable) p.smt_phi = 0;
     StepParams q = sp;
     void *args[] = {&a, &c, &p, &q, &bar, &stamps};
     return cudaLaunchCooperativeKernel((const void *)k_step<PREC, T, KIND, MULTI, NT, SMT, WALK>, dim3(grid), dim3(NT),

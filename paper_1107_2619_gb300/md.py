@@ -66,7 +66,8 @@ WALKS = {v: k for k, v in PASSES.items()}
 
 class md_passes(C.Structure):
     _fields_ = [("walk", C.c_int32), ("cells_per_group", C.c_int32), ("groups", C.c_int32),
-                ("capacity", C.c_int32), ("last_max", C.c_int32), ("active", C.c_int32)]
+                ("capacity", C.c_int32), ("last_max", C.c_int32), ("active", C.c_int32),
+                ("stage_buffers", C.c_int32)]
 
 
 class md_surrogate(C.Structure):
@@ -529,8 +530,9 @@ class System:
 
     def passes(self) -> dict:
         """The step kernel's neighbour walk: walk ("list", "staged", "cells" or "half": the walk prepared),
-        cells_per_group, groups, capacity, last_max (largest group neighbourhood at the last
-        build), active (the next md_step walks the prepared groups)."""
+        cells_per_group, groups, capacity (atoms per stage buffer), last_max (largest group
+        neighbourhood at the last build), active (the next md_step walks the prepared groups),
+        stage_buffers (2 to 4: the next groups are staged while one is computed)."""
         return md_get_passes(self.ctx)
 
     def set_state(self, pos=None, vel=None, force=None):

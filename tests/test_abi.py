@@ -62,7 +62,7 @@ int main(void) {
 
 
 def test_status_strings(libmd):
-    assert libmd.md_abi_version() == 5
+    assert libmd.md_abi_version() == 6
     assert md.status_string(md.MD_ERR_NBR_OVERFLOW) == "neighbour list overflow"
     assert md.status_string(md.MD_ERR_SPECIES) == "unsupported species"
 

@@ -15,7 +15,8 @@ candidate ranges and the group slot tables.
 
 Workloads: fcc Cu (Sutton-Chen knot tables, 5,000 knots, held in shared memory) with Gaussian
 displacements, on 3 x 3 x 3 link cells (stencils that wrap onto the same cell twice), 4^3 cells,
-and a non-cubic 6 x 3 x 4 grid (a shorter last group in a row for most group lengths).
+a non-cubic 6 x 3 x 4 grid, and the same grid with half the sites empty (about 26 atoms per
+cell, so that groups span several cells and the last group of a row is shorter).
 """
 import numpy as np
 import pytest
@@ -54,12 +55,17 @@ def _case(name):
         vel = I.maxwell_boltzmann(w.potential.masses[sp], 300.0, 23)
         return I.Workload(name="fcc Cu 13x8x9", pos=pos, vel=vel, species=sp, box=box, potential=w.potential,
                           skin=w.skin, k_max=w.k_max, dt_fs=w.dt_fs, steps=1, temperature=300.0)
+    if name == "cu_dilute":   # every other atom removed at random: about 26 atoms per cell
+        w = _case("cu_rect")
+        keep = np.sort(np.random.default_rng(25).permutation(w.n_atoms)[: w.n_atoms // 2])
+        return I.Workload(**{**w.__dict__, "name": "fcc Cu 13x8x9, half the sites empty", "pos": w.pos[keep],
+                             "vel": w.vel[keep], "species": w.species[keep]})
     raise ValueError(name)
 
 
 @pytest.mark.parametrize("walk,lanes", [("staged", 1), ("staged", 2), ("staged", 4), ("staged", 8),
                                         ("cells", 1), ("cells", 4), ("half", 1), ("half", 4), ("half", 8)])
-@pytest.mark.parametrize("case", ["cu7", "cu10", "cu_rect"])
+@pytest.mark.parametrize("case", ["cu7", "cu10", "cu_rect", "cu_dilute"])
 def test_group_walk_steps_match_the_oracle(case, walk, lanes):
     w = _case(case)
     n_steps = 12
@@ -68,6 +74,10 @@ def test_group_walk_steps_match_the_oracle(case, walk, lanes):
     with md.System(w, precision="mixed", lanes_per_atom=lanes, passes=walk) as s:
         p = s.passes()
         assert p["walk"] == walk and p["groups"] > 0 and 1 <= p["cells_per_group"] <= 8
+        # at least two stage buffers (the next group staged by bulk copies while one is computed)
+        assert p["stage_buffers"] >= 2
+        if case == "cu_dilute" and walk != "half":
+            assert p["cells_per_group"] >= 4   # groups of several cells, the row's last one shorter
         s.step(n_steps)
         p = s.passes()
         assert p["active"] == 1 and 0 < p["last_max"] <= p["capacity"]
