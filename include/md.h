@@ -190,7 +190,7 @@ enum { MD_INTEGRATOR_VERLET = 0, MD_INTEGRATOR_PC3 = 1 };
  * FP64 accumulators with atomic adds, and F(rho) and the kick follow in phases of their own.
  * Results equal LIST's to FP64 rounding; the order of the atomic adds, and so the last bits,
  * varies from run to run.  AUTO = LIST (on GB300, fcc Cu 500,000 atoms with its 5,000-knot
- *  table: LIST 0.58 ms per step, STAGED 0.67, HALF 1.40, CELLS 2.75; STAGED's passes take about
+ * table: LIST 0.58 ms per step, STAGED 0.67, HALF 1.40, CELLS 2.75; STAGED's passes take about
  * as long as LIST's, its list build longer); a group walk where it does not apply is MD_ERR_ARG
  * at md_create.
  */

@@ -1365,7 +1365,8 @@ md_status step_impl(md_ctx *ctx, int32_t n_steps, const StateOut *out) {
     }
     if (stamps) collect_stamps(ctx, n_steps);
     ctx->forces_valid = ctx->energy_valid = true;
-    ctx->list_valid = ctx->C.tile != kWalkCells;   // a cell-walk rebuild leaves the list behind
+    // a rebuild inside a group walk's step kernel writes the local rows only (the cell walk no list)
+    ctx->list_valid = ctx->C.tile == kWalkList;
     return MD_OK;
 }
 

@@ -480,10 +480,12 @@ __device__ __forceinline__ void for_stencil(const Cells &C, const RepCells &g, i
 // LOCAL (group walks, one system, reach 1): 1, every entry is also written to the 16-bit local
 // list as the slot of the candidate in its cell group's stage (grp_loc of the stencil cell plus
 // the candidate's rank inside its cell); 2, only the entries j > i are, as the half row of the
-// half walk (lcount of them).  Those builds keep one lane per atom.
+// half walk (lcount of them).  Those builds keep one lane per atom, and write the global rows
+// (A.nbr) only when `rows` is set (the counts always): the step kernel's group walks read the
+// local rows alone while every group fits its stage.
 template <int G, int LOCAL>
 __device__ __forceinline__ int build_cell_group(const Atoms &A, const Cells &C, const Box *boxes, int c, int gl,
-                                                double rl2, float band_lo, float band_hi) {
+                                                double rl2, float band_lo, float band_hi, bool rows = true) {
     const int s = C.cell_start[c], e = C.cell_start[c + 1];
     if (s == e) return 0;
     const int r = replica_of(A, s);
@@ -561,7 +563,7 @@ __device__ __forceinline__ int build_cell_group(const Atoms &A, const Cells &C, 
                 const bool in = r2 < band_lo || within_exact_band(A.pos, ii, j, B, rl2);
                 if (in && act && j != i) {
                     if (cnt < kmax) {
-                        *wp = j;
+                        if (LOCAL == 0 || rows) *wp = j;
                         if constexpr (LOCAL == 1) *lwp = (uint16_t)(lbase + (j - js));
                         if constexpr (LOCAL == 2) {
                             if (j > i) {
@@ -638,23 +640,26 @@ __device__ __forceinline__ int build_cell_group(const Atoms &A, const Cells &C, 
 // lane returns the longest row it built (all 32 lanes of a warp take part in every iteration).
 template <int G, int LOCAL>
 __device__ __forceinline__ int build_cells(const Atoms &A, const Cells &C, const Box *boxes, long long warp,
-                                           long long nwarps, int lane, double rl2, float band_lo, float band_hi) {
+                                           long long nwarps, int lane, double rl2, float band_lo, float band_hi,
+                                           bool rows = true) {
     constexpr int CPW = 32 / G;   // cells per warp
     int m = 0;
     for (long long c0 = warp * CPW; c0 < C.ncell; c0 += nwarps * CPW) {
         const long long c = c0 + lane / G;
-        if (c < C.ncell) m = max(m, build_cell_group<G, LOCAL>(A, C, boxes, (int)c, lane & (G - 1), rl2, band_lo, band_hi));
+        if (c < C.ncell)
+            m = max(m, build_cell_group<G, LOCAL>(A, C, boxes, (int)c, lane & (G - 1), rl2, band_lo, band_hi, rows));
     }
     return m;
 }
 
 template <int LOCAL>
 __device__ __forceinline__ int build_cells_any(int G, const Atoms &A, const Cells &C, const Box *boxes, long long warp,
-                                               long long nwarps, int lane, double rl2, float band_lo, float band_hi) {
-    if (G == 4) return build_cells<4, LOCAL>(A, C, boxes, warp, nwarps, lane, rl2, band_lo, band_hi);
-    if (G == 8) return build_cells<8, LOCAL>(A, C, boxes, warp, nwarps, lane, rl2, band_lo, band_hi);
-    if (G == 16) return build_cells<16, LOCAL>(A, C, boxes, warp, nwarps, lane, rl2, band_lo, band_hi);
-    return build_cells<32, LOCAL>(A, C, boxes, warp, nwarps, lane, rl2, band_lo, band_hi);
+                                               long long nwarps, int lane, double rl2, float band_lo, float band_hi,
+                                               bool rows = true) {
+    if (G == 4) return build_cells<4, LOCAL>(A, C, boxes, warp, nwarps, lane, rl2, band_lo, band_hi, rows);
+    if (G == 8) return build_cells<8, LOCAL>(A, C, boxes, warp, nwarps, lane, rl2, band_lo, band_hi, rows);
+    if (G == 16) return build_cells<16, LOCAL>(A, C, boxes, warp, nwarps, lane, rl2, band_lo, band_hi, rows);
+    return build_cells<32, LOCAL>(A, C, boxes, warp, nwarps, lane, rl2, band_lo, band_hi, rows);
 }
 
 }  // namespace ph

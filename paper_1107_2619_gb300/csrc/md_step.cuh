@@ -272,9 +272,12 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? (PREC == MD_PREC_DF ? MD_
             for (long long k = tid; k < A.n; k += stride) ph::copyback_atom(A, boxes, (int)k);
             MD_SYNC();
             MD_STAMP(8);
-            if (WALK != kWalkCells || *reinterpret_cast<volatile int32_t *>(&A.flags->tile_bad)) {
-                int m = ph::build_cells_any<WALK == kWalkStaged ? 1 : (WALK == kWalkHalf ? 2 : 0)>(sp.list_group, A, C, boxes, tid >> 5, stride >> 5,
-                                                                 threadIdx.x & 31, sp.rl2, sp.band_lo, sp.band_hi);
+            // the group walks need the global rows only when some group does not fit its stage
+            const bool rows = !kGroupWalk<WALK> || *reinterpret_cast<volatile int32_t *>(&A.flags->tile_bad);
+            if (WALK != kWalkCells || rows) {
+                int m = ph::build_cells_any<WALK == kWalkStaged ? 1 : (WALK == kWalkHalf ? 2 : 0)>(
+                    sp.list_group, A, C, boxes, tid >> 5, stride >> 5, threadIdx.x & 31, sp.rl2, sp.band_lo, sp.band_hi,
+                    rows);
                 m = __reduce_max_sync(0xffffffffu, m);
                 if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(&A.flags->max_count, m);
             }

@@ -91,8 +91,9 @@ def test_group_walk_steps_match_the_oracle(case, walk, lanes):
 @pytest.mark.parametrize("walk", ["staged", "cells", "half"])
 def test_group_walk_rebuild_phases_inside_the_step_kernel(walk):
     """Rebuilds every 3 steps: the group slot tables (and local lists) of the step kernel's own
-    rebuild phases, then steps that use them; after the cell walk's list-free rebuilds the list
-    is built again, at the current positions, when it is asked for."""
+    rebuild phases, then steps that use them; those rebuilds write no global list rows (the cell
+    walk no list at all), so the list is built again, at the current positions, when it is asked
+    for."""
     w = _case("cu10")
     ref = oracle.run_vv(w.pos, w.vel, w.species, w.potential.masses, w.box, w.potential, w.dt_fs, 14,
                         w.skin, w.k_max, rebuild_every=3)
@@ -105,9 +106,8 @@ def test_group_walk_rebuild_phases_inside_the_step_kernel(walk):
     assert e["n_rebuilds"] >= 4
     assert np.abs(pos - ref["pos"]).max() < 1e-5
     assert_mixed_forces(w, pos, f, img)
-    if walk == "cells":   # the list asked for after list-free steps is built at the current positions
-        ref_counts = oracle.neighbours(pos, w.box, w.potential.r_cut + w.skin, w.k_max, "brute")[0]
-        assert np.array_equal(counts, ref_counts)
+    ref_counts = oracle.neighbours(pos, w.box, w.potential.r_cut + w.skin, w.k_max, "brute")[0]
+    assert np.array_equal(counts, ref_counts)
 
 
 @pytest.mark.parametrize("walk", ["staged", "cells", "half"])
