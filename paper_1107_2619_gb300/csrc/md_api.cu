@@ -667,7 +667,9 @@ md_status create_common(md_ctx *ctx, const md_config *cfg, const md_potential *p
                 return MD_ERR_ARG;
             }
             A.pairs = 1;
+            A.pair_rc2f = (float)(pot->r_cut * pot->r_cut);
             chk(dalloc(ctx, &A.cup, n));
+            chk(dalloc(ctx, &A.cin, n));
             chk(dalloc(ctx, &A.rho_acc, n));
             chk(dalloc(ctx, &A.f_acc, n));
             chk(dalloc(ctx, &A.e_acc, n));

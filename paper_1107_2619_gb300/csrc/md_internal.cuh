@@ -147,7 +147,10 @@ struct Atoms {
                                              // only the entries j > i, lcount of them
     int32_t *lcount;                         // half walk: entries of each half row
     int32_t *cup;                            // FP64 pair walk: entries j > i at the front of each row
+    int32_t *cin;                            // FP64 pair walk: of those, the ones inside r_cut at the
+                                             // build, at the very front
     int pairs;                               // 1: the FP64 pair walk (kWalkPairs)
+    float pair_rc2f;                         // FP64 pair walk: r_cut^2 (the build's FP32 ordering)
     double *rho_acc;                         // half walk: density accumulators [n]
     double *e_acc;                           // FP64 pair walk: pair-energy accumulators [n]
     double4_32a *f_acc;                      // half walk: force (x, y, z) and pair-energy (w) accumulators

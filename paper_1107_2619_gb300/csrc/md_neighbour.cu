@@ -133,7 +133,7 @@ cudaError_t launch_clear_rebuild(Flags *f, cudaStream_t s) {
 // FP64 pair walk: each row's entries j > i first (one warp per atom).
 __global__ void k_partition_rows(Atoms A) {
     const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (w < A.n) ph::partition_row_warp(A, (int)w, threadIdx.x & 31);
+    if (w < A.n) ph::partition_row_warp(A, A.boxes, (int)w, threadIdx.x & 31);
 }
 
 cudaError_t launch_rebuild(const Atoms &A, const Cells &C, double rl2, float band_lo, float band_hi,

@@ -771,9 +771,11 @@ __device__ __forceinline__ void force64_pairs_item(const Atoms &A, const Pot &P,
         auto walk = [&](auto wrapt) {
             using W = decltype(wrapt);
             for (int k = lane; k < cnt; k += T) {
+                const double2 e = ld_phase(drow.ptr(k));
+                // beyond r_cut (the row's skin entries, at its end): nothing to add
+                if ((__double_as_longlong(e.x) | __double_as_longlong(e.y)) == 0) continue;
                 const int j = ld_phase(row.ptr(k));
                 const double4_32a pj = ld_phase(A.p2d + j);
-                const double2 e = ld_phase(drow.ptr(k));
                 const double dx = sep64<W>(pj.x - pi.x, B.L[0], B.invL[0]);
                 const double dy = sep64<W>(pj.y - pi.y, B.L[1], B.invL[1]);
                 const double dz = sep64<W>(pj.z - pi.z, B.L[2], B.invL[2]);
@@ -813,6 +815,258 @@ __device__ __forceinline__ void force64_pairs_item(const Atoms &A, const Pot &P,
         part[2] += wxx; part[3] += wyy; part[4] += wzz;
         part[5] += wyz; part[6] += wxz; part[7] += wxy;
     }
+}
+
+// ---- the pair walk with the warp's rows flattened (T >= 8 lanes per atom)
+// The AW = 32 / T atoms of a warp are walked as one sequence of entries, so that every lane has an
+// entry in every round but the last: first the entries j > i that lay inside r_cut at the build
+// (cin[i] of them, at the front of each row), then the rest of the entries j > i (the skin at the
+// build; their pair terms run only where the pair has since come inside r_cut).  Entry e of a
+// segment belongs to atom a with off[a] <= e < off[a + 1].  A lane's entries belong to atoms in
+// ascending order, so it keeps one running sum per quantity and adds it to its own slot of the
+// warp's shared sums S[q][a][lane] when the atom changes; the T lanes of each atom then add the
+// 32 slots of that atom (and the butterfly of the per-atom walk).  S: this warp's
+// kPairSlots(AW) doubles.
+template <int AW>
+struct FlatRows {
+    int off[AW + 1];   // prefix counts of the segment's entries (the same in every lane)
+    int lo[AW];        // first row entry of each atom's segment
+    // Atom a (0 .. AW-1) of entry e, and the row entry k of e.
+    __device__ __forceinline__ int atom(int e, int &k) const {
+        int a = 0, base = 0, l = lo[0];
+#pragma unroll
+        for (int b = 1; b < AW; b++)
+            if (e >= off[b]) {
+                a = b;
+                base = off[b];
+                l = lo[b];
+            }
+        k = l + (e - base);
+        return a;
+    }
+};
+
+// Segment seg (0: [0, cin), 1: [cin, cup)) of the rows of the warp's atoms; c_in, c_up: atom
+// i0 + lane's counts in lanes < AW (every lane calls).
+template <int AW>
+__device__ __forceinline__ FlatRows<AW> flat_rows(int c_in, int c_up, int seg) {
+    FlatRows<AW> R;
+    R.off[0] = 0;
+#pragma unroll
+    for (int b = 0; b < AW; b++) {
+        const int ci = __shfl_sync(0xffffffffu, c_in, b), cu = __shfl_sync(0xffffffffu, c_up, b);
+        R.lo[b] = seg == 0 ? 0 : ci;
+        R.off[b + 1] = R.off[b] + (seg == 0 ? ci : cu - ci);
+    }
+    return R;
+}
+
+__host__ __device__ constexpr int kPairSlots(int aw) { return 3 * aw * 32; }
+
+// Atom a's sum of slot row q over the warp's 32 lanes, in the T lanes of atom a (butterfly).
+template <int T>
+__device__ __forceinline__ double flat_sum(const double *S, int q) {
+    constexpr int AW = 32 / T;
+    const int lane = threadIdx.x & 31, a = lane / T, l = lane & (T - 1);
+    double x = 0.0;
+#pragma unroll
+    for (int m = 0; m < 32 / T; m++) x += S[(q * AW + a) * 32 + l + T * m];
+    return lane_sum<T>(x);
+}
+
+template <int T, int KIND>
+__device__ __forceinline__ void density64_pairs_flat(const Atoms &A, const Pot &P, const Box *boxes, long long g,
+                                                     bool energy, double *S) {
+    constexpr int AW = 32 / T;
+    const int lane = (int)(g & 31);
+    const int i0 = (int)(g >> 5) * AW;   // the warp's first atom
+    const int me = i0 + lane / T;        // the atom whose sums this lane finishes
+    const bool wrap = needs_image(A, me, me < A.n);
+    int c_in = 0, c_up = 0;
+    if (lane < AW && i0 + lane < A.n) {
+        c_in = ld_phase(A.cin + i0 + lane);
+        c_up = ld_phase(A.cup + i0 + lane);
+    }
+#pragma unroll
+    for (int q = 0; q < 2 * AW; q++) S[q * 32 + lane] = 0.0;
+    auto walk = [&](auto wrapt) {
+        using W = decltype(wrapt);
+        for (int seg = 0; seg < 2; seg++) {
+            const FlatRows<AW> R = flat_rows<AW>(c_in, c_up, seg);
+            int cur = -1;
+            double rho = 0.0, ep = 0.0;
+            for (int e = lane; e < R.off[AW]; e += 32) {
+                int k;
+                const int a = R.atom(e, k);
+                if (a != cur) {
+                    if (cur >= 0) {
+                        S[cur * 32 + lane] += rho;
+                        S[(AW + cur) * 32 + lane] += ep;
+                    }
+                    cur = a;
+                    rho = ep = 0.0;
+                }
+                const int i = i0 + a;
+                const int j = ld_phase(nbr_row(A, i).ptr(k));
+                const double4_32a pi = ld_phase(A.posd + i), pj = ld_phase(A.posd + j);
+                double dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+                if (W::value) {
+                    const Box &B = boxes[ph::replica_of(A, i)];
+                    dx = mi64(dx, B.L[0], B.invL[0]);
+                    dy = mi64(dy, B.L[1], B.invL[1]);
+                    dz = mi64(dz, B.L[2], B.invL[2]);
+                }
+                const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+                double2 *dc = dcache_row(A, i).ptr(k);
+                if (!(r2 < P.rc2)) {
+                    *dc = make_double2(0.0, 0.0);
+                    continue;
+                }
+                const double rinv = rsqrt64(r2);
+                const double r = r2 * rinv;
+                double phi, dV, dphi, V = 0.0;
+                if (KIND == MD_POT_FS_ANALYTIC) {
+                    phi = fs_phi<double>(P.fs, P.bd, r);
+                    V = fs_V<double>(P.fs, r, dV);
+                    dphi = fs_dphi<double>(P.fs, P.bd, r);
+                } else {
+                    double t, d;
+                    bool below;
+                    const int kr = knot_row((r - P.r_min) * P.inv_dr, P.nk, t, below);
+                    if (below) atomicAdd(&A.flags->range_violations, 1ull);
+                    const double4_32a c = P.VP64[(size_t)kr * 2 + 1];
+                    phi = cubic(t, c.x, c.y, c.z, c.w, below, d);
+                    const double4_32a dv = P.D64[2 * kr], dp = P.D64[2 * kr + 1];
+                    dV = below ? dv.x : fma(t, fma(dv.z, t, dv.y), dv.x);
+                    dphi = below ? dp.x : fma(t, fma(dp.z, t, dp.y), dp.x);
+                    if (energy) {
+                        const double4_32a cv = P.VP64[(size_t)kr * 2];
+                        V = cubic(t, cv.x, cv.y, cv.z, cv.w, below, d);
+                    }
+                }
+                rho += phi;
+                atomicAdd(A.rho_acc + j, phi);
+                if (energy) {   // each atom of the pair gets half its pair energy
+                    ep = fma(0.5, V, ep);
+                    atomicAdd(A.e_acc + j, 0.5 * V);
+                }
+                *dc = make_double2(dV * rinv, dphi * rinv);
+            }
+            if (cur >= 0) {
+                S[cur * 32 + lane] += rho;
+                S[(AW + cur) * 32 + lane] += ep;
+            }
+        }
+    };
+    if (wrap) walk(std::true_type{});
+    else walk(std::false_type{});
+    __syncwarp();
+    const double rho = flat_sum<T>(S, 0);
+    const double ep = energy ? flat_sum<T>(S, 1) : 0.0;
+    __syncwarp();   // S is free for the next item of this warp
+    if (me < A.n && (lane & (T - 1)) == 0) {
+        A.rho[me] = rho;
+        if (energy) atomicAdd(A.e_acc + me, ep);
+    }
+}
+
+template <int T, int KIND, bool ENERGY>
+__device__ __forceinline__ void force64_pairs_flat(const Atoms &A, const Pot &P, const Box *boxes, long long g,
+                                                   double (&part)[kPartials], double *S) {
+    constexpr int AW = 32 / T;
+    const int lane = (int)(g & 31);
+    const int i0 = (int)(g >> 5) * AW;
+    const int me = i0 + lane / T;
+    const bool wrap = needs_image(A, me, me < A.n);
+    int c_in = 0, c_up = 0;
+    if (lane < AW && i0 + lane < A.n) {
+        c_in = ld_phase(A.cin + i0 + lane);
+        c_up = ld_phase(A.cup + i0 + lane);
+    }
+#pragma unroll
+    for (int q = 0; q < 3 * AW; q++) S[q * 32 + lane] = 0.0;
+    double wxx = 0.0, wyy = 0.0, wzz = 0.0, wyz = 0.0, wxz = 0.0, wxy = 0.0;
+    auto walk = [&](auto wrapt) {
+        using W = decltype(wrapt);
+        for (int seg = 0; seg < 2; seg++) {
+            const FlatRows<AW> R = flat_rows<AW>(c_in, c_up, seg);
+            int cur = -1;
+            double fx = 0.0, fy = 0.0, fz = 0.0;
+            for (int e = lane; e < R.off[AW]; e += 32) {
+                int k;
+                const int a = R.atom(e, k);
+                const int i = i0 + a;
+                const double2 d = ld_phase(dcache_row(A, i).ptr(k));
+                // beyond r_cut: nothing to add
+                if ((__double_as_longlong(d.x) | __double_as_longlong(d.y)) == 0) continue;
+                if (a != cur) {
+                    if (cur >= 0) {
+                        S[cur * 32 + lane] += fx;
+                        S[(AW + cur) * 32 + lane] += fy;
+                        S[(2 * AW + cur) * 32 + lane] += fz;
+                    }
+                    cur = a;
+                    fx = fy = fz = 0.0;
+                }
+                const int j = ld_phase(nbr_row(A, i).ptr(k));
+                const double4_32a pi = ld_phase(A.p2d + i), pj = ld_phase(A.p2d + j);
+                double dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+                if (W::value) {
+                    const Box &B = boxes[ph::replica_of(A, i)];
+                    dx = mi64(dx, B.L[0], B.invL[0]);
+                    dy = mi64(dy, B.L[1], B.invL[1]);
+                    dz = mi64(dz, B.L[2], B.invL[2]);
+                }
+                const double gr = fma(pi.w + pj.w, d.y, d.x);
+                const double gx = gr * dx, gy = gr * dy, gz = gr * dz;
+                fx += gx;
+                fy += gy;
+                fz += gz;
+                if (ENERGY) {   // the pair's whole virial, once (its energy is in E_i and E_j)
+                    wxx = fma(-gx, dx, wxx);
+                    wyy = fma(-gy, dy, wyy);
+                    wzz = fma(-gz, dz, wzz);
+                    wyz = fma(-gy, dz, wyz);
+                    wxz = fma(-gx, dz, wxz);
+                    wxy = fma(-gx, dy, wxy);
+                }
+                double *acc = reinterpret_cast<double *>(A.f_acc + j);
+                atomicAdd(acc, -gx);
+                atomicAdd(acc + 1, -gy);
+                atomicAdd(acc + 2, -gz);
+            }
+            if (cur >= 0) {
+                S[cur * 32 + lane] += fx;
+                S[(AW + cur) * 32 + lane] += fy;
+                S[(2 * AW + cur) * 32 + lane] += fz;
+            }
+        }
+    };
+    if (wrap) walk(std::true_type{});
+    else walk(std::false_type{});
+    if (ENERGY) {
+        part[2] += wxx; part[3] += wyy; part[4] += wzz;
+        part[5] += wyz; part[6] += wxz; part[7] += wxy;
+    }
+    __syncwarp();
+    const double fx = flat_sum<T>(S, 0), fy = flat_sum<T>(S, 1), fz = flat_sum<T>(S, 2);
+    __syncwarp();
+    if (me < A.n && (lane & (T - 1)) == 0) A.force[me] = make_double4_32a(fx, fy, fz, 0.0);
+}
+
+// The pair walk's passes: the flattened rows for T >= 8 lanes per atom (S: this warp's
+// kPairSlots(32 / T) doubles of shared memory), the per-atom rows otherwise.
+template <int T, int KIND>
+__device__ __forceinline__ void density64_pairs(const Atoms &A, const Pot &P, const Box *boxes, long long g,
+                                                bool energy, double *S) {
+    if constexpr (T >= 8) density64_pairs_flat<T, KIND>(A, P, boxes, g, energy, S);
+    else density64_pairs_item<T, KIND>(A, P, boxes, g, energy);
+}
+template <int T, int KIND, bool ENERGY>
+__device__ __forceinline__ void force64_pairs(const Atoms &A, const Pot &P, const Box *boxes, long long g,
+                                              double (&part)[kPartials], double *S) {
+    if constexpr (T >= 8) force64_pairs_flat<T, KIND, ENERGY>(A, P, boxes, g, part, S);
+    else force64_pairs_item<T, KIND, ENERGY>(A, P, boxes, g, part);
 }
 
 // After the pair force pass, per atom: the force = own share + the neighbours' shares, then what

@@ -348,27 +348,45 @@ __device__ __forceinline__ void copyback_atom(const Atoms &A, const Box *boxes, 
     }
 }
 
-// The FP64 pair walk's row order (one warp per atom): the entries j > i first, then the others,
-// each group in its order, and cup[i] = the number of the first.  The whole row (k_max <=
-// kPairsKMax) is read into registers before any entry is written back.
-__device__ __forceinline__ void partition_row_warp(const Atoms &A, int i, int lane) {
+// The FP64 pair walk's row order (one warp per atom): the entries j > i first, those inside
+// r_cut at this build's FP32 positions (cin[i] of them) ahead of the others, then the entries
+// j < i, each group in its order; cup[i] = the number of entries j > i.  The order only steers
+// the walk (its flattened rows take the inside entries first, so that lanes rarely idle on a
+// pair beyond r_cut); which entries count is still decided by every pass's own FP64 test.  The
+// whole row (k_max <= kPairsKMax) is read into registers before any entry is written back.
+__device__ __forceinline__ void partition_row_warp(const Atoms &A, const Box *boxes, int i, int lane) {
     const int cnt = min(A.count[i], A.k_max);
     const NbrRow row = nbr_row(A, i);
+    const Box &B = boxes[replica_of(A, i)];
+    const float4 pi = A.posf[i];
     int v[kPairsKMax / 32];
+    unsigned in = 0;   // bit c: entry 32 c + lane lies inside r_cut
 #pragma unroll
     for (int c = 0; c < kPairsKMax / 32; c++) {
         const int k = 32 * c + lane;
         v[c] = k < cnt ? *row.ptr(k) : -1;
+        if (v[c] > i) {
+            const float4 pj = A.posf[v[c]];
+            float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+            dx = fmaf(-B.Lf[0], rintf(dx * B.invLf[0]), dx);
+            dy = fmaf(-B.Lf[1], rintf(dy * B.invLf[1]), dy);
+            dz = fmaf(-B.Lf[2], rintf(dz * B.invLf[2]), dz);
+            if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < A.pair_rc2f) in |= 1u << c;
+        }
     }
     __syncwarp();
     const unsigned below = (1u << lane) - 1u;
-    int nup = 0;
+    int nup = 0, nin = 0;
 #pragma unroll
-    for (int c = 0; c < kPairsKMax / 32; c++) {
-        const bool up = v[c] > i;
-        const unsigned m = __ballot_sync(0xffffffffu, up);
-        if (up) *row.ptr(nup + __popc(m & below)) = v[c];
-        nup += __popc(m);
+    for (int pass = 0; pass < 2; pass++) {
+#pragma unroll
+        for (int c = 0; c < kPairsKMax / 32; c++) {
+            const bool up = v[c] > i && ((in >> c & 1u) != 0) == (pass == 0);
+            const unsigned m = __ballot_sync(0xffffffffu, up);
+            if (up) *row.ptr(nup + __popc(m & below)) = v[c];
+            nup += __popc(m);
+        }
+        if (pass == 0) nin = nup;
     }
     int pos = nup;
 #pragma unroll
@@ -378,7 +396,10 @@ __device__ __forceinline__ void partition_row_warp(const Atoms &A, int i, int la
         if (lo) *row.ptr(pos + __popc(m & below)) = v[c];
         pos += __popc(m);
     }
-    if (lane == 0) A.cup[i] = nup;
+    if (lane == 0) {
+        A.cup[i] = nup;
+        A.cin[i] = nin;
+    }
 }
 
 // The exact neighbour test: the IEEE operations, order and absence of contraction of the

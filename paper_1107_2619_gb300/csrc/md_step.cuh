@@ -154,6 +154,10 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? (PREC == MD_PREC_DF ? MD_
     __shared__ int ws[32];
     __shared__ std::conditional_t<kGroupWalk<WALK>, tl::Pipe, int> pipe;   // the group walks' pipeline
     __shared__ uint16_t cells_q[WALK == kWalkCells ? NT / 32 : 1][kCellsQueue];
+    // the FP64 pair walk's per-warp sums (flattened rows, T >= 8)
+    constexpr int kPairSlotsW = WALK == kWalkPairs && T >= 8 ? ps::kPairSlots(32 / T) : 0;
+    __shared__ double pair_sums[kPairSlotsW > 0 ? NT / 32 * kPairSlotsW : 1];
+    double *const psum = pair_sums + (threadIdx.x >> 5) * kPairSlotsW;
     extern __shared__ float4 sm_table_f4[];   // [SMT table][stage]
     // The group walks' stage needs the room: their shared copy holds only the rows of the pass
     // under way (the phi rows in the density pass, the derivative rows in the force pass), loaded
@@ -283,7 +287,7 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? (PREC == MD_PREC_DF ? MD_
             }
             if constexpr (WALK == kWalkPairs) {   // each row's entries j > i first
                 MD_SYNC();
-                for (long long i = tid >> 5; i < A.n; i += stride >> 5) ph::partition_row_warp(A, (int)i, threadIdx.x & 31);
+                for (long long i = tid >> 5; i < A.n; i += stride >> 5) ph::partition_row_warp(A, boxes, (int)i, threadIdx.x & 31);
             }
             MD_SYNC();
             MD_STAMP(9);
@@ -341,7 +345,7 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? (PREC == MD_PREC_DF ? MD_
         const bool energy_step = s == sp.n_steps - 1 && sp.energy_last;
         if constexpr (WALK == kWalkPairs) {   // each pair once, then F(rho) once every share is in
             for (long long g = tid; g < items; g += stride)
-                ps::density64_pairs_item<T, KIND>(A, P, boxes, g, energy_step);
+                ps::density64_pairs<T, KIND>(A, P, boxes, g, energy_step, psum);
             MD_SYNC();
             for (long long i = tid; i < A.n; i += stride) ps::pairs_embed64(A, P, (int)i);
         } else if (!tiled) {
@@ -402,7 +406,7 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? (PREC == MD_PREC_DF ? MD_
             }
             if constexpr (WALK == kWalkPairs) {   // each pair once, then the kicks once every share is in
                 for (long long g = tid; g < items; g += stride)
-                    ps::force64_pairs_item<T, KIND, true>(A, P, boxes, g, part);
+                    ps::force64_pairs<T, KIND, true>(A, P, boxes, g, part, psum);
                 MD_SYNC();
                 for (long long i = tid; i < A.n; i += stride) ps::pairs_kick64<true>(A, (int)i, sp.half_dt, sp.motion, part);
             } else if (!tiled) {
@@ -457,7 +461,7 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? (PREC == MD_PREC_DF ? MD_
             }
             if constexpr (WALK == kWalkPairs) {
                 for (long long g = tid; g < items; g += stride)
-                    ps::force64_pairs_item<T, KIND, false>(A, P, boxes, g, part);
+                    ps::force64_pairs<T, KIND, false>(A, P, boxes, g, part, psum);
                 MD_SYNC();
                 for (long long i = tid; i < A.n; i += stride) {
                     ps::pairs_kick64<false>(A, (int)i, sp.half_dt, sp.motion, part);
