@@ -13,15 +13,32 @@
 namespace mdk {
 namespace eam {
 
-// 1/sqrt(x): the FP32 estimate (within 2 ulp, relative error <= 2.4e-7) refined by Newton-Raphson
-// steps in FP64 (y <- y + y (1 - x y^2) / 2), each of which squares the relative error (times
-// 3/2): one step leaves <= 1e-13, three orders of magnitude inside the 1e-10 parity of the FP64
-// path, two reach FP64 rounding (~1e-16) for 10 % more FP64 work per step (MD_RSQRT64_STEPS=2).
+// Conversions between FP64 and FP32 by the IEEE bit fields, in integer registers (the FP64 pipe,
+// which the FP64 passes keep busy, also executes the conversion instructions): the exponent is
+// rebiased by 1023 - 127 = 896 and the significand shifted by 29 bits.  f32_trunc: x >= 0 below
+// the FP32 overflow threshold, rounded toward zero (relative error < 2^-23), and 0 below the
+// normal FP32 range (so that coincident atoms still give 1/sqrt(0) = inf); f64_exact: f positive,
+// normal or +inf, exact.
+__device__ __forceinline__ float f32_trunc(double x) {
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    return __uint_as_float(hi < (897u << 20) ? 0u : ((hi - (896u << 20)) << 3) | (lo >> 29));
+}
+__device__ __forceinline__ double f64_exact(float f) {
+    const unsigned b = __float_as_uint(f);
+    return b >= 0x7f800000u ? __hiloint2double(0x7ff00000, 0)
+                            : __hiloint2double((int)((b >> 3) + (896u << 20)), (int)(b << 29));
+}
+
+// 1/sqrt(x), x positive: the FP32 estimate (x truncated to FP32, then rsqrtf within 2 ulp: relative
+// error <= 3.6e-7) refined by Newton-Raphson steps in FP64 (y <- y + y (1 - x y^2) / 2), each of
+// which squares the relative error (times 3/2): one step leaves <= 2e-13, three orders of
+// magnitude inside the 1e-10 parity of the FP64 path, two reach FP64 rounding (~1e-16) for 10 %
+// more FP64 work per step (MD_RSQRT64_STEPS=2).
 #ifndef MD_RSQRT64_STEPS
 #define MD_RSQRT64_STEPS 1
 #endif
 __device__ __forceinline__ double rsqrt64(double x) {
-    double y = (double)rsqrtf((float)x);
+    double y = f64_exact(rsqrtf(f32_trunc(x)));
     double e = fma(-x * y, y, 1.0);
     y = fma(0.5 * y, e, y);
     if (MD_RSQRT64_STEPS < 2) return y;

@@ -893,22 +893,28 @@ __device__ __forceinline__ void density64_pairs_flat(const Atoms &A, const Pot &
         using W = decltype(wrapt);
         for (int seg = 0; seg < 2; seg++) {
             const FlatRows<AW> R = flat_rows<AW>(c_in, c_up, seg);
-            int cur = -1;
+            int cur = -1, i = 0;
             double rho = 0.0, ep = 0.0;
+            double4_32a pi = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+            NbrRow row{nullptr, 0};
+            DRow drow{nullptr, 0};
             for (int e = lane; e < R.off[AW]; e += 32) {
                 int k;
                 const int a = R.atom(e, k);
-                if (a != cur) {
+                if (a != cur) {   // the next atom of this lane: flush the sums, load the atom
                     if (cur >= 0) {
                         S[cur * 32 + lane] += rho;
-                        S[(AW + cur) * 32 + lane] += ep;
+                        if (energy) S[(AW + cur) * 32 + lane] += ep;
                     }
                     cur = a;
                     rho = ep = 0.0;
+                    i = i0 + a;
+                    pi = ld_phase(A.posd + i);
+                    row = nbr_row(A, i);
+                    drow = dcache_row(A, i);
                 }
-                const int i = i0 + a;
-                const int j = ld_phase(nbr_row(A, i).ptr(k));
-                const double4_32a pi = ld_phase(A.posd + i), pj = ld_phase(A.posd + j);
+                const int j = ld_phase(row.ptr(k));
+                const double4_32a pj = ld_phase(A.posd + j);
                 double dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
                 if (W::value) {
                     const Box &B = boxes[ph::replica_of(A, i)];
@@ -917,7 +923,7 @@ __device__ __forceinline__ void density64_pairs_flat(const Atoms &A, const Pot &
                     dz = mi64(dz, B.L[2], B.invL[2]);
                 }
                 const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-                double2 *dc = dcache_row(A, i).ptr(k);
+                double2 *dc = drow.ptr(k);
                 if (!(r2 < P.rc2)) {
                     *dc = make_double2(0.0, 0.0);
                     continue;
@@ -954,7 +960,7 @@ __device__ __forceinline__ void density64_pairs_flat(const Atoms &A, const Pot &
             }
             if (cur >= 0) {
                 S[cur * 32 + lane] += rho;
-                S[(AW + cur) * 32 + lane] += ep;
+                if (energy) S[(AW + cur) * 32 + lane] += ep;
             }
         }
     };
@@ -990,16 +996,15 @@ __device__ __forceinline__ void force64_pairs_flat(const Atoms &A, const Pot &P,
         using W = decltype(wrapt);
         for (int seg = 0; seg < 2; seg++) {
             const FlatRows<AW> R = flat_rows<AW>(c_in, c_up, seg);
-            int cur = -1;
+            int cur = -1, i = 0;
             double fx = 0.0, fy = 0.0, fz = 0.0;
+            double4_32a pi = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+            NbrRow row{nullptr, 0};
+            DRow drow{nullptr, 0};
             for (int e = lane; e < R.off[AW]; e += 32) {
                 int k;
                 const int a = R.atom(e, k);
-                const int i = i0 + a;
-                const double2 d = ld_phase(dcache_row(A, i).ptr(k));
-                // beyond r_cut: nothing to add
-                if ((__double_as_longlong(d.x) | __double_as_longlong(d.y)) == 0) continue;
-                if (a != cur) {
+                if (a != cur) {   // the next atom of this lane: flush the sums, load the atom
                     if (cur >= 0) {
                         S[cur * 32 + lane] += fx;
                         S[(AW + cur) * 32 + lane] += fy;
@@ -1007,9 +1012,16 @@ __device__ __forceinline__ void force64_pairs_flat(const Atoms &A, const Pot &P,
                     }
                     cur = a;
                     fx = fy = fz = 0.0;
+                    i = i0 + a;
+                    pi = ld_phase(A.p2d + i);
+                    row = nbr_row(A, i);
+                    drow = dcache_row(A, i);
                 }
-                const int j = ld_phase(nbr_row(A, i).ptr(k));
-                const double4_32a pi = ld_phase(A.p2d + i), pj = ld_phase(A.p2d + j);
+                const double2 d = ld_phase(drow.ptr(k));
+                // beyond r_cut: nothing to add
+                if ((__double_as_longlong(d.x) | __double_as_longlong(d.y)) == 0) continue;
+                const int j = ld_phase(row.ptr(k));
+                const double4_32a pj = ld_phase(A.p2d + j);
                 double dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
                 if (W::value) {
                     const Box &B = boxes[ph::replica_of(A, i)];

@@ -135,6 +135,11 @@ __device__ __forceinline__ void thermo_update(const StepParams &sp, int n_rep, l
 #ifndef MD_STEP_MIN_BLOCKS
 #define MD_STEP_MIN_BLOCKS 8
 #endif
+// Blocks of 128 threads per SM the FP64 step kernel is built for: 4 (128 registers) measured 2-3 %
+// faster than 8 (64 registers, with spills) and 6 on fcc Cu 500k, both list walks.
+#ifndef MD_STEP_MIN_BLOCKS_FP64
+#define MD_STEP_MIN_BLOCKS_FP64 4
+#endif
 
 // NT threads per block.  SMT: the knot table of species pair (0, 0) (of the only species, or of
 // the host species of an alloy) is copied into dynamic shared memory at the start of the launch
@@ -149,7 +154,10 @@ template <int WALK>
 constexpr bool kGroupWalk = WALK == kWalkStaged || WALK == kWalkCells || WALK == kWalkHalf;
 
 template <int PREC, int T, int KIND, bool MULTI, int NT, bool SMT, int WALK>
-__global__ void __launch_bounds__(NT, NT == kThreads ? (PREC == MD_PREC_DF ? MD_STEP_MIN_BLOCKS_DF : MD_STEP_MIN_BLOCKS) : 1)
+__global__ void __launch_bounds__(NT, NT == kThreads ? (PREC == MD_PREC_DF     ? MD_STEP_MIN_BLOCKS_DF
+                                                        : PREC == MD_PREC_FP64 ? MD_STEP_MIN_BLOCKS_FP64
+                                                                               : MD_STEP_MIN_BLOCKS)
+                                                      : 1)
     k_step(Atoms A, Cells C, Pot P, StepParams sp, GridBarrier *bar, unsigned long long *stamps) {
     __shared__ int ws[32];
     __shared__ std::conditional_t<kGroupWalk<WALK>, tl::Pipe, int> pipe;   // the group walks' pipeline
