@@ -38,12 +38,14 @@ __device__ __forceinline__ double f64_exact(float f) {
 #define MD_RSQRT64_STEPS 1
 #endif
 __device__ __forceinline__ double rsqrt64(double x) {
+    // y / 2 by the exponent field (y is positive and normal, or +inf: then e is NaN either way)
+    auto half = [](double y) { return __longlong_as_double(__double_as_longlong(y) - (1LL << 52)); };
     double y = f64_exact(rsqrtf(f32_trunc(x)));
     double e = fma(-x * y, y, 1.0);
-    y = fma(0.5 * y, e, y);
+    y = fma(half(y), e, y);
     if (MD_RSQRT64_STEPS < 2) return y;
     e = fma(-x * y, y, 1.0);
-    return fma(0.5 * y, e, y);
+    return fma(half(y), e, y);
 }
 
 // Error-free FP32 accumulation (Knuth's TwoSum): hi + lo carries the exact running sum.
@@ -69,6 +71,39 @@ __device__ __forceinline__ int knot_row(R x, int nk, R &t, bool &below) {
     int k = (x < (R)(nk - 1)) ? (int)x : nk - 1;
     k = below ? 0 : k;
     t = below ? x : x - (R)k;
+    return k;
+}
+
+// The FP64 passes' versions of the pair cut and of knot_row<double>, with the same results: the
+// comparisons and the conversions between double and int act on the IEEE bit patterns in integer
+// registers (non-negative doubles order as their bit patterns do), which leaves the FP64 pipe to
+// the arithmetic.
+// -x by the sign bit.
+__device__ __forceinline__ double neg64(double x) {
+    return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ULL);
+}
+// r2 < rc2 for r2 >= 0 (or NaN, which is never inside) and rc2 > 0.
+__device__ __forceinline__ bool inside64(double r2, double rc2) {
+    return __double_as_longlong(r2) < __double_as_longlong(rc2);
+}
+// k as a double, 0 <= k < 2^31, exact: the leading bit sets the exponent, the rest the fraction.
+__device__ __forceinline__ double f64_of_count(int k) {
+    const int p = 31 - __clz(k | 1);
+    const long long frac = ((long long)k << (52 - p)) & 0xFFFFFFFFFFFFFLL;
+    const long long bits = ((long long)(1023 + p) << 52) | frac;
+    return k == 0 ? 0.0 : __longlong_as_double(bits);
+}
+// knot_row<double>(x, nk, t, below) for finite x; xtop = nk - 1 as a double.
+__device__ __forceinline__ int knot_row64(double x, int nk, double xtop, double &t, bool &below) {
+    const long long b = __double_as_longlong(x);
+    below = b < 0;   // x < 0 (x = -0 gives the same values either way)
+    const bool top = b >= __double_as_longlong(xtop);
+    const int e = (int)((b >> 52) & 0x7ff) - 1023;   // x >= 1: floor(x) = significand >> (52 - e)
+    const long long sig = (b & 0xFFFFFFFFFFFFFLL) | 0x10000000000000LL;
+    int k = e < 0 ? 0 : (int)(sig >> (52 - min(e, 52)));
+    k = top ? nk - 1 : k;
+    k = below ? 0 : k;
+    t = below ? x : x - f64_of_count(k);
     return k;
 }
 

@@ -408,7 +408,7 @@ __device__ __forceinline__ void density64_item(const Atoms &A, const Pot &P, con
                 const double dy = sep64<W>(pj.y - pi.y, B.L[1], B.invL[1]);
                 const double dz = sep64<W>(pj.z - pi.z, B.L[2], B.invL[2]);
                 const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-                if (!(r2 < P.rc2)) {
+                if (!inside64(r2, P.rc2)) {
                     if (keep) *drow.ptr(k) = make_double2(0.0, 0.0);
                     continue;
                 }
@@ -436,7 +436,7 @@ __device__ __forceinline__ void density64_item(const Atoms &A, const Pot &P, con
                     const int sj = MULTI ? (int)pj.w : 0;
                     double t, d;
                     bool below;
-                    const int kr = knot_row((r - P.r_min) * P.inv_dr, P.nk, t, below);
+                    const int kr = knot_row64(fma(r, P.inv_dr, P.xneg), P.nk, P.xtop, t, below);
                     if (below) atomicAdd(&A.flags->range_violations, 1ull);
                     const size_t ab = ((size_t)(si * P.ns + sj) * P.nk + kr) * 2;
                     const double4_32a c = P.VP64[ab + 1];
@@ -570,7 +570,7 @@ __device__ __forceinline__ int force64_item(const Atoms &A, const Pot &P, const 
                 const double dy = sep64<W>(pj.y - pi.y, B.L[1], B.invL[1]);
                 const double dz = sep64<W>(pj.z - pi.z, B.L[2], B.invL[2]);
                 const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-                if (!(r2 < P.rc2)) continue;
+                if (!inside64(r2, P.rc2)) continue;
                 const double rinv = rsqrt64(r2);
                 const double r = r2 * rinv;
                 const double Fpj = pj.w;
@@ -596,7 +596,7 @@ __device__ __forceinline__ int force64_item(const Atoms &A, const Pot &P, const 
                     const int sj = MULTI ? ld_phase(A.spec + j) : 0;
                     double t;
                     bool below;
-                    const int kr = knot_row((r - P.r_min) * P.inv_dr, P.nk, t, below);
+                    const int kr = knot_row64(fma(r, P.inv_dr, P.xneg), P.nk, P.xtop, t, below);
                     if (below) atomicAdd(&A.flags->range_violations, 1ull);
                     const size_t ab = ((size_t)(si * P.ns + sj) * P.nk + kr) * 2;
                     const double4_32a cv = P.VP64[ab], cp = P.VP64[ab + 1];
@@ -692,7 +692,7 @@ __device__ __forceinline__ void density64_pairs_item(const Atoms &A, const Pot &
                 const double dy = sep64<W>(pj.y - pi.y, B.L[1], B.invL[1]);
                 const double dz = sep64<W>(pj.z - pi.z, B.L[2], B.invL[2]);
                 const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-                if (!(r2 < P.rc2)) {
+                if (!inside64(r2, P.rc2)) {
                     *drow.ptr(k) = make_double2(0.0, 0.0);
                     continue;
                 }
@@ -706,7 +706,7 @@ __device__ __forceinline__ void density64_pairs_item(const Atoms &A, const Pot &
                 } else {
                     double t, d;
                     bool below;
-                    const int kr = knot_row((r - P.r_min) * P.inv_dr, P.nk, t, below);
+                    const int kr = knot_row64(fma(r, P.inv_dr, P.xneg), P.nk, P.xtop, t, below);
                     if (below) atomicAdd(&A.flags->range_violations, 1ull);
                     const double4_32a c = P.VP64[(size_t)kr * 2 + 1];
                     phi = cubic(t, c.x, c.y, c.z, c.w, below, d);
@@ -793,9 +793,9 @@ __device__ __forceinline__ void force64_pairs_item(const Atoms &A, const Pot &P,
                     wxy = fma(-gx, dy, wxy);
                 }
                 double *acc = reinterpret_cast<double *>(A.f_acc + j);
-                atomicAdd(acc, -gx);
-                atomicAdd(acc + 1, -gy);
-                atomicAdd(acc + 2, -gz);
+                atomicAdd(acc, neg64(gx));
+                atomicAdd(acc + 1, neg64(gy));
+                atomicAdd(acc + 2, neg64(gz));
             }
         };
         if (wrap) walk(std::true_type{});
@@ -924,7 +924,7 @@ __device__ __forceinline__ void density64_pairs_flat(const Atoms &A, const Pot &
                 }
                 const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
                 double2 *dc = drow.ptr(k);
-                if (!(r2 < P.rc2)) {
+                if (!inside64(r2, P.rc2)) {
                     *dc = make_double2(0.0, 0.0);
                     continue;
                 }
@@ -938,7 +938,7 @@ __device__ __forceinline__ void density64_pairs_flat(const Atoms &A, const Pot &
                 } else {
                     double t, d;
                     bool below;
-                    const int kr = knot_row((r - P.r_min) * P.inv_dr, P.nk, t, below);
+                    const int kr = knot_row64(fma(r, P.inv_dr, P.xneg), P.nk, P.xtop, t, below);
                     if (below) atomicAdd(&A.flags->range_violations, 1ull);
                     const double4_32a c = P.VP64[(size_t)kr * 2 + 1];
                     phi = cubic(t, c.x, c.y, c.z, c.w, below, d);
@@ -1043,9 +1043,9 @@ __device__ __forceinline__ void force64_pairs_flat(const Atoms &A, const Pot &P,
                     wxy = fma(-gx, dy, wxy);
                 }
                 double *acc = reinterpret_cast<double *>(A.f_acc + j);
-                atomicAdd(acc, -gx);
-                atomicAdd(acc + 1, -gy);
-                atomicAdd(acc + 2, -gz);
+                atomicAdd(acc, neg64(gx));
+                atomicAdd(acc + 1, neg64(gy));
+                atomicAdd(acc + 2, neg64(gz));
             }
             if (cur >= 0) {
                 S[cur * 32 + lane] += fx;
