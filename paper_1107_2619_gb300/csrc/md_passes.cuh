@@ -25,7 +25,17 @@ namespace ps {
 using namespace eam;
 
 __device__ __forceinline__ float mi32(float d, float L, float invL) { return fmaf(-L, rintf(d * invL), d); }
-__device__ __forceinline__ double mi64(double d, double L, double invL) { return fma(-L, rint(d * invL), d); }
+// The FP64 passes' minimum image, for separations of coordinates kept in one periodic image of
+// the box (|d| < 3L/2): d - L rint(d / L) as one addition of -L, 0 or +L, chosen on the bit
+// patterns in integer registers (|d| > L/2, L/2 by the exponent field).  Where |d / L| rounds to
+// exactly 1/2 the choice may differ from rint's, but such a pair is L/2 apart, far beyond r_list,
+// either way.
+__device__ __forceinline__ double mi64(double d, double L, double) {
+    const long long b = __double_as_longlong(d);
+    const bool far = (b & 0x7FFFFFFFFFFFFFFFLL) > __double_as_longlong(L) - (1LL << 52);
+    const double s = far ? (b < 0 ? L : neg64(L)) : 0.0;
+    return d + s;
+}
 
 // The minimum image of a separation, or the separation itself for an atom whose link cell was not
 // on the box boundary at the last build (A.wrap) while the FP32 positions stay in the image of
