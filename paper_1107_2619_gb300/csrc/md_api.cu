@@ -72,6 +72,7 @@ struct md_ctx {
     cudaStream_t cap_stream = nullptr;   // private stream the graphs are recorded on
     std::map<int, cudaGraphExec_t> graphs;
     std::map<int, int> graph_rows;
+    std::map<int, int> graph_launches;
     // Nose-Hoover thermostat (md_set_thermostat)
     bool thermo_on = false;
     Thermo *d_thermo = nullptr;
@@ -374,7 +375,21 @@ StepParams step_params(md_ctx *ctx, int n_steps) {
 
 // The work of md_step(n) after any initial force evaluation: the persistent launch, the
 // energy reduction and the copies back.  `rows` receives the partial-sum rows written.
-cudaError_t enqueue_steps(md_ctx *ctx, int n_steps, unsigned long long *stamps, int *rows, cudaStream_t stream) {
+// Rebuild segments of an md_step(n) call (0: one launch, rebuilds inside it): for systems large
+// enough that the step kernel's in-kernel list build, at the step kernel's occupancy, costs more
+// than two extra launches, about 1.5 per rebuild expected from the rebuild interval seen so far.
+constexpr int64_t kSegmentMinAtoms = 32768;
+constexpr int kSegmentsMax = 64;
+int step_segments(md_ctx *ctx, int n_steps) {
+    if (ctx->n < kSegmentMinAtoms || n_steps < 1) return 0;
+    const unsigned long long nr = ctx->h_flags ? ctx->h_flags->n_rebuilds : 0;
+    const int64_t every = ctx->step > 0 && nr > 0 ? std::max<int64_t>(1, ctx->step / (int64_t)nr) : 8;
+    return (int)std::min<int64_t>(kSegmentsMax, (3 * (int64_t)n_steps) / (2 * every) + 2);
+}
+
+cudaError_t enqueue_steps(md_ctx *ctx, int n_steps, unsigned long long *stamps, int *rows, cudaStream_t stream,
+                          int *launches = nullptr) {
+    if (launches) *launches = 2;
     if (ctx->sur) {
         cudaError_t e = cudaSuccess;
         const int every = ctx->cfg.rebuild_every;
@@ -390,8 +405,24 @@ cudaError_t enqueue_steps(md_ctx *ctx, int n_steps, unsigned long long *stamps, 
     }
     const StepParams sp = step_params(ctx, n_steps);
     int grid = 0;
-    cudaError_t e = launch_step(ctx->A, ctx->C, ctx->P, ctx->precision, ctx->lanes, sp, ctx->d_bar, stamps, &grid,
+    // Segments: the step kernel stops at a rebuild request, the rebuild kernel (more warps per
+    // SM than the step kernel keeps) builds the list, a launch resumes the steps; R such pairs,
+    // the last launch rebuilding in-kernel should more rebuilds fall due than R covers.
+    const int R = step_segments(ctx, n_steps);
+    StepParams sp1 = sp;
+    sp1.stop_at_rebuild = R > 0;
+    cudaError_t e = launch_step(ctx->A, ctx->C, ctx->P, ctx->precision, ctx->lanes, sp1, ctx->d_bar, stamps, &grid,
                                 stream);
+    for (int r = 0; r < R && e == cudaSuccess; r++) {
+        e = launch_rebuild_step(ctx->A, ctx->C, ctx->P, ctx->precision, ctx->lanes, sp, ctx->d_bar, stamps, stream);
+        StepParams sp2 = sp;
+        sp2.resume = 1;
+        sp2.stop_at_rebuild = r + 1 < R;
+        if (e == cudaSuccess)
+            e = launch_step(ctx->A, ctx->C, ctx->P, ctx->precision, ctx->lanes, sp2, ctx->d_bar, stamps, &grid,
+                            stream);
+    }
+    if (launches) *launches = 2 + 2 * R;
     if (e == cudaSuccess) e = launch_reduce(ctx->A, grid, ctx->d_reduce, stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ctx->h_reduce, ctx->d_reduce, sizeof(double) * kPartials, cudaMemcpyDeviceToHost,
@@ -425,6 +456,7 @@ void drop_graphs(md_ctx *ctx) {
     for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.second);
     ctx->graphs.clear();
     ctx->graph_rows.clear();
+    ctx->graph_launches.clear();
 }
 
 // --------------------------------------------------------------------------- creation
@@ -1329,7 +1361,8 @@ md_status step_impl(md_ctx *ctx, int32_t n_steps, const StateOut *out) {
             cudaGraphExec_t ge = nullptr;
             if (!ctx->cap_stream) MD_CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
             MD_CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
-            cudaError_t e = enqueue_steps(ctx, n_steps, nullptr, &rows, ctx->cap_stream);
+            int nl = 2;
+            cudaError_t e = enqueue_steps(ctx, n_steps, nullptr, &rows, ctx->cap_stream, &nl);
             cudaError_t e2 = cudaStreamEndCapture(ctx->cap_stream, &g);
             if (e == cudaSuccess) e = e2;
             if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
@@ -1337,13 +1370,16 @@ md_status step_impl(md_ctx *ctx, int32_t n_steps, const StateOut *out) {
             if (e != cudaSuccess) return fail(ctx, MD_ERR_CUDA, "capturing the step graph", e);
             it = ctx->graphs.emplace(n_steps, ge).first;
             ctx->graph_rows[n_steps] = rows;
+            ctx->graph_launches[n_steps] = nl;
         }
         MD_CK(cudaGraphLaunch(it->second, ctx->stream));
         rows = ctx->graph_rows[n_steps];
+        ctx->launches += ctx->graph_launches[n_steps];
     } else {
-        MD_CK(enqueue_steps(ctx, n_steps, stamps, &rows, ctx->stream));
+        int nl = 2;
+        MD_CK(enqueue_steps(ctx, n_steps, stamps, &rows, ctx->stream, &nl));
+        ctx->launches += nl;
     }
-    ctx->launches += 2;
     ctx->part_rows = rows;
     if (ctx->thermo_on) {  // the last half step rescaled the velocities after the energy sums
         MD_CK(launch_replica_sums(ctx->A, ctx->d_rep_off, ctx->n_rep, ctx->d_rep_sums, ctx->stream));

@@ -53,6 +53,8 @@ struct Flags {
     long long step;         // steps taken (the rebuild schedule counts from here)
     int32_t tile_bad;       // a cell group's neighbourhood exceeded the staging capacity at the last build
     int32_t tile_max;       // largest cell-group neighbourhood (atoms) at the last build
+    int32_t seg_done;       // steps of the md_step call under way done when a launch of the step kernel
+                            // stopped at a rebuild request (n_steps once the call's steps are all done)
 };
 
 // Device view of the potential.  Tables hold, per interval k of a uniform knot grid, the
@@ -322,6 +324,10 @@ struct StepParams {
     int motion;            // kMotionVerlet or kMotionPC3: what the force pass does to each atom after
                            // its force (second half kick, or the corrector) and what opens a step
                            // (half kick + drift, or the predictor)
+    int stop_at_rebuild;   // 1: at a step that needs a list rebuild, record the step in Flags::seg_done
+                           // and end the launch (the rebuild kernel follows, then a resuming launch)
+    int resume;            // 1: continue the md_step call at step Flags::seg_done (already opened: no
+                           // prologue); nothing to do when that is n_steps
 };
 // With sp.n_steps == 0 it only prepares the launch (function attributes, occupancy query):
 // done before a stream capture, so that a captured launch makes no other API call.
@@ -329,6 +335,11 @@ cudaError_t launch_step(const Atoms &A, const Cells &C, const Pot &P, int precis
                         const StepParams &sp, GridBarrier *bar, unsigned long long *stamps, int *grid_out,
                         cudaStream_t s);
 int step_grid(const Pot &P, int precision, int lanes);   // blocks of the persistent launch
+// The list rebuild of an md_step call between two launches of the step kernel: a cooperative
+// kernel of its own (more warps per SM than the step kernel keeps), which does nothing unless
+// the last launch stopped at a rebuild request (Flags::seg_done < sp.n_steps, need_rebuild set).
+cudaError_t launch_rebuild_step(const Atoms &A, const Cells &C, const Pot &P, int precision, int lanes,
+                                const StepParams &sp, GridBarrier *bar, unsigned long long *stamps, cudaStream_t s);
 
 // ---------------------------------------------------------------- learned surrogate
 // Per-atom energy E_i = f(x_i) of standardised radial-basis descriptors x_ik = (G_ik - gmu_k) ginv_k,

@@ -141,6 +141,92 @@ __device__ __forceinline__ void thermo_update(const StepParams &sp, int n_rep, l
 #define MD_STEP_MIN_BLOCKS_FP64 4
 #endif
 
+// The walks over cell groups staged in shared memory (md_tile.cuh).
+template <int WALK>
+constexpr bool kGroupWalk = WALK == kWalkStaged || WALK == kWalkCells || WALK == kWalkHalf;
+
+// The list rebuild (§3.2.1: bin, counting sort, Verlet list; and for the walks that need them the
+// group tables, local rows or the half-list row order), every block of a cooperative launch
+// taking part, with grid barriers between the phases.  srow: the step's profiling stamps (1..9)
+// or NULL.  False once the launch is aborted (a barrier gave up).  G: the lanes per link cell of
+// the list build as a compile-time constant (one build variant in the kernel: fewer registers),
+// or 0 for sp.list_group at run time.
+template <int WALK, int G = 0>
+__device__ __forceinline__ bool rebuild_phases(const Atoms &A, const Cells &C, Box *boxes, const StepParams &sp,
+                                               GridBarrier *bar, int *ws, unsigned long long *srow) {
+    const unsigned nb = gridDim.x;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long stride = (long long)nb * blockDim.x;
+    const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+#define RB_SYNC()                                                   \
+    do {                                                            \
+        if (!grid_sync(bar, nb, sp.spin_limit, A.flags)) return false; \
+    } while (0)
+#define MD_STAMP(q) \
+    if (srow) srow[q] = globaltimer()
+
+    for (long long i = tid; i < A.n; i += stride) ph::bin_atom(A, C, boxes, (int)i);
+    RB_SYNC();
+    MD_STAMP(1);
+    const int ntiles = ph::scan_tiles(C);
+    for (int t = blockIdx.x; t < ntiles; t += nb) ph::scan_tile_sum(C, t, ws);
+    RB_SYNC();
+    MD_STAMP(2);
+    if (blockIdx.x == 0) {
+        if (threadIdx.x == 0) {
+            A.flags->max_count = 0;
+            A.flags->tile_bad = 0;
+            A.flags->tile_max = 0;
+        }
+        ph::scan_top(C, ws);
+    }
+    RB_SYNC();
+    MD_STAMP(3);
+    for (int t = blockIdx.x; t < ntiles; t += nb) ph::scan_apply(C, t, ws);
+    RB_SYNC();
+    MD_STAMP(4);
+    for (long long i = tid; i < A.n; i += stride) ph::scatter_atom(A, C, (int)i);
+    if constexpr (kGroupWalk<WALK>) {
+        for (long long g = tid; g < C.n_groups; g += stride) ph::group_table(C, (int)g, A.flags);
+    } else {
+        if (C.tile && lead) A.flags->tile_bad = 1;   // this build writes no local lists
+    }
+    RB_SYNC();
+    MD_STAMP(5);
+    for (long long c = tid >> 5; c < C.ncell; c += stride >> 5) ph::sort_cell_warp(A, C, (int)c, threadIdx.x & 31);
+    RB_SYNC();
+    MD_STAMP(6);
+    for (long long k = tid; k < A.n; k += stride) ph::gather_atom(A, (int)k);
+    RB_SYNC();
+    MD_STAMP(7);
+    for (long long k = tid; k < A.n; k += stride) ph::copyback_atom(A, boxes, (int)k);
+    RB_SYNC();
+    MD_STAMP(8);
+    // the group walks need the global rows only when some group does not fit its stage
+    const bool rows = !kGroupWalk<WALK> || *reinterpret_cast<volatile int32_t *>(&A.flags->tile_bad);
+    if (WALK != kWalkCells || rows) {
+        constexpr int LOCAL = WALK == kWalkStaged ? 1 : (WALK == kWalkHalf ? 2 : 0);
+        int m;
+        if constexpr (G > 0)
+            m = ph::build_cells<G, LOCAL>(A, C, boxes, tid >> 5, stride >> 5, threadIdx.x & 31, sp.rl2, sp.band_lo,
+                                          sp.band_hi, rows);
+        else
+            m = ph::build_cells_any<LOCAL>(sp.list_group, A, C, boxes, tid >> 5, stride >> 5, threadIdx.x & 31, sp.rl2,
+                                           sp.band_lo, sp.band_hi, rows);
+        m = __reduce_max_sync(0xffffffffu, m);
+        if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(&A.flags->max_count, m);
+    }
+    if constexpr (WALK == kWalkPairs) {   // each row's entries j > i first
+        RB_SYNC();
+        for (long long i = tid >> 5; i < A.n; i += stride >> 5) ph::partition_row_warp(A, boxes, (int)i, threadIdx.x & 31);
+    }
+    RB_SYNC();
+    MD_STAMP(9);
+    return true;
+#undef MD_STAMP
+#undef RB_SYNC
+}
+
 // NT threads per block.  SMT: the knot table of species pair (0, 0) (of the only species, or of
 // the host species of an alloy) is copied into dynamic shared memory at the start of the launch
 // and the passes read it there (one 1024-thread block per SM); other pairs read the global table.
@@ -149,9 +235,6 @@ __device__ __forceinline__ void thermo_update(const StepParams &sp, int n_rep, l
 // else over atoms through the list.  The cell walk builds no list at a rebuild unless a group
 // did not fit (the list walk then needs one).  The half walk adds two phases: F(rho) after the
 // density pass and the kicks after the force pass (each waits for every group's shares).
-// The walks over cell groups staged in shared memory (md_tile.cuh).
-template <int WALK>
-constexpr bool kGroupWalk = WALK == kWalkStaged || WALK == kWalkCells || WALK == kWalkHalf;
 
 template <int PREC, int T, int KIND, bool MULTI, int NT, bool SMT, int WALK>
 __global__ void __launch_bounds__(NT, NT == kThreads ? (PREC == MD_PREC_DF     ? MD_STEP_MIN_BLOCKS_DF
@@ -205,101 +288,62 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? (PREC == MD_PREC_DF     ?
         if (!grid_sync(bar, nb, sp.spin_limit, A.flags)) return;   \
     } while (0)
 
-    if (stamps && lead) stamps[0] = globaltimer();
-    // first half kick + drift of the first step
-    if (strain) {
-        if (lead) strain_boxes(boxes, A.n_rep, sp.strain_scale);
-        MD_SYNC();
-    }
-    if (lead && sp.rebuild_every > 0 && (step + 1) % sp.rebuild_every == 0) A.flags->need_rebuild = 1;
     const bool thermo = sp.thermo != nullptr;
-    if (thermo) {  // the thermostat half step that opens the first step
-        ke_sums(A, sp, tid, stride);
-        MD_SYNC();
-        thermo_update(sp, A.n_rep, tid, stride, false, true);
-        MD_SYNC();
-    }
-    for (long long i = tid; i < A.n; i += stride) {
-        ph::open_step(A, boxes, (int)i, sp.motion, sp.half_dt, sp.dt, sp.strain_scale, strain, sp.lim2,
-                      thermo ? sp.thermo : nullptr);
-        if constexpr (WALK == kWalkHalf) A.rho_acc[i] = 0.0;
-    }
-    if (sp.withhold_arrival && blockIdx.x == 0) {
-        // self-test of the bounded wait: this block never arrives; it waits (bounded) until
-        // the others have given up and marked the launch aborted, then leaves.
-        if (threadIdx.x == 0) {
-            unsigned long long polls = 0;
-            while (!*reinterpret_cast<volatile int *>(&bar->abort) && ++polls < 4 * sp.spin_limit) __nanosleep(100);
-            if (gridDim.x == 1) atomicOr(&A.flags->error, FLAG_TIMEOUT);  // nobody else to give up
+    int s0 = 0;
+    if (sp.resume) {   // the step was opened by the launch that stopped at its rebuild request
+        s0 = *reinterpret_cast<volatile int32_t *>(&A.flags->seg_done);
+        if (s0 >= sp.n_steps || (*reinterpret_cast<volatile int32_t *>(&A.flags->error) & FLAG_TIMEOUT)) return;
+    } else {
+        if (stamps && lead) stamps[0] = globaltimer();
+        // first half kick + drift of the first step
+        if (strain) {
+            if (lead) strain_boxes(boxes, A.n_rep, sp.strain_scale);
+            MD_SYNC();
         }
-        __syncthreads();
-        return;
+        if (lead && sp.rebuild_every > 0 && (step + 1) % sp.rebuild_every == 0) A.flags->need_rebuild = 1;
+        if (thermo) {  // the thermostat half step that opens the first step
+            ke_sums(A, sp, tid, stride);
+            MD_SYNC();
+            thermo_update(sp, A.n_rep, tid, stride, false, true);
+            MD_SYNC();
+        }
+        for (long long i = tid; i < A.n; i += stride) {
+            ph::open_step(A, boxes, (int)i, sp.motion, sp.half_dt, sp.dt, sp.strain_scale, strain, sp.lim2,
+                          thermo ? sp.thermo : nullptr);
+            if constexpr (WALK == kWalkHalf) A.rho_acc[i] = 0.0;
+        }
+        if (sp.withhold_arrival && blockIdx.x == 0) {
+            // self-test of the bounded wait: this block never arrives; it waits (bounded) until
+            // the others have given up and marked the launch aborted, then leaves.
+            if (threadIdx.x == 0) {
+                unsigned long long polls = 0;
+                while (!*reinterpret_cast<volatile int *>(&bar->abort) && ++polls < 4 * sp.spin_limit) __nanosleep(100);
+                if (gridDim.x == 1) atomicOr(&A.flags->error, FLAG_TIMEOUT);  // nobody else to give up
+            }
+            __syncthreads();
+            return;
+        }
+        MD_SYNC();
     }
-    MD_SYNC();
 
     unsigned long long *srow = nullptr;
-    for (int s = 0; s < sp.n_steps; s++) {
+    for (int s = s0; s < sp.n_steps; s++) {
+        // (a resumed step keeps the stamps of the launch that stopped and of the rebuild kernel)
+        const bool resumed = sp.resume && s == s0;
         if (stamps && lead) {
             srow = stamps + kStampsPerStep * (s + 1);
-            srow[0] = globaltimer();
+            if (!resumed) srow[0] = globaltimer();
         }
 #define MD_STAMP(q) \
     if (srow) srow[q] = globaltimer()
         // ------------------------------------------------ list rebuild when flagged
         if (ph::rebuild_requested(A.flags)) {
-            for (long long i = tid; i < A.n; i += stride) ph::bin_atom(A, C, boxes, (int)i);
-            MD_SYNC();
-            MD_STAMP(1);
-            const int ntiles = ph::scan_tiles(C);
-            for (int t = blockIdx.x; t < ntiles; t += nb) ph::scan_tile_sum(C, t, ws);
-            MD_SYNC();
-            MD_STAMP(2);
-            if (blockIdx.x == 0) {
-                if (threadIdx.x == 0) {
-                    A.flags->max_count = 0;
-                    A.flags->tile_bad = 0;
-                    A.flags->tile_max = 0;
-                }
-                ph::scan_top(C, ws);
+            if (sp.stop_at_rebuild) {   // the rebuild kernel takes it, then a resuming launch
+                if (lead) A.flags->seg_done = s;
+                return;
             }
-            MD_SYNC();
-            MD_STAMP(3);
-            for (int t = blockIdx.x; t < ntiles; t += nb) ph::scan_apply(C, t, ws);
-            MD_SYNC();
-            MD_STAMP(4);
-            for (long long i = tid; i < A.n; i += stride) ph::scatter_atom(A, C, (int)i);
-            if constexpr (kGroupWalk<WALK>) {
-                for (long long g = tid; g < C.n_groups; g += stride) ph::group_table(C, (int)g, A.flags);
-            } else {
-                if (C.tile && lead) A.flags->tile_bad = 1;   // this build writes no local lists
-            }
-            MD_SYNC();
-            MD_STAMP(5);
-            for (long long c = tid >> 5; c < C.ncell; c += stride >> 5) ph::sort_cell_warp(A, C, (int)c, threadIdx.x & 31);
-            MD_SYNC();
-            MD_STAMP(6);
-            for (long long k = tid; k < A.n; k += stride) ph::gather_atom(A, (int)k);
-            MD_SYNC();
-            MD_STAMP(7);
-            for (long long k = tid; k < A.n; k += stride) ph::copyback_atom(A, boxes, (int)k);
-            MD_SYNC();
-            MD_STAMP(8);
-            // the group walks need the global rows only when some group does not fit its stage
-            const bool rows = !kGroupWalk<WALK> || *reinterpret_cast<volatile int32_t *>(&A.flags->tile_bad);
-            if (WALK != kWalkCells || rows) {
-                int m = ph::build_cells_any<WALK == kWalkStaged ? 1 : (WALK == kWalkHalf ? 2 : 0)>(
-                    sp.list_group, A, C, boxes, tid >> 5, stride >> 5, threadIdx.x & 31, sp.rl2, sp.band_lo, sp.band_hi,
-                    rows);
-                m = __reduce_max_sync(0xffffffffu, m);
-                if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(&A.flags->max_count, m);
-            }
-            if constexpr (WALK == kWalkPairs) {   // each row's entries j > i first
-                MD_SYNC();
-                for (long long i = tid >> 5; i < A.n; i += stride >> 5) ph::partition_row_warp(A, boxes, (int)i, threadIdx.x & 31);
-            }
-            MD_SYNC();
-            MD_STAMP(9);
-        } else if (srow) {
+            if (!rebuild_phases<WALK>(A, C, boxes, sp, bar, ws, srow)) return;
+        } else if (srow && !resumed) {
             const unsigned long long t0 = srow[0];
             for (int q = 1; q <= 9; q++) srow[q] = t0;
         }
@@ -521,7 +565,10 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? (PREC == MD_PREC_DF     ?
             MD_SYNC();
         }
     }
-    if (lead) A.flags->step = step + sp.n_steps;
+    if (lead) {
+        A.flags->step = step + sp.n_steps;
+        A.flags->seg_done = sp.n_steps;
+    }
 #undef MD_STAMP
 #undef MD_SYNC
 }
@@ -571,6 +618,65 @@ cudaError_t launch_t(const Atoms &A, const Cells &C, const Pot &P, const StepPar
     void *args[] = {&a, &c, &p, &q, &bar, &stamps};
     return cudaLaunchCooperativeKernel((const void *)k_step<PREC, T, KIND, MULTI, NT, SMT, WALK>, dim3(grid), dim3(NT),
                                        args, dyn, s);
+}
+
+// The rebuild between two launches of the step kernel (md_internal.cuh launch_rebuild_step).
+constexpr int kRebuildThreads = 256;
+#ifndef MD_REBUILD_MIN_BLOCKS   // blocks of kRebuildThreads per SM the rebuild kernel is built for
+#define MD_REBUILD_MIN_BLOCKS 4
+#endif
+
+template <int WALK, int G>
+__global__ void __launch_bounds__(kRebuildThreads, MD_REBUILD_MIN_BLOCKS)
+    k_rebuild(Atoms A, Cells C, StepParams sp, GridBarrier *bar, unsigned long long *stamps) {
+    __shared__ int ws[32];
+    // every block reads the same words, written before this launch: all take part or none
+    const int s = *reinterpret_cast<volatile int32_t *>(&A.flags->seg_done);
+    if (s >= sp.n_steps || !ph::rebuild_requested(A.flags) ||
+        (*reinterpret_cast<volatile int32_t *>(&A.flags->error) & FLAG_TIMEOUT))
+        return;
+    const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+    unsigned long long *srow = stamps && lead ? stamps + kStampsPerStep * (s + 1) : nullptr;
+    if (!rebuild_phases<WALK, G>(A, C, A.boxes, sp, bar, ws, srow)) return;
+    if (lead) {   // every block has passed the rebuild decision (the barriers above)
+        A.flags->n_rebuilds++;
+        A.flags->need_rebuild = 0;
+    }
+}
+
+template <int WALK, int G>
+cudaError_t launch_rebuild_g(const Atoms &A, const Cells &C, const StepParams &sp, GridBarrier *bar,
+                             unsigned long long *stamps, cudaStream_t s) {
+    static int grid = 0;
+    if (grid == 0) {
+        int dev = 0, n_sm = 0, per_sm = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rebuild<WALK, G>, kRebuildThreads, 0);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        grid = per_sm * n_sm;
+    }
+    cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(GridBarrier), s);
+    if (e != cudaSuccess) return e;
+    Atoms a = A;
+    Cells c = C;
+    StepParams q = sp;
+    void *args[] = {&a, &c, &q, &bar, &stamps};
+    return cudaLaunchCooperativeKernel((const void *)k_rebuild<WALK, G>, dim3(grid), dim3(kRebuildThreads), args, 0,
+                                       s);
+}
+
+template <int WALK>
+cudaError_t launch_rebuild_t(const Atoms &A, const Cells &C, const StepParams &sp, GridBarrier *bar,
+                             unsigned long long *stamps, cudaStream_t s) {
+    switch (sp.list_group) {
+        case 4: return launch_rebuild_g<WALK, 4>(A, C, sp, bar, stamps, s);
+        case 8: return launch_rebuild_g<WALK, 8>(A, C, sp, bar, stamps, s);
+        case 16: return launch_rebuild_g<WALK, 16>(A, C, sp, bar, stamps, s);
+        default: return launch_rebuild_g<WALK, 32>(A, C, sp, bar, stamps, s);
+    }
 }
 
 template <int PREC, int T>

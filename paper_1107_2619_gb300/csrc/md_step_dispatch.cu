@@ -24,4 +24,25 @@ cudaError_t launch_step(const Atoms &A, const Cells &C, const Pot &P, int precis
 #undef MD_STEP_CASE
 }
 
+// The walk of the step kernel launch_step runs for this context (launch_kind's choice).
+static int step_walk(const Atoms &A, const Cells &C, const Pot &P, int precision, int lanes) {
+    if (precision == MD_PREC_FP64 && A.pairs) return kWalkPairs;
+    if (precision == MD_PREC_MIXED && lanes <= 8 && P.kind == MD_POT_TABLES && P.ns == 1 &&
+        smem_table_bytes(P.kind, P.ns, precision, P.nk) > 0 &&
+        (C.tile == kWalkStaged || C.tile == kWalkCells || C.tile == kWalkHalf))
+        return C.tile;
+    return kWalkList;
+}
+
+cudaError_t launch_rebuild_step(const Atoms &A, const Cells &C, const Pot &P, int precision, int lanes,
+                                const StepParams &sp, GridBarrier *bar, unsigned long long *stamps, cudaStream_t s) {
+    switch (step_walk(A, C, P, precision, lanes)) {
+        case kWalkStaged: return st::launch_rebuild_t<kWalkStaged>(A, C, sp, bar, stamps, s);
+        case kWalkCells: return st::launch_rebuild_t<kWalkCells>(A, C, sp, bar, stamps, s);
+        case kWalkHalf: return st::launch_rebuild_t<kWalkHalf>(A, C, sp, bar, stamps, s);
+        case kWalkPairs: return st::launch_rebuild_t<kWalkPairs>(A, C, sp, bar, stamps, s);
+        default: return st::launch_rebuild_t<kWalkList>(A, C, sp, bar, stamps, s);
+    }
+}
+
 }  // namespace mdk
