@@ -375,13 +375,15 @@ StepParams step_params(md_ctx *ctx, int n_steps) {
 
 // The work of md_step(n) after any initial force evaluation: the persistent launch, the
 // energy reduction and the copies back.  `rows` receives the partial-sum rows written.
-// Rebuild segments of an md_step(n) call (0: one launch, rebuilds inside it): for systems large
-// enough that the step kernel's in-kernel list build, at the step kernel's occupancy, costs more
-// than two extra launches, about 1.5 per rebuild expected from the rebuild interval seen so far.
+// Rebuild segments of an md_step(n) call (0: one launch, rebuilds inside it): for the FP64 step
+// kernel (4 blocks of 128 threads per SM: its in-kernel list build runs at a quarter of the
+// rebuild kernel's occupancy) on systems large enough that a rebuild costs more than two extra
+// launches; about 1.5 per rebuild expected from the rebuild interval seen so far.  (The mixed and
+// double-float step kernels keep 32 warps per SM, and measured no faster with segments.)
 constexpr int64_t kSegmentMinAtoms = 32768;
 constexpr int kSegmentsMax = 64;
 int step_segments(md_ctx *ctx, int n_steps) {
-    if (ctx->n < kSegmentMinAtoms || n_steps < 1) return 0;
+    if (ctx->precision != MD_PREC_FP64 || ctx->n < kSegmentMinAtoms || n_steps < 1) return 0;
     const unsigned long long nr = ctx->h_flags ? ctx->h_flags->n_rebuilds : 0;
     const int64_t every = ctx->step > 0 && nr > 0 ? std::max<int64_t>(1, ctx->step / (int64_t)nr) : 8;
     return (int)std::min<int64_t>(kSegmentsMax, (3 * (int64_t)n_steps) / (2 * every) + 2);

@@ -1010,10 +1010,12 @@ __device__ __forceinline__ void force64_pairs_flat(const Atoms &A, const Pot &P,
             double fx = 0.0, fy = 0.0, fz = 0.0;
             double4_32a pi = make_double4_32a(0.0, 0.0, 0.0, 0.0);
             NbrRow row{nullptr, 0};
-            DRow drow{nullptr, 0};
             for (int e = lane; e < R.off[AW]; e += 32) {
                 int k;
                 const int a = R.atom(e, k);
+                const double2 d = ld_phase(dcache_row(A, i0 + a).ptr(k));
+                // beyond r_cut: nothing to add (the skin segment mostly ends here)
+                if ((__double_as_longlong(d.x) | __double_as_longlong(d.y)) == 0) continue;
                 if (a != cur) {   // the next atom of this lane: flush the sums, load the atom
                     if (cur >= 0) {
                         S[cur * 32 + lane] += fx;
@@ -1025,11 +1027,7 @@ __device__ __forceinline__ void force64_pairs_flat(const Atoms &A, const Pot &P,
                     i = i0 + a;
                     pi = ld_phase(A.p2d + i);
                     row = nbr_row(A, i);
-                    drow = dcache_row(A, i);
                 }
-                const double2 d = ld_phase(drow.ptr(k));
-                // beyond r_cut: nothing to add
-                if ((__double_as_longlong(d.x) | __double_as_longlong(d.y)) == 0) continue;
                 const int j = ld_phase(row.ptr(k));
                 const double4_32a pj = ld_phase(A.p2d + j);
                 double dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
