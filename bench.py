@@ -432,7 +432,8 @@ def run_ours(args):
                                   if fp64_leg == "fp64_half" else "full list: each pair from both sides")),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_tflops, "unit": "TFLOP/s",
                      "frac": achieved / fp64_tflops, "traffic": _traffic("k_step_fp64", n, args.steps),
-                     "kernel": "k_step (persistent: all phases of all K steps in one launch), FP64 pipe",
+                     "kernel": "k_step (persistent: all phases of the K steps, stopping at each rebuild request "
+                               "for the k_rebuild kernel and resuming), FP64 pipe",
                      "peak_source": "measured in this run: md_measure_fp64_peak (FP64 FMA chains, CUDA events)",
                      "flop_model": "47 FP64 flop per list entry inside r_cut over both passes, 20 in the skin "
                                    "shell (an FMA counts 2); half of it with the half list",
