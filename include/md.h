@@ -295,8 +295,13 @@ md_status md_eam_forces(md_ctx *ctx, double *pe_out);
  * [list rebuild when scheduled or when an atom moved > skin/2], density pass,
  * force pass, half kick.  All n_steps run in ONE cooperative launch of a persistent
  * kernel (grid barriers between the phases, each wait bounded: a wait that gives up
- * returns MD_ERR_TIMEOUT).  Energies of the final state are then available from
- * md_energy.  Synchronises the stream once, at the end. */
+ * returns MD_ERR_TIMEOUT).  FP64 contexts of at least 32,768 atoms run the call in
+ * segments instead: the persistent launch stops at a step that needs a list rebuild, a
+ * cooperative rebuild kernel with more warps per SM rebuilds, and a launch resumes at that
+ * step (a few such segments are enqueued per call, from the rebuild interval seen so far;
+ * rebuilds beyond them run inside the last launch).  Results are the same either way.
+ * Energies of the final state are then available from md_energy.  Synchronises the stream
+ * once, at the end. */
 md_status md_step(md_ctx *ctx, int32_t n_steps);
 
 /* Self-test of failure detection: runs one step in which one block of the persistent
