@@ -14,6 +14,11 @@
 //
 // The grid barrier waits at most `spin_limit` polls; a block that gives up marks the launch
 // aborted (FLAG_TIMEOUT) and every block returns at its next barrier.
+//
+// Segments (StepParams::stop_at_rebuild, resume): a launch may instead end at the top of a step
+// that needs a rebuild (the step already opened), recording the step in Flags::seg_done; the
+// rebuild kernel k_rebuild (the same rebuild phases, as a cooperative launch of its own) then
+// rebuilds, and a resuming launch continues at that step without the first-step prologue.
 #pragma once
 
 #include <cuda_runtime.h>
