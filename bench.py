@@ -362,7 +362,8 @@ def run_ours(args):
            "d2h_bytes_per_step": 72 * n + C.sizeof(md.md_energies), "steps": k_e2e,
            "note": "FP64 path (the headline's walk); each step one md_step_io call: positions, velocities "
                    "and forces in from pinned host buffers, md_step(1), the three arrays back into them and "
-                   "the energies, one synchronisation"}
+                   "the energies, one synchronisation; the device reads and writes the pinned buffers "
+                   "directly over the host link (caller order, in the sort kernels)"}
 
     extras = {}
     if not args.no_extras:

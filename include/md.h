@@ -335,7 +335,10 @@ md_status md_set_state(md_ctx *ctx, const double *pos, const double *vel, const 
  * vel_out, force_out and md_energy into *energies, with the copies and kernels in stream order
  * and the stream synchronised once (at the end).  Every argument but ctx may be NULL (that copy
  * is skipped); inputs and outputs may be the same buffers.  Results are bitwise those of the
- * separate calls.  Host buffers are best pinned (page-locked); on_device as for md_get. */
+ * separate calls.  Host buffers are best pinned (page-locked): the device then reads and writes
+ * them itself over the host link, in caller order, inside the kernels that reorder the state
+ * (no copy through a device stage); pageable buffers are copied through a device stage.  The
+ * same holds for md_set_state's inputs.  on_device as for md_get. */
 md_status md_step_io(md_ctx *ctx, int32_t n_steps, const double *pos_in, const double *vel_in,
                      const double *force_in, double *pos_out, double *vel_out, double *force_out,
                      md_energies *energies, int32_t on_device);

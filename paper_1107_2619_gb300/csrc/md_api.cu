@@ -1246,6 +1246,17 @@ struct StateOut {
 
 // The unsort kernels and copies of the requested arrays, enqueued only (three staging regions,
 // so that the copies need no synchronisation in between).
+// The device's address of a caller's host buffer in mapped pinned memory (which the device reads
+// and writes directly over the host link), or NULL (pageable memory: copies through a stage).
+void *mapped_host_ptr(const void *p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 md_status enqueue_state_out(md_ctx *ctx, const StateOut &o) {
     const size_t n3 = 3 * (size_t)ctx->n;
     md_status s = ensure_stage(ctx, 3 * n3 * sizeof(double));
@@ -1254,6 +1265,13 @@ md_status enqueue_state_out(md_ctx *ctx, const StateOut &o) {
     double *dst[3] = {o.pos, o.vel, o.force};
     for (int q = 0; q < 3; q++) {
         if (!dst[q]) continue;
+        if (!o.on_device) {
+            if (double *m = static_cast<double *>(mapped_host_ptr(dst[q]))) {
+                MD_CK(launch_unsort_mapped(ctx->A, src[q], m, ctx->stream));
+                ctx->launches++;
+                continue;
+            }
+        }
         double *stage = static_cast<double *>(ctx->d_stage) + q * n3;
         MD_CK(launch_unsort_vec(ctx->A, src[q], stage, ctx->stream));
         MD_CK(cudaMemcpyAsync(dst[q], stage, n3 * sizeof(double),
@@ -1273,6 +1291,13 @@ md_status enqueue_state_in(md_ctx *ctx, const double *pos, const double *vel, co
     double4_32a *dst[3] = {ctx->A.pos, ctx->A.vel, ctx->A.force};
     for (int q = 0; q < 3; q++) {
         if (!src[q]) continue;
+        if (!on_device) {
+            if (const double *m = static_cast<const double *>(mapped_host_ptr(src[q]))) {
+                MD_CK(launch_sort_in_mapped(ctx->A, m, dst[q], ctx->stream));
+                ctx->launches++;
+                continue;
+            }
+        }
         double *stage = static_cast<double *>(ctx->d_stage) + q * n3;
         MD_CK(cudaMemcpyAsync(stage, src[q], n3 * sizeof(double), kind, ctx->stream));
         MD_CK(launch_sort_in_vec(ctx->A, stage, dst[q], ctx->stream));

@@ -292,6 +292,10 @@ cudaError_t launch_unsort_image(const Atoms &A, double *dst, cudaStream_t s);
 cudaError_t launch_unsort_int(const Atoms &A, const int32_t *src, int32_t *dst, cudaStream_t s);
 cudaError_t launch_unsort_list(const Atoms &A, int32_t *dst, cudaStream_t s);
 cudaError_t launch_sort_in_vec(const Atoms &A, const double *src, double4_32a *dst, cudaStream_t s);
+// The same for caller buffers in mapped pinned host memory (device pointers of them), read or
+// written in caller order by the device over the host link: no separate copy.
+cudaError_t launch_sort_in_mapped(const Atoms &A, const double *src, double4_32a *dst, cudaStream_t s);
+cudaError_t launch_unsort_mapped(const Atoms &A, const double4_32a *src, double *dst, cudaStream_t s);
 cudaError_t launch_replica_sums(const Atoms &A, const int32_t *off, int n_rep, double *out, cudaStream_t s);
 
 // Nose-Hoover thermostat of one replica (md_set_thermostat; §2.1.2).

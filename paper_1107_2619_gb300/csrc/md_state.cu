@@ -77,6 +77,29 @@ __global__ void k_unsort_list(Atoms A, int32_t *dst) {
     for (int k = 0; k < A.k_max; k++) row[k] = k < cnt ? A.id[src[k]] : -1;
 }
 
+// The same two copies for a caller buffer in mapped pinned host memory, read and written by the
+// device over the host link: thread c takes the caller's atom c, so that consecutive threads
+// touch consecutive host bytes, and reaches the cell-ordered slot rank[c] in device memory.
+__global__ void k_sort_in_mapped(Atoms A, const double *src, double4_32a *dst) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= A.n) return;
+    const int k = A.rank[c];
+    double4_32a v = dst[k];
+    v.x = src[3 * (size_t)c];
+    v.y = src[3 * (size_t)c + 1];
+    v.z = src[3 * (size_t)c + 2];
+    dst[k] = v;
+}
+
+__global__ void k_unsort_mapped(Atoms A, const double4_32a *src, double *dst) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= A.n) return;
+    const double4_32a v = src[A.rank[c]];
+    dst[3 * (size_t)c] = v.x;
+    dst[3 * (size_t)c + 1] = v.y;
+    dst[3 * (size_t)c + 2] = v.z;
+}
+
 __global__ void k_sort_in_vec(Atoms A, const double *src, double4_32a *dst) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= A.n) return;
@@ -164,6 +187,18 @@ cudaError_t launch_unsort_list(const Atoms &A, int32_t *dst, cudaStream_t s) {
 cudaError_t launch_sort_in_vec(const Atoms &A, const double *src, double4_32a *dst, cudaStream_t s) {
     if (A.n == 0) return cudaSuccess;
     k_sort_in_vec<<<blocks_for(A.n, kThreads), kThreads, 0, s>>>(A, src, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sort_in_mapped(const Atoms &A, const double *src, double4_32a *dst, cudaStream_t s) {
+    if (A.n == 0) return cudaSuccess;
+    k_sort_in_mapped<<<blocks_for(A.n, kThreads), kThreads, 0, s>>>(A, src, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unsort_mapped(const Atoms &A, const double4_32a *src, double *dst, cudaStream_t s) {
+    if (A.n == 0) return cudaSuccess;
+    k_unsort_mapped<<<blocks_for(A.n, kThreads), kThreads, 0, s>>>(A, src, dst);
     return cudaGetLastError();
 }
 

@@ -287,11 +287,12 @@ def test_device_inputs_match_host_inputs():
         assert np.array_equal(a.forces(), b.forces())
 
 
-@pytest.mark.parametrize("device", [False, True])
+@pytest.mark.parametrize("device", [False, True, "pinned"])
 def test_step_io_equals_the_separate_calls(device):
     """md_step_io (state in, steps, state out, energies; one synchronisation) against
-    md_set_state + md_step + md_get x3 + md_energy: bitwise equal, host or device buffers, and
-    with the same buffers as inputs and outputs."""
+    md_set_state + md_step + md_get x3 + md_energy: bitwise equal, host buffers (pageable: copies
+    through a device stage; pinned: read and written by the device directly), device buffers,
+    and with the same buffers as inputs and outputs."""
     torch = pytest.importorskip("torch")
     w = I.fcc_cu(8, seed=31, sigma=0.03)
     with _gpu_system(w, "mixed") as a, _gpu_system(w, "mixed") as b:
@@ -302,7 +303,11 @@ def test_step_io_equals_the_separate_calls(device):
             b.set_state(p, v, f)
             b.step(4)
             p2, v2, f2, e2 = b.positions(), b.velocities(), b.forces(), b.energy()
-            if device:
+            if device == "pinned":
+                bufs = [torch.from_numpy(x.copy()).pin_memory() for x in (p, v, f)]
+                e1 = a.step_io(4, *bufs, *bufs)
+                p1, v1, f1 = (t.numpy() for t in bufs)
+            elif device:
                 bufs = [torch.from_numpy(x.copy()).cuda() for x in (p, v, f)]
                 e1 = a.step_io(4, *bufs, *bufs)
                 torch.cuda.synchronize()
