@@ -307,8 +307,10 @@ md_status md_step(md_ctx *ctx, int32_t n_steps);
 /* Self-test of failure detection: runs one step in which one block of the persistent
  * kernel withholds its first barrier arrival, so the other blocks' bounded wait runs out
  * (about a millisecond of polling); every block then returns and the call reports
- * MD_ERR_TIMEOUT with no fault.  Afterwards the state is not a clean step boundary
- * (positions have been drifted once); the next call recomputes forces. */
+ * MD_ERR_TIMEOUT with no fault.  When the step kernel stages cell groups (MD_PASSES_STAGED,
+ * CELLS or HALF, every group fitting), block 0's staging producer releases no group instead,
+ * so that its consumers' bounded mbarrier waits run out.  Afterwards the state is not a clean
+ * step boundary (positions have been drifted once); the next call recomputes forces. */
 md_status md_selftest_timeout(md_ctx *ctx);
 
 /* Graph mode (on = 1): md_step(n) records its device work for this n (the persistent

@@ -1681,7 +1681,12 @@ md_status md_selftest_timeout(md_ctx *ctx) {
     StepParams sp = step_params(ctx, 1);
     sp.thermo = nullptr;
     sp.spin_limit = 20000;  // ~2-5 ms of polling
-    sp.withhold_arrival = 1;
+    // a step kernel that stages cell groups (and fits them: no fallback to the list walk) tests
+    // its staging pipeline's waits instead of the grid barrier's
+    const int walk = step_walk(ctx->A, ctx->C, ctx->P, ctx->precision, ctx->lanes);
+    const bool staged = (walk == kWalkStaged || walk == kWalkCells || walk == kWalkHalf) && ctx->h_flags &&
+                        ctx->h_flags->tile_bad == 0;
+    sp.withhold_arrival = staged ? 2 : 1;
     MD_CK(reset_errors(ctx));
     int grid = 0;
     MD_CK(launch_step(ctx->A, ctx->C, ctx->P, ctx->precision, ctx->lanes, sp, ctx->d_bar, nullptr, &grid,

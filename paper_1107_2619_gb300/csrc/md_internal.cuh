@@ -324,7 +324,8 @@ struct StepParams {
     int n_ke_chunks;
     const int32_t *rep_off;  // [n_rep + 1]
     unsigned long long spin_limit;
-    int withhold_arrival;  // self-test of the bounded wait: block 0 skips its first arrival
+    int withhold_arrival;  // self-test of the bounded waits: 1, block 0 skips its first grid-barrier
+                           // arrival; 2 (group walks), block 0's staging producer releases no group
     int motion;            // kMotionVerlet or kMotionPC3: what the force pass does to each atom after
                            // its force (second half kick, or the corrector) and what opens a step
                            // (half kick + drift, or the predictor)
@@ -339,6 +340,8 @@ cudaError_t launch_step(const Atoms &A, const Cells &C, const Pot &P, int precis
                         const StepParams &sp, GridBarrier *bar, unsigned long long *stamps, int *grid_out,
                         cudaStream_t s);
 int step_grid(const Pot &P, int precision, int lanes);   // blocks of the persistent launch
+// The neighbour walk (kWalk*) of the step kernel launch_step runs for these arguments.
+int step_walk(const Atoms &A, const Cells &C, const Pot &P, int precision, int lanes);
 // The list rebuild of an md_step call between two launches of the step kernel: a cooperative
 // kernel of its own (more warps per SM than the step kernel keeps), which does nothing unless
 // the last launch stopped at a rebuild request (Flags::seg_done < sp.n_steps, need_rebuild set).

@@ -281,7 +281,9 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? (PREC == MD_PREC_DF     ?
         __syncthreads();
     }
     unsigned seq = 0;   // groups this block has taken in this launch: the pipeline's phase count
-    const tl::PassCtl ctl{sp.spin_limit, &bar->abort, A.flags};
+    // (withhold_arrival 2: block 0's staging producer releases no group, so that its consumers'
+    // bounded waits run out; the self-test of those waits)
+    const tl::PassCtl ctl{sp.spin_limit, &bar->abort, A.flags, sp.withhold_arrival == 2 && blockIdx.x == 0};
     const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
     const bool strain = sp.strain_scale != 1.0;
     Box *boxes = A.boxes;
@@ -317,7 +319,7 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? (PREC == MD_PREC_DF     ?
                           thermo ? sp.thermo : nullptr);
             if constexpr (WALK == kWalkHalf) A.rho_acc[i] = 0.0;
         }
-        if (sp.withhold_arrival && blockIdx.x == 0) {
+        if (sp.withhold_arrival == 1 && blockIdx.x == 0) {
             // self-test of the bounded wait: this block never arrives; it waits (bounded) until
             // the others have given up and marked the launch aborted, then leaves.
             if (threadIdx.x == 0) {

@@ -25,7 +25,7 @@ cudaError_t launch_step(const Atoms &A, const Cells &C, const Pot &P, int precis
 }
 
 // The walk of the step kernel launch_step runs for this context (launch_kind's choice).
-static int step_walk(const Atoms &A, const Cells &C, const Pot &P, int precision, int lanes) {
+int step_walk(const Atoms &A, const Cells &C, const Pot &P, int precision, int lanes) {
     if (precision == MD_PREC_FP64 && A.pairs) return kWalkPairs;
     if (precision == MD_PREC_MIXED && lanes <= 8 && P.kind == MD_POT_TABLES && P.ns == 1 &&
         smem_table_bytes(P.kind, P.ns, precision, P.nk) > 0 &&

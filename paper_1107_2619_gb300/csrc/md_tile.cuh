@@ -135,6 +135,7 @@ struct PassCtl {
     unsigned long long limit;   // polls of a bounded wait
     int *abort;                 // the grid barrier's abort word
     Flags *flags;
+    bool withhold;              // self-test of the bounded waits: this block's producer stages nothing
 };
 
 // Group g's geometry.
@@ -294,6 +295,7 @@ __device__ __forceinline__ bool is_producer() {
 template <int HALF_FORCE>
 __device__ __noinline__ void produce(const Atoms &A, const Cells &C, const Box &B, const float4 *src, Pipe &p,
                                      float4 *stage, float4 *accs, unsigned seq, const PassCtl &ctl) {
+    if (ctl.withhold) return;   // the consumers' waits run out; nothing is in flight
     const unsigned nbuf = (unsigned)C.nbuf, count = block_groups(C);
     unsigned held = 0, u_last[kStageBufs];
     bool ok = true;

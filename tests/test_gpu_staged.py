@@ -172,3 +172,23 @@ def test_overfull_group_falls_back_to_the_list_walk_and_back(walk):
         assert s.passes()["active"] == 1
         pos, f, img = s.positions(), s.forces(), s.get(md.MD_GET_IMAGE)
     assert_mixed_forces(wk, pos, f, img)
+
+
+@pytest.mark.parametrize("walk", ["staged", "cells", "half"])
+def test_bounded_staging_waits_report_timeout_and_recover(walk):
+    """Failure detection without a fault: block 0's staging producer releases no cell group, its
+    consumers' bounded mbarrier waits run out, the call returns MD_ERR_TIMEOUT, and the context
+    then steps as a fresh one does (the half walk to the run-to-run spread of its FP32 shared
+    atomic sums)."""
+    w = _case("cu10")
+    with md.System(w, precision="mixed", lanes_per_atom=4, passes=walk) as s, \
+            md.System(w, precision="mixed", lanes_per_atom=4, passes=walk) as ref:
+        s.eam_forces()
+        assert s.passes()["active"] == 1
+        assert md.md_selftest_timeout(s.ctx) == md.MD_ERR_TIMEOUT
+        s.set_state(pos=w.pos, vel=w.vel)
+        s.step(6)
+        ref.step(6)
+        tol = 1e-7 if walk == "half" else 1e-9
+        assert np.abs(s.positions() - ref.positions()).max() < tol
+        assert abs(s.energy()["pe"] - ref.energy()["pe"]) <= tol * abs(ref.energy()["pe"])
