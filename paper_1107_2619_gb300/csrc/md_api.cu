@@ -139,6 +139,16 @@ float ulp32(double x) {
 // and the difference once more (< ulp32(r_list)/2 near the cutoff), so each component of d is
 // within delta = 3u + ulp32(r_list)/2 of the FP64 one.  Then |r2_32 - r2_64| <= 2 sqrt(3)
 // r_list delta + 3 delta^2 plus the FP32 rounding of r^2 (< 6e-7 r_list^2).  The band is 4x.
+// The same bound for r_cut: an FP32 r^2 above rc2 + 4 bound is beyond r_cut in FP64 too.
+float cut_skin_bound(const md_ctx *c, double r_cut) {
+    double Lmax = 0.0;
+    for (double l : c->L) Lmax = std::fmax(Lmax, l);
+    const double u = ulp32(Lmax), rc2 = r_cut * r_cut;
+    const double delta = 3.0 * u + 0.5 * ulp32(r_cut);
+    const double bound = 2.0 * std::sqrt(3.0) * r_cut * delta + 3.0 * delta * delta + 6e-7 * rc2;
+    return std::nextafter((float)(rc2 + 4.0 * bound), INFINITY);
+}
+
 void list_band(const md_ctx *c, float &lo, float &hi) {
     double Lmax = 0.0;
     for (double l : c->L) Lmax = std::fmax(Lmax, l);
@@ -774,6 +784,7 @@ md_status create_common(md_ctx *ctx, const md_config *cfg, const md_potential *p
     P.ns = ns;
     P.rc2 = pot->r_cut * pot->r_cut;
     P.rc2f = (float)P.rc2;
+    P.rc2f_skin = cut_skin_bound(ctx, pot->r_cut);
     for (int k = 0; k < 7; k++) {
         P.fs[k] = pot->fs[k];
         P.fsf[k] = (float)pot->fs[k];

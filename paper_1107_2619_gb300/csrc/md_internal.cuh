@@ -67,6 +67,8 @@ struct Pot {
     int smt_phi;   // table copy in shared memory: first phi row (nk; 0 where a pass holds only its own rows)
     double rc2;
     float rc2f;
+    float rc2f_skin;   // FP32 r^2 above which a pair is beyond r_cut whatever the FP32 rounding of its
+                       // coordinates (the FP64 half list's skip of its skin entries)
     double fs[7];   // d, c, A, beta, c0, c1, c2
     float fsf[7];
     double bd;      // beta / d

@@ -924,6 +924,24 @@ __device__ __forceinline__ void density64_pairs_flat(const Atoms &A, const Pot &
                     drow = dcache_row(A, i);
                 }
                 const int j = ld_phase(row.ptr(k));
+                double2 *dc = drow.ptr(k);
+                if (seg == 1) {
+                    // the skin at the build: an FP32 test on the FP32 copies (same periodic image)
+                    // drops the pairs still beyond r_cut before any FP64 work (rc2f_skin: r_cut^2
+                    // plus 4x the bound on the FP32 error of r^2, as for the list build's band)
+                    const float4 fi = ld_phase(A.posf + i), fj = ld_phase(A.posf + j);
+                    float ex = fj.x - fi.x, ey = fj.y - fi.y, ez = fj.z - fi.z;
+                    if (W::value) {
+                        const Box &B = boxes[ph::replica_of(A, i)];
+                        ex = fmaf(-B.Lf[0], rintf(ex * B.invLf[0]), ex);
+                        ey = fmaf(-B.Lf[1], rintf(ey * B.invLf[1]), ey);
+                        ez = fmaf(-B.Lf[2], rintf(ez * B.invLf[2]), ez);
+                    }
+                    if (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) > P.rc2f_skin) {
+                        *dc = make_double2(0.0, 0.0);
+                        continue;
+                    }
+                }
                 const double4_32a pj = ld_phase(A.posd + j);
                 double dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
                 if (W::value) {
@@ -933,7 +951,6 @@ __device__ __forceinline__ void density64_pairs_flat(const Atoms &A, const Pot &
                     dz = mi64(dz, B.L[2], B.invL[2]);
                 }
                 const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-                double2 *dc = drow.ptr(k);
                 if (!inside64(r2, P.rc2)) {
                     *dc = make_double2(0.0, 0.0);
                     continue;
