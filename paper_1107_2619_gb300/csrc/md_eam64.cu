@@ -36,10 +36,10 @@ __global__ void __launch_bounds__(kThreads) k_force64(Atoms A, Pot P, double hal
 // The pair walk (A.pairs): each pair once, then the per-atom phase that needs every share.
 template <int T, int KIND>
 __global__ void __launch_bounds__(kThreads) k_density64_pairs(Atoms A, Pot P) {
-    __shared__ double sums[T >= 8 ? kThreads / 32 * ps::kPairSlots(32 / T) : 1];
+    __shared__ double sums[T >= ps::kFlatLanes ? kThreads / 32 * ps::kPairSlots(32 / T) : 1];
     clear_rebuild_once(A.flags);
     ps::density64_pairs<T, KIND>(A, P, A.boxes, (long long)blockIdx.x * kThreads + threadIdx.x, true,
-                                 sums + (T >= 8 ? (threadIdx.x >> 5) * ps::kPairSlots(32 / T) : 0));
+                                 sums + (T >= ps::kFlatLanes ? (threadIdx.x >> 5) * ps::kPairSlots(32 / T) : 0));
 }
 
 __global__ void __launch_bounds__(kThreads) k_embed64_pairs(Atoms A, Pot P) {
@@ -52,9 +52,9 @@ __global__ void __launch_bounds__(kThreads) k_force64_pairs(Atoms A, Pot P) {
     double part[kPartials];
 #pragma unroll
     for (int q = 0; q < kPartials; q++) part[q] = 0.0;
-    __shared__ double sums[T >= 8 ? kThreads / 32 * ps::kPairSlots(32 / T) : 1];
+    __shared__ double sums[T >= ps::kFlatLanes ? kThreads / 32 * ps::kPairSlots(32 / T) : 1];
     ps::force64_pairs<T, KIND, ENERGY>(A, P, A.boxes, (long long)blockIdx.x * kThreads + threadIdx.x, part,
-                                       sums + (T >= 8 ? (threadIdx.x >> 5) * ps::kPairSlots(32 / T) : 0));
+                                       sums + (T >= ps::kFlatLanes ? (threadIdx.x >> 5) * ps::kPairSlots(32 / T) : 0));
     if (ENERGY) block_partials(part, A.partials, A.part_stride);
 }
 

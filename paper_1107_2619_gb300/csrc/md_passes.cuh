@@ -827,15 +827,15 @@ __device__ __forceinline__ void force64_pairs_item(const Atoms &A, const Pot &P,
     }
 }
 
-// ---- the pair walk with the warp's rows flattened (T >= 8 lanes per atom)
+// ---- the pair walk with the warp's rows flattened (T >= kFlatLanes lanes per atom)
 // The AW = 32 / T atoms of a warp are walked as one sequence of entries, so that every lane has an
 // entry in every round but the last: first the entries j > i that lay inside r_cut at the build
 // (cin[i] of them, at the front of each row), then the rest of the entries j > i (the skin at the
 // build; their pair terms run only where the pair has since come inside r_cut).  Entry e of a
 // segment belongs to atom a with off[a] <= e < off[a + 1].  A lane's entries belong to atoms in
 // ascending order, so it keeps one running sum per quantity and adds it to its own slot of the
-// warp's shared sums S[q][a][lane] when the atom changes; the T lanes of each atom then add the
-// 32 slots of that atom (and the butterfly of the per-atom walk).  S: this warp's
+// warp's shared sums S[q][a][lane] when the atom changes (put_slot); the T lanes of each atom then
+// add the 32 slots of that atom (and the butterfly of the per-atom walk).  S: this warp's
 // kPairSlots(AW) doubles.
 template <int AW>
 struct FlatRows {
@@ -872,15 +872,26 @@ __device__ __forceinline__ FlatRows<AW> flat_rows(int c_in, int c_up, int seg) {
 }
 
 __host__ __device__ constexpr int kPairSlots(int aw) { return 3 * aw * 32; }
+// The fewest lanes per atom that take the flattened walk (at most 32 / kFlatLanes atoms a warp).
+constexpr int kFlatLanes = 4;
+
+// A lane's running sum of one atom into its slot.  A lane's entries of an atom form one run in
+// each segment and the slots start cleared, so the first segment stores the sum; the second adds
+// it only where it is not zero (a bit-pattern test: the skin segment's sums mostly are).
+__device__ __forceinline__ void put_slot(double *s, double v, int seg) {
+    if (seg == 0) *s = v;
+    else if (__double_as_longlong(v) << 1) *s += v;
+}
 
 // Atom a's sum of slot row q over the warp's 32 lanes, in the T lanes of atom a (butterfly).
 template <int T>
 __device__ __forceinline__ double flat_sum(const double *S, int q) {
     constexpr int AW = 32 / T;
     const int lane = threadIdx.x & 31, a = lane / T, l = lane & (T - 1);
-    double x = 0.0;
+    const double *row = S + (q * AW + a) * 32 + l;
+    double x = row[0];
 #pragma unroll
-    for (int m = 0; m < 32 / T; m++) x += S[(q * AW + a) * 32 + l + T * m];
+    for (int m = 1; m < 32 / T; m++) x += row[T * m];
     return lane_sum<T>(x);
 }
 
@@ -913,8 +924,8 @@ __device__ __forceinline__ void density64_pairs_flat(const Atoms &A, const Pot &
                 const int a = R.atom(e, k);
                 if (a != cur) {   // the next atom of this lane: flush the sums, load the atom
                     if (cur >= 0) {
-                        S[cur * 32 + lane] += rho;
-                        if (energy) S[(AW + cur) * 32 + lane] += ep;
+                        put_slot(S + cur * 32 + lane, rho, seg);
+                        if (energy) put_slot(S + (AW + cur) * 32 + lane, ep, seg);
                     }
                     cur = a;
                     rho = ep = 0.0;
@@ -986,8 +997,8 @@ __device__ __forceinline__ void density64_pairs_flat(const Atoms &A, const Pot &
                 *dc = make_double2(dV * rinv, dphi * rinv);
             }
             if (cur >= 0) {
-                S[cur * 32 + lane] += rho;
-                if (energy) S[(AW + cur) * 32 + lane] += ep;
+                put_slot(S + cur * 32 + lane, rho, seg);
+                if (energy) put_slot(S + (AW + cur) * 32 + lane, ep, seg);
             }
         }
     };
@@ -1035,9 +1046,9 @@ __device__ __forceinline__ void force64_pairs_flat(const Atoms &A, const Pot &P,
                 if ((__double_as_longlong(d.x) | __double_as_longlong(d.y)) == 0) continue;
                 if (a != cur) {   // the next atom of this lane: flush the sums, load the atom
                     if (cur >= 0) {
-                        S[cur * 32 + lane] += fx;
-                        S[(AW + cur) * 32 + lane] += fy;
-                        S[(2 * AW + cur) * 32 + lane] += fz;
+                        put_slot(S + cur * 32 + lane, fx, seg);
+                        put_slot(S + (AW + cur) * 32 + lane, fy, seg);
+                        put_slot(S + (2 * AW + cur) * 32 + lane, fz, seg);
                     }
                     cur = a;
                     fx = fy = fz = 0.0;
@@ -1073,9 +1084,9 @@ __device__ __forceinline__ void force64_pairs_flat(const Atoms &A, const Pot &P,
                 atomicAdd(acc + 2, neg64(gz));
             }
             if (cur >= 0) {
-                S[cur * 32 + lane] += fx;
-                S[(AW + cur) * 32 + lane] += fy;
-                S[(2 * AW + cur) * 32 + lane] += fz;
+                put_slot(S + cur * 32 + lane, fx, seg);
+                put_slot(S + (AW + cur) * 32 + lane, fy, seg);
+                put_slot(S + (2 * AW + cur) * 32 + lane, fz, seg);
             }
         }
     };
@@ -1091,18 +1102,18 @@ __device__ __forceinline__ void force64_pairs_flat(const Atoms &A, const Pot &P,
     if (me < A.n && (lane & (T - 1)) == 0) A.force[me] = make_double4_32a(fx, fy, fz, 0.0);
 }
 
-// The pair walk's passes: the flattened rows for T >= 8 lanes per atom (S: this warp's
+// The pair walk's passes: the flattened rows for T >= kFlatLanes lanes per atom (S: this warp's
 // kPairSlots(32 / T) doubles of shared memory), the per-atom rows otherwise.
 template <int T, int KIND>
 __device__ __forceinline__ void density64_pairs(const Atoms &A, const Pot &P, const Box *boxes, long long g,
                                                 bool energy, double *S) {
-    if constexpr (T >= 8) density64_pairs_flat<T, KIND>(A, P, boxes, g, energy, S);
+    if constexpr (T >= kFlatLanes) density64_pairs_flat<T, KIND>(A, P, boxes, g, energy, S);
     else density64_pairs_item<T, KIND>(A, P, boxes, g, energy);
 }
 template <int T, int KIND, bool ENERGY>
 __device__ __forceinline__ void force64_pairs(const Atoms &A, const Pot &P, const Box *boxes, long long g,
                                               double (&part)[kPartials], double *S) {
-    if constexpr (T >= 8) force64_pairs_flat<T, KIND, ENERGY>(A, P, boxes, g, part, S);
+    if constexpr (T >= kFlatLanes) force64_pairs_flat<T, KIND, ENERGY>(A, P, boxes, g, part, S);
     else force64_pairs_item<T, KIND, ENERGY>(A, P, boxes, g, part);
 }
 

@@ -250,8 +250,8 @@ __global__ void __launch_bounds__(NT, NT == kThreads ? (PREC == MD_PREC_DF     ?
     __shared__ int ws[32];
     __shared__ std::conditional_t<kGroupWalk<WALK>, tl::Pipe, int> pipe;   // the group walks' pipeline
     __shared__ uint16_t cells_q[WALK == kWalkCells ? NT / 32 : 1][kCellsQueue];
-    // the FP64 pair walk's per-warp sums (flattened rows, T >= 8)
-    constexpr int kPairSlotsW = WALK == kWalkPairs && T >= 8 ? ps::kPairSlots(32 / T) : 0;
+    // the FP64 pair walk's per-warp sums (flattened rows, T >= kFlatLanes)
+    constexpr int kPairSlotsW = WALK == kWalkPairs && T >= ps::kFlatLanes ? ps::kPairSlots(32 / T) : 0;
     __shared__ double pair_sums[kPairSlotsW > 0 ? NT / 32 * kPairSlotsW : 1];
     double *const psum = pair_sums + (threadIdx.x >> 5) * kPairSlotsW;
     extern __shared__ float4 sm_table_f4[];   // [SMT table][stage]
