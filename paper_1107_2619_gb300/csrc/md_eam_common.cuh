@@ -29,23 +29,55 @@ __device__ __forceinline__ double f64_exact(float f) {
                             : __hiloint2double((int)((b >> 3) + (896u << 20)), (int)(b << 29));
 }
 
-// 1/sqrt(x), x positive: the FP32 estimate (x truncated to FP32, then rsqrtf within 2 ulp: relative
-// error <= 3.6e-7) refined by Newton-Raphson steps in FP64 (y <- y + y (1 - x y^2) / 2), each of
-// which squares the relative error (times 3/2): one step leaves <= 2e-13, three orders of
-// magnitude inside the 1e-10 parity of the FP64 path, two reach FP64 rounding (~1e-16) for 10 %
-// more FP64 work per step (MD_RSQRT64_STEPS=2).
+// The rest x - f32_trunc(x) of a positive normal x, as FP32: its 29 low significand bits m, worth
+// m 2^(E - 52), rounded to nearest (0 where m = 0 or E < -70, below which the exponent field
+// would not hold it; the FP64 path's r^2 lie far inside).
+__device__ __forceinline__ float f32_rest(double x) {
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const unsigned m = lo & 0x1FFFFFFFu;
+    const int E = (int)(hi >> 20) - 1023;
+    const float mf = __uint2float_rn(m);
+    return (m == 0u || E < -70) ? 0.f : __int_as_float(__float_as_int(mf) + (E - 52) * (1 << 23));
+}
+// f as a double, exact, any sign: 0 for |f| below the normal FP32 range, NaN for inf or NaN.
+__device__ __forceinline__ double f64_of_f32(float f) {
+    const unsigned b = __float_as_uint(f), mag = b & 0x7fffffffu;
+    const double v = __hiloint2double((int)((b & 0x80000000u) | ((mag >> 3) + (896u << 20))), (int)(mag << 29));
+    return mag >= 0x7f800000u ? __hiloint2double(0x7ff80000, 0) : (mag < 0x00800000u ? 0.0 : v);
+}
+
+// 1/sqrt(x), x positive: the FP32 estimate y (x truncated to FP32, then rsqrtf within 2 ulp:
+// relative error eps <= 3.6e-7) and one Newton-Raphson step y + y e / 2, e = 1 - x y^2, which
+// leaves (3/2) eps^2 <= 2e-13.  The step's correction is small, so it is formed in FP32 from
+// exact pieces (Dekker's product y^2 = ph + pl; x = xf + xr split on its bit fields): 1 - xf ph
+// by one FMA (|e| < 2^-20, so rounded to within 2^-44), the rest x y^2 - xf ph to about 2^-46,
+// y e / 2 to 2^-24 of itself; e and the correction add at most 1e-13 to the relative error, <=
+// 3e-13 in all, three orders of magnitude inside the 1e-10 parity of the FP64 path, for one FP64
+// addition (the FP64 pipe bounds the FP64 passes).  Coincident atoms (x = 0) still give a
+// non-finite value.
+// MD_RSQRT64_STEPS=2: two Newton steps in FP64 instead, to FP64 rounding (~1e-16).
 #ifndef MD_RSQRT64_STEPS
 #define MD_RSQRT64_STEPS 1
 #endif
 __device__ __forceinline__ double rsqrt64(double x) {
+#if MD_RSQRT64_STEPS >= 2
     // y / 2 by the exponent field (y is positive and normal, or +inf: then e is NaN either way)
     auto half = [](double y) { return __longlong_as_double(__double_as_longlong(y) - (1LL << 52)); };
     double y = f64_exact(rsqrtf(f32_trunc(x)));
-    double e = fma(-x * y, y, 1.0);
-    y = fma(half(y), e, y);
-    if (MD_RSQRT64_STEPS < 2) return y;
-    e = fma(-x * y, y, 1.0);
-    return fma(half(y), e, y);
+    for (int s = 0; s < 2; s++) {
+        const double e = fma(-x * y, y, 1.0);
+        y = fma(half(y), e, y);
+    }
+    return y;
+#else
+    const float xf = f32_trunc(x), xr = f32_rest(x);
+    const float y = rsqrtf(xf);
+    const float ph = __fmul_rn(y, y), pl = __fmaf_rn(y, y, -ph);   // y^2 = ph + pl exactly
+    const float a = __fmaf_rn(-xf, ph, 1.0f);                     // 1 - xf ph, one rounding
+    const float b = __fmaf_rn(xf, pl, __fmul_rn(xr, ph));         // x y^2 - xf ph (xr pl dropped)
+    const float h = __fmul_rn(__fmul_rn(0.5f, y), __fsub_rn(a, b));  // y e / 2
+    return f64_exact(y) + f64_of_f32(h);
+#endif
 }
 
 // Error-free FP32 accumulation (Knuth's TwoSum): hi + lo carries the exact running sum.
@@ -78,10 +110,6 @@ __device__ __forceinline__ int knot_row(R x, int nk, R &t, bool &below) {
 // comparisons and the conversions between double and int act on the IEEE bit patterns in integer
 // registers (non-negative doubles order as their bit patterns do), which leaves the FP64 pipe to
 // the arithmetic.
-// -x by the sign bit.
-__device__ __forceinline__ double neg64(double x) {
-    return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ULL);
-}
 // r2 < rc2 for r2 >= 0 (or NaN, which is never inside) and rc2 > 0.
 __device__ __forceinline__ bool inside64(double r2, double rc2) {
     return __double_as_longlong(r2) < __double_as_longlong(rc2);

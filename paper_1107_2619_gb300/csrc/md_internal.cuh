@@ -141,8 +141,9 @@ struct Atoms {
     double2 *dcache;                         // FP64 path, one species: per list entry (same plane layout
                                              // as nbr) the radial factors of the pair force, (V'(r) / r,
                                              // phi'(r) / r), written by the density pass and read by
-                                             // the force passes that need no energy; (0, 0) beyond
-                                             // r_cut.  NULL: not kept
+                                             // the force passes that need no energy (the pair walk:
+                                             // both negated, read by every force pass); (0, 0)
+                                             // beyond r_cut.  NULL: not kept
     uint8_t *wrap;                           // 1: the atom's link cell is on the box boundary at the
                                              // last build (some neighbour cell is a periodic image)
     int image_fixed;                         // 1: no strain ramp, so posf/p2f stay in the periodic

@@ -26,15 +26,24 @@ using namespace eam;
 
 __device__ __forceinline__ float mi32(float d, float L, float invL) { return fmaf(-L, rintf(d * invL), d); }
 // The FP64 passes' minimum image, for separations of coordinates kept in one periodic image of
-// the box (|d| < 3L/2): d - L rint(d / L) as one addition of -L, 0 or +L, chosen on the bit
-// patterns in integer registers (|d| > L/2, L/2 by the exponent field).  Where |d / L| rounds to
-// exactly 1/2 the choice may differ from rint's, but such a pair is L/2 apart, far beyond r_list,
-// either way.
+// the box (|d| < 3L/2): d - L rint(d / L) as one subtraction of L with the sign of d, or of 0,
+// chosen and signed on the bit patterns in integer registers (|d| > L/2, L/2 by the exponent
+// field), so that the FP64 pipe does the one subtraction only.  Where |d / L| rounds to exactly
+// 1/2 the choice may differ from rint's, but such a pair is L/2 apart, far beyond r_list, either
+// way.
 __device__ __forceinline__ double mi64(double d, double L, double) {
     const long long b = __double_as_longlong(d);
     const bool far = (b & 0x7FFFFFFFFFFFFFFFLL) > __double_as_longlong(L) - (1LL << 52);
-    const double s = far ? (b < 0 ? L : neg64(L)) : 0.0;
-    return d + s;
+    const long long sL = __double_as_longlong(L) | (b & (long long)0x8000000000000000ULL);   // L, sign of d
+    return d - (far ? __longlong_as_double(sL) : 0.0);
+}
+
+// A knot row's cubic at t, continued linearly below the first knot (cubic() with `below`): there
+// c2 and c3 are taken as 0, chosen in integer registers, so the linear branch costs no second
+// evaluation on the FP64 pipe (fma(t, 0, 0) = 0 and fma(t, 0, c1) = c1 exactly).
+__device__ __forceinline__ double cubic64(double t, const double4_32a &c, bool below) {
+    const double c2 = below ? 0.0 : c.z, c3 = below ? 0.0 : c.w;
+    return fma(t, fma(t, fma(t, c3, c2), c.y), c.x);
 }
 
 // The minimum image of a separation, or the separation itself for an atom whose link cell was not
@@ -714,18 +723,18 @@ __device__ __forceinline__ void density64_pairs_item(const Atoms &A, const Pot &
                     V = fs_V<double>(P.fs, r, dV);
                     dphi = fs_dphi<double>(P.fs, P.bd, r);
                 } else {
-                    double t, d;
+                    double t;
                     bool below;
                     const int kr = knot_row64(fma(r, P.inv_dr, P.xneg), P.nk, P.xtop, t, below);
                     if (below) atomicAdd(&A.flags->range_violations, 1ull);
                     const double4_32a c = P.VP64[(size_t)kr * 2 + 1];
-                    phi = cubic(t, c.x, c.y, c.z, c.w, below, d);
+                    phi = cubic64(t, c, below);
                     const double4_32a dv = P.D64[2 * kr], dp = P.D64[2 * kr + 1];
                     dV = below ? dv.x : fma(t, fma(dv.z, t, dv.y), dv.x);
                     dphi = below ? dp.x : fma(t, fma(dp.z, t, dp.y), dp.x);
                     if (energy) {
                         const double4_32a cv = P.VP64[(size_t)kr * 2];
-                        V = cubic(t, cv.x, cv.y, cv.z, cv.w, below, d);
+                        V = cubic64(t, cv, below);
                     }
                 }
                 rho += phi;
@@ -734,7 +743,7 @@ __device__ __forceinline__ void density64_pairs_item(const Atoms &A, const Pot &
                     ep = fma(0.5, V, ep);
                     atomicAdd(A.e_acc + j, 0.5 * V);
                 }
-                *drow.ptr(k) = make_double2(dV * rinv, dphi * rinv);
+                *drow.ptr(k) = make_double2(-dV * rinv, -dphi * rinv);   // negated (the force pass needs -g)
             }
         };
         if (wrap) walk(std::true_type{});
@@ -789,23 +798,24 @@ __device__ __forceinline__ void force64_pairs_item(const Atoms &A, const Pot &P,
                 const double dx = sep64<W>(pj.x - pi.x, B.L[0], B.invL[0]);
                 const double dy = sep64<W>(pj.y - pi.y, B.L[1], B.invL[1]);
                 const double dz = sep64<W>(pj.z - pi.z, B.L[2], B.invL[2]);
-                const double gr = fma(pi.w + pj.w, e.y, e.x);
-                const double gx = gr * dx, gy = gr * dy, gz = gr * dz;
-                fx += gx;
-                fy += gy;
-                fz += gz;
+                // -g d, the neighbour's share, from the negated radial factors (no negation)
+                const double ngr = fma(pi.w + pj.w, e.y, e.x);
+                const double ngx = ngr * dx, ngy = ngr * dy, ngz = ngr * dz;
+                fx -= ngx;
+                fy -= ngy;
+                fz -= ngz;
                 if (ENERGY) {   // the pair's whole virial, once (its energy is in E_i and E_j)
-                    wxx = fma(-gx, dx, wxx);
-                    wyy = fma(-gy, dy, wyy);
-                    wzz = fma(-gz, dz, wzz);
-                    wyz = fma(-gy, dz, wyz);
-                    wxz = fma(-gx, dz, wxz);
-                    wxy = fma(-gx, dy, wxy);
+                    wxx = fma(ngx, dx, wxx);
+                    wyy = fma(ngy, dy, wyy);
+                    wzz = fma(ngz, dz, wzz);
+                    wyz = fma(ngy, dz, wyz);
+                    wxz = fma(ngx, dz, wxz);
+                    wxy = fma(ngx, dy, wxy);
                 }
                 double *acc = reinterpret_cast<double *>(A.f_acc + j);
-                atomicAdd(acc, neg64(gx));
-                atomicAdd(acc + 1, neg64(gy));
-                atomicAdd(acc + 2, neg64(gz));
+                atomicAdd(acc, ngx);
+                atomicAdd(acc + 1, ngy);
+                atomicAdd(acc + 2, ngz);
             }
         };
         if (wrap) walk(std::true_type{});
@@ -974,18 +984,18 @@ __device__ __forceinline__ void density64_pairs_flat(const Atoms &A, const Pot &
                     V = fs_V<double>(P.fs, r, dV);
                     dphi = fs_dphi<double>(P.fs, P.bd, r);
                 } else {
-                    double t, d;
+                    double t;
                     bool below;
                     const int kr = knot_row64(fma(r, P.inv_dr, P.xneg), P.nk, P.xtop, t, below);
                     if (below) atomicAdd(&A.flags->range_violations, 1ull);
                     const double4_32a c = P.VP64[(size_t)kr * 2 + 1];
-                    phi = cubic(t, c.x, c.y, c.z, c.w, below, d);
+                    phi = cubic64(t, c, below);
                     const double4_32a dv = P.D64[2 * kr], dp = P.D64[2 * kr + 1];
                     dV = below ? dv.x : fma(t, fma(dv.z, t, dv.y), dv.x);
                     dphi = below ? dp.x : fma(t, fma(dp.z, t, dp.y), dp.x);
                     if (energy) {
                         const double4_32a cv = P.VP64[(size_t)kr * 2];
-                        V = cubic(t, cv.x, cv.y, cv.z, cv.w, below, d);
+                        V = cubic64(t, cv, below);
                     }
                 }
                 rho += phi;
@@ -994,7 +1004,7 @@ __device__ __forceinline__ void density64_pairs_flat(const Atoms &A, const Pot &
                     ep = fma(0.5, V, ep);
                     atomicAdd(A.e_acc + j, 0.5 * V);
                 }
-                *dc = make_double2(dV * rinv, dphi * rinv);
+                *dc = make_double2(-dV * rinv, -dphi * rinv);   // negated (the force pass needs -g)
             }
             if (cur >= 0) {
                 put_slot(S + cur * 32 + lane, rho, seg);
@@ -1037,11 +1047,13 @@ __device__ __forceinline__ void force64_pairs_flat(const Atoms &A, const Pot &P,
             int cur = -1, i = 0;
             double fx = 0.0, fy = 0.0, fz = 0.0;
             double4_32a pi = make_double4_32a(0.0, 0.0, 0.0, 0.0);
-            NbrRow row{nullptr, 0};
             for (int e = lane; e < R.off[AW]; e += 32) {
                 int k;
                 const int a = R.atom(e, k);
+                // the entry's radial factors and its neighbour index, both loaded before either is
+                // used (one memory latency for the two)
                 const double2 d = ld_phase(dcache_row(A, i0 + a).ptr(k));
+                const int j = ld_phase(nbr_row(A, i0 + a).ptr(k));
                 // beyond r_cut: nothing to add (the skin segment mostly ends here)
                 if ((__double_as_longlong(d.x) | __double_as_longlong(d.y)) == 0) continue;
                 if (a != cur) {   // the next atom of this lane: flush the sums, load the atom
@@ -1054,9 +1066,7 @@ __device__ __forceinline__ void force64_pairs_flat(const Atoms &A, const Pot &P,
                     fx = fy = fz = 0.0;
                     i = i0 + a;
                     pi = ld_phase(A.p2d + i);
-                    row = nbr_row(A, i);
                 }
-                const int j = ld_phase(row.ptr(k));
                 const double4_32a pj = ld_phase(A.p2d + j);
                 double dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
                 if (W::value) {
@@ -1065,23 +1075,24 @@ __device__ __forceinline__ void force64_pairs_flat(const Atoms &A, const Pot &P,
                     dy = mi64(dy, B.L[1], B.invL[1]);
                     dz = mi64(dz, B.L[2], B.invL[2]);
                 }
-                const double gr = fma(pi.w + pj.w, d.y, d.x);
-                const double gx = gr * dx, gy = gr * dy, gz = gr * dz;
-                fx += gx;
-                fy += gy;
-                fz += gz;
+                // -g d, the neighbour's share, from the negated radial factors (no negation)
+                const double ngr = fma(pi.w + pj.w, d.y, d.x);
+                const double ngx = ngr * dx, ngy = ngr * dy, ngz = ngr * dz;
+                fx -= ngx;
+                fy -= ngy;
+                fz -= ngz;
                 if (ENERGY) {   // the pair's whole virial, once (its energy is in E_i and E_j)
-                    wxx = fma(-gx, dx, wxx);
-                    wyy = fma(-gy, dy, wyy);
-                    wzz = fma(-gz, dz, wzz);
-                    wyz = fma(-gy, dz, wyz);
-                    wxz = fma(-gx, dz, wxz);
-                    wxy = fma(-gx, dy, wxy);
+                    wxx = fma(ngx, dx, wxx);
+                    wyy = fma(ngy, dy, wyy);
+                    wzz = fma(ngz, dz, wzz);
+                    wyz = fma(ngy, dz, wyz);
+                    wxz = fma(ngx, dz, wxz);
+                    wxy = fma(ngx, dy, wxy);
                 }
                 double *acc = reinterpret_cast<double *>(A.f_acc + j);
-                atomicAdd(acc, neg64(gx));
-                atomicAdd(acc + 1, neg64(gy));
-                atomicAdd(acc + 2, neg64(gz));
+                atomicAdd(acc, ngx);
+                atomicAdd(acc + 1, ngy);
+                atomicAdd(acc + 2, ngz);
             }
             if (cur >= 0) {
                 put_slot(S + cur * 32 + lane, fx, seg);
