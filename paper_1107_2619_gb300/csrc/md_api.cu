@@ -797,7 +797,6 @@ md_status create_common(md_ctx *ctx, const md_config *cfg, const md_potential *p
         const int nk = pot->n_knots;
         P.nk = nk;
         P.smt_phi = nk;
-        P.xtop = (double)(nk - 1);
         P.r_min = pot->r_min;
         P.inv_dr = (nk - 1) / (pot->r_cut - pot->r_min);
         P.xneg = -(pot->r_min * P.inv_dr);

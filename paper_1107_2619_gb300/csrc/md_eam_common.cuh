@@ -114,25 +114,25 @@ __device__ __forceinline__ int knot_row(R x, int nk, R &t, bool &below) {
 __device__ __forceinline__ bool inside64(double r2, double rc2) {
     return __double_as_longlong(r2) < __double_as_longlong(rc2);
 }
-// k as a double, 0 <= k < 2^31, exact: the leading bit sets the exponent, the rest the fraction.
-__device__ __forceinline__ double f64_of_count(int k) {
-    const int p = 31 - __clz(k | 1);
-    const long long frac = ((long long)k << (52 - p)) & 0xFFFFFFFFFFFFFLL;
-    const long long bits = ((long long)(1023 + p) << 52) | frac;
-    return k == 0 ? 0.0 : __longlong_as_double(bits);
-}
-// knot_row<double>(x, nk, t, below) for finite x; xtop = nk - 1 as a double.
-__device__ __forceinline__ int knot_row64(double x, int nk, double xtop, double &t, bool &below) {
+// knot_row<double>(x, nk, t, below) for finite x < nk, which holds for every pair inside r_cut
+// (the last knot): k = min(floor(x), nk - 1) from the significand, and t = x - floor(x) (exactly
+// x - k, as x - k is exact) from the fraction's bits, normalised in integer registers, so that the
+// knot interval and its coordinate take no FP64 operation.
+__device__ __forceinline__ int knot_row64(double x, int nk, double &t, bool &below) {
     const long long b = __double_as_longlong(x);
     below = b < 0;   // x < 0 (x = -0 gives the same values either way)
-    const bool top = b >= __double_as_longlong(xtop);
     const int e = (int)((b >> 52) & 0x7ff) - 1023;   // x >= 1: floor(x) = significand >> (52 - e)
     const long long sig = (b & 0xFFFFFFFFFFFFFLL) | 0x10000000000000LL;
-    int k = e < 0 ? 0 : (int)(sig >> (52 - min(e, 52)));
-    k = top ? nk - 1 : k;
-    k = below ? 0 : k;
-    t = below ? x : x - f64_of_count(k);
-    return k;
+    const int sh = 52 - min(max(e, 0), 52);           // bits below the binary point (e >= 0)
+    const long long fb = sig & ((1LL << sh) - 1);     // the fraction, fb 2^(e - 52)
+    const int p = 63 - __clzll(fb | 1);               // its leading bit
+    const long long tb = ((long long)(1023 + e - 52 + p) << 52) | ((fb << (52 - p)) & 0xFFFFFFFFFFFFFLL);
+    // e >= 31 (x >= 2^31: only a NaN or infinite x, from coincident atoms): the last row, and t = x
+    // carries the non-finite value on
+    const bool huge = e >= 31;
+    const int k = e < 0 ? 0 : (huge ? nk - 1 : min((int)(sig >> sh), nk - 1));
+    t = (below || e < 0 || huge) ? x : (fb == 0 ? 0.0 : __longlong_as_double(tb));
+    return below ? 0 : k;
 }
 
 template <typename R>

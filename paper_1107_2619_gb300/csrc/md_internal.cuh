@@ -74,7 +74,6 @@ struct Pot {
     double bd;      // beta / d
     float bdf;
     double r_min, inv_dr, rho_min, inv_drho;
-    double xtop;    // nk - 1 (the last knot interval's index as a double)
     double xneg;    // -r_min inv_dr: the knot coordinate of r is fma(r, inv_dr, xneg)
     float r_minf, inv_drf;
     const double4_32a *VP64;  // [((a*ns+b)*nk + k)*2 + {0: V, 1: phi_ab}]

@@ -455,7 +455,7 @@ __device__ __forceinline__ void density64_item(const Atoms &A, const Pot &P, con
                     const int sj = MULTI ? (int)pj.w : 0;
                     double t, d;
                     bool below;
-                    const int kr = knot_row64(fma(r, P.inv_dr, P.xneg), P.nk, P.xtop, t, below);
+                    const int kr = knot_row64(fma(r, P.inv_dr, P.xneg), P.nk, t, below);
                     if (below) atomicAdd(&A.flags->range_violations, 1ull);
                     const size_t ab = ((size_t)(si * P.ns + sj) * P.nk + kr) * 2;
                     const double4_32a c = P.VP64[ab + 1];
@@ -615,7 +615,7 @@ __device__ __forceinline__ int force64_item(const Atoms &A, const Pot &P, const 
                     const int sj = MULTI ? ld_phase(A.spec + j) : 0;
                     double t;
                     bool below;
-                    const int kr = knot_row64(fma(r, P.inv_dr, P.xneg), P.nk, P.xtop, t, below);
+                    const int kr = knot_row64(fma(r, P.inv_dr, P.xneg), P.nk, t, below);
                     if (below) atomicAdd(&A.flags->range_violations, 1ull);
                     const size_t ab = ((size_t)(si * P.ns + sj) * P.nk + kr) * 2;
                     const double4_32a cv = P.VP64[ab], cp = P.VP64[ab + 1];
@@ -725,7 +725,7 @@ __device__ __forceinline__ void density64_pairs_item(const Atoms &A, const Pot &
                 } else {
                     double t;
                     bool below;
-                    const int kr = knot_row64(fma(r, P.inv_dr, P.xneg), P.nk, P.xtop, t, below);
+                    const int kr = knot_row64(fma(r, P.inv_dr, P.xneg), P.nk, t, below);
                     if (below) atomicAdd(&A.flags->range_violations, 1ull);
                     const double4_32a c = P.VP64[(size_t)kr * 2 + 1];
                     phi = cubic64(t, c, below);
@@ -986,7 +986,7 @@ __device__ __forceinline__ void density64_pairs_flat(const Atoms &A, const Pot &
                 } else {
                     double t;
                     bool below;
-                    const int kr = knot_row64(fma(r, P.inv_dr, P.xneg), P.nk, P.xtop, t, below);
+                    const int kr = knot_row64(fma(r, P.inv_dr, P.xneg), P.nk, t, below);
                     if (below) atomicAdd(&A.flags->range_violations, 1ull);
                     const double4_32a c = P.VP64[(size_t)kr * 2 + 1];
                     phi = cubic64(t, c, below);
