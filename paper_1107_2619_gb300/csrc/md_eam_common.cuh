@@ -46,6 +46,44 @@ __device__ __forceinline__ double f64_of_f32(float f) {
     return mag >= 0x7f800000u ? __hiloint2double(0x7ff80000, 0) : (mag < 0x00800000u ? 0.0 : v);
 }
 
+// d = dh + dl for any sign: dh = d truncated to FP32, dl the rest rounded to FP32 (|dl| < 2^-23
+// |dh|, relative rounding 2^-24), both on the bit fields in integer registers; 0 and 0 where |d|
+// lies below FP32's normal range.
+__device__ __forceinline__ void split64(double d, float &dh, float &dl) {
+    const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+    const unsigned mag = hi & 0x7fffffffu, sgn = hi & 0x80000000u;
+    const bool tiny = mag < (897u << 20);
+    dh = __uint_as_float(tiny ? 0u : (sgn | ((mag - (896u << 20)) << 3) | (lo >> 29)));
+    const float r = f32_rest(__hiloint2double((int)mag, (int)lo));
+    dl = tiny ? 0.f : __uint_as_float(__float_as_uint(r) | sgn);
+}
+// dx^2 + dy^2 + dz^2 from FP32 pieces: each square as Dekker's exact product of the high part
+// plus the cross term 2 dh dl in FP32 (dl^2, below 2^-46 of the square, dropped), the three
+// exact high products summed exactly by Knuth's two-sum and the small terms (at most 2^-21.7 of
+// the sum) in FP32, then one FP64 addition.  Worst-case relative error 1.7e-13 (the six FP32
+// roundings of the small terms, 2^-24 of them each, and the replaced and dropped parts of the
+// squares), so that 1/r from it and rsqrt64 stays within 4e-13.
+__device__ __forceinline__ double r2_split(double dx, double dy, double dz) {
+    float xh, xl, yh, yl, zh, zl;
+    split64(dx, xh, xl);
+    split64(dy, yh, yl);
+    split64(dz, zh, zl);
+    const float px = __fmul_rn(xh, xh), py = __fmul_rn(yh, yh), pz = __fmul_rn(zh, zh);
+    float e = __fmaf_rn(xh, xh, -px);   // the products' low parts and the cross terms
+    e = __fadd_rn(e, __fmaf_rn(yh, yh, -py));
+    e = __fadd_rn(e, __fmaf_rn(zh, zh, -pz));
+    e = __fmaf_rn(__fmul_rn(2.f, xh), xl, e);
+    e = __fmaf_rn(__fmul_rn(2.f, yh), yl, e);
+    e = __fmaf_rn(__fmul_rn(2.f, zh), zl, e);
+    float s = __fadd_rn(px, py);        // px + py + pz = s2 + c exactly
+    float bb = __fsub_rn(s, px);
+    float c = __fadd_rn(__fsub_rn(px, __fsub_rn(s, bb)), __fsub_rn(py, bb));
+    const float s2 = __fadd_rn(s, pz);
+    bb = __fsub_rn(s2, s);
+    c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, __fsub_rn(s2, bb)), __fsub_rn(pz, bb)));
+    return f64_of_f32(s2) + f64_of_f32(__fadd_rn(c, e));
+}
+
 // 1/sqrt(x), x positive: the FP32 estimate y (x truncated to FP32, then rsqrtf within 2 ulp:
 // relative error eps <= 3.6e-7) and one Newton-Raphson step y + y e / 2, e = 1 - x y^2, which
 // leaves (3/2) eps^2 <= 2e-13.  The step's correction is small, so it is formed in FP32 from

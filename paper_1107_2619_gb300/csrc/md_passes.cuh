@@ -971,7 +971,7 @@ __device__ __forceinline__ void density64_pairs_flat(const Atoms &A, const Pot &
                     dy = mi64(dy, B.L[1], B.invL[1]);
                     dz = mi64(dz, B.L[2], B.invL[2]);
                 }
-                const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+                const double r2 = r2_split(dx, dy, dz);   // FP32 pieces, one FP64 addition
                 if (!inside64(r2, P.rc2)) {
                     *dc = make_double2(0.0, 0.0);
                     continue;
