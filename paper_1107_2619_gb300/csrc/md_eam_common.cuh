@@ -48,12 +48,13 @@ __device__ __forceinline__ double f64_of_f32(float f) {
 
 // d = dh + dl for any sign: dh = d truncated to FP32, dl the rest rounded to FP32 (|dl| < 2^-23
 // |dh|, relative rounding 2^-24), both on the bit fields in integer registers; 0 and 0 where |d|
-// lies below FP32's normal range.
+// lies below FP32's normal range, and a NaN dh where |d| >= 2^128 or d is not finite.
 __device__ __forceinline__ void split64(double d, float &dh, float &dl) {
     const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
     const unsigned mag = hi & 0x7fffffffu, sgn = hi & 0x80000000u;
     const bool tiny = mag < (897u << 20);
-    dh = __uint_as_float(tiny ? 0u : (sgn | ((mag - (896u << 20)) << 3) | (lo >> 29)));
+    const unsigned h = mag >= (1151u << 20) ? 0x7fc00000u : ((mag - (896u << 20)) << 3) | (lo >> 29);
+    dh = __uint_as_float(tiny ? 0u : (sgn | h));
     const float r = f32_rest(__hiloint2double((int)mag, (int)lo));
     dl = tiny ? 0.f : __uint_as_float(__float_as_uint(r) | sgn);
 }
