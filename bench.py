@@ -83,7 +83,7 @@ def fp64_flop_per_step(sum_counts, w):
     return sum_counts * (f_in * FP64_FLOP_IN + (1.0 - f_in) * FP64_FLOP_SHELL)
 
 
-def fp64_peak(md, stream, repeats=3, iters=20000):
+def fp64_peak(md, stream, repeats=3, iters=5000):
     """Best of `repeats` runs of the library's FP64 FMA-chain kernel (md_measure_fp64_peak)."""
     return max(md.md_measure_fp64_peak(iters, stream)[0] for _ in range(repeats))
 

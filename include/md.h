@@ -112,7 +112,11 @@ typedef struct {
     int32_t k_max;         /* `nnbrs`: list capacity per atom */
     int32_t rebuild_every; /* `nbrupdate`: rebuild every n steps; 0 = only when needed */
     double dt_fs;          /* `deltat` */
-    int32_t precision;     /* MD_PREC_FP64, or MD_PREC_MIXED (FP32 pair/density terms,
+    int32_t precision;     /* MD_PREC_FP64 (every sum, the integration and the reductions in
+                              FP64; of the pair terms, 1/r and, in the half list's density
+                              pass, r^2 are formed to FP64 accuracy from exact FP32 pieces,
+                              relative error <= 4e-13, the rest is FP64 arithmetic), or
+                              MD_PREC_MIXED (FP32 pair/density terms,
                               FP64 positions, velocities, density sum and reductions; with
                               one species and knot tables the force pass takes the quadratic
                               and cubic coefficients of each table cubic's derivative as
@@ -188,8 +192,9 @@ enum { MD_INTEGRATOR_VERLET = 0, MD_INTEGRATOR_PC3 = 1 };
  * reorders every row so that its entries j > i (cell order) come first, each pass computes every
  * pair once from those entries and adds the neighbour's share of rho, force and pair energy to
  * FP64 accumulators with atomic adds, and F(rho) and the kick follow in phases of their own.
- * Results equal LIST's to FP64 rounding; the order of the atomic adds, and so the last bits,
- * varies from run to run.  AUTO = LIST (on GB300, fcc Cu 500,000 atoms with its 5,000-knot
+ * Results agree with LIST's to about 1e-12 (relative; r^2 in its density pass comes from FP32
+ * pieces, see `precision`); the order of the atomic adds, and so the last bits, varies from run
+ * to run.  AUTO = LIST (on GB300, fcc Cu 500,000 atoms with its 5,000-knot
  * table: LIST 0.58 ms per step, STAGED 0.67, HALF 1.40, CELLS 2.75; STAGED's passes take about
  * as long as LIST's, its list build longer); a group walk where it does not apply is MD_ERR_ARG
  * at md_create.
