@@ -141,9 +141,14 @@ __device__ __forceinline__ void thermo_update(const StepParams &sp, int n_rep, l
 #define MD_STEP_MIN_BLOCKS 8
 #endif
 // Blocks of 128 threads per SM the FP64 step kernel is built for: 4 (128 registers) measured 2-3 %
-// faster than 8 (64 registers, with spills) and 6 on fcc Cu 500k, both list walks.
+// faster than 8 (64 registers, with spills) and 6 on fcc Cu 500k with the full list; the pair
+// walk over the half list is built for 5 (96 registers): 2.80 -> 2.74 ms per step against 4, 2.86
+// at 6 (the full list at 5: 4.79 -> 4.89).
 #ifndef MD_STEP_MIN_BLOCKS_FP64
 #define MD_STEP_MIN_BLOCKS_FP64 4
+#endif
+#ifndef MD_STEP_MIN_BLOCKS_PAIRS
+#define MD_STEP_MIN_BLOCKS_PAIRS 5
 #endif
 
 // The walks over cell groups staged in shared memory (md_tile.cuh).
@@ -242,9 +247,10 @@ __device__ __forceinline__ bool rebuild_phases(const Atoms &A, const Cells &C, B
 // density pass and the kicks after the force pass (each waits for every group's shares).
 
 template <int PREC, int T, int KIND, bool MULTI, int NT, bool SMT, int WALK>
-__global__ void __launch_bounds__(NT, NT == kThreads ? (PREC == MD_PREC_DF     ? MD_STEP_MIN_BLOCKS_DF
-                                                        : PREC == MD_PREC_FP64 ? MD_STEP_MIN_BLOCKS_FP64
-                                                                               : MD_STEP_MIN_BLOCKS)
+__global__ void __launch_bounds__(NT, NT == kThreads ? (PREC == MD_PREC_DF       ? MD_STEP_MIN_BLOCKS_DF
+                                                        : WALK == kWalkPairs     ? MD_STEP_MIN_BLOCKS_PAIRS
+                                                        : PREC == MD_PREC_FP64   ? MD_STEP_MIN_BLOCKS_FP64
+                                                                                 : MD_STEP_MIN_BLOCKS)
                                                       : 1)
     k_step(Atoms A, Cells C, Pot P, StepParams sp, GridBarrier *bar, unsigned long long *stamps) {
     __shared__ int ws[32];
