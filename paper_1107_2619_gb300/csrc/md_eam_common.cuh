@@ -149,6 +149,11 @@ __device__ __forceinline__ int knot_row(R x, int nk, R &t, bool &below) {
 // comparisons and the conversions between double and int act on the IEEE bit patterns in integer
 // registers (non-negative doubles order as their bit patterns do), which leaves the FP64 pipe to
 // the arithmetic.
+// v / 2 by the exponent field (no FP64 operation); |v| below 2^-1021 (a subnormal half) gives 0.
+__device__ __forceinline__ double half64(double v) {
+    const long long b = __double_as_longlong(v);
+    return (b & 0x7FF0000000000000LL) > (1LL << 52) ? __longlong_as_double(b - (1LL << 52)) : 0.0;
+}
 // r2 < rc2 for r2 >= 0 (or NaN, which is never inside) and rc2 > 0.
 __device__ __forceinline__ bool inside64(double r2, double rc2) {
     return __double_as_longlong(r2) < __double_as_longlong(rc2);

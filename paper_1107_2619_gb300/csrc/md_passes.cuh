@@ -31,11 +31,41 @@ __device__ __forceinline__ float mi32(float d, float L, float invL) { return fma
 // field), so that the FP64 pipe does the one subtraction only.  Where |d / L| rounds to exactly
 // 1/2 the choice may differ from rint's, but such a pair is L/2 apart, far beyond r_list, either
 // way.
-__device__ __forceinline__ double mi64(double d, double L, double) {
+__device__ __forceinline__ double mi64s(double d, double L, double &shift) {
     const long long b = __double_as_longlong(d);
     const bool far = (b & 0x7FFFFFFFFFFFFFFFLL) > __double_as_longlong(L) - (1LL << 52);
     const long long sL = __double_as_longlong(L) | (b & (long long)0x8000000000000000ULL);   // L, sign of d
-    return d - (far ? __longlong_as_double(sL) : 0.0);
+    shift = far ? __longlong_as_double(sL) : 0.0;
+    return d - shift;
+}
+__device__ __forceinline__ double mi64(double d, double L, double) {
+    double s;
+    return mi64s(d, L, s);
+}
+// The image shift s = d_raw - d of one pair (zero off the box boundary), for the virial.
+template <typename WRAP>
+__device__ __forceinline__ double sep64s(double d, double L, double &s) {
+    if (WRAP::value) return mi64s(d, L, s);
+    s = 0.0;
+    return d;
+}
+
+// The pair walk's virial (energy steps).  With d = x_j - x_i - s (s the image shift) and -g d
+// the neighbour's share, sum over pairs d_a (-g d)_b equals sum over atoms x_a F_b (the kick
+// phase adds it, from the force on each atom) minus sum over pairs s_a (-g d)_b, which only pairs
+// across the box boundary have: so each pair adds nothing, and those six products only where s
+// is not zero.
+__device__ __forceinline__ void virial_shift(double sx, double sy, double sz, double ngx, double ngy, double ngz,
+                                             double &wxx, double &wyy, double &wzz, double &wyz, double &wxz,
+                                             double &wxy) {
+    if ((__double_as_longlong(sx) | __double_as_longlong(sy) | __double_as_longlong(sz)) << 1) {
+        wxx = fma(-sx, ngx, wxx);
+        wyy = fma(-sy, ngy, wyy);
+        wzz = fma(-sz, ngz, wzz);
+        wyz = fma(-sy, ngz, wyz);
+        wxz = fma(-sx, ngz, wxz);
+        wxy = fma(-sx, ngy, wxy);
+    }
 }
 
 // A knot row's cubic at t, continued linearly below the first knot (cubic() with `below`): there
@@ -740,8 +770,9 @@ __device__ __forceinline__ void density64_pairs_item(const Atoms &A, const Pot &
                 rho += phi;
                 atomicAdd(A.rho_acc + j, phi);
                 if (energy) {   // each atom of the pair gets half its pair energy
-                    ep = fma(0.5, V, ep);
-                    atomicAdd(A.e_acc + j, 0.5 * V);
+                    const double hV = half64(V);
+                    ep += hV;
+                    atomicAdd(A.e_acc + j, hV);
                 }
                 *drow.ptr(k) = make_double2(-dV * rinv, -dphi * rinv);   // negated (the force pass needs -g)
             }
@@ -795,23 +826,17 @@ __device__ __forceinline__ void force64_pairs_item(const Atoms &A, const Pot &P,
                 if ((__double_as_longlong(e.x) | __double_as_longlong(e.y)) == 0) continue;
                 const int j = ld_phase(row.ptr(k));
                 const double4_32a pj = ld_phase(A.p2d + j);
-                const double dx = sep64<W>(pj.x - pi.x, B.L[0], B.invL[0]);
-                const double dy = sep64<W>(pj.y - pi.y, B.L[1], B.invL[1]);
-                const double dz = sep64<W>(pj.z - pi.z, B.L[2], B.invL[2]);
+                double sx, sy, sz;
+                const double dx = sep64s<W>(pj.x - pi.x, B.L[0], sx);
+                const double dy = sep64s<W>(pj.y - pi.y, B.L[1], sy);
+                const double dz = sep64s<W>(pj.z - pi.z, B.L[2], sz);
                 // -g d, the neighbour's share, from the negated radial factors (no negation)
                 const double ngr = fma(pi.w + pj.w, e.y, e.x);
                 const double ngx = ngr * dx, ngy = ngr * dy, ngz = ngr * dz;
                 fx -= ngx;
                 fy -= ngy;
                 fz -= ngz;
-                if (ENERGY) {   // the pair's whole virial, once (its energy is in E_i and E_j)
-                    wxx = fma(ngx, dx, wxx);
-                    wyy = fma(ngy, dy, wyy);
-                    wzz = fma(ngz, dz, wzz);
-                    wyz = fma(ngy, dz, wyz);
-                    wxz = fma(ngx, dz, wxz);
-                    wxy = fma(ngx, dy, wxy);
-                }
+                if (ENERGY && W::value) virial_shift(sx, sy, sz, ngx, ngy, ngz, wxx, wyy, wzz, wyz, wxz, wxy);
                 double *acc = reinterpret_cast<double *>(A.f_acc + j);
                 atomicAdd(acc, ngx);
                 atomicAdd(acc + 1, ngy);
@@ -1001,8 +1026,9 @@ __device__ __forceinline__ void density64_pairs_flat(const Atoms &A, const Pot &
                 rho += phi;
                 atomicAdd(A.rho_acc + j, phi);
                 if (energy) {   // each atom of the pair gets half its pair energy
-                    ep = fma(0.5, V, ep);
-                    atomicAdd(A.e_acc + j, 0.5 * V);
+                    const double hV = half64(V);
+                    ep += hV;
+                    atomicAdd(A.e_acc + j, hV);
                 }
                 *dc = make_double2(-dV * rinv, -dphi * rinv);   // negated (the force pass needs -g)
             }
@@ -1068,12 +1094,12 @@ __device__ __forceinline__ void force64_pairs_flat(const Atoms &A, const Pot &P,
                     pi = ld_phase(A.p2d + i);
                 }
                 const double4_32a pj = ld_phase(A.p2d + j);
-                double dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+                double dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z, sx = 0.0, sy = 0.0, sz = 0.0;
                 if (W::value) {
                     const Box &B = boxes[ph::replica_of(A, i)];
-                    dx = mi64(dx, B.L[0], B.invL[0]);
-                    dy = mi64(dy, B.L[1], B.invL[1]);
-                    dz = mi64(dz, B.L[2], B.invL[2]);
+                    dx = mi64s(dx, B.L[0], sx);
+                    dy = mi64s(dy, B.L[1], sy);
+                    dz = mi64s(dz, B.L[2], sz);
                 }
                 // -g d, the neighbour's share, from the negated radial factors (no negation)
                 const double ngr = fma(pi.w + pj.w, d.y, d.x);
@@ -1081,14 +1107,7 @@ __device__ __forceinline__ void force64_pairs_flat(const Atoms &A, const Pot &P,
                 fx -= ngx;
                 fy -= ngy;
                 fz -= ngz;
-                if (ENERGY) {   // the pair's whole virial, once (its energy is in E_i and E_j)
-                    wxx = fma(ngx, dx, wxx);
-                    wyy = fma(ngy, dy, wyy);
-                    wzz = fma(ngz, dz, wzz);
-                    wyz = fma(ngy, dz, wyz);
-                    wxz = fma(ngx, dz, wxz);
-                    wxy = fma(ngx, dy, wxy);
-                }
+                if (ENERGY && W::value) virial_shift(sx, sy, sz, ngx, ngy, ngz, wxx, wyy, wzz, wyz, wxz, wxy);
                 double *acc = reinterpret_cast<double *>(A.f_acc + j);
                 atomicAdd(acc, ngx);
                 atomicAdd(acc + 1, ngy);
@@ -1140,6 +1159,14 @@ __device__ __forceinline__ void pairs_kick64(const Atoms &A, int i, double half_
     double4_32a v = A.vel[i];
     finish_motion(A, i, v, fx, fy, fz, half_dt, motion);
     if (ENERGY) {
+        // the virial's per-atom part x_a F_b (virial_shift), x as the force pass took it
+        const double4_32a x = A.p2d[i];
+        part[2] = fma(x.x, fx, part[2]);
+        part[3] = fma(x.y, fy, part[3]);
+        part[4] = fma(x.z, fz, part[4]);
+        part[5] = fma(x.y, fz, part[5]);
+        part[6] = fma(x.x, fz, part[6]);
+        part[7] = fma(x.x, fy, part[7]);
         const double e = A.e_atom[i];
         const double m = 1.0 / (kMvv2e * v.w);
         part[0] += e;
