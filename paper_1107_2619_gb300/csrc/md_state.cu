@@ -78,26 +78,62 @@ __global__ void k_unsort_list(Atoms A, int32_t *dst) {
 }
 
 // The same two copies for a caller buffer in mapped pinned host memory, read and written by the
-// device over the host link: thread c takes the caller's atom c, so that consecutive threads
-// touch consecutive host bytes, and reaches the cell-ordered slot rank[c] in device memory.
-__global__ void k_sort_in_mapped(Atoms A, const double *src, double4_32a *dst) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= A.n) return;
-    const int k = A.rank[c];
+// device over the host link.  A block takes the caller's atoms c0 .. c0 + kThreads - 1, whose 3
+// doubles each are one contiguous host range: it is moved in 16-byte pieces by consecutive
+// threads (whole lines over the link; the range starts 16-byte aligned when the buffer does, as
+// 24 kThreads is a multiple of 16), staged in shared memory, and each thread c reaches the
+// cell-ordered slot rank[c] in device memory.  VEC = false: 8-byte pieces, for a buffer that is
+// not 16-byte aligned.
+template <bool VEC>
+__device__ __forceinline__ void host_range_in(const double *src, double *sh, int c0, int nb) {
+    const int m = 3 * nb;   // doubles of this block
+    if (VEC) {
+        const double2 *s2 = reinterpret_cast<const double2 *>(src + 3 * (size_t)c0);
+        for (int q = threadIdx.x; q < m / 2; q += blockDim.x) reinterpret_cast<double2 *>(sh)[q] = s2[q];
+        if ((m & 1) && threadIdx.x == 0) sh[m - 1] = src[3 * (size_t)c0 + m - 1];
+    } else {
+        for (int q = threadIdx.x; q < m; q += blockDim.x) sh[q] = src[3 * (size_t)c0 + q];
+    }
+}
+template <bool VEC>
+__device__ __forceinline__ void host_range_out(double *dst, const double *sh, int c0, int nb) {
+    const int m = 3 * nb;
+    if (VEC) {
+        double2 *d2 = reinterpret_cast<double2 *>(dst + 3 * (size_t)c0);
+        for (int q = threadIdx.x; q < m / 2; q += blockDim.x) d2[q] = reinterpret_cast<const double2 *>(sh)[q];
+        if ((m & 1) && threadIdx.x == 0) dst[3 * (size_t)c0 + m - 1] = sh[m - 1];
+    } else {
+        for (int q = threadIdx.x; q < m; q += blockDim.x) dst[3 * (size_t)c0 + q] = sh[q];
+    }
+}
+
+template <bool VEC>
+__global__ void __launch_bounds__(kThreads) k_sort_in_mapped(Atoms A, const double *src, double4_32a *dst) {
+    __shared__ __align__(16) double sh[3 * kThreads];
+    const int c0 = blockIdx.x * kThreads, nb = min(kThreads, A.n - c0);
+    host_range_in<VEC>(src, sh, c0, nb);
+    __syncthreads();
+    if ((int)threadIdx.x >= nb) return;
+    const int k = A.rank[c0 + threadIdx.x];
     double4_32a v = dst[k];
-    v.x = src[3 * (size_t)c];
-    v.y = src[3 * (size_t)c + 1];
-    v.z = src[3 * (size_t)c + 2];
+    v.x = sh[3 * threadIdx.x];
+    v.y = sh[3 * threadIdx.x + 1];
+    v.z = sh[3 * threadIdx.x + 2];
     dst[k] = v;
 }
 
-__global__ void k_unsort_mapped(Atoms A, const double4_32a *src, double *dst) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= A.n) return;
-    const double4_32a v = src[A.rank[c]];
-    dst[3 * (size_t)c] = v.x;
-    dst[3 * (size_t)c + 1] = v.y;
-    dst[3 * (size_t)c + 2] = v.z;
+template <bool VEC>
+__global__ void __launch_bounds__(kThreads) k_unsort_mapped(Atoms A, const double4_32a *src, double *dst) {
+    __shared__ __align__(16) double sh[3 * kThreads];
+    const int c0 = blockIdx.x * kThreads, nb = min(kThreads, A.n - c0);
+    if ((int)threadIdx.x < nb) {
+        const double4_32a v = src[A.rank[c0 + threadIdx.x]];
+        sh[3 * threadIdx.x] = v.x;
+        sh[3 * threadIdx.x + 1] = v.y;
+        sh[3 * threadIdx.x + 2] = v.z;
+    }
+    __syncthreads();
+    host_range_out<VEC>(dst, sh, c0, nb);
 }
 
 __global__ void k_sort_in_vec(Atoms A, const double *src, double4_32a *dst) {
@@ -192,13 +228,19 @@ cudaError_t launch_sort_in_vec(const Atoms &A, const double *src, double4_32a *d
 
 cudaError_t launch_sort_in_mapped(const Atoms &A, const double *src, double4_32a *dst, cudaStream_t s) {
     if (A.n == 0) return cudaSuccess;
-    k_sort_in_mapped<<<blocks_for(A.n, kThreads), kThreads, 0, s>>>(A, src, dst);
+    if (reinterpret_cast<uintptr_t>(src) % 16 == 0)
+        k_sort_in_mapped<true><<<blocks_for(A.n, kThreads), kThreads, 0, s>>>(A, src, dst);
+    else
+        k_sort_in_mapped<false><<<blocks_for(A.n, kThreads), kThreads, 0, s>>>(A, src, dst);
     return cudaGetLastError();
 }
 
 cudaError_t launch_unsort_mapped(const Atoms &A, const double4_32a *src, double *dst, cudaStream_t s) {
     if (A.n == 0) return cudaSuccess;
-    k_unsort_mapped<<<blocks_for(A.n, kThreads), kThreads, 0, s>>>(A, src, dst);
+    if (reinterpret_cast<uintptr_t>(dst) % 16 == 0)
+        k_unsort_mapped<true><<<blocks_for(A.n, kThreads), kThreads, 0, s>>>(A, src, dst);
+    else
+        k_unsort_mapped<false><<<blocks_for(A.n, kThreads), kThreads, 0, s>>>(A, src, dst);
     return cudaGetLastError();
 }
 

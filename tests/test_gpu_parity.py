@@ -322,6 +322,40 @@ def test_step_io_equals_the_separate_calls(device):
         assert np.array_equal(p1, a.positions()) and e["pe"] == a.energy()["pe"]
 
 
+@pytest.mark.parametrize("offset", [0, 1])
+def test_step_io_pinned_ragged_and_unaligned(offset):
+    """The direct pinned-buffer copies move each block's range in 16-byte pieces when the buffer
+    is 16-byte aligned, 8-byte pieces when it is not (offset 1: the arrays start one double into a
+    pinned allocation): 2,047 atoms (15 full blocks of 128 and a last one of 127, an odd number of
+    doubles), bitwise against the separate calls."""
+    import dataclasses
+    torch = pytest.importorskip("torch")
+    w = I.fcc_cu(8, seed=33, sigma=0.03)
+    w = dataclasses.replace(w, pos=w.pos[:-1].copy(), vel=w.vel[:-1].copy(), species=w.species[:-1].copy())
+    n = w.pos.shape[0]
+    assert n % 128 == 127
+    with _gpu_system(w, "fp64") as a, _gpu_system(w, "fp64") as b:
+        a.eam_forces()
+        b.eam_forces()
+        p, v, f = a.positions(), a.velocities(), a.forces()
+        bufs = []
+        for x in (p, v, f):
+            t = torch.empty(3 * n + offset, dtype=torch.float64).pin_memory()
+            view = t[offset:].view(n, 3)
+            view.copy_(torch.from_numpy(x))
+            bufs.append(view)
+        assert all((t.data_ptr() % 16 == 0) == (offset == 0) for t in bufs)
+        for _ in range(2):
+            b.set_state(p, v, f)
+            b.step(3)
+            p2, v2, f2, e2 = b.positions(), b.velocities(), b.forces(), b.energy()
+            e1 = a.step_io(3, *bufs, *bufs)
+            p1, v1, f1 = (t.numpy().copy() for t in bufs)
+            assert np.array_equal(p1, p2) and np.array_equal(v1, v2) and np.array_equal(f1, f2)
+            assert e1["pe"] == e2["pe"] and e1["ke"] == e2["ke"]
+            p, v, f = p1, v1, f1
+
+
 # --------------------------------------------------------------------------- edge cases
 def test_empty_and_single_atom_systems():
     pot = I.fs_fe_analytic()
