@@ -58,9 +58,17 @@ def test_strain_ramp():
         s.step(12)
         e = s.energy()
         pos = s.positions()
+        s.eam_forces()   # energies and virial at the final, strained state
+        ev = s.energy()
     assert e["n_rebuilds"] >= 4
     assert np.array_equal(e["box"], ref["box"])
     assert np.abs(pos - ref["pos"]).max() < 1e-9
+    # the pair walk's virial (atoms' x (x) F plus the image-shift terms of boundary pairs; under the
+    # ramp every warp takes the minimum image) against the oracle's pair form, same state
+    fv = oracle.forces(pos, w.species, e["box"], w.potential, skin=w.skin, k_max=w.k_max)
+    for got in (e, ev):   # the step kernel's last step, the stand-alone passes
+        assert np.abs(got["virial"] - fv["virial"]).max() <= TOL * np.abs(fv["virial"]).max()
+        assert abs(got["pe"] - fv["pe"]) <= TOL * abs(fv["pe"])
 
 
 def test_thermostat():
