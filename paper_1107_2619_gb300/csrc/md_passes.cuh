@@ -58,7 +58,7 @@ __device__ __forceinline__ double sep64s(double d, double L, double &s) {
 __device__ __forceinline__ void virial_shift(double sx, double sy, double sz, double ngx, double ngy, double ngz,
                                              double &wxx, double &wyy, double &wzz, double &wyz, double &wxz,
                                              double &wxy) {
-    if ((__double_as_longlong(sx) | __double_as_longlong(sy) | __double_as_longlong(sz)) << 1) {
+    if (((unsigned long long)(__double_as_longlong(sx) | __double_as_longlong(sy) | __double_as_longlong(sz))) << 1) {
         wxx = fma(-sx, ngx, wxx);
         wyy = fma(-sy, ngy, wyy);
         wzz = fma(-sz, ngz, wzz);
@@ -915,7 +915,7 @@ constexpr int kFlatLanes = 4;
 // it only where it is not zero (a bit-pattern test: the skin segment's sums mostly are).
 __device__ __forceinline__ void put_slot(double *s, double v, int seg) {
     if (seg == 0) *s = v;
-    else if (__double_as_longlong(v) << 1) *s += v;
+    else if ((unsigned long long)__double_as_longlong(v) << 1) *s += v;
 }
 
 // Atom a's sum of slot row q over the warp's 32 lanes, in the T lanes of atom a (butterfly).
